@@ -1,0 +1,169 @@
+"""Seeded synthetic inputs for the phaseless-AFQMC hot path.
+
+This module is shared by the oracle, the tests and the benchmark.  It holds
+none of the method's arithmetic: it only draws the Hamiltonian (one-body
+integrals h1e, Cholesky vectors L[naux, N, N], constant E0) and builds the
+single-determinant trial that the method takes as input.
+
+The paper's workloads are molecules (the S22 benzene dimer and [Cu2O2]2+,
+Section "Distributed Hamiltonian" and "GPU accelerated MSD-AFQMC"); their
+integrals are not available, so these generators produce inputs with the same
+shapes (N orbitals, electron counts, naux, walker count) and the structure of
+real Cholesky factorisations: symmetric L^gamma whose norms decay
+geometrically, so that sum_gamma L^gamma (x) L^gamma is a positive
+semidefinite ERI tensor (Eq. 3).
+
+The trial determinant comes from a plain restricted / unrestricted Hartree-Fock
+fixed-point iteration (a fixed number of Roothaan steps from the core guess, no
+damping or DIIS).  It is an input-preparation step, not part of the AFQMC
+method, and any determinant would do for parity.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+BASE_SEED = 240616238
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic Hamiltonian plus trial (all float64, C-contiguous)."""
+
+    h1e: np.ndarray      # [N, N] real symmetric
+    chol: np.ndarray     # [naux, N, N] real symmetric per gamma
+    ecore: float
+    nalpha: int
+    nbeta: int
+    psiT: np.ndarray     # [N, nalpha + nbeta], alpha columns first
+    name: str = ""
+
+    @property
+    def norb(self) -> int:
+        return self.h1e.shape[0]
+
+    @property
+    def naux(self) -> int:
+        return self.chol.shape[0]
+
+
+def _sym_gaussian(rng, n):
+    a = rng.standard_normal((n, n))
+    return 0.5 * (a + a.T)
+
+
+def cholesky_vectors(rng, norb: int, naux: int, tau: float, orthogonalise: bool = True) -> np.ndarray:
+    """L^gamma = exp(-gamma/tau) * S_gamma / ||S_gamma||_F with S_gamma random symmetric.
+
+    With orthogonalise=True the vec(S_gamma) are Gram-Schmidt orthonormalised
+    first (needs naux <= N(N+1)/2), so the singular values of the
+    [naux, N*N] Cholesky matrix are exactly exp(-gamma/tau).
+    """
+    s = np.empty((naux, norb, norb))
+    for g in range(naux):
+        s[g] = _sym_gaussian(rng, norb)
+    flat = s.reshape(naux, norb * norb)
+    if orthogonalise:
+        if naux > norb * (norb + 1) // 2:
+            raise ValueError("naux exceeds the dimension of symmetric matrices")
+        q, r = np.linalg.qr(flat.T)           # columns orthonormal
+        q = q * np.sign(np.diag(r))[None, :]
+        flat = q.T.copy()
+    else:
+        flat = flat / np.linalg.norm(flat, axis=1, keepdims=True)
+    scale = np.exp(-np.arange(naux) / tau)
+    chol = (flat * scale[:, None]).reshape(naux, norb, norb)
+    # exact symmetry (Gram-Schmidt keeps it up to rounding)
+    chol = 0.5 * (chol + chol.transpose(0, 2, 1))
+    return np.ascontiguousarray(chol)
+
+
+def one_body(rng, norb: int, ramp: float = 4.0, noise: float = 0.1) -> np.ndarray:
+    """Diagonal ramp 0..ramp Ha plus symmetric N(0, noise^2) off-diagonal."""
+    h = np.diag(np.linspace(0.0, ramp, norb))
+    off = rng.standard_normal((norb, norb)) * noise
+    off = np.triu(off, 1)
+    return np.ascontiguousarray(h + off + off.T)
+
+
+def _coulomb(chol, dm):
+    return np.einsum("gpq,g->pq", chol, np.einsum("gpq,qp->g", chol, dm))
+
+
+def _exchange(chol, dm):
+    return np.einsum("gpr,rs,gsq->pq", chol, dm, chol, optimize=True)
+
+
+def hartree_fock_trial(h1e, chol, nalpha, nbeta, iterations=20, unrestricted=False):
+    """Trial orbitals [N, nalpha+nbeta] from plain Roothaan iterations.
+
+    RHF: F = h + 2J[P] - K[P] with P the per-spin density of the nalpha lowest
+    orbitals.  UHF: F^s = h + J[Pa+Pb] - K[P^s]; the beta guess mixes its HOMO
+    and LUMO by pi/4 to break spin symmetry.
+    """
+    norb = h1e.shape[0]
+    _, c = np.linalg.eigh(h1e)
+    if not unrestricted:
+        if nalpha != nbeta:
+            raise ValueError("restricted trial needs nalpha == nbeta")
+        for _ in range(iterations):
+            occ = c[:, :nalpha]
+            dm = occ @ occ.T
+            fock = h1e + 2.0 * _coulomb(chol, dm) - _exchange(chol, dm)
+            _, c = np.linalg.eigh(fock)
+        occ = c[:, :nalpha]
+        return np.ascontiguousarray(np.hstack([occ, occ]))
+    ca = c.copy()
+    cb = c.copy()
+    if nbeta < norb and nbeta > 0:
+        h, l = cb[:, nbeta - 1].copy(), cb[:, nbeta].copy()
+        cb[:, nbeta - 1] = (h + l) / np.sqrt(2.0)
+        cb[:, nbeta] = (l - h) / np.sqrt(2.0)
+    for _ in range(iterations):
+        da = ca[:, :nalpha] @ ca[:, :nalpha].T
+        db = cb[:, :nbeta] @ cb[:, :nbeta].T
+        j = _coulomb(chol, da + db)
+        _, ca = np.linalg.eigh(h1e + j - _exchange(chol, da))
+        _, cb = np.linalg.eigh(h1e + j - _exchange(chol, db))
+    return np.ascontiguousarray(np.hstack([ca[:, :nalpha], cb[:, :nbeta]]))
+
+
+def make_problem(norb, nalpha, nbeta, naux, tau, seed, unrestricted=False,
+                 ecore=1.5, orthogonalise=None, scf_iterations=20, name="") -> Problem:
+    rng = np.random.default_rng(seed)
+    h1e = one_body(rng, norb)
+    if orthogonalise is None:
+        orthogonalise = norb <= 300 and naux <= norb * (norb + 1) // 2
+    chol = cholesky_vectors(rng, norb, naux, tau, orthogonalise)
+    psiT = hartree_fock_trial(h1e, chol, nalpha, nbeta, scf_iterations, unrestricted)
+    return Problem(h1e, chol, float(ecore), nalpha, nbeta, psiT, name)
+
+
+# Workload shapes (walker counts and step counts live with the runner).
+def config_small(seed_offset=1):
+    """N=8, 2a+2b, naux=24, tau=4, RHF (20 SCF iterations)."""
+    return make_problem(8, 2, 2, 24, 4.0, BASE_SEED + seed_offset, name="N8_n2_X24")
+
+
+def config_medium(seed_offset=2):
+    """N=108, 21a+21b, naux=432, tau=40, RHF: the 108-orbital / 640-walker shape."""
+    return make_problem(108, 21, 21, 432, 40.0, BASE_SEED + seed_offset, name="N108_n21_X432")
+
+
+def config_cv(seed_offset=5):
+    """N=300, 25a+25b, naux=1500, tau=150, RHF."""
+    return make_problem(300, 25, 25, 1500, 150.0, BASE_SEED + seed_offset, name="N300_n25_X1500")
+
+
+def tiny_problem(norb=4, nalpha=2, nbeta=2, naux=6, tau=3.0, seed=7, unrestricted=False, ecore=0.7):
+    """4-orbital systems small enough for brute-force Fock-space checks."""
+    return make_problem(norb, nalpha, nbeta, naux, tau, seed, unrestricted=unrestricted,
+                        ecore=ecore, orthogonalise=True)
+
+
+def random_walkers(rng, norb, ncols, nwalkers, spread=0.3, psiT=None):
+    """Complex determinants near psiT (or random), for kernel-level parity cases."""
+    base = psiT if psiT is not None else rng.standard_normal((norb, ncols))
+    noise = rng.standard_normal((nwalkers, norb, ncols)) + 1j * rng.standard_normal((nwalkers, norb, ncols))
+    return np.ascontiguousarray(base[None, :, :] + spread * noise)
