@@ -1,0 +1,187 @@
+/*
+ * afqmc.h -- C ABI of the B300 (sm_103a) phaseless-AFQMC hot path.
+ *
+ * The library propagates a batch of single-determinant walkers under a
+ * Cholesky-factorised ab initio Hamiltonian with a single-determinant RHF/UHF
+ * trial, and measures the mixed local energy.  Equation numbers refer to
+ * arXiv:2406.16238 ("Improved Modularity and New Features in ipie"),
+ * Section "Theory of AFQMC":
+ *
+ *   Eq. 2-3   H = sum h_pq a+_p a_q + 1/2 sum g_psqr a+_p a+_q a_r a_s,
+ *             g_psqr = sum_gamma L^gamma_ps L^gamma_qr         (inputs h1e, chol)
+ *   Eq. 4-6   H = v0 - 1/2 sum v_gamma^2, v_gamma = i sum L^gamma a+a
+ *   Eq. 7-8   symmetric Trotter split and B(x) = e^{-dt/2 v0} e^{-sqrt(dt) x.v} e^{-dt/2 v0}
+ *   Eq. 9     mixed energy estimator E = sum w E_loc                (afqmc_local_energy)
+ *   Eq. 10-11 walker and weight update with shifted fields     (afqmc_propagate)
+ *   Eq. 12    force bias with the mean-field shift
+ *   Eq. 13-16 phaseless / hybrid importance function, overlap ratio, phase
+ * plus the stabilisation and population control the driver performs each
+ * block (Section "AFQMC driver"; afqmc_reortho, afqmc_popcontrol).
+ *
+ * Conventions (all calls):
+ *   - Host arrays are row-major, float64, C-contiguous, owned by the caller
+ *     and only read during the call (or written, for outputs).
+ *   - Complex host arrays are interleaved (re, im) float64 pairs.
+ *   - Device memory is never allocated by the library: the caller passes one
+ *     device workspace of afqmc_workspace_size() bytes to afqmc_create and
+ *     keeps it alive until afqmc_destroy.
+ *   - Every call is ordered on the stream given in afqmc_params (NULL = the
+ *     legacy default stream).  Calls that return host data synchronise that
+ *     stream; afqmc_propagate, afqmc_reortho and afqmc_popcontrol only enqueue.
+ *   - Errors are returned as afqmc_status; afqmc_last_error() gives a
+ *     thread-local message.  Device-side conditions (a singular overlap, a
+ *     non-finite weight, all weights zero) are recorded in a device status word
+ *     and reported by the next synchronising call; the offending walkers get
+ *     weight 0.  No call traps or aborts.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afqmc_ctx afqmc_ctx;
+
+typedef enum {
+  AFQMC_OK = 0,
+  AFQMC_EINVAL = 1,       /* bad argument (sizes, NaN input, non-symmetric L, ...) */
+  AFQMC_ENOMEM = 2,       /* workspace smaller than afqmc_workspace_size() */
+  AFQMC_ECUDA = 3,        /* a CUDA runtime call or launch failed */
+  AFQMC_ESINGULAR = 4,    /* a walker's overlap matrix had a zero pivot (walker weight set to 0) */
+  AFQMC_ENONFINITE = 5,   /* a walker's weight became NaN/Inf (walker weight set to 0) */
+  AFQMC_ENOWALKERS = 6,   /* every walker weight is zero: population control cannot proceed */
+  AFQMC_ETIMEOUT = 7      /* afqmc_synchronize gave up waiting */
+} afqmc_status;
+
+/* Arithmetic of the three large contractions (force bias, VHS build, exchange).
+ * FP64: walkers complex128, every product and sum in binary64.
+ * FP32: walkers complex64, contractions in binary32 (CUDA cores).
+ * BF16: walkers complex64, contractions on the tcgen05 tensor cores with bf16
+ *       operands (L scaled per gamma by s_gamma = max|L^gamma|) and fp32
+ *       accumulation.
+ * BF16X3: as BF16, but each fp32 operand is split into bf16 hi + lo parts and
+ *       the products hi*hi + hi*lo + lo*hi are accumulated in fp32.
+ * In every form the n x n overlap inverses and log-determinants, the phases
+ * and weights, QR reorthogonalisation and the energy reductions are binary64. */
+typedef enum { AFQMC_PREC_FP64 = 0, AFQMC_PREC_FP32 = 1, AFQMC_PREC_BF16 = 2, AFQMC_PREC_BF16X3 = 3 } afqmc_prec;
+
+typedef struct {
+  double dt;              /* imaginary time step Delta tau (> 0) */
+  int32_t nwalkers;       /* walkers W (>= 1) */
+  int32_t taylor_order;   /* terms of the exp(VHS) Taylor series (1..12; 6 usual) */
+  double fb_cap;          /* |xbar_gamma| cap (<= 0: no cap) */
+  uint64_t seed;          /* Philox4x32-10 key */
+  int32_t prec;           /* afqmc_prec */
+  int32_t reserved;       /* must be 0 */
+  double e_trial;         /* energy shift E_T of the weights; NaN -> the trial's variational energy */
+  void* stream;           /* cudaStream_t the context works on (NULL: default stream) */
+} afqmc_params;
+
+typedef struct {
+  int32_t norb, naux, nalpha, nbeta, nwalkers;
+  int32_t restricted;     /* 1: RHF trial with nalpha == nbeta, one spin block stored and propagated */
+  int32_t prec;
+  int32_t reserved;
+  uint64_t step;          /* completed propagation steps (the Philox step counter) */
+  double e_var;           /* <Psi_T|H|Psi_T> as measured by the library at create */
+  double e_trial;         /* energy shift in use */
+  double e_core_mf;       /* E_c = E0 - 1/2 sum lbar^2 (mean-field constant) */
+  size_t workspace_bytes;
+} afqmc_info;
+
+/* Bytes of device workspace that afqmc_create needs for these sizes.
+ * psiT [norb, nalpha+nbeta] (host) decides whether the trial is restricted. */
+afqmc_status afqmc_workspace_size(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta,
+                                  const double* psiT, const afqmc_params* params, size_t* bytes);
+
+/* Build a context (the paper's HamGeneric(h1e, chol, ecore) + SingleDet(psiT) +
+ * AFQMC.build, Sections "Hamiltonian", "Trial wavefunctions", "AFQMC driver").
+ *   h1e   [norb, norb]          one-body integrals h_pq, symmetric
+ *   chol  [naux, norb, norb]    Cholesky vectors L^gamma_pq, each symmetric (Eq. 3)
+ *   ecore                       constant E0
+ *   psiT  [norb, nalpha+nbeta]  trial orbitals, alpha columns first (real)
+ * Precomputes on the device: the mean-field shift lbar_gamma = Tr L^gamma P_T,
+ * h_eff = h - 1/2 sum L L + sum lbar L and exp(-dt/2 h_eff), the half-rotated
+ * Ltilde^gamma = Phi^T L^gamma and htilde = Phi^T h, and initialises every walker
+ * to psiT with weight 1.  Limits: 1 <= nalpha, 0 <= nbeta, nalpha, nbeta <= min(norb, 64).
+ * workspace: device pointer, 256-byte aligned, >= afqmc_workspace_size() bytes. */
+afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore,
+                          int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta,
+                          const double* psiT, const afqmc_params* params,
+                          void* workspace, size_t workspace_bytes, afqmc_ctx** out);
+
+/* nsteps phaseless steps (Eqs. 10-16), each: Green's function / Theta and the
+ * force bias at the current walkers (reused from afqmc_local_energy when it
+ * was measured at the same walkers), Philox fields x with counter = the step,
+ * shifted fields, VHS = -i sqrt(dt) sum_g (x - xbar)_g L^g, walkers
+ * exp(-dt/2 h_eff) exp_Taylor(VHS) exp(-dt/2 h_eff) psi, new overlaps, weights
+ * w |I| max(0, cos theta) exp(dt (E_T - E_c)).  Walkers of weight 0 are frozen. */
+afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps);
+
+/* Mixed local energy (Eq. 9) of every walker and the estimator sums
+ *   sums[4] = {ENumer = sum w Re E_L, EDenom = sum w, E1Body = sum w Re(E0 + E1),
+ *              E2Body = sum w Re(J - K)}   (host, may be NULL)
+ *   eloc    [nwalkers][3][2] (host, may be NULL): (E_L, E0 + E1, J - K) per walker.
+ * Synchronises the stream when either output is non-NULL. */
+afqmc_status afqmc_local_energy(afqmc_ctx* ctx, double* sums, double* eloc);
+
+/* QR stabilisation of every walker: psi^s = Q R with diag(R) > 0, psi^s <- Q,
+ * log O -= sum log R_ii (all binary64). */
+afqmc_status afqmc_reortho(afqmc_ctx* ctx);
+
+/* Comb population control: ordered prefix of the weights, one uniform xi
+ * (Philox stream 1, counter = the step), teeth ((k + xi) W_tot) / W, copies in
+ * ascending walker order, all weights <- W_tot / W. */
+afqmc_status afqmc_popcontrol(afqmc_ctx* ctx);
+
+/* The driver loop on the device: for each of nsteps steps, the energy when
+ * step % energy_every == 0 (energy_every <= 0: never), one propagation step,
+ * then QR when the new step count is a multiple of reortho_every and the comb
+ * when it is a multiple of comb_every (<= 0: never).  energies (host, may be
+ * NULL) receives 4 sums per measurement in order; nmeas (may be NULL) their
+ * count.  One synchronisation at the end. */
+afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
+                       int32_t comb_every, double* energies, int32_t* nmeas);
+
+/* Walker state (checkpoint / resume; bit-exact resume since the fields are
+ * counter-based).  psi [nwalkers][norb][nalpha+nbeta][2] complex, logO
+ * [nwalkers][2], w [nwalkers], step.  Any output may be NULL.  For a
+ * restricted context afqmc_set_walkers requires identical alpha and beta blocks. */
+afqmc_status afqmc_get_walkers(afqmc_ctx* ctx, double* psi, double* logO, double* w, uint64_t* step);
+afqmc_status afqmc_set_walkers(afqmc_ctx* ctx, const double* psi, const double* w, uint64_t step);
+
+/* Fields of the most recent propagation step: x [nwalkers][naux] and the force
+ * bias shift xbar [nwalkers][naux][2] (either may be NULL). */
+afqmc_status afqmc_get_fields(afqmc_ctx* ctx, double* x, double* xbar);
+
+/* Standalone field draw: out[w][gamma] ~ N(0,1) for walker slots w < nwalkers,
+ * gamma < naux, from Philox4x32-10 with key = seed and counter
+ * (gamma / 2, w, step mod 2^32, (step >> 32) mod 2^16 | stream_id << 16),
+ * Box-Muller with series log / sin / cos (bit-reproducible).  out: device,
+ * nwalkers * naux doubles.  stream: cudaStream_t or NULL. */
+afqmc_status afqmc_draw_normals(uint64_t seed, uint64_t step, uint32_t stream_id, int32_t nwalkers,
+                                int32_t naux, double* out, void* stream);
+
+afqmc_status afqmc_get_info(afqmc_ctx* ctx, afqmc_info* info);
+afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial);
+
+/* Wait for the context's stream, polling, for at most timeout_s seconds. */
+afqmc_status afqmc_synchronize(afqmc_ctx* ctx, double timeout_s);
+
+/* Free host-side state (the caller frees the workspace afterwards). */
+void afqmc_destroy(afqmc_ctx* ctx);
+
+/* Number of kernel launches the context has issued (for launch accounting). */
+uint64_t afqmc_launch_count(afqmc_ctx* ctx);
+
+const char* afqmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -1,0 +1,228 @@
+"""ctypes binding of libafqmc.so (the C ABI declared in include/afqmc.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device workspace and the stream.  There
+is no fallback: if the library is missing or cannot be loaded, importing the
+binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libafqmc.so")
+
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3}
+STATUS = {0: "AFQMC_OK", 1: "AFQMC_EINVAL", 2: "AFQMC_ENOMEM", 3: "AFQMC_ECUDA", 4: "AFQMC_ESINGULAR",
+          5: "AFQMC_ENONFINITE", 6: "AFQMC_ENOWALKERS", 7: "AFQMC_ETIMEOUT"}
+
+
+class AfqmcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("nwalkers", ctypes.c_int32), ("taylor_order", ctypes.c_int32),
+                ("fb_cap", ctypes.c_double), ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("e_trial", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("norb", ctypes.c_int32), ("naux", ctypes.c_int32), ("nalpha", ctypes.c_int32),
+                ("nbeta", ctypes.c_int32), ("nwalkers", ctypes.c_int32), ("restricted", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32), ("step", ctypes.c_uint64),
+                ("e_var", ctypes.c_double), ("e_trial", ctypes.c_double), ("e_core_mf", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_u64 = ctypes.c_uint64
+
+# name -> (restype, argtypes); every symbol include/afqmc.h declares
+SIGNATURES = {
+    "afqmc_workspace_size": (_i32, [_i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
+    "afqmc_create": (_i32, [_dp, _dp, ctypes.c_double, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params), _vp,
+                            ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "afqmc_propagate": (_i32, [_vp, _i32]),
+    "afqmc_local_energy": (_i32, [_vp, _dp, _dp]),
+    "afqmc_reortho": (_i32, [_vp]),
+    "afqmc_popcontrol": (_i32, [_vp]),
+    "afqmc_run": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
+    "afqmc_get_walkers": (_i32, [_vp, _dp, _dp, _dp, ctypes.POINTER(_u64)]),
+    "afqmc_set_walkers": (_i32, [_vp, _dp, _dp, _u64]),
+    "afqmc_get_fields": (_i32, [_vp, _dp, _dp]),
+    "afqmc_draw_normals": (_i32, [_u64, _u64, ctypes.c_uint32, _i32, _i32, _vp, _vp]),
+    "afqmc_get_info": (_i32, [_vp, ctypes.POINTER(Info)]),
+    "afqmc_set_etrial": (_i32, [_vp, ctypes.c_double]),
+    "afqmc_synchronize": (_i32, [_vp, ctypes.c_double]),
+    "afqmc_destroy": (None, [_vp]),
+    "afqmc_launch_count": (_u64, [_vp]),
+    "afqmc_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libafqmc.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing; build it with `python -m paper_2406_16238_b300.build` "
+                          "(or __graft_entry__.build())")
+    try:
+        import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    except ImportError:
+        pass
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise AfqmcError(status, load().afqmc_last_error().decode(errors="replace"))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and a.shape != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Afqmc:
+    """One walker batch of phaseless AFQMC on the current CUDA device (afqmc_create ... afqmc_destroy)."""
+
+    def __init__(self, h1e, chol, ecore, nalpha, nbeta, psiT, *, nwalkers, dt=0.005, taylor_order=6, fb_cap=1.0,
+                 seed=0, prec="fp64", e_trial=None, device=None, stream=None):
+        import torch
+        lib = load()
+        self.h1e = _f64(h1e)
+        norb = self.h1e.shape[0]
+        self.chol = _f64(chol)
+        naux = self.chol.shape[0]
+        if self.chol.shape != (naux, norb, norb):
+            raise ValueError("chol must be [naux, norb, norb]")
+        self.psiT = _f64(psiT, (norb, nalpha + nbeta))
+        self.norb, self.naux, self.nalpha, self.nbeta, self.nwalkers = norb, naux, nalpha, nbeta, int(nwalkers)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.prec = prec
+        self.params = Params(float(dt), int(nwalkers), int(taylor_order), float(fb_cap), int(seed) & (2 ** 64 - 1),
+                             PREC[prec], 0, math.nan if e_trial is None else float(e_trial),
+                             ctypes.c_void_p(self.stream.cuda_stream))
+        nbytes = ctypes.c_size_t()
+        _check(lib.afqmc_workspace_size(norb, naux, nalpha, nbeta, _ptr(self.psiT), ctypes.byref(self.params),
+                                        ctypes.byref(nbytes)))
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        _check(lib.afqmc_create(_ptr(self.h1e), _ptr(self.chol), float(ecore), norb, naux, nalpha, nbeta,
+                                _ptr(self.psiT), ctypes.byref(self.params), ctypes.c_void_p(self.workspace.data_ptr()),
+                                nbytes.value, ctypes.byref(ctx)))
+        self._ctx = ctx
+        self._lib = lib
+
+    # --- the hot path -------------------------------------------------------------------
+    def propagate(self, nsteps=1):
+        _check(self._lib.afqmc_propagate(self._ctx, int(nsteps)))
+
+    def local_energy(self, per_walker=False):
+        sums = np.zeros(4)
+        eloc = np.zeros((self.nwalkers, 3, 2)) if per_walker else None
+        _check(self._lib.afqmc_local_energy(self._ctx, _ptr(sums), _ptr(eloc) if per_walker else None))
+        if per_walker:
+            return sums, eloc[..., 0] + 1j * eloc[..., 1]
+        return sums
+
+    def reortho(self):
+        _check(self._lib.afqmc_reortho(self._ctx))
+
+    def popcontrol(self):
+        _check(self._lib.afqmc_popcontrol(self._ctx))
+
+    def run(self, nsteps, energy_every=1, reortho_every=5, comb_every=10):
+        nmax = (nsteps + energy_every - 1) // energy_every + 1 if energy_every > 0 else 1
+        out = np.zeros((nmax, 4))
+        nmeas = ctypes.c_int32()
+        _check(self._lib.afqmc_run(self._ctx, int(nsteps), int(energy_every), int(reortho_every), int(comb_every),
+                                   _ptr(out), ctypes.byref(nmeas)))
+        return out[: nmeas.value]
+
+    # --- state --------------------------------------------------------------------------
+    def get_walkers(self):
+        nt = self.nalpha + self.nbeta
+        psi = np.zeros((self.nwalkers, self.norb, nt, 2))
+        logo = np.zeros((self.nwalkers, 2))
+        w = np.zeros(self.nwalkers)
+        step = ctypes.c_uint64()
+        _check(self._lib.afqmc_get_walkers(self._ctx, _ptr(psi), _ptr(logo), _ptr(w), ctypes.byref(step)))
+        return psi[..., 0] + 1j * psi[..., 1], logo[:, 0] + 1j * logo[:, 1], w, int(step.value)
+
+    def set_walkers(self, psi, w, step):
+        psi = np.asarray(psi, dtype=np.complex128)
+        buf = _f64(np.stack([psi.real, psi.imag], axis=-1))
+        ww = _f64(w, (self.nwalkers,))
+        _check(self._lib.afqmc_set_walkers(self._ctx, _ptr(buf), _ptr(ww), int(step)))
+
+    def get_fields(self):
+        x = np.zeros((self.nwalkers, self.naux))
+        xb = np.zeros((self.nwalkers, self.naux, 2))
+        _check(self._lib.afqmc_get_fields(self._ctx, _ptr(x), _ptr(xb)))
+        return x, xb[..., 0] + 1j * xb[..., 1]
+
+    def info(self):
+        inf = Info()
+        _check(self._lib.afqmc_get_info(self._ctx, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def set_etrial(self, e):
+        _check(self._lib.afqmc_set_etrial(self._ctx, float(e)))
+
+    def synchronize(self, timeout_s=60.0):
+        _check(self._lib.afqmc_synchronize(self._ctx, float(timeout_s)))
+
+    def launch_count(self):
+        return int(self._lib.afqmc_launch_count(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self.stream.synchronize()
+            self._lib.afqmc_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def draw_normals(seed, step, nwalkers, naux, stream_id=0, device="cuda"):
+    """Philox fields x[w, gamma] on the device (afqmc_draw_normals); returns a float64 torch tensor."""
+    import torch
+    lib = load()
+    out = torch.empty((nwalkers, naux), dtype=torch.float64, device=device)
+    s = torch.cuda.current_stream(out.device)
+    _check(lib.afqmc_draw_normals(int(seed), int(step), int(stream_id), int(nwalkers), int(naux),
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+    return out

@@ -1,0 +1,895 @@
+// C ABI of the phaseless-AFQMC hot path (declared in include/afqmc.h).
+//
+// The context carves one caller-provided device workspace into the buffers of
+// the walker batch and the Hamiltonian store, runs the set-up, and enqueues
+// the kernels of each step on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+#include "afqmc.h"
+#include "kernels_simt.cuh"
+#include "tc_gemm.cuh"
+
+using namespace afq;
+
+namespace {
+
+thread_local char g_err[1024] = "";
+
+afqmc_status fail(afqmc_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CU(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(AFQMC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CHECK_LAUNCH(ctx)                                                                      \
+  do {                                                                                         \
+    (ctx)->launches++;                                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                       \
+    if (e_ != cudaSuccess) return fail(AFQMC_ECUDA, "kernel launch failed (%s:%d): %s", __FILE__, __LINE__, \
+                                       cudaGetErrorString(e_));                                \
+  } while (0)
+
+constexpr int kHistory = 4096;    // energy measurements buffered on the device by afqmc_run
+constexpr int kMaxOcc = 64;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Dims {
+  int N, X, na, nb, W, ncol, nblk, c0[2], nbk[2];
+  bool restricted;
+  int prec;
+  int gchunk, nchunk;
+  size_t rsz() const { return prec == AFQMC_PREC_FP64 ? 8 : 4; }
+};
+
+// Offsets of every device buffer inside the workspace.
+struct Layout {
+  size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp;
+  size_t phi, hrot, lbar, lrot, chol, eh;
+  size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
+  size_t exch_part, eloc, hist, status, step, src, cum, neww;
+  size_t tc;          // tensor-core operand buffers (BF16 forms)
+  size_t setup;       // set-up scratch (aliases vhs; binary64 L, L L products, Ltilde)
+  size_t setup_bytes, vhs_bytes, tc_bytes;
+  size_t total;
+};
+
+Layout plan(const Dims& d) {
+  Layout L{};
+  size_t cur = 0;
+  auto take = [&](size_t bytes) { size_t o = align_up(cur, 256); cur = o + bytes; return o; };
+  const size_t R = d.rsz(), C = 2 * R;
+  const size_t W = d.W, N = d.N, X = d.X, nc = d.ncol;
+  L.psi = take(W * N * nc * C);
+  L.thetaT = take(W * nc * N * C);
+  L.tA = take(W * N * nc * C);
+  L.tB = take(W * N * nc * C);
+  L.tC = take(W * N * nc * C);
+  L.psi_tmp = take(W * N * nc * C);
+  L.th_tmp = take(W * nc * N * C);
+  L.logO = take(W * 16);
+  L.logO_tmp = take(W * 16);
+  L.w = take(W * 8);
+  L.w_tmp = take(W * 8);
+  L.phi = take(N * nc * 8);
+  L.hrot = take(nc * N * 8);
+  L.lbar = take(X * 8);
+  L.lrot = take(X * nc * N * R);
+  L.chol = take(X * N * N * R);
+  L.eh = take(N * N * R);
+  L.vbias = take(W * X * C);
+  L.x = take(W * X * 8);
+  L.xbar = take(W * X * 16);
+  L.coef = take(W * X * C);
+  L.cmf = take(W * 16);
+  L.xxbar = take(W * 16);
+  L.exch_part = take(W * (size_t)d.nchunk * 16);
+  L.eloc = take(W * 3 * 16);
+  L.hist = take((size_t)kHistory * 4 * 8);
+  L.status = take(256);
+  L.step = take(256);
+  L.src = take(W * 4);
+  L.cum = take(W * 8);
+  L.neww = take(256);
+  L.tc_bytes = tc::operand_bytes(d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk);
+  L.tc = take(L.tc_bytes);
+  L.vhs_bytes = W * N * N * C;
+  L.setup_bytes = align_up(X * N * N * 8, 256) * 2 + align_up(N * N * 8, 256) + align_up(X * nc * N * 8, 256);
+  L.vhs = take(std::max(L.vhs_bytes, L.setup_bytes));
+  L.setup = L.vhs;
+  L.total = align_up(cur, 256);
+  return L;
+}
+
+afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta, const double* psiT,
+                       const afqmc_params* p, Dims* d) {
+  if (!p) return fail(AFQMC_EINVAL, "params is NULL");
+  if (norb < 1 || naux < 1) return fail(AFQMC_EINVAL, "norb and naux must be >= 1 (got %d, %d)", norb, naux);
+  if (nalpha < 1 || nbeta < 0 || nalpha > norb || nbeta > norb || nalpha > kMaxOcc || nbeta > kMaxOcc)
+    return fail(AFQMC_EINVAL, "need 1 <= nalpha <= min(norb, %d), 0 <= nbeta <= min(norb, %d) (got %d, %d)",
+                kMaxOcc, kMaxOcc, nalpha, nbeta);
+  if (p->nwalkers < 1 || p->nwalkers > 65535) return fail(AFQMC_EINVAL, "nwalkers must be in [1, 65535]");
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(AFQMC_EINVAL, "dt must be positive and finite");
+  if (p->taylor_order < 1 || p->taylor_order > 12) return fail(AFQMC_EINVAL, "taylor_order must be in [1, 12]");
+  if (p->prec < AFQMC_PREC_FP64 || p->prec > AFQMC_PREC_BF16X3) return fail(AFQMC_EINVAL, "unknown prec %d", p->prec);
+  if (p->reserved != 0) return fail(AFQMC_EINVAL, "params.reserved must be 0");
+  if (!psiT) return fail(AFQMC_EINVAL, "psiT is NULL");
+  if ((long long)norb * norb > (1ll << 31) / 2) return fail(AFQMC_EINVAL, "norb too large");
+  d->N = norb; d->X = naux; d->na = nalpha; d->nb = nbeta; d->W = p->nwalkers; d->prec = p->prec;
+  bool same = nalpha == nbeta;
+  const int nt = nalpha + nbeta;
+  for (int r = 0; same && r < norb; ++r)
+    for (int c = 0; c < nalpha; ++c)
+      if (psiT[(size_t)r * nt + c] != psiT[(size_t)r * nt + nalpha + c]) { same = false; break; }
+  d->restricted = same;
+  d->ncol = same ? nalpha : nt;
+  d->nblk = (same || nbeta == 0) ? 1 : 2;
+  d->c0[0] = 0; d->nbk[0] = nalpha;
+  d->c0[1] = nalpha; d->nbk[1] = same ? 0 : nbeta;
+  d->gchunk = 8;
+  d->nchunk = (naux + d->gchunk - 1) / d->gchunk;
+  return AFQMC_OK;
+}
+
+// Host binary64 helpers for the set-up ------------------------------------------------
+bool invert_small(std::vector<double>& a, int n) {   // Gauss-Jordan with partial pivoting, in place
+  std::vector<double> inv(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int pv = k;
+    for (int i = k + 1; i < n; ++i) if (std::fabs(a[i * n + k]) > std::fabs(a[pv * n + k])) pv = i;
+    if (a[pv * n + k] == 0.0) return false;
+    for (int j = 0; j < n; ++j) { std::swap(a[k * n + j], a[pv * n + j]); std::swap(inv[k * n + j], inv[pv * n + j]); }
+    const double d = a[k * n + k];
+    for (int j = 0; j < n; ++j) { a[k * n + j] /= d; inv[k * n + j] /= d; }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = a[i * n + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) { a[i * n + j] -= f * a[k * n + j]; inv[i * n + j] -= f * inv[k * n + j]; }
+    }
+  }
+  a = inv;
+  return true;
+}
+
+void matmul(const std::vector<double>& a, const std::vector<double>& b, std::vector<double>& c, int n) {
+  c.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const double aik = a[(size_t)i * n + k];
+      if (aik == 0.0) continue;
+      for (int j = 0; j < n; ++j) c[(size_t)i * n + j] += aik * b[(size_t)k * n + j];
+    }
+}
+
+// exp(A) for a symmetric A by scaling and squaring of the Taylor series.
+void expm_host(const std::vector<double>& a, int n, std::vector<double>& out) {
+  double norm1 = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += std::fabs(a[(size_t)i * n + j]);
+    norm1 = std::max(norm1, s);
+  }
+  int sq = 0;
+  while (norm1 / std::ldexp(1.0, sq) > 0.25) ++sq;
+  const double scale = std::ldexp(1.0, -sq);
+  std::vector<double> b(a.size());
+  for (size_t i = 0; i < a.size(); ++i) b[i] = a[i] * scale;
+  out.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) out[(size_t)i * n + i] = 1.0;
+  std::vector<double> term = out, tmp;
+  for (int k = 1; k <= 30; ++k) {
+    matmul(term, b, tmp, n);
+    double tn = 0.0;
+    for (size_t i = 0; i < tmp.size(); ++i) { term[i] = tmp[i] / k; out[i] += term[i]; tn = std::max(tn, std::fabs(term[i])); }
+    if (tn < 1e-18) break;
+  }
+  for (int s = 0; s < sq; ++s) { matmul(out, out, tmp, n); out.swap(tmp); }
+}
+
+}  // namespace
+
+struct afqmc_ctx {
+  Dims d;
+  Layout L;
+  char* base;
+  cudaStream_t stream;
+  double dt, sdt, cap, ecore, e_c, e_var, e_trial, smul;
+  int taylor;
+  unsigned long long seed, host_step, launches;
+  bool theta_fresh, vbias_fresh;
+  int hist_used;
+  template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
+};
+
+namespace {
+
+// --------------------------------------------------------------------------------------
+template <typename R, bool CA, bool CB>
+afqmc_status gemm(afqmc_ctx* c, const GemmDesc& g) {
+  if (g.M <= 0 || g.Nc <= 0 || g.batch <= 0) return AFQMC_OK;
+  dim3 grid((g.Nc + 63) / 64, (g.M + 63) / 64, g.batch);
+  if (grid.y > 65535 || grid.z > 65535) return fail(AFQMC_EINVAL, "GEMM grid too large");
+  k_gemm<R, CA, CB><<<grid, 256, 0, c->stream>>>(g);
+  CHECK_LAUNCH(c);
+  return AFQMC_OK;
+}
+
+GemmDesc gdesc(int M, int Nc, int K, int batch) {
+  GemmDesc g{};
+  g.M = M; g.Nc = Nc; g.K = K; g.batch = batch;
+  g.alpha_re = 1.0;
+  return g;
+}
+
+template <typename R>
+OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
+  OverlapArgs<R> a{};
+  a.N = c->d.N; a.ncol = c->d.ncol; a.nblk = c->d.nblk;
+  a.c0[0] = c->d.c0[0]; a.c0[1] = c->d.c0[1]; a.nb[0] = c->d.nbk[0]; a.nb[1] = c->d.nbk[1];
+  a.smul = c->smul;
+  a.psi = c->at<cplx_t<R>>(c->L.psi);
+  a.phi = c->at<double>(c->L.phi);
+  a.thetaT = c->at<cplx_t<R>>(c->L.thetaT);
+  a.logO = c->at<double2>(c->L.logO);
+  a.w = c->at<double>(c->L.w);
+  a.status = c->at<int>(c->L.status);
+  a.mode = mode;
+  a.cmf = c->at<double2>(c->L.cmf);
+  a.xxbar = c->at<double2>(c->L.xxbar);
+  a.dt = c->dt; a.e_trial = c->e_trial; a.e_c = c->e_c;
+  a.step = mode == 1 ? c->at<unsigned long long>(c->L.step) : nullptr;
+  return a;
+}
+
+size_t overlap_smem(const Dims& d) {
+  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
+  return (size_t)2 * nmax * nmax * sizeof(double2);
+}
+
+template <typename R>
+afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
+  const size_t sm = overlap_smem(c->d);
+  k_overlap<R><<<c->d.W, 256, sm, c->stream>>>(overlap_args<R>(c, mode));
+  CHECK_LAUNCH(c);
+  return AFQMC_OK;
+}
+
+size_t exchange_smem(const Dims& d) {
+  const size_t R = d.rsz();
+  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
+  const size_t cn = (size_t)d.ncol * d.N;
+  return cn * 2 * R + (cn + (cn & 1)) * R + (size_t)nmax * nmax * 2 * R;
+}
+
+template <typename R>
+afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange) {
+  ExchangeArgs<R> a{};
+  a.N = c->d.N; a.X = c->d.X; a.ncol = c->d.ncol; a.nblk = c->d.nblk;
+  a.c0[0] = c->d.c0[0]; a.c0[1] = c->d.c0[1]; a.nb[0] = c->d.nbk[0]; a.nb[1] = c->d.nbk[1];
+  a.smul = c->smul; a.gchunk = c->d.gchunk; a.nchunk = c->d.nchunk;
+  a.thetaT = c->at<cplx_t<R>>(c->L.thetaT);
+  a.lrot = c->at<R>(c->L.lrot);
+  a.vbias = c->at<cplx_t<R>>(c->L.vbias);
+  a.exch_part = c->at<double2>(c->L.exch_part);
+  a.with_exchange = with_exchange;
+  dim3 grid(c->d.nchunk, c->d.W);
+  k_exchange<R><<<grid, 256, exchange_smem(c->d), c->stream>>>(a);
+  CHECK_LAUNCH(c);
+  return AFQMC_OK;
+}
+
+template <typename R>
+afqmc_status set_smem_limits(const Dims& d) {
+  const size_t ov = overlap_smem(d), ex = exchange_smem(d);
+  const size_t qr = (size_t)std::max(d.nbk[0], d.nbk[1]) * d.N * sizeof(double2);
+  const size_t lim = 227 * 1024;
+  if (ov > lim || ex > lim || qr > lim)
+    return fail(AFQMC_EINVAL, "problem too large for the CUDA-core kernels' shared-memory staging "
+                              "(overlap %zu, exchange %zu, qr %zu bytes > %zu)", ov, ex, qr, lim);
+  CU(cudaFuncSetAttribute(k_overlap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ov));
+  CU(cudaFuncSetAttribute(k_exchange<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ex));
+  CU(cudaFuncSetAttribute(k_qr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr));
+  return AFQMC_OK;
+}
+
+// Local energy at the current walkers into eloc and the weighted sums into sums_dev.
+template <typename R>
+afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
+  afqmc_status st;
+  if (!c->theta_fresh) {
+    if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
+    c->theta_fresh = true;
+  }
+  if (c->d.prec == AFQMC_PREC_BF16 || c->d.prec == AFQMC_PREC_BF16X3) {
+    if ((st = tc::exchange(c->d.prec, c->stream, c->at<char>(c->L.tc), c->d.W, c->d.N, c->d.X, c->d.ncol, c->d.c0,
+                           c->d.nbk, c->d.nblk, c->smul, c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias),
+                           c->at<double2>(c->L.exch_part), c->d.nchunk, &c->launches)) != AFQMC_OK)
+      return st;
+  } else {
+    if ((st = launch_exchange<R>(c, 1)) != AFQMC_OK) return st;
+  }
+  k_energy_walker<R><<<c->d.W, 256, 0, c->stream>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
+                                                   c->at<cplx_t<R>>(c->L.thetaT), c->at<double>(c->L.hrot),
+                                                   c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
+                                                   c->at<double2>(c->L.eloc));
+  CHECK_LAUNCH(c);
+  k_energy_sums<<<1, 256, 0, c->stream>>>(c->d.W, c->at<double>(c->L.w), c->at<double2>(c->L.eloc), sums_dev);
+  CHECK_LAUNCH(c);
+  c->vbias_fresh = true;
+  return AFQMC_OK;
+}
+
+template <typename R>
+afqmc_status step_impl(afqmc_ctx* c) {
+  afqmc_status st;
+  const Dims& d = c->d;
+  using R2 = cplx_t<R>;
+  if (!c->theta_fresh) {
+    if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
+    c->theta_fresh = true;
+  }
+  if (!c->vbias_fresh) {
+    if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
+      if ((st = tc::force_bias(d.prec, c->stream, c->at<char>(c->L.tc), d.W, d.N, d.X, d.ncol, c->smul,
+                               c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias), &c->launches)) != AFQMC_OK)
+        return st;
+    } else {
+      // vbias[w][g] = smul * sum_k thetaT[w][k] * lrot[g][k],  k = (c, p)
+      GemmDesc g = gdesc(d.W, d.X, d.ncol * d.N, 1);
+      g.A = c->at<R2>(c->L.thetaT); g.sAm = (long long)d.ncol * d.N; g.sAk = 1;
+      g.B = c->at<R>(c->L.lrot); g.sBk = 1; g.sBn = (long long)d.ncol * d.N;
+      g.C = c->at<R2>(c->L.vbias); g.sCm = d.X; g.sCn = 1;
+      g.alpha_re = c->smul;
+      if ((st = gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
+    }
+  }
+  FieldArgs<R> fa{};
+  fa.X = d.X; fa.sdt = c->sdt; fa.cap = c->cap; fa.seed = c->seed;
+  fa.step = c->at<unsigned long long>(c->L.step);
+  fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar);
+  fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
+  fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
+  k_fields<R><<<d.W, 256, 0, c->stream>>>(fa);
+  CHECK_LAUNCH(c);
+  const long long NN = (long long)d.N * d.N, Nc = (long long)d.N * d.ncol;
+  // VHS[w][pq] = sum_g coef[w][g] L[g][pq]
+  if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
+    if ((st = tc::vhs(d.prec, c->stream, c->at<char>(c->L.tc), d.W, d.N, d.X, c->at<float2>(c->L.coef),
+                      c->at<float2>(c->L.vhs), &c->launches)) != AFQMC_OK)
+      return st;
+  } else {
+    GemmDesc g = gdesc(d.W, (int)NN, d.X, 1);
+    g.A = c->at<R2>(c->L.coef); g.sAm = d.X; g.sAk = 1;
+    g.B = c->at<R>(c->L.chol); g.sBk = NN; g.sBn = 1;
+    g.C = c->at<R2>(c->L.vhs); g.sCm = NN; g.sCn = 1;
+    if ((st = gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
+  }
+  // psi <- E_h Taylor(VHS) E_h psi   (tA = accumulator, tB/tC = Taylor terms)
+  const double* skip = c->at<double>(c->L.w);
+  {
+    GemmDesc g = gdesc(d.N, d.ncol, d.N, d.W);
+    g.A = c->at<R>(c->L.eh); g.sAb = 0; g.sAm = d.N; g.sAk = 1;
+    g.B = c->at<R2>(c->L.psi); g.sBb = Nc; g.sBk = d.ncol; g.sBn = 1;
+    g.C = c->at<R2>(c->L.tB); g.sCb = Nc; g.sCm = d.ncol; g.sCn = 1;
+    g.D = c->at<R2>(c->L.tA); g.sDb = Nc; g.sDm = d.ncol; g.sDn = 1; g.d_add = 0;
+    g.skip = skip;
+    if ((st = gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
+  }
+  size_t tin = c->L.tB, tout = c->L.tC;
+  for (int k = 1; k <= c->taylor; ++k) {
+    GemmDesc g = gdesc(d.N, d.ncol, d.N, d.W);
+    g.A = c->at<R2>(c->L.vhs); g.sAb = NN; g.sAm = d.N; g.sAk = 1;
+    g.B = c->at<R2>(tin); g.sBb = Nc; g.sBk = d.ncol; g.sBn = 1;
+    g.C = k < c->taylor ? c->at<R2>(tout) : nullptr; g.sCb = Nc; g.sCm = d.ncol; g.sCn = 1;
+    g.D = c->at<R2>(c->L.tA); g.sDb = Nc; g.sDm = d.ncol; g.sDn = 1; g.d_add = 1;
+    g.alpha_re = 1.0 / k;
+    g.skip = skip;
+    if ((st = gemm<R, true, true>(c, g)) != AFQMC_OK) return st;
+    std::swap(tin, tout);
+  }
+  {
+    GemmDesc g = gdesc(d.N, d.ncol, d.N, d.W);
+    g.A = c->at<R>(c->L.eh); g.sAb = 0; g.sAm = d.N; g.sAk = 1;
+    g.B = c->at<R2>(c->L.tA); g.sBb = Nc; g.sBk = d.ncol; g.sBn = 1;
+    g.C = c->at<R2>(c->L.psi); g.sCb = Nc; g.sCm = d.ncol; g.sCn = 1;
+    g.skip = skip;
+    if ((st = gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
+  }
+  if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
+  c->theta_fresh = true;
+  c->vbias_fresh = false;
+  c->host_step++;
+  return AFQMC_OK;
+}
+
+template <typename R>
+afqmc_status qr_impl(afqmc_ctx* c) {
+  const Dims& d = c->d;
+  const size_t sm = (size_t)std::max(d.nbk[0], d.nbk[1]) * d.N * sizeof(double2);
+  k_qr<R><<<d.W, 256, sm, c->stream>>>(d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1], c->smul,
+                                       c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO), c->at<double>(c->L.w));
+  CHECK_LAUNCH(c);
+  c->theta_fresh = false;
+  c->vbias_fresh = false;
+  return AFQMC_OK;
+}
+
+template <typename R>
+afqmc_status comb_impl(afqmc_ctx* c) {
+  const Dims& d = c->d;
+  using R2 = cplx_t<R>;
+  k_comb_plan<<<1, 256, 0, c->stream>>>(d.W, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.w),
+                                        c->at<double>(c->L.cum), c->at<int>(c->L.src), c->at<double>(c->L.neww),
+                                        c->at<int>(c->L.status));
+  CHECK_LAUNCH(c);
+  const int pe = d.N * d.ncol;
+  if (!c->theta_fresh) {
+    afqmc_status st = launch_overlap<R>(c, 2);
+    if (st != AFQMC_OK) return st;
+    c->theta_fresh = true;
+  }
+  k_comb_gather<R><<<d.W, 256, 0, c->stream>>>(d.W, pe, pe, c->at<int>(c->L.src), c->at<double>(c->L.neww),
+                                               c->at<R2>(c->L.psi), c->at<R2>(c->L.psi_tmp), c->at<R2>(c->L.thetaT),
+                                               c->at<R2>(c->L.th_tmp), c->at<double2>(c->L.logO),
+                                               c->at<double2>(c->L.logO_tmp), c->at<double>(c->L.w),
+                                               c->at<double>(c->L.w_tmp));
+  CHECK_LAUNCH(c);
+  const size_t pb = (size_t)d.W * pe * sizeof(R2);
+  CU(cudaMemcpyAsync(c->base + c->L.psi, c->base + c->L.psi_tmp, pb, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.thetaT, c->base + c->L.th_tmp, pb, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.logO, c->base + c->L.logO_tmp, d.W * 16, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.w, c->base + c->L.w_tmp, d.W * 8, cudaMemcpyDeviceToDevice, c->stream));
+  c->vbias_fresh = false;
+  return AFQMC_OK;
+}
+
+afqmc_status read_status(afqmc_ctx* c) {
+  int st = 0;
+  CU(cudaMemcpyAsync(&st, c->base + c->L.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (st == 0) return AFQMC_OK;
+  CU(cudaMemsetAsync(c->base + c->L.status, 0, sizeof(int), c->stream));
+  if (st & kStatusNoWalkers) return fail(AFQMC_ENOWALKERS, "all walker weights are zero");
+  if (st & kStatusNonFinite) return fail(AFQMC_ENONFINITE, "a walker weight became non-finite (set to 0)");
+  return fail(AFQMC_ESINGULAR, "a walker overlap matrix was singular (weight set to 0)");
+}
+
+#define DISPATCH(ctx, fn, ...)                                                      \
+  ((ctx)->d.prec == AFQMC_PREC_FP64 ? fn<double>(ctx, ##__VA_ARGS__) : fn<float>(ctx, ##__VA_ARGS__))
+
+template <typename R>
+afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, const double* psiT) {
+  const Dims& d = c->d;
+  const int N = d.N, X = d.X, nc = d.ncol, nt = d.na + d.nb;
+  afqmc_status st;
+  if ((st = set_smem_limits<R>(d)) != AFQMC_OK) return st;
+  // trial columns that are stored (restricted: alpha only)
+  std::vector<double> phi((size_t)N * nc);
+  for (int p = 0; p < N; ++p)
+    for (int col = 0; col < nc; ++col) phi[(size_t)p * nc + col] = psiT[(size_t)p * nt + col];
+  // P = sum_s Phi_s (Phi_s^T Phi_s)^-1 Phi_s^T over both spins
+  std::vector<double> P((size_t)N * N, 0.0);
+  for (int s = 0; s < 2; ++s) {
+    const int off = s == 0 ? 0 : d.na, n = s == 0 ? d.na : d.nb;
+    if (n == 0) continue;
+    std::vector<double> S((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int p = 0; p < N; ++p) acc += psiT[(size_t)p * nt + off + i] * psiT[(size_t)p * nt + off + j];
+        S[(size_t)i * n + j] = acc;
+      }
+    if (!invert_small(S, n)) return fail(AFQMC_EINVAL, "trial orbitals of spin %d are linearly dependent", s);
+    std::vector<double> tmp((size_t)N * n, 0.0);   // Phi S^-1
+    for (int p = 0; p < N; ++p)
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) acc += psiT[(size_t)p * nt + off + i] * S[(size_t)i * n + j];
+        tmp[(size_t)p * n + j] = acc;
+      }
+    for (int p = 0; p < N; ++p)
+      for (int q = 0; q < N; ++q) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += tmp[(size_t)p * n + j] * psiT[(size_t)q * nt + off + j];
+        P[(size_t)p * N + q] += acc;
+      }
+  }
+  // lbar_g = Tr(L^g P); E_c = E0 - 1/2 sum lbar^2; sum_g lbar_g L^g
+  std::vector<double> lbar(X), lsum((size_t)N * N, 0.0);
+  double l2 = 0.0;
+  for (int g = 0; g < X; ++g) {
+    const double* Lg = chol + (size_t)g * N * N;
+    double acc = 0.0;
+    for (size_t i = 0; i < (size_t)N * N; ++i) acc += Lg[i] * P[i];
+    lbar[g] = acc;
+    l2 += acc * acc;
+    for (size_t i = 0; i < (size_t)N * N; ++i) lsum[i] += acc * Lg[i];
+  }
+  c->e_c = c->ecore - 0.5 * l2;
+  // htilde = Phi^T h  [nc][N]
+  std::vector<double> hrot((size_t)nc * N, 0.0);
+  for (int col = 0; col < nc; ++col)
+    for (int q = 0; q < N; ++q) {
+      double acc = 0.0;
+      for (int p = 0; p < N; ++p) acc += phi[(size_t)p * nc + col] * h1e[(size_t)p * N + q];
+      hrot[(size_t)col * N + q] = acc;
+    }
+  // device: binary64 L, products L^g L^g, Ltilde
+  double* chol64 = c->at<double>(c->L.setup);
+  double* prod = chol64 + align_up((size_t)X * N * N * 8, 256) / 8;
+  double* msum = prod + align_up((size_t)X * N * N * 8, 256) / 8;
+  double* lrot64 = msum + align_up((size_t)N * N * 8, 256) / 8;
+  CU(cudaMemcpyAsync(chol64, chol, (size_t)X * N * N * 8, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.hrot, hrot.data(), hrot.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.lbar, lbar.data(), lbar.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  {   // prod[g] = L^g L^g
+    GemmDesc g = gdesc(N, N, N, X);
+    g.A = chol64; g.sAb = (long long)N * N; g.sAm = N; g.sAk = 1;
+    g.B = chol64; g.sBb = (long long)N * N; g.sBk = N; g.sBn = 1;
+    g.C = prod; g.sCb = (long long)N * N; g.sCm = N; g.sCn = 1;
+    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
+    k_sum_batches<<<148, 256, 0, c->stream>>>(X, (size_t)N * N, prod, msum);
+    CHECK_LAUNCH(c);
+  }
+  {   // Ltilde[g] = Phi^T L^g  ([nc][N] per gamma)
+    GemmDesc g = gdesc(nc, N, N, X);
+    g.A = c->at<double>(c->L.phi); g.sAb = 0; g.sAm = 1; g.sAk = nc;
+    g.B = chol64; g.sBb = (long long)N * N; g.sBk = N; g.sBn = 1;
+    g.C = lrot64; g.sCb = (long long)nc * N; g.sCm = N; g.sCn = 1;
+    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
+  }
+  std::vector<double> m((size_t)N * N);
+  CU(cudaMemcpyAsync(m.data(), msum, m.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  // h_eff = h - 1/2 sum L L + sum lbar L; E_h = exp(-dt/2 h_eff)
+  std::vector<double> heff((size_t)N * N), eh;
+  for (size_t i = 0; i < heff.size(); ++i) heff[i] = -0.5 * c->dt * (h1e[i] - 0.5 * m[i] + lsum[i]);
+  for (int p = 0; p < N; ++p)   // symmetrise the rounding
+    for (int q = p + 1; q < N; ++q) {
+      const double v = 0.5 * (heff[(size_t)p * N + q] + heff[(size_t)q * N + p]);
+      heff[(size_t)p * N + q] = heff[(size_t)q * N + p] = v;
+    }
+  expm_host(heff, N, eh);
+  std::vector<R> ehr(eh.begin(), eh.end());
+  CU(cudaMemcpyAsync(c->base + c->L.eh, ehr.data(), ehr.size() * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));   // ehr goes out of scope
+  k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * N * N, chol64, c->at<R>(c->L.chol));
+  CHECK_LAUNCH(c);
+  k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * nc * N, lrot64, c->at<R>(c->L.lrot));
+  CHECK_LAUNCH(c);
+  if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
+    if ((st = tc::prepare(d.prec, c->stream, c->at<char>(c->L.tc), d.W, N, X, nc, d.c0, d.nbk, d.nblk, chol64,
+                          lrot64, &c->launches)) != AFQMC_OK)
+      return st;
+  }
+  CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.step, 0, 256, c->stream));
+  k_init_walkers<R><<<296, 256, 0, c->stream>>>(d.W, N, nc, c->at<double>(c->L.phi), c->at<cplx_t<R>>(c->L.psi),
+                                                c->at<double>(c->L.w));
+  CHECK_LAUNCH(c);
+  if ((st = launch_overlap<R>(c, 0)) != AFQMC_OK) return st;
+  c->theta_fresh = true;
+  c->vbias_fresh = false;
+  // E_var = E_L(psiT) (every walker is the trial)
+  if ((st = energy_impl<R>(c, c->at<double>(c->L.hist))) != AFQMC_OK) return st;
+  double2 e0;
+  CU(cudaMemcpyAsync(&e0, c->base + c->L.eloc, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->e_var = e0.x;
+  return read_status(c);
+}
+
+afqmc_status check_ctx(afqmc_ctx* c) {
+  if (!c) return fail(AFQMC_EINVAL, "context is NULL");
+  return AFQMC_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+const char* afqmc_last_error(void) { return g_err; }
+
+afqmc_status afqmc_workspace_size(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta, const double* psiT,
+                                  const afqmc_params* params, size_t* bytes) {
+  if (!bytes) return fail(AFQMC_EINVAL, "bytes is NULL");
+  Dims d{};
+  afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d);
+  if (st != AFQMC_OK) return st;
+  *bytes = plan(d).total;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, int32_t norb, int32_t naux,
+                          int32_t nalpha, int32_t nbeta, const double* psiT, const afqmc_params* params,
+                          void* workspace, size_t workspace_bytes, afqmc_ctx** out) {
+  if (!out) return fail(AFQMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!h1e || !chol) return fail(AFQMC_EINVAL, "h1e or chol is NULL");
+  Dims d{};
+  afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d);
+  if (st != AFQMC_OK) return st;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(AFQMC_EINVAL, "workspace must be a non-NULL 256-byte aligned device pointer");
+  Layout L = plan(d);
+  if (workspace_bytes < L.total)
+    return fail(AFQMC_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+  if (!std::isfinite(ecore)) return fail(AFQMC_EINVAL, "ecore is not finite");
+  const size_t N = norb, X = naux, nt = nalpha + nbeta;
+  double lmax = 0.0, hmax = 0.0;
+  for (size_t i = 0; i < N * N; ++i) {
+    if (!std::isfinite(h1e[i])) return fail(AFQMC_EINVAL, "h1e has a non-finite entry");
+    hmax = std::max(hmax, std::fabs(h1e[i]));
+  }
+  for (size_t i = 0; i < X * N * N; ++i) {
+    if (!std::isfinite(chol[i])) return fail(AFQMC_EINVAL, "chol has a non-finite entry at %zu", i);
+    lmax = std::max(lmax, std::fabs(chol[i]));
+  }
+  for (size_t i = 0; i < N * nt; ++i)
+    if (!std::isfinite(psiT[i])) return fail(AFQMC_EINVAL, "psiT has a non-finite entry");
+  for (size_t p = 0; p < N; ++p)
+    for (size_t q = p + 1; q < N; ++q) {
+      if (std::fabs(h1e[p * N + q] - h1e[q * N + p]) > 1e-12 * std::max(1.0, hmax))
+        return fail(AFQMC_EINVAL, "h1e is not symmetric at (%zu, %zu)", p, q);
+      for (size_t g = 0; g < X; ++g)
+        if (std::fabs(chol[g * N * N + p * N + q] - chol[g * N * N + q * N + p]) > 1e-12 * std::max(1.0, lmax))
+          return fail(AFQMC_EINVAL, "chol[%zu] is not symmetric at (%zu, %zu)", g, p, q);
+    }
+  afqmc_ctx* c = new afqmc_ctx();
+  c->d = d;
+  c->L = L;
+  c->base = static_cast<char*>(workspace);
+  c->stream = static_cast<cudaStream_t>(params->stream);
+  c->dt = params->dt;
+  c->sdt = std::sqrt(params->dt);
+  c->cap = params->fb_cap;
+  c->ecore = ecore;
+  c->taylor = params->taylor_order;
+  c->seed = params->seed;
+  c->smul = d.restricted ? 2.0 : 1.0;
+  c->host_step = 0;
+  c->launches = 0;
+  c->hist_used = 0;
+  c->e_trial = 0.0;
+  st = DISPATCH(c, create_impl, h1e, chol, psiT);
+  if (st != AFQMC_OK) {
+    delete c;
+    return st;
+  }
+  c->e_trial = std::isnan(params->e_trial) ? c->e_var : params->e_trial;
+  *out = c;
+  return AFQMC_OK;
+}
+
+void afqmc_destroy(afqmc_ctx* ctx) { delete ctx; }
+
+uint64_t afqmc_launch_count(afqmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
+  for (int s = 0; s < nsteps; ++s)
+    if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_local_energy(afqmc_ctx* ctx, double* sums, double* eloc) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  double* dsums = ctx->at<double>(ctx->L.hist) + 4 * (kHistory - 1);
+  if ((st = DISPATCH(ctx, energy_impl, dsums)) != AFQMC_OK) return st;
+  if (sums) CU(cudaMemcpyAsync(sums, dsums, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (eloc)
+    CU(cudaMemcpyAsync(eloc, ctx->base + ctx->L.eloc, (size_t)ctx->d.W * 3 * sizeof(double2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (sums || eloc) return read_status(ctx);
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_reortho(afqmc_ctx* ctx) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  return DISPATCH(ctx, qr_impl);
+}
+
+afqmc_status afqmc_popcontrol(afqmc_ctx* ctx) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  return DISPATCH(ctx, comb_impl);
+}
+
+afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
+                       int32_t comb_every, double* energies, int32_t* nmeas) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
+  int used = 0, total = 0;
+  double* hist = ctx->at<double>(ctx->L.hist);
+  auto flush = [&]() -> afqmc_status {
+    if (used > 0 && energies)
+      CU(cudaMemcpyAsync(energies + 4 * (size_t)(total - used), hist, (size_t)used * 4 * sizeof(double),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    used = 0;
+    return AFQMC_OK;
+  };
+  for (int s = 0; s < nsteps; ++s) {
+    if (energy_every > 0 && ctx->host_step % (unsigned long long)energy_every == 0) {
+      if (used == kHistory - 1 && (st = flush()) != AFQMC_OK) return st;
+      if ((st = DISPATCH(ctx, energy_impl, hist + 4 * used)) != AFQMC_OK) return st;
+      ++used;
+      ++total;
+    }
+    if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
+    if (reortho_every > 0 && ctx->host_step % (unsigned long long)reortho_every == 0)
+      if ((st = DISPATCH(ctx, qr_impl)) != AFQMC_OK) return st;
+    if (comb_every > 0 && ctx->host_step % (unsigned long long)comb_every == 0)
+      if ((st = DISPATCH(ctx, comb_impl)) != AFQMC_OK) return st;
+  }
+  if ((st = flush()) != AFQMC_OK) return st;
+  if (nmeas) *nmeas = total;
+  return read_status(ctx);
+}
+
+afqmc_status afqmc_get_walkers(afqmc_ctx* ctx, double* psi, double* logO, double* w, uint64_t* step) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  const Dims& d = ctx->d;
+  if (psi) {
+    const size_t n = (size_t)d.W * d.N * d.ncol;
+    std::vector<double> buf(2 * n);
+    if (d.prec == AFQMC_PREC_FP64) {
+      CU(cudaMemcpyAsync(buf.data(), ctx->base + ctx->L.psi, n * 16, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+    } else {
+      std::vector<float> f(2 * n);
+      CU(cudaMemcpyAsync(f.data(), ctx->base + ctx->L.psi, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      for (size_t i = 0; i < 2 * n; ++i) buf[i] = f[i];
+    }
+    const int nt = d.na + d.nb;
+    for (int wk = 0; wk < d.W; ++wk)
+      for (int p = 0; p < d.N; ++p)
+        for (int col = 0; col < nt; ++col) {
+          const int sc = (d.restricted && col >= d.na) ? col - d.na : col;
+          const size_t si = ((size_t)wk * d.N + p) * d.ncol + sc, di = ((size_t)wk * d.N + p) * nt + col;
+          psi[2 * di] = buf[2 * si];
+          psi[2 * di + 1] = buf[2 * si + 1];
+        }
+  }
+  if (logO) CU(cudaMemcpyAsync(logO, ctx->base + ctx->L.logO, (size_t)d.W * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  if (w) CU(cudaMemcpyAsync(w, ctx->base + ctx->L.w, (size_t)d.W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (step) *step = ctx->host_step;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_walkers(afqmc_ctx* ctx, const double* psi, const double* w, uint64_t step) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  const Dims& d = ctx->d;
+  if (!psi || !w) return fail(AFQMC_EINVAL, "psi and w are required");
+  const int nt = d.na + d.nb;
+  const size_t n = (size_t)d.W * d.N * d.ncol;
+  std::vector<double> buf(2 * n);
+  for (int wk = 0; wk < d.W; ++wk) {
+    if (!(w[wk] >= 0.0) || !std::isfinite(w[wk])) return fail(AFQMC_EINVAL, "weight %d is negative or non-finite", wk);
+    for (int p = 0; p < d.N; ++p)
+      for (int col = 0; col < nt; ++col) {
+        const size_t si = ((size_t)wk * d.N + p) * nt + col;
+        if (!std::isfinite(psi[2 * si]) || !std::isfinite(psi[2 * si + 1]))
+          return fail(AFQMC_EINVAL, "psi has a non-finite entry");
+        if (d.restricted && col >= d.na) {
+          const size_t ai = ((size_t)wk * d.N + p) * nt + (col - d.na);
+          if (psi[2 * si] != psi[2 * ai] || psi[2 * si + 1] != psi[2 * ai + 1])
+            return fail(AFQMC_EINVAL, "restricted context: alpha and beta blocks of walker %d differ", wk);
+          continue;
+        }
+        const size_t di = ((size_t)wk * d.N + p) * d.ncol + col;
+        buf[2 * di] = psi[2 * si];
+        buf[2 * di + 1] = psi[2 * si + 1];
+      }
+  }
+  if (d.prec == AFQMC_PREC_FP64) {
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.psi, buf.data(), n * 16, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    std::vector<float> f(buf.begin(), buf.end());
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.psi, f.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  CU(cudaMemcpyAsync(ctx->base + ctx->L.w, w, (size_t)d.W * 8, cudaMemcpyHostToDevice, ctx->stream));
+  unsigned long long s64 = step;
+  CU(cudaMemcpyAsync(ctx->base + ctx->L.step, &s64, 8, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->host_step = step;
+  ctx->theta_fresh = false;
+  ctx->vbias_fresh = false;
+  st = DISPATCH(ctx, launch_overlap, 0);
+  if (st != AFQMC_OK) return st;
+  ctx->theta_fresh = true;
+  return read_status(ctx);
+}
+
+afqmc_status afqmc_get_fields(afqmc_ctx* ctx, double* x, double* xbar) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  const size_t n = (size_t)ctx->d.W * ctx->d.X;
+  if (x) CU(cudaMemcpyAsync(x, ctx->base + ctx->L.x, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (xbar) CU(cudaMemcpyAsync(xbar, ctx->base + ctx->L.xbar, n * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_draw_normals(uint64_t seed, uint64_t step, uint32_t stream_id, int32_t nwalkers, int32_t naux,
+                                double* out, void* stream) {
+  if (nwalkers < 0 || naux < 0 || nwalkers > 65535) return fail(AFQMC_EINVAL, "bad sizes");
+  if (stream_id > 0xffff) return fail(AFQMC_EINVAL, "stream_id must fit 16 bits");
+  if (nwalkers == 0 || naux == 0) return AFQMC_OK;
+  if (!out) return fail(AFQMC_EINVAL, "out is NULL");
+  k_draw_normals<<<nwalkers, 256, 0, static_cast<cudaStream_t>(stream)>>>(seed, step, stream_id, nwalkers, naux, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "draw_normals launch: %s", cudaGetErrorString(e));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_get_info(afqmc_ctx* ctx, afqmc_info* info) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!info) return fail(AFQMC_EINVAL, "info is NULL");
+  info->norb = ctx->d.N; info->naux = ctx->d.X; info->nalpha = ctx->d.na; info->nbeta = ctx->d.nb;
+  info->nwalkers = ctx->d.W; info->restricted = ctx->d.restricted ? 1 : 0; info->prec = ctx->d.prec;
+  info->reserved = 0;
+  info->step = ctx->host_step;
+  info->e_var = ctx->e_var; info->e_trial = ctx->e_trial; info->e_core_mf = ctx->e_c;
+  info->workspace_bytes = ctx->L.total;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!std::isfinite(e_trial)) return fail(AFQMC_EINVAL, "e_trial must be finite");
+  ctx->e_trial = e_trial;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_synchronize(afqmc_ctx* ctx, double timeout_s) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  cudaEvent_t ev;
+  CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, ctx->stream);
+  if (e != cudaSuccess) { cudaEventDestroy(ev); return fail(AFQMC_ECUDA, "event record: %s", cudaGetErrorString(e)); }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return fail(AFQMC_ECUDA, "event query: %s", cudaGetErrorString(e)); }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_s) { cudaEventDestroy(ev); return fail(AFQMC_ETIMEOUT, "stream still busy after %.3f s", el); }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  return read_status(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical inputs.
+
+Tolerances: fields are compared bit for bit; FP64-form quantities to 1e-11
+relative per kernel and 1e-10 relative along trajectories (the floating-point
+sums run in a different order on the two sides); reduced-precision forms to
+0.1 mHa in the mixed energy over a 10-step horizon with identical fields.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2406_16238_b300 as pkg
+from oracle import afqmc as orc
+from oracle import philox
+from synthetic_inputs import config_medium, config_small, make_problem, random_walkers, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(prob, nw, prec="fp64", seed=5, dt=0.005, **kw):
+    return pkg.Afqmc(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, nwalkers=nw, dt=dt,
+                     seed=seed, prec=prec, **kw)
+
+
+def _setup(prob, dt=0.005):
+    return orc.build_setup(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, dt)
+
+
+def _restricted(prob):
+    return prob.nalpha == prob.nbeta and np.array_equal(prob.psiT[:, :prob.nalpha], prob.psiT[:, prob.nalpha:])
+
+
+def _random_state(prob, nw, seed, spread=0.3):
+    rng = np.random.default_rng(seed)
+    if _restricted(prob):
+        half = random_walkers(rng, prob.norb, prob.nalpha, nw, spread, prob.psiT[:, :prob.nalpha])
+        psi = np.concatenate([half, half], axis=2)
+    else:
+        psi = random_walkers(rng, prob.norb, prob.nalpha + prob.nbeta, nw, spread, prob.psiT)
+    w = rng.uniform(0.5, 1.5, nw)
+    return psi, w
+
+
+def _wrapdiff(a, b):
+    return np.abs(np.angle(np.exp(1j * (np.asarray(a) - np.asarray(b)))))
+
+
+PROBLEMS = {
+    "rhf_N8": lambda: config_small(),
+    "uhf_N13_3_2": lambda: make_problem(13, 3, 2, 17, 5.0, 31, unrestricted=True),
+    "rhf_N6_nbeta0": lambda: make_problem(6, 2, 0, 9, 3.0, 41, unrestricted=True),
+    "uhf_N4_2_2": lambda: tiny_problem(4, 2, 2, naux=7, seed=3, unrestricted=True),
+}
+
+
+@pytest.mark.parametrize("seed,step,nw,naux,stream", [(1, 0, 3, 7, 0), (2 ** 40 + 5, 2 ** 33 + 17, 64, 24, 0),
+                                                     (240616238, 12345, 640, 432, 0), (7, 3, 1, 1, 1),
+                                                     (99, 2 ** 47 - 1, 5, 33, 1)])
+def test_fields_bit_exact(seed, step, nw, naux, stream):
+    x = pkg.draw_normals(seed, step, nw, naux, stream_id=stream).cpu().numpy()
+    ref = philox.normals(seed, step, nw, naux, stream=stream)
+    assert np.array_equal(x.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("nw", [1, 37])
+def test_overlap_and_local_energy_parity(name, nw):
+    prob = PROBLEMS[name]()
+    st = _setup(prob)
+    ctx = _ctx(prob, nw)
+    assert abs(ctx.info()["e_var"] - st.evar) < 1e-11 * max(1, abs(st.evar))
+    psi, w = _random_state(prob, nw, seed=nw)
+    w[0] = 0.0 if nw > 1 else w[0]
+    ctx.set_walkers(psi, w, 0)
+    sums, eloc = ctx.local_energy(per_walker=True)
+    _, logo, _, _ = ctx.get_walkers()
+    ref = np.zeros(4)
+    for i in range(nw):
+        lo, th_a, th_b = orc.overlap_theta(st, psi[i])
+        e = orc.local_energy(st, th_a, th_b)
+        assert abs(logo[i].real - lo.real) < 1e-11 * max(1, abs(lo.real))
+        assert _wrapdiff(logo[i].imag, lo.imag) < 1e-11
+        for k in range(3):
+            assert abs(eloc[i, k] - e[k]) < 1e-11 * max(1, abs(e[k])), (i, k, eloc[i, k], e[k])
+        if w[i] > 0:
+            ref += w[i] * np.array([e[0].real, 1.0, e[1].real, e[2].real])
+    assert np.allclose(sums, ref, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_one_step_parity(name):
+    prob = PROBLEMS[name]()
+    nw, seed = 9, 77
+    st = _setup(prob, dt=0.01)
+    ctx = _ctx(prob, nw, seed=seed, dt=0.01, fb_cap=0.5)
+    psi, w = _random_state(prob, nw, seed=3, spread=0.2)
+    ctx.set_walkers(psi, w, 41)
+    ctx.propagate(1)
+    x, xbar = ctx.get_fields()
+    psi_g, logo_g, w_g, step = ctx.get_walkers()
+    assert step == 42
+    wk = orc.Walkers(psi.copy(), np.array([orc.overlap_theta(st, p)[0] for p in psi]), w.copy(), 41)
+    rec = []
+    xref = orc.phaseless_step(st, wk, seed, st.evar, fb_cap=0.5, record=rec)
+    assert np.array_equal(x.view(np.uint64), xref.view(np.uint64))
+    for r in rec:
+        i = r["walker"]
+        assert np.allclose(xbar[i], r["xbar"], rtol=0, atol=1e-12)
+    assert np.allclose(psi_g, wk.psi, rtol=0, atol=1e-11)
+    assert np.allclose(w_g, wk.w, rtol=1e-11, atol=0)
+    assert np.allclose(logo_g.real, wk.logo.real, rtol=1e-11, atol=1e-11)
+    assert np.all(_wrapdiff(logo_g.imag, wk.logo.imag) < 1e-10)
+
+
+def test_trajectory_parity_small_config():
+    """N=8, 2+2, naux=24, 64 walkers, dt=0.005, 200 steps, QR every 5, comb every 10 (FP64)."""
+    prob = config_small()
+    nw, nsteps, seed = 64, 200, 240616239
+    st = _setup(prob)
+    ctx = _ctx(prob, nw, seed=seed)
+    e_gpu = ctx.run(nsteps, energy_every=1, reortho_every=5, comb_every=10)
+    hist, wk = orc.run_phaseless(st, prob.psiT, nw, nsteps, seed, reortho_every=5, comb_every=10)
+    assert e_gpu.shape == hist.shape == (nsteps, 4)
+    eg, er = e_gpu[:, 0] / e_gpu[:, 1], hist[:, 0] / hist[:, 1]
+    assert np.max(np.abs(eg - er) / np.abs(er)) < 1e-10
+    assert np.allclose(e_gpu[:, 1], hist[:, 1], rtol=1e-10, atol=0)
+    psi_g, logo_g, w_g, step = ctx.get_walkers()
+    assert step == nsteps
+    assert np.allclose(w_g, wk.w, rtol=1e-10)
+    assert np.allclose(psi_g, wk.psi, atol=1e-9)
+
+
+def test_qr_parity():
+    prob = PROBLEMS["uhf_N13_3_2"]()
+    st = _setup(prob)
+    nw = 11
+    ctx = _ctx(prob, nw)
+    psi, w = _random_state(prob, nw, seed=8, spread=0.6)
+    psi *= 2.5
+    ctx.set_walkers(psi, w, 0)
+    ctx.reortho()
+    psi_g, logo_g, _, _ = ctx.get_walkers()
+    wk = orc.Walkers(psi.copy(), np.array([orc.overlap_theta(st, p)[0] for p in psi]), w.copy())
+    orc.reorthogonalise(st, wk)
+    assert np.allclose(psi_g, wk.psi, atol=1e-12)
+    assert np.allclose(logo_g.real, wk.logo.real, atol=1e-11)
+    sums, eloc = ctx.local_energy(per_walker=True)
+    for i in range(nw):
+        _, ta, tb = orc.overlap_theta(st, wk.psi[i])
+        assert abs(eloc[i, 0] - orc.local_energy(st, ta, tb)[0]) < 1e-10
+
+
+def test_comb_parity_and_zero_weights():
+    prob = config_small()
+    nw = 50
+    ctx = _ctx(prob, nw, seed=123)
+    psi, w = _random_state(prob, nw, seed=2)
+    rng = np.random.default_rng(4)
+    w = rng.exponential(size=nw)
+    w[[0, 7, 8, 49]] = 0.0
+    ctx.set_walkers(psi, w, 30)
+    ctx.popcontrol()
+    psi_g, logo_g, w_g, _ = ctx.get_walkers()
+    src, wnew = orc.comb_assignment(w, philox.comb_uniform(123, 30))
+    assert np.array_equal(psi_g, psi[src])
+    assert np.allclose(w_g, wnew, rtol=1e-15)
+    assert not set(src) & {0, 7, 8, 49}
+
+
+def test_frozen_walkers_stay_frozen():
+    prob = config_small()
+    nw = 8
+    ctx = _ctx(prob, nw)
+    psi, w = _random_state(prob, nw, seed=5)
+    w[3] = 0.0
+    ctx.set_walkers(psi, w, 0)
+    ctx.propagate(2)
+    psi_g, _, w_g, _ = ctx.get_walkers()
+    assert w_g[3] == 0.0 and np.array_equal(psi_g[3], psi[3])
+
+
+def test_singular_walker_is_reported_and_killed():
+    prob = PROBLEMS["uhf_N13_3_2"]()
+    nw = 4
+    ctx = _ctx(prob, nw)
+    psi, w = _random_state(prob, nw, seed=5)
+    psi[2][:, 1] = 0.0
+    with pytest.raises(pkg.AfqmcError) as e:
+        ctx.set_walkers(psi, w, 0)
+    assert e.value.name == "AFQMC_ESINGULAR"
+    _, _, w_g, _ = ctx.get_walkers()
+    assert w_g[2] == 0.0 and np.all(w_g[[0, 1, 3]] > 0)
+    ctx.propagate(1)                           # the dead walker is skipped, the rest proceed
+    sums = ctx.local_energy()
+    assert np.isfinite(sums).all()
+
+
+def test_all_weights_zero_is_reported():
+    prob = config_small()
+    ctx = _ctx(prob, 4)
+    psi, _ = _random_state(prob, 4, seed=1)
+    ctx.set_walkers(psi, np.zeros(4), 0)
+    ctx.popcontrol()
+    with pytest.raises(pkg.AfqmcError) as e:
+        ctx.synchronize(30.0)
+    assert e.value.name == "AFQMC_ENOWALKERS"
+
+
+def test_restricted_context_rejects_spin_broken_walkers():
+    prob = config_small()
+    ctx = _ctx(prob, 2)
+    psi, w = _random_state(prob, 2, seed=1)
+    psi[1, 0, 3] += 0.1
+    with pytest.raises(pkg.AfqmcError) as e:
+        ctx.set_walkers(psi, w, 0)
+    assert e.value.name == "AFQMC_EINVAL"
+
+
+def test_synchronize_timeout_is_bounded():
+    prob = config_medium()
+    ctx = _ctx(prob, 64, prec="fp64")
+    ctx.propagate(3)
+    with pytest.raises(pkg.AfqmcError) as e:
+        ctx.synchronize(1e-6)
+    assert e.value.name == "AFQMC_ETIMEOUT"
+    ctx.synchronize(120.0)
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_reduced_precision_energy_within_tolerance(prec):
+    """|E_red - E_fp64| <= 0.1 mHa per step over a 10-step horizon with identical fields (no comb)."""
+    prob = config_medium()
+    nw = 64
+    e = {}
+    for p in ("fp64", prec):
+        ctx = _ctx(prob, nw, prec=p, seed=9)
+        e[p] = ctx.run(10, energy_every=1, reortho_every=5, comb_every=0)
+        ctx.close()
+    d = np.abs(e[prec][:, 0] / e[prec][:, 1] - e["fp64"][:, 0] / e["fp64"][:, 1])
+    assert np.max(d) <= 1e-4, d
+
+
+def test_full_size_sampled_walkers():
+    """N=108, 21+21, naux=432, 640 walkers (the benchmark workload): sampled walkers against the oracle."""
+    prob = config_medium()
+    nw, seed, dt = 640, 240616240, 0.005
+    st = _setup(prob, dt)
+    ctx = _ctx(prob, nw, seed=seed, dt=dt)
+    assert abs(ctx.info()["e_var"] - st.evar) < 1e-11 * abs(st.evar)
+    sums0, eloc0 = ctx.local_energy(per_walker=True)
+    assert np.allclose(eloc0[:, 0], st.evar, rtol=1e-11)
+    ctx.propagate(1)
+    sums1, eloc1 = ctx.local_energy(per_walker=True)
+    psi_g, logo_g, w_g, _ = ctx.get_walkers()
+    x = philox.normals(seed, 0, nw, prob.naux)
+    psi0 = prob.psiT.astype(complex)
+    lo0, ta, tb = orc.overlap_theta(st, psi0)
+    vb = orc.force_bias(st, ta, tb)
+    xbar = orc.field_shift(st, vb, 1.0)
+    for i in (0, 1, 333, 639):
+        p1, cmf = orc.propagate_determinant(st, psi0, x[i] - xbar)
+        lo1, ta1, tb1 = orc.overlap_theta(st, p1)
+        w1, _, _ = orc.weight_update(st, 1.0, lo0, lo1, cmf, x[i], xbar, st.evar)
+        assert np.allclose(psi_g[i], p1, atol=1e-11)
+        assert abs(w_g[i] - w1) < 1e-11 * w1
+        e1 = orc.local_energy(st, ta1, tb1)[0]
+        assert abs(eloc1[i, 0] - e1) < 1e-10 * abs(e1)
