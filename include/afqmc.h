@@ -176,6 +176,26 @@ afqmc_status afqmc_synchronize(afqmc_ctx* ctx, double timeout_s);
 /* Free host-side state (the caller frees the workspace afterwards). */
 void afqmc_destroy(afqmc_ctx* ctx);
 
+/* Tracing: per-stage device time from CUDA events recorded on the context's
+ * stream around each stage.  enable = 1 resets the counters and starts
+ * recording, 0 stops.  afqmc_stage_times synchronises the stream and returns,
+ * for each of the AFQMC_NSTAGES stages, the accumulated milliseconds and the
+ * number of timed stage executions (either output may be NULL). */
+enum {
+  AFQMC_STAGE_OVERLAP = 0,     /* overlap, LU, log det, Theta (+ weight update) */
+  AFQMC_STAGE_FORCE_BIAS = 1,  /* vbias when the energy was not measured at the same walkers */
+  AFQMC_STAGE_EXCHANGE = 2,    /* T = Ltilde Theta contraction: exchange partials + vbias */
+  AFQMC_STAGE_ENERGY = 3,      /* per-walker E_L assembly and the weighted sums */
+  AFQMC_STAGE_FIELDS = 4,      /* Philox fields, shift, VHS coefficients */
+  AFQMC_STAGE_VHS = 5,         /* VHS = sum_g coef_g L^g */
+  AFQMC_STAGE_PROPAGATE = 6,   /* exp(-dt/2 h_eff) Taylor(VHS) exp(-dt/2 h_eff) on the walkers */
+  AFQMC_STAGE_QR = 7,
+  AFQMC_STAGE_COMB = 8,
+  AFQMC_NSTAGES = 9
+};
+afqmc_status afqmc_profile(afqmc_ctx* ctx, int32_t enable);
+afqmc_status afqmc_stage_times(afqmc_ctx* ctx, double* ms, int64_t* count);
+
 /* Number of kernel launches the context has issued (for launch accounting). */
 uint64_t afqmc_launch_count(afqmc_ctx* ctx);
 

@@ -21,6 +21,9 @@ STATUS = {0: "AFQMC_OK", 1: "AFQMC_EINVAL", 2: "AFQMC_ENOMEM", 3: "AFQMC_ECUDA",
           5: "AFQMC_ENONFINITE", 6: "AFQMC_ENOWALKERS", 7: "AFQMC_ETIMEOUT"}
 
 
+STAGES = ["overlap", "force_bias", "exchange", "energy", "fields", "vhs", "propagate", "qr", "comb"]
+
+
 class AfqmcError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
@@ -66,6 +69,8 @@ SIGNATURES = {
     "afqmc_synchronize": (_i32, [_vp, ctypes.c_double]),
     "afqmc_destroy": (None, [_vp]),
     "afqmc_launch_count": (_u64, [_vp]),
+    "afqmc_profile": (_i32, [_vp, _i32]),
+    "afqmc_stage_times": (_i32, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "afqmc_last_error": (ctypes.c_char_p, []),
 }
 
@@ -200,6 +205,16 @@ class Afqmc:
 
     def synchronize(self, timeout_s=60.0):
         _check(self._lib.afqmc_synchronize(self._ctx, float(timeout_s)))
+
+    def profile(self, enable=True):
+        _check(self._lib.afqmc_profile(self._ctx, 1 if enable else 0))
+
+    def stage_times(self):
+        """{stage name: (milliseconds, timed executions)} since profile(True)."""
+        ms = np.zeros(len(STAGES))
+        cnt = (ctypes.c_int64 * len(STAGES))()
+        _check(self._lib.afqmc_stage_times(self._ctx, _ptr(ms), cnt))
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(STAGES)}
 
     def launch_count(self):
         return int(self._lib.afqmc_launch_count(self._ctx))

@@ -214,10 +214,59 @@ struct afqmc_ctx {
   unsigned long long seed, host_step, launches;
   bool theta_fresh, vbias_fresh;
   int hist_used;
+  // tracing
+  bool prof = false;
+  std::vector<cudaEvent_t> free_events;
+  struct Pending { int stage; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  double stage_ms[AFQMC_NSTAGES] = {};
+  long long stage_n[AFQMC_NSTAGES] = {};
+  ~afqmc_ctx() {
+    for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : free_events) cudaEventDestroy(e);
+  }
+  cudaEvent_t take_event() {
+    if (!free_events.empty()) { cudaEvent_t e = free_events.back(); free_events.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  void drain() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        stage_ms[p.stage] += ms;
+        stage_n[p.stage] += 1;
+      }
+      free_events.push_back(p.a);
+      free_events.push_back(p.b);
+    }
+    pending.clear();
+  }
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(base + off); }
 };
 
 namespace {
+
+// Records a CUDA event pair around a stage when tracing is on.
+struct StageTimer {
+  afqmc_ctx* c;
+  int id;
+  cudaEvent_t a = nullptr;
+  StageTimer(afqmc_ctx* ctx, int stage) : c(ctx), id(stage) {
+    if (!c->prof) return;
+    if (c->pending.size() > 4096) c->drain();
+    a = c->take_event();
+    if (a) cudaEventRecord(a, c->stream);
+  }
+  ~StageTimer() {
+    if (!a) return;
+    cudaEvent_t b = c->take_event();
+    if (!b) { c->free_events.push_back(a); return; }
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({id, a, b});
+  }
+};
 
 // --------------------------------------------------------------------------------------
 template <typename R, bool CA, bool CB>
@@ -264,6 +313,7 @@ size_t overlap_smem(const Dims& d) {
 
 template <typename R>
 afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
+  StageTimer timer(c, AFQMC_STAGE_OVERLAP);
   const size_t sm = overlap_smem(c->d);
   k_overlap<R><<<c->d.W, 256, sm, c->stream>>>(overlap_args<R>(c, mode));
   CHECK_LAUNCH(c);
@@ -316,6 +366,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
     if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
     c->theta_fresh = true;
   }
+  StageTimer* tx = new StageTimer(c, AFQMC_STAGE_EXCHANGE);
   if (c->d.prec == AFQMC_PREC_BF16 || c->d.prec == AFQMC_PREC_BF16X3) {
     if ((st = tc::exchange(c->d.prec, c->stream, c->at<char>(c->L.tc), c->d.W, c->d.N, c->d.X, c->d.ncol, c->d.c0,
                            c->d.nbk, c->d.nblk, c->smul, c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias),
@@ -324,6 +375,8 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
   } else {
     if ((st = launch_exchange<R>(c, 1)) != AFQMC_OK) return st;
   }
+  delete tx;
+  StageTimer te(c, AFQMC_STAGE_ENERGY);
   k_energy_walker<R><<<c->d.W, 256, 0, c->stream>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
                                                    c->at<cplx_t<R>>(c->L.thetaT), c->at<double>(c->L.hrot),
                                                    c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
@@ -345,6 +398,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     c->theta_fresh = true;
   }
   if (!c->vbias_fresh) {
+    StageTimer timer(c, AFQMC_STAGE_FORCE_BIAS);
     if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
       if ((st = tc::force_bias(d.prec, c->stream, c->at<char>(c->L.tc), d.W, d.N, d.X, d.ncol, c->smul,
                                c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias), &c->launches)) != AFQMC_OK)
@@ -359,6 +413,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
       if ((st = gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
     }
   }
+  StageTimer* tf = new StageTimer(c, AFQMC_STAGE_FIELDS);
   FieldArgs<R> fa{};
   fa.X = d.X; fa.sdt = c->sdt; fa.cap = c->cap; fa.seed = c->seed;
   fa.step = c->at<unsigned long long>(c->L.step);
@@ -366,9 +421,11 @@ afqmc_status step_impl(afqmc_ctx* c) {
   fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
   fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
   k_fields<R><<<d.W, 256, 0, c->stream>>>(fa);
+  delete tf;
   CHECK_LAUNCH(c);
   const long long NN = (long long)d.N * d.N, Nc = (long long)d.N * d.ncol;
   // VHS[w][pq] = sum_g coef[w][g] L[g][pq]
+  StageTimer* tv = new StageTimer(c, AFQMC_STAGE_VHS);
   if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
     if ((st = tc::vhs(d.prec, c->stream, c->at<char>(c->L.tc), d.W, d.N, d.X, c->at<float2>(c->L.coef),
                       c->at<float2>(c->L.vhs), &c->launches)) != AFQMC_OK)
@@ -380,8 +437,10 @@ afqmc_status step_impl(afqmc_ctx* c) {
     g.C = c->at<R2>(c->L.vhs); g.sCm = NN; g.sCn = 1;
     if ((st = gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
   }
+  delete tv;
   // psi <- E_h Taylor(VHS) E_h psi   (tA = accumulator, tB/tC = Taylor terms)
   const double* skip = c->at<double>(c->L.w);
+  StageTimer* tp = new StageTimer(c, AFQMC_STAGE_PROPAGATE);
   {
     GemmDesc g = gdesc(d.N, d.ncol, d.N, d.W);
     g.A = c->at<R>(c->L.eh); g.sAb = 0; g.sAm = d.N; g.sAk = 1;
@@ -411,6 +470,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     g.skip = skip;
     if ((st = gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
   }
+  delete tp;
   if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
   c->theta_fresh = true;
   c->vbias_fresh = false;
@@ -422,6 +482,7 @@ template <typename R>
 afqmc_status qr_impl(afqmc_ctx* c) {
   const Dims& d = c->d;
   const size_t sm = (size_t)std::max(d.nbk[0], d.nbk[1]) * d.N * sizeof(double2);
+  StageTimer timer(c, AFQMC_STAGE_QR);
   k_qr<R><<<d.W, 256, sm, c->stream>>>(d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1], c->smul,
                                        c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO), c->at<double>(c->L.w));
   CHECK_LAUNCH(c);
@@ -434,6 +495,7 @@ template <typename R>
 afqmc_status comb_impl(afqmc_ctx* c) {
   const Dims& d = c->d;
   using R2 = cplx_t<R>;
+  StageTimer timer(c, AFQMC_STAGE_COMB);
   k_comb_plan<<<1, 256, 0, c->stream>>>(d.W, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.w),
                                         c->at<double>(c->L.cum), c->at<int>(c->L.src), c->at<double>(c->L.neww),
                                         c->at<int>(c->L.status));
@@ -682,6 +744,30 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
 void afqmc_destroy(afqmc_ctx* ctx) { delete ctx; }
 
 uint64_t afqmc_launch_count(afqmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+afqmc_status afqmc_profile(afqmc_ctx* ctx, int32_t enable) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (enable) {
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->drain();
+    for (int i = 0; i < AFQMC_NSTAGES; ++i) { ctx->stage_ms[i] = 0.0; ctx->stage_n[i] = 0; }
+  }
+  ctx->prof = enable != 0;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_stage_times(afqmc_ctx* ctx, double* ms, int64_t* count) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->drain();
+  for (int i = 0; i < AFQMC_NSTAGES; ++i) {
+    if (ms) ms[i] = ctx->stage_ms[i];
+    if (count) count[i] = ctx->stage_n[i];
+  }
+  return AFQMC_OK;
+}
 
 afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps) {
   afqmc_status st = check_ctx(ctx);
