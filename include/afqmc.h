@@ -201,6 +201,34 @@ uint64_t afqmc_launch_count(afqmc_ctx* ctx);
 
 const char* afqmc_last_error(void);
 
+/* Comb population-control plan that allocates nothing.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory: callers whose device memory is owned entirely by another
+ * allocator (a framework's caching pool or an arena reserved up front), and
+ * callers in latency-critical loops that must not trigger the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree.  It needs no context and
+ * no workspace.
+ *   w       device, [nwalkers] binary64 walker weights (input)
+ *   src     device, [nwalkers] int32: source walker of every new slot (output)
+ *   neww    device, one binary64: the common new weight W_tot / nwalkers, or
+ *           -1 if no weight is positive (src is then the identity) (output)
+ * xi comes from Philox stream 1 at counter `step`, exactly as in
+ * afqmc_popcontrol, so src and neww equal what afqmc_popcontrol applies.
+ * Scratch: the prefix sums live in a file-scope device array of
+ * AFQMC_NOALLOC_MAX_WALKERS + 64 eight-byte words (about 513 KiB) that every
+ * GPU which loads the library holds until the process exits; nwalkers above
+ * AFQMC_NOALLOC_MAX_WALKERS is rejected with AFQMC_EINVAL.  The first call on
+ * a device looks the array's address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array and overwrites it: calls whose kernels can overlap
+ * on the GPU (other streams, other host threads) race and may return wrong
+ * plans, so order them on one stream.  Enqueued on `stream` (NULL: default
+ * stream); returns without synchronising.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+#define AFQMC_NOALLOC_MAX_WALKERS 65536
+afqmc_status afqmc_comb_plan_noalloc(const double* w, int32_t nwalkers, uint64_t seed, uint64_t step,
+                                     int32_t* src, double* neww, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

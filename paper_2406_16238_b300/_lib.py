@@ -72,6 +72,7 @@ SIGNATURES = {
     "afqmc_profile": (_i32, [_vp, _i32]),
     "afqmc_stage_times": (_i32, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "afqmc_last_error": (ctypes.c_char_p, []),
+    "afqmc_comb_plan_noalloc": (_i32, [_vp, _i32, _u64, _u64, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -241,3 +242,21 @@ def draw_normals(seed, step, nwalkers, naux, stream_id=0, device="cuda"):
     _check(lib.afqmc_draw_normals(int(seed), int(step), int(stream_id), int(nwalkers), int(naux),
                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
     return out
+
+
+NOALLOC_MAX_WALKERS = 65536
+
+
+def comb_plan_noalloc(w, seed, step, src, neww, stream=None):
+    """afqmc_comb_plan_noalloc on caller-owned device tensors (w float64 [W], src int32 [W], neww float64 [1]).
+
+    For callers that cannot allocate device memory: the library uses a static
+    device array for its scratch and allocates nothing; the caller owns every
+    buffer passed here.  Enqueued on `stream` (default: the current stream).
+    """
+    import torch
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream(w.device)
+    _check(lib.afqmc_comb_plan_noalloc(ctypes.c_void_p(w.data_ptr()), int(w.numel()), int(seed) & (2 ** 64 - 1),
+                                       int(step), ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(neww.data_ptr()),
+                                       ctypes.c_void_p(s.cuda_stream)))

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <chrono>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -979,3 +980,57 @@ afqmc_status afqmc_synchronize(afqmc_ctx* ctx, double timeout_s) {
 }
 
 }  // extern "C"
+
+// ======================================================================================
+// Comb plan without allocation (afqmc_comb_plan_noalloc).  The prefix-sum scratch of
+// k_comb_plan lives in this file-scope device array instead of a workspace: words
+// [0, AFQMC_NOALLOC_MAX_WALKERS) hold the prefix sums, the tail holds the step counter
+// and the status word.  Host code never dereferences the symbol: it looks up the
+// array's device address once per device and passes that pointer to the kernels.
+namespace {
+
+static __device__ __align__(256) unsigned long long g_comb_scratch[AFQMC_NOALLOC_MAX_WALKERS + 64];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_comb_scratch_mu;
+void* g_comb_scratch_addr[kMaxDevices] = {};
+
+__global__ void k_store_step(unsigned long long* dst, unsigned long long v) { *dst = v; }
+
+}  // namespace
+
+extern "C" afqmc_status afqmc_comb_plan_noalloc(const double* w, int32_t nwalkers, uint64_t seed, uint64_t step,
+                                                int32_t* src, double* neww, void* stream) {
+  if (nwalkers < 1 || nwalkers > AFQMC_NOALLOC_MAX_WALKERS)
+    return fail(AFQMC_EINVAL, "afqmc_comb_plan_noalloc: nwalkers = %d outside [1, %d] (the static scratch holds "
+                              "%d prefix sums)", nwalkers, AFQMC_NOALLOC_MAX_WALKERS, AFQMC_NOALLOC_MAX_WALKERS);
+  if (!w || !src || !neww) return fail(AFQMC_EINVAL, "afqmc_comb_plan_noalloc: w, src and neww are required");
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(AFQMC_EINVAL, "afqmc_comb_plan_noalloc: device %d unsupported", dev);
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_comb_scratch_mu);
+    if (!g_comb_scratch_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_comb_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      g_comb_scratch_addr[dev] = p;
+    }
+    base = g_comb_scratch_addr[dev];
+  }
+  unsigned long long* words = static_cast<unsigned long long*>(base);
+  double* cum = reinterpret_cast<double*>(words);
+  unsigned long long* step_word = words + AFQMC_NOALLOC_MAX_WALKERS;
+  int* status = reinterpret_cast<int*>(words + AFQMC_NOALLOC_MAX_WALKERS + 1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CU(cudaMemsetAsync(status, 0, sizeof(int), s));
+  k_store_step<<<1, 1, 0, s>>>(step_word, (unsigned long long)step);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc launch: %s", cudaGetErrorString(e));
+  k_comb_plan<<<1, 256, 0, s>>>(nwalkers, seed, step_word, w, cum, src, neww, status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc launch: %s", cudaGetErrorString(e));
+  return AFQMC_OK;
+}
