@@ -55,6 +55,7 @@ struct Dims {
   int prec;
   int gchunk, nchunk;
   size_t rsz() const { return prec == AFQMC_PREC_FP64 ? 8 : 4; }
+  bool tensor() const { return prec == AFQMC_PREC_BF16 || prec == AFQMC_PREC_BF16X3; }
 };
 
 // Offsets of every device buffer inside the workspace.
@@ -106,7 +107,10 @@ Layout plan(const Dims& d) {
   L.src = take(W * 4);
   L.cum = take(W * 8);
   L.neww = take(256);
-  L.tc_bytes = tc::operand_bytes(d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk);
+  {
+    tc::TcState tmp;
+    L.tc_bytes = tc::plan(&tmp, d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk);
+  }
   L.tc = take(L.tc_bytes);
   L.vhs_bytes = W * N * N * C;
   L.setup_bytes = align_up(X * N * N * 8, 256) * 2 + align_up(N * N * 8, 256) + align_up(X * nc * N * 8, 256);
@@ -143,6 +147,11 @@ afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta
   d->c0[1] = nalpha; d->nbk[1] = same ? 0 : nbeta;
   d->gchunk = 8;
   d->nchunk = (naux + d->gchunk - 1) / d->gchunk;
+  if (d->tensor()) {   // exchange partials come per (spin block, M tile) of the tensor-core kernel
+    tc::TcState tmp;
+    tc::plan(&tmp, d->prec, d->W, d->N, d->X, d->ncol, d->c0, d->nbk, d->nblk);
+    d->nchunk = tmp.nchunk;
+  }
   return AFQMC_OK;
 }
 
@@ -215,6 +224,7 @@ struct afqmc_ctx {
   unsigned long long seed, host_step, launches;
   bool theta_fresh, vbias_fresh;
   int hist_used;
+  tc::TcState tcs;
   // tracing
   bool prof = false;
   std::vector<cudaEvent_t> free_events;
@@ -369,9 +379,9 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
   }
   StageTimer* tx = new StageTimer(c, AFQMC_STAGE_EXCHANGE);
   if (c->d.prec == AFQMC_PREC_BF16 || c->d.prec == AFQMC_PREC_BF16X3) {
-    if ((st = tc::exchange(c->d.prec, c->stream, c->at<char>(c->L.tc), c->d.W, c->d.N, c->d.X, c->d.ncol, c->d.c0,
-                           c->d.nbk, c->d.nblk, c->smul, c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias),
-                           c->at<double2>(c->L.exch_part), c->d.nchunk, &c->launches)) != AFQMC_OK)
+    if ((st = tc::exchange(&c->tcs, c->stream, c->at<char>(c->L.tc), c->smul, c->at<float2>(c->L.thetaT),
+                           c->at<float2>(c->L.vbias), c->at<double2>(c->L.exch_part), c->at<int>(c->L.status),
+                           &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
       return st;
   } else {
     if ((st = launch_exchange<R>(c, 1)) != AFQMC_OK) return st;
@@ -400,11 +410,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   }
   if (!c->vbias_fresh) {
     StageTimer timer(c, AFQMC_STAGE_FORCE_BIAS);
-    if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
-      if ((st = tc::force_bias(d.prec, c->stream, c->at<char>(c->L.tc), d.W, d.N, d.X, d.ncol, c->smul,
-                               c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias), &c->launches)) != AFQMC_OK)
-        return st;
-    } else {
+    {
       // vbias[w][g] = smul * sum_k thetaT[w][k] * lrot[g][k],  k = (c, p)
       GemmDesc g = gdesc(d.W, d.X, d.ncol * d.N, 1);
       g.A = c->at<R2>(c->L.thetaT); g.sAm = (long long)d.ncol * d.N; g.sAk = 1;
@@ -427,9 +433,9 @@ afqmc_status step_impl(afqmc_ctx* c) {
   const long long NN = (long long)d.N * d.N, Nc = (long long)d.N * d.ncol;
   // VHS[w][pq] = sum_g coef[w][g] L[g][pq]
   StageTimer* tv = new StageTimer(c, AFQMC_STAGE_VHS);
-  if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
-    if ((st = tc::vhs(d.prec, c->stream, c->at<char>(c->L.tc), d.W, d.N, d.X, c->at<float2>(c->L.coef),
-                      c->at<float2>(c->L.vhs), &c->launches)) != AFQMC_OK)
+  if (d.tensor()) {   // planar fp32 output: VHS_w = vhs[w][0][:] + i vhs[w][1][:]
+    if ((st = tc::vhs(&c->tcs, c->stream, c->at<char>(c->L.tc), c->at<float2>(c->L.coef), c->at<float>(c->L.vhs),
+                      c->at<int>(c->L.status), &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
       return st;
   } else {
     GemmDesc g = gdesc(d.W, (int)NN, d.X, 1);
@@ -455,6 +461,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   for (int k = 1; k <= c->taylor; ++k) {
     GemmDesc g = gdesc(d.N, d.ncol, d.N, d.W);
     g.A = c->at<R2>(c->L.vhs); g.sAb = NN; g.sAm = d.N; g.sAk = 1;
+    if (d.tensor()) { g.a_planar = 1; g.a_im_off = NN; g.sAb = 2 * NN; }
     g.B = c->at<R2>(tin); g.sBb = Nc; g.sBk = d.ncol; g.sBn = 1;
     g.C = k < c->taylor ? c->at<R2>(tout) : nullptr; g.sCb = Nc; g.sCm = d.ncol; g.sCn = 1;
     g.D = c->at<R2>(c->L.tA); g.sDb = Nc; g.sDm = d.ncol; g.sDn = 1; g.d_add = 1;
@@ -528,6 +535,7 @@ afqmc_status read_status(afqmc_ctx* c) {
   CU(cudaStreamSynchronize(c->stream));
   if (st == 0) return AFQMC_OK;
   CU(cudaMemsetAsync(c->base + c->L.status, 0, sizeof(int), c->stream));
+  if (st & 8) return fail(AFQMC_ETIMEOUT, "a tensor-core kernel gave up waiting on its pipeline (bounded wait)");
   if (st & kStatusNoWalkers) return fail(AFQMC_ENOWALKERS, "all walker weights are zero");
   if (st & kStatusNonFinite) return fail(AFQMC_ENONFINITE, "a walker weight became non-finite (set to 0)");
   return fail(AFQMC_ESINGULAR, "a walker overlap matrix was singular (weight set to 0)");
@@ -638,8 +646,9 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * nc * N, lrot64, c->at<R>(c->L.lrot));
   CHECK_LAUNCH(c);
   if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
-    if ((st = tc::prepare(d.prec, c->stream, c->at<char>(c->L.tc), d.W, N, X, nc, d.c0, d.nbk, d.nblk, chol64,
-                          lrot64, &c->launches)) != AFQMC_OK)
+    tc::plan(&c->tcs, d.prec, d.W, N, X, nc, d.c0, d.nbk, d.nblk);
+    if ((st = tc::prepare(&c->tcs, c->stream, c->at<char>(c->L.tc), chol64, lrot64, &c->launches, g_err,
+                          sizeof(g_err))) != AFQMC_OK)
       return st;
   }
   CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));

@@ -22,6 +22,8 @@ struct GemmDesc {
   int d_add;
   double alpha_re, alpha_im;
   const double* skip;
+  int a_planar;          // complex A stored as separate real and imaginary planes
+  long long a_im_off;    // element offset of the imaginary plane (a_planar)
 };
 
 template <typename R, bool CA, bool CB>
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
   if (g.skip != nullptr && g.skip[b] == 0.0) return;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const char* Ab = (const char*)g.A + (size_t)b * g.sAb * (CA ? sizeof(R2) : sizeof(R));
+  const char* Ab = (const char*)g.A + (size_t)b * g.sAb * ((CA && !g.a_planar) ? sizeof(R2) : sizeof(R));
   const char* Bb = (const char*)g.B + (size_t)b * g.sBb * (CB ? sizeof(R2) : sizeof(R));
   R acc_re[4][4], acc_im[4][4];
 #pragma unroll
@@ -54,8 +56,10 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
       R vr = R(0), vi = R(0);
       if (m < g.M && k < g.K) {
         const long long idx = (long long)m * g.sAm + (long long)k * g.sAk;
-        if (CA) { R2 v = ((const R2*)Ab)[idx]; vr = v.x; vi = v.y; }
-        else vr = ((const R*)Ab)[idx];
+        if (CA) {
+          if (g.a_planar) { vr = ((const R*)Ab)[idx]; vi = ((const R*)Ab)[idx + g.a_im_off]; }
+          else { R2 v = ((const R2*)Ab)[idx]; vr = v.x; vi = v.y; }
+        } else vr = ((const R*)Ab)[idx];
       }
       As_re[kk][mm] = vr;
       if (CA) As_im[kk][mm] = vi;

@@ -1,24 +1,726 @@
-// Tensor-core (tcgen05) contractions for the BF16 and BF16x3 forms.
+// Tensor-core (tcgen05 + TMA) contractions for the BF16 and BF16x3 forms.
+//
+// One persistent, warp-specialised GEMM kernel D = A B^T (A [M][K], B [Ncols][K],
+// both bf16 K-major, fp32 accumulation in tensor memory) with two epilogues:
+//   EPI 0 (exchange): the tile holds T^{g}_{ab} for gpt gammas x wpt walkers;
+//          the epilogue forms Tr T (force bias) and sum_ab T_ab T_ba (exchange).
+//   EPI 1 (store): the tile is written to an fp32 matrix (the VHS build).
+// Roles per CTA: warp 0 issues TMA loads into a ring of shared-memory stages,
+// warp 1 allocates tensor memory and one of its threads issues tcgen05.mma
+// (M = 128, N = bn, K = 16 per instruction) into one of two accumulators,
+// warps 2.. read the finished accumulator with tcgen05.ld while the next tile
+// is being multiplied.  Every wait is bounded: on timeout the kernel records
+// kStatusTimeout, the roles stop, and tensor memory is released.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
 #include "tc_gemm.cuh"
 
 namespace afq {
 namespace tc {
 
-size_t operand_bytes(int prec, int, int, int, int, const int*, const int*, int) {
-  (void)prec;
-  return 0;
+constexpr int kBM = 128;
+constexpr int kBK = 64;                          // bf16 elements per 128-byte swizzled row
+constexpr int kStageA = kBM * kBK * 2;           // 16 KiB
+constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr int kStatusTimeout = 8;
+constexpr int kMaxSmem = 227 * 1024;
+
+struct Geom {
+  int m_tiles, n_tiles, k_blocks;
+  int m_step, n_step;       // TMA row coordinate of tile (mt, nt): mt * m_step, nt * n_step
+  int bn;                   // MMA N
+  int stages, epi_groups;
+  int epi_bytes;            // per epilogue group
+  int tmem_cols;
+};
+
+struct Params {
+  Geom g;
+  int* status;
+  // exchange epilogue
+  int W, X, n, gpt, wpt, chunk_offset, nchunk, vbias_add;
+  float smul;
+  float2* vbias;
+  double2* exch_part;
+  // store epilogue
+  float* out;
+  long long ldo;
+  int out_rows, out_cols;
+};
+
+// ----------------------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase of `parity`; false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-static afqmc_status not_built() { return AFQMC_EINVAL; }
+// 32 lanes x 32-bit, N consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld1(uint32_t taddr, float* v) {
+  uint32_t r;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r);
+}
 
-afqmc_status prepare(int, cudaStream_t, char*, int, int, int, int, const int*, const int*, int, const double*,
-                     const double*, unsigned long long*) { return not_built(); }
-afqmc_status exchange(int, cudaStream_t, char*, int, int, int, int, const int*, const int*, int, double,
-                      const float2*, float2*, double2*, int, unsigned long long*) { return not_built(); }
-afqmc_status force_bias(int, cudaStream_t, char*, int, int, int, int, double, const float2*, float2*,
-                        unsigned long long*) { return not_built(); }
-afqmc_status vhs(int, cudaStream_t, char*, int, int, int, const float2*, float2*, unsigned long long*) {
-  return not_built();
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = 128, N = bn.
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Columns [col, col + ncols) of this thread's accumulator row into dst (shared memory).
+__device__ __forceinline__ void tmem_row_to_smem(uint32_t taddr, int ncols, float* dst) {
+  float v[16];
+  int c = 0;
+  for (; c + 16 <= ncols; c += 16) {
+    tmem_ld16(taddr + c, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dst[c + i] = v[i];
+  }
+  for (; c + 4 <= ncols; c += 4) {
+    tmem_ld4(taddr + c, v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dst[c + i] = v[i];
+  }
+  for (; c < ncols; ++c) {
+    tmem_ld1(taddr + c, v);
+    dst[c] = v[0];
+  }
+}
+
+// ----------------------------------------------------------------------------- epilogues
+struct EpiSmem {
+  float* buf;      // [128][2n + 1]
+  float2* diag;    // [128]
+  float2* red;     // [4]
+  int* ok;
+};
+
+// Group region: [ok flag (16 B)] [buf] [diag] [red]; the store epilogue uses only the flag.
+__device__ __forceinline__ EpiSmem epi_smem(uint8_t* base, const Params& p, int group) {
+  EpiSmem e;
+  uint8_t* g = base + (size_t)group * p.g.epi_bytes;
+  const int ld = 2 * p.n + 1;
+  e.ok = reinterpret_cast<int*>(g);
+  e.buf = reinterpret_cast<float*>(g + 16);
+  e.diag = reinterpret_cast<float2*>(g + 16 + ((128 * ld * 4 + 15) & ~15));
+  e.red = e.diag + 128;
+  return e;
+}
+
+__device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
+                              int wig, int r, int lane) {
+  const int n = p.n, n2 = 2 * n, ld = n2 + 1, rows = p.gpt * n;
+  const int bar_id = 1 + group, nthr = 128;
+  for (int v = group; v < p.wpt; v += p.g.epi_groups) {
+    const int w = nt * p.wpt + v;
+    tmem_row_to_smem(tacc + (uint32_t)(v * n2), n2, e.buf + r * ld);
+    named_bar(bar_id, nthr);
+    float er = 0.f, ei = 0.f;
+    float2 dg = make_float2(0.f, 0.f);
+    if (r < rows) {
+      const int g = r / n, a = r % n;
+      if (mt * p.gpt + g < p.X) {
+        const float* rowr = e.buf + r * ld;
+        const float* blk = e.buf + (g * n) * ld;
+        for (int b = 0; b < n; ++b) {
+          const float tr = rowr[b], ti = rowr[n + b];
+          const float ur = blk[b * ld + a], ui = blk[b * ld + n + a];
+          er += tr * ur - ti * ui;
+          ei += tr * ui + ti * ur;
+        }
+        dg = make_float2(rowr[a], rowr[n + a]);
+      }
+    }
+    e.diag[r] = dg;
+    er = warp_sum_f(er);
+    ei = warp_sum_f(ei);
+    if (lane == 0) e.red[wig] = make_float2(er, ei);
+    named_bar(bar_id, nthr);
+    if (w < p.W && wig == 0) {
+      for (int gl = lane; gl < p.gpt; gl += 32) {
+        const int gam = mt * p.gpt + gl;
+        if (gam >= p.X) continue;
+        float sr = 0.f, si = 0.f;
+        for (int a = 0; a < n; ++a) {
+          sr += e.diag[gl * n + a].x;
+          si += e.diag[gl * n + a].y;
+        }
+        float2* dst = p.vbias + (size_t)w * p.X + gam;
+        float2 val = make_float2(p.smul * sr, p.smul * si);
+        if (p.vbias_add) {
+          val.x += dst->x;
+          val.y += dst->y;
+        }
+        *dst = val;
+      }
+      if (lane == 0) {
+        const double sr = (double)e.red[0].x + e.red[1].x + e.red[2].x + e.red[3].x;
+        const double si = (double)e.red[0].y + e.red[1].y + e.red[2].y + e.red[3].y;
+        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] = make_double2(p.smul * sr, p.smul * si);
+      }
+    }
+    named_bar(bar_id, nthr);
+  }
+}
+
+__device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
+  const int row = mt * p.g.m_step + r;
+  const int c0 = nt * p.g.n_step;
+  const int ncols = p.g.bn / p.g.epi_groups;     // each group covers a contiguous half of the columns
+  const int cbeg = group * ncols;
+  float v[16];
+  for (int c = cbeg; c < cbeg + ncols; c += 16) {
+    tmem_ld16(tacc + (uint32_t)c, v);
+    if (row >= p.out_rows) continue;
+    float* dst = p.out + (size_t)row * p.ldo + c0 + c;
+    const int rem = p.out_cols - (c0 + c);
+    if (rem >= 16 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+      for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    } else {
+      for (int i = 0; i < 16 && i < rem; ++i) dst[i] = v[i];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- the kernel
+template <int EPI>
+__global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                    const __grid_constant__ CUtensorMap mapB, const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const Geom& g = p.g;
+  const int stage_bytes = kStageA + g.bn * kBK * 2;
+  uint8_t* epi_base = smem + (size_t)g.stages * stage_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + (size_t)g.epi_groups * g.epi_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + g.stages;
+  uint64_t* tfull = bars + 2 * g.stages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = g.m_tiles * g.n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < g.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4 * g.epi_groups);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(g.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {   // TMA producer
+      int stage = 0;
+      uint32_t ph = 0;
+      bool go = true;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
+        const int mt = t % g.m_tiles, nt = t / g.m_tiles;
+        for (int kb = 0; kb < g.k_blocks; ++kb) {
+          if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
+          uint8_t* sa = smem + (size_t)stage * stage_bytes;
+          mbar_expect_tx(&full[stage], (uint32_t)stage_bytes);
+          tma_load_2d(sa, &mapA, &full[stage], kb * kBK, mt * g.m_step);
+          tma_load_2d(sa + kStageA, &mapB, &full[stage], kb * kBK, nt * g.n_step);
+          if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+        }
+      }
+      if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      int stage = 0;
+      uint32_t ph = 0;
+      int it = 0;
+      bool go = true;
+      const uint32_t idesc = idesc_bf16(g.bn);
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+        if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { go = false; break; }
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(acc * g.bn);
+        for (int kb = 0; kb < g.k_blocks; ++kb) {
+          if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes), sb = sa + kStageA;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
+          umma_commit(&empty[stage]);
+          if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+        }
+        if (!go) break;
+        umma_commit(&tfull[acc]);
+      }
+      if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else {   // epilogue warps
+    const int ew = warp - 2, group = ew >> 2, wig = ew & 3, q = warp & 3;
+    const int r = 32 * q + lane;
+    const EpiSmem es = epi_smem(epi_base, p, group);
+    int it = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+      const int acc = it & 1;
+      const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+      if (wig == 0 && lane == 0) {
+        const bool ok = mbar_wait(&tfull[acc], aph, abort_flag);
+        if (!ok) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+        *es.ok = ok ? 1 : 0;
+      }
+      named_bar(1 + group, 128);
+      const int ok = *es.ok;
+      named_bar(1 + group, 128);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
+      const int mt = t % g.m_tiles, nt = t / g.m_tiles;
+      if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
+      else store_tile(p, mt, nt, tacc, group, r);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) {   // let in-flight copies and MMAs drain before freeing tensor memory
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < 2000000ull) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(g.tmem_cols) : "memory");
+}
+
+// ----------------------------------------------------------------------------- operand conversion
+// Theta^T complex64 [W][ncol][N] -> per block rows (w, part, b) of nseg * kst bf16: B = [hi | hi | lo].
+__global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int nseg, const float2* thetaT,
+                             __nv_bfloat16* out) {
+  const int w = blockIdx.x;
+  const int rowlen = nseg * kst;
+  for (int idx = threadIdx.x; idx < 2 * n * kst; idx += blockDim.x) {
+    const int row = idx / kst, pp = idx % kst;
+    const int part = row / n, b = row % n;
+    float v = 0.f;
+    if (pp < N) {
+      const float2 t = thetaT[((size_t)w * ncol + c0 + b) * N + pp];
+      v = part ? t.y : t.x;
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16* dst = out + ((size_t)w * 2 * n + row) * rowlen + pp;
+    dst[0] = hi;
+    if (nseg == 3) {
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      dst[kst] = hi;
+      dst[2 * kst] = lo;
+    }
+  }
+}
+
+// Ltilde binary64 [X][ncol][N] -> block rows (g, a) of nseg * kst bf16: A = [hi | lo | hi].
+__global__ void k_lrot_bf16(int X, int N, int ncol, int c0, int n, int kst, int nseg, const double* lrot,
+                            __nv_bfloat16* out) {
+  const int rowlen = nseg * kst;
+  const size_t total = (size_t)X * n * kst;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = idx / kst;
+    const int pp = (int)(idx % kst);
+    const int g = (int)(row / n), a = (int)(row % n);
+    const double v = pp < N ? lrot[((size_t)g * ncol + c0 + a) * N + pp] : 0.0;
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    __nv_bfloat16* dst = out + row * rowlen + pp;
+    dst[0] = hi;
+    if (nseg == 3) {
+      dst[kst] = __double2bfloat16(v - (double)__bfloat162float(hi));
+      dst[2 * kst] = hi;
+    }
+  }
+}
+
+// L binary64 [X][N][N] -> Lt rows pq of nseg * kx bf16 (gamma contiguous): B = [hi | hi | lo].
+__global__ void k_lt_bf16(int X, int NN, int kx, int nseg, const double* chol, __nv_bfloat16* out) {
+  const int rowlen = nseg * kx;
+  const size_t total = (size_t)NN * kx;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t pq = idx / kx;
+    const int g = (int)(idx % kx);
+    const double v = g < X ? chol[(size_t)g * NN + pq] : 0.0;
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    __nv_bfloat16* dst = out + pq * rowlen + g;
+    dst[0] = hi;
+    if (nseg == 3) {
+      dst[kx] = hi;
+      dst[2 * kx] = __double2bfloat16(v - (double)__bfloat162float(hi));
+    }
+  }
+}
+
+// VHS coefficients complex64 [W][X] -> rows (w, part) of nseg * kx bf16: A = [hi | lo | hi].
+__global__ void k_coef_bf16(int W, int X, int kx, int nseg, const float2* coef, __nv_bfloat16* out) {
+  const int w = blockIdx.x;
+  const int rowlen = nseg * kx;
+  for (int idx = threadIdx.x; idx < 2 * kx; idx += blockDim.x) {
+    const int part = idx / kx, g = idx % kx;
+    float v = 0.f;
+    if (g < X) {
+      const float2 c = coef[(size_t)w * X + g];
+      v = part ? c.y : c.x;
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16* dst = out + ((size_t)w * 2 + part) * rowlen + g;
+    dst[0] = hi;
+    if (nseg == 3) {
+      dst[kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+      dst[2 * kx] = hi;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+namespace {
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int epi_bytes_exchange(int n) {
+  const int ld = 2 * n + 1;
+  return 16 + ((128 * ld * 4 + 15) & ~15) + 128 * 8 + 4 * 8;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, unsigned long long rows, unsigned long long kcols, unsigned box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {kcols, rows};
+  const cuuint64_t strides[1] = {kcols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+int tmem_cols_for(int bn) {
+  int c = 32;
+  while (c < 2 * bn) c <<= 1;
+  return c;
+}
+
+// Pick the stage count for a given B box height and epilogue footprint.
+bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
+  g->epi_groups = epi_groups;
+  g->epi_bytes = epi_bytes_per_group;
+  const int stage_bytes = kStageA + g->bn * kBK * 2;
+  const int fixed = 1024 + epi_groups * epi_bytes_per_group + 256;
+  int st = (kMaxSmem - fixed) / stage_bytes;
+  if (st > 4) st = 4;
+  if (st < 2) return false;
+  g->stages = st;
+  g->tmem_cols = tmem_cols_for(g->bn);
+  return g->tmem_cols <= 512;
+}
+
+size_t smem_bytes(const Geom& g) {
+  return 1024 + (size_t)g.stages * (kStageA + g.bn * kBK * 2) + (size_t)g.epi_groups * g.epi_bytes + 256;
+}
+
+template <int EPI>
+afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s,
+                    unsigned long long* launches, char* err, size_t errlen) {
+  const size_t sm = smem_bytes(g);
+  static size_t configured = 0;
+  if (sm > configured) {
+    if (cudaFuncSetAttribute(k_tc_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+      snprintf(err, errlen, "tcgen05 GEMM: cannot reserve %zu bytes of shared memory", sm);
+      return AFQMC_ECUDA;
+    }
+    configured = sm;
+  }
+  const int tiles = g.m_tiles * g.n_tiles;
+  const int grid = std::min(tiles, num_sms());
+  k_tc_gemm<EPI><<<grid, 64 + 128 * g.epi_groups, sm, s>>>(a, b, p);
+  ++*launches;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "tcgen05 GEMM launch: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
+}  // namespace
+
+size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk) {
+  if (prec != AFQMC_PREC_BF16 && prec != AFQMC_PREC_BF16X3) return 0;
+  st->prec = prec;
+  st->W = W; st->N = N; st->X = X; st->ncol = ncol; st->nblk = nblk;
+  st->nseg = prec == AFQMC_PREC_BF16X3 ? 3 : 1;
+  st->kst = (N + kBK - 1) / kBK * kBK;
+  st->kx = (X + kBK - 1) / kBK * kBK;
+  size_t cur = 0;
+  st->nchunk = 0;
+  for (int s = 0; s < nblk; ++s) {
+    BlockMaps& b = st->blk[s];
+    b.n = nb[s];
+    b.c0 = c0[s];
+    if (b.n == 0) { b.m_tiles = b.n_tiles = 0; continue; }
+    b.gpt = kBM / b.n;
+    b.wpt = 256 / (2 * b.n);
+    b.bn = (b.wpt * 2 * b.n + 15) / 16 * 16;
+    b.m_tiles = (X + b.gpt - 1) / b.gpt;
+    b.n_tiles = (W + b.wpt - 1) / b.wpt;
+    b.off_l = cur;
+    cur = align256(cur + (size_t)X * b.n * st->nseg * st->kst * 2);
+    b.off_th = cur;
+    cur = align256(cur + (size_t)W * 2 * b.n * st->nseg * st->kst * 2);
+    st->nchunk += b.m_tiles;
+  }
+  st->off_lt = cur;
+  cur = align256(cur + (size_t)N * N * st->nseg * st->kx * 2);
+  st->off_coef = cur;
+  cur = align256(cur + (size_t)W * 2 * st->nseg * st->kx * 2);
+  st->vhs_m_tiles = (2 * W + kBM - 1) / kBM;
+  st->vhs_n_tiles = (N * N + 255) / 256;
+  return cur;
+}
+
+afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* chol64, const double* lrot64,
+                     unsigned long long* launches, char* err, size_t errlen) {
+  if (!encode_fn()) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled is not available from the driver");
+    return AFQMC_ECUDA;
+  }
+  for (int b = 0; b < st->nblk; ++b) {
+    BlockMaps& bm = st->blk[b];
+    if (bm.n == 0) continue;
+    __nv_bfloat16* l = reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_l);
+    k_lrot_bf16<<<592, 256, 0, s>>>(st->X, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, lrot64, l);
+    ++*launches;
+    if (!make_map(&bm.map_l, l, (unsigned long long)st->X * bm.n, (unsigned long long)st->nseg * st->kst, kBM) ||
+        !make_map(&bm.map_th, tcbuf + bm.off_th, (unsigned long long)st->W * 2 * bm.n,
+                  (unsigned long long)st->nseg * st->kst, (unsigned)bm.bn)) {
+      snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the exchange operands");
+      return AFQMC_ECUDA;
+    }
+  }
+  __nv_bfloat16* lt = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt);
+  k_lt_bf16<<<1184, 256, 0, s>>>(st->X, st->N * st->N, st->kx, st->nseg, chol64, lt);
+  ++*launches;
+  if (!make_map(&st->map_lt, lt, (unsigned long long)st->N * st->N, (unsigned long long)st->nseg * st->kx, 256) ||
+      !make_map(&st->map_coef, tcbuf + st->off_coef, (unsigned long long)st->W * 2,
+                (unsigned long long)st->nseg * st->kx, kBM)) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS operands");
+    return AFQMC_ECUDA;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "tc prepare: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  st->ready = true;
+  return AFQMC_OK;
+}
+
+afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
+                      double2* exch_part, int* status, unsigned long long* launches, char* err, size_t errlen) {
+  int chunk = 0;
+  bool first = true;
+  for (int b = 0; b < st->nblk; ++b) {
+    BlockMaps& bm = st->blk[b];
+    if (bm.n == 0) continue;
+    k_theta_bf16<<<st->W, 256, 0, s>>>(st->W, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, thetaT,
+                                       reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th));
+    ++*launches;
+    Geom g{};
+    g.m_tiles = bm.m_tiles;
+    g.n_tiles = bm.n_tiles;
+    g.k_blocks = st->nseg * st->kst / kBK;
+    g.m_step = bm.gpt * bm.n;
+    g.n_step = bm.wpt * 2 * bm.n;
+    g.bn = bm.bn;
+    const int epb = epi_bytes_exchange(bm.n);
+    if (!finish_geom(&g, epb, 2) && !finish_geom(&g, epb, 1)) {
+      snprintf(err, errlen, "tcgen05 exchange: n = %d does not fit shared memory", bm.n);
+      return AFQMC_EINVAL;
+    }
+    Params p{};
+    p.g = g;
+    p.status = status;
+    p.W = st->W; p.X = st->X; p.n = bm.n; p.gpt = bm.gpt; p.wpt = bm.wpt;
+    p.chunk_offset = chunk; p.nchunk = st->nchunk; p.vbias_add = first ? 0 : 1;
+    p.smul = (float)smul;
+    p.vbias = vbias;
+    p.exch_part = exch_part;
+    afqmc_status r = launch<0>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    if (r != AFQMC_OK) return r;
+    chunk += bm.m_tiles;
+    first = false;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, float* out, int* status,
+                 unsigned long long* launches, char* err, size_t errlen) {
+  k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
+                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
+  ++*launches;
+  Geom g{};
+  g.m_tiles = st->vhs_m_tiles;
+  g.n_tiles = st->vhs_n_tiles;
+  g.k_blocks = st->nseg * st->kx / kBK;
+  g.m_step = kBM;
+  g.n_step = 256;
+  g.bn = 256;
+  if (!finish_geom(&g, 16, 2)) {
+    snprintf(err, errlen, "tcgen05 VHS: shared memory plan failed");
+    return AFQMC_EINVAL;
+  }
+  Params p{};
+  p.g = g;
+  p.status = status;
+  p.out = out;
+  p.ldo = (long long)st->N * st->N;
+  p.out_rows = 2 * st->W;
+  p.out_cols = st->N * st->N;
+  return launch<1>(g, st->map_coef, st->map_lt, p, s, launches, err, errlen);
 }
 
 }  // namespace tc
