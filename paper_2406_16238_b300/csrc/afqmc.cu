@@ -319,14 +319,23 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
 
 size_t overlap_smem(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return (size_t)2 * nmax * nmax * sizeof(double2);
+  return ((size_t)2 * nmax * nmax + nmax) * sizeof(double2) + (size_t)nmax * nmax * 2 * d.rsz();
 }
+
+size_t qr_smem(const Dims& d) {
+  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
+  return ((size_t)2 * nmax * nmax + (size_t)nmax * d.N) * sizeof(double2) + (size_t)nmax * nmax * 2 * d.rsz();
+}
+
+size_t prop_smem(const Dims& d) { return prop_smem_floats(d.N, d.ncol, nullptr, nullptr) * sizeof(float); }
+
+bool use_fused_propagation(const Dims& d) { return d.prec != AFQMC_PREC_FP64 && prop_smem(d) <= 227 * 1024; }
 
 template <typename R>
 afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
   StageTimer timer(c, AFQMC_STAGE_OVERLAP);
   const size_t sm = overlap_smem(c->d);
-  k_overlap<R><<<c->d.W, 256, sm, c->stream>>>(overlap_args<R>(c, mode));
+  k_overlap_gj<R><<<c->d.W, 256, sm, c->stream>>>(overlap_args<R>(c, mode));
   CHECK_LAUNCH(c);
   return AFQMC_OK;
 }
@@ -357,15 +366,16 @@ afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange) {
 
 template <typename R>
 afqmc_status set_smem_limits(const Dims& d) {
-  const size_t ov = overlap_smem(d), ex = exchange_smem(d);
-  const size_t qr = (size_t)std::max(d.nbk[0], d.nbk[1]) * d.N * sizeof(double2);
+  const size_t ov = overlap_smem(d), ex = d.tensor() ? 0 : exchange_smem(d), qr = qr_smem(d);
   const size_t lim = 227 * 1024;
   if (ov > lim || ex > lim || qr > lim)
     return fail(AFQMC_EINVAL, "problem too large for the CUDA-core kernels' shared-memory staging "
                               "(overlap %zu, exchange %zu, qr %zu bytes > %zu)", ov, ex, qr, lim);
-  CU(cudaFuncSetAttribute(k_overlap<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ov));
-  CU(cudaFuncSetAttribute(k_exchange<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ex));
-  CU(cudaFuncSetAttribute(k_qr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr));
+  CU(cudaFuncSetAttribute(k_overlap_gj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ov));
+  if (ex) CU(cudaFuncSetAttribute(k_exchange<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ex));
+  CU(cudaFuncSetAttribute(k_qr_chol<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr));
+  if (use_fused_propagation(d))
+    CU(cudaFuncSetAttribute(k_propagate_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prop_smem(d)));
   return AFQMC_OK;
 }
 
@@ -448,6 +458,29 @@ afqmc_status step_impl(afqmc_ctx* c) {
   // psi <- E_h Taylor(VHS) E_h psi   (tA = accumulator, tB/tC = Taylor terms)
   const double* skip = c->at<double>(c->L.w);
   StageTimer* tp = new StageTimer(c, AFQMC_STAGE_PROPAGATE);
+  if (use_fused_propagation(d)) {
+    PropArgs pa{};
+    pa.N = d.N; pa.ncol = d.ncol; pa.order = c->taylor;
+    prop_smem_floats(d.N, d.ncol, &pa.ldv, &pa.ldc);
+    pa.eh = c->at<float>(c->L.eh);
+    pa.vhs = c->base + c->L.vhs;
+    pa.planar = d.tensor() ? 1 : 0;
+    pa.psi = c->at<float2>(c->L.psi);
+    pa.w = skip;
+    pa.W = d.W;
+    pa.status = c->at<int>(c->L.status);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_propagate_smem<<<std::min(d.W, sms), 256, prop_smem(d), c->stream>>>(pa);
+    delete tp;
+    CHECK_LAUNCH(c);
+    if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
+    c->theta_fresh = true;
+    c->vbias_fresh = false;
+    c->host_step++;
+    return AFQMC_OK;
+  }
   {
     GemmDesc g = gdesc(d.N, d.ncol, d.N, d.W);
     g.A = c->at<R>(c->L.eh); g.sAb = 0; g.sAm = d.N; g.sAk = 1;
@@ -489,10 +522,10 @@ afqmc_status step_impl(afqmc_ctx* c) {
 template <typename R>
 afqmc_status qr_impl(afqmc_ctx* c) {
   const Dims& d = c->d;
-  const size_t sm = (size_t)std::max(d.nbk[0], d.nbk[1]) * d.N * sizeof(double2);
   StageTimer timer(c, AFQMC_STAGE_QR);
-  k_qr<R><<<d.W, 256, sm, c->stream>>>(d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1], c->smul,
-                                       c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO), c->at<double>(c->L.w));
+  k_qr_chol<R><<<d.W, 256, qr_smem(d), c->stream>>>(d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1],
+                                                   c->smul, c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO),
+                                                   c->at<double>(c->L.w), c->at<int>(c->L.status));
   CHECK_LAUNCH(c);
   c->theta_fresh = false;
   c->vbias_fresh = false;
@@ -535,7 +568,7 @@ afqmc_status read_status(afqmc_ctx* c) {
   CU(cudaStreamSynchronize(c->stream));
   if (st == 0) return AFQMC_OK;
   CU(cudaMemsetAsync(c->base + c->L.status, 0, sizeof(int), c->stream));
-  if (st & 8) return fail(AFQMC_ETIMEOUT, "a tensor-core kernel gave up waiting on its pipeline (bounded wait)");
+  if (st & kStatusTimeout) return fail(AFQMC_ETIMEOUT, "a kernel gave up waiting for an asynchronous copy or tensor-core operation (bounded wait)");
   if (st & kStatusNoWalkers) return fail(AFQMC_ENOWALKERS, "all walker weights are zero");
   if (st & kStatusNonFinite) return fail(AFQMC_ENONFINITE, "a walker weight became non-finite (set to 0)");
   return fail(AFQMC_ESINGULAR, "a walker overlap matrix was singular (weight set to 0)");

@@ -187,6 +187,6 @@ __device__ __forceinline__ void normal_pair(unsigned long long seed, uint32_t pa
 }
 
 // Device status bits (sticky until read by the host).
-enum : int { kStatusSingular = 1, kStatusNonFinite = 2, kStatusNoWalkers = 4 };
+enum : int { kStatusSingular = 1, kStatusNonFinite = 2, kStatusNoWalkers = 4, kStatusTimeout = 8 };
 
 }  // namespace afq

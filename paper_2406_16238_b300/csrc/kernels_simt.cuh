@@ -138,9 +138,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
 }
 
 // ============================================================================
-// Overlap, Theta and (optionally) the weight update, one CTA per walker.
-//   A^s = Phi^sT psi^s (binary64), LU with partial pivoting (binary64), log det,
-//   (A^s)^-1 by triangular solves, Theta^sT = (psi^s (A^s)^-1)^T.
+// Arguments of the overlap / Theta / weight-update kernel (k_overlap_gj below).
 // mode 0: write log O; mode 1: weight update (Eqs. 13-16) from the stored
 // log O, c_mf and sum(x xbar - xbar^2/2); mode 2: Theta only.
 // ============================================================================
@@ -162,167 +160,6 @@ struct OverlapArgs {
 };
 
 __device__ __forceinline__ double wrap_angle(double t) { return atan2(sin(t), cos(t)); }
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_overlap(OverlapArgs<R> a) {
-  using R2 = cplx_t<R>;
-  extern __shared__ double2 sm_ov[];
-  __shared__ int perm_s[64];
-  __shared__ int piv_s, sing_s;
-  __shared__ double2 logdet_s;
-  const int w = blockIdx.x, tid = threadIdx.x;
-  if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
-  if (a.mode == 1 && a.w[w] == 0.0) return;          // frozen walker: psi unchanged, Theta still valid
-  const int nmax = max(a.nb[0], a.nblk > 1 ? a.nb[1] : 0);
-  double2* A = sm_ov;
-  double2* Ai = sm_ov + nmax * nmax;
-  double ld_re = 0.0, ld_im = 0.0;
-  bool singular = false;
-  for (int s = 0; s < a.nblk; ++s) {
-    const int c0 = a.c0[s], n = a.nb[s];
-    if (n == 0) continue;
-    // A = Phi^T psi
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx % n;
-      double2 acc = mk(0.0, 0.0);
-      for (int p = 0; p < a.N; ++p) {
-        const double ph = a.phi[(size_t)p * a.ncol + c0 + i];
-        const double2 ps = to_d2(a.psi[((size_t)w * a.N + p) * a.ncol + c0 + j]);
-        acc.x += ph * ps.x;
-        acc.y += ph * ps.y;
-      }
-      A[i * n + j] = acc;
-    }
-    if (tid == 0) { sing_s = 0; logdet_s = mk(0.0, 0.0); }
-    __syncthreads();
-    int swaps = 0;
-    for (int k = 0; k < n; ++k) {
-      if (tid < 32) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + tid; i < n; i += 32) {
-          const double2 v = A[i * n + k];
-          const double m = fabs(v.x) + fabs(v.y);
-          if (m > best) { best = m; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (tid == 0) {
-          piv_s = bi;
-          perm_s[k] = bi;
-          if (!(best > 0.0) || !isfinite(best)) sing_s = 1;
-        }
-      }
-      __syncthreads();
-      if (sing_s) break;
-      const int pv = piv_s;
-      if (pv != k) {
-        for (int j = tid; j < n; j += blockDim.x) {
-          const double2 t = A[k * n + j];
-          A[k * n + j] = A[pv * n + j];
-          A[pv * n + j] = t;
-        }
-        ++swaps;
-      }
-      __syncthreads();
-      const double2 inv = cdiv(mk(1.0, 0.0), A[k * n + k]);
-      for (int i = k + 1 + tid; i < n; i += blockDim.x) A[i * n + k] = cmul(A[i * n + k], inv);
-      __syncthreads();
-      const int rem = n - k - 1;
-      for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
-        const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-        A[i * n + j] = csub(A[i * n + j], cmul(A[i * n + k], A[k * n + j]));
-      }
-      __syncthreads();
-    }
-    if (sing_s) {
-      singular = true;
-      for (int idx = tid; idx < n * a.N; idx += blockDim.x) {
-        const int b = idx / a.N, p = idx % a.N;
-        a.thetaT[((size_t)w * a.ncol + c0 + b) * a.N + p] = from_d2<R>(mk(0.0, 0.0));
-      }
-      __syncthreads();
-      continue;
-    }
-    if (tid == 0) {
-      double re = 0.0, im = 0.0;
-      for (int k = 0; k < n; ++k) {
-        const double2 u = A[k * n + k];
-        re += log(hypot(u.x, u.y));
-        im += atan2(u.y, u.x);
-      }
-      im += (swaps & 1) ? 3.141592653589793 : 0.0;
-      logdet_s = mk(re, im);
-    }
-    // A^-1: column j solves L U x = P e_j (one thread per column, x kept in Ai[:, j])
-    for (int j = tid; j < n; j += blockDim.x) {
-      for (int i = 0; i < n; ++i) Ai[i * n + j] = mk(i == j ? 1.0 : 0.0, 0.0);
-      for (int k = 0; k < n; ++k) {
-        const int pk = perm_s[k];
-        if (pk != k) { double2 t = Ai[k * n + j]; Ai[k * n + j] = Ai[pk * n + j]; Ai[pk * n + j] = t; }
-      }
-      for (int i = 0; i < n; ++i) {
-        double2 y = Ai[i * n + j];
-        for (int k = 0; k < i; ++k) y = csub(y, cmul(A[i * n + k], Ai[k * n + j]));
-        Ai[i * n + j] = y;
-      }
-      for (int i = n - 1; i >= 0; --i) {
-        double2 y = Ai[i * n + j];
-        for (int k = i + 1; k < n; ++k) y = csub(y, cmul(A[i * n + k], Ai[k * n + j]));
-        Ai[i * n + j] = cdiv(y, A[i * n + i]);
-      }
-    }
-    __syncthreads();
-    // Theta^T[b][p] = sum_j psi[p][j] Ainv[j][b]
-    for (int idx = tid; idx < n * a.N; idx += blockDim.x) {
-      const int b = idx / a.N, p = idx % a.N;
-      const R2* prow = a.psi + ((size_t)w * a.N + p) * a.ncol + c0;
-      R accr = R(0), acci = R(0);
-      for (int j = 0; j < n; ++j) {
-        const R2 ps = prow[j];
-        const double2 iv = Ai[j * n + b];
-        const R ivr = (R)iv.x, ivi = (R)iv.y;
-        accr += ps.x * ivr - ps.y * ivi;
-        acci += ps.x * ivi + ps.y * ivr;
-      }
-      R2 out;
-      out.x = accr;
-      out.y = acci;
-      a.thetaT[((size_t)w * a.ncol + c0 + b) * a.N + p] = out;
-    }
-    ld_re += logdet_s.x;
-    ld_im += logdet_s.y;
-    __syncthreads();
-  }
-  if (tid != 0) return;
-  if (singular) {
-    if (a.mode != 2) a.w[w] = 0.0;
-    atomicOr(a.status, kStatusSingular);
-    return;
-  }
-  const double2 lo_new = mk(a.smul * ld_re, wrap_angle(a.smul * ld_im));
-  if (a.mode == 0) {
-    a.logO[w] = lo_new;
-  } else if (a.mode == 1) {
-    const double2 lo_old = a.logO[w];
-    const double2 c = a.cmf[w];
-    const double2 xx = a.xxbar[w];
-    const double ls_re = lo_new.x - lo_old.x + c.x;
-    const double theta = lo_new.y - lo_old.y + c.y;
-    const double li_re = ls_re + xx.x;
-    double wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * exp(a.dt * (a.e_trial - a.e_c));
-    if (!isfinite(wn)) {
-      wn = 0.0;
-      atomicOr(a.status, kStatusNonFinite);
-    }
-    a.w[w] = wn;
-    a.logO[w] = lo_new;
-  }
-}
 
 // ============================================================================
 // Local energy pieces on CUDA cores.  CTA (chunk, walker): for gamma in the
@@ -535,67 +372,6 @@ __global__ void __launch_bounds__(256) k_draw_normals(unsigned long long seed, u
 }
 
 // ============================================================================
-// QR stabilisation (classical Gram-Schmidt with one reorthogonalisation pass,
-// binary64), one CTA per walker.  diag(R) > 0 by construction.
-// ============================================================================
-template <typename R>
-__global__ void __launch_bounds__(256) k_qr(int N, int ncol, int nblk, int c00, int n0, int c01, int n1, double smul,
-                                            cplx_t<R>* psi, double2* logO, const double* wgt) {
-  extern __shared__ double2 sm_qr[];
-  __shared__ double red[32];
-  __shared__ double2 rcoef[64];
-  const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
-  if (wgt[w] == 0.0) return;
-  double logsum = 0.0;
-  for (int s = 0; s < nblk; ++s) {
-    const int c0 = s == 0 ? c00 : c01, n = s == 0 ? n0 : n1;
-    if (n == 0) continue;
-    double2* Q = sm_qr;   // column-major [n][N]
-    for (int idx = tid; idx < n * N; idx += blockDim.x) {
-      const int p = idx / n, j = idx % n;
-      Q[(size_t)j * N + p] = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
-    }
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-      double2* v = Q + (size_t)j * N;
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int i = wid; i < j; i += nwarp) {
-          const double2* q = Q + (size_t)i * N;
-          double re = 0.0, im = 0.0;
-          for (int p = lane; p < N; p += 32) {   // conj(q) . v
-            re += q[p].x * v[p].x + q[p].y * v[p].y;
-            im += q[p].x * v[p].y - q[p].y * v[p].x;
-          }
-          re = warp_sum(re);
-          im = warp_sum(im);
-          if (lane == 0) rcoef[i] = mk(re, im);
-        }
-        __syncthreads();
-        for (int p = tid; p < N; p += blockDim.x) {
-          double2 acc = v[p];
-          for (int i = 0; i < j; ++i) acc = csub(acc, cmul(Q[(size_t)i * N + p], rcoef[i]));
-          v[p] = acc;
-        }
-        __syncthreads();
-      }
-      double nrm = 0.0;
-      for (int p = tid; p < N; p += blockDim.x) nrm += v[p].x * v[p].x + v[p].y * v[p].y;
-      nrm = sqrt(block_sum(nrm, red));
-      const double inv = 1.0 / nrm;
-      for (int p = tid; p < N; p += blockDim.x) v[p] = cscale(v[p], inv);
-      logsum += log(nrm);
-      __syncthreads();
-    }
-    for (int idx = tid; idx < n * N; idx += blockDim.x) {
-      const int p = idx / n, j = idx % n;
-      psi[((size_t)w * N + p) * ncol + c0 + j] = from_d2<R>(Q[(size_t)j * N + p]);
-    }
-    __syncthreads();
-  }
-  if (tid == 0) logO[w].x -= smul * logsum;
-}
-
-// ============================================================================
 // Comb population control.  One CTA: sequential (index-order) binary64 prefix
 // of the weights, xi from Philox stream 1, tooth search.  Then a gather.
 // ============================================================================
@@ -673,6 +449,488 @@ __global__ void k_sum_batches(int nb, size_t len, const double* in, double* out)
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += in[(size_t)b * len + i];
     out[i] = s;
+  }
+}
+
+}  // namespace afq
+
+namespace afq {
+
+// ============================================================================
+// Fused propagation for the fp32 forms, one CTA per walker, everything staged
+// in shared memory:  t = E_h psi;  acc = t;  t <- VHS t / k, acc += t  (k = 1..p);
+// psi = E_h acc.  VHS and E_h are symmetric, so row q of each is also column q.
+// Thread tile: 4 rows x 3 columns of the N x ncol block.
+// ============================================================================
+struct PropArgs {
+  int N, ncol, order, ldv, ldc;
+  const float* eh;        // [N][N]
+  const void* vhs;        // planar [W][2][N*N] or interleaved complex [W][N*N]
+  int planar;
+  float2* psi;            // [W][N][ncol]
+  const double* w;
+  int W;
+  int* status;
+};
+
+__host__ __device__ inline size_t prop_smem_floats(int N, int ncol, int* ldv_out, int* ldc_out) {
+  const int ldv = (N + 3) / 4 * 4;
+  const int ldc = (ncol + 2) / 3 * 3;
+  if (ldv_out) *ldv_out = ldv;
+  if (ldc_out) *ldc_out = ldc;
+  return (size_t)3 * N * ldv + (size_t)6 * N * ldc;
+}
+
+template <bool REALV>
+__device__ __forceinline__ void prop_product(int N, int ldv, int ldc, int ncol, const float* Vr, const float* Vi,
+                                             const float* Tr, const float* Ti, float* Or, float* Oi, float* Ar,
+                                             float* Ai, float scale, int acc_mode) {
+  // Out = scale * V T (V real if REALV); acc_mode 0: none, 1: Acc = Out, 2: Acc += Out
+  const int ptiles = (N + 3) / 4, ctiles = ldc / 3;
+  for (int tile = threadIdx.x; tile < ptiles * ctiles; tile += blockDim.x) {
+    const int p0 = 4 * (tile / ctiles), c0 = 3 * (tile % ctiles);
+    float accr[4][3], acci[4][3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.f;
+    for (int q = 0; q < N; ++q) {
+      const float4 vr = *reinterpret_cast<const float4*>(Vr + (size_t)q * ldv + p0);
+      float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!REALV) vi = *reinterpret_cast<const float4*>(Vi + (size_t)q * ldv + p0);
+      const float* tr = Tr + (size_t)q * ldc + c0;
+      const float* ti = Ti + (size_t)q * ldc + c0;
+      const float br[3] = {tr[0], tr[1], tr[2]}, bi[3] = {ti[0], ti[1], ti[2]};
+      const float ar[4] = {vr.x, vr.y, vr.z, vr.w}, ai[4] = {vi.x, vi.y, vi.z, vi.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
+          acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
+          if (!REALV) {
+            accr[i][j] = fmaf(-ai[i], bi[j], accr[i][j]);
+            acci[i][j] = fmaf(ai[i], br[j], acci[i][j]);
+          }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = p0 + i;
+      if (p >= N) continue;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int c = c0 + j;
+        if (c >= ncol) continue;
+        const float orv = scale * accr[i][j], oiv = scale * acci[i][j];
+        const size_t o = (size_t)p * ldc + c;
+        if (Or) { Or[o] = orv; Oi[o] = oiv; }
+        if (acc_mode == 1) { Ar[o] = orv; Ai[o] = oiv; }
+        else if (acc_mode == 2) { Ar[o] += orv; Ai[o] += oiv; }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_addr_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Bulk global->shared copy completing on an mbarrier (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr_u32(dst)),
+               "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_addr_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr_u32(bar);
+  unsigned long long t0 = 0;
+  for (int it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (it == 0) t0 = t;
+    else if (t - t0 > 2000000000ull) return false;
+  }
+}
+
+// Persistent: each CTA loads E_h once and loops over walkers; with planar VHS and N % 4 == 0
+// the walker's VHS (re and im planes) arrives by two bulk copies, the next walker's copy
+// being issued as soon as the Taylor terms of the current one are done.
+__global__ void __launch_bounds__(256) k_propagate_smem(PropArgs a) {
+  extern __shared__ __align__(16) float sm_pr[];
+  const int N = a.N, ldv = a.ldv, ldc = a.ldc;
+  const size_t NN = (size_t)N * N;
+  float* Vr = sm_pr;
+  float* Vi = Vr + (size_t)N * ldv;
+  float* E = Vi + (size_t)N * ldv;
+  float* T0r = E + (size_t)N * ldv;
+  float* T0i = T0r + (size_t)N * ldc;
+  float* T1r = T0i + (size_t)N * ldc;
+  float* T1i = T1r + (size_t)N * ldc;
+  float* Ar = T1i + (size_t)N * ldc;
+  float* Ai = Ar + (size_t)N * ldc;
+  __shared__ __align__(8) uint64_t vbar;
+  __shared__ int go_s;
+  const bool bulk = a.planar && ldv == N && ((NN * 4) % 16 == 0);
+  for (size_t i = threadIdx.x; i < (size_t)N * ldv; i += blockDim.x) {
+    const int q = (int)(i / ldv), p = (int)(i % ldv);
+    E[i] = p < N ? a.eh[(size_t)q * N + p] : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr_u32(&vbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto next_live = [&](int from) {
+    for (int k = from; k < a.W; k += gridDim.x)
+      if (a.w[k] != 0.0) return k;
+    return a.W;
+  };
+  auto issue = [&](int wk) {   // thread 0 only
+    const float* v = reinterpret_cast<const float*>(a.vhs) + (size_t)wk * 2 * NN;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr_u32(&vbar)),
+                 "r"((uint32_t)(2 * NN * 4))
+                 : "memory");
+    bulk_g2s(Vr, v, (uint32_t)(NN * 4), &vbar);
+    bulk_g2s(Vi, v + NN, (uint32_t)(NN * 4), &vbar);
+  };
+  uint32_t phase = 0;
+  int wk = next_live(blockIdx.x);
+  if (bulk && threadIdx.x == 0 && wk < a.W) issue(wk);
+  while (wk < a.W) {
+    if (bulk) {
+      if (threadIdx.x == 0) {
+        go_s = mbar_wait_bounded(&vbar, phase) ? 1 : 0;
+        if (!go_s) atomicOr(a.status, kStatusTimeout);
+      }
+    } else {
+      for (size_t i = threadIdx.x; i < (size_t)N * ldv; i += blockDim.x) {
+        const int q = (int)(i / ldv), p = (int)(i % ldv);
+        float vr = 0.f, vi = 0.f;
+        if (p < N) {
+          const size_t o = (size_t)q * N + p;
+          if (a.planar) {
+            const float* v = reinterpret_cast<const float*>(a.vhs) + (size_t)wk * 2 * NN;
+            vr = v[o];
+            vi = v[NN + o];
+          } else {
+            const float2 v = reinterpret_cast<const float2*>(a.vhs)[(size_t)wk * NN + o];
+            vr = v.x;
+            vi = v.y;
+          }
+        }
+        Vr[i] = vr;
+        Vi[i] = vi;
+      }
+      if (threadIdx.x == 0) go_s = 1;
+    }
+    for (int i = threadIdx.x; i < N * ldc; i += blockDim.x) {
+      const int p = i / ldc, c = i % ldc;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < a.ncol) v = a.psi[((size_t)wk * N + p) * a.ncol + c];
+      T0r[i] = v.x;
+      T0i[i] = v.y;
+      T1r[i] = 0.f;
+      T1i[i] = 0.f;
+      Ar[i] = 0.f;
+      Ai[i] = 0.f;
+    }
+    __syncthreads();
+    if (!go_s) break;
+    phase ^= 1u;
+    prop_product<true>(N, ldv, ldc, a.ncol, E, nullptr, T0r, T0i, T1r, T1i, Ar, Ai, 1.f, 1);
+    __syncthreads();
+    float *tin_r = T1r, *tin_i = T1i, *tout_r = T0r, *tout_i = T0i;
+    for (int k = 1; k <= a.order; ++k) {
+      prop_product<false>(N, ldv, ldc, a.ncol, Vr, Vi, tin_r, tin_i, k < a.order ? tout_r : nullptr,
+                          k < a.order ? tout_i : nullptr, Ar, Ai, 1.f / (float)k, 2);
+      __syncthreads();
+      float* t = tin_r; tin_r = tout_r; tout_r = t;
+      t = tin_i; tin_i = tout_i; tout_i = t;
+    }
+    const int nxt = next_live(wk + gridDim.x);
+    if (bulk && threadIdx.x == 0 && nxt < a.W) issue(nxt);   // VHS buffer is free from here on
+    prop_product<true>(N, ldv, ldc, a.ncol, E, nullptr, Ar, Ai, tout_r, tout_i, nullptr, nullptr, 1.f, 0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * a.ncol; i += blockDim.x) {
+      const int p = i / a.ncol, c = i % a.ncol;
+      a.psi[((size_t)wk * N + p) * a.ncol + c] =
+          make_float2(tout_r[(size_t)p * ldc + c], tout_i[(size_t)p * ldc + c]);
+    }
+    __syncthreads();
+    wk = nxt;
+  }
+  if (threadIdx.x == 0 && bulk && !go_s) {   // a copy may still be in flight after a timeout: let it land
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do { asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t)); } while (t - t0 < 2000000ull);
+  }
+}
+
+// ============================================================================
+// Overlap, Theta and weight update with a Gauss-Jordan inverse (binary64) of
+// A^s = Phi^sT psi^s.  The product A is formed at the walkers' precision R with
+// an accumulator of the same type (binary64 in the FP64 form); pivoting,
+// determinant and inverse are binary64.  Same modes as k_overlap.
+// ============================================================================
+template <typename R>
+__global__ void __launch_bounds__(256) k_overlap_gj(OverlapArgs<R> a) {
+  using R2 = cplx_t<R>;
+  extern __shared__ double2 sm_gj[];
+  __shared__ int piv_s, sing_s;
+  __shared__ double2 inv_s, prod_s;   // pivot reciprocal; running product of pivots (scaled)
+  __shared__ int exp_s, swaps_s;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
+  if (a.mode == 1 && a.w[w] == 0.0) return;
+  const int nmax = max(a.nb[0], a.nblk > 1 ? a.nb[1] : 0);
+  double2* M = sm_gj;                      // [n][2n]: [A | I] -> [I | A^-1]
+  double2* col = sm_gj + 2 * nmax * nmax;  // saved pivot column
+  R2* Ainv = reinterpret_cast<R2*>(col + nmax);   // A^-1 at the walkers' precision, [n][n]
+  double ld_re = 0.0, ld_im = 0.0;
+  bool singular = false;
+  for (int s = 0; s < a.nblk; ++s) {
+    const int c0 = a.c0[s], n = a.nb[s], n2 = 2 * n;
+    if (n == 0) continue;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      R accr = R(0), acci = R(0);
+      for (int p = 0; p < a.N; ++p) {
+        const R ph = (R)a.phi[(size_t)p * a.ncol + c0 + i];
+        const R2 ps = a.psi[((size_t)w * a.N + p) * a.ncol + c0 + j];
+        accr += ph * ps.x;
+        acci += ph * ps.y;
+      }
+      M[i * n2 + j] = mk((double)accr, (double)acci);
+      M[i * n2 + n + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+    }
+    if (tid == 0) { sing_s = 0; prod_s = mk(1.0, 0.0); exp_s = 0; swaps_s = 0; }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + tid; i < n; i += 32) {
+          const double2 v = M[i * n2 + k];
+          const double m = fabs(v.x) + fabs(v.y);
+          if (m > best) { best = m; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) {
+          piv_s = bi;
+          if (!(best > 0.0) || !isfinite(best)) sing_s = 1;
+          if (!sing_s) {   // the pivot is row bi's entry in column k (before the swap)
+            const double2 pk = M[bi * n2 + k];
+            inv_s = cdiv(mk(1.0, 0.0), pk);
+            double2 pr = cmul(prod_s, pk);
+            int e;
+            const double m = frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
+            (void)m;
+            pr = mk(ldexp(pr.x, -e), ldexp(pr.y, -e));
+            prod_s = pr;
+            exp_s += e;
+            if (bi != k) swaps_s ^= 1;
+          }
+        }
+      }
+      __syncthreads();
+      if (sing_s) break;
+      const int pv = piv_s;
+      if (pv != k) {
+        for (int j = tid; j < n2; j += blockDim.x) {
+          const double2 t = M[k * n2 + j];
+          M[k * n2 + j] = M[pv * n2 + j];
+          M[pv * n2 + j] = t;
+        }
+      }
+      __syncthreads();
+      const double2 inv = inv_s;
+      for (int i = tid; i < n; i += blockDim.x) col[i] = M[i * n2 + k];
+      __syncthreads();
+      for (int j = k + 1 + tid; j < n2; j += blockDim.x) M[k * n2 + j] = cmul(M[k * n2 + j], inv);
+      __syncthreads();
+      const int width = n2 - k - 1;
+      for (int idx = tid; idx < (n - 1) * width; idx += blockDim.x) {
+        int i = idx / width;
+        const int j = k + 1 + idx % width;
+        if (i >= k) ++i;
+        M[i * n2 + j] = csub(M[i * n2 + j], cmul(col[i], M[k * n2 + j]));
+      }
+      __syncthreads();
+    }
+    if (sing_s) {
+      singular = true;
+      for (int idx = tid; idx < n * a.N; idx += blockDim.x) {
+        const int b = idx / a.N, p = idx % a.N;
+        a.thetaT[((size_t)w * a.ncol + c0 + b) * a.N + p] = from_d2<R>(mk(0.0, 0.0));
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of A^-1 to R per entry
+      const int j = idx / n, b = idx % n;
+      Ainv[idx] = from_d2<R>(M[j * n2 + n + b]);
+    }
+    __syncthreads();
+    // Theta^T[b][p] = sum_j psi[p][j] Ainv[j][b]
+    for (int idx = tid; idx < n * a.N; idx += blockDim.x) {
+      const int b = idx / a.N, p = idx % a.N;
+      const R2* prow = a.psi + ((size_t)w * a.N + p) * a.ncol + c0;
+      R accr = R(0), acci = R(0);
+      for (int j = 0; j < n; ++j) {
+        const R2 ps = prow[j];
+        const R2 iv = Ainv[j * n + b];
+        accr += ps.x * iv.x - ps.y * iv.y;
+        acci += ps.x * iv.y + ps.y * iv.x;
+      }
+      R2 out;
+      out.x = accr;
+      out.y = acci;
+      a.thetaT[((size_t)w * a.ncol + c0 + b) * a.N + p] = out;
+    }
+    if (tid == 0) {   // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps)
+      const double2 pr = prod_s;
+      ld_re += log(hypot(pr.x, pr.y)) + exp_s * 0.6931471805599453;
+      ld_im += atan2(pr.y, pr.x) + (swaps_s ? 3.141592653589793 : 0.0);
+    }
+    __syncthreads();
+  }
+  if (tid != 0) return;
+  if (singular) {
+    if (a.mode != 2) a.w[w] = 0.0;
+    atomicOr(a.status, kStatusSingular);
+    return;
+  }
+  const double2 lo_new = mk(a.smul * ld_re, wrap_angle(a.smul * ld_im));
+  if (a.mode == 0) {
+    a.logO[w] = lo_new;
+  } else if (a.mode == 1) {
+    const double2 lo_old = a.logO[w];
+    const double2 c = a.cmf[w];
+    const double2 xx = a.xxbar[w];
+    const double ls_re = lo_new.x - lo_old.x + c.x;
+    const double theta = lo_new.y - lo_old.y + c.y;
+    const double li_re = ls_re + xx.x;
+    double wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * exp(a.dt * (a.e_trial - a.e_c));
+    if (!isfinite(wn)) {
+      wn = 0.0;
+      atomicOr(a.status, kStatusNonFinite);
+    }
+    a.w[w] = wn;
+    a.logO[w] = lo_new;
+  }
+}
+
+// ============================================================================
+// Cholesky QR in binary64, one CTA per walker: G = psi^H psi (Hermitian),
+// G = R^H R with R upper triangular and diag R > 0, psi <- psi R^-1 (= Q with
+// diag R > 0, the unique thin QR), log O -= smul sum log R_ii.
+// ============================================================================
+template <typename R>
+__global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int c00, int n0, int c01, int n1,
+                                                 double smul, cplx_t<R>* psi, double2* logO, const double* wgt,
+                                                 int* status) {
+  extern __shared__ double2 sm_cq[];
+  __shared__ double logsum_s, rinv_s;
+  __shared__ int bad_s;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  if (wgt[w] == 0.0) return;
+  if (tid == 0) { logsum_s = 0.0; bad_s = 0; }
+  for (int s = 0; s < nblk; ++s) {
+    const int c0 = s == 0 ? c00 : c01, n = s == 0 ? n0 : n1;
+    if (n == 0) continue;
+    double2* G = sm_cq;               // [n][n], becomes R (upper)
+    double2* Ri = sm_cq + n * n;      // [n][n], R^-1 (upper)
+    double2* P = Ri + n * n;          // psi block, column-major [n][N], binary64
+    cplx_t<R>* Rl = reinterpret_cast<cplx_t<R>*>(P + (size_t)n * N);   // R^-1 at the walkers' precision
+    __syncthreads();
+    for (int idx = tid; idx < n * N; idx += blockDim.x) {
+      const int p = idx / n, j = idx % n;
+      P[(size_t)j * N + p] = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      if (j < i) continue;
+      double re = 0.0, im = 0.0;      // (psi^H psi)_ij = sum_p conj(psi_pi) psi_pj
+      const double2* u = P + (size_t)i * N;
+      const double2* v = P + (size_t)j * N;
+      for (int p = 0; p < N; ++p) {
+        re += u[p].x * v[p].x + u[p].y * v[p].y;
+        im += u[p].x * v[p].y - u[p].y * v[p].x;
+      }
+      G[i * n + j] = mk(re, im);
+    }
+    __syncthreads();
+    // right-looking Cholesky on the upper triangle: G_kk -> R_kk, row k -> R_kj
+    for (int k = 0; k < n; ++k) {
+      if (tid == 0) {
+        const double d = G[k * n + k].x;
+        if (!(d > 0.0) || !isfinite(d)) bad_s = 1;
+        const double r = sqrt(fmax(d, 1e-300));
+        G[k * n + k] = mk(r, 0.0);
+        rinv_s = 1.0 / r;
+        logsum_s += log(r);
+      }
+      __syncthreads();
+      const double rinv = rinv_s;
+      for (int j = k + 1 + tid; j < n; j += blockDim.x) G[k * n + j] = cscale(G[k * n + j], rinv);
+      __syncthreads();
+      const int rem = n - k - 1;
+      for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+        const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+        if (j < i) continue;
+        const double2 rki = G[k * n + i], rkj = G[k * n + j];   // G_ij -= conj(R_ki) R_kj
+        G[i * n + j] = csub(G[i * n + j], mk(rki.x * rkj.x + rki.y * rkj.y, rki.x * rkj.y - rki.y * rkj.x));
+      }
+      __syncthreads();
+    }
+    // R^-1 (upper): one thread per column j, back substitution
+    for (int j = tid; j < n; j += blockDim.x) {
+      for (int i = n - 1; i >= 0; --i) {
+        if (i > j) { Ri[i * n + j] = mk(0.0, 0.0); continue; }
+        double2 acc = mk(i == j ? 1.0 : 0.0, 0.0);
+        for (int k = i + 1; k <= j; ++k) acc = csub(acc, cmul(G[i * n + k], Ri[k * n + j]));
+        Ri[i * n + j] = cdiv(acc, G[i * n + i]);
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += blockDim.x) Rl[idx] = from_d2<R>(Ri[idx]);
+    __syncthreads();
+    // psi <- psi R^-1 at the walkers' precision (R^-1 itself is binary64); column j needs psi_pk for
+    // k <= j only, so each row is updated right to left in place
+    for (int p = tid; p < N; p += blockDim.x) {
+      cplx_t<R>* row = psi + ((size_t)w * N + p) * ncol + c0;
+      for (int j = n - 1; j >= 0; --j) {
+        R accr = R(0), acci = R(0);
+        for (int k = 0; k <= j; ++k) {
+          const cplx_t<R> v = row[k];
+          const cplx_t<R> ri = Rl[k * n + j];
+          accr += v.x * ri.x - v.y * ri.y;
+          acci += v.x * ri.y + v.y * ri.x;
+        }
+        cplx_t<R> o;
+        o.x = accr;
+        o.y = acci;
+        row[j] = o;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (bad_s) atomicOr(status, kStatusSingular);
+    logO[w].x -= smul * logsum_s;
   }
 }
 

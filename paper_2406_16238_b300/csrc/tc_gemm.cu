@@ -28,7 +28,6 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;                          // bf16 elements per 128-byte swizzled row
 constexpr int kStageA = kBM * kBK * 2;           // 16 KiB
 constexpr unsigned long long kWaitNs = 2000000000ull;
-constexpr int kStatusTimeout = 8;
 constexpr int kMaxSmem = 227 * 1024;
 
 struct Geom {
@@ -139,6 +138,25 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld2_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_ld1_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[0]) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld1(uint32_t taddr, float* v) {
   uint32_t r;
   asm volatile(
@@ -166,54 +184,66 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// Columns [col, col + ncols) of this thread's accumulator row into dst (shared memory).
-__device__ __forceinline__ void tmem_row_to_smem(uint32_t taddr, int ncols, float* dst) {
-  float v[16];
-  int c = 0;
-  for (; c + 16 <= ncols; c += 16) {
-    tmem_ld16(taddr + c, v);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) dst[c + i] = v[i];
-  }
-  for (; c + 4 <= ncols; c += 4) {
-    tmem_ld4(taddr + c, v);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) dst[c + i] = v[i];
-  }
-  for (; c < ncols; ++c) {
-    tmem_ld1(taddr + c, v);
-    dst[c] = v[0];
-  }
-}
-
 // ----------------------------------------------------------------------------- epilogues
+// Exchange epilogue state of one warpgroup: [ok flags 2 x int (16 B)] [buf 128 x (2n+1) floats]
+// [diag 128 float2] [red 4 float2].  Each group handles one walker per tile (wpt == groups).
 struct EpiSmem {
-  float* buf;      // [128][2n + 1]
-  float2* diag;    // [128]
-  float2* red;     // [4]
+  float* buf;
+  float2* diag;
+  float2* red;
   int* ok;
 };
 
-// Group region: [ok flag (16 B)] [buf] [diag] [red]; the store epilogue uses only the flag.
+__host__ __device__ __forceinline__ int exch_buf_bytes(int n) { return ((128 * (2 * n + 1) * 4) + 15) & ~15; }
+
 __device__ __forceinline__ EpiSmem epi_smem(uint8_t* base, const Params& p, int group) {
   EpiSmem e;
   uint8_t* g = base + (size_t)group * p.g.epi_bytes;
-  const int ld = 2 * p.n + 1;
   e.ok = reinterpret_cast<int*>(g);
   e.buf = reinterpret_cast<float*>(g + 16);
-  e.diag = reinterpret_cast<float2*>(g + 16 + ((128 * ld * 4 + 15) & ~15));
+  e.diag = reinterpret_cast<float2*>(g + 16 + exch_buf_bytes(p.n));
   e.red = e.diag + 128;
   return e;
 }
 
+// ncols accumulator columns of this thread's row into dst, loads batched 32 + 8 + 2 + 1 under one wait
+// per 32-column chunk.
+__device__ __forceinline__ void tmem_row_to_smem(uint32_t taddr, int ncols, float* dst) {
+  int c = 0;
+  for (; c + 32 <= ncols; c += 32) {
+    float v[16];
+    tmem_ld16(taddr + c, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dst[c + i] = v[i];
+    tmem_ld16(taddr + c + 16, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dst[c + 16 + i] = v[i];
+  }
+  const int rem = ncols - c;
+  if (rem <= 0) return;
+  uint32_t r[32];
+  int k = 0;
+  if (rem & 16) { uint32_t* q = r + k; float v[16]; tmem_ld16(taddr + c + k, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) q[i] = __float_as_uint(v[i]);
+    k += 16; }
+  if (rem & 8) { tmem_ld8_nowait(taddr + c + k, r + k); k += 8; }
+  if (rem & 4) { tmem_ld4_nowait(taddr + c + k, r + k); k += 4; }
+  if (rem & 2) { tmem_ld2_nowait(taddr + c + k, r + k); k += 2; }
+  if (rem & 1) { tmem_ld1_nowait(taddr + c + k, r + k); k += 1; }
+  tmem_wait();
+  for (int i = 0; i < rem; ++i) dst[c + i] = __uint_as_float(r[i]);
+}
+
+// One walker per group and tile: stage its 2n accumulator columns, form the row products,
+// then warp 0 of the group writes vbias for the tile's gammas and the exchange partial.
 __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
                               int wig, int r, int lane) {
   const int n = p.n, n2 = 2 * n, ld = n2 + 1, rows = p.gpt * n;
-  const int bar_id = 1 + group, nthr = 128;
+  const int bar_id = 1 + group;
   for (int v = group; v < p.wpt; v += p.g.epi_groups) {
-    const int w = nt * p.wpt + v;
     tmem_row_to_smem(tacc + (uint32_t)(v * n2), n2, e.buf + r * ld);
-    named_bar(bar_id, nthr);
+    named_bar(bar_id, 128);
     float er = 0.f, ei = 0.f;
     float2 dg = make_float2(0.f, 0.f);
     if (r < rows) {
@@ -221,11 +251,14 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
       if (mt * p.gpt + g < p.X) {
         const float* rowr = e.buf + r * ld;
         const float* blk = e.buf + (g * n) * ld;
+#pragma unroll 4
         for (int b = 0; b < n; ++b) {
           const float tr = rowr[b], ti = rowr[n + b];
           const float ur = blk[b * ld + a], ui = blk[b * ld + n + a];
-          er += tr * ur - ti * ui;
-          ei += tr * ui + ti * ur;
+          er = fmaf(tr, ur, er);
+          er = fmaf(-ti, ui, er);
+          ei = fmaf(tr, ui, ei);
+          ei = fmaf(ti, ur, ei);
         }
         dg = make_float2(rowr[a], rowr[n + a]);
       }
@@ -234,15 +267,17 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
     er = warp_sum_f(er);
     ei = warp_sum_f(ei);
     if (lane == 0) e.red[wig] = make_float2(er, ei);
-    named_bar(bar_id, nthr);
+    named_bar(bar_id, 128);
+    const int w = nt * p.wpt + v;
     if (w < p.W && wig == 0) {
-      for (int gl = lane; gl < p.gpt; gl += 32) {
+      for (int gl = lane; gl < p.gpt; gl += 32) {   // one gamma per lane, sequential sum over its n rows
         const int gam = mt * p.gpt + gl;
         if (gam >= p.X) continue;
         float sr = 0.f, si = 0.f;
         for (int a = 0; a < n; ++a) {
-          sr += e.diag[gl * n + a].x;
-          si += e.diag[gl * n + a].y;
+          const float2 d = e.diag[gl * n + a];
+          sr += d.x;
+          si += d.y;
         }
         float2* dst = p.vbias + (size_t)w * p.X + gam;
         float2 val = make_float2(p.smul * sr, p.smul * si);
@@ -253,19 +288,20 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
         *dst = val;
       }
       if (lane == 0) {
-        const double sr = (double)e.red[0].x + e.red[1].x + e.red[2].x + e.red[3].x;
-        const double si = (double)e.red[0].y + e.red[1].y + e.red[2].y + e.red[3].y;
-        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] = make_double2(p.smul * sr, p.smul * si);
+        const float sr = (e.red[0].x + e.red[1].x) + (e.red[2].x + e.red[3].x);
+        const float si = (e.red[0].y + e.red[1].y) + (e.red[2].y + e.red[3].y);
+        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] =
+            make_double2((double)(p.smul * sr), (double)(p.smul * si));
       }
     }
-    named_bar(bar_id, nthr);
+    if (v + p.g.epi_groups < p.wpt) named_bar(bar_id, 128);   // buffers reused by the next walker
   }
 }
 
 __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
   const int row = mt * p.g.m_step + r;
   const int c0 = nt * p.g.n_step;
-  const int ncols = p.g.bn / p.g.epi_groups;     // each group covers a contiguous half of the columns
+  const int ncols = p.g.bn / p.g.epi_groups;     // each group covers a contiguous share of the columns
   const int cbeg = group * ncols;
   float v[16];
   for (int c = cbeg; c < cbeg + ncols; c += 16) {
@@ -284,7 +320,7 @@ __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int g
 
 // ----------------------------------------------------------------------------- the kernel
 template <int EPI>
-__global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                     const __grid_constant__ CUtensorMap mapB, const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -378,14 +414,13 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ CUte
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
       const int acc = it & 1;
       const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-      if (wig == 0 && lane == 0) {
+      if (wig == 0 && lane == 0) {   // slot it & 1 is rewritten two tiles later, after this group's next barrier
         const bool ok = mbar_wait(&tfull[acc], aph, abort_flag);
         if (!ok) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
-        *es.ok = ok ? 1 : 0;
+        es.ok[it & 1] = ok ? 1 : 0;
       }
-      named_bar(1 + group, 128);
-      const int ok = *es.ok;
-      named_bar(1 + group, 128);
+      named_bar(1 + group, 128);   // also: every thread of the group is done with the previous tile's buffers
+      const int ok = es.ok[it & 1];
       if (!ok) break;
       tc_fence_after();
       const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
@@ -498,10 +533,7 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-int epi_bytes_exchange(int n) {
-  const int ld = 2 * n + 1;
-  return 16 + ((128 * ld * 4 + 15) & ~15) + 128 * 8 + 4 * 8;
-}
+int epi_bytes_exchange(int n) { return 16 + exch_buf_bytes(n) + 128 * 8 + 4 * 8; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -547,9 +579,9 @@ int tmem_cols_for(int bn) {
 // Pick the stage count for a given B box height and epilogue footprint.
 bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
   g->epi_groups = epi_groups;
-  g->epi_bytes = epi_bytes_per_group;
+  g->epi_bytes = (epi_bytes_per_group + 15) & ~15;
   const int stage_bytes = kStageA + g->bn * kBK * 2;
-  const int fixed = 1024 + epi_groups * epi_bytes_per_group + 256;
+  const int fixed = 1024 + epi_groups * g->epi_bytes + 256;
   int st = (kMaxSmem - fixed) / stage_bytes;
   if (st > 4) st = 4;
   if (st < 2) return false;
@@ -588,6 +620,17 @@ afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, c
 
 }  // namespace
 
+// Largest epilogue group count (<= 4, <= walkers per tile) whose buffers fit beside two stages.
+int exchange_groups(int n, int wpt) {
+  const int bn = (wpt * 2 * n + 15) / 16 * 16;
+  const int stage_bytes = kStageA + bn * kBK * 2;
+  for (int g = std::min(4, wpt); g > 1; --g) {
+    const int need = 1024 + g * ((epi_bytes_exchange(n) + 15) & ~15) + 256 + 2 * stage_bytes;
+    if (need <= kMaxSmem) return g;
+  }
+  return 1;
+}
+
 size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk) {
   if (prec != AFQMC_PREC_BF16 && prec != AFQMC_PREC_BF16X3) return 0;
   st->prec = prec;
@@ -604,6 +647,8 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     if (b.n == 0) { b.m_tiles = b.n_tiles = 0; continue; }
     b.gpt = kBM / b.n;
     b.wpt = 256 / (2 * b.n);
+    b.groups = exchange_groups(b.n, b.wpt);
+    b.wpt = b.wpt / b.groups * b.groups;   // every epilogue group takes the same number of walkers
     b.bn = (b.wpt * 2 * b.n + 15) / 16 * 16;
     b.m_tiles = (X + b.gpt - 1) / b.gpt;
     b.n_tiles = (W + b.wpt - 1) / b.wpt;
@@ -677,7 +722,7 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     g.n_step = bm.wpt * 2 * bm.n;
     g.bn = bm.bn;
     const int epb = epi_bytes_exchange(bm.n);
-    if (!finish_geom(&g, epb, 2) && !finish_geom(&g, epb, 1)) {
+    if (!finish_geom(&g, epb, bm.groups)) {
       snprintf(err, errlen, "tcgen05 exchange: n = %d does not fit shared memory", bm.n);
       return AFQMC_EINVAL;
     }
@@ -709,7 +754,7 @@ afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, f
   g.m_step = kBM;
   g.n_step = 256;
   g.bn = 256;
-  if (!finish_geom(&g, 16, 2)) {
+  if (!finish_geom(&g, 16, 4)) {
     snprintf(err, errlen, "tcgen05 VHS: shared memory plan failed");
     return AFQMC_EINVAL;
   }

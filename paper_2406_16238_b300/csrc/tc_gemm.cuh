@@ -18,6 +18,7 @@ struct BlockMaps {
   int c0;            // first stored column of the block
   int gpt, wpt;      // gammas per M tile (gpt * n <= 128), walkers per N tile (wpt * 2n <= 256)
   int bn;            // MMA N (multiple of 16, >= wpt * 2n)
+  int groups;        // epilogue warpgroups of the exchange kernel (wpt is a multiple of it)
   int m_tiles, n_tiles;
   size_t off_l, off_th;   // byte offsets of the bf16 Ltilde / Theta^T copies in the tc buffer
   CUtensorMap map_l, map_th;
