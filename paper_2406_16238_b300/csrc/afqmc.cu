@@ -61,7 +61,7 @@ struct Dims {
 // Offsets of every device buffer inside the workspace.
 struct Layout {
   size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp;
-  size_t phi, hrot, lbar, lrot, chol, eh;
+  size_t phi, phi_r, hrot, hrot_r, lbar, lrot, chol, eh;
   size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
   size_t exch_part, eloc, hist, status, step, src, cum, neww;
   size_t tc;          // tensor-core operand buffers (BF16 forms)
@@ -88,7 +88,9 @@ Layout plan(const Dims& d) {
   L.w = take(W * 8);
   L.w_tmp = take(W * 8);
   L.phi = take(N * nc * 8);
+  L.phi_r = take(N * nc * R);
   L.hrot = take(nc * N * 8);
+  L.hrot_r = take(nc * N * R);
   L.lbar = take(X * 8);
   L.lrot = take(X * nc * N * R);
   L.chol = take(X * N * N * R);
@@ -305,6 +307,7 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   a.smul = c->smul;
   a.psi = c->at<cplx_t<R>>(c->L.psi);
   a.phi = c->at<double>(c->L.phi);
+  a.phi_r = c->at<R>(c->L.phi_r);
   a.thetaT = c->at<cplx_t<R>>(c->L.thetaT);
   a.logO = c->at<double2>(c->L.logO);
   a.w = c->at<double>(c->L.w);
@@ -399,7 +402,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
   delete tx;
   StageTimer te(c, AFQMC_STAGE_ENERGY);
   k_energy_walker<R><<<c->d.W, 256, 0, c->stream>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
-                                                   c->at<cplx_t<R>>(c->L.thetaT), c->at<double>(c->L.hrot),
+                                                   c->at<cplx_t<R>>(c->L.thetaT), c->at<R>(c->L.hrot_r),
                                                    c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
                                                    c->at<double2>(c->L.eloc));
   CHECK_LAUNCH(c);
@@ -472,7 +475,9 @@ afqmc_status step_impl(afqmc_ctx* c) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_propagate_smem<<<std::min(d.W, sms), 256, prop_smem(d), c->stream>>>(pa);
+    const int tiles = ((d.N + 3) / 4) * ((d.ncol + 1) / 2);
+    const int threads = std::min(512, std::max(64, (tiles + 31) / 32 * 32));
+    k_propagate_smem<<<std::min(d.W, sms), threads, prop_smem(d), c->stream>>>(pa);
     delete tp;
     CHECK_LAUNCH(c);
     if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
@@ -677,6 +682,10 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * N * N, chol64, c->at<R>(c->L.chol));
   CHECK_LAUNCH(c);
   k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * nc * N, lrot64, c->at<R>(c->L.lrot));
+  CHECK_LAUNCH(c);
+  k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc, c->at<double>(c->L.phi), c->at<R>(c->L.phi_r));
+  CHECK_LAUNCH(c);
+  k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc, c->at<double>(c->L.hrot), c->at<R>(c->L.hrot_r));
   CHECK_LAUNCH(c);
   if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
     tc::plan(&c->tcs, d.prec, d.W, N, X, nc, d.c0, d.nbk, d.nblk);

@@ -148,6 +148,7 @@ struct OverlapArgs {
   double smul;                    // 2 for a restricted (one stored spin block) context, else 1
   const cplx_t<R>* psi;           // [W][N][ncol]
   const double* phi;              // [N][ncol]
+  const R* phi_r;                 // [N][ncol] at the walkers' precision
   cplx_t<R>* thetaT;              // [W][ncol][N]
   double2* logO;                  // [W]
   double* w;                      // [W]
@@ -248,14 +249,20 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
 // J = 1/2 sum_g vbias_g^2, K = 1/2 sum exchange partials.  eloc[w] = (E, E0+E1, J-K).
 template <typename R>
 __global__ void __launch_bounds__(256) k_energy_walker(int N, int X, int ncol, double smul, double ecore,
-                                                         int nchunk, const cplx_t<R>* thetaT, const double* hrot,
+                                                         int nchunk, const cplx_t<R>* thetaT, const R* hrot_r,
                                                          const cplx_t<R>* vbias, const double2* exch_part,
                                                          double2* eloc) {
   __shared__ double red[32];
   const int w = blockIdx.x, tid = threadIdx.x;
   const int cn = ncol * N;
-  double2 e1 = mk(0.0, 0.0);
-  for (int i = tid; i < cn; i += blockDim.x) e1 = cadd(e1, cscale(to_d2(thetaT[(size_t)w * cn + i]), hrot[i]));
+  R e1r = R(0), e1i = R(0);   // per-thread partial at the walkers' precision, summed across threads in binary64
+  for (int i = tid; i < cn; i += blockDim.x) {
+    const cplx_t<R> t = thetaT[(size_t)w * cn + i];
+    const R h = hrot_r[i];
+    e1r += t.x * h;
+    e1i += t.y * h;
+  }
+  double2 e1 = mk((double)e1r, (double)e1i);
   double2 j = mk(0.0, 0.0);
   for (int g = tid; g < X; g += blockDim.x) {
     const double2 v = to_d2(vbias[(size_t)w * X + g]);
@@ -460,7 +467,7 @@ namespace afq {
 // Fused propagation for the fp32 forms, one CTA per walker, everything staged
 // in shared memory:  t = E_h psi;  acc = t;  t <- VHS t / k, acc += t  (k = 1..p);
 // psi = E_h acc.  VHS and E_h are symmetric, so row q of each is also column q.
-// Thread tile: 4 rows x 3 columns of the N x ncol block.
+// Thread tile: 4 rows x 2 columns of the N x ncol block.
 // ============================================================================
 struct PropArgs {
   int N, ncol, order, ldv, ldc;
@@ -475,7 +482,7 @@ struct PropArgs {
 
 __host__ __device__ inline size_t prop_smem_floats(int N, int ncol, int* ldv_out, int* ldc_out) {
   const int ldv = (N + 3) / 4 * 4;
-  const int ldc = (ncol + 2) / 3 * 3;
+  const int ldc = (ncol + 1) / 2 * 2;
   if (ldv_out) *ldv_out = ldv;
   if (ldc_out) *ldc_out = ldc;
   return (size_t)3 * N * ldv + (size_t)6 * N * ldc;
@@ -485,27 +492,28 @@ template <bool REALV>
 __device__ __forceinline__ void prop_product(int N, int ldv, int ldc, int ncol, const float* Vr, const float* Vi,
                                              const float* Tr, const float* Ti, float* Or, float* Oi, float* Ar,
                                              float* Ai, float scale, int acc_mode) {
-  // Out = scale * V T (V real if REALV); acc_mode 0: none, 1: Acc = Out, 2: Acc += Out
-  const int ptiles = (N + 3) / 4, ctiles = ldc / 3;
+  // Out = scale * V T (V real if REALV); acc_mode 0: none, 1: Acc = Out, 2: Acc += Out.
+  // Thread tile: 4 rows (one float4 of V per part) x 2 columns (one float2 of T per part).
+  const int ptiles = (N + 3) / 4, ctiles = ldc / 2;
   for (int tile = threadIdx.x; tile < ptiles * ctiles; tile += blockDim.x) {
-    const int p0 = 4 * (tile / ctiles), c0 = 3 * (tile % ctiles);
-    float accr[4][3], acci[4][3];
+    const int p0 = 4 * (tile / ctiles), c0 = 2 * (tile % ctiles);
+    float accr[4][2], acci[4][2];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.f;
+      for (int j = 0; j < 2; ++j) accr[i][j] = acci[i][j] = 0.f;
     for (int q = 0; q < N; ++q) {
       const float4 vr = *reinterpret_cast<const float4*>(Vr + (size_t)q * ldv + p0);
       float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!REALV) vi = *reinterpret_cast<const float4*>(Vi + (size_t)q * ldv + p0);
-      const float* tr = Tr + (size_t)q * ldc + c0;
-      const float* ti = Ti + (size_t)q * ldc + c0;
-      const float br[3] = {tr[0], tr[1], tr[2]}, bi[3] = {ti[0], ti[1], ti[2]};
+      const float2 tr = *reinterpret_cast<const float2*>(Tr + (size_t)q * ldc + c0);
+      const float2 ti = *reinterpret_cast<const float2*>(Ti + (size_t)q * ldc + c0);
+      const float br[2] = {tr.x, tr.y}, bi[2] = {ti.x, ti.y};
       const float ar[4] = {vr.x, vr.y, vr.z, vr.w}, ai[4] = {vi.x, vi.y, vi.z, vi.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < 2; ++j) {
           accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
           acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
           if (!REALV) {
@@ -519,7 +527,7 @@ __device__ __forceinline__ void prop_product(int N, int ldv, int ldc, int ncol, 
       const int p = p0 + i;
       if (p >= N) continue;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 0; j < 2; ++j) {
         const int c = c0 + j;
         if (c >= ncol) continue;
         const float orv = scale * accr[i][j], oiv = scale * acci[i][j];
@@ -562,7 +570,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Persistent: each CTA loads E_h once and loops over walkers; with planar VHS and N % 4 == 0
 // the walker's VHS (re and im planes) arrives by two bulk copies, the next walker's copy
 // being issued as soon as the Taylor terms of the current one are done.
-__global__ void __launch_bounds__(256) k_propagate_smem(PropArgs a) {
+__global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
   extern __shared__ __align__(16) float sm_pr[];
   const int N = a.N, ldv = a.ldv, ldc = a.ldc;
   const size_t NN = (size_t)N * N;
@@ -702,7 +710,7 @@ __global__ void __launch_bounds__(256) k_overlap_gj(OverlapArgs<R> a) {
       const int i = idx / n, j = idx % n;
       R accr = R(0), acci = R(0);
       for (int p = 0; p < a.N; ++p) {
-        const R ph = (R)a.phi[(size_t)p * a.ncol + c0 + i];
+        const R ph = a.phi_r[(size_t)p * a.ncol + c0 + i];
         const R2 ps = a.psi[((size_t)w * a.N + p) * a.ncol + c0 + j];
         accr += ph * ps.x;
         acci += ph * ps.y;
