@@ -168,6 +168,11 @@ afqmc_status afqmc_draw_normals(uint64_t seed, uint64_t step, uint32_t stream_id
                                 int32_t naux, double* out, void* stream);
 
 afqmc_status afqmc_get_info(afqmc_ctx* ctx, afqmc_info* info);
+
+/* afqmc_run replays each step pattern (energy + propagation, propagation alone, QR, comb) as a
+ * CUDA graph captured on first use (enable = 1, the default); enable = 0 launches every kernel
+ * directly.  Results are identical either way.  Tracing (afqmc_profile) uses direct launches. */
+afqmc_status afqmc_set_graphs(afqmc_ctx* ctx, int32_t enable);
 afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial);
 
 /* Wait for the context's stream, polling, for at most timeout_s seconds. */

@@ -66,6 +66,7 @@ SIGNATURES = {
     "afqmc_draw_normals": (_i32, [_u64, _u64, ctypes.c_uint32, _i32, _i32, _vp, _vp]),
     "afqmc_get_info": (_i32, [_vp, ctypes.POINTER(Info)]),
     "afqmc_set_etrial": (_i32, [_vp, ctypes.c_double]),
+    "afqmc_set_graphs": (_i32, [_vp, _i32]),
     "afqmc_synchronize": (_i32, [_vp, ctypes.c_double]),
     "afqmc_destroy": (None, [_vp]),
     "afqmc_launch_count": (_u64, [_vp]),
@@ -200,6 +201,9 @@ class Afqmc:
         inf = Info()
         _check(self._lib.afqmc_get_info(self._ctx, ctypes.byref(inf)))
         return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def set_graphs(self, enable=True):
+        _check(self._lib.afqmc_set_graphs(self._ctx, 1 if enable else 0))
 
     def set_etrial(self, e):
         _check(self._lib.afqmc_set_etrial(self._ctx, float(e)))

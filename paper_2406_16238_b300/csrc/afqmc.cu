@@ -63,7 +63,7 @@ struct Layout {
   size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp;
   size_t phi, phi_r, hrot, hrot_r, lbar, lrot, chol, eh;
   size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
-  size_t exch_part, eloc, hist, status, step, src, cum, neww;
+  size_t exch_part, eloc, hist, status, step, src, cum, neww, slot;
   size_t tc;          // tensor-core operand buffers (BF16 forms)
   size_t setup;       // set-up scratch (aliases vhs; binary64 L, L L products, Ltilde)
   size_t setup_bytes, vhs_bytes, tc_bytes;
@@ -109,6 +109,7 @@ Layout plan(const Dims& d) {
   L.src = take(W * 4);
   L.cum = take(W * 8);
   L.neww = take(256);
+  L.slot = take(256);
   {
     tc::TcState tmp;
     L.tc_bytes = tc::plan(&tmp, d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk);
@@ -227,6 +228,18 @@ struct afqmc_ctx {
   bool theta_fresh, vbias_fresh;
   int hist_used;
   tc::TcState tcs;
+  // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
+  bool graphs_on = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g_step[4] = {};       // bit 0: energy measured, bit 1: Theta refreshed first
+  unsigned long long g_step_k[4] = {};
+  cudaGraphExec_t g_qr = nullptr, g_comb[2] = {};
+  unsigned long long g_qr_k = 0, g_comb_k[2] = {};
+  void drop_graphs() {
+    for (auto& g : g_step) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto& g : g_comb) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (g_qr) { cudaGraphExecDestroy(g_qr); g_qr = nullptr; }
+  }
   // tracing
   bool prof = false;
   std::vector<cudaEvent_t> free_events;
@@ -235,6 +248,8 @@ struct afqmc_ctx {
   double stage_ms[AFQMC_NSTAGES] = {};
   long long stage_n[AFQMC_NSTAGES] = {};
   ~afqmc_ctx() {
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : free_events) cudaEventDestroy(e);
   }
@@ -282,14 +297,35 @@ struct StageTimer {
 };
 
 // --------------------------------------------------------------------------------------
+template <typename R, bool CA, bool CB, int TM, int TN>
+afqmc_status gemm_tiled(afqmc_ctx* c, const GemmDesc& g) {
+  dim3 grid((g.Nc + 16 * TN - 1) / (16 * TN), (g.M + 16 * TM - 1) / (16 * TM), g.batch);
+  if (grid.y > 65535 || grid.z > 65535) return fail(AFQMC_EINVAL, "GEMM grid too large");
+  k_gemm<R, CA, CB, TM, TN><<<grid, 256, 0, c->stream>>>(g);
+  CHECK_LAUNCH(c);
+  return AFQMC_OK;
+}
+
+// Block tile picked from the output shape: 64-wide tiles for large dimensions, 32 or 16 for small
+// ones, so that tiny or skinny batched products do not run mostly on padding.
 template <typename R, bool CA, bool CB>
 afqmc_status gemm(afqmc_ctx* c, const GemmDesc& g) {
   if (g.M <= 0 || g.Nc <= 0 || g.batch <= 0) return AFQMC_OK;
-  dim3 grid((g.Nc + 63) / 64, (g.M + 63) / 64, g.batch);
-  if (grid.y > 65535 || grid.z > 65535) return fail(AFQMC_EINVAL, "GEMM grid too large");
-  k_gemm<R, CA, CB><<<grid, 256, 0, c->stream>>>(g);
-  CHECK_LAUNCH(c);
-  return AFQMC_OK;
+  int tm = g.M >= 48 ? 4 : (g.M > 16 ? 2 : 1);
+  int tn = g.Nc >= 48 ? 4 : (g.Nc > 16 ? 2 : 1);
+  auto ctas = [&](int a, int b) {
+    return (long long)((g.M + 16 * a - 1) / (16 * a)) * ((g.Nc + 16 * b - 1) / (16 * b)) * g.batch;
+  };
+  while (ctas(tm, tn) < 148 && (tm > 1 || tn > 1)) {   // fill the SMs before using larger tiles
+    if (tm >= tn) tm /= 2; else tn /= 2;
+  }
+  if (tm == 4 && tn == 1) tn = 2;
+  if (tm == 4 && tn == 4) return gemm_tiled<R, CA, CB, 4, 4>(c, g);
+  if (tm == 4) return gemm_tiled<R, CA, CB, 4, 2>(c, g);
+  if (tm == 2 && tn == 4) return gemm_tiled<R, CA, CB, 2, 4>(c, g);
+  if (tm == 2) return gemm_tiled<R, CA, CB, 2, 2>(c, g);
+  if (tn >= 2) return gemm_tiled<R, CA, CB, 1, 4>(c, g);
+  return gemm_tiled<R, CA, CB, 1, 1>(c, g);
 }
 
 GemmDesc gdesc(int M, int Nc, int K, int batch) {
@@ -325,9 +361,17 @@ size_t overlap_smem(const Dims& d) {
   return ((size_t)2 * nmax * nmax + nmax) * sizeof(double2) + (size_t)nmax * nmax * 2 * d.rsz();
 }
 
+size_t qr_smem_base(const Dims& d) {
+  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
+  return (size_t)2 * nmax * nmax * sizeof(double2) + ((size_t)nmax * nmax + 1) * 2 * d.rsz() + 16;
+}
+bool qr_stage_psi(const Dims& d) {
+  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
+  return qr_smem_base(d) + (size_t)nmax * d.N * sizeof(double2) <= 227 * 1024;
+}
 size_t qr_smem(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return ((size_t)2 * nmax * nmax + (size_t)nmax * d.N) * sizeof(double2) + (size_t)nmax * nmax * 2 * d.rsz();
+  return qr_smem_base(d) + (qr_stage_psi(d) ? (size_t)nmax * d.N * sizeof(double2) : 0);
 }
 
 size_t prop_smem(const Dims& d) { return prop_smem_floats(d.N, d.ncol, nullptr, nullptr) * sizeof(float); }
@@ -384,7 +428,7 @@ afqmc_status set_smem_limits(const Dims& d) {
 
 // Local energy at the current walkers into eloc and the weighted sums into sums_dev.
 template <typename R>
-afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
+afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
   afqmc_status st;
   if (!c->theta_fresh) {
     if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
@@ -406,7 +450,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev) {
                                                    c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
                                                    c->at<double2>(c->L.eloc));
   CHECK_LAUNCH(c);
-  k_energy_sums<<<1, 256, 0, c->stream>>>(c->d.W, c->at<double>(c->L.w), c->at<double2>(c->L.eloc), sums_dev);
+  k_energy_sums<<<1, 256, 0, c->stream>>>(c->d.W, c->at<double>(c->L.w), c->at<double2>(c->L.eloc), sums_dev, slot);
   CHECK_LAUNCH(c);
   c->vbias_fresh = true;
   return AFQMC_OK;
@@ -530,7 +574,8 @@ afqmc_status qr_impl(afqmc_ctx* c) {
   StageTimer timer(c, AFQMC_STAGE_QR);
   k_qr_chol<R><<<d.W, 256, qr_smem(d), c->stream>>>(d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1],
                                                    c->smul, c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO),
-                                                   c->at<double>(c->L.w), c->at<int>(c->L.status));
+                                                   c->at<double>(c->L.w), c->at<int>(c->L.status),
+                                                   qr_stage_psi(d) ? 1 : 0);
   CHECK_LAUNCH(c);
   c->theta_fresh = false;
   c->vbias_fresh = false;
@@ -715,6 +760,75 @@ afqmc_status check_ctx(afqmc_ctx* c) {
   return AFQMC_OK;
 }
 
+// Captures `body` (which enqueues on c->stream) into an executable graph.  Host-side state is
+// restored afterwards; the caller applies the state change of one replay itself.
+template <typename F>
+afqmc_status capture(afqmc_ctx* c, F body, cudaGraphExec_t* out, unsigned long long* nkernels) {
+  if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const bool tf = c->theta_fresh, vf = c->vbias_fresh;
+  const unsigned long long hs = c->host_step, l0 = c->launches;
+  cudaStream_t user = c->stream;
+  CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap_stream;
+  afqmc_status st = body();
+  c->stream = user;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  *nkernels = c->launches - l0;
+  c->theta_fresh = tf; c->vbias_fresh = vf; c->host_step = hs; c->launches = l0;
+  if (st != AFQMC_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return fail(AFQMC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
+  return AFQMC_OK;
+}
+
+// One driver-loop step (optional energy into the history slot, then propagation) via a graph.
+afqmc_status graph_step(afqmc_ctx* c, bool energy) {
+  const int v = (energy ? 1 : 0) | (c->theta_fresh ? 0 : 2);
+  if (!c->g_step[v]) {
+    afqmc_status st = capture(c, [&]() -> afqmc_status {
+      afqmc_status s2;
+      if (energy && (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot))) != AFQMC_OK)
+        return s2;
+      return DISPATCH(c, step_impl);
+    }, &c->g_step[v], &c->g_step_k[v]);
+    if (st != AFQMC_OK) return st;
+  }
+  CU(cudaGraphLaunch(c->g_step[v], c->stream));
+  c->launches += c->g_step_k[v];
+  c->theta_fresh = true;
+  c->vbias_fresh = false;
+  c->host_step++;
+  return AFQMC_OK;
+}
+
+afqmc_status graph_qr(afqmc_ctx* c) {
+  if (!c->g_qr) {
+    afqmc_status st = capture(c, [&]() { return DISPATCH(c, qr_impl); }, &c->g_qr, &c->g_qr_k);
+    if (st != AFQMC_OK) return st;
+  }
+  CU(cudaGraphLaunch(c->g_qr, c->stream));
+  c->launches += c->g_qr_k;
+  c->theta_fresh = false;
+  c->vbias_fresh = false;
+  return AFQMC_OK;
+}
+
+afqmc_status graph_comb(afqmc_ctx* c) {
+  const int v = c->theta_fresh ? 0 : 1;
+  if (!c->g_comb[v]) {
+    afqmc_status st = capture(c, [&]() { return DISPATCH(c, comb_impl); }, &c->g_comb[v], &c->g_comb_k[v]);
+    if (st != AFQMC_OK) return st;
+  }
+  CU(cudaGraphLaunch(c->g_comb[v], c->stream));
+  c->launches += c->g_comb_k[v];
+  c->theta_fresh = true;
+  c->vbias_fresh = false;
+  return AFQMC_OK;
+}
+
 }  // namespace
 
 // ======================================================================================
@@ -862,26 +976,31 @@ afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int
   if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
   int used = 0, total = 0;
   double* hist = ctx->at<double>(ctx->L.hist);
+  const bool graphs = ctx->graphs_on && !ctx->prof;
   auto flush = [&]() -> afqmc_status {
     if (used > 0 && energies)
       CU(cudaMemcpyAsync(energies + 4 * (size_t)(total - used), hist, (size_t)used * 4 * sizeof(double),
                          cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     used = 0;
+    if (graphs) CU(cudaMemsetAsync(ctx->base + ctx->L.slot, 0, sizeof(int), ctx->stream));
     return AFQMC_OK;
   };
+  if (graphs) CU(cudaMemsetAsync(ctx->base + ctx->L.slot, 0, sizeof(int), ctx->stream));
   for (int s = 0; s < nsteps; ++s) {
-    if (energy_every > 0 && ctx->host_step % (unsigned long long)energy_every == 0) {
-      if (used == kHistory - 1 && (st = flush()) != AFQMC_OK) return st;
-      if ((st = DISPATCH(ctx, energy_impl, hist + 4 * used)) != AFQMC_OK) return st;
-      ++used;
-      ++total;
+    const bool energy = energy_every > 0 && ctx->host_step % (unsigned long long)energy_every == 0;
+    if (energy && used == kHistory - 1 && (st = flush()) != AFQMC_OK) return st;
+    if (graphs) {
+      if ((st = graph_step(ctx, energy)) != AFQMC_OK) return st;
+    } else {
+      if (energy && (st = DISPATCH(ctx, energy_impl, hist + 4 * used)) != AFQMC_OK) return st;
+      if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
     }
-    if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
+    if (energy) { ++used; ++total; }
     if (reortho_every > 0 && ctx->host_step % (unsigned long long)reortho_every == 0)
-      if ((st = DISPATCH(ctx, qr_impl)) != AFQMC_OK) return st;
+      if ((st = graphs ? graph_qr(ctx) : DISPATCH(ctx, qr_impl)) != AFQMC_OK) return st;
     if (comb_every > 0 && ctx->host_step % (unsigned long long)comb_every == 0)
-      if ((st = DISPATCH(ctx, comb_impl)) != AFQMC_OK) return st;
+      if ((st = graphs ? graph_comb(ctx) : DISPATCH(ctx, comb_impl)) != AFQMC_OK) return st;
   }
   if ((st = flush()) != AFQMC_OK) return st;
   if (nmeas) *nmeas = total;
@@ -1006,7 +1125,18 @@ afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial) {
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;
   if (!std::isfinite(e_trial)) return fail(AFQMC_EINVAL, "e_trial must be finite");
+  if (e_trial != ctx->e_trial) {
+    CU(cudaStreamSynchronize(ctx->stream));   // captured graphs hold the old value: rebuild them
+    ctx->drop_graphs();
+  }
   ctx->e_trial = e_trial;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_graphs(afqmc_ctx* ctx, int32_t enable) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  ctx->graphs_on = enable != 0;
   return AFQMC_OK;
 }
 

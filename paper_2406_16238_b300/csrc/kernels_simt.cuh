@@ -26,9 +26,10 @@ struct GemmDesc {
   long long a_im_off;    // element offset of the imaginary plane (a_planar)
 };
 
-template <typename R, bool CA, bool CB>
+// Block tile BM x BN = 16 TM x 16 TN, each of the 256 threads owns a TM x TN register tile.
+template <typename R, bool CA, bool CB, int TM, int TN>
 __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
   constexpr bool CC = CA || CB;
   using R2 = cplx_t<R>;
   __shared__ R As_re[BK][BM], As_im[CA ? BK : 1][CA ? BM : 1];
@@ -39,11 +40,11 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const char* Ab = (const char*)g.A + (size_t)b * g.sAb * ((CA && !g.a_planar) ? sizeof(R2) : sizeof(R));
   const char* Bb = (const char*)g.B + (size_t)b * g.sBb * (CB ? sizeof(R2) : sizeof(R));
-  R acc_re[4][4], acc_im[4][4];
+  R acc_re[TM][TN], acc_im[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc_re[i][j] = acc_im[i][j] = R(0);
+    for (int j = 0; j < TN; ++j) acc_re[i][j] = acc_im[i][j] = R(0);
   const bool a_kfast = g.sAk == 1;
   const bool b_nfast = g.sBn == 1 || g.sBk != 1;
   for (int k0 = 0; k0 < g.K; k0 += BK) {
@@ -82,15 +83,15 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      R ar[4], ai[4], br[4], bi[4];
+      R ar[TM], ai[TM], br[TN], bi[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) { ar[i] = As_re[kk][ty + 16 * i]; ai[i] = CA ? As_im[kk][ty + 16 * i] : R(0); }
+      for (int i = 0; i < TM; ++i) { ar[i] = As_re[kk][ty + 16 * i]; ai[i] = CA ? As_im[kk][ty + 16 * i] : R(0); }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { br[j] = Bs_re[kk][tx + 16 * j]; bi[j] = CB ? Bs_im[kk][tx + 16 * j] : R(0); }
+      for (int j = 0; j < TN; ++j) { br[j] = Bs_re[kk][tx + 16 * j]; bi[j] = CB ? Bs_im[kk][tx + 16 * j] : R(0); }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           if (!CA && !CB) {
             acc_re[i][j] += ar[i] * br[j];
           } else if (CA && !CB) {
@@ -109,11 +110,11 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
   }
   const R al_r = (R)g.alpha_re, al_i = (R)g.alpha_im;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int m = m0 + ty + 16 * i;
     if (m >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= g.Nc) continue;
       if (CC) {
@@ -282,8 +283,10 @@ __global__ void __launch_bounds__(256) k_energy_walker(int N, int X, int ncol, d
   }
 }
 
-// Weighted estimator sums (ENumer, EDenom, E1Body, E2Body), fixed reduction order.
-__global__ void __launch_bounds__(256) k_energy_sums(int W, const double* w, const double2* eloc, double* out) {
+// Weighted estimator sums (ENumer, EDenom, E1Body, E2Body), fixed reduction order.  With a slot
+// counter, the sums go to out + 4 * (*slot) and the counter advances (graph-replayable history).
+__global__ void __launch_bounds__(256) k_energy_sums(int W, const double* w, const double2* eloc, double* out,
+                                                     int* slot) {
   __shared__ double red[32];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -298,7 +301,11 @@ __global__ void __launch_bounds__(256) k_energy_sums(int W, const double* w, con
   s1 = block_sum(s1, red);
   s2 = block_sum(s2, red);
   s3 = block_sum(s3, red);
-  if (threadIdx.x == 0) { out[0] = s0; out[1] = s1; out[2] = s2; out[3] = s3; }
+  if (threadIdx.x == 0) {
+    double* o = slot ? out + 4 * (size_t)(*slot) : out;
+    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
+    if (slot) *slot += 1;
+  }
 }
 
 // ============================================================================
@@ -848,7 +855,7 @@ __global__ void __launch_bounds__(256) k_overlap_gj(OverlapArgs<R> a) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int c00, int n0, int c01, int n1,
                                                  double smul, cplx_t<R>* psi, double2* logO, const double* wgt,
-                                                 int* status) {
+                                                 int* status, int stage_psi) {
   extern __shared__ double2 sm_cq[];
   __shared__ double logsum_s, rinv_s;
   __shared__ int bad_s;
@@ -860,23 +867,34 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
     if (n == 0) continue;
     double2* G = sm_cq;               // [n][n], becomes R (upper)
     double2* Ri = sm_cq + n * n;      // [n][n], R^-1 (upper)
-    double2* P = Ri + n * n;          // psi block, column-major [n][N], binary64
-    cplx_t<R>* Rl = reinterpret_cast<cplx_t<R>*>(P + (size_t)n * N);   // R^-1 at the walkers' precision
+    cplx_t<R>* Rl = reinterpret_cast<cplx_t<R>*>(Ri + n * n);   // R^-1 at the walkers' precision
+    double2* P = reinterpret_cast<double2*>(Rl + n * n + (n & 1));   // staged psi block [n][N] (stage_psi)
     __syncthreads();
-    for (int idx = tid; idx < n * N; idx += blockDim.x) {
-      const int p = idx / n, j = idx % n;
-      P[(size_t)j * N + p] = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
+    if (stage_psi) {
+      for (int idx = tid; idx < n * N; idx += blockDim.x) {
+        const int p = idx / n, j = idx % n;
+        P[(size_t)j * N + p] = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
       const int i = idx / n, j = idx % n;
       if (j < i) continue;
       double re = 0.0, im = 0.0;      // (psi^H psi)_ij = sum_p conj(psi_pi) psi_pj
-      const double2* u = P + (size_t)i * N;
-      const double2* v = P + (size_t)j * N;
-      for (int p = 0; p < N; ++p) {
-        re += u[p].x * v[p].x + u[p].y * v[p].y;
-        im += u[p].x * v[p].y - u[p].y * v[p].x;
+      if (stage_psi) {
+        const double2* u = P + (size_t)i * N;
+        const double2* v = P + (size_t)j * N;
+        for (int p = 0; p < N; ++p) {
+          re += u[p].x * v[p].x + u[p].y * v[p].y;
+          im += u[p].x * v[p].y - u[p].y * v[p].x;
+        }
+      } else {
+        for (int p = 0; p < N; ++p) {
+          const double2 u = to_d2(psi[((size_t)w * N + p) * ncol + c0 + i]);
+          const double2 v = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
+          re += u.x * v.x + u.y * v.y;
+          im += u.x * v.y - u.y * v.x;
+        }
       }
       G[i * n + j] = mk(re, im);
     }

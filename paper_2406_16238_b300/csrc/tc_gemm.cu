@@ -598,13 +598,9 @@ template <int EPI>
 afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s,
                     unsigned long long* launches, char* err, size_t errlen) {
   const size_t sm = smem_bytes(g);
-  static size_t configured = 0;
-  if (sm > configured) {
-    if (cudaFuncSetAttribute(k_tc_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-      snprintf(err, errlen, "tcgen05 GEMM: cannot reserve %zu bytes of shared memory", sm);
-      return AFQMC_ECUDA;
-    }
-    configured = sm;
+  if (sm > (size_t)kMaxSmem) {
+    snprintf(err, errlen, "tcgen05 GEMM: %zu bytes of shared memory exceed the limit", sm);
+    return AFQMC_EINVAL;
   }
   const int tiles = g.m_tiles * g.n_tiles;
   const int grid = std::min(tiles, num_sms());
@@ -698,6 +694,12 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(err, errlen, "tc prepare: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  // reserve the kernels' shared memory now (not while a stream is being captured)
+  if (cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+    snprintf(err, errlen, "tcgen05 GEMM: cannot reserve shared memory");
     return AFQMC_ECUDA;
   }
   st->ready = true;

@@ -311,3 +311,23 @@ def test_full_size_sampled_walkers():
         assert abs(w_g[i] - w1) < 1e-11 * w1
         e1 = orc.local_energy(st, ta1, tb1)[0]
         assert abs(eloc1[i, 0] - e1) < 1e-10 * abs(e1)
+
+
+@pytest.mark.parametrize("prec,name,nw", [("fp64", "rhf_N8", 64), ("fp64", "uhf_N13_3_2", 16), ("bf16x3", "rhf_N8", 32)])
+def test_graph_replay_is_bit_identical_to_direct_launches(prec, name, nw):
+    """afqmc_run with captured CUDA graphs == direct launches, bit for bit (energy every 2nd step, QR, comb)."""
+    prob = PROBLEMS[name]()
+    out = {}
+    for graphs in (False, True):
+        ctx = _ctx(prob, nw, prec=prec, seed=31)
+        ctx.set_graphs(graphs)
+        e = ctx.run(23, energy_every=2, reortho_every=5, comb_every=10)
+        psi, logo, w, step = ctx.get_walkers()
+        e2 = ctx.run(7, energy_every=1, reortho_every=5, comb_every=10)   # continues: graphs reused
+        out[graphs] = (e, psi, w, step, e2, ctx.launch_count())
+        ctx.close()
+    a, b = out[False], out[True]
+    assert a[3] == b[3] == 23
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[4], b[4])
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert a[5] == b[5]                      # the same kernels ran, counted per graph node
