@@ -169,6 +169,37 @@ afqmc_status afqmc_draw_normals(uint64_t seed, uint64_t step, uint32_t stream_id
 
 afqmc_status afqmc_get_info(afqmc_ctx* ctx, afqmc_info* info);
 
+/* Learned control variate for the exchange energy (the mixed estimator of Eq. 9 split
+ * as E_L = A - K, A = Re(E0 + E1 + J) for every walker, K = the exchange term).  An MLP
+ * f(z): 2 norb + 8 -> 256 -> 256 -> 256 -> 1 (tanh) of per-walker features z = [diag Re
+ * G^alpha, diag Re G^beta, mean / variance / skewness / kurtosis of Re and Im vbias]
+ * predicts K; exact K on m = round(sample_frac W) walkers drawn uniformly without
+ * replacement each measurement (Philox stream 2) keeps the estimator unbiased:
+ *   ENumer = sum_i w_i (A_i - f_i) - (W / m) sum_{i in S} w_i (K_i - f_i),
+ * EDenom = sum w, E1Body = sum w Re(E0 + E1), E2Body = ENumer - E1Body.
+ * The network is trained on the GPU (Adam, MSE) on (z, K) pairs the method generates.
+ * cv_attach carves the network, optimiser state and a training set of `capacity` pairs
+ * from a caller device block (256-byte aligned, afqmc_cv_workspace_size bytes).
+ * Requires nwalkers <= 8192.  While enabled, afqmc_local_energy returns the sums only. */
+afqmc_status afqmc_cv_workspace_size(afqmc_ctx* ctx, int32_t capacity, int32_t batch, size_t* bytes);
+afqmc_status afqmc_cv_attach(afqmc_ctx* ctx, int32_t capacity, int32_t batch, double sample_frac, uint64_t init_seed,
+                             void* dev, size_t bytes);
+/* Runs nsteps plain steps (energy every step, QR / comb at the given cadences), storing every
+ * walker's (z, exact K) until the training set is full; *npairs = pairs stored so far. */
+afqmc_status afqmc_cv_collect(afqmc_ctx* ctx, int32_t nsteps, int32_t reortho_every, int32_t comb_every,
+                              int32_t* npairs);
+/* Standardises the training set (first call) and runs `epochs` of minibatch Adam; losses[e]
+ * (host, may be NULL) = mean minibatch loss of epoch e (standardised units). */
+afqmc_status afqmc_cv_train(afqmc_ctx* ctx, int32_t epochs, double lr, double* losses);
+afqmc_status afqmc_cv_enable(afqmc_ctx* ctx, int32_t enable);
+/* Network parameters [W1 (in x 256), b1, W2, b2, W3, b3, W4 (256 x 1), b4] as float32 (get: set = 0). */
+afqmc_status afqmc_cv_params(afqmc_ctx* ctx, int32_t set, float* host);
+/* Forward pass on rows of x [rows][dim] (network inputs); with y, also the MSE loss and every
+ * gradient (same layout as the parameters).  rows <= batch. */
+afqmc_status afqmc_cv_eval(afqmc_ctx* ctx, const float* x, const float* y, int32_t rows, float* out, float* loss,
+                           float* grads);
+afqmc_status afqmc_cv_info(afqmc_ctx* ctx, int32_t* dim, uint64_t* nparams, int32_t* npairs, int32_t* nsample);
+
 /* afqmc_run replays each step pattern (energy + propagation, propagation alone, QR, comb) as a
  * CUDA graph captured on first use (enable = 1, the default); enable = 0 launches every kernel
  * directly.  Results are identical either way.  Tracing (afqmc_profile) uses direct launches. */

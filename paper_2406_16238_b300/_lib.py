@@ -46,6 +46,7 @@ class Info(ctypes.Structure):
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _u64 = ctypes.c_uint64
@@ -67,6 +68,14 @@ SIGNATURES = {
     "afqmc_get_info": (_i32, [_vp, ctypes.POINTER(Info)]),
     "afqmc_set_etrial": (_i32, [_vp, ctypes.c_double]),
     "afqmc_set_graphs": (_i32, [_vp, _i32]),
+    "afqmc_cv_workspace_size": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "afqmc_cv_attach": (_i32, [_vp, _i32, _i32, ctypes.c_double, _u64, _vp, ctypes.c_size_t]),
+    "afqmc_cv_collect": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
+    "afqmc_cv_train": (_i32, [_vp, _i32, ctypes.c_double, _dp]),
+    "afqmc_cv_enable": (_i32, [_vp, _i32]),
+    "afqmc_cv_params": (_i32, [_vp, _i32, _fp]),
+    "afqmc_cv_eval": (_i32, [_vp, _fp, _fp, _i32, _fp, _fp, _fp]),
+    "afqmc_cv_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_u64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "afqmc_synchronize": (_i32, [_vp, ctypes.c_double]),
     "afqmc_destroy": (None, [_vp]),
     "afqmc_launch_count": (_u64, [_vp]),
@@ -201,6 +210,55 @@ class Afqmc:
         inf = Info()
         _check(self._lib.afqmc_get_info(self._ctx, ctypes.byref(inf)))
         return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    # --- learned control variate -------------------------------------------------------
+    def cv_attach(self, capacity=100000, batch=1024, sample_frac=0.125, seed=1):
+        import torch
+        nbytes = ctypes.c_size_t()
+        _check(self._lib.afqmc_cv_workspace_size(self._ctx, int(capacity), int(batch), ctypes.byref(nbytes)))
+        self.cv_workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        _check(self._lib.afqmc_cv_attach(self._ctx, int(capacity), int(batch), float(sample_frac), int(seed),
+                                         ctypes.c_void_p(self.cv_workspace.data_ptr()), nbytes.value))
+        dim, npar, npairs, nsample = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.afqmc_cv_info(self._ctx, ctypes.byref(dim), ctypes.byref(npar), ctypes.byref(npairs),
+                                       ctypes.byref(nsample)))
+        self.cv_dim, self.cv_nparams, self.cv_batch, self.cv_nsample = dim.value, npar.value, int(batch), nsample.value
+
+    def cv_collect(self, nsteps, reortho_every=5, comb_every=10):
+        n = ctypes.c_int32()
+        _check(self._lib.afqmc_cv_collect(self._ctx, int(nsteps), int(reortho_every), int(comb_every), ctypes.byref(n)))
+        return n.value
+
+    def cv_train(self, epochs, lr=1e-3):
+        losses = np.zeros(max(1, epochs))
+        _check(self._lib.afqmc_cv_train(self._ctx, int(epochs), float(lr), _ptr(losses)))
+        return losses[:epochs]
+
+    def cv_enable(self, enable=True):
+        _check(self._lib.afqmc_cv_enable(self._ctx, 1 if enable else 0))
+
+    def cv_get_params(self):
+        p = np.zeros(self.cv_nparams, dtype=np.float32)
+        _check(self._lib.afqmc_cv_params(self._ctx, 0, p.ctypes.data_as(_fp)))
+        return p
+
+    def cv_set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.cv_nparams
+        _check(self._lib.afqmc_cv_params(self._ctx, 1, p.ctypes.data_as(_fp)))
+
+    def cv_eval(self, x, y=None):
+        """Forward (and, with y, loss + gradients) of the network on host rows x [rows][dim]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        rows = x.shape[0]
+        out = np.zeros(rows, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        grads = np.zeros(self.cv_nparams, dtype=np.float32)
+        yy = None if y is None else np.ascontiguousarray(y, dtype=np.float32)
+        _check(self._lib.afqmc_cv_eval(self._ctx, x.ctypes.data_as(_fp), None if yy is None else yy.ctypes.data_as(_fp),
+                                       rows, out.ctypes.data_as(_fp), loss.ctypes.data_as(_fp),
+                                       grads.ctypes.data_as(_fp)))
+        return (out, float(loss[0]), grads) if y is not None else out
 
     def set_graphs(self, enable=True):
         _check(self._lib.afqmc_set_graphs(self._ctx, 1 if enable else 0))

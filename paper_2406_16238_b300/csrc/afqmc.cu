@@ -7,13 +7,16 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <chrono>
 #include <mutex>
+#include <random>
 #include <thread>
 #include <vector>
 
 #include "afqmc.h"
 #include "kernels_simt.cuh"
+#include "cv_kernels.cuh"
 #include "tc_gemm.cuh"
 
 using namespace afq;
@@ -228,6 +231,7 @@ struct afqmc_ctx {
   bool theta_fresh, vbias_fresh;
   int hist_used;
   tc::TcState tcs;
+  CvState cv;
   // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
   bool graphs_on = true;
   cudaStream_t cap_stream = nullptr;
@@ -395,7 +399,7 @@ size_t exchange_smem(const Dims& d) {
 }
 
 template <typename R>
-afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange) {
+afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange, const int* widx = nullptr, int rows = -1) {
   ExchangeArgs<R> a{};
   a.N = c->d.N; a.X = c->d.X; a.ncol = c->d.ncol; a.nblk = c->d.nblk;
   a.c0[0] = c->d.c0[0]; a.c0[1] = c->d.c0[1]; a.nb[0] = c->d.nbk[0]; a.nb[1] = c->d.nbk[1];
@@ -405,7 +409,9 @@ afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange) {
   a.vbias = c->at<cplx_t<R>>(c->L.vbias);
   a.exch_part = c->at<double2>(c->L.exch_part);
   a.with_exchange = with_exchange;
-  dim3 grid(c->d.nchunk, c->d.W);
+  a.widx = widx;
+  a.with_vbias = widx ? 0 : 1;
+  dim3 grid(c->d.nchunk, rows < 0 ? c->d.W : rows);
   k_exchange<R><<<grid, 256, exchange_smem(c->d), c->stream>>>(a);
   CHECK_LAUNCH(c);
   return AFQMC_OK;
@@ -428,7 +434,11 @@ afqmc_status set_smem_limits(const Dims& d) {
 
 // Local energy at the current walkers into eloc and the weighted sums into sums_dev.
 template <typename R>
+afqmc_status energy_cv_impl(afqmc_ctx* c, double* sums_dev, int* slot);
+
+template <typename R>
 afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
+  if (c->cv.enabled) return energy_cv_impl<R>(c, sums_dev, slot);
   afqmc_status st;
   if (!c->theta_fresh) {
     if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
@@ -438,7 +448,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
   if (c->d.prec == AFQMC_PREC_BF16 || c->d.prec == AFQMC_PREC_BF16X3) {
     if ((st = tc::exchange(&c->tcs, c->stream, c->at<char>(c->L.tc), c->smul, c->at<float2>(c->L.thetaT),
                            c->at<float2>(c->L.vbias), c->at<double2>(c->L.exch_part), c->at<int>(c->L.status),
-                           &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
+                           nullptr, c->d.W, &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
       return st;
   } else {
     if ((st = launch_exchange<R>(c, 1)) != AFQMC_OK) return st;
@@ -760,6 +770,8 @@ afqmc_status check_ctx(afqmc_ctx* c) {
   return AFQMC_OK;
 }
 
+#include "cv_host.inc"
+
 // Captures `body` (which enqueues on c->stream) into an executable graph.  Host-side state is
 // restored afterwards; the caller applies the state change of one replay itself.
 template <typename F>
@@ -947,6 +959,8 @@ afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps) {
 afqmc_status afqmc_local_energy(afqmc_ctx* ctx, double* sums, double* eloc) {
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;
+  if (eloc && ctx->cv.enabled)
+    return fail(AFQMC_EINVAL, "per-walker energies are not formed in the control-variate form (exchange is subsampled)");
   double* dsums = ctx->at<double>(ctx->L.hist) + 4 * (kHistory - 1);
   if ((st = DISPATCH(ctx, energy_impl, dsums)) != AFQMC_OK) return st;
   if (sums) CU(cudaMemcpyAsync(sums, dsums, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1130,6 +1144,135 @@ afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial) {
     ctx->drop_graphs();
   }
   ctx->e_trial = e_trial;
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- learned control variate
+afqmc_status afqmc_cv_workspace_size(afqmc_ctx* ctx, int32_t capacity, int32_t batch, size_t* bytes) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!bytes || capacity < 1 || batch < 1) return fail(AFQMC_EINVAL, "cv: capacity and batch must be >= 1");
+  CvState tmp;
+  *bytes = cv_plan(&tmp, 2 * ctx->d.N + 8, ctx->d.W, capacity, batch, nullptr);
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_cv_attach(afqmc_ctx* ctx, int32_t capacity, int32_t batch, double sample_frac, uint64_t init_seed,
+                             void* dev, size_t bytes) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (capacity < 1 || batch < 1) return fail(AFQMC_EINVAL, "cv: capacity and batch must be >= 1");
+  if (!(sample_frac > 0.0 && sample_frac <= 1.0)) return fail(AFQMC_EINVAL, "cv: sample_frac must be in (0, 1]");
+  if (ctx->d.W > 8192) return fail(AFQMC_EINVAL, "cv: at most 8192 walkers (subsample drawn in one block)");
+  if (!dev || (reinterpret_cast<uintptr_t>(dev) & 255)) return fail(AFQMC_EINVAL, "cv: device block must be 256-byte aligned");
+  CvState v;
+  const size_t need = cv_plan(&v, 2 * ctx->d.N + 8, ctx->d.W, capacity, batch, nullptr);
+  if (bytes < need) return fail(AFQMC_ENOMEM, "cv: device block has %zu bytes, %zu needed", bytes, need);
+  cv_plan(&v, 2 * ctx->d.N + 8, ctx->d.W, capacity, batch, static_cast<char*>(dev));
+  v.attached = true;
+  v.cap = capacity;
+  v.B = batch;
+  v.frac = sample_frac;
+  v.m = std::max(1, std::min(ctx->d.W, (int)std::lround(sample_frac * ctx->d.W)));
+  v.seed = init_seed;
+  v.bytes = need;
+  // Glorot-uniform weights, zero biases
+  std::vector<float> p(v.nparams, 0.f);
+  std::mt19937_64 rng(init_seed);
+  auto glorot = [&](size_t off, int a, int b) {
+    std::uniform_real_distribution<double> u(-std::sqrt(6.0 / (a + b)), std::sqrt(6.0 / (a + b)));
+    for (size_t i = 0; i < (size_t)a * b; ++i) p[off + i] = (float)u(rng);
+  };
+  glorot(v.oW1, v.D, v.H);
+  glorot(v.oW2, v.H, v.H);
+  glorot(v.oW3, v.H, v.H);
+  glorot(v.oW4, v.H, 1);
+  CU(cudaMemcpyAsync(v.P, p.data(), v.nparams * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemsetAsync(v.Mo, 0, v.nparams * 4, ctx->stream));
+  CU(cudaMemsetAsync(v.Vo, 0, v.nparams * 4, ctx->stream));
+  const float ident[2] = {0.f, 1.f};
+  CU(cudaMemcpyAsync(v.ystat, ident, 8, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  int P2 = 1;
+  while (P2 < ctx->d.W) P2 <<= 1;
+  CU(cudaFuncSetAttribute(k_cv_select, cudaFuncAttributeMaxDynamicSharedMemorySize, P2 * 8));
+  ctx->drop_graphs();
+  ctx->cv = v;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_cv_collect(afqmc_ctx* ctx, int32_t nsteps, int32_t reortho_every, int32_t comb_every,
+                              int32_t* npairs) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!ctx->cv.attached) return fail(AFQMC_EINVAL, "cv: not attached");
+  if (ctx->cv.scaled) return fail(AFQMC_EINVAL, "cv: training data are already standardised (collect before training)");
+  if ((st = DISPATCH(ctx, cv_collect_impl, nsteps, reortho_every, comb_every)) != AFQMC_OK) return st;
+  if (npairs) *npairs = ctx->cv.ndata;
+  return read_status(ctx);
+}
+
+afqmc_status afqmc_cv_train(afqmc_ctx* ctx, int32_t epochs, double lr, double* losses) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!ctx->cv.attached) return fail(AFQMC_EINVAL, "cv: not attached");
+  if (epochs < 0 || !(lr > 0.0)) return fail(AFQMC_EINVAL, "cv: epochs >= 0 and lr > 0 required");
+  return cv_train_impl(ctx, epochs, lr, losses);
+}
+
+afqmc_status afqmc_cv_enable(afqmc_ctx* ctx, int32_t enable) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (enable && !ctx->cv.attached) return fail(AFQMC_EINVAL, "cv: not attached");
+  if ((enable != 0) != ctx->cv.enabled) {
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->drop_graphs();
+  }
+  ctx->cv.enabled = enable != 0;
+  ctx->vbias_fresh = false;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_cv_params(afqmc_ctx* ctx, int32_t set, float* host) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!ctx->cv.attached || !host) return fail(AFQMC_EINVAL, "cv: not attached or NULL buffer");
+  const size_t b = ctx->cv.nparams * 4;
+  if (set) CU(cudaMemcpyAsync(ctx->cv.P, host, b, cudaMemcpyHostToDevice, ctx->stream));
+  else CU(cudaMemcpyAsync(host, ctx->cv.P, b, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_cv_eval(afqmc_ctx* ctx, const float* x, const float* y, int32_t rows, float* out, float* loss,
+                           float* grads) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  CvState& v = ctx->cv;
+  if (!v.attached || !x) return fail(AFQMC_EINVAL, "cv: not attached or NULL input");
+  if (rows < 1 || rows > v.B) return fail(AFQMC_EINVAL, "cv: rows must be in [1, batch = %d]", v.B);
+  CU(cudaMemcpyAsync(v.X, x, (size_t)rows * v.D * 4, cudaMemcpyHostToDevice, ctx->stream));
+  if ((st = cv_forward(ctx, rows, v.X, v.A1, v.A2, v.A3, v.out)) != AFQMC_OK) return st;
+  if (y) {
+    CU(cudaMemcpyAsync(v.yb, y, (size_t)rows * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(v.loss, 0, 4, ctx->stream));
+    if ((st = cv_backward(ctx, rows)) != AFQMC_OK) return st;
+    if (loss) CU(cudaMemcpyAsync(loss, v.loss, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (grads) CU(cudaMemcpyAsync(grads, v.G, v.nparams * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (out) CU(cudaMemcpyAsync(out, v.out, (size_t)rows * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_cv_info(afqmc_ctx* ctx, int32_t* dim, uint64_t* nparams, int32_t* npairs, int32_t* nsample) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  const CvState& v = ctx->cv;
+  if (dim) *dim = 2 * ctx->d.N + 8;
+  if (nparams) { CvState tmp; cv_plan(&tmp, 2 * ctx->d.N + 8, 1, 1, 1, nullptr); *nparams = tmp.nparams; }
+  if (npairs) *npairs = v.ndata;
+  if (nsample) *nsample = v.m;
   return AFQMC_OK;
 }
 

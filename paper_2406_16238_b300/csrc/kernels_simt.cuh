@@ -176,8 +176,10 @@ struct ExchangeArgs {
   const cplx_t<R>* thetaT;   // [W][ncol][N]
   const R* lrot;             // [X][ncol][N]
   cplx_t<R>* vbias;          // [W][X]
-  double2* exch_part;        // [W][nchunk]
+  double2* exch_part;        // [rows][nchunk]
   int with_exchange;
+  const int* widx;           // optional: CTA row y works on walker widx[y] (its partials go to row y)
+  int with_vbias;
 };
 
 template <typename R>
@@ -185,7 +187,8 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
   using R2 = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char sm_ex[];
   __shared__ double red[32];
-  const int chunk = blockIdx.x, w = blockIdx.y, tid = threadIdx.x;
+  const int chunk = blockIdx.x, row = blockIdx.y, tid = threadIdx.x;
+  const int w = a.widx ? a.widx[row] : row;
   const int cn = a.ncol * a.N;
   R2* th = (R2*)sm_ex;                                // [ncol][N]
   R* lr = (R*)(th + cn);                              // [ncol][N]
@@ -239,11 +242,11 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
       }
       __syncthreads();
     }
-    if (tid == 0) a.vbias[(size_t)w * a.X + g] = from_d2<R>(cscale(vb, a.smul));
+    if (tid == 0 && a.with_vbias) a.vbias[(size_t)w * a.X + g] = from_d2<R>(cscale(vb, a.smul));
   }
   if (!a.with_exchange) return;
   const double2 tot = block_sum2(exx, red);
-  if (tid == 0) a.exch_part[(size_t)w * a.nchunk + chunk] = cscale(tot, a.smul);
+  if (tid == 0) a.exch_part[(size_t)row * a.nchunk + chunk] = cscale(tot, a.smul);
 }
 
 // Per-walker local energy from the pieces: E1 = smul sum htilde . Theta^T,

@@ -270,7 +270,7 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
     named_bar(bar_id, 128);
     const int w = nt * p.wpt + v;
     if (w < p.W && wig == 0) {
-      for (int gl = lane; gl < p.gpt; gl += 32) {   // one gamma per lane, sequential sum over its n rows
+      for (int gl = lane; p.vbias && gl < p.gpt; gl += 32) {   // one gamma per lane, sequential sum over its n rows
         const int gam = mt * p.gpt + gl;
         if (gam >= p.X) continue;
         float sr = 0.f, si = 0.f;
@@ -447,15 +447,16 @@ __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUte
 // ----------------------------------------------------------------------------- operand conversion
 // Theta^T complex64 [W][ncol][N] -> per block rows (w, part, b) of nseg * kst bf16: B = [hi | hi | lo].
 __global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int nseg, const float2* thetaT,
-                             __nv_bfloat16* out) {
-  const int w = blockIdx.x;
+                             __nv_bfloat16* out, const int* widx) {
+  const int w = blockIdx.x;              // output row block
+  const int src = widx ? widx[w] : w;    // walker it holds
   const int rowlen = nseg * kst;
   for (int idx = threadIdx.x; idx < 2 * n * kst; idx += blockDim.x) {
     const int row = idx / kst, pp = idx % kst;
     const int part = row / n, b = row % n;
     float v = 0.f;
     if (pp < N) {
-      const float2 t = thetaT[((size_t)w * ncol + c0 + b) * N + pp];
+      const float2 t = thetaT[((size_t)src * ncol + c0 + b) * N + pp];
       v = part ? t.y : t.x;
     }
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -707,18 +708,20 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
 }
 
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
-                      double2* exch_part, int* status, unsigned long long* launches, char* err, size_t errlen) {
+                      double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
+                      char* err, size_t errlen) {
   int chunk = 0;
   bool first = true;
+  if (nw <= 0) return AFQMC_OK;
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
     if (bm.n == 0) continue;
-    k_theta_bf16<<<st->W, 256, 0, s>>>(st->W, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, thetaT,
-                                       reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th));
+    k_theta_bf16<<<nw, 256, 0, s>>>(nw, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, thetaT,
+                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th), widx);
     ++*launches;
     Geom g{};
     g.m_tiles = bm.m_tiles;
-    g.n_tiles = bm.n_tiles;
+    g.n_tiles = (nw + bm.wpt - 1) / bm.wpt;
     g.k_blocks = st->nseg * st->kst / kBK;
     g.m_step = bm.gpt * bm.n;
     g.n_step = bm.wpt * 2 * bm.n;
@@ -731,7 +734,7 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     Params p{};
     p.g = g;
     p.status = status;
-    p.W = st->W; p.X = st->X; p.n = bm.n; p.gpt = bm.gpt; p.wpt = bm.wpt;
+    p.W = nw; p.X = st->X; p.n = bm.n; p.gpt = bm.gpt; p.wpt = bm.wpt;
     p.chunk_offset = chunk; p.nchunk = st->nchunk; p.vbias_add = first ? 0 : 1;
     p.smul = (float)smul;
     p.vbias = vbias;
