@@ -200,6 +200,29 @@ afqmc_status afqmc_cv_eval(afqmc_ctx* ctx, const float* x, const float* y, int32
                            float* grads);
 afqmc_status afqmc_cv_info(afqmc_ctx* ctx, int32_t* dim, uint64_t* nparams, int32_t* npairs, int32_t* nsample);
 
+/* Project autotuner: times `steps` propagation + energy steps of every candidate setting
+ * (CUDA-core GEMM block tile 64 / 32, fused or batched-GEMM propagation, 1 / 2 / 4 tensor-core
+ * epilogue warpgroups) on the context's own walkers, restores the walkers, keeps the fastest.
+ * chosen (may be NULL) receives it; afqmc_set_tuning applies a setting directly. */
+typedef struct {
+  int32_t tile_cap;       /* 4: 64-wide CUDA-core GEMM tiles allowed, 2: at most 32, 1: 16 */
+  int32_t prop_generic;   /* 1: batched GEMMs for the propagation instead of the fused kernel */
+  int32_t exch_groups;    /* tensor-core exchange epilogue warpgroups (0: largest that fits) */
+  float ms_per_step;      /* measured by afqmc_autotune */
+} afqmc_tuning;
+afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen);
+afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t);
+
+/* Batched independent systems: the contexts (same device, same nwalkers cadence) advance in
+ * lockstep, each step being ONE CUDA graph launch whose branches are the systems' step graphs,
+ * so uneven systems run concurrently.  energies (host, may be NULL): [nsys][nmeas][4].
+ * The batch launches on the first context's stream; do not use the contexts concurrently. */
+typedef struct afqmc_batch afqmc_batch;
+afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batch** out);
+afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
+                             int32_t comb_every, double* energies, int32_t* nmeas);
+void afqmc_batch_destroy(afqmc_batch* b);
+
 /* afqmc_run replays each step pattern (energy + propagation, propagation alone, QR, comb) as a
  * CUDA graph captured on first use (enable = 1, the default); enable = 0 launches every kernel
  * directly.  Results are identical either way.  Tracing (afqmc_profile) uses direct launches. */

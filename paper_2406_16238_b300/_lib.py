@@ -45,6 +45,11 @@ class Info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_cap", ctypes.c_int32), ("prop_generic", ctypes.c_int32), ("exch_groups", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_float)]
+
+
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
@@ -68,6 +73,11 @@ SIGNATURES = {
     "afqmc_get_info": (_i32, [_vp, ctypes.POINTER(Info)]),
     "afqmc_set_etrial": (_i32, [_vp, ctypes.c_double]),
     "afqmc_set_graphs": (_i32, [_vp, _i32]),
+    "afqmc_autotune": (_i32, [_vp, _i32, ctypes.POINTER(Tuning)]),
+    "afqmc_set_tuning": (_i32, [_vp, ctypes.POINTER(Tuning)]),
+    "afqmc_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "afqmc_batch_run": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
+    "afqmc_batch_destroy": (None, [_vp]),
     "afqmc_cv_workspace_size": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
     "afqmc_cv_attach": (_i32, [_vp, _i32, _i32, ctypes.c_double, _u64, _vp, ctypes.c_size_t]),
     "afqmc_cv_collect": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
@@ -260,6 +270,15 @@ class Afqmc:
                                        grads.ctypes.data_as(_fp)))
         return (out, float(loss[0]), grads) if y is not None else out
 
+    def autotune(self, steps=3):
+        t = Tuning()
+        _check(self._lib.afqmc_autotune(self._ctx, int(steps), ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def set_tuning(self, tile_cap=4, prop_generic=0, exch_groups=0):
+        t = Tuning(int(tile_cap), int(prop_generic), int(exch_groups), 0.0)
+        _check(self._lib.afqmc_set_tuning(self._ctx, ctypes.byref(t)))
+
     def set_graphs(self, enable=True):
         _check(self._lib.afqmc_set_graphs(self._ctx, 1 if enable else 0))
 
@@ -322,3 +341,35 @@ def comb_plan_noalloc(w, seed, step, src, neww, stream=None):
     _check(lib.afqmc_comb_plan_noalloc(ctypes.c_void_p(w.data_ptr()), int(w.numel()), int(seed) & (2 ** 64 - 1),
                                        int(step), ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(neww.data_ptr()),
                                        ctypes.c_void_p(s.cuda_stream)))
+
+
+class Batch:
+    """Independent contexts advanced in lockstep, one CUDA graph launch per step (afqmc_batch_*)."""
+
+    def __init__(self, contexts):
+        self._lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._ctx.value for c in self.contexts])
+        b = ctypes.c_void_p()
+        _check(self._lib.afqmc_batch_create(len(self.contexts), arr, ctypes.byref(b)))
+        self._b = b
+
+    def run(self, nsteps, energy_every=1, reortho_every=5, comb_every=10):
+        start = self.contexts[0].info()["step"]
+        nm = sum(1 for k in range(nsteps) if energy_every > 0 and (start + k) % energy_every == 0)
+        out = np.zeros((len(self.contexts), max(nm, 1), 4))
+        n = ctypes.c_int32()
+        _check(self._lib.afqmc_batch_run(self._b, int(nsteps), int(energy_every), int(reortho_every), int(comb_every),
+                                         _ptr(out), ctypes.byref(n)))
+        return out[:, : n.value]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.afqmc_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <mutex>
 #include <random>
 #include <thread>
@@ -232,6 +233,8 @@ struct afqmc_ctx {
   int hist_used;
   tc::TcState tcs;
   CvState cv;
+  int tile_cap = 4;          // largest CUDA-core GEMM register tile (4: 64-wide block tiles, 2: 32, 1: 16)
+  int prop_generic = 0;      // 1: batched GEMMs for the propagation even where the fused kernel fits
   // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
   bool graphs_on = true;
   cudaStream_t cap_stream = nullptr;
@@ -315,8 +318,8 @@ afqmc_status gemm_tiled(afqmc_ctx* c, const GemmDesc& g) {
 template <typename R, bool CA, bool CB>
 afqmc_status gemm(afqmc_ctx* c, const GemmDesc& g) {
   if (g.M <= 0 || g.Nc <= 0 || g.batch <= 0) return AFQMC_OK;
-  int tm = g.M >= 48 ? 4 : (g.M > 16 ? 2 : 1);
-  int tn = g.Nc >= 48 ? 4 : (g.Nc > 16 ? 2 : 1);
+  int tm = std::min(c->tile_cap, g.M >= 48 ? 4 : (g.M > 16 ? 2 : 1));
+  int tn = std::min(c->tile_cap, g.Nc >= 48 ? 4 : (g.Nc > 16 ? 2 : 1));
   auto ctas = [&](int a, int b) {
     return (long long)((g.M + 16 * a - 1) / (16 * a)) * ((g.Nc + 16 * b - 1) / (16 * b)) * g.batch;
   };
@@ -417,18 +420,31 @@ afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange, const int* widx = 
   return AFQMC_OK;
 }
 
+afqmc_status allow_max_dynamic_smem(const void* fn) {
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  CU(cudaFuncGetAttributes(&fa, fn));
+  CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+  return AFQMC_OK;
+}
+
 template <typename R>
 afqmc_status set_smem_limits(const Dims& d) {
+  afqmc_status st_;
   const size_t ov = overlap_smem(d), ex = d.tensor() ? 0 : exchange_smem(d), qr = qr_smem(d);
   const size_t lim = 227 * 1024;
   if (ov > lim || ex > lim || qr > lim)
     return fail(AFQMC_EINVAL, "problem too large for the CUDA-core kernels' shared-memory staging "
                               "(overlap %zu, exchange %zu, qr %zu bytes > %zu)", ov, ex, qr, lim);
-  CU(cudaFuncSetAttribute(k_overlap_gj<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ov));
-  if (ex) CU(cudaFuncSetAttribute(k_exchange<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ex));
-  CU(cudaFuncSetAttribute(k_qr_chol<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr));
-  if (use_fused_propagation(d))
-    CU(cudaFuncSetAttribute(k_propagate_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prop_smem(d)));
+  // The attribute is per kernel, shared by every context in the process: allow the largest
+  // dynamic size the device permits next to the kernel's static shared memory (each launch still
+  // requests only its own size).
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_gj<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_exchange<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_chol<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem))) != AFQMC_OK) return st_;
   return AFQMC_OK;
 }
 
@@ -515,7 +531,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   // psi <- E_h Taylor(VHS) E_h psi   (tA = accumulator, tB/tC = Taylor terms)
   const double* skip = c->at<double>(c->L.w);
   StageTimer* tp = new StageTimer(c, AFQMC_STAGE_PROPAGATE);
-  if (use_fused_propagation(d)) {
+  if (use_fused_propagation(d) && !c->prop_generic) {
     PropArgs pa{};
     pa.N = d.N; pa.ncol = d.ncol; pa.order = c->taylor;
     prop_smem_floats(d.N, d.ncol, &pa.ldv, &pa.ldc);
@@ -772,10 +788,10 @@ afqmc_status check_ctx(afqmc_ctx* c) {
 
 #include "cv_host.inc"
 
-// Captures `body` (which enqueues on c->stream) into an executable graph.  Host-side state is
-// restored afterwards; the caller applies the state change of one replay itself.
+// Captures `body` (which enqueues on c->stream) into a graph.  Host-side state is restored
+// afterwards; the caller applies the state change of one replay itself.
 template <typename F>
-afqmc_status capture(afqmc_ctx* c, F body, cudaGraphExec_t* out, unsigned long long* nkernels) {
+afqmc_status capture_graph(afqmc_ctx* c, F body, cudaGraph_t* out, unsigned long long* nkernels) {
   if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   const bool tf = c->theta_fresh, vf = c->vbias_fresh;
   const unsigned long long hs = c->host_step, l0 = c->launches;
@@ -790,6 +806,17 @@ afqmc_status capture(afqmc_ctx* c, F body, cudaGraphExec_t* out, unsigned long l
   c->theta_fresh = tf; c->vbias_fresh = vf; c->host_step = hs; c->launches = l0;
   if (st != AFQMC_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  *out = graph;
+  return AFQMC_OK;
+}
+
+// Captures `body` (which enqueues on c->stream) into an executable graph.  Host-side state is
+// restored afterwards; the caller applies the state change of one replay itself.
+template <typename F>
+afqmc_status capture(afqmc_ctx* c, F body, cudaGraphExec_t* out, unsigned long long* nkernels) {
+  cudaGraph_t graph = nullptr;
+  afqmc_status st = capture_graph(c, body, &graph, nkernels);
+  if (st != AFQMC_OK) return st;
   const cudaError_t e2 = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e2 != cudaSuccess) return fail(AFQMC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
@@ -1195,7 +1222,8 @@ afqmc_status afqmc_cv_attach(afqmc_ctx* ctx, int32_t capacity, int32_t batch, do
   CU(cudaStreamSynchronize(ctx->stream));
   int P2 = 1;
   while (P2 < ctx->d.W) P2 <<= 1;
-  CU(cudaFuncSetAttribute(k_cv_select, cudaFuncAttributeMaxDynamicSharedMemorySize, P2 * 8));
+  (void)P2;
+  if ((st = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_cv_select))) != AFQMC_OK) return st;
   ctx->drop_graphs();
   ctx->cv = v;
   return AFQMC_OK;
@@ -1274,6 +1302,89 @@ afqmc_status afqmc_cv_info(afqmc_ctx* ctx, int32_t* dim, uint64_t* nparams, int3
   if (npairs) *npairs = v.ndata;
   if (nsample) *nsample = v.m;
   return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!t || (t->tile_cap != 1 && t->tile_cap != 2 && t->tile_cap != 4)) return fail(AFQMC_EINVAL, "tuning: tile_cap 1, 2 or 4");
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->drop_graphs();
+  ctx->tile_cap = t->tile_cap;
+  ctx->prop_generic = t->prop_generic ? 1 : 0;
+  if (ctx->d.tensor()) tc::set_exchange_groups(&ctx->tcs, ctx->at<char>(ctx->L.tc), t->exch_groups);
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (steps < 1) return fail(AFQMC_EINVAL, "autotune: steps >= 1");
+  const Dims& d = ctx->d;
+  // snapshot of the walkers (host copies), restored after every trial
+  const size_t pb = (size_t)d.W * d.N * d.ncol * 2 * d.rsz();
+  std::vector<char> psi(pb), logo((size_t)d.W * 16), w((size_t)d.W * 8);
+  CU(cudaMemcpyAsync(psi.data(), ctx->base + ctx->L.psi, pb, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(logo.data(), ctx->base + ctx->L.logO, logo.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(w.data(), ctx->base + ctx->L.w, w.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  const unsigned long long step0 = ctx->host_step;
+  auto restore = [&]() -> afqmc_status {
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.psi, psi.data(), pb, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.logO, logo.data(), logo.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.w, w.data(), w.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.step, &step0, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->host_step = step0;
+    ctx->theta_fresh = false;
+    ctx->vbias_fresh = false;
+    return AFQMC_OK;
+  };
+  std::vector<afqmc_tuning> cands;
+  const bool fused_ok = use_fused_propagation(d);
+  std::vector<int> groups = {0};
+  if (d.tensor()) groups = {1, 2, 4};
+  for (int tc_cap : {4, 2})
+    for (int pg : {0, 1}) {
+      if (pg == 0 && !fused_ok && tc_cap == 2) continue;   // identical to pg = 1
+      for (int g : groups) cands.push_back(afqmc_tuning{tc_cap, fused_ok ? pg : 1, g, 0.f});
+    }
+  const bool graphs_was = ctx->graphs_on, prof_was = ctx->prof;
+  ctx->graphs_on = false;
+  ctx->prof = false;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  afqmc_tuning best{4, 0, 0, 1e30f};
+  double* scratch = ctx->at<double>(ctx->L.hist) + 4 * (kHistory - 1);
+  for (auto& cnd : cands) {
+    if ((st = afqmc_set_tuning(ctx, &cnd)) != AFQMC_OK) break;
+    if ((st = restore()) != AFQMC_OK) break;
+    if ((st = DISPATCH(ctx, energy_impl, scratch)) != AFQMC_OK) break;   // warm-up step
+    if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) break;
+    CU(cudaEventRecord(e0, ctx->stream));
+    for (int k = 0; k < steps && st == AFQMC_OK; ++k) {
+      st = DISPATCH(ctx, energy_impl, scratch);
+      if (st == AFQMC_OK) st = DISPATCH(ctx, step_impl);
+    }
+    if (st != AFQMC_OK) break;
+    CU(cudaEventRecord(e1, ctx->stream));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    cnd.ms_per_step = ms / steps;
+    if (cnd.ms_per_step < best.ms_per_step) best = cnd;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->graphs_on = graphs_was;
+  ctx->prof = prof_was;
+  if (st != AFQMC_OK) return st;
+  if ((st = afqmc_set_tuning(ctx, &best)) != AFQMC_OK) return st;
+  if ((st = restore()) != AFQMC_OK) return st;
+  if (chosen) *chosen = best;
+  return read_status(ctx);
 }
 
 afqmc_status afqmc_set_graphs(afqmc_ctx* ctx, int32_t enable) {
@@ -1358,3 +1469,134 @@ extern "C" afqmc_status afqmc_comb_plan_noalloc(const double* w, int32_t nwalker
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc launch: %s", cudaGetErrorString(e));
   return AFQMC_OK;
 }
+
+// ======================================================================================
+// Batched independent systems: one graph launch per step with one branch per system.
+struct afqmc_batch {
+  std::vector<afqmc_ctx*> sys;
+  struct Exec {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned long long> nk;
+    std::vector<char> end_theta, end_vbias;
+  };
+  std::map<int, Exec> cache;
+  ~afqmc_batch() {
+    for (auto& kv : cache)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  }
+};
+
+namespace {
+
+afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb, afqmc_batch::Exec** out) {
+  auto it = b->cache.find(key);
+  if (it != b->cache.end()) { *out = &it->second; return AFQMC_OK; }
+  afqmc_batch::Exec ex;
+  cudaGraph_t bg = nullptr;
+  CU(cudaGraphCreate(&bg, 0));
+  for (afqmc_ctx* c : b->sys) {
+    cudaGraph_t g = nullptr;
+    unsigned long long nk = 0;
+    bool end_tf = false, end_vf = false;
+    afqmc_status st = capture_graph(c, [&]() -> afqmc_status {
+      afqmc_status s2;
+      if (energy && (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot))) != AFQMC_OK)
+        return s2;
+      if ((s2 = DISPATCH(c, step_impl)) != AFQMC_OK) return s2;
+      if (qr && (s2 = DISPATCH(c, qr_impl)) != AFQMC_OK) return s2;
+      if (comb && (s2 = DISPATCH(c, comb_impl)) != AFQMC_OK) return s2;
+      end_tf = c->theta_fresh;
+      end_vf = c->vbias_fresh;
+      return AFQMC_OK;
+    }, &g, &nk);
+    if (st != AFQMC_OK) { cudaGraphDestroy(bg); return st; }
+    cudaGraphNode_t node;
+    const cudaError_t e = cudaGraphAddChildGraphNode(&node, bg, nullptr, 0, g);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { cudaGraphDestroy(bg); return fail(AFQMC_ECUDA, "batch graph: %s", cudaGetErrorString(e)); }
+    ex.nk.push_back(nk);
+    ex.end_theta.push_back(end_tf);
+    ex.end_vbias.push_back(end_vf);
+  }
+  const cudaError_t e = cudaGraphInstantiate(&ex.exec, bg, 0);
+  cudaGraphDestroy(bg);
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "batch graph instantiation: %s", cudaGetErrorString(e));
+  auto res = b->cache.emplace(key, std::move(ex));
+  *out = &res.first->second;
+  return AFQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batch** out) {
+  if (!out || !ctxs || nsys < 1) return fail(AFQMC_EINVAL, "batch: need nsys >= 1 contexts");
+  *out = nullptr;
+  for (int i = 0; i < nsys; ++i) {
+    if (!ctxs[i]) return fail(AFQMC_EINVAL, "batch: context %d is NULL", i);
+    if (ctxs[i]->host_step != ctxs[0]->host_step) return fail(AFQMC_EINVAL, "batch: contexts must be at the same step");
+    if (ctxs[i]->cv.enabled) return fail(AFQMC_EINVAL, "batch: the control-variate form is not batched");
+  }
+  afqmc_batch* b = new afqmc_batch();
+  b->sys.assign(ctxs, ctxs + nsys);
+  *out = b;
+  return AFQMC_OK;
+}
+
+void afqmc_batch_destroy(afqmc_batch* b) { delete b; }
+
+afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
+                             int32_t comb_every, double* energies, int32_t* nmeas) {
+  if (!b) return fail(AFQMC_EINVAL, "batch is NULL");
+  if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
+  afqmc_ctx* c0 = b->sys[0];
+  cudaStream_t s = c0->stream;
+  const int nsys = (int)b->sys.size();
+  int total = 0;
+  for (int k = 0; k < nsteps; ++k)
+    if (energy_every > 0 && (c0->host_step + k) % (unsigned long long)energy_every == 0) ++total;
+  int used = 0, done = 0;
+  auto flush = [&]() -> afqmc_status {
+    for (int i = 0; i < nsys && energies && used > 0; ++i)
+      CU(cudaMemcpyAsync(energies + ((size_t)i * total + done) * 4, b->sys[i]->at<double>(b->sys[i]->L.hist),
+                         (size_t)used * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    done += used;
+    used = 0;
+    for (afqmc_ctx* c : b->sys) CU(cudaMemsetAsync(c->base + c->L.slot, 0, sizeof(int), s));
+    return AFQMC_OK;
+  };
+  for (afqmc_ctx* c : b->sys) {
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemsetAsync(c->base + c->L.slot, 0, sizeof(int), s));
+  }
+  afqmc_status st;
+  for (int k = 0; k < nsteps; ++k) {
+    const unsigned long long hs = c0->host_step;
+    const bool energy = energy_every > 0 && hs % (unsigned long long)energy_every == 0;
+    const bool qr = reortho_every > 0 && (hs + 1) % (unsigned long long)reortho_every == 0;
+    const bool comb = comb_every > 0 && (hs + 1) % (unsigned long long)comb_every == 0;
+    const bool refresh = !c0->theta_fresh;
+    const int key = (energy ? 1 : 0) | (refresh ? 2 : 0) | (qr ? 4 : 0) | (comb ? 8 : 0);
+    if (energy && used == kHistory - 1 && (st = flush()) != AFQMC_OK) return st;
+    afqmc_batch::Exec* ex = nullptr;
+    if ((st = batch_exec(b, key, energy, qr, comb, &ex)) != AFQMC_OK) return st;
+    CU(cudaGraphLaunch(ex->exec, s));
+    for (int i = 0; i < nsys; ++i) {
+      afqmc_ctx* c = b->sys[i];
+      c->launches += ex->nk[i];
+      c->theta_fresh = ex->end_theta[i];
+      c->vbias_fresh = ex->end_vbias[i];
+      c->host_step++;
+    }
+    if (energy) ++used;
+  }
+  if ((st = flush()) != AFQMC_OK) return st;
+  if (nmeas) *nmeas = total;
+  for (afqmc_ctx* c : b->sys)
+    if ((st = read_status(c)) != AFQMC_OK) return st;
+  return AFQMC_OK;
+}
+
+}  // extern "C"

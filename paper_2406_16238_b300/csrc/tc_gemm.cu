@@ -664,6 +664,26 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   return cur;
 }
 
+int set_exchange_groups(TcState* st, char* tcbuf, int groups) {
+  int used = 0;
+  for (int b = 0; b < st->nblk; ++b) {
+    BlockMaps& bm = st->blk[b];
+    if (bm.n == 0) continue;
+    const int wpt0 = 256 / (2 * bm.n);
+    int g = exchange_groups(bm.n, wpt0);
+    if (groups > 0) g = std::max(1, std::min(g, groups));
+    bm.groups = g;
+    bm.wpt = wpt0 / g * g;
+    bm.bn = (bm.wpt * 2 * bm.n + 15) / 16 * 16;
+    bm.n_tiles = (st->W + bm.wpt - 1) / bm.wpt;
+    if (tcbuf)
+      make_map(&bm.map_th, tcbuf + bm.off_th, (unsigned long long)st->W * 2 * bm.n,
+               (unsigned long long)st->nseg * st->kst, (unsigned)bm.bn);
+    if (!used) used = g;
+  }
+  return used;
+}
+
 afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* chol64, const double* lrot64,
                      unsigned long long* launches, char* err, size_t errlen) {
   if (!encode_fn()) {

@@ -41,6 +41,10 @@ struct TcState {
 // Fills the geometry of st (no device work) and returns the bytes of the tc buffer.
 size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk);
 
+// Caps the exchange epilogue warpgroups at `groups` (0: largest that fits) and re-derives the walker
+// tiling and the Theta tensor map; returns the groups in use for block 0.
+int set_exchange_groups(TcState* st, char* tcbuf, int groups);
+
 // One-time bf16 copies of Ltilde (from binary64 [X][ncol][N]) and of L^T (from binary64 [X][N][N]),
 // and the TMA descriptors over the tc buffer.
 afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* chol64, const double* lrot64,

@@ -167,3 +167,18 @@ def random_walkers(rng, norb, ncols, nwalkers, spread=0.3, psiT=None):
     base = psiT if psiT is not None else rng.standard_normal((norb, ncols))
     noise = rng.standard_normal((nwalkers, norb, ncols)) + 1j * rng.standard_normal((nwalkers, norb, ncols))
     return np.ascontiguousarray(base[None, :, :] + spread * noise)
+
+
+def config_batched(nsys=32, seed_offset=4, nmin=50, nmax=300):
+    """Uneven independent systems: N ~ U[nmin, nmax] (seeded), n = N // 6 per spin, naux = 4N,
+    tau = naux / 10, RHF trial from the core guess (the lowest eigenvectors of h1e), L
+    Frobenius-normalised only (no Gram-Schmidt, to keep generation fast at N = 300)."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    sizes = rng.integers(nmin, nmax + 1, size=nsys)
+    probs = []
+    for i, n in enumerate(sizes):
+        n = int(n)
+        nocc = max(1, n // 6)
+        probs.append(make_problem(n, nocc, nocc, 4 * n, 0.4 * n, BASE_SEED + 1000 + i, orthogonalise=False,
+                                  scf_iterations=0, name=f"sys{i}_N{n}"))
+    return probs
