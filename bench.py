@@ -145,17 +145,48 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(prec):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, if the kernel is unchanged."""
+def traffic_from_profiles(prec, stage):
+    """DRAM bytes per launch of a stage's main kernel from the committed ncu summary, if the source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         data = json.load(f)
-    ent = data.get(prec)
+    ent = data.get(f"{prec}:{stage}")
     if not ent or ent.get("source_hash") != source_hash():
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+def stage_rooflines(prec, norb, ncol, naux, nw, stages):
+    """Algorithmic work per launch of the main stages against the peak of the unit that bounds them."""
+    peaks, src = measured_peaks()
+    tensor = prec in ("bf16", "bf16x3")
+    tpeak = peaks["bf16_tflops_sustained"] * (1.0 if prec == "bf16" else 1.0 / 3.0)
+    tnote = f"bf16 sustained ({src})" + ("" if prec == "bf16" else " / 3 products")
+    alu = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+    anote = "nominal FP64 (recipe table)" if prec == "fp64" else "FP32 CUDA cores: 148 SM x 128 x 2 x 2.032 GHz"
+    fl = step_flops_per_walker(norb, ncol, naux)
+    n = ncol
+    gj_fp64 = 12 * n ** 3                               # Gauss-Jordan on [A | I] (binary64)
+    work = {
+        "exchange": (fl["exchange"] * nw, "tensor" if tensor else "alu", tpeak if tensor else alu,
+                     tnote if tensor else anote),
+        "propagate": (fl["propagate"] * nw, "alu", alu, anote),
+        "vhs": (fl["vhs"] * nw, "tensor" if tensor else "alu", tpeak if tensor else alu, tnote if tensor else anote),
+        "overlap": (gj_fp64 * nw, "alu", FP64_PEAK_TFLOPS, "nominal FP64 (recipe table); binary64 inverse work only"),
+    }
+    out = {}
+    for k, (flops, bound, peak, note) in work.items():
+        ms, cnt = stages.get(k, (0.0, 0))
+        if not cnt:
+            continue
+        per = ms / cnt
+        ach = flops / (per / 1e3) / 1e12
+        out[k] = {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                  "peak_source": note, "algorithmic_flops_per_launch": flops, "ms_per_launch": per,
+                  "launches_per_step": cnt / max(1, stages.get("_steps", (1, 1))[0]), "traffic": None}
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -253,6 +284,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
     launches = ctx.launch_count() - l0
     stages = ctx.stage_times()
+    stages["_steps"] = (args.steps, 1)
     ctx.profile(False)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -263,7 +295,22 @@ def run_ours(args):
     if args.skip_extras:
         ctx.close()
         return None if rank != 0 else {"value": value, "ms_per_step": total_ms / args.steps,
-                                       "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()}}
+                                       "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()
+                                                              if not k.startswith("_")}}
+    fp64_form = None
+    if rank == 0 and args.prec != "fp64":   # the plain FP64 form on the same workload (context for the ratio)
+        c64 = pkg.Afqmc(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, nwalkers=nw,
+                        dt=WORKLOAD["dt"], seed=seed, prec="fp64", device=dev, stream=stream)
+        c64.run(3, 1, 5, 10)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        c64.run(5, 1, 5, 10)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms64 = ev0.elapsed_time(ev1) / 5
+        fp64_form = {"value": nw / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": 5}
+        c64.close()
+        del c64
     # end to end through the public API from pinned host buffers: create (H2D of h1e, L, psiT)
     # + the same steps with the energy sums read back to the host every step
     h1e_p = torch.from_numpy(prob.h1e).pin_memory().numpy()
@@ -293,20 +340,12 @@ def run_ours(args):
 
     if rank != 0:
         return None
-    peaks, peak_src = measured_peaks()
     fl = step_flops_per_walker(prob.norb, ncol, prob.naux)
-    exch_ms, exch_n = stages["exchange"]
-    exch_flops_launch = exchange_flops_per_walker(prob.norb, ncol, prob.naux) * nw
-    achieved = exch_flops_launch / (exch_ms / exch_n / 1e3) / 1e12 if exch_n else None
-    if args.prec == "fp64":
-        bound, peak, unit, peak_note = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "nominal FP64 (recipe table)"
-    elif args.prec == "fp32":
-        bound, peak, unit, peak_note = "alu", FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 CUDA-core: 148 SM x 128 x 2 x 2.032 GHz"
-    else:
-        scale = 1.0 if args.prec == "bf16" else 1.0 / 3.0
-        bound, peak, unit = "tensor", peaks["bf16_tflops_sustained"] * scale, "TFLOP/s"
-        peak_note = f"bf16 sustained ({peak_src})" + (" / 3 products" if scale < 1 else "")
-    traffic = traffic_from_profiles(args.prec)
+    rooflines = stage_rooflines(args.prec, prob.norb, ncol, prob.naux, nw, stages)
+    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_launch"] * rooflines[k]["launches_per_step"])
+    roof = dict(rooflines[dominant])
+    roof["kernel"] = dominant
+    roof["traffic"] = traffic_from_profiles(args.prec, dominant)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -318,12 +357,11 @@ def run_ours(args):
                           f"inputs larger than L2 (workspace {ws_bytes / 2**20:.0f} MiB > 2 x L2)"),
                    "max_abs_dE_vs_fp64_Ha_10steps": acc,
                    "meets_0.1mHa": None if acc is None else bool(acc <= 1e-4)},
-        "roofline": {"kernel": "exchange (T = Ltilde Theta, fused Tr T and Tr T T)", "bound": bound,
-                     "achieved": achieved, "peak": peak, "unit": unit, "peak_source": peak_note,
-                     "frac": achieved / peak if achieved else None, "traffic": traffic,
-                     "algorithmic_flops_per_launch": exch_flops_launch},
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "roofline": roof,
+        "rooflines": rooflines,
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if not k.startswith("_")},
         "step_flops_per_walker": fl,
+        "fp64_form": fp64_form,
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "e2e": {"value": world * nw * args.steps / e2e_s, "unit": UNIT,
@@ -333,6 +371,93 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, seed, args.cpu_budget)
     return line
+
+
+def run_batched(args):
+    """32 uneven systems (N ~ U[50, 300], n = N/6, naux = 4N), 256 walkers each, split-bf16 GEMMs
+    with fp32 accumulation, autotuned per system, one CUDA graph launch per step."""
+    import torch
+    import paper_2406_16238_b300 as pkg
+    from paper_2406_16238_b300._lib import Batch
+    from synthetic_inputs import config_batched
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    probs = config_batched(nsys=args.nsys)
+    ctxs, tunings, sizes = [], [], []
+    for i, p in enumerate(probs):
+        c = pkg.Afqmc(p.h1e, p.chol, p.ecore, p.nalpha, p.nbeta, p.psiT, nwalkers=256, dt=WORKLOAD["dt"],
+                      seed=240616238 + i, prec=args.prec, device=dev, stream=stream)
+        tunings.append(c.autotune(steps=2))
+        ctxs.append(c)
+        sizes.append(p.norb)
+        p.chol = None
+    b = Batch(ctxs)
+    b.run(args.warmup, 1, 5, 10)
+    torch.cuda.synchronize(dev)
+    l0 = sum(c.launch_count() for c in ctxs)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        e = b.run(args.steps, 1, 5, 10)
+        ev1.record(stream)
+        ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = sum(c.launch_count() for c in ctxs) - l0
+    total_ws = len(ctxs) * 256 * args.steps
+    return {"metric": METRIC, "value": total_ws / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
+            "config": {"workload": f"batched uneven systems: {len(ctxs)} x (N in [50,300], n=N/6, naux=4N, W=256), "
+                                   "one CUDA graph launch per step", "form": args.prec, "norb": sizes,
+                       "tuning": tunings, "l2": "inputs larger than L2"},
+            "energies_finite": bool(np.isfinite(e).all()), "clocks": clk.summary(), "gpu_launches": int(launches)}
+
+
+def run_cv(args):
+    """N=300, 25a+25b, naux=1500, 2048 walkers: learned control variate vs the plain form."""
+    import torch
+    import paper_2406_16238_b300 as pkg
+    from paper_2406_16238_b300.analysis import energy_series, error_bar
+    from synthetic_inputs import config_cv
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    prob = config_cv()
+    nw = 2048
+    ctx = pkg.Afqmc(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, nwalkers=nw,
+                    dt=WORKLOAD["dt"], seed=240616243, prec=args.prec, device=dev, stream=stream)
+    ctx.cv_attach(capacity=args.cv_pairs, batch=1024, sample_frac=0.125, seed=7)
+    t0 = time.perf_counter()
+    npairs = ctx.cv_collect((args.cv_pairs + nw - 1) // nw, 5, 10)
+    losses = ctx.cv_train(args.cv_epochs, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    psi, logo, w, step = ctx.get_walkers()
+    out = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for form in ("plain", "cv"):
+        ctx.set_walkers(psi, w, step)
+        ctx.cv_enable(form == "cv")
+        ctx.run(args.warmup, 1, 5, 10)
+        ev0.record(stream)
+        sums = ctx.run(args.steps, 1, 5, 10)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        e = energy_series(sums)
+        eb = error_bar(e[len(e) // 5:])
+        t = ms / 1e3
+        out[form] = {"walker_steps_per_s": nw * args.steps / t, "ms_per_step": ms / args.steps,
+                     "mean_energy": float(e[len(e) // 5:].mean()), "error_bar": eb,
+                     "error_bar_per_second": 1.0 / (eb * eb * t) if eb > 0 else None}
+    ctx.cv_enable(False)
+    return {"metric": METRIC, "value": out["cv"]["walker_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["cv"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
+            "data": "synthetic",
+            "config": {"workload": "learned control variate: N=300 25a+25b naux=1500 W=2048 dt=0.005, exact exchange "
+                                   "on 1/8 of the walkers per step", "form": args.prec, "training_pairs": npairs,
+                       "epochs": args.cv_epochs, "final_loss": float(losses[-1]) if len(losses) else None,
+                       "collect_and_train_s": t_train},
+            "forms": out}
 
 
 def run_reference(args):
@@ -382,12 +507,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-walkers", type=int, default=8)
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "cv"])
+    ap.add_argument("--nsys", type=int, default=32)
+    ap.add_argument("--cv-pairs", type=int, default=100000)
+    ap.add_argument("--cv-epochs", type=int, default=30)
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the steps only (no accuracy check, e2e or CPU baseline), e.g. under ncu")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "batched":
+        line = run_batched(args)
+    elif args.workload == "cv":
+        line = run_cv(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 
