@@ -235,6 +235,7 @@ struct afqmc_ctx {
   CvState cv;
   int tile_cap = 4;          // largest CUDA-core GEMM register tile (4: 64-wide block tiles, 2: 32, 1: 16)
   int prop_generic = 0;      // 1: batched GEMMs for the propagation even where the fused kernel fits
+  int prop_tile = 0;         // fused propagation register tile: 0: 4 rows x 2 columns, 1: 8 x 2, 2: 4 x 4
   // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
   bool graphs_on = true;
   cudaStream_t cap_stream = nullptr;
@@ -444,7 +445,9 @@ afqmc_status set_smem_limits(const Dims& d) {
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_gj<R>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_exchange<R>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_chol<R>))) != AFQMC_OK) return st_;
-  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<4, 2>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<8, 2>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<4, 4>))) != AFQMC_OK) return st_;
   return AFQMC_OK;
 }
 
@@ -545,9 +548,13 @@ afqmc_status step_impl(afqmc_ctx* c) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = ((d.N + 3) / 4) * ((d.ncol + 1) / 2);
+    const int tm = c->prop_tile == 1 ? 8 : 4, tcw = c->prop_tile == 2 ? 4 : 2;
+    const int tiles = ((d.N + tm - 1) / tm) * (pa.ldc / tcw);
     const int threads = std::min(512, std::max(64, (tiles + 31) / 32 * 32));
-    k_propagate_smem<<<std::min(d.W, sms), threads, prop_smem(d), c->stream>>>(pa);
+    const int grid = std::min(d.W, sms);
+    if (c->prop_tile == 1) k_propagate_smem<8, 2><<<grid, threads, prop_smem(d), c->stream>>>(pa);
+    else if (c->prop_tile == 2) k_propagate_smem<4, 4><<<grid, threads, prop_smem(d), c->stream>>>(pa);
+    else k_propagate_smem<4, 2><<<grid, threads, prop_smem(d), c->stream>>>(pa);
     delete tp;
     CHECK_LAUNCH(c);
     if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
@@ -1313,6 +1320,7 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t) {
   ctx->drop_graphs();
   ctx->tile_cap = t->tile_cap;
   ctx->prop_generic = t->prop_generic ? 1 : 0;
+  ctx->prop_tile = (t->prop_tile >= 0 && t->prop_tile <= 2) ? t->prop_tile : 0;
   if (ctx->d.tensor()) tc::set_exchange_groups(&ctx->tcs, ctx->at<char>(ctx->L.tc), t->exch_groups);
   return AFQMC_OK;
 }
@@ -1347,8 +1355,14 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
   if (d.tensor()) groups = {1, 2, 4};
   for (int tc_cap : {4, 2})
     for (int pg : {0, 1}) {
-      if (pg == 0 && !fused_ok && tc_cap == 2) continue;   // identical to pg = 1
-      for (int g : groups) cands.push_back(afqmc_tuning{tc_cap, fused_ok ? pg : 1, g, 0.f});
+      if (pg == 0 && !fused_ok) continue;
+      for (int g : groups) {
+        if (pg == 0) {
+          for (int pt : {0, 1, 2}) cands.push_back(afqmc_tuning{tc_cap, 0, g, pt, 0.f});
+        } else {
+          cands.push_back(afqmc_tuning{tc_cap, 1, g, 0, 0.f});
+        }
+      }
     }
   const bool graphs_was = ctx->graphs_on, prof_was = ctx->prof;
   ctx->graphs_on = false;
@@ -1356,7 +1370,7 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  afqmc_tuning best{4, 0, 0, 1e30f};
+  afqmc_tuning best{4, 0, 0, 0, 1e30f};
   double* scratch = ctx->at<double>(ctx->L.hist) + 4 * (kHistory - 1);
   for (auto& cnd : cands) {
     if ((st = afqmc_set_tuning(ctx, &cnd)) != AFQMC_OK) break;

@@ -491,39 +491,50 @@ struct PropArgs {
 };
 
 __host__ __device__ inline size_t prop_smem_floats(int N, int ncol, int* ldv_out, int* ldc_out) {
+  // V rows padded to a multiple of 4 (float4 loads; the last float4 of an 8-row tile may read 4
+  // floats past a row, which stay inside the next shared-memory array and feed rows >= N only)
   const int ldv = (N + 3) / 4 * 4;
-  const int ldc = (ncol + 1) / 2 * 2;
+  const int ldc = (ncol + 3) / 4 * 4;   // columns padded for 4-column register tiles
   if (ldv_out) *ldv_out = ldv;
   if (ldc_out) *ldc_out = ldc;
-  return (size_t)3 * N * ldv + (size_t)6 * N * ldc;
+  return (size_t)3 * N * ldv + (size_t)6 * N * ldc + 8;
 }
 
-template <bool REALV>
+// Out = scale * V T (V real if REALV); acc_mode 0: none, 1: Acc = Out, 2: Acc += Out.
+// Thread tile: TM rows (TM/4 float4 of V per part) x TC columns (TC/2 float2 of T per part).
+template <bool REALV, int TM, int TC>
 __device__ __forceinline__ void prop_product(int N, int ldv, int ldc, int ncol, const float* Vr, const float* Vi,
                                              const float* Tr, const float* Ti, float* Or, float* Oi, float* Ar,
                                              float* Ai, float scale, int acc_mode) {
-  // Out = scale * V T (V real if REALV); acc_mode 0: none, 1: Acc = Out, 2: Acc += Out.
-  // Thread tile: 4 rows (one float4 of V per part) x 2 columns (one float2 of T per part).
-  const int ptiles = (N + 3) / 4, ctiles = ldc / 2;
+  const int ptiles = (N + TM - 1) / TM, ctiles = ldc / TC;
   for (int tile = threadIdx.x; tile < ptiles * ctiles; tile += blockDim.x) {
-    const int p0 = 4 * (tile / ctiles), c0 = 2 * (tile % ctiles);
-    float accr[4][2], acci[4][2];
+    const int p0 = TM * (tile / ctiles), c0 = TC * (tile % ctiles);
+    float accr[TM][TC], acci[TM][TC];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) accr[i][j] = acci[i][j] = 0.f;
+      for (int j = 0; j < TC; ++j) accr[i][j] = acci[i][j] = 0.f;
     for (int q = 0; q < N; ++q) {
-      const float4 vr = *reinterpret_cast<const float4*>(Vr + (size_t)q * ldv + p0);
-      float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!REALV) vi = *reinterpret_cast<const float4*>(Vi + (size_t)q * ldv + p0);
-      const float2 tr = *reinterpret_cast<const float2*>(Tr + (size_t)q * ldc + c0);
-      const float2 ti = *reinterpret_cast<const float2*>(Ti + (size_t)q * ldc + c0);
-      const float br[2] = {tr.x, tr.y}, bi[2] = {ti.x, ti.y};
-      const float ar[4] = {vr.x, vr.y, vr.z, vr.w}, ai[4] = {vi.x, vi.y, vi.z, vi.w};
+      float ar[TM], ai[TM], br[TC], bi[TC];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; i += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(Vr + (size_t)q * ldv + p0 + i);
+        ar[i] = v.x; ar[i + 1] = v.y; ar[i + 2] = v.z; ar[i + 3] = v.w;
+        if (!REALV) {
+          const float4 u = *reinterpret_cast<const float4*>(Vi + (size_t)q * ldv + p0 + i);
+          ai[i] = u.x; ai[i + 1] = u.y; ai[i + 2] = u.z; ai[i + 3] = u.w;
+        }
+      }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < TC; j += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(Tr + (size_t)q * ldc + c0 + j);
+        const float2 u = *reinterpret_cast<const float2*>(Ti + (size_t)q * ldc + c0 + j);
+        br[j] = t.x; br[j + 1] = t.y; bi[j] = u.x; bi[j + 1] = u.y;
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TC; ++j) {
           accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
           acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
           if (!REALV) {
@@ -533,11 +544,11 @@ __device__ __forceinline__ void prop_product(int N, int ldv, int ldc, int ncol, 
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
       const int p = p0 + i;
       if (p >= N) continue;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < TC; ++j) {
         const int c = c0 + j;
         if (c >= ncol) continue;
         const float orv = scale * accr[i][j], oiv = scale * acci[i][j];
@@ -580,6 +591,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Persistent: each CTA loads E_h once and loops over walkers; with planar VHS and N % 4 == 0
 // the walker's VHS (re and im planes) arrives by two bulk copies, the next walker's copy
 // being issued as soon as the Taylor terms of the current one are done.
+template <int TM, int TC>
 __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
   extern __shared__ __align__(16) float sm_pr[];
   const int N = a.N, ldv = a.ldv, ldc = a.ldc;
@@ -595,7 +607,7 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
   float* Ai = Ar + (size_t)N * ldc;
   __shared__ __align__(8) uint64_t vbar;
   __shared__ int go_s;
-  const bool bulk = a.planar && ldv == N && ((NN * 4) % 16 == 0);
+  const bool bulk = a.planar && ldv == N && ((NN * 4) % 16 == 0);   // rows are contiguous in smem
   for (size_t i = threadIdx.x; i < (size_t)N * ldv; i += blockDim.x) {
     const int q = (int)(i / ldv), p = (int)(i % ldv);
     E[i] = p < N ? a.eh[(size_t)q * N + p] : 0.f;
@@ -662,11 +674,11 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
     __syncthreads();
     if (!go_s) break;
     phase ^= 1u;
-    prop_product<true>(N, ldv, ldc, a.ncol, E, nullptr, T0r, T0i, T1r, T1i, Ar, Ai, 1.f, 1);
+    prop_product<true, TM, TC>(N, ldv, ldc, a.ncol, E, nullptr, T0r, T0i, T1r, T1i, Ar, Ai, 1.f, 1);
     __syncthreads();
     float *tin_r = T1r, *tin_i = T1i, *tout_r = T0r, *tout_i = T0i;
     for (int k = 1; k <= a.order; ++k) {
-      prop_product<false>(N, ldv, ldc, a.ncol, Vr, Vi, tin_r, tin_i, k < a.order ? tout_r : nullptr,
+      prop_product<false, TM, TC>(N, ldv, ldc, a.ncol, Vr, Vi, tin_r, tin_i, k < a.order ? tout_r : nullptr,
                           k < a.order ? tout_i : nullptr, Ar, Ai, 1.f / (float)k, 2);
       __syncthreads();
       float* t = tin_r; tin_r = tout_r; tout_r = t;
@@ -674,7 +686,7 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
     }
     const int nxt = next_live(wk + gridDim.x);
     if (bulk && threadIdx.x == 0 && nxt < a.W) issue(nxt);   // VHS buffer is free from here on
-    prop_product<true>(N, ldv, ldc, a.ncol, E, nullptr, Ar, Ai, tout_r, tout_i, nullptr, nullptr, 1.f, 0);
+    prop_product<true, TM, TC>(N, ldv, ldc, a.ncol, E, nullptr, Ar, Ai, tout_r, tout_i, nullptr, nullptr, 1.f, 0);
     __syncthreads();
     for (int i = threadIdx.x; i < N * a.ncol; i += blockDim.x) {
       const int p = i / a.ncol, c = i % a.ncol;
