@@ -201,13 +201,16 @@ afqmc_status afqmc_cv_eval(afqmc_ctx* ctx, const float* x, const float* y, int32
 afqmc_status afqmc_cv_info(afqmc_ctx* ctx, int32_t* dim, uint64_t* nparams, int32_t* npairs, int32_t* nsample);
 
 /* Project autotuner: times `steps` propagation + energy steps of every candidate setting
- * (CUDA-core GEMM block tile 64 / 32, fused or batched-GEMM propagation and its register tile,
+ * (CUDA-core GEMM block tile 64 / 32, tensor-core, fused CUDA-core or batched-GEMM propagation and
+ * the fused kernel's register tile,
  * 1 / 2 / 4 tensor-core epilogue warpgroups) on the context's own walkers, restores the walkers,
  * keeps the fastest.
  * chosen (may be NULL) receives it; afqmc_set_tuning applies a setting directly. */
 typedef struct {
   int32_t tile_cap;       /* 4: 64-wide CUDA-core GEMM tiles allowed, 2: at most 32, 1: 16 */
-  int32_t prop_generic;   /* 1: batched GEMMs for the propagation instead of the fused kernel */
+  int32_t prop_path;      /* propagation: 0 tensor cores in the BF16 forms (N <= 128), else the fused
+                             CUDA-core kernel where it fits, else batched GEMMs; 1 batched GEMMs;
+                             2 fused CUDA-core kernel */
   int32_t exch_groups;    /* tensor-core exchange epilogue warpgroups (0: largest that fits) */
   int32_t prop_tile;      /* fused propagation register tile: 0: 4 rows x 2 columns, 1: 8 x 2, 2: 4 x 4 */
   float ms_per_step;      /* measured by afqmc_autotune */

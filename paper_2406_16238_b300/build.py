@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libafqmc.so")
-SOURCES = ["afqmc.cu", "tc_gemm.cu"]
+SOURCES = ["afqmc.cu", "tc_gemm.cu", "tc_prop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

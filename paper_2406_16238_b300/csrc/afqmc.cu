@@ -234,7 +234,8 @@ struct afqmc_ctx {
   tc::TcState tcs;
   CvState cv;
   int tile_cap = 4;          // largest CUDA-core GEMM register tile (4: 64-wide block tiles, 2: 32, 1: 16)
-  int prop_generic = 0;      // 1: batched GEMMs for the propagation even where the fused kernel fits
+  int prop_path = 0;         // 0: tensor cores (BF16 forms) else fused CUDA-core kernel where they fit,
+                             // 1: batched GEMMs, 2: fused CUDA-core kernel
   int prop_tile = 0;         // fused propagation register tile: 0: 4 rows x 2 columns, 1: 8 x 2, 2: 4 x 4
   // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
   bool graphs_on = true;
@@ -386,6 +387,8 @@ size_t prop_smem(const Dims& d) { return prop_smem_floats(d.N, d.ncol, nullptr, 
 
 bool use_fused_propagation(const Dims& d) { return d.prec != AFQMC_PREC_FP64 && prop_smem(d) <= 227 * 1024; }
 
+bool use_tc_propagation(const afqmc_ctx* c) { return c->d.tensor() && c->tcs.pg.ok && c->prop_path == 0; }
+
 template <typename R>
 afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
   StageTimer timer(c, AFQMC_STAGE_OVERLAP);
@@ -519,7 +522,12 @@ afqmc_status step_impl(afqmc_ctx* c) {
   const long long NN = (long long)d.N * d.N, Nc = (long long)d.N * d.ncol;
   // VHS[w][pq] = sum_g coef[w][g] L[g][pq]
   StageTimer* tv = new StageTimer(c, AFQMC_STAGE_VHS);
-  if (d.tensor()) {   // planar fp32 output: VHS_w = vhs[w][0][:] + i vhs[w][1][:]
+  const bool tc_prop = use_tc_propagation(c);
+  if (tc_prop) {   // bf16 hi/lo planes for the tensor-core propagation
+    if ((st = tc::vhs_planes(&c->tcs, c->stream, c->at<char>(c->L.tc), c->at<float2>(c->L.coef),
+                             c->at<int>(c->L.status), &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
+      return st;
+  } else if (d.tensor()) {   // planar fp32 output: VHS_w = vhs[w][0][:] + i vhs[w][1][:]
     if ((st = tc::vhs(&c->tcs, c->stream, c->at<char>(c->L.tc), c->at<float2>(c->L.coef), c->at<float>(c->L.vhs),
                       c->at<int>(c->L.status), &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
       return st;
@@ -534,7 +542,18 @@ afqmc_status step_impl(afqmc_ctx* c) {
   // psi <- E_h Taylor(VHS) E_h psi   (tA = accumulator, tB/tC = Taylor terms)
   const double* skip = c->at<double>(c->L.w);
   StageTimer* tp = new StageTimer(c, AFQMC_STAGE_PROPAGATE);
-  if (use_fused_propagation(d) && !c->prop_generic) {
+  if (tc_prop) {
+    if ((st = tc::propagate(&c->tcs, c->stream, c->at<char>(c->L.tc), c->taylor, c->at<float2>(c->L.psi), skip,
+                            c->at<int>(c->L.status), &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
+      return st;
+    delete tp;
+    if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
+    c->theta_fresh = true;
+    c->vbias_fresh = false;
+    c->host_step++;
+    return AFQMC_OK;
+  }
+  if (use_fused_propagation(d) && c->prop_path != 1) {
     PropArgs pa{};
     pa.N = d.N; pa.ncol = d.ncol; pa.order = c->taylor;
     prop_smem_floats(d.N, d.ncol, &pa.ldv, &pa.ldc);
@@ -770,6 +789,15 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
     if ((st = tc::prepare(&c->tcs, c->stream, c->at<char>(c->L.tc), chol64, lrot64, &c->launches, g_err,
                           sizeof(g_err))) != AFQMC_OK)
       return st;
+    if (c->tcs.pg.ok) {   // F = E_h - I in binary64 for the tensor-core propagation
+      std::vector<double> f(eh);
+      for (int p = 0; p < N; ++p) f[(size_t)p * N + p] -= 1.0;
+      CU(cudaMemcpyAsync(prod, f.data(), f.size() * 8, cudaMemcpyHostToDevice, c->stream));
+      if ((st = tc::prepare_prop(&c->tcs, c->stream, c->at<char>(c->L.tc), prod, &c->launches, g_err,
+                                 sizeof(g_err))) != AFQMC_OK)
+        return st;
+      CU(cudaStreamSynchronize(c->stream));   // f goes out of scope
+    }
   }
   CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.step, 0, 256, c->stream));
@@ -1319,7 +1347,7 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t) {
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->drop_graphs();
   ctx->tile_cap = t->tile_cap;
-  ctx->prop_generic = t->prop_generic ? 1 : 0;
+  ctx->prop_path = (t->prop_path >= 0 && t->prop_path <= 2) ? t->prop_path : 0;
   ctx->prop_tile = (t->prop_tile >= 0 && t->prop_tile <= 2) ? t->prop_tile : 0;
   if (ctx->d.tensor()) tc::set_exchange_groups(&ctx->tcs, ctx->at<char>(ctx->L.tc), t->exch_groups);
   return AFQMC_OK;
@@ -1350,19 +1378,15 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
     return AFQMC_OK;
   };
   std::vector<afqmc_tuning> cands;
-  const bool fused_ok = use_fused_propagation(d);
+  const bool fused_ok = use_fused_propagation(d), tc_ok = d.tensor() && ctx->tcs.pg.ok;
   std::vector<int> groups = {0};
   if (d.tensor()) groups = {1, 2, 4};
   for (int tc_cap : {4, 2})
-    for (int pg : {0, 1}) {
-      if (pg == 0 && !fused_ok) continue;
-      for (int g : groups) {
-        if (pg == 0) {
-          for (int pt : {0, 1, 2}) cands.push_back(afqmc_tuning{tc_cap, 0, g, pt, 0.f});
-        } else {
-          cands.push_back(afqmc_tuning{tc_cap, 1, g, 0, 0.f});
-        }
-      }
+    for (int g : groups) {
+      if (tc_ok) cands.push_back(afqmc_tuning{tc_cap, 0, g, 0, 0.f});
+      if (fused_ok)
+        for (int pt : {0, 1, 2}) cands.push_back(afqmc_tuning{tc_cap, 2, g, pt, 0.f});
+      cands.push_back(afqmc_tuning{tc_cap, 1, g, 0, 0.f});
     }
   const bool graphs_was = ctx->graphs_on, prof_was = ctx->prof;
   ctx->graphs_on = false;

@@ -20,15 +20,12 @@
 
 #include "common.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace afq {
 namespace tc {
 
-constexpr int kBM = 128;
-constexpr int kBK = 64;                          // bf16 elements per 128-byte swizzled row
 constexpr int kStageA = kBM * kBK * 2;           // 16 KiB
-constexpr unsigned long long kWaitNs = 2000000000ull;
-constexpr int kMaxSmem = 227 * 1024;
 
 struct Geom {
   int m_tiles, n_tiles, k_blocks;
@@ -51,138 +48,11 @@ struct Params {
   float* out;
   long long ldo;
   int out_rows, out_cols;
+  // bf16 plane epilogue
+  __nv_bfloat16* planes;
+  int npad;
 };
 
-// ----------------------------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait for the phase of `parity`; false on timeout or when another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (global_ns() - t0 > kWaitNs) return false;
-  }
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-          d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void named_bar(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// 32 lanes x 32-bit, N consecutive columns per thread.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-  uint32_t r[4];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld2_nowait(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr) : "memory");
-}
-__device__ __forceinline__ void tmem_ld1_nowait(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[0]) : "r"(taddr) : "memory");
-}
-__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld1(uint32_t taddr, float* v) {
-  uint32_t r;
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r)
-      : "r"(taddr)
-      : "memory");
-  v[0] = __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = 128, N = bn.
-__host__ __device__ __forceinline__ uint32_t idesc_bf16(int bn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // ----------------------------------------------------------------------------- epilogues
 // Exchange epilogue state of one warpgroup: [ok flags 2 x int (16 B)] [buf 128 x (2n+1) floats]
@@ -318,6 +188,33 @@ __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int g
   }
 }
 
+// Tile rows are pq = p N + q (M over N^2), columns are (w, part) = 2 w + part.  Each value is
+// split into hi = bf16(v), lo = bf16(v - hi) and written to the plane
+// [w][hi re, hi im, lo re, lo im][npad][128] at (p, q).  Consecutive lanes hold consecutive pq,
+// so every store instruction covers a contiguous run of q.
+__device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
+  const int pq = mt * kBM + r;
+  const bool live = pq < p.out_cols;
+  const int pp = live ? pq / p.n : 0, qq = live ? pq - pp * p.n : 0;
+  const int ncols = p.g.bn / p.g.epi_groups;
+  const int cbeg = group * ncols;
+  const size_t plane = (size_t)p.npad * 128;
+  float v[16];
+  for (int c = cbeg; c < cbeg + ncols; c += 16) {
+    tmem_ld16(tacc + (uint32_t)c, v);
+    if (!live) continue;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int col = nt * p.g.n_step + c + i;
+      if (col >= p.out_rows) break;
+      __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * 128 + qq;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
+      dst[0] = hi;
+      dst[2 * plane] = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- the kernel
 template <int EPI>
 __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
@@ -426,7 +323,8 @@ __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUte
       const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
       const int mt = t % g.m_tiles, nt = t / g.m_tiles;
       if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
-      else store_tile(p, mt, nt, tacc, group, r);
+      else if (EPI == 1) store_tile(p, mt, nt, tacc, group, r);
+      else store_planes(p, mt, nt, tacc, group, r);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -548,6 +446,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+}  // namespace
+
 bool make_map(CUtensorMap* m, const void* base, unsigned long long rows, unsigned long long kcols, unsigned box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -570,6 +470,8 @@ int num_sms() {
   }
   return sms;
 }
+
+namespace {
 
 int tmem_cols_for(int bn) {
   int c = 32;
@@ -661,6 +563,13 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   cur = align256(cur + (size_t)W * 2 * st->nseg * st->kx * 2);
   st->vhs_m_tiles = (2 * W + kBM - 1) / kBM;
   st->vhs_n_tiles = (N * N + 255) / 256;
+  st->pg = prop_geom(N, ncol);
+  if (st->pg.ok) {
+    st->off_vp = cur;
+    cur = align256(cur + (size_t)W * 4 * st->pg.npad * 128 * 2);
+    st->off_fp = cur;
+    cur = align256(cur + (size_t)2 * st->pg.npad * 128 * 2);
+  }
   return cur;
 }
 
@@ -712,6 +621,13 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS operands");
     return AFQMC_ECUDA;
   }
+  if (st->pg.ok &&
+      (!make_map(&st->map_lt_a, lt, (unsigned long long)st->N * st->N, (unsigned long long)st->nseg * st->kx, kBM) ||
+       !make_map(&st->map_coef_b, tcbuf + st->off_coef, (unsigned long long)st->W * 2,
+                 (unsigned long long)st->nseg * st->kx, 256))) {
+    snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS plane operands");
+    return AFQMC_ECUDA;
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(err, errlen, "tc prepare: %s", cudaGetErrorString(e));
@@ -719,7 +635,8 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
   }
   // reserve the kernels' shared memory now (not while a stream is being captured)
   if (cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+      cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
     snprintf(err, errlen, "tcgen05 GEMM: cannot reserve shared memory");
     return AFQMC_ECUDA;
   }
@@ -765,6 +682,37 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     first = false;
   }
   return AFQMC_OK;
+}
+
+afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, int* status,
+                        unsigned long long* launches, char* err, size_t errlen) {
+  if (!st->pg.ok) {
+    snprintf(err, errlen, "tensor-core propagation is not available for this problem");
+    return AFQMC_EINVAL;
+  }
+  k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
+                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
+  ++*launches;
+  Geom g{};
+  g.m_tiles = (st->N * st->N + kBM - 1) / kBM;
+  g.n_tiles = (2 * st->W + 255) / 256;
+  g.k_blocks = st->nseg * st->kx / kBK;
+  g.m_step = kBM;
+  g.n_step = 256;
+  g.bn = 256;
+  if (!finish_geom(&g, 16, 4)) {
+    snprintf(err, errlen, "tcgen05 VHS: shared memory plan failed");
+    return AFQMC_EINVAL;
+  }
+  Params p{};
+  p.g = g;
+  p.status = status;
+  p.n = st->N;
+  p.out_rows = 2 * st->W;
+  p.out_cols = st->N * st->N;
+  p.planes = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_vp);
+  p.npad = st->pg.npad;
+  return launch<2>(g, st->map_lt_a, st->map_coef_b, p, s, launches, err, errlen);
 }
 
 afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, float* out, int* status,

@@ -24,6 +24,23 @@ struct BlockMaps {
   CUtensorMap map_l, map_th;
 };
 
+// Geometry of the tensor-core propagation kernel (N <= 128).  Per walker and column chunk the
+// kernel forms t = E_h psi, the Taylor terms V t / k and E_h acc as D = A B^T with A = V or
+// F = E_h - I (rows p, K = q) and B = the current term, both split into bf16 hi + lo.
+// Shared memory, from a 1024-byte aligned base: V hi | V lo (4 swizzle atoms of npad rows:
+// Re V q < 64, Re V q >= 64, Im V q < 64, Im V q >= 64) | F hi | F lo (2 atoms) | B hi | B lo
+// (4 atoms of 2 cwp rows) | mbarriers.
+struct PropGeom {
+  int ok = 0;
+  int npad = 0;        // N rounded up to 8: rows of the V and F planes
+  int nk = 0;          // 16-wide k-steps per K half, ceil(N / 16)
+  int cw = 0, cwp = 0; // columns per chunk and its padding to a multiple of 8
+  int nch = 0;         // chunks per walker
+  int off_vlo = 0, off_fhi = 0, off_flo = 0, off_bhi = 0, off_blo = 0, off_bar = 0;
+  int smem = 0;        // dynamic shared memory bytes including the alignment slack
+};
+PropGeom prop_geom(int N, int ncol);
+
 struct TcState {
   int prec = 0, W = 0, N = 0, X = 0, ncol = 0, nblk = 0;
   int kst = 0;        // padded length of one K segment of the exchange operands (multiple of 64)
@@ -35,6 +52,10 @@ struct TcState {
   size_t off_lt = 0, off_coef = 0;
   int vhs_m_tiles = 0, vhs_n_tiles = 0;
   CUtensorMap map_lt, map_coef;
+  // tensor-core propagation
+  PropGeom pg;
+  size_t off_vp = 0, off_fp = 0;   // V planes [W][4][npad][128], F planes [2][npad][128] (bf16)
+  CUtensorMap map_vp, map_fp, map_lt_a, map_coef_b;
   bool ready = false;
 };
 
@@ -61,6 +82,19 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
 // VHS planar fp32: out[w][0][pq] + i out[w][1][pq] = sum_g coef[w][g] L^g_pq, coef complex64 [W][X].
 afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, float* out, int* status,
                  unsigned long long* launches, char* err, size_t errlen);
+
+// Tensor-core propagation: one-time F = E_h - I planes from binary64 f64 [N][N], zeroed V planes
+// and the tensor maps.  Only when st->pg.ok.
+afqmc_status prepare_prop(TcState* st, cudaStream_t s, char* tcbuf, const double* f64, unsigned long long* launches,
+                          char* err, size_t errlen);
+
+// VHS into the bf16 hi/lo planes read by the tensor-core propagation.
+afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, int* status,
+                        unsigned long long* launches, char* err, size_t errlen);
+
+// psi <- E_h sum_{k<=order} V^k / k! E_h psi for every walker with w != 0 (psi complex64 [W][N][ncol]).
+afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, float2* psi, const double* w,
+                       int* status, unsigned long long* launches, char* err, size_t errlen);
 
 }  // namespace tc
 }  // namespace afq
