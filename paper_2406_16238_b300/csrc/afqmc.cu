@@ -365,22 +365,29 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   return a;
 }
 
+bool overlap_stage(const Dims& d) {
+  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
+  const size_t sm = d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, true)
+                                              : overlap_lu_smem<float>(d.N, nmax, true);
+  return sm <= 100 * 1024;   // leaves room for two CTAs per SM
+}
 size_t overlap_smem(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return ((size_t)2 * nmax * nmax + nmax) * sizeof(double2) + (size_t)nmax * nmax * 2 * d.rsz();
+  const bool st = overlap_stage(d);
+  return d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, st) : overlap_lu_smem<float>(d.N, nmax, st);
 }
 
 size_t qr_smem_base(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return (size_t)2 * nmax * nmax * sizeof(double2) + ((size_t)nmax * nmax + 1) * 2 * d.rsz() + 16;
+  return (size_t)nmax * nmax * sizeof(double2) + ((size_t)nmax * nmax + 1) * 2 * d.rsz() + 16;
 }
 bool qr_stage_psi(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return qr_smem_base(d) + (size_t)nmax * d.N * sizeof(double2) <= 227 * 1024;
+  return qr_smem_base(d) + (size_t)nmax * qr_pitch(d.N) * sizeof(double2) <= 227 * 1024;
 }
 size_t qr_smem(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return qr_smem_base(d) + (qr_stage_psi(d) ? (size_t)nmax * d.N * sizeof(double2) : 0);
+  return qr_smem_base(d) + (qr_stage_psi(d) ? (size_t)nmax * qr_pitch(d.N) * sizeof(double2) : 0);
 }
 
 size_t prop_smem(const Dims& d) { return prop_smem_floats(d.N, d.ncol, nullptr, nullptr) * sizeof(float); }
@@ -393,7 +400,8 @@ template <typename R>
 afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
   StageTimer timer(c, AFQMC_STAGE_OVERLAP);
   const size_t sm = overlap_smem(c->d);
-  k_overlap_gj<R><<<c->d.W, 256, sm, c->stream>>>(overlap_args<R>(c, mode));
+  if (overlap_stage(c->d)) k_overlap_lu<R, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+  else k_overlap_lu<R, false><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
   CHECK_LAUNCH(c);
   return AFQMC_OK;
 }
@@ -445,7 +453,8 @@ afqmc_status set_smem_limits(const Dims& d) {
   // The attribute is per kernel, shared by every context in the process: allow the largest
   // dynamic size the device permits next to the kernel's static shared memory (each launch still
   // requests only its own size).
-  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_gj<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, true>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, false>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_exchange<R>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_chol<R>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<4, 2>))) != AFQMC_OK) return st_;

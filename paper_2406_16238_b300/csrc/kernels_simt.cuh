@@ -704,50 +704,72 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
 }
 
 // ============================================================================
-// Overlap, Theta and weight update with a Gauss-Jordan inverse (binary64) of
-// A^s = Phi^sT psi^s.  The product A is formed at the walkers' precision R with
-// an accumulator of the same type (binary64 in the FP64 form); pivoting,
-// determinant and inverse are binary64.  Same modes as k_overlap.
+// Overlap, Theta and weight update (Eqs. 13-16), one CTA per walker.  Per spin
+// block: A = Phi^T psi is formed at the walkers' precision R (an R accumulator;
+// binary64 in the FP64 form) and stored in binary64; LU with partial pivoting
+// P A = L U in binary64 gives log det A = sum log U_kk (+ i pi for an odd
+// number of row swaps); Theta = psi A^-1 = psi U^-1 L^-1 P is applied row by
+// row by forward (U) and backward (unit L) substitution at the walkers'
+// precision with the factors rounded once to R.  mode 0: log O only;
+// mode 1: also the weight update; mode 2: Theta and log det, no weights.
 // ============================================================================
+// STAGE: psi rows and the substitution vectors live in shared memory (Y); otherwise the
+// vectors live in Theta^T itself (row perm[k] holds y_k throughout, so no final permutation).
 template <typename R>
-__global__ void __launch_bounds__(256) k_overlap_gj(OverlapArgs<R> a) {
+__host__ __device__ inline size_t overlap_lu_smem(int N, int nmax, bool stage) {
+  const int lda = nmax + 1, ldy = nmax | 1;
+  return (size_t)nmax * lda * sizeof(double2) + (stage ? (size_t)N * ldy * 2 * sizeof(R) : 0) +
+         (size_t)nmax * nmax * 2 * sizeof(R) + (size_t)nmax * sizeof(int) + 16;
+}
+
+template <typename R, bool STAGE>
+__global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
   using R2 = cplx_t<R>;
-  extern __shared__ double2 sm_gj[];
-  __shared__ int piv_s, sing_s;
+  extern __shared__ __align__(16) unsigned char sm_lu[];
+  __shared__ int piv_s, sing_s, exp_s, swaps_s;
   __shared__ double2 inv_s, prod_s;   // pivot reciprocal; running product of pivots (scaled)
-  __shared__ int exp_s, swaps_s;
-  const int w = blockIdx.x, tid = threadIdx.x;
+  const int w = blockIdx.x, tid = threadIdx.x, N = a.N;
   if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
   if (a.mode == 1 && a.w[w] == 0.0) return;
   const int nmax = max(a.nb[0], a.nblk > 1 ? a.nb[1] : 0);
-  double2* M = sm_gj;                      // [n][2n]: [A | I] -> [I | A^-1]
-  double2* col = sm_gj + 2 * nmax * nmax;  // saved pivot column
-  R2* Ainv = reinterpret_cast<R2*>(col + nmax);   // A^-1 at the walkers' precision, [n][n]
+  const int lda = nmax + 1, ldy = nmax | 1;
+  double2* A = reinterpret_cast<double2*>(sm_lu);          // [n][lda] binary64, becomes L\U
+  R2* Y = reinterpret_cast<R2*>(A + (size_t)nmax * lda);   // [N][ldy]: psi rows, then Theta rows
+  R2* F = Y + (STAGE ? (size_t)N * ldy : 0);               // [n][n] factors at R (diagonal: 1 / U_kk)
+  int* perm = reinterpret_cast<int*>(F + (size_t)nmax * nmax);
   double ld_re = 0.0, ld_im = 0.0;
   bool singular = false;
   for (int s = 0; s < a.nblk; ++s) {
-    const int c0 = a.c0[s], n = a.nb[s], n2 = 2 * n;
+    const int c0 = a.c0[s], n = a.nb[s];
     if (n == 0) continue;
+    __syncthreads();
+    const R2* psw = a.psi + (size_t)w * N * a.ncol + c0;
+    if (STAGE)
+      for (int idx = tid; idx < N * n; idx += blockDim.x) {
+        const int p = idx / n, j = idx % n;
+        Y[(size_t)p * ldy + j] = psw[(size_t)p * a.ncol + j];
+      }
+    if (tid < n) perm[tid] = tid;
+    if (tid == 0) { sing_s = 0; prod_s = mk(1.0, 0.0); exp_s = 0; swaps_s = 0; }
+    __syncthreads();
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
       const int i = idx / n, j = idx % n;
       R accr = R(0), acci = R(0);
-      for (int p = 0; p < a.N; ++p) {
+      for (int p = 0; p < N; ++p) {
         const R ph = a.phi_r[(size_t)p * a.ncol + c0 + i];
-        const R2 ps = a.psi[((size_t)w * a.N + p) * a.ncol + c0 + j];
+        const R2 ps = STAGE ? Y[(size_t)p * ldy + j] : psw[(size_t)p * a.ncol + j];
         accr += ph * ps.x;
         acci += ph * ps.y;
       }
-      M[i * n2 + j] = mk((double)accr, (double)acci);
-      M[i * n2 + n + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+      A[i * lda + j] = mk((double)accr, (double)acci);
     }
-    if (tid == 0) { sing_s = 0; prod_s = mk(1.0, 0.0); exp_s = 0; swaps_s = 0; }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-      if (tid < 32) {
+      if (tid < 32) {   // pivot: largest |re| + |im| in column k, lowest row on ties
         double best = -1.0;
         int bi = k;
         for (int i = k + tid; i < n; i += 32) {
-          const double2 v = M[i * n2 + k];
+          const double2 v = A[i * lda + k];
           const double m = fabs(v.x) + fabs(v.y);
           if (m > best) { best = m; bi = i; }
         }
@@ -760,75 +782,94 @@ __global__ void __launch_bounds__(256) k_overlap_gj(OverlapArgs<R> a) {
         if (tid == 0) {
           piv_s = bi;
           if (!(best > 0.0) || !isfinite(best)) sing_s = 1;
-          if (!sing_s) {   // the pivot is row bi's entry in column k (before the swap)
-            const double2 pk = M[bi * n2 + k];
+          if (!sing_s) {
+            const double2 pk = A[bi * lda + k];
             inv_s = cdiv(mk(1.0, 0.0), pk);
             double2 pr = cmul(prod_s, pk);
             int e;
-            const double m = frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
-            (void)m;
-            pr = mk(ldexp(pr.x, -e), ldexp(pr.y, -e));
-            prod_s = pr;
+            frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
+            prod_s = mk(ldexp(pr.x, -e), ldexp(pr.y, -e));
             exp_s += e;
-            if (bi != k) swaps_s ^= 1;
+            if (bi != k) {
+              swaps_s ^= 1;
+              const int t = perm[k];
+              perm[k] = perm[bi];
+              perm[bi] = t;
+            }
           }
         }
       }
       __syncthreads();
       if (sing_s) break;
       const int pv = piv_s;
-      if (pv != k) {
-        for (int j = tid; j < n2; j += blockDim.x) {
-          const double2 t = M[k * n2 + j];
-          M[k * n2 + j] = M[pv * n2 + j];
-          M[pv * n2 + j] = t;
+      if (pv != k)
+        for (int j = tid; j < n; j += blockDim.x) {
+          const double2 t = A[k * lda + j];
+          A[k * lda + j] = A[pv * lda + j];
+          A[pv * lda + j] = t;
         }
-      }
       __syncthreads();
       const double2 inv = inv_s;
-      for (int i = tid; i < n; i += blockDim.x) col[i] = M[i * n2 + k];
+      for (int i = k + 1 + tid; i < n; i += blockDim.x) A[i * lda + k] = cmul(A[i * lda + k], inv);
       __syncthreads();
-      for (int j = k + 1 + tid; j < n2; j += blockDim.x) M[k * n2 + j] = cmul(M[k * n2 + j], inv);
-      __syncthreads();
-      const int width = n2 - k - 1;
-      for (int idx = tid; idx < (n - 1) * width; idx += blockDim.x) {
-        int i = idx / width;
-        const int j = k + 1 + idx % width;
-        if (i >= k) ++i;
-        M[i * n2 + j] = csub(M[i * n2 + j], cmul(col[i], M[k * n2 + j]));
+      const int rem = n - k - 1;
+      for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+        const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+        A[i * lda + j] = csub(A[i * lda + j], cmul(A[i * lda + k], A[k * lda + j]));
       }
       __syncthreads();
     }
     if (sing_s) {
       singular = true;
-      for (int idx = tid; idx < n * a.N; idx += blockDim.x) {
-        const int b = idx / a.N, p = idx % a.N;
-        a.thetaT[((size_t)w * a.ncol + c0 + b) * a.N + p] = from_d2<R>(mk(0.0, 0.0));
+      for (int idx = tid; idx < n * N; idx += blockDim.x) {
+        const int b = idx / N, p = idx % N;
+        a.thetaT[((size_t)w * a.ncol + c0 + b) * N + p] = from_d2<R>(mk(0.0, 0.0));
       }
-      __syncthreads();
       continue;
     }
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of A^-1 to R per entry
-      const int j = idx / n, b = idx % n;
-      Ainv[idx] = from_d2<R>(M[j * n2 + n + b]);
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each factor entry to R
+      const int i = idx / n, j = idx % n;
+      F[idx] = from_d2<R>(i == j ? cdiv(mk(1.0, 0.0), A[i * lda + j]) : A[i * lda + j]);
     }
     __syncthreads();
-    // Theta^T[b][p] = sum_j psi[p][j] Ainv[j][b]
-    for (int idx = tid; idx < n * a.N; idx += blockDim.x) {
-      const int b = idx / a.N, p = idx % a.N;
-      const R2* prow = a.psi + ((size_t)w * a.N + p) * a.ncol + c0;
-      R accr = R(0), acci = R(0);
-      for (int j = 0; j < n; ++j) {
-        const R2 ps = prow[j];
-        const R2 iv = Ainv[j * n + b];
-        accr += ps.x * iv.x - ps.y * iv.y;
-        acci += ps.x * iv.y + ps.y * iv.x;
+    R2* thw = a.thetaT + ((size_t)w * a.ncol + c0) * N;
+    for (int p = tid; p < N; p += blockDim.x) {
+      // y_k of row p: Y[p][k] (STAGE) or Theta^T[perm[k]][p]
+      auto at = [&](int k) -> R2& { return STAGE ? Y[(size_t)p * ldy + k] : thw[(size_t)perm[k] * N + p]; };
+      if (!STAGE)
+        for (int j = 0; j < n; ++j) at(j) = psw[(size_t)p * a.ncol + j];
+      for (int j = 0; j < n; ++j) {   // z U = psi_p
+        R sr = at(j).x, si = at(j).y;
+        for (int k = 0; k < j; ++k) {
+          const R2 z = at(k), u = F[k * n + j];
+          sr -= z.x * u.x - z.y * u.y;
+          si -= z.x * u.y + z.y * u.x;
+        }
+        const R2 d = F[j * n + j];
+        R2 o;
+        o.x = sr * d.x - si * d.y;
+        o.y = sr * d.y + si * d.x;
+        at(j) = o;
       }
-      R2 out;
-      out.x = accr;
-      out.y = acci;
-      a.thetaT[((size_t)w * a.ncol + c0 + b) * a.N + p] = out;
+      for (int j = n - 2; j >= 0; --j) {   // y L = z (unit lower L)
+        R sr = at(j).x, si = at(j).y;
+        for (int k = j + 1; k < n; ++k) {
+          const R2 z = at(k), l = F[k * n + j];
+          sr -= z.x * l.x - z.y * l.y;
+          si -= z.x * l.y + z.y * l.x;
+        }
+        R2 o;
+        o.x = sr;
+        o.y = si;
+        at(j) = o;
+      }
     }
+    __syncthreads();
+    if (STAGE)
+      for (int idx = tid; idx < n * N; idx += blockDim.x) {   // Theta^T[perm[i]][p] = y_i
+        const int i = idx / N, p = idx % N;
+        thw[(size_t)perm[i] * N + p] = Y[(size_t)p * ldy + i];
+      }
     if (tid == 0) {   // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps)
       const double2 pr = prod_s;
       ld_re += log(hypot(pr.x, pr.y)) + exp_s * 0.6931471805599453;
@@ -863,32 +904,40 @@ __global__ void __launch_bounds__(256) k_overlap_gj(OverlapArgs<R> a) {
 }
 
 // ============================================================================
-// Cholesky QR in binary64, one CTA per walker: G = psi^H psi (Hermitian),
-// G = R^H R with R upper triangular and diag R > 0, psi <- psi R^-1 (= Q with
-// diag R > 0, the unique thin QR), log O -= smul sum log R_ii.
+// Cholesky QR, one CTA per walker: G = psi^H psi accumulated in binary64
+// (Hermitian; products of walker-precision entries are exact in binary64),
+// G = R^H R in binary64 with R upper triangular and diag R > 0, then
+// psi <- psi R^-1 (= Q with diag R > 0, the unique thin QR) by forward
+// substitution on each row at the walkers' precision with R rounded once, and
+// log O -= smul sum log R_ii.  stage_psi: the block's columns are staged in
+// shared memory as binary64 rows P[j][p] with an odd row pitch.
 // ============================================================================
+__host__ __device__ inline int qr_pitch(int N) { return N | 1; }
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int c00, int n0, int c01, int n1,
                                                  double smul, cplx_t<R>* psi, double2* logO, const double* wgt,
                                                  int* status, int stage_psi) {
+  using R2 = cplx_t<R>;
   extern __shared__ double2 sm_cq[];
   __shared__ double logsum_s, rinv_s;
   __shared__ int bad_s;
   const int w = blockIdx.x, tid = threadIdx.x;
   if (wgt[w] == 0.0) return;
   if (tid == 0) { logsum_s = 0.0; bad_s = 0; }
+  const int ldp = qr_pitch(N);
   for (int s = 0; s < nblk; ++s) {
     const int c0 = s == 0 ? c00 : c01, n = s == 0 ? n0 : n1;
     if (n == 0) continue;
-    double2* G = sm_cq;               // [n][n], becomes R (upper)
-    double2* Ri = sm_cq + n * n;      // [n][n], R^-1 (upper)
-    cplx_t<R>* Rl = reinterpret_cast<cplx_t<R>*>(Ri + n * n);   // R^-1 at the walkers' precision
-    double2* P = reinterpret_cast<double2*>(Rl + n * n + (n & 1));   // staged psi block [n][N] (stage_psi)
+    double2* G = sm_cq;                                 // [n][n], becomes R (upper)
+    R2* Rl = reinterpret_cast<R2*>(G + n * n);          // R at the walkers' precision, diagonal 1 / R_kk
+    double2* P = reinterpret_cast<double2*>(Rl + n * n + (n & 1));   // staged block [n][ldp] (stage_psi)
+    R2* pw = psi + (size_t)w * N * ncol + c0;
     __syncthreads();
     if (stage_psi) {
       for (int idx = tid; idx < n * N; idx += blockDim.x) {
         const int p = idx / n, j = idx % n;
-        P[(size_t)j * N + p] = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
+        P[(size_t)j * ldp + p] = to_d2(pw[(size_t)p * ncol + j]);
       }
       __syncthreads();
     }
@@ -897,16 +946,16 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
       if (j < i) continue;
       double re = 0.0, im = 0.0;      // (psi^H psi)_ij = sum_p conj(psi_pi) psi_pj
       if (stage_psi) {
-        const double2* u = P + (size_t)i * N;
-        const double2* v = P + (size_t)j * N;
+        const double2* u = P + (size_t)i * ldp;
+        const double2* v = P + (size_t)j * ldp;
         for (int p = 0; p < N; ++p) {
           re += u[p].x * v[p].x + u[p].y * v[p].y;
           im += u[p].x * v[p].y - u[p].y * v[p].x;
         }
       } else {
         for (int p = 0; p < N; ++p) {
-          const double2 u = to_d2(psi[((size_t)w * N + p) * ncol + c0 + i]);
-          const double2 v = to_d2(psi[((size_t)w * N + p) * ncol + c0 + j]);
+          const double2 u = to_d2(pw[(size_t)p * ncol + i]);
+          const double2 v = to_d2(pw[(size_t)p * ncol + j]);
           re += u.x * v.x + u.y * v.y;
           im += u.x * v.y - u.y * v.x;
         }
@@ -937,33 +986,30 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
       }
       __syncthreads();
     }
-    // R^-1 (upper): one thread per column j, back substitution
-    for (int j = tid; j < n; j += blockDim.x) {
-      for (int i = n - 1; i >= 0; --i) {
-        if (i > j) { Ri[i * n + j] = mk(0.0, 0.0); continue; }
-        double2 acc = mk(i == j ? 1.0 : 0.0, 0.0);
-        for (int k = i + 1; k <= j; ++k) acc = csub(acc, cmul(G[i * n + k], Ri[k * n + j]));
-        Ri[i * n + j] = cdiv(acc, G[i * n + i]);
-      }
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each entry of R to R
+      const int i = idx / n, j = idx % n;
+      Rl[idx] = from_d2<R>(i == j ? mk(1.0 / G[idx].x, 0.0) : (j > i ? G[idx] : mk(0.0, 0.0)));
     }
     __syncthreads();
-    for (int idx = tid; idx < n * n; idx += blockDim.x) Rl[idx] = from_d2<R>(Ri[idx]);
-    __syncthreads();
-    // psi <- psi R^-1 at the walkers' precision (R^-1 itself is binary64); column j needs psi_pk for
-    // k <= j only, so each row is updated right to left in place
+    // row p of Q: x R = psi_p, x_j = (psi_pj - sum_{k<j} x_k R_kj) / R_jj
     for (int p = tid; p < N; p += blockDim.x) {
-      cplx_t<R>* row = psi + ((size_t)w * N + p) * ncol + c0;
-      for (int j = n - 1; j >= 0; --j) {
-        R accr = R(0), acci = R(0);
-        for (int k = 0; k <= j; ++k) {
-          const cplx_t<R> v = row[k];
-          const cplx_t<R> ri = Rl[k * n + j];
-          accr += v.x * ri.x - v.y * ri.y;
-          acci += v.x * ri.y + v.y * ri.x;
+      R2* row = pw + (size_t)p * ncol;
+      auto x = [&](int k) -> R2 {
+        if (stage_psi) return from_d2<R>(P[(size_t)k * ldp + p]);
+        return row[k];
+      };
+      for (int j = 0; j < n; ++j) {
+        R sr = x(j).x, si = x(j).y;
+        for (int k = 0; k < j; ++k) {
+          const R2 z = x(k), r = Rl[k * n + j];
+          sr -= z.x * r.x - z.y * r.y;
+          si -= z.x * r.y + z.y * r.x;
         }
-        cplx_t<R> o;
-        o.x = accr;
-        o.y = acci;
+        const R d = Rl[j * n + j].x;
+        R2 o;
+        o.x = sr * d;
+        o.y = si * d;
+        if (stage_psi) P[(size_t)j * ldp + p] = to_d2(o);
         row[j] = o;
       }
     }

@@ -11,9 +11,10 @@
 // so that D[p][c] = Re (V t)[p][c] and D[p][cwp + c] = Im (V t)[p][c].  Operands are split-bf16
 // (hi + lo, products hi*hi + lo*hi + hi*lo, fp32 accumulation in tensor memory).
 //
-// Roles: warp 4 (one thread) loads F once and each walker's V planes by TMA and issues the MMAs;
-// warps 0-3 own accumulator lanes 0-127: thread p reads row p of D, keeps row p of acc in
-// registers, and writes the next B operand column k = p (hi and lo) into shared memory.  V of the
+// Roles: warp 16 (one thread) loads F once and each walker's V planes by TMA and issues the MMAs;
+// warps 0-15 read the accumulator, warp w covering lanes 32 (w % 4) .. + 31 (rows p) and a
+// quarter of the chunk's columns: it keeps its part of row p of acc in registers and writes the
+// matching entries of column k = p of the next B operand (hi and lo) into shared memory.  V of the
 // next walker is fetched as soon as the last Taylor product of the current one has completed.
 // Rows p >= N of D (padding, and rows 112-127 which the MMA reads from the following buffer)
 // are never used: those threads write zeros into B.  Every wait is bounded.
@@ -52,18 +53,20 @@ __device__ __forceinline__ void st_bf16(uint8_t* base, uint32_t off, __nv_bfloat
   *reinterpret_cast<__nv_bfloat16*>(base + off) = v;
 }
 
-// Column k = p of the next B operand from this thread's row of the term (ur, ui); `both` also
-// writes the second K half (needed by the V products, not by the F products).
-template <int CWP>
-__device__ __forceinline__ void write_b(uint8_t* bhi, uint8_t* blo, int p, const float* ur, const float* ui,
+// Columns j0 .. j0 + SW - 1 of column k = p of the next B operand from this thread's slice of
+// the term (ur, ui); `both` also writes the second K half (needed by the V products, not by the
+// F products).
+template <int CWP, int SW>
+__device__ __forceinline__ void write_b(uint8_t* bhi, uint8_t* blo, int p, int j0, const float* ur, const float* ui,
                                         bool both) {
   constexpr int ab = 2 * CWP * 128;
 #pragma unroll
-  for (int j = 0; j < CWP; ++j) {
-    const __nv_bfloat16 rh = __float2bfloat16_rn(ur[j]);
-    const __nv_bfloat16 rl = __float2bfloat16_rn(ur[j] - __bfloat162float(rh));
-    const __nv_bfloat16 ih = __float2bfloat16_rn(ui[j]);
-    const __nv_bfloat16 il = __float2bfloat16_rn(ui[j] - __bfloat162float(ih));
+  for (int jj = 0; jj < SW; ++jj) {
+    const int j = j0 + jj;
+    const __nv_bfloat16 rh = __float2bfloat16_rn(ur[jj]);
+    const __nv_bfloat16 rl = __float2bfloat16_rn(ur[jj] - __bfloat162float(rh));
+    const __nv_bfloat16 ih = __float2bfloat16_rn(ui[jj]);
+    const __nv_bfloat16 il = __float2bfloat16_rn(ui[jj] - __bfloat162float(ih));
     const uint32_t o_r = sw_off(j, p, ab), o_i = sw_off(CWP + j, p, ab);
     st_bf16(bhi, o_r, rh);
     st_bf16(blo, o_r, rl);
@@ -96,25 +99,44 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return ok != 0;
 }
 
-// Row of D: dr[j] = D[p][j], di[j] = D[p][CWP + j].
-template <int CWP>
-__device__ __forceinline__ void load_d(uint32_t trow, float* dr, float* di) {
-#pragma unroll
-  for (int c = 0; c < 2 * CWP; c += 16) {
-    float v[16];
-    tmem_ld16(trow + (uint32_t)c, v);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int col = c + i;
-      if (col < CWP) dr[col] = v[i];
-      else di[col - CWP] = v[i];
-    }
+// SW consecutive accumulator columns of this thread's lane (no wait).
+template <int SW>
+__device__ __forceinline__ void ld_cols(uint32_t taddr, uint32_t* r) {
+  if constexpr (SW == 2) {
+    tmem_ld2_nowait(taddr, r);
+  } else if constexpr (SW == 4) {
+    tmem_ld4_nowait(taddr, r);
+  } else if constexpr (SW == 6) {
+    tmem_ld4_nowait(taddr, r);
+    tmem_ld2_nowait(taddr + 4, r + 4);
+  } else {
+    static_assert(SW == 8, "slice width");
+    tmem_ld8_nowait(taddr, r);
   }
 }
 
+// This thread's slice of row p of D: dr[jj] = D[p][j0 + jj], di[jj] = D[p][CWP + j0 + jj].
+template <int CWP, int SW>
+__device__ __forceinline__ void load_d(uint32_t trow, int j0, float* dr, float* di) {
+  uint32_t r[SW], q[SW];
+  ld_cols<SW>(trow + (uint32_t)j0, r);
+  ld_cols<SW>(trow + (uint32_t)(CWP + j0), q);
+  tmem_wait();
+#pragma unroll
+  for (int jj = 0; jj < SW; ++jj) {
+    dr[jj] = __uint_as_float(r[jj]);
+    di[jj] = __uint_as_float(q[jj]);
+  }
+}
+
+constexpr int kEpiWarps = 16;                 // 4 lane quadrants x 4 column slices
+constexpr int kPropThreads = 32 * kEpiWarps + 32;
+
 template <int CWP>
-__global__ void __launch_bounds__(160, 1) k_prop_tc(const __grid_constant__ CUtensorMap mapV,
-                                                    const __grid_constant__ CUtensorMap mapF, const PropTcParams a) {
+__global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_constant__ CUtensorMap mapV,
+                                                             const __grid_constant__ CUtensorMap mapF,
+                                                             const PropTcParams a) {
+  constexpr int SW = CWP / 4;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + a.off_bar);
@@ -130,11 +152,11 @@ __global__ void __launch_bounds__(160, 1) k_prop_tc(const __grid_constant__ CUte
     mbar_init(bar_v, 1);
     mbar_init(bar_f, 1);
     mbar_init(bar_mma, 1);
-    mbar_init(bar_b, 4);
+    mbar_init(bar_b, kEpiWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) {
+  if (warp == kEpiWarps) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(a.tmem_cols)
                  : "memory");
@@ -151,11 +173,15 @@ __global__ void __launch_bounds__(160, 1) k_prop_tc(const __grid_constant__ CUte
     return a.W;
   };
 
-  if (warp == 4) {
+  if (warp == kEpiWarps) {
     if (lane == 0) {   // TMA + MMA issue
       const uint32_t s0 = smem_u32(sm);
       const uint32_t vatom = (uint32_t)a.npad * 128u, batom = 2u * CWP * 128u;
       const uint32_t idesc = idesc_bf16(2 * CWP);
+      // descriptors are linear in the address: desc(base + off) = desc(base) + off / 16
+      const uint64_t dvhi = sw128_desc(s0), dvlo = sw128_desc(s0 + (uint32_t)a.off_vlo);
+      const uint64_t dfhi = sw128_desc(s0 + (uint32_t)a.off_fhi), dflo = sw128_desc(s0 + (uint32_t)a.off_flo);
+      const uint64_t dbhi = sw128_desc(s0 + (uint32_t)a.off_bhi), dblo = sw128_desc(s0 + (uint32_t)a.off_blo);
       auto issue_v = [&](int wk) {
         mbar_expect_tx(bar_v, 8u * vatom);
         for (int pl = 0; pl < 4; ++pl)
@@ -165,18 +191,17 @@ __global__ void __launch_bounds__(160, 1) k_prop_tc(const __grid_constant__ CUte
           }
       };
       auto product = [&](bool isv) {
-        const uint32_t ahi = s0 + (isv ? 0u : (uint32_t)a.off_fhi), alo = s0 + (uint32_t)(isv ? a.off_vlo : a.off_flo);
-        const uint32_t bhi = s0 + (uint32_t)a.off_bhi, blo = s0 + (uint32_t)a.off_blo;
+        const uint64_t ah = isv ? dvhi : dfhi, al = isv ? dvlo : dflo;
         uint32_t accf = 0;
         for (int h = 0; h < (isv ? 2 : 1); ++h)
           for (int ks = 0; ks < a.nk; ++ks) {
             const int atom = 2 * h + (ks >> 2);
             const uint32_t ko = (uint32_t)(ks & 3) * 32u;
-            const uint32_t ao = (uint32_t)atom * vatom + ko, bo = (uint32_t)atom * batom + ko;
-            umma_bf16(tmem, sw128_desc(ahi + ao), sw128_desc(bhi + bo), idesc, accf);
+            const uint64_t ao = ((uint32_t)atom * vatom + ko) >> 4, bo = ((uint32_t)atom * batom + ko) >> 4;
+            umma_bf16(tmem, ah + ao, dbhi + bo, idesc, accf);
             accf = 1;
-            umma_bf16(tmem, sw128_desc(alo + ao), sw128_desc(bhi + bo), idesc, 1);
-            umma_bf16(tmem, sw128_desc(ahi + ao), sw128_desc(blo + bo), idesc, 1);
+            umma_bf16(tmem, al + ao, dbhi + bo, idesc, 1);
+            umma_bf16(tmem, ah + ao, dblo + bo, idesc, 1);
           }
         umma_commit(bar_mma);
       };
@@ -228,62 +253,63 @@ __global__ void __launch_bounds__(160, 1) k_prop_tc(const __grid_constant__ CUte
         *abort_flag = 1;
       }
     }
-  } else {   // warps 0-3: accumulator lanes 32 warp .. 32 warp + 31
-    const int p = threadIdx.x;
+  } else {   // epilogue warp: lanes 32 (warp % 4) .. + 31, columns j0 .. j0 + SW - 1 of the chunk
+    const int quad = warp & 3, j0 = (warp >> 2) * SW;
+    const int p = 32 * quad + lane;
     const bool row = p < a.N;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
     uint8_t* bhi = sm + a.off_bhi;
     uint8_t* blo = sm + a.off_blo;
     uint32_t ph_m = 0;
     bool go = true;
-    float accr[CWP], acci[CWP], dr[CWP], di[CWP];
+    float accr[SW], acci[SW], dr[SW], di[SW];
     for (int wk = next_live(blockIdx.x); wk < a.W && go; wk = next_live(wk + gridDim.x)) {
       for (int ch = 0; ch < a.nch; ++ch) {
         const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
         float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol + c0;
 #pragma unroll
-        for (int j = 0; j < CWP; ++j) {
+        for (int jj = 0; jj < SW; ++jj) {
           float2 v = make_float2(0.f, 0.f);
-          if (row && j < cwn) v = prow[j];
-          accr[j] = dr[j] = v.x;
-          acci[j] = di[j] = v.y;
+          if (row && j0 + jj < cwn) v = prow[j0 + jj];
+          accr[jj] = dr[jj] = v.x;
+          acci[jj] = di[jj] = v.y;
         }
-        write_b<CWP>(bhi, blo, p, dr, di, false);
+        write_b<CWP, SW>(bhi, blo, p, j0, dr, di, false);
         signal_b(bar_b, lane);
         if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
         ph_m ^= 1u;
-        load_d<CWP>(trow, dr, di);   // F psi
+        load_d<CWP, SW>(trow, j0, dr, di);   // F psi
 #pragma unroll
-        for (int j = 0; j < CWP; ++j) {   // t_0 = psi + F psi
-          accr[j] = row ? accr[j] + dr[j] : 0.f;
-          acci[j] = row ? acci[j] + di[j] : 0.f;
+        for (int jj = 0; jj < SW; ++jj) {   // t_0 = psi + F psi
+          accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
+          acci[jj] = row ? acci[jj] + di[jj] : 0.f;
         }
-        write_b<CWP>(bhi, blo, p, accr, acci, true);
+        write_b<CWP, SW>(bhi, blo, p, j0, accr, acci, true);
         signal_b(bar_b, lane);
         for (int k = 1; k <= a.order; ++k) {
           if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
           ph_m ^= 1u;
-          load_d<CWP>(trow, dr, di);   // t_k
+          load_d<CWP, SW>(trow, j0, dr, di);   // t_k
           const float s = 1.f / (float)(k + 1);
 #pragma unroll
-          for (int j = 0; j < CWP; ++j) {
-            const float tr = row ? dr[j] : 0.f, ti = row ? di[j] : 0.f;
-            accr[j] += tr;
-            acci[j] += ti;
-            dr[j] = tr * s;   // next operand t_k / (k + 1)
-            di[j] = ti * s;
+          for (int jj = 0; jj < SW; ++jj) {
+            const float tr = row ? dr[jj] : 0.f, ti = row ? di[jj] : 0.f;
+            accr[jj] += tr;
+            acci[jj] += ti;
+            dr[jj] = tr * s;   // next operand t_k / (k + 1)
+            di[jj] = ti * s;
           }
-          if (k < a.order) write_b<CWP>(bhi, blo, p, dr, di, true);
-          else write_b<CWP>(bhi, blo, p, accr, acci, false);
+          if (k < a.order) write_b<CWP, SW>(bhi, blo, p, j0, dr, di, true);
+          else write_b<CWP, SW>(bhi, blo, p, j0, accr, acci, false);
           signal_b(bar_b, lane);
         }
         if (!go) break;
         if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
         ph_m ^= 1u;
-        load_d<CWP>(trow, dr, di);   // F acc
+        load_d<CWP, SW>(trow, j0, dr, di);   // F acc
 #pragma unroll
-        for (int j = 0; j < CWP; ++j)
-          if (row && j < cwn) prow[j] = make_float2(accr[j] + dr[j], acci[j] + di[j]);
+        for (int jj = 0; jj < SW; ++jj)
+          if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
       }
     }
     if (!go && lane == 0) {
@@ -299,7 +325,7 @@ __global__ void __launch_bounds__(160, 1) k_prop_tc(const __grid_constant__ CUte
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 4)
+  if (warp == kEpiWarps)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
@@ -318,7 +344,7 @@ template <int CWP>
 afqmc_status launch_prop(const TcState* st, cudaStream_t s, const PropTcParams& p, unsigned long long* launches,
                          char* err, size_t errlen) {
   const int grid = std::min(st->W, num_sms());
-  k_prop_tc<CWP><<<grid, 160, st->pg.smem, s>>>(st->map_vp, st->map_fp, p);
+  k_prop_tc<CWP><<<grid, kPropThreads, st->pg.smem, s>>>(st->map_vp, st->map_fp, p);
   ++*launches;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
