@@ -379,7 +379,7 @@ size_t overlap_smem(const Dims& d) {
 
 size_t qr_smem_base(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return (size_t)nmax * nmax * sizeof(double2) + ((size_t)nmax * nmax + 1) * 2 * d.rsz() + 16;
+  return (size_t)nmax * nmax * sizeof(double2) + ((size_t)nmax * nmax + 1) * 2 * d.rsz() + (size_t)nmax * 16 + 16;
 }
 bool qr_stage_psi(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);

@@ -332,7 +332,7 @@ struct FieldArgs {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_fields(FieldArgs<R> a) {
+__global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
   __shared__ SeriesTables tab;
   __shared__ double red[32];
   const int w = blockIdx.x, tid = threadIdx.x;
@@ -351,9 +351,12 @@ __global__ void __launch_bounds__(256) k_fields(FieldArgs<R> a) {
       const double2 vb = to_d2(a.vbias[(size_t)w * a.X + g]);
       const double dre = vb.x - a.lbar[g], dim = vb.y;
       double2 xb = mk(a.sdt * dim, -a.sdt * dre);
-      if (a.cap > 0.0) {
-        const double m = sqrt(xb.x * xb.x + xb.y * xb.y);
-        if (m > a.cap) xb = cscale(xb, a.cap / m);
+      if (a.cap > 0.0) {   // |xb| > cap, tested on the squares (the square root only when capping)
+        const double m2 = xb.x * xb.x + xb.y * xb.y;
+        if (m2 > a.cap * a.cap) {
+          const double m = sqrt(m2);
+          if (m > a.cap) xb = cscale(xb, a.cap / m);
+        }
       }
       const double2 xs = mk(x - xb.x, -xb.y);
       a.coef[(size_t)w * a.X + g] = from_d2<R>(mk(a.sdt * xs.y, -a.sdt * xs.x));
@@ -719,7 +722,7 @@ template <typename R>
 __host__ __device__ inline size_t overlap_lu_smem(int N, int nmax, bool stage) {
   const int lda = nmax + 1, ldy = nmax | 1;
   return (size_t)nmax * lda * sizeof(double2) + (stage ? (size_t)N * ldy * 2 * sizeof(R) : 0) +
-         (size_t)nmax * nmax * 2 * sizeof(R) + (size_t)nmax * sizeof(int) + 16;
+         (size_t)nmax * nmax * 2 * sizeof(R) + (size_t)(nmax + 1) * sizeof(int) + (size_t)nmax * sizeof(double2) + 16;
 }
 
 template <typename R, bool STAGE>
@@ -764,32 +767,44 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
       A[i * lda + j] = mk((double)accr, (double)acci);
     }
     __syncthreads();
+    double2* dinv = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(perm + nmax) + 15) & ~(uintptr_t)15);  // 1 / U_kk
     for (int k = 0; k < n; ++k) {
       if (tid < 32) {   // pivot: largest |re| + |im| in column k, lowest row on ties
-        double best = -1.0;
+        // non-negative doubles order like their bit patterns: compare as integers
+        long long best = -1;
         int bi = k;
         for (int i = k + tid; i < n; i += 32) {
           const double2 v = A[i * lda + k];
-          const double m = fabs(v.x) + fabs(v.y);
+          const long long m = __double_as_longlong(fabs(v.x) + fabs(v.y));
           if (m > best) { best = m; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         if (tid == 0) {
           piv_s = bi;
-          if (!(best > 0.0) || !isfinite(best)) sing_s = 1;
+          // zero, NaN or infinity: the sum's bit pattern is 0 or has every exponent bit set
+          if (best <= 0 || best >= 0x7ff0000000000000LL) sing_s = 1;
           if (!sing_s) {
             const double2 pk = A[bi * lda + k];
-            inv_s = cdiv(mk(1.0, 0.0), pk);
-            double2 pr = cmul(prod_s, pk);
-            int e;
-            frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
-            prod_s = mk(ldexp(pr.x, -e), ldexp(pr.y, -e));
-            exp_s += e;
+            const double r = 1.0 / fma(pk.x, pk.x, pk.y * pk.y);   // 1 / pk = conj(pk) / |pk|^2
+            const double2 inv = mk(pk.x * r, -pk.y * r);
+            inv_s = inv;
+            dinv[k] = inv;
+            const double2 pr = prod_s;
+            double2 q = mk(fma(pr.x, pk.x, -pr.y * pk.y), fma(pr.x, pk.y, pr.y * pk.x));
+            // renormalise by the power of two of the larger component (exact)
+            const long long big = __double_as_longlong(fmax(fabs(q.x), fabs(q.y)));
+            const int e = (int)((big >> 52) & 0x7ff) - 1023;
+            if (e > -1000 && e < 1000) {
+              const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+              q = mk(q.x * sc, q.y * sc);
+              exp_s += e;
+            }
+            prod_s = q;
             if (bi != k) {
               swaps_s ^= 1;
               const int t = perm[k];
@@ -810,12 +825,19 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
         }
       __syncthreads();
       const double2 inv = inv_s;
-      for (int i = k + 1 + tid; i < n; i += blockDim.x) A[i * lda + k] = cmul(A[i * lda + k], inv);
+      for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+        const double2 v = A[i * lda + k];
+        A[i * lda + k] = mk(fma(v.x, inv.x, -v.y * inv.y), fma(v.x, inv.y, v.y * inv.x));
+      }
       __syncthreads();
       const int rem = n - k - 1;
       for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
         const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-        A[i * lda + j] = csub(A[i * lda + j], cmul(A[i * lda + k], A[k * lda + j]));
+        const double2 l = A[i * lda + k], u = A[k * lda + j];
+        double2 v = A[i * lda + j];
+        v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
+        v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
+        A[i * lda + j] = v;
       }
       __syncthreads();
     }
@@ -829,7 +851,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     }
     for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each factor entry to R
       const int i = idx / n, j = idx % n;
-      F[idx] = from_d2<R>(i == j ? cdiv(mk(1.0, 0.0), A[i * lda + j]) : A[i * lda + j]);
+      F[idx] = from_d2<R>(i == j ? dinv[i] : A[i * lda + j]);
     }
     __syncthreads();
     R2* thw = a.thetaT + ((size_t)w * a.ncol + c0) * N;
@@ -931,7 +953,7 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
     if (n == 0) continue;
     double2* G = sm_cq;                                 // [n][n], becomes R (upper)
     R2* Rl = reinterpret_cast<R2*>(G + n * n);          // R at the walkers' precision, diagonal 1 / R_kk
-    double2* P = reinterpret_cast<double2*>(Rl + n * n + (n & 1));   // staged block [n][ldp] (stage_psi)
+    double2* P = reinterpret_cast<double2*>(Rl + n * n + (n & 1) + n * (sizeof(double) / sizeof(R2) + 1));   // [n][ldp]
     R2* pw = psi + (size_t)w * N * ncol + c0;
     __syncthreads();
     if (stage_psi) {
@@ -963,7 +985,8 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
       G[i * n + j] = mk(re, im);
     }
     __syncthreads();
-    // right-looking Cholesky on the upper triangle: G_kk -> R_kk, row k -> R_kj
+    // right-looking Cholesky on the upper triangle: G_kk -> R_kk, row k -> R_kj (1 / R_kk kept in rinv)
+    double* rinv = reinterpret_cast<double*>(Rl + n * n);
     for (int k = 0; k < n; ++k) {
       if (tid == 0) {
         const double d = G[k * n + k].x;
@@ -971,37 +994,42 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
         const double r = sqrt(fmax(d, 1e-300));
         G[k * n + k] = mk(r, 0.0);
         rinv_s = 1.0 / r;
-        logsum_s += log(r);
+        rinv[k] = rinv_s;
       }
       __syncthreads();
-      const double rinv = rinv_s;
-      for (int j = k + 1 + tid; j < n; j += blockDim.x) G[k * n + j] = cscale(G[k * n + j], rinv);
+      const double ri = rinv_s;
+      for (int j = k + 1 + tid; j < n; j += blockDim.x) G[k * n + j] = cscale(G[k * n + j], ri);
       __syncthreads();
       const int rem = n - k - 1;
       for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
         const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
         if (j < i) continue;
         const double2 rki = G[k * n + i], rkj = G[k * n + j];   // G_ij -= conj(R_ki) R_kj
-        G[i * n + j] = csub(G[i * n + j], mk(rki.x * rkj.x + rki.y * rkj.y, rki.x * rkj.y - rki.y * rkj.x));
+        double2 g = G[i * n + j];
+        g.x = fma(-rki.x, rkj.x, fma(-rki.y, rkj.y, g.x));
+        g.y = fma(-rki.x, rkj.y, fma(rki.y, rkj.x, g.y));
+        G[i * n + j] = g;
       }
       __syncthreads();
     }
+    if (tid < 32) {   // sum_k log R_kk, one lane per diagonal entry
+      double ls = 0.0;
+      for (int k = tid; k < n; k += 32) ls += log(G[k * n + k].x);
+      ls = warp_sum(ls);
+      if (tid == 0) logsum_s += ls;
+    }
     for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each entry of R to R
       const int i = idx / n, j = idx % n;
-      Rl[idx] = from_d2<R>(i == j ? mk(1.0 / G[idx].x, 0.0) : (j > i ? G[idx] : mk(0.0, 0.0)));
+      Rl[idx] = from_d2<R>(i == j ? mk(rinv[i], 0.0) : (j > i ? G[idx] : mk(0.0, 0.0)));
     }
     __syncthreads();
-    // row p of Q: x R = psi_p, x_j = (psi_pj - sum_{k<j} x_k R_kj) / R_jj
+    // row p of Q: x R = psi_p, x_j = (psi_pj - sum_{k<j} x_k R_kj) / R_jj, in place on the row
     for (int p = tid; p < N; p += blockDim.x) {
       R2* row = pw + (size_t)p * ncol;
-      auto x = [&](int k) -> R2 {
-        if (stage_psi) return from_d2<R>(P[(size_t)k * ldp + p]);
-        return row[k];
-      };
       for (int j = 0; j < n; ++j) {
-        R sr = x(j).x, si = x(j).y;
+        R sr = row[j].x, si = row[j].y;
         for (int k = 0; k < j; ++k) {
-          const R2 z = x(k), r = Rl[k * n + j];
+          const R2 z = row[k], r = Rl[k * n + j];
           sr -= z.x * r.x - z.y * r.y;
           si -= z.x * r.y + z.y * r.x;
         }
@@ -1009,7 +1037,6 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
         R2 o;
         o.x = sr * d;
         o.y = si * d;
-        if (stage_psi) P[(size_t)j * ldp + p] = to_d2(o);
         row[j] = o;
       }
     }
