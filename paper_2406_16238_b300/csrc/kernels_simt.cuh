@@ -398,16 +398,29 @@ __global__ void __launch_bounds__(256) k_draw_normals(unsigned long long seed, u
 __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long seed, const unsigned long long* step,
                                                    const double* w, double* cum, int* src, double* neww,
                                                    int* status) {
+  constexpr int kTile = 2048;
+  __shared__ double ws[kTile];
   __shared__ double total_s, xi_s;
   __shared__ int last_s, ok_s;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    int last = -1;
-    for (int i = 0; i < W; ++i) {
-      t = t + w[i];
-      cum[i] = t;
-      if (w[i] > 0.0) last = i;
+  double t = 0.0;
+  int last = -1;
+  for (int base = 0; base < W; base += kTile) {   // weights staged per tile, summed by one thread in index order
+    const int len = min(kTile, W - base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) ws[i] = w[base + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < len; ++i) {
+        const double wi = ws[i];
+        t = t + wi;
+        ws[i] = t;
+        if (wi > 0.0) last = base + i;
+      }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) cum[base + i] = ws[i];
+  }
+  if (threadIdx.x == 0) {
     total_s = t;
     last_s = last;
     ok_s = (t > 0.0) && isfinite(t) && last >= 0;
@@ -419,13 +432,14 @@ __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long see
   }
   __syncthreads();
   const double total = total_s, xi = xi_s;
+  const double* cs = W <= kTile ? ws : cum;   // the prefix sums (still in shared memory for one tile)
   for (int k = threadIdx.x; k < W; k += blockDim.x) {
     if (!ok_s) { src[k] = k; continue; }
     const double tooth = __ddiv_rn(__dmul_rn(__dadd_rn((double)k, xi), total), (double)W);
     int lo = 0, hi = W;   // first i with cum[i] > tooth
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (cum[mid] > tooth) hi = mid; else lo = mid + 1;
+      if (cs[mid] > tooth) hi = mid; else lo = mid + 1;
     }
     src[k] = lo < W ? lo : last_s;
   }
@@ -963,9 +977,11 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
       }
       __syncthreads();
     }
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx % n;
-      if (j < i) continue;
+    const int npk = n * (n + 1) / 2;
+    for (int e = tid; e < npk; e += blockDim.x) {   // packed upper triangle, row by row
+      int i = 0, rest = e;
+      while (rest >= n - i) { rest -= n - i; ++i; }
+      const int j = i + rest;
       double re = 0.0, im = 0.0;      // (psi^H psi)_ij = sum_p conj(psi_pi) psi_pj
       if (stage_psi) {
         const double2* u = P + (size_t)i * ldp;
