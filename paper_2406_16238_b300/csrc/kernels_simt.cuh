@@ -730,30 +730,50 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
 // precision with the factors rounded once to R.  mode 0: log O only;
 // mode 1: also the weight update; mode 2: Theta and log det, no weights.
 // ============================================================================
-// STAGE: psi rows and the substitution vectors live in shared memory (Y); otherwise the
+// STAGE: psi rows, Phi and the substitution vectors live in shared memory (Y); otherwise the
 // vectors live in Theta^T itself (row perm[k] holds y_k throughout, so no final permutation).
+// Shared memory: A [n][lda] binary64 | pivots, 1 / pivots [n] binary64 | perm [n] | F [n][n] R |
+// (STAGE) Y [N][ldy] R complex | Phi [N][n] R.
 template <typename R>
 __host__ __device__ inline size_t overlap_lu_smem(int N, int nmax, bool stage) {
   const int lda = nmax + 1, ldy = nmax | 1;
-  return (size_t)nmax * lda * sizeof(double2) + (stage ? (size_t)N * ldy * 2 * sizeof(R) : 0) +
-         (size_t)nmax * nmax * 2 * sizeof(R) + (size_t)(nmax + 1) * sizeof(int) + (size_t)nmax * sizeof(double2) + 16;
+  const size_t fixed = (size_t)nmax * lda * 16 + (size_t)nmax * 32 + ((size_t)nmax * 4 + 15) / 16 * 16 +
+                       (size_t)nmax * nmax * 2 * sizeof(R);
+  return fixed + (stage ? (size_t)N * ldy * 2 * sizeof(R) + (size_t)N * nmax * sizeof(R) : 0) + 16;
+}
+
+// Complex product with the larger component renormalised to [1, 2) (exact power of two); e
+// accumulates the exponent removed.
+__device__ __forceinline__ double2 cmul_renorm(double2 a, double2 b, int* e) {
+  double2 q = mk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+  const long long big = __double_as_longlong(fmax(fabs(q.x), fabs(q.y)));
+  const int ex = (int)((big >> 52) & 0x7ff) - 1023;
+  if (ex > -1000 && ex < 1000) {
+    const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+    q = mk(q.x * sc, q.y * sc);
+    *e += ex;
+  }
+  return q;
 }
 
 template <typename R, bool STAGE>
 __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
   using R2 = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char sm_lu[];
-  __shared__ int piv_s, sing_s, exp_s, swaps_s;
-  __shared__ double2 inv_s, prod_s;   // pivot reciprocal; running product of pivots (scaled)
+  __shared__ int piv_s, sing_s, swaps_s, exp_s;
+  __shared__ double2 inv_s, prod_s;
   const int w = blockIdx.x, tid = threadIdx.x, N = a.N;
   if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
   if (a.mode == 1 && a.w[w] == 0.0) return;
   const int nmax = max(a.nb[0], a.nblk > 1 ? a.nb[1] : 0);
   const int lda = nmax + 1, ldy = nmax | 1;
-  double2* A = reinterpret_cast<double2*>(sm_lu);          // [n][lda] binary64, becomes L\U
-  R2* Y = reinterpret_cast<R2*>(A + (size_t)nmax * lda);   // [N][ldy]: psi rows, then Theta rows
-  R2* F = Y + (STAGE ? (size_t)N * ldy : 0);               // [n][n] factors at R (diagonal: 1 / U_kk)
-  int* perm = reinterpret_cast<int*>(F + (size_t)nmax * nmax);
+  double2* A = reinterpret_cast<double2*>(sm_lu);           // [n][lda] binary64, becomes L\U
+  double2* pivv = A + (size_t)nmax * lda;                   // pivots U_kk
+  double2* dinv = pivv + nmax;                              // 1 / U_kk
+  int* perm = reinterpret_cast<int*>(dinv + nmax);
+  R2* F = reinterpret_cast<R2*>(reinterpret_cast<unsigned char*>(perm) + ((size_t)nmax * 4 + 15) / 16 * 16);
+  R2* Y = F + (size_t)nmax * nmax;                          // [N][ldy]: psi rows, then Theta rows
+  R* PH = reinterpret_cast<R*>(Y + (size_t)N * ldy);        // [N][n] Phi block
   double ld_re = 0.0, ld_im = 0.0;
   bool singular = false;
   for (int s = 0; s < a.nblk; ++s) {
@@ -761,27 +781,47 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     if (n == 0) continue;
     __syncthreads();
     const R2* psw = a.psi + (size_t)w * N * a.ncol + c0;
-    if (STAGE)
+    if (STAGE) {
       for (int idx = tid; idx < N * n; idx += blockDim.x) {
         const int p = idx / n, j = idx % n;
         Y[(size_t)p * ldy + j] = psw[(size_t)p * a.ncol + j];
+        PH[idx] = a.phi_r[(size_t)p * a.ncol + c0 + j];
       }
+    }
     if (tid < n) perm[tid] = tid;
-    if (tid == 0) { sing_s = 0; prod_s = mk(1.0, 0.0); exp_s = 0; swaps_s = 0; }
+    if (tid == 0) { sing_s = 0; swaps_s = 0; }
     __syncthreads();
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx % n;
-      R accr = R(0), acci = R(0);
+    // A = Phi^T psi: 2 x 2 register tiles
+    const int nt = (n + 1) / 2;
+    for (int t = tid; t < nt * nt; t += blockDim.x) {
+      const int i0 = 2 * (t / nt), j0 = 2 * (t % nt);
+      const bool i1ok = i0 + 1 < n, j1ok = j0 + 1 < n;
+      R acc[2][2][2] = {};
       for (int p = 0; p < N; ++p) {
-        const R ph = a.phi_r[(size_t)p * a.ncol + c0 + i];
-        const R2 ps = STAGE ? Y[(size_t)p * ldy + j] : psw[(size_t)p * a.ncol + j];
-        accr += ph * ps.x;
-        acci += ph * ps.y;
+        R ph0, ph1;
+        R2 ps0, ps1;
+        if (STAGE) {
+          ph0 = PH[p * n + i0];
+          ph1 = i1ok ? PH[p * n + i0 + 1] : R(0);
+          ps0 = Y[(size_t)p * ldy + j0];
+          ps1 = j1ok ? Y[(size_t)p * ldy + j0 + 1] : ps0;
+        } else {
+          ph0 = a.phi_r[(size_t)p * a.ncol + c0 + i0];
+          ph1 = i1ok ? a.phi_r[(size_t)p * a.ncol + c0 + i0 + 1] : R(0);
+          ps0 = psw[(size_t)p * a.ncol + j0];
+          ps1 = j1ok ? psw[(size_t)p * a.ncol + j0 + 1] : ps0;
+        }
+        acc[0][0][0] += ph0 * ps0.x; acc[0][0][1] += ph0 * ps0.y;
+        acc[0][1][0] += ph0 * ps1.x; acc[0][1][1] += ph0 * ps1.y;
+        acc[1][0][0] += ph1 * ps0.x; acc[1][0][1] += ph1 * ps0.y;
+        acc[1][1][0] += ph1 * ps1.x; acc[1][1][1] += ph1 * ps1.y;
       }
-      A[i * lda + j] = mk((double)accr, (double)acci);
+      for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj)
+          if ((di == 0 || i1ok) && (dj == 0 || j1ok))
+            A[(i0 + di) * lda + j0 + dj] = mk((double)acc[di][dj][0], (double)acc[di][dj][1]);
     }
     __syncthreads();
-    double2* dinv = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(perm + nmax) + 15) & ~(uintptr_t)15);  // 1 / U_kk
     for (int k = 0; k < n; ++k) {
       if (tid < 32) {   // pivot: largest |re| + |im| in column k, lowest row on ties
         // non-negative doubles order like their bit patterns: compare as integers
@@ -808,17 +848,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
             const double2 inv = mk(pk.x * r, -pk.y * r);
             inv_s = inv;
             dinv[k] = inv;
-            const double2 pr = prod_s;
-            double2 q = mk(fma(pr.x, pk.x, -pr.y * pk.y), fma(pr.x, pk.y, pr.y * pk.x));
-            // renormalise by the power of two of the larger component (exact)
-            const long long big = __double_as_longlong(fmax(fabs(q.x), fabs(q.y)));
-            const int e = (int)((big >> 52) & 0x7ff) - 1023;
-            if (e > -1000 && e < 1000) {
-              const double sc = __longlong_as_double((long long)(1023 - e) << 52);
-              q = mk(q.x * sc, q.y * sc);
-              exp_s += e;
-            }
-            prod_s = q;
+            pivv[k] = pk;
             if (bi != k) {
               swaps_s ^= 1;
               const int t = perm[k];
@@ -863,6 +893,19 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
       }
       continue;
     }
+    if (tid < 32) {   // det U = product of the pivots: butterfly with exact renormalisation
+      double2 q = tid < n ? pivv[tid] : mk(1.0, 0.0);
+      int e = 0;
+      for (int i = tid + 32; i < n; i += 32) q = cmul_renorm(q, pivv[i], &e);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double2 oq = mk(__shfl_xor_sync(0xffffffffu, q.x, o), __shfl_xor_sync(0xffffffffu, q.y, o));
+        const int oe = __shfl_xor_sync(0xffffffffu, e, o);
+        q = cmul_renorm(q, oq, &e);
+        e += oe;
+      }
+      if (tid == 0) { prod_s = q; exp_s = e; }
+    }
     for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each factor entry to R
       const int i = idx / n, j = idx % n;
       F[idx] = from_d2<R>(i == j ? dinv[i] : A[i * lda + j]);
@@ -874,13 +917,22 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
       auto at = [&](int k) -> R2& { return STAGE ? Y[(size_t)p * ldy + k] : thw[(size_t)perm[k] * N + p]; };
       if (!STAGE)
         for (int j = 0; j < n; ++j) at(j) = psw[(size_t)p * a.ncol + j];
-      for (int j = 0; j < n; ++j) {   // z U = psi_p
-        R sr = at(j).x, si = at(j).y;
-        for (int k = 0; k < j; ++k) {
-          const R2 z = at(k), u = F[k * n + j];
-          sr -= z.x * u.x - z.y * u.y;
-          si -= z.x * u.y + z.y * u.x;
+      for (int j = 0; j < n; ++j) {   // z U = psi_p (two independent partial sums)
+        R sr0 = at(j).x, si0 = at(j).y, sr1 = R(0), si1 = R(0);
+        int k = 0;
+        for (; k + 1 < j; k += 2) {
+          const R2 z0 = at(k), u0 = F[k * n + j], z1 = at(k + 1), u1 = F[(k + 1) * n + j];
+          sr0 -= z0.x * u0.x - z0.y * u0.y;
+          si0 -= z0.x * u0.y + z0.y * u0.x;
+          sr1 -= z1.x * u1.x - z1.y * u1.y;
+          si1 -= z1.x * u1.y + z1.y * u1.x;
         }
+        if (k < j) {
+          const R2 z0 = at(k), u0 = F[k * n + j];
+          sr0 -= z0.x * u0.x - z0.y * u0.y;
+          si0 -= z0.x * u0.y + z0.y * u0.x;
+        }
+        const R sr = sr0 + sr1, si = si0 + si1;
         const R2 d = F[j * n + j];
         R2 o;
         o.x = sr * d.x - si * d.y;
@@ -888,15 +940,23 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
         at(j) = o;
       }
       for (int j = n - 2; j >= 0; --j) {   // y L = z (unit lower L)
-        R sr = at(j).x, si = at(j).y;
-        for (int k = j + 1; k < n; ++k) {
-          const R2 z = at(k), l = F[k * n + j];
-          sr -= z.x * l.x - z.y * l.y;
-          si -= z.x * l.y + z.y * l.x;
+        R sr0 = at(j).x, si0 = at(j).y, sr1 = R(0), si1 = R(0);
+        int k = j + 1;
+        for (; k + 1 < n; k += 2) {
+          const R2 z0 = at(k), l0 = F[k * n + j], z1 = at(k + 1), l1 = F[(k + 1) * n + j];
+          sr0 -= z0.x * l0.x - z0.y * l0.y;
+          si0 -= z0.x * l0.y + z0.y * l0.x;
+          sr1 -= z1.x * l1.x - z1.y * l1.y;
+          si1 -= z1.x * l1.y + z1.y * l1.x;
+        }
+        if (k < n) {
+          const R2 z0 = at(k), l0 = F[k * n + j];
+          sr0 -= z0.x * l0.x - z0.y * l0.y;
+          si0 -= z0.x * l0.y + z0.y * l0.x;
         }
         R2 o;
-        o.x = sr;
-        o.y = si;
+        o.x = sr0 + sr1;
+        o.y = si0 + si1;
         at(j) = o;
       }
     }
