@@ -29,6 +29,7 @@ constexpr int kStageA = kBM * kBK * 2;           // 16 KiB
 
 struct Geom {
   int m_tiles, n_tiles, k_blocks;
+  int k_steps;              // 16-wide MMA k-steps with data (the last k-block may be partly past K)
   int m_step, n_step;       // TMA row coordinate of tile (mt, nt): mt * m_step, nt * n_step
   int bn;                   // MMA N
   int stages, epi_groups;
@@ -64,7 +65,10 @@ struct EpiSmem {
   int* ok;
 };
 
-__host__ __device__ __forceinline__ int exch_buf_bytes(int n) { return ((128 * (2 * n + 1) * 4) + 15) & ~15; }
+// Row pitch of the staged tile, >= 2n + 1 and = 1 (mod 32): thread r's row r and the partner rows
+// (g n + b) it reads at column a then fall in distinct banks for the 32 rows of a warp.
+__host__ __device__ __forceinline__ int exch_ld(int n) { return 32 * ((2 * n + 31) / 32) + 1; }
+__host__ __device__ __forceinline__ int exch_buf_bytes(int n) { return ((128 * exch_ld(n) * 4) + 15) & ~15; }
 
 __device__ __forceinline__ EpiSmem epi_smem(uint8_t* base, const Params& p, int group) {
   EpiSmem e;
@@ -109,7 +113,7 @@ __device__ __forceinline__ void tmem_row_to_smem(uint32_t taddr, int ncols, floa
 // then warp 0 of the group writes vbias for the tile's gammas and the exchange partial.
 __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
                               int wig, int r, int lane) {
-  const int n = p.n, n2 = 2 * n, ld = n2 + 1, rows = p.gpt * n;
+  const int n = p.n, n2 = 2 * n, ld = exch_ld(n), rows = p.gpt * n;
   const int bar_id = 1 + group;
   for (int v = group; v < p.wpt; v += p.g.epi_groups) {
     tmem_row_to_smem(tacc + (uint32_t)(v * n2), n2, e.buf + r * ld);
@@ -168,6 +172,122 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
   }
 }
 
+// NB consecutive accumulator columns of this thread's lane into v (no wait).
+template <int NB>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
+  static_assert(NB % 8 == 0 && NB <= 32, "column count");
+  if constexpr (NB >= 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+  }
+  if constexpr (NB == 32) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr + 16)
+        : "memory");
+  }
+  if constexpr (NB % 16 == 8) tmem_ld8_nowait(taddr + (NB - 8), v + (NB - 8));
+}
+
+// As exchange_tile, with the thread's own row T_ab (b < n <= NB) kept in registers: the real
+// parts come from columns [v 2n, v 2n + NB), the imaginary parts from [v 2n + n, v 2n + n + NB)
+// (the columns past the walker are read and ignored), and only the partner entries T_ba are
+// read back from shared memory.
+template <int NB>
+__device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
+                                  int wig, int r, int lane) {
+  const int n = p.n, n2 = 2 * n, ld = exch_ld(n), rows = p.gpt * n;
+  const int bar_id = 1 + group;
+  const int g = r / n, a = r - (r / n) * n;
+  const bool live = r < rows && mt * p.gpt + g < p.X;
+  float* rowp = e.buf + r * ld;
+  const float* blk = e.buf + (g * n) * ld;
+  for (int v = group; v < p.wpt; v += p.g.epi_groups) {
+    uint32_t ur[NB], ui[NB];
+    tmem_ld_cols<NB>(tacc + (uint32_t)(v * n2), ur);
+    tmem_ld_cols<NB>(tacc + (uint32_t)(v * n2 + n), ui);
+    tmem_wait();
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (b < n) {
+        rowp[b] = __uint_as_float(ur[b]);
+        rowp[n + b] = __uint_as_float(ui[b]);
+      }
+    named_bar(bar_id, 128);
+    float er0 = 0.f, ei0 = 0.f, er1 = 0.f, ei1 = 0.f;
+    float2 dg = make_float2(0.f, 0.f);
+    if (live) {
+#pragma unroll
+      for (int b = 0; b < NB; b += 2) {
+        if (b < n) {
+          const float tr = __uint_as_float(ur[b]), ti = __uint_as_float(ui[b]);
+          const float pr = blk[b * ld + a], pi = blk[b * ld + n + a];
+          er0 = fmaf(tr, pr, er0);
+          er0 = fmaf(-ti, pi, er0);
+          ei0 = fmaf(tr, pi, ei0);
+          ei0 = fmaf(ti, pr, ei0);
+        }
+        if (b + 1 < n) {
+          const float tr = __uint_as_float(ur[b + 1]), ti = __uint_as_float(ui[b + 1]);
+          const float pr = blk[(b + 1) * ld + a], pi = blk[(b + 1) * ld + n + a];
+          er1 = fmaf(tr, pr, er1);
+          er1 = fmaf(-ti, pi, er1);
+          ei1 = fmaf(tr, pi, ei1);
+          ei1 = fmaf(ti, pr, ei1);
+        }
+      }
+      dg = make_float2(rowp[a], rowp[n + a]);
+    }
+    e.diag[r] = dg;
+    float er = er0 + er1, ei = ei0 + ei1;
+    er = warp_sum_f(er);
+    ei = warp_sum_f(ei);
+    if (lane == 0) e.red[wig] = make_float2(er, ei);
+    named_bar(bar_id, 128);
+    const int w = nt * p.wpt + v;
+    if (w < p.W && wig == 0) {   // 4 lanes per gamma: strided partial sums of the diagonal, then 2 shuffles
+      for (int g0 = 0; p.vbias && g0 < p.gpt; g0 += 8) {
+        const int gl = g0 + (lane >> 2), part = lane & 3;
+        float sr = 0.f, si = 0.f;
+        if (gl < p.gpt)
+          for (int aa = part; aa < n; aa += 4) {
+            const float2 d = e.diag[gl * n + aa];
+            sr += d.x;
+            si += d.y;
+          }
+        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+        si += __shfl_xor_sync(0xffffffffu, si, 1);
+        sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+        si += __shfl_xor_sync(0xffffffffu, si, 2);
+        const int gam = mt * p.gpt + gl;
+        if (part == 0 && gl < p.gpt && gam < p.X) {
+          float2* dst = p.vbias + (size_t)w * p.X + gam;
+          float2 val = make_float2(p.smul * sr, p.smul * si);
+          if (p.vbias_add) {
+            val.x += dst->x;
+            val.y += dst->y;
+          }
+          *dst = val;
+        }
+      }
+      if (lane == 0) {
+        const float sr = (e.red[0].x + e.red[1].x) + (e.red[2].x + e.red[3].x);
+        const float si = (e.red[0].y + e.red[1].y) + (e.red[2].y + e.red[3].y);
+        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] =
+            make_double2((double)(p.smul * sr), (double)(p.smul * si));
+      }
+    }
+    // No barrier before the next walker: every partner read of buf happened before the barrier
+    // above, and e.diag / e.red are read by warp 0 before it reaches the next walker's barrier.
+  }
+}
+
 __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
   const int row = mt * p.g.m_step + r;
   const int c0 = nt * p.g.n_step;
@@ -216,7 +336,7 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
 }
 
 // ----------------------------------------------------------------------------- the kernel
-template <int EPI>
+template <int EPI, int NB = 0>
 __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                     const __grid_constant__ CUtensorMap mapB, const Params p) {
   extern __shared__ uint8_t smem_raw[];
@@ -294,7 +414,8 @@ __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUte
           const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes), sb = sa + kStageA;
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
-            umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
+            if (kb * (kBK / 16) + k < g.k_steps)
+              umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
           umma_commit(&empty[stage]);
           if (++stage == g.stages) { stage = 0; ph ^= 1u; }
         }
@@ -322,7 +443,8 @@ __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUte
       tc_fence_after();
       const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
       const int mt = t % g.m_tiles, nt = t / g.m_tiles;
-      if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
+      if constexpr (EPI == 0 && NB > 0) exchange_tile_reg<NB>(p, mt, nt, tacc, es, group, wig, r, lane);
+      else if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
       else if (EPI == 1) store_tile(p, mt, nt, tacc, group, r);
       else store_planes(p, mt, nt, tacc, group, r);
       tc_fence_before();
@@ -497,7 +619,7 @@ size_t smem_bytes(const Geom& g) {
   return 1024 + (size_t)g.stages * (kStageA + g.bn * kBK * 2) + (size_t)g.epi_groups * g.epi_bytes + 256;
 }
 
-template <int EPI>
+template <int EPI, int NB = 0>
 afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s,
                     unsigned long long* launches, char* err, size_t errlen) {
   const size_t sm = smem_bytes(g);
@@ -507,7 +629,7 @@ afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, c
   }
   const int tiles = g.m_tiles * g.n_tiles;
   const int grid = std::min(tiles, num_sms());
-  k_tc_gemm<EPI><<<grid, 64 + 128 * g.epi_groups, sm, s>>>(a, b, p);
+  k_tc_gemm<EPI, NB><<<grid, 64 + 128 * g.epi_groups, sm, s>>>(a, b, p);
   ++*launches;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -535,7 +657,7 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   st->prec = prec;
   st->W = W; st->N = N; st->X = X; st->ncol = ncol; st->nblk = nblk;
   st->nseg = prec == AFQMC_PREC_BF16X3 ? 3 : 1;
-  st->kst = (N + kBK - 1) / kBK * kBK;
+  st->kst = (N + 15) / 16 * 16;   // segments padded to the MMA k-step only; the last TMA box reads past K
   st->kx = (X + kBK - 1) / kBK * kBK;
   size_t cur = 0;
   st->nchunk = 0;
@@ -636,7 +758,11 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
   // reserve the kernels' shared memory now (not while a stream is being captured)
   if (cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+      cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
     snprintf(err, errlen, "tcgen05 GEMM: cannot reserve shared memory");
     return AFQMC_ECUDA;
   }
@@ -659,7 +785,8 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     Geom g{};
     g.m_tiles = bm.m_tiles;
     g.n_tiles = (nw + bm.wpt - 1) / bm.wpt;
-    g.k_blocks = st->nseg * st->kst / kBK;
+    g.k_blocks = (st->nseg * st->kst + kBK - 1) / kBK;
+    g.k_steps = st->nseg * st->kst / 16;
     g.m_step = bm.gpt * bm.n;
     g.n_step = bm.wpt * 2 * bm.n;
     g.bn = bm.bn;
@@ -676,7 +803,15 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     p.smul = (float)smul;
     p.vbias = vbias;
     p.exch_part = exch_part;
-    afqmc_status r = launch<0>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    // register-row epilogue when the imaginary-part loads of the last walker stay inside tensor memory
+    const int nb = (bm.n + 7) / 8 * 8;
+    const bool reg = nb <= 32 && g.bn + (bm.wpt - 1) * 2 * bm.n + bm.n + nb <= g.tmem_cols;
+    afqmc_status r;
+    if (!reg) r = launch<0>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    else if (nb == 8) r = launch<0, 8>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    else if (nb == 16) r = launch<0, 16>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    else if (nb == 24) r = launch<0, 24>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    else r = launch<0, 32>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
     if (r != AFQMC_OK) return r;
     chunk += bm.m_tiles;
     first = false;
@@ -697,6 +832,7 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   g.m_tiles = (st->N * st->N + kBM - 1) / kBM;
   g.n_tiles = (2 * st->W + 255) / 256;
   g.k_blocks = st->nseg * st->kx / kBK;
+  g.k_steps = st->nseg * st->kx / 16;
   g.m_step = kBM;
   g.n_step = 256;
   g.bn = 256;
@@ -724,6 +860,7 @@ afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, f
   g.m_tiles = st->vhs_m_tiles;
   g.n_tiles = st->vhs_n_tiles;
   g.k_blocks = st->nseg * st->kx / kBK;
+  g.k_steps = st->nseg * st->kx / 16;
   g.m_step = kBM;
   g.n_step = 256;
   g.bn = 256;
