@@ -168,13 +168,14 @@ def stage_rooflines(prec, norb, ncol, naux, nw, stages):
     anote = "nominal FP64 (recipe table)" if prec == "fp64" else "FP32 CUDA cores: 148 SM x 128 x 2 x 2.032 GHz"
     fl = step_flops_per_walker(norb, ncol, naux)
     n = ncol
-    gj_fp64 = 12 * n ** 3                               # Gauss-Jordan on [A | I] (binary64)
+    lu_fp64 = 8 * n ** 3 / 3                            # LU with partial pivoting, complex (binary64)
     work = {
         "exchange": (fl["exchange"] * nw, "tensor" if tensor else "alu", tpeak if tensor else alu,
                      tnote if tensor else anote),
-        "propagate": (fl["propagate"] * nw, "alu", alu, anote),
+        "propagate": (fl["propagate"] * nw, "tensor" if tensor else "alu", tpeak if tensor else alu,
+                      tnote if tensor else anote),
         "vhs": (fl["vhs"] * nw, "tensor" if tensor else "alu", tpeak if tensor else alu, tnote if tensor else anote),
-        "overlap": (gj_fp64 * nw, "alu", FP64_PEAK_TFLOPS, "nominal FP64 (recipe table); binary64 inverse work only"),
+        "overlap": (lu_fp64 * nw, "alu", FP64_PEAK_TFLOPS, "nominal FP64 (recipe table); binary64 LU work only"),
     }
     out = {}
     for k, (flops, bound, peak, note) in work.items():
@@ -260,7 +261,6 @@ def run_ours(args):
     per_step_flush = ws_bytes < 2 * L2_BYTES
     if world > 1:
         torch.distributed.barrier()
-    ctx.profile(True)
     l0 = ctx.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms = []
@@ -283,8 +283,13 @@ def run_ours(args):
             total_ms = ev0.elapsed_time(ev1)
         torch.cuda.synchronize(dev)
     launches = ctx.launch_count() - l0
+    # stage times from a separate pass with per-stage events (direct launches, no graph replay)
+    nprof = min(args.steps, 20)
+    ctx.profile(True)
+    ctx.run(nprof, WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+    torch.cuda.synchronize(dev)
     stages = ctx.stage_times()
-    stages["_steps"] = (args.steps, 1)
+    stages["_steps"] = (nprof, 1)
     ctx.profile(False)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -295,7 +300,7 @@ def run_ours(args):
     if args.skip_extras:
         ctx.close()
         return None if rank != 0 else {"value": value, "ms_per_step": total_ms / args.steps,
-                                       "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()
+                                       "stages_ms_per_step": {k: v[0] / nprof for k, v in stages.items()
                                                               if not k.startswith("_")}}
     fp64_form = None
     if rank == 0 and args.prec != "fp64":   # the plain FP64 form on the same workload (context for the ratio)
@@ -359,7 +364,9 @@ def run_ours(args):
                    "meets_0.1mHa": None if acc is None else bool(acc <= 1e-4)},
         "roofline": roof,
         "rooflines": rooflines,
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if not k.startswith("_")},
+        "stages_ms_per_step": {k: v[0] / nprof for k, v in stages.items() if not k.startswith("_")},
+        "stages_note": f"per-stage CUDA events over {nprof} separately run steps (direct launches); "
+                       "value and ms_per_step come from the graph-replayed timed region",
         "step_flops_per_walker": fl,
         "fp64_form": fp64_form,
         "clocks": clk.summary(),
@@ -500,7 +507,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
