@@ -240,6 +240,9 @@ struct afqmc_ctx {
   // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
   bool graphs_on = true;
   cudaStream_t cap_stream = nullptr;
+  // the tensor-core exchange draws the current step's normals into L.x with a spare warp (its
+  // binary64 work overlaps the contraction); the next fields kernel uses them instead of drawing
+  bool normals_pending = false;
   cudaGraphExec_t g_step[4] = {};       // bit 0: energy measured, bit 1: Theta refreshed first
   unsigned long long g_step_k[4] = {};
   cudaGraphExec_t g_qr = nullptr, g_comb[2] = {};
@@ -477,10 +480,12 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
   }
   StageTimer* tx = new StageTimer(c, AFQMC_STAGE_EXCHANGE);
   if (c->d.prec == AFQMC_PREC_BF16 || c->d.prec == AFQMC_PREC_BF16X3) {
+    tc::NormalsJob nj{c->at<double>(c->L.x), c->seed, c->at<unsigned long long>(c->L.step), c->d.W, c->d.X};
     if ((st = tc::exchange(&c->tcs, c->stream, c->at<char>(c->L.tc), c->smul, c->at<float2>(c->L.thetaT),
                            c->at<float2>(c->L.vbias), c->at<double2>(c->L.exch_part), c->at<int>(c->L.status),
-                           nullptr, c->d.W, &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
+                           nullptr, c->d.W, &c->launches, g_err, sizeof(g_err), &nj)) != AFQMC_OK)
       return st;
+    c->normals_pending = true;   // valid for the next step_impl while the step counter is unchanged
   } else {
     if ((st = launch_exchange<R>(c, 1)) != AFQMC_OK) return st;
   }
@@ -494,6 +499,16 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
   k_energy_sums<<<1, 256, 0, c->stream>>>(c->d.W, c->at<double>(c->L.w), c->at<double2>(c->L.eloc), sums_dev, slot);
   CHECK_LAUNCH(c);
   c->vbias_fresh = true;
+  return AFQMC_OK;
+}
+
+// Draws the current step's normals into L.x (unless the energy's tensor-core exchange already has).
+afqmc_status draw_normals(afqmc_ctx* c) {
+  const long long pairs = (long long)c->d.W * ((c->d.X + 1) / 2);
+  const int grid = (int)std::max(1LL, std::min<long long>(1LL << 20, (pairs + 127) / 128));
+  k_normals<<<grid, 128, 0, c->stream>>>(c->seed, c->at<unsigned long long>(c->L.step), c->d.W, c->d.X,
+                                         c->at<double>(c->L.x));
+  CHECK_LAUNCH(c);
   return AFQMC_OK;
 }
 
@@ -519,6 +534,8 @@ afqmc_status step_impl(afqmc_ctx* c) {
     }
   }
   StageTimer* tf = new StageTimer(c, AFQMC_STAGE_FIELDS);
+  if (!c->normals_pending && (st = draw_normals(c)) != AFQMC_OK) return st;
+  c->normals_pending = false;
   FieldArgs<R> fa{};
   fa.X = d.X; fa.sdt = c->sdt; fa.cap = c->cap; fa.seed = c->seed;
   fa.step = c->at<unsigned long long>(c->L.step);
@@ -840,6 +857,9 @@ afqmc_status capture_graph(afqmc_ctx* c, F body, cudaGraph_t* out, unsigned long
   const bool tf = c->theta_fresh, vf = c->vbias_fresh;
   const unsigned long long hs = c->host_step, l0 = c->launches;
   cudaStream_t user = c->stream;
+  // a captured step draws its normals unless the same capture's energy does (never from a flag
+  // left by earlier direct calls); after a replay no drawn normals are pending
+  c->normals_pending = false;
   CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   c->stream = c->cap_stream;
   afqmc_status st = body();
@@ -847,7 +867,7 @@ afqmc_status capture_graph(afqmc_ctx* c, F body, cudaGraph_t* out, unsigned long
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   *nkernels = c->launches - l0;
-  c->theta_fresh = tf; c->vbias_fresh = vf; c->host_step = hs; c->launches = l0;
+  c->theta_fresh = tf; c->vbias_fresh = vf; c->host_step = hs; c->launches = l0; c->normals_pending = false;
   if (st != AFQMC_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
   *out = graph;
@@ -880,6 +900,7 @@ afqmc_status graph_step(afqmc_ctx* c, bool energy) {
     if (st != AFQMC_OK) return st;
   }
   CU(cudaGraphLaunch(c->g_step[v], c->stream));
+  c->normals_pending = false;
   c->launches += c->g_step_k[v];
   c->theta_fresh = true;
   c->vbias_fresh = false;
@@ -893,6 +914,7 @@ afqmc_status graph_qr(afqmc_ctx* c) {
     if (st != AFQMC_OK) return st;
   }
   CU(cudaGraphLaunch(c->g_qr, c->stream));
+  c->normals_pending = false;
   c->launches += c->g_qr_k;
   c->theta_fresh = false;
   c->vbias_fresh = false;
@@ -906,6 +928,7 @@ afqmc_status graph_comb(afqmc_ctx* c) {
     if (st != AFQMC_OK) return st;
   }
   CU(cudaGraphLaunch(c->g_comb[v], c->stream));
+  c->normals_pending = false;
   c->launches += c->g_comb_k[v];
   c->theta_fresh = true;
   c->vbias_fresh = false;
@@ -1164,6 +1187,7 @@ afqmc_status afqmc_set_walkers(afqmc_ctx* ctx, const double* psi, const double* 
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->host_step = step;
   ctx->theta_fresh = false;
+  ctx->normals_pending = false;
   ctx->vbias_fresh = false;
   st = DISPATCH(ctx, launch_overlap, 0);
   if (st != AFQMC_OK) return st;
@@ -1635,6 +1659,7 @@ afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_ever
       c->launches += ex->nk[i];
       c->theta_fresh = ex->end_theta[i];
       c->vbias_fresh = ex->end_vbias[i];
+      c->normals_pending = false;
       c->host_step++;
     }
     if (energy) ++used;

@@ -331,23 +331,38 @@ struct FieldArgs {
   double2* xxbar;           // [W]
 };
 
+// The N(0,1) fields of every walker slot at the current step counter (stream 0) into x[w][g],
+// one thread per pair (2j, 2j+1), grid-stride.
+__global__ void __launch_bounds__(128) k_normals(unsigned long long seed, const unsigned long long* step, int W,
+                                                 int X, double* x) {
+  __shared__ SeriesTables tab;
+  if (threadIdx.x == 0) fill_series_tables(&tab);
+  __syncthreads();
+  const unsigned long long st = *step;
+  const int npairs = (X + 1) / 2;
+  const long long total = (long long)W * npairs;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(i / npairs), j = (int)(i - (long long)w * npairs);
+    double z0, z1;
+    normal_pair(seed, (uint32_t)j, (uint32_t)w, st, 0u, tab, &z0, &z1);
+    x[(size_t)w * X + 2 * j] = z0;
+    if (2 * j + 1 < X) x[(size_t)w * X + 2 * j + 1] = z1;
+  }
+}
+
+// Fields of one walker per CTA from the normals x[w][g] drawn by k_normals.
 template <typename R>
 __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
-  __shared__ SeriesTables tab;
   __shared__ double red[32];
   const int w = blockIdx.x, tid = threadIdx.x;
-  if (tid == 0) fill_series_tables(&tab);
-  __syncthreads();
-  const unsigned long long step = *a.step;
   double2 cm = mk(0.0, 0.0), xx = mk(0.0, 0.0);
   const int npairs = (a.X + 1) / 2;
   for (int j = tid; j < npairs; j += blockDim.x) {
-    double z[2];
-    normal_pair(a.seed, (uint32_t)j, (uint32_t)w, step, 0u, tab, &z[0], &z[1]);
     for (int t = 0; t < 2; ++t) {
       const int g = 2 * j + t;
       if (g >= a.X) break;
-      const double x = z[t];
+      const double x = a.x[(size_t)w * a.X + g];
       const double2 vb = to_d2(a.vbias[(size_t)w * a.X + g]);
       const double dre = vb.x - a.lbar[g], dim = vb.y;
       double2 xb = mk(a.sdt * dim, -a.sdt * dre);
@@ -363,7 +378,6 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
       const double l = a.lbar[g];
       cm = cadd(cm, mk(-a.sdt * l * xs.y, a.sdt * l * xs.x));
       xx = cadd(xx, mk(x * xb.x - 0.5 * (xb.x * xb.x - xb.y * xb.y), x * xb.y - xb.x * xb.y));
-      a.x[(size_t)w * a.X + g] = x;
       a.xbar[(size_t)w * a.X + g] = xb;
     }
   }

@@ -26,6 +26,7 @@ namespace afq {
 namespace tc {
 
 constexpr int kStageA = kBM * kBK * 2;           // 16 KiB
+constexpr int kTailBytes = 512;                  // mbarriers, TMEM slot, abort flag (< 256 B), then the series tables
 
 struct Geom {
   int m_tiles, n_tiles, k_blocks;
@@ -52,6 +53,8 @@ struct Params {
   // bf16 plane epilogue
   __nv_bfloat16* planes;
   int npad;
+  // exchange: an extra warp draws the step's normals (nrm.x != nullptr)
+  NormalsJob nrm;
 };
 
 
@@ -337,7 +340,7 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
 
 // ----------------------------------------------------------------------------- the kernel
 template <int EPI, int NB = 0>
-__global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                     const __grid_constant__ CUtensorMap mapB, const Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -423,6 +426,22 @@ __global__ void __launch_bounds__(576, 1) k_tc_gemm(const __grid_constant__ CUte
         umma_commit(&tfull[acc]);
       }
       if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else if (warp >= 2 + 4 * g.epi_groups) {   // spare warp: the step's normals (binary64 pipe)
+    if (EPI == 0 && p.nrm.x) {
+      SeriesTables& tab = *reinterpret_cast<SeriesTables*>(reinterpret_cast<uint8_t*>(bars) + 256);
+      if (lane == 0) fill_series_tables(&tab);
+      __syncwarp();
+      const unsigned long long st = *p.nrm.step;
+      const int npairs = (p.nrm.X + 1) / 2;
+      const long long total = (long long)p.nrm.W * npairs;
+      for (long long i = (long long)blockIdx.x * 32 + lane; i < total; i += (long long)gridDim.x * 32) {
+        const int w = (int)(i / npairs), j = (int)(i - (long long)w * npairs);
+        double z0, z1;
+        normal_pair(p.nrm.seed, (uint32_t)j, (uint32_t)w, st, 0u, tab, &z0, &z1);
+        p.nrm.x[(size_t)w * p.nrm.X + 2 * j] = z0;
+        if (2 * j + 1 < p.nrm.X) p.nrm.x[(size_t)w * p.nrm.X + 2 * j + 1] = z1;
+      }
     }
   } else {   // epilogue warps
     const int ew = warp - 2, group = ew >> 2, wig = ew & 3, q = warp & 3;
@@ -606,7 +625,7 @@ bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
   g->epi_groups = epi_groups;
   g->epi_bytes = (epi_bytes_per_group + 15) & ~15;
   const int stage_bytes = kStageA + g->bn * kBK * 2;
-  const int fixed = 1024 + epi_groups * g->epi_bytes + 256;
+  const int fixed = 1024 + epi_groups * g->epi_bytes + kTailBytes;
   int st = (kMaxSmem - fixed) / stage_bytes;
   if (st > 4) st = 4;
   if (st < 2) return false;
@@ -616,7 +635,7 @@ bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
 }
 
 size_t smem_bytes(const Geom& g) {
-  return 1024 + (size_t)g.stages * (kStageA + g.bn * kBK * 2) + (size_t)g.epi_groups * g.epi_bytes + 256;
+  return 1024 + (size_t)g.stages * (kStageA + g.bn * kBK * 2) + (size_t)g.epi_groups * g.epi_bytes + kTailBytes;
 }
 
 template <int EPI, int NB = 0>
@@ -629,7 +648,7 @@ afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, c
   }
   const int tiles = g.m_tiles * g.n_tiles;
   const int grid = std::min(tiles, num_sms());
-  k_tc_gemm<EPI, NB><<<grid, 64 + 128 * g.epi_groups, sm, s>>>(a, b, p);
+  k_tc_gemm<EPI, NB><<<grid, 64 + 128 * g.epi_groups + (p.nrm.x ? 32 : 0), sm, s>>>(a, b, p);
   ++*launches;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -646,7 +665,7 @@ int exchange_groups(int n, int wpt) {
   const int bn = (wpt * 2 * n + 15) / 16 * 16;
   const int stage_bytes = kStageA + bn * kBK * 2;
   for (int g = std::min(4, wpt); g > 1; --g) {
-    const int need = 1024 + g * ((epi_bytes_exchange(n) + 15) & ~15) + 256 + 2 * stage_bytes;
+    const int need = 1024 + g * ((epi_bytes_exchange(n) + 15) & ~15) + kTailBytes + 2 * stage_bytes;
     if (need <= kMaxSmem) return g;
   }
   return 1;
@@ -772,7 +791,7 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
 
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
                       double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
-                      char* err, size_t errlen) {
+                      char* err, size_t errlen, const NormalsJob* nj) {
   int chunk = 0;
   bool first = true;
   if (nw <= 0) return AFQMC_OK;
@@ -803,6 +822,7 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     p.smul = (float)smul;
     p.vbias = vbias;
     p.exch_part = exch_part;
+    if (first && nj) p.nrm = *nj;
     // register-row epilogue when the imaginary-part loads of the last walker stay inside tensor memory
     const int nb = (bm.n + 7) / 8 * 8;
     const bool reg = nb <= 32 && g.bn + (bm.wpt - 1) * 2 * bm.n + bm.n + nb <= g.tmem_cols;

@@ -71,13 +71,23 @@ int set_exchange_groups(TcState* st, char* tcbuf, int groups);
 afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* chol64, const double* lrot64,
                      unsigned long long* launches, char* err, size_t errlen);
 
+// N(0,1) fields of the step counter *step (stream 0) for W walker slots x X into x[w][g]; drawn by
+// a spare warp of the exchange kernel, whose binary64 pipe is otherwise idle.
+struct NormalsJob {
+  double* x;
+  unsigned long long seed;
+  const unsigned long long* step;
+  int W, X;
+};
+
 // vbias[w][g] = smul sum_s Tr T^{g s}, exch_part[w][chunk] = smul sum over the chunk's gammas of
 // sum_ab T_ab T_ba, with T^{g s} = Ltilde^{g s} Theta^s; Theta^T complex64 [W][ncol][N].
 // widx (optional, nw entries): the kernel works on walkers widx[0..nw) and writes their partials
 // to rows 0..nw of exch_part; vbias may be NULL (not written).
+// nj (optional): the first launch also draws those normals.
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
                       double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
-                      char* err, size_t errlen);
+                      char* err, size_t errlen, const NormalsJob* nj = nullptr);
 
 // VHS planar fp32: out[w][0][pq] + i out[w][1][pq] = sum_g coef[w][g] L^g_pq, coef complex64 [W][X].
 afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, float* out, int* status,

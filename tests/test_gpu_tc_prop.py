@@ -99,3 +99,28 @@ def test_tensor_core_propagation_skips_frozen_walkers():
     for i in (0, 3, 148, 149):
         assert w_g[i] == 0.0 and np.array_equal(psi_g[i], psi[i].astype(np.complex64))
     assert not np.allclose(psi_g[1], psi[1], atol=1e-6)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_fields_drawn_by_the_exchange_warp_are_bit_exact(graphs):
+    """With the energy measured, the tensor-core exchange's spare warp draws the step's normals;
+    they must equal the oracle's Philox / Box-Muller draws bit for bit, as must the normals that a
+    step without an energy draws itself (direct launches and CUDA-graph replays alike)."""
+    from oracle import philox
+    prob = config_small()
+    nw, seed = 24, 77
+    ctx = pkg.Afqmc(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, nwalkers=nw, dt=0.01,
+                    seed=seed, prec="bf16x3")
+    ctx.set_graphs(graphs)
+    for steps, energy_every in ((1, 1), (1, 0), (3, 2), (2, 1)):
+        step0 = ctx.get_walkers()[3]
+        ctx.run(steps, energy_every, 0, 0)
+        x, _ = ctx.get_fields()
+        ref = philox.normals(seed, step0 + steps - 1, nw, prob.naux)
+        assert np.array_equal(x.view(np.uint64), ref.view(np.uint64)), (steps, energy_every)
+    ctx.local_energy()          # draws the normals of the current step ...
+    step0 = ctx.get_walkers()[3]
+    ctx.propagate(1)            # ... which this step uses
+    x, _ = ctx.get_fields()
+    assert np.array_equal(x.view(np.uint64), philox.normals(seed, step0, nw, prob.naux).view(np.uint64))
+    ctx.close()
