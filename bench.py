@@ -467,6 +467,9 @@ def run_cv(args):
             "forms": out}
 
 
+REF_BUDGET_S = 150.0
+
+
 def run_reference(args):
     """The oracle arm: the FP64 CPU oracle on the same workload, a bounded walker sample per step."""
     rank, world, _ = dist_env()
@@ -475,9 +478,16 @@ def run_reference(args):
     from oracle import afqmc as orc
     prob = make_problem()
     st = orc.build_setup(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, WORKLOAD["dt"])
-    nw = args.ref_walkers
-    wk = orc.init_walkers(st, prob.psiT, nw)
     seed = 240616238
+    # walker sample per step: at most --ref-walkers, fewer when --steps is large, so that the whole
+    # run stays within about REF_BUDGET_S seconds (calibrated on one step of two walkers)
+    cal = orc.init_walkers(st, prob.psiT, 2)
+    t0 = time.perf_counter()
+    orc.energy_sums(st, cal)
+    orc.phaseless_step(st, cal, seed, st.evar)
+    per_walker = (time.perf_counter() - t0) / 2
+    nw = int(max(1, min(args.ref_walkers, REF_BUDGET_S / max(1e-9, per_walker * (args.steps + args.warmup)))))
+    wk = orc.init_walkers(st, prob.psiT, nw)
 
     def one():
         orc.energy_sums(st, wk)
@@ -507,7 +517,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 2000 for the medium workload, 50 for batched and cv)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
@@ -521,6 +532,8 @@ def main():
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the steps only (no accuracy check, e2e or CPU baseline), e.g. under ncu")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 2000 if args.workload == "medium" and args.impl == "ours" else 50
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

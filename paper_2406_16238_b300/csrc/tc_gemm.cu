@@ -52,7 +52,7 @@ struct Params {
   int out_rows, out_cols;
   // bf16 plane epilogue
   __nv_bfloat16* planes;
-  int npad;
+  int npad, kq;   // plane rows, plane row pitch (elements)
   // exchange: an extra warp draws the step's normals (nrm.x != nullptr)
   NormalsJob nrm;
 };
@@ -313,7 +313,7 @@ __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int g
 
 // Tile rows are pq = p N + q (M over N^2), columns are (w, part) = 2 w + part.  Each value is
 // split into hi = bf16(v), lo = bf16(v - hi) and written to the plane
-// [w][hi re, hi im, lo re, lo im][npad][128] at (p, q).  Consecutive lanes hold consecutive pq,
+// [w][hi re, hi im, lo re, lo im][npad][kq] at (p, q).  Consecutive lanes hold consecutive pq,
 // so every store instruction covers a contiguous run of q.
 __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
   const int pq = mt * kBM + r;
@@ -321,7 +321,7 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
   const int pp = live ? pq / p.n : 0, qq = live ? pq - pp * p.n : 0;
   const int ncols = p.g.bn / p.g.epi_groups;
   const int cbeg = group * ncols;
-  const size_t plane = (size_t)p.npad * 128;
+  const size_t plane = (size_t)p.npad * p.kq;
   float v[16];
   for (int c = cbeg; c < cbeg + ncols; c += 16) {
     tmem_ld16(tacc + (uint32_t)c, v);
@@ -330,7 +330,7 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
     for (int i = 0; i < 16; ++i) {
       const int col = nt * p.g.n_step + c + i;
       if (col >= p.out_rows) break;
-      __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * 128 + qq;
+      __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * p.kq + qq;
       const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
       dst[0] = hi;
       dst[2 * plane] = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
@@ -706,10 +706,19 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   st->vhs_n_tiles = (N * N + 255) / 256;
   st->pg = prop_geom(N, ncol);
   if (st->pg.ok) {
+    const PropGeom& pg = st->pg;
     st->off_vp = cur;
-    cur = align256(cur + (size_t)W * 4 * st->pg.npad * 128 * 2);
+    cur = align256(cur + (size_t)W * 4 * pg.npad * pg.kq * 2);
     st->off_fp = cur;
-    cur = align256(cur + (size_t)2 * st->pg.npad * 128 * 2);
+    cur = align256(cur + (size_t)2 * pg.npad * pg.kq * 2);
+    if (pg.large) {   // term operands (two, ping-pong) and the Taylor sum
+      for (int i = 0; i < 2; ++i) {
+        st->off_b[i] = cur;
+        cur = align256(cur + (size_t)W * 2 * (2 * pg.ncolp) * (2 * pg.kq) * 2);
+      }
+      st->off_acc = cur;
+      cur = align256(cur + (size_t)W * pg.npad * pg.ncolp * 8);
+    }
   }
   return cur;
 }
@@ -868,6 +877,7 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   p.out_cols = st->N * st->N;
   p.planes = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_vp);
   p.npad = st->pg.npad;
+  p.kq = st->pg.kq;
   return launch<2>(g, st->map_lt_a, st->map_coef_b, p, s, launches, err, errlen);
 }
 

@@ -32,7 +32,11 @@ struct BlockMaps {
 // (4 atoms of 2 cwp rows) | mbarriers.
 struct PropGeom {
   int ok = 0;
+  int large = 0;       // 1: N > 128, the batched form (V streamed per product, one launch per product)
   int npad = 0;        // N rounded up to 8: rows of the V and F planes
+  int kq = 0;          // row pitch of the planes: 128 (N <= 128) or N rounded up to 64
+  int ncolp = 0;       // large form: walker columns rounded up to 8 (B operand rows 2 ncolp)
+  int mtiles = 0;      // large form: 128-row tiles per walker
   int nk = 0;          // 16-wide k-steps per K half, ceil(N / 16)
   int cw = 0, cwp = 0; // columns per chunk and its padding to a multiple of 8
   int nch = 0;         // chunks per walker
@@ -54,8 +58,10 @@ struct TcState {
   CUtensorMap map_lt, map_coef;
   // tensor-core propagation
   PropGeom pg;
-  size_t off_vp = 0, off_fp = 0;   // V planes [W][4][npad][128], F planes [2][npad][128] (bf16)
-  CUtensorMap map_vp, map_fp, map_lt_a, map_coef_b;
+  size_t off_vp = 0, off_fp = 0;   // V planes [W][4][npad][kq], F planes [2][npad][kq] (bf16)
+  size_t off_b[2] = {0, 0};        // large form: term operands [W][hi, lo][2 ncolp][2 kq] (bf16)
+  size_t off_acc = 0;              // large form: Taylor sum [W][npad][ncolp] complex64
+  CUtensorMap map_vp, map_fp, map_lt_a, map_coef_b, map_b[2];
   bool ready = false;
 };
 

@@ -329,11 +329,258 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
 
-// F = E_h - I (binary64 [N][N]) -> planes [hi, lo][npad][128], zero outside N x N.
-__global__ void k_f_planes(int N, int npad, const double* f64, __nv_bfloat16* out) {
-  const int per = npad * 128;
+// ---------------------------------------------------------------------------------------------
+// Large form (N > 128): one launch per product over all (walker, 128-row tile) pairs.  A is the
+// walker's V (K = Re V | Im V) or F, streamed through a ring of TMA stages; B is the current term
+// as split bf16 [hi, lo][2 ncolp rows][2 kq] (rows: real parts, then imaginary parts; K halves as
+// in the fused kernel).  The epilogue (4 warps, thread = row p) adds the product to the Taylor
+// sum acc [W][npad][ncolp] (complex64), writes the next term operand (column k = p of its rows,
+// consecutive lanes on consecutive addresses), and the last product writes psi.
+// mode 0: D = F psi, t_0 = psi + D;  mode k = 1..order: D = V t_{k-1} / k = t_k;
+// mode order + 1: D = F acc, psi = acc + D.
+struct PropGemmParams {
+  int N, npad, kq, nq, ncol, ncolp, bn, mtiles, W, order, mode, stages;
+  float2* psi;
+  const double* w;
+  float2* acc;
+  __nv_bfloat16* bnext;   // next term operand, [W][2][bn][2 kq]
+  int* status;
+};
+
+__device__ __forceinline__ int prop_kblocks(const PropGemmParams& a) {
+  const bool fmode = a.mode == 0 || a.mode == a.order + 1;
+  return 3 * (fmode ? 1 : 2) * a.nq;
+}
+
+// TMA coordinates and k-steps of k-block j of tile (wk, mt): segments (A hi, B hi), (A lo, B hi),
+// (A hi, B lo); V products run over two K halves (Re V against the first half of B, Im V against
+// the second).
+__device__ __forceinline__ void prop_kblock(const PropGemmParams& a, int wk, int mt, int j, int* ax, int* ay, int* bx,
+                                            int* by, int* ksteps) {
+  const bool fmode = a.mode == 0 || a.mode == a.order + 1;
+  const int halves = fmode ? 1 : 2;
+  const int seg = j / (halves * a.nq), h = (j / a.nq) % halves, qb = j % a.nq;
+  const int alo = seg == 1 ? 1 : 0, blo = seg == 2 ? 1 : 0;
+  *ax = qb * 64;
+  *ay = fmode ? alo * a.npad + mt * 128 : (wk * 4 + 2 * alo + h) * a.npad + mt * 128;
+  *bx = h * a.kq + qb * 64;
+  *by = (wk * 2 + blo) * a.bn;
+  *ksteps = min(4, (a.N - qb * 64 + 15) / 16);
+}
+
+__global__ void __launch_bounds__(192, 1) k_prop_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                      const __grid_constant__ CUtensorMap mapB,
+                                                      const PropGemmParams a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int stage_bytes = 16384 + a.bn * 128;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)a.stages * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + a.stages;
+  uint64_t* tfull = bars + 2 * a.stages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = a.W * a.mtiles, nkb = prop_kblocks(a);
+  const int tmem_cols = 2 * a.bn <= 32 ? 32 : (2 * a.bn <= 64 ? 64 : (2 * a.bn <= 128 ? 128 : (2 * a.bn <= 256 ? 256 : 512)));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {   // TMA producer
+      int stage = 0;
+      uint32_t ph = 0;
+      bool go = true;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
+        const int wk = t / a.mtiles, mt = t % a.mtiles;
+        if (a.w[wk] == 0.0) continue;
+        for (int j = 0; j < nkb; ++j) {
+          int ax, ay, bx, by, ks;
+          prop_kblock(a, wk, mt, j, &ax, &ay, &bx, &by, &ks);
+          if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
+          uint8_t* sa = smem + (size_t)stage * stage_bytes;
+          mbar_expect_tx(&full[stage], (uint32_t)stage_bytes);
+          tma_load_2d(sa, &mapA, &full[stage], ax, ay);
+          tma_load_2d(sa + 16384, &mapB, &full[stage], bx, by);
+          if (++stage == a.stages) { stage = 0; ph ^= 1u; }
+        }
+      }
+      if (!go) { atomicOr(a.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      int stage = 0;
+      uint32_t ph = 0;
+      int it = 0;
+      bool go = true;
+      const uint32_t idesc = idesc_bf16(a.bn);
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
+        const int wk = t / a.mtiles;
+        if (a.w[wk] == 0.0) continue;
+        const int acc = it & 1;
+        const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+        ++it;
+        if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { go = false; break; }
+        tc_fence_after();
+        const uint32_t dtm = tmem + (uint32_t)(acc * a.bn);
+        bool first = true;
+        for (int j = 0; j < nkb; ++j) {
+          int ax, ay, bx, by, ks;
+          prop_kblock(a, wk, t % a.mtiles, j, &ax, &ay, &bx, &by, &ks);
+          if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes), sb = sa + 16384;
+          for (int k = 0; k < ks; ++k) {
+            umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, first ? 0u : 1u);
+            first = false;
+          }
+          umma_commit(&empty[stage]);
+          if (++stage == a.stages) { stage = 0; ph ^= 1u; }
+        }
+        if (!go) break;
+        umma_commit(&tfull[acc]);
+      }
+      if (!go) { atomicOr(a.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else {   // epilogue: warps 2-5, lane quadrant warp % 4
+    const int q = warp & 3;
+    int it = 0;
+    const float s = (a.mode >= 1 && a.mode < a.order) ? 1.f / (float)(a.mode + 1) : 1.f;
+    const size_t kk2 = (size_t)2 * a.kq;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int wk = t / a.mtiles, mt = t % a.mtiles;
+      if (a.w[wk] == 0.0) continue;
+      const int acc = it & 1;
+      const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+      ++it;
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(&tfull[acc], aph, abort_flag) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) { atomicOr(a.status, kStatusTimeout); *abort_flag = 1; }
+        break;
+      }
+      tc_fence_after();
+      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * a.bn);
+      const int p = mt * 128 + 32 * q + lane;
+      const bool row = p < a.N, kpad = p < a.kq;
+      float2* accrow = a.acc + ((size_t)wk * a.npad + (row ? p : 0)) * a.ncolp;
+      float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol;
+      __nv_bfloat16* bw = a.bnext + (size_t)wk * 2 * a.bn * kk2;
+      for (int c0 = 0; c0 < a.ncolp; c0 += 8) {
+        uint32_t ur[8], ui[8];
+        tmem_ld8_nowait(trow + (uint32_t)c0, ur);
+        tmem_ld8_nowait(trow + (uint32_t)(a.ncolp + c0), ui);
+        tmem_wait();
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int c = c0 + jj;
+          float2 d = make_float2(__uint_as_float(ur[jj]), __uint_as_float(ui[jj]));
+          float2 u = make_float2(0.f, 0.f);   // next operand entry
+          bool both = true;
+          if (row) {
+            if (a.mode == 0) {
+              const float2 ps = c < a.ncol ? prow[c] : make_float2(0.f, 0.f);
+              u = make_float2(ps.x + d.x, ps.y + d.y);
+              accrow[c] = u;
+            } else if (a.mode <= a.order) {
+              float2 sum = accrow[c];
+              sum.x += d.x;
+              sum.y += d.y;
+              accrow[c] = sum;
+              if (a.mode < a.order) {
+                u = make_float2(d.x * s, d.y * s);
+              } else {
+                u = sum;
+                both = false;
+              }
+            } else {
+              const float2 sum = accrow[c];
+              if (c < a.ncol) prow[c] = make_float2(sum.x + d.x, sum.y + d.y);
+            }
+          }
+          if (a.mode <= a.order && kpad) {
+            const __nv_bfloat16 rh = __float2bfloat16_rn(u.x), ih = __float2bfloat16_rn(u.y);
+            const __nv_bfloat16 rl = __float2bfloat16_rn(u.x - __bfloat162float(rh));
+            const __nv_bfloat16 il = __float2bfloat16_rn(u.y - __bfloat162float(ih));
+            __nv_bfloat16* hre = bw + (size_t)c * kk2;                 // row c (real parts)
+            __nv_bfloat16* him = bw + (size_t)(a.ncolp + c) * kk2;     // row ncolp + c (imaginary parts)
+            const size_t lo = (size_t)a.bn * kk2;                      // the lo plane
+            hre[p] = rh; hre[lo + p] = rl;
+            him[p] = ih; him[lo + p] = il;
+            if (both) {
+              hre[a.kq + p] = __hneg(ih); hre[lo + a.kq + p] = __hneg(il);
+              him[a.kq + p] = rh;         him[lo + a.kq + p] = rl;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) {   // let in-flight copies and MMAs drain before freeing tensor memory
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < 2000000ull) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// First operand of the large form: psi of every walker as split bf16 rows (real parts, then
+// imaginary parts) over the first K half; K positions N .. kq - 1 and padding columns are zero.
+__global__ void k_psi_to_b(int W, int N, int ncol, int ncolp, int kq, const float2* psi, __nv_bfloat16* b) {
+  const int bn = 2 * ncolp;
+  const size_t kk2 = (size_t)2 * kq;
+  const size_t total = (size_t)W * ncolp * kq;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(idx % kq);
+    const size_t r = idx / kq;
+    const int c = (int)(r % ncolp);
+    const int wk = (int)(r / ncolp);
+    float2 v = make_float2(0.f, 0.f);
+    if (p < N && c < ncol) v = psi[((size_t)wk * N + p) * ncol + c];
+    const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+    __nv_bfloat16* bw = b + (size_t)wk * 2 * bn * kk2;
+    const size_t lo = (size_t)bn * kk2;
+    bw[(size_t)c * kk2 + p] = rh;
+    bw[lo + (size_t)c * kk2 + p] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+    bw[(size_t)(ncolp + c) * kk2 + p] = ih;
+    bw[lo + (size_t)(ncolp + c) * kk2 + p] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+  }
+}
+
+// F = E_h - I (binary64 [N][N]) -> planes [hi, lo][npad][kq], zero outside N x N.
+__global__ void k_f_planes(int N, int npad, int kq, const double* f64, __nv_bfloat16* out) {
+  const int per = npad * kq;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * per; idx += gridDim.x * blockDim.x) {
-    const int pl = idx / per, rem = idx % per, p = rem / 128, q = rem % 128;
+    const int pl = idx / per, rem = idx % per, p = rem / kq, q = rem % kq;
     const double v = (p < N && q < N) ? f64[(size_t)p * N + q] : 0.0;
     const __nv_bfloat16 hi = __double2bfloat16(v);
     out[idx] = pl ? __double2bfloat16(v - (double)__bfloat162float(hi)) : hi;
@@ -356,9 +603,22 @@ afqmc_status launch_prop(const TcState* st, cudaStream_t s, const PropTcParams& 
 
 }  // namespace
 
+int prop_gemm_stages(int bn) { return std::min(6, (kMaxSmem - 1024 - 256) / (16384 + bn * 128)); }
+size_t prop_gemm_smem(int bn) { return 1024 + (size_t)prop_gemm_stages(bn) * (16384 + bn * 128) + 256; }
+
 PropGeom prop_geom(int N, int ncol) {
   PropGeom g{};
-  if (N < 1 || N > 128 || ncol < 1) return g;
+  if (N < 1 || ncol < 1) return g;
+  if (N > 128) {   // large form
+    if (ncol > 128) return g;
+    g.large = 1;
+    g.npad = (N + 7) / 8 * 8;
+    g.kq = (N + 63) / 64 * 64;
+    g.ncolp = (ncol + 7) / 8 * 8;
+    g.mtiles = (N + 127) / 128;
+    g.ok = prop_gemm_stages(2 * g.ncolp) >= 2 ? 1 : 0;
+    return g;
+  }
   const int npad = (N + 7) / 8 * 8;
   for (int cwmax : {32, 24, 16, 8}) {
     const int nch = (ncol + cwmax - 1) / cwmax;
@@ -366,6 +626,7 @@ PropGeom prop_geom(int N, int ncol) {
     const int cwp = (cw + 7) / 8 * 8;
     PropGeom t{};
     t.npad = npad;
+    t.kq = 128;
     t.nk = (N + 15) / 16;
     t.cw = cw;
     t.cwp = cwp;
@@ -394,16 +655,33 @@ afqmc_status prepare_prop(TcState* st, cudaStream_t s, char* tcbuf, const double
   const PropGeom& g = st->pg;
   __nv_bfloat16* vp = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_vp);
   __nv_bfloat16* fp = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_fp);
-  if (cudaMemsetAsync(vp, 0, (size_t)st->W * 4 * g.npad * 128 * 2, s) != cudaSuccess) {
+  if (cudaMemsetAsync(vp, 0, (size_t)st->W * 4 * g.npad * g.kq * 2, s) != cudaSuccess) {
     snprintf(err, errlen, "tensor-core propagation: clearing the V planes failed");
     return AFQMC_ECUDA;
   }
-  k_f_planes<<<64, 256, 0, s>>>(st->N, g.npad, f64, fp);
+  k_f_planes<<<64, 256, 0, s>>>(st->N, g.npad, g.kq, f64, fp);
   ++*launches;
-  if (!make_map(&st->map_vp, vp, (unsigned long long)st->W * 4 * g.npad, 128, (unsigned)g.npad) ||
-      !make_map(&st->map_fp, fp, (unsigned long long)2 * g.npad, 128, (unsigned)g.npad)) {
+  const unsigned box = g.large ? 128u : (unsigned)g.npad;   // one 128-row tile, or every row
+  if (!make_map(&st->map_vp, vp, (unsigned long long)st->W * 4 * g.npad, g.kq, box) ||
+      !make_map(&st->map_fp, fp, (unsigned long long)2 * g.npad, g.kq, box)) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the propagation planes");
     return AFQMC_ECUDA;
+  }
+  if (g.large) {
+    for (int i = 0; i < 2; ++i) {
+      void* b = tcbuf + st->off_b[i];
+      const size_t bytes = (size_t)st->W * 2 * (2 * g.ncolp) * (2 * g.kq) * 2;
+      if (cudaMemsetAsync(b, 0, bytes, s) != cudaSuccess ||
+          !make_map(&st->map_b[i], b, (unsigned long long)st->W * 2 * 2 * g.ncolp, 2ull * g.kq,
+                    (unsigned)(2 * g.ncolp))) {
+        snprintf(err, errlen, "tensor-core propagation: term operand buffers");
+        return AFQMC_ECUDA;
+      }
+    }
+    if (cudaFuncSetAttribute(k_prop_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+      snprintf(err, errlen, "tensor-core propagation: cannot reserve shared memory");
+      return AFQMC_ECUDA;
+    }
   }
   const void* fns[4] = {reinterpret_cast<const void*>(k_prop_tc<8>), reinterpret_cast<const void*>(k_prop_tc<16>),
                         reinterpret_cast<const void*>(k_prop_tc<24>), reinterpret_cast<const void*>(k_prop_tc<32>)};
@@ -427,6 +705,32 @@ afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, floa
   if (!g.ok) {
     snprintf(err, errlen, "tensor-core propagation is not available for this problem");
     return AFQMC_EINVAL;
+  }
+  if (g.large) {
+    __nv_bfloat16* b[2] = {reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_b[0]),
+                           reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_b[1])};
+    k_psi_to_b<<<1184, 256, 0, s>>>(st->W, st->N, st->ncol, g.ncolp, g.kq, psi, b[0]);
+    ++*launches;
+    PropGemmParams q{};
+    q.N = st->N; q.npad = g.npad; q.kq = g.kq; q.nq = g.kq / 64; q.ncol = st->ncol; q.ncolp = g.ncolp;
+    q.bn = 2 * g.ncolp; q.mtiles = g.mtiles; q.W = st->W; q.order = order;
+    q.stages = prop_gemm_stages(q.bn);
+    q.psi = psi; q.w = w; q.acc = reinterpret_cast<float2*>(tcbuf + st->off_acc); q.status = status;
+    const int grid = std::min(st->W * g.mtiles, num_sms());
+    const size_t smem = prop_gemm_smem(q.bn);
+    for (int m = 0; m <= order + 1; ++m) {   // operand m % 2 in, (m + 1) % 2 out
+      q.mode = m;
+      q.bnext = b[(m + 1) % 2];
+      const bool fmode = m == 0 || m == order + 1;
+      k_prop_gemm<<<grid, 192, smem, s>>>(fmode ? st->map_fp : st->map_vp, st->map_b[m % 2], q);
+      ++*launches;
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        snprintf(err, errlen, "tensor-core propagation launch: %s", cudaGetErrorString(e));
+        return AFQMC_ECUDA;
+      }
+    }
+    return AFQMC_OK;
   }
   PropTcParams p{};
   p.N = st->N; p.npad = g.npad; p.nk = g.nk; p.ncol = st->ncol; p.cw = g.cw; p.nch = g.nch;

@@ -6,7 +6,8 @@ exp(-dt/2 h_eff) Taylor_6(VHS) exp(-dt/2 h_eff) on x - x̄ (Eq. 8).  The GPU bui
 every product from split-bf16 operands (about 16 significant bits per product, fp32
 accumulation), so ψ agrees to a few parts in 1e6 of its largest entry; plain BF16 builds VHS
 from single bf16 operands (8 bits) and is held to 5e-3.  Shapes cover one column chunk, several
-chunks, N not a multiple of 8 or 16, nbeta = 0 and N = 128 (the largest the kernel takes).
+chunks, N not a multiple of 8 or 16, nbeta = 0 and N = 128 (the largest the fused kernel takes);
+N = 150, 200, 300 run the batched form (two or three 128-row tiles per walker).
 """
 import numpy as np
 import pytest
@@ -27,6 +28,10 @@ CASES = {
     "uhf_N64_40_30": lambda: make_problem(64, 40, 30, 96, 12.0, 44, unrestricted=True),  # 3 chunks
     "rhf_N108": lambda: config_medium(),
     "uhf_N128_9_7": lambda: make_problem(128, 9, 7, 160, 10.0, 45, unrestricted=True),
+    # N > 128: the batched form (V streamed, one launch per product)
+    "rhf_N150_12": lambda: make_problem(150, 12, 12, 300, 15.0, 46),
+    "uhf_N200_20_16": lambda: make_problem(200, 20, 16, 400, 20.0, 47, unrestricted=True),
+    "rhf_N300_25": lambda: make_problem(300, 25, 25, 600, 60.0, 48),
 }
 
 
@@ -87,8 +92,9 @@ def test_propagation_paths_agree(path):
     assert np.max(np.abs(out[path] - out[1])) < 2e-5 * scale
 
 
-def test_tensor_core_propagation_skips_frozen_walkers():
-    prob = config_medium()
+@pytest.mark.parametrize("large", [False, True])
+def test_tensor_core_propagation_skips_frozen_walkers(large):
+    prob = make_problem(150, 12, 12, 300, 15.0, 46) if large else config_medium()
     nw = 150   # more walkers than SMs: some CTAs take a second walker after a frozen one
     psi, w = _state(prob, nw, seed=10)
     w[[0, 3, 148, 149]] = 0.0
