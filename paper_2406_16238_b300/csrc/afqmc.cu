@@ -243,8 +243,9 @@ struct afqmc_ctx {
   // the tensor-core exchange draws the current step's normals into L.x with a spare warp (its
   // binary64 work overlaps the contraction); the next fields kernel uses them instead of drawing
   bool normals_pending = false;
-  cudaGraphExec_t g_step[4] = {};       // bit 0: energy measured, bit 1: Theta refreshed first
-  unsigned long long g_step_k[4] = {};
+  bool thb_valid = false;    // the bf16 Theta^T exchange operand (tensor forms) matches Theta^T
+  cudaGraphExec_t g_step[8] = {};       // bit 0: energy measured, bit 1: Theta refreshed first,
+  unsigned long long g_step_k[8] = {};  // bit 2: the energy reuses the bf16 Theta operand
   cudaGraphExec_t g_qr = nullptr, g_comb[2] = {};
   unsigned long long g_qr_k = 0, g_comb_k[2] = {};
   void drop_graphs() {
@@ -365,6 +366,12 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   a.xxbar = c->at<double2>(c->L.xxbar);
   a.dt = c->dt; a.e_trial = c->e_trial; a.e_c = c->e_c;
   a.step = mode == 1 ? c->at<unsigned long long>(c->L.step) : nullptr;
+  for (int s = 0; s < 2; ++s)
+    a.thb[s] = (c->d.tensor() && s < c->d.nblk && c->tcs.blk[s].n > 0)
+                   ? reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.blk[s].off_th)
+                   : nullptr;
+  a.kst = c->tcs.kst;
+  a.nseg = c->tcs.nseg;
   return a;
 }
 
@@ -405,6 +412,7 @@ afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
   const size_t sm = overlap_smem(c->d);
   if (overlap_stage(c->d)) k_overlap_lu<R, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
   else k_overlap_lu<R, false><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+  c->thb_valid = c->d.tensor();
   CHECK_LAUNCH(c);
   return AFQMC_OK;
 }
@@ -483,7 +491,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
     tc::NormalsJob nj{c->at<double>(c->L.x), c->seed, c->at<unsigned long long>(c->L.step), c->d.W, c->d.X};
     if ((st = tc::exchange(&c->tcs, c->stream, c->at<char>(c->L.tc), c->smul, c->at<float2>(c->L.thetaT),
                            c->at<float2>(c->L.vbias), c->at<double2>(c->L.exch_part), c->at<int>(c->L.status),
-                           nullptr, c->d.W, &c->launches, g_err, sizeof(g_err), &nj)) != AFQMC_OK)
+                           nullptr, c->d.W, &c->launches, g_err, sizeof(g_err), &nj, c->thb_valid)) != AFQMC_OK)
       return st;
     c->normals_pending = true;   // valid for the next step_impl while the step counter is unchanged
   } else {
@@ -542,6 +550,11 @@ afqmc_status step_impl(afqmc_ctx* c) {
   fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar);
   fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
   fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
+  if (d.tensor()) {
+    fa.coefb = reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.off_coef);
+    fa.kx = c->tcs.kx;
+    fa.nseg = c->tcs.nseg;
+  }
   k_fields<R><<<d.W, 256, 0, c->stream>>>(fa);
   delete tf;
   CHECK_LAUNCH(c);
@@ -551,7 +564,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   const bool tc_prop = use_tc_propagation(c);
   if (tc_prop) {   // bf16 hi/lo planes for the tensor-core propagation
     if ((st = tc::vhs_planes(&c->tcs, c->stream, c->at<char>(c->L.tc), c->at<float2>(c->L.coef),
-                             c->at<int>(c->L.status), &c->launches, g_err, sizeof(g_err))) != AFQMC_OK)
+                             c->at<int>(c->L.status), &c->launches, g_err, sizeof(g_err), true)) != AFQMC_OK)
       return st;
   } else if (d.tensor()) {   // planar fp32 output: VHS_w = vhs[w][0][:] + i vhs[w][1][:]
     if ((st = tc::vhs(&c->tcs, c->stream, c->at<char>(c->L.tc), c->at<float2>(c->L.coef), c->at<float>(c->L.vhs),
@@ -687,6 +700,7 @@ afqmc_status comb_impl(afqmc_ctx* c) {
   CU(cudaMemcpyAsync(c->base + c->L.logO, c->base + c->L.logO_tmp, d.W * 16, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemcpyAsync(c->base + c->L.w, c->base + c->L.w_tmp, d.W * 8, cudaMemcpyDeviceToDevice, c->stream));
   c->vbias_fresh = false;
+  c->thb_valid = false;   // the gather reordered Theta^T, not its bf16 copy
   return AFQMC_OK;
 }
 
@@ -854,7 +868,7 @@ afqmc_status check_ctx(afqmc_ctx* c) {
 template <typename F>
 afqmc_status capture_graph(afqmc_ctx* c, F body, cudaGraph_t* out, unsigned long long* nkernels) {
   if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  const bool tf = c->theta_fresh, vf = c->vbias_fresh;
+  const bool tf = c->theta_fresh, vf = c->vbias_fresh, tb = c->thb_valid;
   const unsigned long long hs = c->host_step, l0 = c->launches;
   cudaStream_t user = c->stream;
   // a captured step draws its normals unless the same capture's energy does (never from a flag
@@ -868,6 +882,7 @@ afqmc_status capture_graph(afqmc_ctx* c, F body, cudaGraph_t* out, unsigned long
   const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   *nkernels = c->launches - l0;
   c->theta_fresh = tf; c->vbias_fresh = vf; c->host_step = hs; c->launches = l0; c->normals_pending = false;
+  c->thb_valid = tb;
   if (st != AFQMC_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
   *out = graph;
@@ -889,7 +904,7 @@ afqmc_status capture(afqmc_ctx* c, F body, cudaGraphExec_t* out, unsigned long l
 
 // One driver-loop step (optional energy into the history slot, then propagation) via a graph.
 afqmc_status graph_step(afqmc_ctx* c, bool energy) {
-  const int v = (energy ? 1 : 0) | (c->theta_fresh ? 0 : 2);
+  const int v = (energy ? 1 : 0) | (c->theta_fresh ? 0 : 2) | (energy && c->theta_fresh && c->thb_valid ? 4 : 0);
   if (!c->g_step[v]) {
     afqmc_status st = capture(c, [&]() -> afqmc_status {
       afqmc_status s2;
@@ -901,6 +916,7 @@ afqmc_status graph_step(afqmc_ctx* c, bool energy) {
   }
   CU(cudaGraphLaunch(c->g_step[v], c->stream));
   c->normals_pending = false;
+  c->thb_valid = c->d.tensor();   // the step ends with the overlap
   c->launches += c->g_step_k[v];
   c->theta_fresh = true;
   c->vbias_fresh = false;
@@ -915,6 +931,7 @@ afqmc_status graph_qr(afqmc_ctx* c) {
   }
   CU(cudaGraphLaunch(c->g_qr, c->stream));
   c->normals_pending = false;
+  c->thb_valid = false;
   c->launches += c->g_qr_k;
   c->theta_fresh = false;
   c->vbias_fresh = false;
@@ -929,6 +946,7 @@ afqmc_status graph_comb(afqmc_ctx* c) {
   }
   CU(cudaGraphLaunch(c->g_comb[v], c->stream));
   c->normals_pending = false;
+  c->thb_valid = false;
   c->launches += c->g_comb_k[v];
   c->theta_fresh = true;
   c->vbias_fresh = false;
@@ -1548,7 +1566,7 @@ struct afqmc_batch {
   struct Exec {
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned long long> nk;
-    std::vector<char> end_theta, end_vbias;
+    std::vector<char> end_theta, end_vbias, end_thb;
   };
   std::map<int, Exec> cache;
   ~afqmc_batch() {
@@ -1568,7 +1586,7 @@ afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb
   for (afqmc_ctx* c : b->sys) {
     cudaGraph_t g = nullptr;
     unsigned long long nk = 0;
-    bool end_tf = false, end_vf = false;
+    bool end_tf = false, end_vf = false, end_tb = false;
     afqmc_status st = capture_graph(c, [&]() -> afqmc_status {
       afqmc_status s2;
       if (energy && (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot))) != AFQMC_OK)
@@ -1577,6 +1595,7 @@ afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb
       if (qr && (s2 = DISPATCH(c, qr_impl)) != AFQMC_OK) return s2;
       if (comb && (s2 = DISPATCH(c, comb_impl)) != AFQMC_OK) return s2;
       end_tf = c->theta_fresh;
+      end_tb = c->thb_valid;
       end_vf = c->vbias_fresh;
       return AFQMC_OK;
     }, &g, &nk);
@@ -1587,6 +1606,7 @@ afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb
     if (e != cudaSuccess) { cudaGraphDestroy(bg); return fail(AFQMC_ECUDA, "batch graph: %s", cudaGetErrorString(e)); }
     ex.nk.push_back(nk);
     ex.end_theta.push_back(end_tf);
+    ex.end_thb.push_back(end_tb);
     ex.end_vbias.push_back(end_vf);
   }
   const cudaError_t e = cudaGraphInstantiate(&ex.exec, bg, 0);
@@ -1649,7 +1669,8 @@ afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_ever
     const bool qr = reortho_every > 0 && (hs + 1) % (unsigned long long)reortho_every == 0;
     const bool comb = comb_every > 0 && (hs + 1) % (unsigned long long)comb_every == 0;
     const bool refresh = !c0->theta_fresh;
-    const int key = (energy ? 1 : 0) | (refresh ? 2 : 0) | (qr ? 4 : 0) | (comb ? 8 : 0);
+    const int key = (energy ? 1 : 0) | (refresh ? 2 : 0) | (qr ? 4 : 0) | (comb ? 8 : 0) |
+                    (energy && !refresh && c0->thb_valid ? 16 : 0);
     if (energy && used == kHistory - 1 && (st = flush()) != AFQMC_OK) return st;
     afqmc_batch::Exec* ex = nullptr;
     if ((st = batch_exec(b, key, energy, qr, comb, &ex)) != AFQMC_OK) return st;
@@ -1658,6 +1679,7 @@ afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_ever
       afqmc_ctx* c = b->sys[i];
       c->launches += ex->nk[i];
       c->theta_fresh = ex->end_theta[i];
+      c->thb_valid = ex->end_thb[i];
       c->vbias_fresh = ex->end_vbias[i];
       c->normals_pending = false;
       c->host_step++;

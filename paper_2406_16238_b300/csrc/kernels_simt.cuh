@@ -3,6 +3,8 @@
 // log-determinants, weights, QR and all energy reductions are binary64 in both.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace afq {
@@ -159,7 +161,30 @@ struct OverlapArgs {
   const double2* xxbar;           // [W]
   double dt, e_trial, e_c;
   unsigned long long* step;       // incremented once (mode 1) if non-null
+  // optional: Theta^T also as the tensor-core exchange operand of each spin block s, rows
+  // (w, part, b) of nseg * kst bf16 = [hi | hi | lo] (hi only when nseg = 1)
+  __nv_bfloat16* thb[2];
+  int kst, nseg;
 };
+
+// Theta^T entry (b, p) of walker w as the split-bf16 exchange operand of its block.
+template <typename R2>
+__device__ __forceinline__ void store_theta_bf16(__nv_bfloat16* out, int kst, int nseg, int n, int w, int b, int p,
+                                                 R2 v) {
+  const size_t rowlen = (size_t)nseg * kst;
+  __nv_bfloat16* re = out + ((size_t)w * 2 * n + b) * rowlen + p;
+  __nv_bfloat16* im = re + (size_t)n * rowlen;
+  const float fx = (float)v.x, fy = (float)v.y;
+  const __nv_bfloat16 hr = __float2bfloat16_rn(fx), hi = __float2bfloat16_rn(fy);
+  re[0] = hr;
+  im[0] = hi;
+  if (nseg == 3) {
+    re[kst] = hr;
+    im[kst] = hi;
+    re[2 * kst] = __float2bfloat16_rn(fx - __bfloat162float(hr));
+    im[2 * kst] = __float2bfloat16_rn(fy - __bfloat162float(hi));
+  }
+}
 
 __device__ __forceinline__ double wrap_angle(double t) { return atan2(sin(t), cos(t)); }
 
@@ -327,6 +352,8 @@ struct FieldArgs {
   double* x;                // [W][X]
   double2* xbar;            // [W][X]
   cplx_t<R>* coef;          // [W][X]
+  __nv_bfloat16* coefb;     // optional: rows (w, part) of nseg * kx bf16, [hi | lo | hi] (hi only if nseg = 1)
+  int kx, nseg;
   double2* cmf;             // [W]
   double2* xxbar;           // [W]
 };
@@ -374,7 +401,23 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
         }
       }
       const double2 xs = mk(x - xb.x, -xb.y);
-      a.coef[(size_t)w * a.X + g] = from_d2<R>(mk(a.sdt * xs.y, -a.sdt * xs.x));
+      const cplx_t<R> cf = from_d2<R>(mk(a.sdt * xs.y, -a.sdt * xs.x));
+      a.coef[(size_t)w * a.X + g] = cf;
+      if (a.coefb) {
+        const size_t rowlen = (size_t)a.nseg * a.kx;
+        __nv_bfloat16* re = a.coefb + (size_t)w * 2 * rowlen + g;
+        __nv_bfloat16* im = re + rowlen;
+        const float fx = (float)cf.x, fy = (float)cf.y;
+        const __nv_bfloat16 hr = __float2bfloat16_rn(fx), hi = __float2bfloat16_rn(fy);
+        re[0] = hr;
+        im[0] = hi;
+        if (a.nseg == 3) {
+          re[a.kx] = __float2bfloat16_rn(fx - __bfloat162float(hr));
+          im[a.kx] = __float2bfloat16_rn(fy - __bfloat162float(hi));
+          re[2 * a.kx] = hr;
+          im[2 * a.kx] = hi;
+        }
+      }
       const double l = a.lbar[g];
       cm = cadd(cm, mk(-a.sdt * l * xs.y, a.sdt * l * xs.x));
       xx = cadd(xx, mk(x * xb.x - 0.5 * (xb.x * xb.x - xb.y * xb.y), x * xb.y - xb.x * xb.y));
@@ -903,7 +946,9 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
       singular = true;
       for (int idx = tid; idx < n * N; idx += blockDim.x) {
         const int b = idx / N, p = idx % N;
-        a.thetaT[((size_t)w * a.ncol + c0 + b) * N + p] = from_d2<R>(mk(0.0, 0.0));
+        const R2 z = from_d2<R>(mk(0.0, 0.0));
+        a.thetaT[((size_t)w * a.ncol + c0 + b) * N + p] = z;
+        if (a.thb[s]) store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, z);
       }
       continue;
     }
@@ -978,7 +1023,14 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     if (STAGE)
       for (int idx = tid; idx < n * N; idx += blockDim.x) {   // Theta^T[perm[i]][p] = y_i
         const int i = idx / N, p = idx % N;
-        thw[(size_t)perm[i] * N + p] = Y[(size_t)p * ldy + i];
+        const R2 v = Y[(size_t)p * ldy + i];
+        thw[(size_t)perm[i] * N + p] = v;
+        if (a.thb[s]) store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, perm[i], p, v);
+      }
+    else if (a.thb[s])
+      for (int idx = tid; idx < n * N; idx += blockDim.x) {
+        const int b = idx / N, p = idx % N;
+        store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, thw[(size_t)b * N + p]);
       }
     if (tid == 0) {   // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps)
       const double2 pr = prod_s;

@@ -749,6 +749,13 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
     snprintf(err, errlen, "cuTensorMapEncodeTiled is not available from the driver");
     return AFQMC_ECUDA;
   }
+  // the Theta and coefficient operands are also written by the overlap and fields kernels, which
+  // leave the K padding untouched: clear it once
+  if (cudaMemsetAsync(tcbuf, 0, st->off_lt, s) != cudaSuccess ||
+      cudaMemsetAsync(tcbuf + st->off_coef, 0, (size_t)st->W * 2 * st->nseg * st->kx * 2, s) != cudaSuccess) {
+    snprintf(err, errlen, "tc prepare: clearing the operand buffers failed");
+    return AFQMC_ECUDA;
+  }
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
     if (bm.n == 0) continue;
@@ -800,16 +807,18 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
 
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
                       double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
-                      char* err, size_t errlen, const NormalsJob* nj) {
+                      char* err, size_t errlen, const NormalsJob* nj, bool theta_ready) {
   int chunk = 0;
   bool first = true;
   if (nw <= 0) return AFQMC_OK;
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
     if (bm.n == 0) continue;
-    k_theta_bf16<<<nw, 256, 0, s>>>(nw, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, thetaT,
-                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th), widx);
-    ++*launches;
+    if (!theta_ready || widx) {
+      k_theta_bf16<<<nw, 256, 0, s>>>(nw, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, thetaT,
+                                      reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th), widx);
+      ++*launches;
+    }
     Geom g{};
     g.m_tiles = bm.m_tiles;
     g.n_tiles = (nw + bm.wpt - 1) / bm.wpt;
@@ -849,14 +858,16 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
 }
 
 afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, int* status,
-                        unsigned long long* launches, char* err, size_t errlen) {
+                        unsigned long long* launches, char* err, size_t errlen, bool coef_ready) {
   if (!st->pg.ok) {
     snprintf(err, errlen, "tensor-core propagation is not available for this problem");
     return AFQMC_EINVAL;
   }
-  k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
-                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
-  ++*launches;
+  if (!coef_ready) {
+    k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
+                                      reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
+    ++*launches;
+  }
   Geom g{};
   g.m_tiles = (st->N * st->N + kBM - 1) / kBM;
   g.n_tiles = (2 * st->W + 255) / 256;

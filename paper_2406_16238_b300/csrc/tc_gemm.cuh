@@ -90,10 +90,11 @@ struct NormalsJob {
 // sum_ab T_ab T_ba, with T^{g s} = Ltilde^{g s} Theta^s; Theta^T complex64 [W][ncol][N].
 // widx (optional, nw entries): the kernel works on walkers widx[0..nw) and writes their partials
 // to rows 0..nw of exch_part; vbias may be NULL (not written).
-// nj (optional): the first launch also draws those normals.
+// nj (optional): the first launch also draws those normals.  theta_ready: the bf16 operand copy of
+// Theta^T (every walker, in walker order) is already current, so it is not rebuilt (ignored with widx).
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
                       double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
-                      char* err, size_t errlen, const NormalsJob* nj = nullptr);
+                      char* err, size_t errlen, const NormalsJob* nj = nullptr, bool theta_ready = false);
 
 // VHS planar fp32: out[w][0][pq] + i out[w][1][pq] = sum_g coef[w][g] L^g_pq, coef complex64 [W][X].
 afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, float* out, int* status,
@@ -105,8 +106,9 @@ afqmc_status prepare_prop(TcState* st, cudaStream_t s, char* tcbuf, const double
                           char* err, size_t errlen);
 
 // VHS into the bf16 hi/lo planes read by the tensor-core propagation.
+// coef_ready: the split-bf16 coefficients were written by the fields kernel (not rebuilt from coef).
 afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, int* status,
-                        unsigned long long* launches, char* err, size_t errlen);
+                        unsigned long long* launches, char* err, size_t errlen, bool coef_ready = false);
 
 // psi <- E_h sum_{k<=order} V^k / k! E_h psi for every walker with w != 0 (psi complex64 [W][N][ncol]).
 afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, float2* psi, const double* w,
