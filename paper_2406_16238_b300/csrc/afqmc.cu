@@ -499,12 +499,11 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
   }
   delete tx;
   StageTimer te(c, AFQMC_STAGE_ENERGY);
-  k_energy_walker<R><<<c->d.W, 256, 0, c->stream>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
-                                                   c->at<cplx_t<R>>(c->L.thetaT), c->at<R>(c->L.hrot_r),
-                                                   c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
-                                                   c->at<double2>(c->L.eloc));
-  CHECK_LAUNCH(c);
-  k_energy_sums<<<1, 256, 0, c->stream>>>(c->d.W, c->at<double>(c->L.w), c->at<double2>(c->L.eloc), sums_dev, slot);
+  k_energy<R><<<c->d.W, 256, 0, c->stream>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
+                                              c->at<cplx_t<R>>(c->L.thetaT), c->at<R>(c->L.hrot_r),
+                                              c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
+                                              c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w), sums_dev, slot,
+                                              reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64));
   CHECK_LAUNCH(c);
   c->vbias_fresh = true;
   return AFQMC_OK;
@@ -841,6 +840,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   }
   CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.step, 0, 256, c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.slot, 0, 256, c->stream));   // history slot, energy completion counter
   k_init_walkers<R><<<296, 256, 0, c->stream>>>(d.W, N, nc, c->at<double>(c->L.phi), c->at<cplx_t<R>>(c->L.psi),
                                                 c->at<double>(c->L.w));
   CHECK_LAUNCH(c);

@@ -63,6 +63,32 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
   return t;
 }
 
+// NQ deterministic block sums at once for a 256-thread block: a fixed-order shared-memory tree
+// down to 32 values per quantity, then one warp per quantity.  Binary64 additions on few warps:
+// on B300 an FP64 warp instruction costs an issue slot of the slow FP64 pipe whatever its active
+// lanes, so this uses about a third of the FP64 instructions of NQ separate block_sum calls.
+// part: NQ * 256 doubles of shared memory; the sums land in out[0..NQ) (shared); all threads call.
+template <int NQ>
+__device__ __forceinline__ void block_sum_multi(const double* v, double* part, double* out) {
+  static_assert(NQ >= 1 && NQ <= 8, "at most one warp per quantity");
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) part[q * 256 + tid] = v[q];
+  for (int stride = 128; stride >= 32; stride >>= 1) {
+    __syncthreads();
+    if (tid < stride)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) part[q * 256 + tid] += part[q * 256 + tid + stride];
+  }
+  __syncthreads();
+  const int wid = tid >> 5, lane = tid & 31;
+  if (wid < NQ) {
+    const double s = warp_sum(part[wid * 256 + lane]);
+    if (lane == 0) out[wid] = s;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ double2 block_sum2(double2 v, double* scratch) {
   double a = block_sum(v.x, scratch);
   double b = block_sum(v.y, scratch);

@@ -276,63 +276,88 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
 
 // Per-walker local energy from the pieces: E1 = smul sum htilde . Theta^T,
 // J = 1/2 sum_g vbias_g^2, K = 1/2 sum exchange partials.  eloc[w] = (E, E0+E1, J-K).
+// The last CTA to finish (completion counter `done`, reset by it) forms the weighted estimator
+// sums (ENumer, EDenom, E1Body, E2Body) over all walkers in a fixed order; with a slot counter
+// they go to out + 4 * (*slot) and the counter advances (graph-replayable history).
 template <typename R>
-__global__ void __launch_bounds__(256) k_energy_walker(int N, int X, int ncol, double smul, double ecore,
-                                                         int nchunk, const cplx_t<R>* thetaT, const R* hrot_r,
-                                                         const cplx_t<R>* vbias, const double2* exch_part,
-                                                         double2* eloc) {
+__global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double smul, double ecore, int nchunk,
+                                                const cplx_t<R>* thetaT, const R* hrot_r, const cplx_t<R>* vbias,
+                                                const double2* exch_part, double2* eloc, int W, const double* wgt,
+                                                double* out, int* slot, unsigned int* done) {
   __shared__ double red[32];
+  __shared__ double part[6 * 256];
+  __shared__ int last_s;
   const int w = blockIdx.x, tid = threadIdx.x;
   const int cn = ncol * N;
-  R e1r = R(0), e1i = R(0);   // per-thread partial at the walkers' precision, summed across threads in binary64
-  for (int i = tid; i < cn; i += blockDim.x) {
-    const cplx_t<R> t = thetaT[(size_t)w * cn + i];
+  const cplx_t<R>* th = thetaT + (size_t)w * cn;
+  // per-thread partials at the walkers' precision (four independent chains), summed in binary64
+  R ar[4] = {R(0), R(0), R(0), R(0)}, ai[4] = {R(0), R(0), R(0), R(0)};
+  int i = tid;
+  for (; i + 3 * 256 < cn; i += 4 * 256) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const cplx_t<R> t = th[i + u * 256];
+      const R h = hrot_r[i + u * 256];
+      ar[u] += t.x * h;
+      ai[u] += t.y * h;
+    }
+  }
+  for (; i < cn; i += 256) {
+    const cplx_t<R> t = th[i];
     const R h = hrot_r[i];
-    e1r += t.x * h;
-    e1i += t.y * h;
+    ar[0] += t.x * h;
+    ai[0] += t.y * h;
   }
-  double2 e1 = mk((double)e1r, (double)e1i);
-  double2 j = mk(0.0, 0.0);
-  for (int g = tid; g < X; g += blockDim.x) {
-    const double2 v = to_d2(vbias[(size_t)w * X + g]);
-    j = cadd(j, cmul(v, v));
+  double v[6];
+  v[0] = (double)((ar[0] + ar[1]) + (ar[2] + ar[3]));
+  v[1] = (double)((ai[0] + ai[1]) + (ai[2] + ai[3]));
+  double jr = 0.0, ji = 0.0;
+  for (int g = tid; g < X; g += 256) {   // vbias_g^2
+    const double2 vb = to_d2(vbias[(size_t)w * X + g]);
+    jr = fma(vb.x, vb.x, fma(-vb.y, vb.y, jr));
+    ji = fma(2.0 * vb.x, vb.y, ji);
   }
-  double2 k = mk(0.0, 0.0);
-  for (int c = tid; c < nchunk; c += blockDim.x) k = cadd(k, exch_part[(size_t)w * nchunk + c]);
-  e1 = block_sum2(e1, red);
-  j = block_sum2(j, red);
-  k = block_sum2(k, red);
+  v[2] = jr;
+  v[3] = ji;
+  double kr = 0.0, ki = 0.0;
+  for (int c = tid; c < nchunk; c += 256) {
+    const double2 e = exch_part[(size_t)w * nchunk + c];
+    kr += e.x;
+    ki += e.y;
+  }
+  v[4] = kr;
+  v[5] = ki;
+  block_sum_multi<6>(v, part, red);
   if (tid == 0) {
-    const double2 one = mk(ecore + smul * e1.x, smul * e1.y);
-    const double2 two = mk(0.5 * (j.x - k.x), 0.5 * (j.y - k.y));
+    const double2 one = mk(ecore + smul * red[0], smul * red[1]);
+    const double2 two = mk(0.5 * (red[2] - red[4]), 0.5 * (red[3] - red[5]));
     eloc[3 * w + 0] = cadd(one, two);
     eloc[3 * w + 1] = one;
     eloc[3 * w + 2] = two;
+    __threadfence();
+    last_s = atomicAdd(done, 1u) == (unsigned int)(W - 1);
   }
-}
-
-// Weighted estimator sums (ENumer, EDenom, E1Body, E2Body), fixed reduction order.  With a slot
-// counter, the sums go to out + 4 * (*slot) and the counter advances (graph-replayable history).
-__global__ void __launch_bounds__(256) k_energy_sums(int W, const double* w, const double2* eloc, double* out,
-                                                     int* slot) {
-  __shared__ double red[32];
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) {
-    const double wi = w[i];
+  for (int u = tid; u < W; u += blockDim.x) {
+    const double wi = wgt[u];
     if (wi == 0.0) continue;
-    s0 += wi * eloc[3 * i].x;
+    s0 += wi * __ldcg(&eloc[3 * u].x);
     s1 += wi;
-    s2 += wi * eloc[3 * i + 1].x;
-    s3 += wi * eloc[3 * i + 2].x;
+    s2 += wi * __ldcg(&eloc[3 * u + 1].x);
+    s3 += wi * __ldcg(&eloc[3 * u + 2].x);
   }
   s0 = block_sum(s0, red);
   s1 = block_sum(s1, red);
   s2 = block_sum(s2, red);
   s3 = block_sum(s3, red);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double* o = slot ? out + 4 * (size_t)(*slot) : out;
     o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
     if (slot) *slot += 1;
+    *done = 0u;
   }
 }
 
@@ -424,11 +449,12 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
       a.xbar[(size_t)w * a.X + g] = xb;
     }
   }
-  cm = block_sum2(cm, red);
-  xx = block_sum2(xx, red);
+  __shared__ double part[4 * 256];
+  const double v4[4] = {cm.x, cm.y, xx.x, xx.y};
+  block_sum_multi<4>(v4, part, red);
   if (tid == 0) {
-    a.cmf[w] = cm;
-    a.xxbar[w] = xx;
+    a.cmf[w] = mk(red[0], red[1]);
+    a.xxbar[w] = mk(red[2], red[3]);
   }
 }
 
