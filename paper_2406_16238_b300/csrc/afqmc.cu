@@ -365,6 +365,7 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   a.cmf = c->at<double2>(c->L.cmf);
   a.xxbar = c->at<double2>(c->L.xxbar);
   a.dt = c->dt; a.e_trial = c->e_trial; a.e_c = c->e_c;
+  a.eshift = std::exp(c->dt * (c->e_trial - c->e_c));
   a.step = mode == 1 ? c->at<unsigned long long>(c->L.step) : nullptr;
   for (int s = 0; s < 2; ++s)
     a.thb[s] = (c->d.tensor() && s < c->d.nblk && c->tcs.blk[s].n > 0)

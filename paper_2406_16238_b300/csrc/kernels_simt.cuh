@@ -160,6 +160,7 @@ struct OverlapArgs {
   const double2* cmf;             // [W]
   const double2* xxbar;           // [W]
   double dt, e_trial, e_c;
+  double eshift;                  // exp(dt (E_T - E_c)), the same factor for every walker
   unsigned long long* step;       // incremented once (mode 1) if non-null
   // optional: Theta^T also as the tensor-core exchange operand of each spin block s, rows
   // (w, part, b) of nseg * kst bf16 = [hi | hi | lo] (hi only when nseg = 1)
@@ -186,7 +187,15 @@ __device__ __forceinline__ void store_theta_bf16(__nv_bfloat16* out, int kst, in
   }
 }
 
-__device__ __forceinline__ double wrap_angle(double t) { return atan2(sin(t), cos(t)); }
+// t mapped to (-pi, pi] by subtracting a multiple of 2 pi (few binary64 operations; the slow FP64
+// units make atan2(sin t, cos t) a long serial chain).
+__device__ __forceinline__ double wrap_angle(double t) {
+  const double twopi = 6.283185307179586, pi = 3.141592653589793;
+  double r = fma(-twopi, rint(t * (1.0 / twopi)), t);
+  if (r > pi) r -= twopi;
+  else if (r <= -pi) r += twopi;
+  return r;
+}
 
 // ============================================================================
 // Local energy pieces on CUDA cores.  CTA (chunk, walker): for gamma in the
@@ -1060,7 +1069,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
       }
     if (tid == 0) {   // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps)
       const double2 pr = prod_s;
-      ld_re += log(hypot(pr.x, pr.y)) + exp_s * 0.6931471805599453;
+      ld_re += 0.5 * log(fma(pr.x, pr.x, pr.y * pr.y)) + exp_s * 0.6931471805599453;   // |pr| in [1, 2 sqrt 2)
       ld_im += atan2(pr.y, pr.x) + (swaps_s ? 3.141592653589793 : 0.0);
     }
     __syncthreads();
@@ -1081,7 +1090,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     const double ls_re = lo_new.x - lo_old.x + c.x;
     const double theta = lo_new.y - lo_old.y + c.y;
     const double li_re = ls_re + xx.x;
-    double wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * exp(a.dt * (a.e_trial - a.e_c));
+    double wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * a.eshift;
     if (!isfinite(wn)) {
       wn = 0.0;
       atomicOr(a.status, kStatusNonFinite);
