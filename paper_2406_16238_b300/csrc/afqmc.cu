@@ -668,8 +668,8 @@ afqmc_status qr_impl(afqmc_ctx* c) {
                                                    c->at<double>(c->L.w), c->at<int>(c->L.status),
                                                    qr_stage_psi(d) ? 1 : 0);
   CHECK_LAUNCH(c);
-  c->theta_fresh = false;
-  c->vbias_fresh = false;
+  // Theta = psi (Phi^T psi)^-1 is unchanged by psi -> psi R^-1 (Phi^T psi picks up the same R^-1),
+  // so Theta, its bf16 copy and the force bias stay valid; log O was updated by -sum log R_ii.
   return AFQMC_OK;
 }
 
@@ -932,11 +932,8 @@ afqmc_status graph_qr(afqmc_ctx* c) {
   }
   CU(cudaGraphLaunch(c->g_qr, c->stream));
   c->normals_pending = false;
-  c->thb_valid = false;
   c->launches += c->g_qr_k;
-  c->theta_fresh = false;
-  c->vbias_fresh = false;
-  return AFQMC_OK;
+  return AFQMC_OK;   // Theta and its copies stay valid (see qr_impl)
 }
 
 afqmc_status graph_comb(afqmc_ctx* c) {

@@ -331,3 +331,22 @@ def test_graph_replay_is_bit_identical_to_direct_launches(prec, name, nw):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[4], b[4])
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     assert a[5] == b[5]                      # the same kernels ran, counted per graph node
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("bf16x3", 1e-6)])
+def test_theta_kept_across_qr_matches_recomputation(prec, tol):
+    """QR leaves Theta = psi (Phi^T psi)^-1 unchanged (psi -> psi R^-1 multiplies Phi^T psi by the
+    same R^-1), so the energy measured right after a QR with the cached Theta equals the energy
+    after Theta is rebuilt from the orthonormalised walkers."""
+    prob = PROBLEMS["uhf_N13_3_2"]()
+    nw = 16
+    ctx = _ctx(prob, nw, prec=prec, seed=21)
+    ctx.run(4, energy_every=0, reortho_every=0, comb_every=0)
+    ctx.reortho()
+    _, e_cached = ctx.local_energy(per_walker=True)
+    psi, logo, w, step = ctx.get_walkers()
+    ctx.set_walkers(psi, w, step)                 # forces Theta to be rebuilt from psi
+    _, e_fresh = ctx.local_energy(per_walker=True)
+    scale = np.max(np.abs(e_fresh[:, 0]))
+    assert np.max(np.abs(e_cached[:, 0] - e_fresh[:, 0])) < tol * scale
+    ctx.close()
