@@ -1429,7 +1429,7 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
   std::vector<afqmc_tuning> cands;
   const bool fused_ok = use_fused_propagation(d), tc_ok = d.tensor() && ctx->tcs.pg.ok;
   std::vector<int> groups = {0};
-  if (d.tensor()) groups = {1, 2, 4};
+  if (d.tensor()) groups = {1, 2, 3, 4};
   for (int tc_cap : {4, 2})
     for (int g : groups) {
       if (tc_ok) cands.push_back(afqmc_tuning{tc_cap, 0, g, 0, 0.f});

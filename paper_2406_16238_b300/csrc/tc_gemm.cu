@@ -660,11 +660,13 @@ afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, c
 
 }  // namespace
 
-// Largest epilogue group count (<= 4, <= walkers per tile) whose buffers fit beside two stages.
-int exchange_groups(int n, int wpt) {
-  const int bn = (wpt * 2 * n + 15) / 16 * 16;
-  const int stage_bytes = kStageA + bn * kBK * 2;
-  for (int g = std::min(4, wpt); g > 1; --g) {
+// Largest epilogue group count (<= 4, <= walkers per tile) whose buffers fit beside two stages of
+// the tile it implies (walkers per tile = the largest multiple of the group count <= wpt0).
+int exchange_groups(int n, int wpt0) {
+  for (int g = std::min(4, wpt0); g > 1; --g) {
+    const int wpt = wpt0 / g * g;
+    const int bn = (wpt * 2 * n + 15) / 16 * 16;
+    const int stage_bytes = kStageA + bn * kBK * 2;
     const int need = 1024 + g * ((epi_bytes_exchange(n) + 15) & ~15) + kTailBytes + 2 * stage_bytes;
     if (need <= kMaxSmem) return g;
   }
