@@ -28,8 +28,8 @@ struct BlockMaps {
 // kernel forms t = E_h psi, the Taylor terms V t / k and E_h acc as D = A B^T with A = V or
 // F = E_h - I (rows p, K = q) and B = the current term, both split into bf16 hi + lo.
 // Shared memory, from a 1024-byte aligned base: V hi | V lo (4 swizzle atoms of npad rows:
-// Re V q < 64, Re V q >= 64, Im V q < 64, Im V q >= 64) | F hi | F lo (2 atoms) | B hi | B lo
-// (4 atoms of 2 cwp rows) | mbarriers.
+// Re V q < 64, Re V q >= 64, Im V q < 64, Im V q >= 64) | F hi | F lo (2 atoms) | B (2 atoms of
+// 4 cwp rows: the term's hi parts, then its lo parts) | mbarriers.
 struct PropGeom {
   int ok = 0;
   int large = 0;       // 1: N > 128, the batched form (V streamed per product, one launch per product)
@@ -40,7 +40,7 @@ struct PropGeom {
   int nk = 0;          // 16-wide k-steps per K half, ceil(N / 16)
   int cw = 0, cwp = 0; // columns per chunk and its padding to a multiple of 8
   int nch = 0;         // chunks per walker
-  int off_vlo = 0, off_fhi = 0, off_flo = 0, off_bhi = 0, off_blo = 0, off_bar = 0;
+  int off_vlo = 0, off_fhi = 0, off_flo = 0, off_b = 0, off_bar = 0;
   int smem = 0;        // dynamic shared memory bytes including the alignment slack
 };
 PropGeom prop_geom(int N, int ncol);

@@ -3,20 +3,21 @@
 // with E_h = exp(-dt/2 h_eff) applied as psi + F psi, F = E_h - I (F is O(dt), so its split-bf16
 // product error is far below that of E_h itself).
 //
-// Per walker and chunk of cw columns every product is one tcgen05 contraction D = A B^T,
-// M = 128 rows p (orbitals), N = 2 cwp (real parts of the chunk's columns, then imaginary
-// parts), K = q over two halves:
-//   A = [Re V | Im V]  (K = 256: q of Re V, then q of Im V),  A = F for E_h (first half only),
-//   B rows c:        [Re t(:,c) | -Im t(:,c)],   B rows cwp + c: [Im t(:,c) | Re t(:,c)],
-// so that D[p][c] = Re (V t)[p][c] and D[p][cwp + c] = Im (V t)[p][c].  Operands are split-bf16
-// (hi + lo, products hi*hi + lo*hi + hi*lo, fp32 accumulation in tensor memory).
+// Per walker and chunk of cw columns every product is a set of tcgen05 contractions D = A B^T with
+// M = 128 rows p (orbitals) and K = q.  B holds the current term of the chunk once, as split bf16:
+// rows 0 .. 2 cwp - 1 its hi parts (real parts of the columns, then imaginary parts, grouped by the
+// epilogue's column slices), rows 2 cwp .. 4 cwp - 1 its lo parts.  Per 16-wide k-step two MMAs
+// form A hi [B hi; B lo] (N = 4 cwp) and A lo B hi (N = 2 cwp, into the first half), so each
+// accumulator holds the three split-bf16 partial products (hi*hi + lo*hi, hi*lo side by side; fp32
+// in tensor memory).  An F product uses one accumulator D1 = F t; a V product two, D1 = Re V t and
+// D2 = Im V t, and the epilogue forms Re (V t) = Re D1 - Im D2, Im (V t) = Im D1 + Re D2.
 //
 // Roles: warp 16 (one thread) loads F once and each walker's V planes by TMA and issues the MMAs;
 // warps 0-15 read the accumulator, warp w covering lanes 32 (w % 4) .. + 31 (rows p) and a
 // quarter of the chunk's columns: it keeps its part of row p of acc in registers and writes the
 // matching entries of column k = p of the next B operand (hi and lo) into shared memory.  V of the
 // next walker is fetched as soon as the last Taylor product of the current one has completed.
-// Rows p >= N of D (padding, and rows 112-127 which the MMA reads from the following buffer)
+// Rows p >= N of D (padding, and rows npad .. 127 which the MMA reads from the following buffer)
 // are never used: those threads write zeros into B.  Every wait is bounded.
 #include <cuda_bf16.h>
 
@@ -34,7 +35,7 @@ namespace {
 
 struct PropTcParams {
   int N, npad, nk, ncol, cw, nch, order, W;
-  int off_vlo, off_fhi, off_flo, off_bhi, off_blo, off_bar;
+  int off_vlo, off_fhi, off_flo, off_b, off_bar;
   int tmem_cols;
   float2* psi;
   const double* w;
@@ -53,32 +54,25 @@ __device__ __forceinline__ void st_bf16(uint8_t* base, uint32_t off, __nv_bfloat
   *reinterpret_cast<__nv_bfloat16*>(base + off) = v;
 }
 
-// Columns j0 .. j0 + SW - 1 of column k = p of the next B operand from this thread's slice of
-// the term (ur, ui); `both` also writes the second K half (needed by the V products, not by the
-// F products).
+// Column k = p of the next B operand for this thread's slice (columns j0 .. j0 + SW - 1) of the
+// term (ur, ui).  B is K-major with 128-byte swizzling, two 64-wide K atoms of 4 CWP rows; the
+// slice owns hi rows 2 j0 + jj (real parts) and 2 j0 + SW + jj (imaginary parts), and the lo rows
+// 2 CWP further on, so its accumulator columns are consecutive.
 template <int CWP, int SW>
-__device__ __forceinline__ void write_b(uint8_t* bhi, uint8_t* blo, int p, int j0, const float* ur, const float* ui,
-                                        bool both) {
-  constexpr int ab = 2 * CWP * 128;
+__device__ __forceinline__ void write_b(uint8_t* b, int p, int j0, const float* ur, const float* ui) {
+  constexpr int ab = 4 * CWP * 128;
+  constexpr uint32_t lo = 256u * CWP;   // 2 CWP rows further (2 CWP is a multiple of 8)
 #pragma unroll
   for (int jj = 0; jj < SW; ++jj) {
-    const int j = j0 + jj;
     const __nv_bfloat16 rh = __float2bfloat16_rn(ur[jj]);
     const __nv_bfloat16 rl = __float2bfloat16_rn(ur[jj] - __bfloat162float(rh));
     const __nv_bfloat16 ih = __float2bfloat16_rn(ui[jj]);
     const __nv_bfloat16 il = __float2bfloat16_rn(ui[jj] - __bfloat162float(ih));
-    const uint32_t o_r = sw_off(j, p, ab), o_i = sw_off(CWP + j, p, ab);
-    st_bf16(bhi, o_r, rh);
-    st_bf16(blo, o_r, rl);
-    st_bf16(bhi, o_i, ih);
-    st_bf16(blo, o_i, il);
-    if (both) {
-      const uint32_t o_r2 = sw_off(j, 128 + p, ab), o_i2 = sw_off(CWP + j, 128 + p, ab);
-      st_bf16(bhi, o_r2, __hneg(ih));
-      st_bf16(blo, o_r2, __hneg(il));
-      st_bf16(bhi, o_i2, rh);
-      st_bf16(blo, o_i2, rl);
-    }
+    const uint32_t o_r = sw_off(2 * j0 + jj, p, ab), o_i = sw_off(2 * j0 + SW + jj, p, ab);
+    st_bf16(b, o_r, rh);
+    st_bf16(b, o_r + lo, rl);
+    st_bf16(b, o_i, ih);
+    st_bf16(b, o_i + lo, il);
   }
 }
 
@@ -99,33 +93,49 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return ok != 0;
 }
 
-// SW consecutive accumulator columns of this thread's lane (no wait).
-template <int SW>
+// NC consecutive accumulator columns of this thread's lane (no wait).
+template <int NC>
 __device__ __forceinline__ void ld_cols(uint32_t taddr, uint32_t* r) {
-  if constexpr (SW == 2) {
-    tmem_ld2_nowait(taddr, r);
-  } else if constexpr (SW == 4) {
+  if constexpr (NC == 4) {
     tmem_ld4_nowait(taddr, r);
-  } else if constexpr (SW == 6) {
-    tmem_ld4_nowait(taddr, r);
-    tmem_ld2_nowait(taddr + 4, r + 4);
-  } else {
-    static_assert(SW == 8, "slice width");
+  } else if constexpr (NC == 8) {
     tmem_ld8_nowait(taddr, r);
+  } else if constexpr (NC == 12) {
+    tmem_ld8_nowait(taddr, r);
+    tmem_ld4_nowait(taddr + 8, r + 8);
+  } else {
+    static_assert(NC == 16, "slice width");
+    tmem_ld16_nowait(taddr, r);
   }
 }
 
-// This thread's slice of row p of D: dr[jj] = D[p][j0 + jj], di[jj] = D[p][CWP + j0 + jj].
-template <int CWP, int SW>
+// This thread's slice of row p of the product: dr[jj] + i di[jj] = (A t)[p][j0 + jj].  The hi and
+// lo halves of each accumulator are added; a V product combines D1 = Re V t (columns 0 .. 4 CWP - 1)
+// and D2 = Im V t (columns 4 CWP .. 8 CWP - 1).
+template <int CWP, int SW, bool V>
 __device__ __forceinline__ void load_d(uint32_t trow, int j0, float* dr, float* di) {
-  uint32_t r[SW], q[SW];
-  ld_cols<SW>(trow + (uint32_t)j0, r);
-  ld_cols<SW>(trow + (uint32_t)(CWP + j0), q);
+  constexpr int NC = 2 * SW;
+  uint32_t h1[NC], l1[NC], h2[V ? NC : 1], l2[V ? NC : 1];
+  ld_cols<NC>(trow + (uint32_t)(2 * j0), h1);
+  ld_cols<NC>(trow + (uint32_t)(2 * CWP + 2 * j0), l1);
+  if constexpr (V) {
+    ld_cols<NC>(trow + (uint32_t)(4 * CWP + 2 * j0), h2);
+    ld_cols<NC>(trow + (uint32_t)(6 * CWP + 2 * j0), l2);
+  }
   tmem_wait();
 #pragma unroll
   for (int jj = 0; jj < SW; ++jj) {
-    dr[jj] = __uint_as_float(r[jj]);
-    di[jj] = __uint_as_float(q[jj]);
+    const float ar = __uint_as_float(h1[jj]) + __uint_as_float(l1[jj]);
+    const float ai = __uint_as_float(h1[SW + jj]) + __uint_as_float(l1[SW + jj]);
+    if constexpr (V) {
+      const float br = __uint_as_float(h2[jj]) + __uint_as_float(l2[jj]);
+      const float bi = __uint_as_float(h2[SW + jj]) + __uint_as_float(l2[SW + jj]);
+      dr[jj] = ar - bi;
+      di[jj] = ai + br;
+    } else {
+      dr[jj] = ar;
+      di[jj] = ai;
+    }
   }
 }
 
@@ -176,12 +186,12 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
   if (warp == kEpiWarps) {
     if (lane == 0) {   // TMA + MMA issue
       const uint32_t s0 = smem_u32(sm);
-      const uint32_t vatom = (uint32_t)a.npad * 128u, batom = 2u * CWP * 128u;
-      const uint32_t idesc = idesc_bf16(2 * CWP);
+      const uint32_t vatom = (uint32_t)a.npad * 128u, batom = 4u * CWP * 128u;
+      const uint32_t idesc_w = idesc_bf16(4 * CWP), idesc_n = idesc_bf16(2 * CWP);
       // descriptors are linear in the address: desc(base + off) = desc(base) + off / 16
       const uint64_t dvhi = sw128_desc(s0), dvlo = sw128_desc(s0 + (uint32_t)a.off_vlo);
       const uint64_t dfhi = sw128_desc(s0 + (uint32_t)a.off_fhi), dflo = sw128_desc(s0 + (uint32_t)a.off_flo);
-      const uint64_t dbhi = sw128_desc(s0 + (uint32_t)a.off_bhi), dblo = sw128_desc(s0 + (uint32_t)a.off_blo);
+      const uint64_t db = sw128_desc(s0 + (uint32_t)a.off_b);
       auto issue_v = [&](int wk) {
         mbar_expect_tx(bar_v, 8u * vatom);
         for (int pl = 0; pl < 4; ++pl)
@@ -190,19 +200,19 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
             tma_load_2d(sm + dst, &mapV, bar_v, 64 * at, (wk * 4 + pl) * a.npad);
           }
       };
+      // F: D1 = F t.  V: D1 = Re V t (A atoms 0, 1), D2 = Im V t (A atoms 2, 3).
       auto product = [&](bool isv) {
         const uint64_t ah = isv ? dvhi : dfhi, al = isv ? dvlo : dflo;
-        uint32_t accf = 0;
-        for (int h = 0; h < (isv ? 2 : 1); ++h)
+        for (int h = 0; h < (isv ? 2 : 1); ++h) {
+          const uint32_t d = tmem + (uint32_t)(h * 4 * CWP);
           for (int ks = 0; ks < a.nk; ++ks) {
-            const int atom = 2 * h + (ks >> 2);
             const uint32_t ko = (uint32_t)(ks & 3) * 32u;
-            const uint64_t ao = ((uint32_t)atom * vatom + ko) >> 4, bo = ((uint32_t)atom * batom + ko) >> 4;
-            umma_bf16(tmem, ah + ao, dbhi + bo, idesc, accf);
-            accf = 1;
-            umma_bf16(tmem, al + ao, dbhi + bo, idesc, 1);
-            umma_bf16(tmem, ah + ao, dblo + bo, idesc, 1);
+            const uint64_t ao = ((uint32_t)(2 * h + (ks >> 2)) * vatom + ko) >> 4;
+            const uint64_t bo = ((uint32_t)(ks >> 2) * batom + ko) >> 4;
+            umma_bf16(d, ah + ao, db + bo, idesc_w, ks > 0 ? 1u : 0u);   // A hi [B hi; B lo]
+            umma_bf16(d, al + ao, db + bo, idesc_n, 1u);                 // A lo B hi
           }
+        }
         umma_commit(bar_mma);
       };
       bool go = true;
@@ -258,8 +268,7 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
     const int p = 32 * quad + lane;
     const bool row = p < a.N;
     const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
-    uint8_t* bhi = sm + a.off_bhi;
-    uint8_t* blo = sm + a.off_blo;
+    uint8_t* bsm = sm + a.off_b;
     uint32_t ph_m = 0;
     bool go = true;
     float accr[SW], acci[SW], dr[SW], di[SW];
@@ -274,22 +283,22 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
           accr[jj] = dr[jj] = v.x;
           acci[jj] = di[jj] = v.y;
         }
-        write_b<CWP, SW>(bhi, blo, p, j0, dr, di, false);
+        write_b<CWP, SW>(bsm, p, j0, dr, di);
         signal_b(bar_b, lane);
         if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
         ph_m ^= 1u;
-        load_d<CWP, SW>(trow, j0, dr, di);   // F psi
+        load_d<CWP, SW, false>(trow, j0, dr, di);   // F psi
 #pragma unroll
         for (int jj = 0; jj < SW; ++jj) {   // t_0 = psi + F psi
           accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
           acci[jj] = row ? acci[jj] + di[jj] : 0.f;
         }
-        write_b<CWP, SW>(bhi, blo, p, j0, accr, acci, true);
+        write_b<CWP, SW>(bsm, p, j0, accr, acci);
         signal_b(bar_b, lane);
         for (int k = 1; k <= a.order; ++k) {
           if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
           ph_m ^= 1u;
-          load_d<CWP, SW>(trow, j0, dr, di);   // t_k
+          load_d<CWP, SW, true>(trow, j0, dr, di);   // t_k
           const float s = 1.f / (float)(k + 1);
 #pragma unroll
           for (int jj = 0; jj < SW; ++jj) {
@@ -299,14 +308,14 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
             dr[jj] = tr * s;   // next operand t_k / (k + 1)
             di[jj] = ti * s;
           }
-          if (k < a.order) write_b<CWP, SW>(bhi, blo, p, j0, dr, di, true);
-          else write_b<CWP, SW>(bhi, blo, p, j0, accr, acci, false);
+          if (k < a.order) write_b<CWP, SW>(bsm, p, j0, dr, di);
+          else write_b<CWP, SW>(bsm, p, j0, accr, acci);
           signal_b(bar_b, lane);
         }
         if (!go) break;
         if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
         ph_m ^= 1u;
-        load_d<CWP, SW>(trow, j0, dr, di);   // F acc
+        load_d<CWP, SW, false>(trow, j0, dr, di);   // F acc
 #pragma unroll
         for (int jj = 0; jj < SW; ++jj)
           if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
@@ -634,9 +643,8 @@ PropGeom prop_geom(int N, int ncol) {
     t.off_vlo = npad * 512;
     t.off_fhi = npad * 1024;
     t.off_flo = npad * 1280;
-    t.off_bhi = npad * 1536;
-    t.off_blo = t.off_bhi + cwp * 1024;
-    int end = t.off_blo + cwp * 1024;
+    t.off_b = npad * 1536;
+    int end = t.off_b + cwp * 1024;   // 2 K atoms of 4 cwp rows
     // an M = 128 product reads 16 KiB from the start of every A atom, rows npad..127 included
     end = std::max(end, t.off_flo + npad * 128 + 16384);
     t.off_bar = (end + 63) / 64 * 64;
@@ -736,8 +744,8 @@ afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, floa
   p.N = st->N; p.npad = g.npad; p.nk = g.nk; p.ncol = st->ncol; p.cw = g.cw; p.nch = g.nch;
   p.order = order; p.W = st->W;
   p.off_vlo = g.off_vlo; p.off_fhi = g.off_fhi; p.off_flo = g.off_flo;
-  p.off_bhi = g.off_bhi; p.off_blo = g.off_blo; p.off_bar = g.off_bar;
-  p.tmem_cols = 2 * g.cwp <= 32 ? 32 : 64;
+  p.off_b = g.off_b; p.off_bar = g.off_bar;
+  p.tmem_cols = 8 * g.cwp <= 64 ? 64 : (8 * g.cwp <= 128 ? 128 : 256);   // D1 and D2, 4 cwp columns each
   p.psi = psi;
   p.w = w;
   p.status = status;
