@@ -202,8 +202,8 @@ afqmc_status afqmc_cv_info(afqmc_ctx* ctx, int32_t* dim, uint64_t* nparams, int3
 
 /* Project autotuner: times `steps` propagation + energy steps of every candidate setting
  * (CUDA-core GEMM block tile 64 / 32, tensor-core, fused CUDA-core or batched-GEMM propagation and
- * the fused kernel's register tile,
- * 1 / 2 / 4 tensor-core epilogue warpgroups) on the context's own walkers, restores the walkers,
+ * the fused kernel's register tile, 1 to 4 tensor-core exchange epilogue warpgroups and the
+ * exchange form) on the context's own walkers, restores the walkers,
  * keeps the fastest.
  * chosen (may be NULL) receives it; afqmc_set_tuning applies a setting directly. */
 typedef struct {
@@ -213,6 +213,8 @@ typedef struct {
                              2 fused CUDA-core kernel */
   int32_t exch_groups;    /* tensor-core exchange epilogue warpgroups (0: largest that fits) */
   int32_t prop_tile;      /* fused propagation register tile: 0: 4 rows x 2 columns, 1: 8 x 2, 2: 4 x 4 */
+  int32_t exch_form;      /* tensor-core exchange: 0 the rotated Cholesky tile resident in tensor memory
+                             where it fits (BF16x3, n <= 32), else streamed; 1 both operands streamed */
   float ms_per_step;      /* measured by afqmc_autotune */
 } afqmc_tuning;
 afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen);

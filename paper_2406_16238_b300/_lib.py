@@ -47,7 +47,7 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_cap", ctypes.c_int32), ("prop_path", ctypes.c_int32), ("exch_groups", ctypes.c_int32),
-                ("prop_tile", ctypes.c_int32), ("ms_per_step", ctypes.c_float)]
+                ("prop_tile", ctypes.c_int32), ("exch_form", ctypes.c_int32), ("ms_per_step", ctypes.c_float)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -275,8 +275,8 @@ class Afqmc:
         _check(self._lib.afqmc_autotune(self._ctx, int(steps), ctypes.byref(t)))
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
-    def set_tuning(self, tile_cap=4, prop_path=0, exch_groups=0, prop_tile=0):
-        t = Tuning(int(tile_cap), int(prop_path), int(exch_groups), int(prop_tile), 0.0)
+    def set_tuning(self, tile_cap=4, prop_path=0, exch_groups=0, prop_tile=0, exch_form=0):
+        t = Tuning(int(tile_cap), int(prop_path), int(exch_groups), int(prop_tile), int(exch_form), 0.0)
         _check(self._lib.afqmc_set_tuning(self._ctx, ctypes.byref(t)))
 
     def set_graphs(self, enable=True):

@@ -1398,7 +1398,8 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t) {
   ctx->tile_cap = t->tile_cap;
   ctx->prop_path = (t->prop_path >= 0 && t->prop_path <= 2) ? t->prop_path : 0;
   ctx->prop_tile = (t->prop_tile >= 0 && t->prop_tile <= 2) ? t->prop_tile : 0;
-  if (ctx->d.tensor()) tc::set_exchange_groups(&ctx->tcs, ctx->at<char>(ctx->L.tc), t->exch_groups);
+  if (ctx->d.tensor())
+    tc::set_exchange_groups(&ctx->tcs, ctx->at<char>(ctx->L.tc), t->exch_groups, t->exch_form == 1 ? 1 : 0);
   return AFQMC_OK;
 }
 
@@ -1432,10 +1433,12 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
   if (d.tensor()) groups = {1, 2, 3, 4};
   for (int tc_cap : {4, 2})
     for (int g : groups) {
-      if (tc_ok) cands.push_back(afqmc_tuning{tc_cap, 0, g, 0, 0.f});
+      if (tc_ok)
+        for (int form : {0, 1})
+          if (form == 0 || (tc_cap == 4 && d.prec == AFQMC_PREC_BF16X3)) cands.push_back(afqmc_tuning{tc_cap, 0, g, 0, form, 0.f});
       if (fused_ok)
-        for (int pt : {0, 1, 2}) cands.push_back(afqmc_tuning{tc_cap, 2, g, pt, 0.f});
-      cands.push_back(afqmc_tuning{tc_cap, 1, g, 0, 0.f});
+        for (int pt : {0, 1, 2}) cands.push_back(afqmc_tuning{tc_cap, 2, g, pt, 0, 0.f});
+      cands.push_back(afqmc_tuning{tc_cap, 1, g, 0, 0, 0.f});
     }
   const bool graphs_was = ctx->graphs_on, prof_was = ctx->prof;
   ctx->graphs_on = false;
@@ -1443,7 +1446,7 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  afqmc_tuning best{4, 0, 0, 0, 1e30f};
+  afqmc_tuning best{4, 0, 0, 0, 0, 1e30f};
   double* scratch = ctx->at<double>(ctx->L.hist) + 4 * (kHistory - 1);
   for (auto& cnd : cands) {
     if ((st = afqmc_set_tuning(ctx, &cnd)) != AFQMC_OK) break;

@@ -55,11 +55,14 @@ struct Params {
   int npad, kq;   // plane rows, plane row pitch (elements)
   // exchange: an extra warp draws the step's normals (nrm.x != nullptr)
   NormalsJob nrm;
+  // exchange with the Ltilde tile in tensor memory: segment length and the tensor-memory column of
+  // its hi half (the lo half follows kst / 2 columns later)
+  int kst, a0;
 };
 
 
 // ----------------------------------------------------------------------------- epilogues
-// Exchange epilogue state of one warpgroup: [ok flags 2 x int (16 B)] [buf 128 x (2n+1) floats]
+// Exchange epilogue state of one warpgroup: [ok flags 2 x int (16 B)] [buf: the staged tile]
 // [diag 128 float2] [red 4 float2].  Each group handles one walker per tile (wpt == groups).
 struct EpiSmem {
   float* buf;
@@ -72,13 +75,17 @@ struct EpiSmem {
 // (g n + b) it reads at column a then fall in distinct banks for the 32 rows of a warp.
 __host__ __device__ __forceinline__ int exch_ld(int n) { return 32 * ((2 * n + 31) / 32) + 1; }
 __host__ __device__ __forceinline__ int exch_buf_bytes(int n) { return ((128 * exch_ld(n) * 4) + 15) & ~15; }
+// Register-row epilogue: rows of complex entries (float2), pitch n | 1 entries.  An odd pitch puts
+// the 8-byte entries of 16 consecutive rows (one half-warp access) in distinct bank pairs.
+__host__ __device__ __forceinline__ int exch_ld2(int n) { return n | 1; }
+__host__ __device__ __forceinline__ int exch_buf2_bytes(int n) { return ((128 * exch_ld2(n) * 8) + 15) & ~15; }
 
-__device__ __forceinline__ EpiSmem epi_smem(uint8_t* base, const Params& p, int group) {
+__device__ __forceinline__ EpiSmem epi_smem(uint8_t* base, const Params& p, int group, bool reg) {
   EpiSmem e;
   uint8_t* g = base + (size_t)group * p.g.epi_bytes;
   e.ok = reinterpret_cast<int*>(g);
   e.buf = reinterpret_cast<float*>(g + 16);
-  e.diag = reinterpret_cast<float2*>(g + 16 + exch_buf_bytes(p.n));
+  e.diag = reinterpret_cast<float2*>(g + 16 + (reg ? exch_buf2_bytes(p.n) : exch_buf_bytes(p.n)));
   e.red = e.diag + 128;
   return e;
 }
@@ -200,17 +207,20 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
 
 // As exchange_tile, with the thread's own row T_ab (b < n <= NB) kept in registers: the real
 // parts come from columns [v 2n, v 2n + NB), the imaginary parts from [v 2n + n, v 2n + n + NB)
-// (the columns past the walker are read and ignored), and only the partner entries T_ba are
-// read back from shared memory.
+// (the columns past the walker are read and ignored).  The row goes to shared memory as complex
+// entries, and each partner entry T_ba is read back with one 8-byte load.  After the second
+// barrier the four warps share the per-gamma traces (force bias): warp k sums the diagonal of
+// gammas k and k + 4 (then k + 8, k + 12, ...) with one lane per diagonal entry.
 template <int NB>
 __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
                                   int wig, int r, int lane) {
-  const int n = p.n, n2 = 2 * n, ld = exch_ld(n), rows = p.gpt * n;
+  const int n = p.n, n2 = 2 * n, ld2 = exch_ld2(n), rows = p.gpt * n;
   const int bar_id = 1 + group;
   const int g = r / n, a = r - (r / n) * n;
   const bool live = r < rows && mt * p.gpt + g < p.X;
-  float* rowp = e.buf + r * ld;
-  const float* blk = e.buf + (g * n) * ld;
+  float2* buf = reinterpret_cast<float2*>(e.buf);
+  float2* rowp = buf + r * ld2;
+  const float2* part = buf + (g * n) * ld2 + a;   // T_ba at part[b ld2]
   for (int v = group; v < p.wpt; v += p.g.epi_groups) {
     uint32_t ur[NB], ui[NB];
     tmem_ld_cols<NB>(tacc + (uint32_t)(v * n2), ur);
@@ -218,10 +228,7 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
     tmem_wait();
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-      if (b < n) {
-        rowp[b] = __uint_as_float(ur[b]);
-        rowp[n + b] = __uint_as_float(ui[b]);
-      }
+      if (b < n) rowp[b] = make_float2(__uint_as_float(ur[b]), __uint_as_float(ui[b]));
     named_bar(bar_id, 128);
     float er0 = 0.f, ei0 = 0.f, er1 = 0.f, ei1 = 0.f;
     float2 dg = make_float2(0.f, 0.f);
@@ -230,22 +237,22 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
       for (int b = 0; b < NB; b += 2) {
         if (b < n) {
           const float tr = __uint_as_float(ur[b]), ti = __uint_as_float(ui[b]);
-          const float pr = blk[b * ld + a], pi = blk[b * ld + n + a];
-          er0 = fmaf(tr, pr, er0);
-          er0 = fmaf(-ti, pi, er0);
-          ei0 = fmaf(tr, pi, ei0);
-          ei0 = fmaf(ti, pr, ei0);
+          const float2 q = part[b * ld2];
+          er0 = fmaf(tr, q.x, er0);
+          er0 = fmaf(-ti, q.y, er0);
+          ei0 = fmaf(tr, q.y, ei0);
+          ei0 = fmaf(ti, q.x, ei0);
         }
         if (b + 1 < n) {
           const float tr = __uint_as_float(ur[b + 1]), ti = __uint_as_float(ui[b + 1]);
-          const float pr = blk[(b + 1) * ld + a], pi = blk[(b + 1) * ld + n + a];
-          er1 = fmaf(tr, pr, er1);
-          er1 = fmaf(-ti, pi, er1);
-          ei1 = fmaf(tr, pi, ei1);
-          ei1 = fmaf(ti, pr, ei1);
+          const float2 q = part[(b + 1) * ld2];
+          er1 = fmaf(tr, q.x, er1);
+          er1 = fmaf(-ti, q.y, er1);
+          ei1 = fmaf(tr, q.y, ei1);
+          ei1 = fmaf(ti, q.x, ei1);
         }
       }
-      dg = make_float2(rowp[a], rowp[n + a]);
+      dg = rowp[a];
     }
     e.diag[r] = dg;
     float er = er0 + er1, ei = ei0 + ei1;
@@ -254,24 +261,27 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
     if (lane == 0) e.red[wig] = make_float2(er, ei);
     named_bar(bar_id, 128);
     const int w = nt * p.wpt + v;
-    if (w < p.W && wig == 0) {   // 4 lanes per gamma: strided partial sums of the diagonal, then 2 shuffles
-      for (int g0 = 0; p.vbias && g0 < p.gpt; g0 += 8) {
-        const int gl = g0 + (lane >> 2), part = lane & 3;
-        float sr = 0.f, si = 0.f;
-        if (gl < p.gpt)
-          for (int aa = part; aa < n; aa += 4) {
-            const float2 d = e.diag[gl * n + aa];
-            sr += d.x;
-            si += d.y;
-          }
-        sr += __shfl_xor_sync(0xffffffffu, sr, 1);
-        si += __shfl_xor_sync(0xffffffffu, si, 1);
-        sr += __shfl_xor_sync(0xffffffffu, sr, 2);
-        si += __shfl_xor_sync(0xffffffffu, si, 2);
-        const int gam = mt * p.gpt + gl;
-        if (part == 0 && gl < p.gpt && gam < p.X) {
+    if (w < p.W) {
+      for (int g0 = wig; p.vbias && g0 < p.gpt; g0 += 8) {   // gammas g0 and g0 + 4
+        const int g1 = g0 + 4;
+        float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
+        if (lane < n) {
+          d0 = e.diag[g0 * n + lane];
+          if (g1 < p.gpt) d1 = e.diag[g1 * n + lane];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          d0.x += __shfl_xor_sync(0xffffffffu, d0.x, o);
+          d0.y += __shfl_xor_sync(0xffffffffu, d0.y, o);
+          d1.x += __shfl_xor_sync(0xffffffffu, d1.x, o);
+          d1.y += __shfl_xor_sync(0xffffffffu, d1.y, o);
+        }
+        const int gg = lane == 0 ? g0 : g1;
+        const float2 d = lane == 0 ? d0 : d1;
+        const int gam = mt * p.gpt + gg;
+        if (lane < 2 && gg < p.gpt && gam < p.X) {
           float2* dst = p.vbias + (size_t)w * p.X + gam;
-          float2 val = make_float2(p.smul * sr, p.smul * si);
+          float2 val = make_float2(p.smul * d.x, p.smul * d.y);
           if (p.vbias_add) {
             val.x += dst->x;
             val.y += dst->y;
@@ -279,7 +289,7 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
           *dst = val;
         }
       }
-      if (lane == 0) {
+      if (wig == 0 && lane == 0) {
         const float sr = (e.red[0].x + e.red[1].x) + (e.red[2].x + e.red[3].x);
         const float si = (e.red[0].y + e.red[1].y) + (e.red[2].y + e.red[3].y);
         p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] =
@@ -287,7 +297,7 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
       }
     }
     // No barrier before the next walker: every partner read of buf happened before the barrier
-    // above, and e.diag / e.red are read by warp 0 before it reaches the next walker's barrier.
+    // above, and e.diag / e.red are read before each warp reaches the next walker's first barrier.
   }
 }
 
@@ -335,6 +345,24 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
       dst[0] = hi;
       dst[2 * plane] = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
     }
+  }
+}
+
+// The step's normals drawn by one warp per CTA (pairs strided over the grid); tab_mem holds the
+// series tables.
+__device__ void draw_normals_warp(const NormalsJob& nj, uint8_t* tab_mem, int lane) {
+  SeriesTables& tab = *reinterpret_cast<SeriesTables*>(tab_mem);
+  if (lane == 0) fill_series_tables(&tab);
+  __syncwarp();
+  const unsigned long long st = *nj.step;
+  const int npairs = (nj.X + 1) / 2;
+  const long long total = (long long)nj.W * npairs;
+  for (long long i = (long long)blockIdx.x * 32 + lane; i < total; i += (long long)gridDim.x * 32) {
+    const int w = (int)(i / npairs), j = (int)(i - (long long)w * npairs);
+    double z0, z1;
+    normal_pair(nj.seed, (uint32_t)j, (uint32_t)w, st, 0u, tab, &z0, &z1);
+    nj.x[(size_t)w * nj.X + 2 * j] = z0;
+    if (2 * j + 1 < nj.X) nj.x[(size_t)w * nj.X + 2 * j + 1] = z1;
   }
 }
 
@@ -428,25 +456,11 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
     }
   } else if (warp >= 2 + 4 * g.epi_groups) {   // spare warp: the step's normals (binary64 pipe)
-    if (EPI == 0 && p.nrm.x) {
-      SeriesTables& tab = *reinterpret_cast<SeriesTables*>(reinterpret_cast<uint8_t*>(bars) + 256);
-      if (lane == 0) fill_series_tables(&tab);
-      __syncwarp();
-      const unsigned long long st = *p.nrm.step;
-      const int npairs = (p.nrm.X + 1) / 2;
-      const long long total = (long long)p.nrm.W * npairs;
-      for (long long i = (long long)blockIdx.x * 32 + lane; i < total; i += (long long)gridDim.x * 32) {
-        const int w = (int)(i / npairs), j = (int)(i - (long long)w * npairs);
-        double z0, z1;
-        normal_pair(p.nrm.seed, (uint32_t)j, (uint32_t)w, st, 0u, tab, &z0, &z1);
-        p.nrm.x[(size_t)w * p.nrm.X + 2 * j] = z0;
-        if (2 * j + 1 < p.nrm.X) p.nrm.x[(size_t)w * p.nrm.X + 2 * j + 1] = z1;
-      }
-    }
+    if (EPI == 0 && p.nrm.x) draw_normals_warp(p.nrm, reinterpret_cast<uint8_t*>(bars) + 256, lane);
   } else {   // epilogue warps
     const int ew = warp - 2, group = ew >> 2, wig = ew & 3, q = warp & 3;
     const int r = 32 * q + lane;
-    const EpiSmem es = epi_smem(epi_base, p, group);
+    const EpiSmem es = epi_smem(epi_base, p, group, NB > 0);
     int it = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
       const int acc = it & 1;
@@ -466,6 +480,192 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       else if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
       else if (EPI == 1) store_tile(p, mt, nt, tacc, group, r);
       else store_planes(p, mt, nt, tacc, group, r);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+  }
+  if (threadIdx.x == 0 && *abort_flag) {   // let in-flight copies and MMAs drain before freeing tensor memory
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < 2000000ull) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(g.tmem_cols) : "memory");
+}
+
+
+// ----------------------------------------------------------------------------- exchange, Ltilde resident
+// The exchange contraction with its A operand, the Ltilde tile of gpt gammas (hi and lo halves), held
+// in tensor memory.  Each CTA takes a contiguous range of tiles in M-major order, so the tile is
+// staged through the shared-memory ring and copied into tensor memory (tcgen05.cp) once or twice per
+// CTA; Theta of the tile's walkers streams through the ring as [hi | lo] K blocks, and each 16-wide
+// k-step issues A_hi B_hi, A_lo B_hi and A_hi B_lo with A read from tensor memory.  Shared memory
+// then carries each B byte once (TMA write, MMA read) plus the epilogue's transposition, against
+// three copies of every operand in the streamed form (K-concatenated [hi | lo | hi] x [hi | hi | lo]).
+// Tensor memory: accumulators [0, bn) and [bn, 2 bn), A hi [a0, a0 + kst / 2), A lo up to 512.
+// Roles, epilogue and bounded waits as in k_tc_gemm.
+__host__ __device__ __forceinline__ int tm_stage_bytes(int bn) { return 2 * (kStageA > bn * 128 ? kStageA : bn * 128); }
+
+template <int NB>
+__global__ void __launch_bounds__(608, 1) k_exch_tm(const __grid_constant__ CUtensorMap mapA,
+                                                    const __grid_constant__ CUtensorMap mapB, const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const Geom& g = p.g;
+  const int stage_bytes = tm_stage_bytes(g.bn);
+  uint8_t* epi_base = smem + (size_t)g.stages * stage_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + (size_t)g.epi_groups * g.epi_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + g.stages;
+  uint64_t* tfull = bars + 2 * g.stages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* adone = tempty + 2;   // MMAs done with the resident tile before it is replaced
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(adone + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long tiles = (long long)g.m_tiles * g.n_tiles;
+  const int t_beg = (int)(tiles * blockIdx.x / gridDim.x), t_end = (int)(tiles * (blockIdx.x + 1) / gridDim.x);
+  const int nks = p.kst / 16, nkb = (p.kst + kBK - 1) / kBK, half = p.kst / 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < g.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4 * g.epi_groups);
+    }
+    mbar_init(adone, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(g.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {   // TMA producer: the A tile (hi, lo) on every change of mt, then B (hi, lo) per tile
+      int stage = 0;
+      uint32_t ph = 0;
+      bool go = true;
+      int mt_prev = -1;
+      for (int t = t_beg; t < t_end && go; ++t) {
+        const int mt = t / g.n_tiles, nt = t - (t / g.n_tiles) * g.n_tiles;
+        for (int part = (mt != mt_prev ? 0 : 1); part < 2 && go; ++part)
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
+            uint8_t* st = smem + (size_t)stage * stage_bytes;
+            if (part == 0) {
+              mbar_expect_tx(&full[stage], 2u * kStageA);
+              tma_load_2d(st, &mapA, &full[stage], kb * kBK, mt * g.m_step);
+              tma_load_2d(st + kStageA, &mapA, &full[stage], p.kst + kb * kBK, mt * g.m_step);
+            } else {
+              mbar_expect_tx(&full[stage], (uint32_t)(2 * g.bn * 128));
+              tma_load_2d(st, &mapB, &full[stage], kb * kBK, nt * g.n_step);
+              tma_load_2d(st + g.bn * 128, &mapB, &full[stage], 2 * p.kst + kb * kBK, nt * g.n_step);
+            }
+            if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+          }
+        mt_prev = mt;
+      }
+      if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      int stage = 0;
+      uint32_t ph = 0, ph_a = 0;
+      int it = 0, mt_prev = -1;
+      bool go = true;
+      const uint32_t idesc = idesc_bf16(g.bn);
+      const uint32_t a_hi = tmem_base + (uint32_t)p.a0, a_lo = a_hi + (uint32_t)half;
+      for (int t = t_beg; t < t_end && go; ++t, ++it) {
+        const int mt = t / g.n_tiles;
+        if (mt != mt_prev) {   // replace the resident tile once the MMAs reading it have completed
+          if (mt_prev >= 0) {
+            umma_commit(adone);
+            if (!mbar_wait(adone, ph_a, abort_flag)) { go = false; break; }
+            ph_a ^= 1u;
+          }
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k) {
+              const int ks = kb * (kBK / 16) + k;
+              if (ks < nks) {
+                tmem_cp_128x256b(a_hi + (uint32_t)(ks * 8), sw128_desc(sa + 32 * k));
+                tmem_cp_128x256b(a_lo + (uint32_t)(ks * 8), sw128_desc(sa + kStageA + 32 * k));
+              }
+            }
+            umma_commit(&empty[stage]);
+            if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+          }
+          if (!go) break;
+          mt_prev = mt;
+        }
+        const int acc = it & 1;
+        const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+        if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { go = false; break; }
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(acc * g.bn);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
+          tc_fence_after();
+          const uint32_t sb = smem_u32(smem + (size_t)stage * stage_bytes);
+          const uint64_t dbh = sw128_desc(sb), dbl = sw128_desc(sb + (uint32_t)(g.bn * 128));
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            const int ks = kb * (kBK / 16) + k;
+            if (ks < nks) {
+              const uint32_t ah = a_hi + (uint32_t)(ks * 8), al = a_lo + (uint32_t)(ks * 8);
+              umma_bf16_ts(dtm, ah, dbh + (uint64_t)(2 * k), idesc, ks > 0 ? 1u : 0u);   // A hi B hi
+              umma_bf16_ts(dtm, al, dbh + (uint64_t)(2 * k), idesc, 1u);                 // A lo B hi
+              umma_bf16_ts(dtm, ah, dbl + (uint64_t)(2 * k), idesc, 1u);                 // A hi B lo
+            }
+          }
+          umma_commit(&empty[stage]);
+          if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+        }
+        if (!go) break;
+        umma_commit(&tfull[acc]);
+      }
+      if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+    }
+  } else if (warp >= 2 + 4 * g.epi_groups) {   // spare warp: the step's normals (binary64 pipe)
+    if (p.nrm.x) draw_normals_warp(p.nrm, reinterpret_cast<uint8_t*>(bars) + 256, lane);
+  } else {   // epilogue warps
+    const int ew = warp - 2, group = ew >> 2, wig = ew & 3, q = warp & 3;
+    const int r = 32 * q + lane;
+    const EpiSmem es = epi_smem(epi_base, p, group, true);
+    int it = 0;
+    for (int t = t_beg; t < t_end; ++t, ++it) {
+      const int acc = it & 1;
+      const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+      if (wig == 0 && lane == 0) {   // slot it & 1 is rewritten two tiles later, after this group's next barrier
+        const bool ok = mbar_wait(&tfull[acc], aph, abort_flag);
+        if (!ok) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+        es.ok[it & 1] = ok ? 1 : 0;
+      }
+      named_bar(1 + group, 128);   // also: every thread of the group is done with the previous tile's buffers
+      const int ok = es.ok[it & 1];
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
+      const int mt = t / g.n_tiles, nt = t - (t / g.n_tiles) * g.n_tiles;
+      exchange_tile_reg<NB>(p, mt, nt, tacc, es, group, wig, r, lane);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -573,7 +773,9 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-int epi_bytes_exchange(int n) { return 16 + exch_buf_bytes(n) + 128 * 8 + 4 * 8; }
+int epi_bytes_exchange(int n, bool reg) {
+  return 16 + (reg ? exch_buf2_bytes(n) : exch_buf_bytes(n)) + 128 * 8 + 4 * 8;
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -620,6 +822,13 @@ int tmem_cols_for(int bn) {
   return c;
 }
 
+// The register-row exchange epilogue applies when n <= 32 and the imaginary-part loads of the last
+// walker of the second accumulator stay inside tensor memory.
+bool exchange_reg(int n, int wpt, int bn) {
+  const int nb = (n + 7) / 8 * 8;
+  return nb <= 32 && bn + (wpt - 1) * 2 * n + n + nb <= tmem_cols_for(bn);
+}
+
 // Pick the stage count for a given B box height and epilogue footprint.
 bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
   g->epi_groups = epi_groups;
@@ -658,6 +867,26 @@ afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, c
   return AFQMC_OK;
 }
 
+template <int NB>
+afqmc_status launch_tm(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, const Params& p, cudaStream_t s,
+                       unsigned long long* launches, char* err, size_t errlen) {
+  const size_t sm = 1024 + (size_t)g.stages * tm_stage_bytes(g.bn) + (size_t)g.epi_groups * g.epi_bytes + kTailBytes;
+  if (sm > (size_t)kMaxSmem) {
+    snprintf(err, errlen, "tcgen05 exchange: %zu bytes of shared memory exceed the limit", sm);
+    return AFQMC_EINVAL;
+  }
+  const int tiles = g.m_tiles * g.n_tiles;
+  const int grid = std::min(tiles, num_sms());
+  k_exch_tm<NB><<<grid, 64 + 128 * g.epi_groups + (p.nrm.x ? 32 : 0), sm, s>>>(a, b, p);
+  ++*launches;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "tcgen05 exchange launch: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
 }  // namespace
 
 // Largest epilogue group count (<= 4, <= walkers per tile) whose buffers fit beside two stages of
@@ -667,11 +896,48 @@ int exchange_groups(int n, int wpt0) {
     const int wpt = wpt0 / g * g;
     const int bn = (wpt * 2 * n + 15) / 16 * 16;
     const int stage_bytes = kStageA + bn * kBK * 2;
-    const int need = 1024 + g * ((epi_bytes_exchange(n) + 15) & ~15) + kTailBytes + 2 * stage_bytes;
+    const int need =
+        1024 + g * ((epi_bytes_exchange(n, exchange_reg(n, wpt, bn)) + 15) & ~15) + kTailBytes + 2 * stage_bytes;
     if (need <= kMaxSmem) return g;
   }
   return 1;
 }
+
+// Walker tiling of one block: epilogue groups, walkers per tile, MMA N and form.  The resident-A
+// form (k_exch_tm, BF16x3 only) needs the register-row epilogue (n <= 32), 2 bn + kst <= 512 tensor-memory
+// columns and two ring stages beside the epilogue buffers; it takes the largest group count (at
+// most `groups` when that is > 0) for which some multiple of it walkers fits, and the most walkers.
+// Otherwise (or with form 1) the streamed form with the largest group count that fits.
+namespace {
+void exchange_config(TcState* st, BlockMaps& bm, int groups, int form) {
+  const int n = bm.n, wpt0 = 256 / (2 * n);
+  if (form != 1 && st->nseg == 3 && (n + 7) / 8 * 8 <= 32) {
+    for (int g = std::min(4, wpt0); g >= 1; --g) {
+      if (groups > 0 && g > groups) continue;
+      int wpt = 0;
+      for (int w = g; w <= wpt0; w += g)
+        if (2 * ((w * 2 * n + 15) / 16 * 16) + st->kst <= 512) wpt = w;
+      if (wpt == 0) continue;
+      const int bn = (wpt * 2 * n + 15) / 16 * 16;
+      const int need = 1024 + g * ((epi_bytes_exchange(n, true) + 15) & ~15) + kTailBytes + 2 * tm_stage_bytes(bn);
+      if (need > kMaxSmem) continue;
+      bm.groups = g;
+      bm.wpt = wpt;
+      bm.bn = bn;
+      bm.form = 1;
+      bm.n_tiles = (st->W + wpt - 1) / wpt;
+      return;
+    }
+  }
+  int g = exchange_groups(n, wpt0);
+  if (groups > 0) g = std::max(1, std::min(g, groups));
+  bm.groups = g;
+  bm.wpt = wpt0 / g * g;
+  bm.bn = (bm.wpt * 2 * n + 15) / 16 * 16;
+  bm.form = 0;
+  bm.n_tiles = (st->W + bm.wpt - 1) / bm.wpt;
+}
+}  // namespace
 
 size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk) {
   if (prec != AFQMC_PREC_BF16 && prec != AFQMC_PREC_BF16X3) return 0;
@@ -688,12 +954,8 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     b.c0 = c0[s];
     if (b.n == 0) { b.m_tiles = b.n_tiles = 0; continue; }
     b.gpt = kBM / b.n;
-    b.wpt = 256 / (2 * b.n);
-    b.groups = exchange_groups(b.n, b.wpt);
-    b.wpt = b.wpt / b.groups * b.groups;   // every epilogue group takes the same number of walkers
-    b.bn = (b.wpt * 2 * b.n + 15) / 16 * 16;
+    exchange_config(st, b, 0, 0);   // every epilogue group takes the same number of walkers
     b.m_tiles = (X + b.gpt - 1) / b.gpt;
-    b.n_tiles = (W + b.wpt - 1) / b.wpt;
     b.off_l = cur;
     cur = align256(cur + (size_t)X * b.n * st->nseg * st->kst * 2);
     b.off_th = cur;
@@ -725,18 +987,13 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   return cur;
 }
 
-int set_exchange_groups(TcState* st, char* tcbuf, int groups) {
+int set_exchange_groups(TcState* st, char* tcbuf, int groups, int form) {
   int used = 0;
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
     if (bm.n == 0) continue;
-    const int wpt0 = 256 / (2 * bm.n);
-    int g = exchange_groups(bm.n, wpt0);
-    if (groups > 0) g = std::max(1, std::min(g, groups));
-    bm.groups = g;
-    bm.wpt = wpt0 / g * g;
-    bm.bn = (bm.wpt * 2 * bm.n + 15) / 16 * 16;
-    bm.n_tiles = (st->W + bm.wpt - 1) / bm.wpt;
+    exchange_config(st, bm, groups, form);
+    const int g = bm.groups;
     if (tcbuf)
       make_map(&bm.map_th, tcbuf + bm.off_th, (unsigned long long)st->W * 2 * bm.n,
                (unsigned long long)st->nseg * st->kst, (unsigned)bm.bn);
@@ -799,7 +1056,11 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
       cudaFuncSetAttribute(k_tc_gemm<0, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_tc_gemm<0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_tc_gemm<0, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+      cudaFuncSetAttribute(k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_exch_tm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_exch_tm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_exch_tm<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_exch_tm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
     snprintf(err, errlen, "tcgen05 GEMM: cannot reserve shared memory");
     return AFQMC_ECUDA;
   }
@@ -829,12 +1090,25 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     g.m_step = bm.gpt * bm.n;
     g.n_step = bm.wpt * 2 * bm.n;
     g.bn = bm.bn;
-    const int epb = epi_bytes_exchange(bm.n);
-    if (!finish_geom(&g, epb, bm.groups)) {
+    const bool reg = bm.form == 1 || exchange_reg(bm.n, bm.wpt, g.bn);
+    const int epb = epi_bytes_exchange(bm.n, reg);
+    if (bm.form == 0 && !finish_geom(&g, epb, bm.groups)) {
       snprintf(err, errlen, "tcgen05 exchange: n = %d does not fit shared memory", bm.n);
       return AFQMC_EINVAL;
     }
     Params p{};
+    if (bm.form == 1) {   // Ltilde resident in tensor memory: its own ring and tensor-memory plan
+      g.epi_groups = bm.groups;
+      g.epi_bytes = (epi_bytes_exchange(bm.n, true) + 15) & ~15;
+      g.stages = std::min(4, (kMaxSmem - 1024 - g.epi_groups * g.epi_bytes - kTailBytes) / tm_stage_bytes(g.bn));
+      g.tmem_cols = 512;
+      if (g.stages < 2 || 2 * g.bn + st->kst > 512) {
+        snprintf(err, errlen, "tcgen05 exchange: resident form does not fit (n = %d)", bm.n);
+        return AFQMC_EINVAL;
+      }
+      p.kst = st->kst;
+      p.a0 = 512 - st->kst;
+    }
     p.g = g;
     p.status = status;
     p.W = nw; p.X = st->X; p.n = bm.n; p.gpt = bm.gpt; p.wpt = bm.wpt;
@@ -843,11 +1117,14 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     p.vbias = vbias;
     p.exch_part = exch_part;
     if (first && nj) p.nrm = *nj;
-    // register-row epilogue when the imaginary-part loads of the last walker stay inside tensor memory
     const int nb = (bm.n + 7) / 8 * 8;
-    const bool reg = nb <= 32 && g.bn + (bm.wpt - 1) * 2 * bm.n + bm.n + nb <= g.tmem_cols;
     afqmc_status r;
-    if (!reg) r = launch<0>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    if (bm.form == 1) {
+      if (nb == 8) r = launch_tm<8>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+      else if (nb == 16) r = launch_tm<16>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+      else if (nb == 24) r = launch_tm<24>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+      else r = launch_tm<32>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
+    } else if (!reg) r = launch<0>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
     else if (nb == 8) r = launch<0, 8>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
     else if (nb == 16) r = launch<0, 16>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
     else if (nb == 24) r = launch<0, 24>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);

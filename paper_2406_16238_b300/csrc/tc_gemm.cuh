@@ -19,6 +19,7 @@ struct BlockMaps {
   int gpt, wpt;      // gammas per M tile (gpt * n <= 128), walkers per N tile (wpt * 2n <= 256)
   int bn;            // MMA N (multiple of 16, >= wpt * 2n)
   int groups;        // epilogue warpgroups of the exchange kernel (wpt is a multiple of it)
+  int form;          // 1: the Ltilde tile stays in tensor memory (k_exch_tm), 0: both operands streamed
   int m_tiles, n_tiles;
   size_t off_l, off_th;   // byte offsets of the bf16 Ltilde / Theta^T copies in the tc buffer
   CUtensorMap map_l, map_th;
@@ -47,7 +48,7 @@ PropGeom prop_geom(int N, int ncol);
 
 struct TcState {
   int prec = 0, W = 0, N = 0, X = 0, ncol = 0, nblk = 0;
-  int kst = 0;        // padded length of one K segment of the exchange operands (multiple of 64)
+  int kst = 0;        // padded length of one K segment of the exchange operands (multiple of 16)
   int nseg = 1;       // 1 (BF16) or 3 (BF16x3)
   int nchunk = 0;     // exchange partials per walker (sum of m_tiles over blocks)
   BlockMaps blk[2];
@@ -68,9 +69,10 @@ struct TcState {
 // Fills the geometry of st (no device work) and returns the bytes of the tc buffer.
 size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk);
 
-// Caps the exchange epilogue warpgroups at `groups` (0: largest that fits) and re-derives the walker
-// tiling and the Theta tensor map; returns the groups in use for block 0.
-int set_exchange_groups(TcState* st, char* tcbuf, int groups);
+// Caps the exchange epilogue warpgroups at `groups` (0: largest that fits), selects the form (0: the
+// Ltilde tile resident in tensor memory where it fits, else streamed; 1: streamed) and re-derives
+// the walker tiling and the Theta tensor map; returns the groups in use for block 0.
+int set_exchange_groups(TcState* st, char* tcbuf, int groups, int form = 0);
 
 // One-time bf16 copies of Ltilde (from binary64 [X][ncol][N]) and of L^T (from binary64 [X][N][N]),
 // and the TMA descriptors over the tc buffer.
