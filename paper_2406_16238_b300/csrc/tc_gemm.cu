@@ -76,7 +76,9 @@ struct EpiSmem {
 __host__ __device__ __forceinline__ int exch_ld(int n) { return 32 * ((2 * n + 31) / 32) + 1; }
 __host__ __device__ __forceinline__ int exch_buf_bytes(int n) { return ((128 * exch_ld(n) * 4) + 15) & ~15; }
 // Register-row epilogue: rows of complex entries (float2), pitch n | 1 entries.  An odd pitch puts
-// the 8-byte entries of 16 consecutive rows (one half-warp access) in distinct bank pairs.
+// the 8-byte entries of 16 consecutive rows (one half-warp access) in distinct bank pairs; partner
+// reads whose half-warp spans two gamma blocks may meet 2-way conflicts.  (A pitch with n (ld2 - 1)
+// a multiple of 16 removes those, but the larger buffers cost ring stages and measured slower.)
 __host__ __device__ __forceinline__ int exch_ld2(int n) { return n | 1; }
 __host__ __device__ __forceinline__ int exch_buf2_bytes(int n) { return ((128 * exch_ld2(n) * 8) + 15) & ~15; }
 
@@ -209,8 +211,8 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
 // parts come from columns [v 2n, v 2n + NB), the imaginary parts from [v 2n + n, v 2n + n + NB)
 // (the columns past the walker are read and ignored).  The row goes to shared memory as complex
 // entries, and each partner entry T_ba is read back with one 8-byte load.  After the second
-// barrier the four warps share the per-gamma traces (force bias): warp k sums the diagonal of
-// gammas k and k + 4 (then k + 8, k + 12, ...) with one lane per diagonal entry.
+// barrier the four warps share the per-gamma traces (force bias): warp k sums the diagonals of
+// gammas 2k and 2k + 1 (then 2k + 8, 2k + 9, ...), one half-warp per gamma.
 template <int NB>
 __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
                                   int wig, int r, int lane) {
@@ -262,24 +264,24 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
     named_bar(bar_id, 128);
     const int w = nt * p.wpt + v;
     if (w < p.W) {
-      for (int g0 = wig; p.vbias && g0 < p.gpt; g0 += 8) {   // gammas g0 and g0 + 4
-        const int g1 = g0 + 4;
-        float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
-        if (lane < n) {
-          d0 = e.diag[g0 * n + lane];
-          if (g1 < p.gpt) d1 = e.diag[g1 * n + lane];
+      for (int g0 = 2 * wig; p.vbias && g0 < p.gpt; g0 += 8) {   // half-warp h: gamma g0 + h, 16 lanes
+        const int gg = g0 + (lane >> 4), k = lane & 15;
+        float2 d = make_float2(0.f, 0.f);
+        if (gg < p.gpt) {
+          if (k < n) d = e.diag[gg * n + k];
+          if (k + 16 < n) {
+            const float2 d2 = e.diag[gg * n + k + 16];
+            d.x += d2.x;
+            d.y += d2.y;
+          }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d0.x += __shfl_xor_sync(0xffffffffu, d0.x, o);
-          d0.y += __shfl_xor_sync(0xffffffffu, d0.y, o);
-          d1.x += __shfl_xor_sync(0xffffffffu, d1.x, o);
-          d1.y += __shfl_xor_sync(0xffffffffu, d1.y, o);
+        for (int o = 8; o > 0; o >>= 1) {
+          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
         }
-        const int gg = lane == 0 ? g0 : g1;
-        const float2 d = lane == 0 ? d0 : d1;
         const int gam = mt * p.gpt + gg;
-        if (lane < 2 && gg < p.gpt && gam < p.X) {
+        if (k == 0 && gg < p.gpt && gam < p.X) {
           float2* dst = p.vbias + (size_t)w * p.X + gam;
           float2 val = make_float2(p.smul * d.x, p.smul * d.y);
           if (p.vbias_add) {
