@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
       }
       bool f_ready = false;
       while (wk < a.W && go) {
+        const int nxt = next_live(wk + gridDim.x);
         for (int ch = 0; ch < a.nch && go; ++ch) {
           if (!mbar_wait(bar_b, ph_b, abort_flag)) { go = false; break; }
           ph_b ^= 1u;
@@ -242,6 +243,9 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
             if (ch == 0 && k == 1) {
               if (!mbar_wait(bar_v, ph_v, abort_flag)) { go = false; break; }
               ph_v ^= 1u;
+              if (nxt < a.W)   // the next walker's V into L2 now, into shared memory later
+                for (int pl = 0; pl < 4; ++pl)
+                  for (int at = 0; at < 2; ++at) tma_prefetch_l2_2d(&mapV, 64 * at, (nxt * 4 + pl) * a.npad);
             }
             tc_fence_after();
             product(true);   // V t_{k-1} / k
@@ -249,14 +253,11 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
           if (!go) break;
           if (!mbar_wait(bar_b, ph_b, abort_flag)) { go = false; break; }
           ph_b ^= 1u;
-          if (ch == a.nch - 1) {   // every V product of this walker has completed
-            const int nxt = next_live(wk + gridDim.x);
-            if (nxt < a.W) issue_v(nxt);
-          }
+          if (ch == a.nch - 1 && nxt < a.W) issue_v(nxt);   // every V product of this walker has completed
           tc_fence_after();
           product(false);   // F acc
         }
-        wk = next_live(wk + gridDim.x);
+        wk = nxt;
       }
       if (!go) {
         atomicOr(a.status, kStatusTimeout);
@@ -272,54 +273,67 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
     uint32_t ph_m = 0;
     bool go = true;
     float accr[SW], acci[SW], dr[SW], di[SW];
-    for (int wk = next_live(blockIdx.x); wk < a.W && go; wk = next_live(wk + gridDim.x)) {
-      for (int ch = 0; ch < a.nch; ++ch) {
-        const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
-        float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol + c0;
+    float2 nxv[SW];   // this thread's psi slice of the next (walker, chunk), loaded one item ahead
+    auto load_slice = [&](int w_, int c_) {
+      const int c0 = c_ * a.cw, cwn = min(a.cw, a.ncol - c0);
+      const float2* src = a.psi + ((size_t)w_ * a.N + (row ? p : 0)) * a.ncol + c0;
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) nxv[jj] = (row && j0 + jj < cwn) ? src[j0 + jj] : make_float2(0.f, 0.f);
+    };
+    int wk = next_live(blockIdx.x), ch = 0;
+    if (wk < a.W) load_slice(wk, 0);
+    while (wk < a.W && go) {
+      const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
+      float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol + c0;
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) {
+        accr[jj] = dr[jj] = nxv[jj].x;
+        acci[jj] = di[jj] = nxv[jj].y;
+      }
+      int nwk = wk, nch = ch + 1;
+      if (nch == a.nch) {
+        nch = 0;
+        nwk = next_live(wk + gridDim.x);
+      }
+      if (nwk < a.W) load_slice(nwk, nch);   // lands while this item's products run
+      write_b<CWP, SW>(bsm, p, j0, dr, di);
+      signal_b(bar_b, lane);
+      if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
+      ph_m ^= 1u;
+      load_d<CWP, SW, false>(trow, j0, dr, di);   // F psi
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) {   // t_0 = psi + F psi
+        accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
+        acci[jj] = row ? acci[jj] + di[jj] : 0.f;
+      }
+      write_b<CWP, SW>(bsm, p, j0, accr, acci);
+      signal_b(bar_b, lane);
+      for (int k = 1; k <= a.order; ++k) {
+        if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
+        ph_m ^= 1u;
+        load_d<CWP, SW, true>(trow, j0, dr, di);   // t_k
+        const float s = 1.f / (float)(k + 1);
 #pragma unroll
         for (int jj = 0; jj < SW; ++jj) {
-          float2 v = make_float2(0.f, 0.f);
-          if (row && j0 + jj < cwn) v = prow[j0 + jj];
-          accr[jj] = dr[jj] = v.x;
-          acci[jj] = di[jj] = v.y;
+          const float tr = row ? dr[jj] : 0.f, ti = row ? di[jj] : 0.f;
+          accr[jj] += tr;
+          acci[jj] += ti;
+          dr[jj] = tr * s;   // next operand t_k / (k + 1)
+          di[jj] = ti * s;
         }
-        write_b<CWP, SW>(bsm, p, j0, dr, di);
+        if (k < a.order) write_b<CWP, SW>(bsm, p, j0, dr, di);
+        else write_b<CWP, SW>(bsm, p, j0, accr, acci);
         signal_b(bar_b, lane);
-        if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
-        ph_m ^= 1u;
-        load_d<CWP, SW, false>(trow, j0, dr, di);   // F psi
-#pragma unroll
-        for (int jj = 0; jj < SW; ++jj) {   // t_0 = psi + F psi
-          accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
-          acci[jj] = row ? acci[jj] + di[jj] : 0.f;
-        }
-        write_b<CWP, SW>(bsm, p, j0, accr, acci);
-        signal_b(bar_b, lane);
-        for (int k = 1; k <= a.order; ++k) {
-          if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
-          ph_m ^= 1u;
-          load_d<CWP, SW, true>(trow, j0, dr, di);   // t_k
-          const float s = 1.f / (float)(k + 1);
-#pragma unroll
-          for (int jj = 0; jj < SW; ++jj) {
-            const float tr = row ? dr[jj] : 0.f, ti = row ? di[jj] : 0.f;
-            accr[jj] += tr;
-            acci[jj] += ti;
-            dr[jj] = tr * s;   // next operand t_k / (k + 1)
-            di[jj] = ti * s;
-          }
-          if (k < a.order) write_b<CWP, SW>(bsm, p, j0, dr, di);
-          else write_b<CWP, SW>(bsm, p, j0, accr, acci);
-          signal_b(bar_b, lane);
-        }
-        if (!go) break;
-        if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
-        ph_m ^= 1u;
-        load_d<CWP, SW, false>(trow, j0, dr, di);   // F acc
-#pragma unroll
-        for (int jj = 0; jj < SW; ++jj)
-          if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
       }
+      if (!go) break;
+      if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
+      ph_m ^= 1u;
+      load_d<CWP, SW, false>(trow, j0, dr, di);   // F acc
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj)
+        if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
+      wk = nwk;
+      ch = nch;
     }
     if (!go && lane == 0) {
       atomicOr(a.status, kStatusTimeout);
