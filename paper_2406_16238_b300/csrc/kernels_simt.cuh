@@ -873,11 +873,29 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     if (n == 0) continue;
     __syncthreads();
     const R2* psw = a.psi + (size_t)w * N * a.ncol + c0;
-    if (STAGE) {
-      for (int idx = tid; idx < N * n; idx += blockDim.x) {
-        const int p = idx / n, j = idx % n;
-        Y[(size_t)p * ldy + j] = psw[(size_t)p * a.ncol + j];
-        PH[idx] = a.phi_r[(size_t)p * a.ncol + c0 + j];
+    if (STAGE) {   // batches of loads in flight before the stores
+      constexpr int U = 6;
+      for (int base = tid; base < N * n; base += U * 128) {
+        R2 pv[U];
+        R fv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base + u * 128;
+          if (idx < N * n) {
+            const int p = idx / n, j = idx - (idx / n) * n;
+            pv[u] = psw[(size_t)p * a.ncol + j];
+            fv[u] = a.phi_r[(size_t)p * a.ncol + c0 + j];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = base + u * 128;
+          if (idx < N * n) {
+            const int p = idx / n, j = idx - (idx / n) * n;
+            Y[(size_t)p * ldy + j] = pv[u];
+            PH[idx] = fv[u];
+          }
+        }
       }
     }
     if (tid < n) perm[tid] = tid;
@@ -889,9 +907,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
       const int i0 = 2 * (t / nt), j0 = 2 * (t % nt);
       const bool i1ok = i0 + 1 < n, j1ok = j0 + 1 < n;
       R acc[2][2][2] = {};
-      for (int p = 0; p < N; ++p) {
-        R ph0, ph1;
-        R2 ps0, ps1;
+      auto fetch = [&](int p, R& ph0, R& ph1, R2& ps0, R2& ps1) {
         if (STAGE) {
           ph0 = PH[p * n + i0];
           ph1 = i1ok ? PH[p * n + i0 + 1] : R(0);
@@ -903,10 +919,27 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
           ps0 = psw[(size_t)p * a.ncol + j0];
           ps1 = j1ok ? psw[(size_t)p * a.ncol + j0 + 1] : ps0;
         }
+      };
+      auto mac = [&](R ph0, R ph1, R2 ps0, R2 ps1) {
         acc[0][0][0] += ph0 * ps0.x; acc[0][0][1] += ph0 * ps0.y;
         acc[0][1][0] += ph0 * ps1.x; acc[0][1][1] += ph0 * ps1.y;
         acc[1][0][0] += ph1 * ps0.x; acc[1][0][1] += ph1 * ps0.y;
         acc[1][1][0] += ph1 * ps1.x; acc[1][1][1] += ph1 * ps1.y;
+      };
+      int p = 0;
+      for (; p + 4 <= N; p += 4) {   // four rows of loads in flight, then their products in order
+        R f0[4], f1[4];
+        R2 g0[4], g1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) fetch(p + u, f0[u], f1[u], g0[u], g1[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mac(f0[u], f1[u], g0[u], g1[u]);
+      }
+      for (; p < N; ++p) {
+        R f0, f1;
+        R2 g0, g1;
+        fetch(p, f0, f1, g0, g1);
+        mac(f0, f1, g0, g1);
       }
       for (int di = 0; di < 2; ++di)
         for (int dj = 0; dj < 2; ++dj)
