@@ -388,17 +388,15 @@ size_t overlap_smem(const Dims& d) {
   return d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, st) : overlap_lu_smem<float>(d.N, nmax, st);
 }
 
-size_t qr_smem_base(const Dims& d) {
-  const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return (size_t)nmax * nmax * sizeof(double2) + ((size_t)nmax * nmax + 1) * 2 * d.rsz() + (size_t)nmax * 16 + 16;
-}
 bool qr_stage_psi(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return qr_smem_base(d) + (size_t)nmax * qr_pitch(d.N) * sizeof(double2) <= 227 * 1024;
+  return (d.prec == AFQMC_PREC_FP64 ? qr_smem_bytes<double>(d.N, nmax, true) : qr_smem_bytes<float>(d.N, nmax, true)) <=
+         227 * 1024;
 }
 size_t qr_smem(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  return qr_smem_base(d) + (qr_stage_psi(d) ? (size_t)nmax * qr_pitch(d.N) * sizeof(double2) : 0);
+  const bool st = qr_stage_psi(d);
+  return d.prec == AFQMC_PREC_FP64 ? qr_smem_bytes<double>(d.N, nmax, st) : qr_smem_bytes<float>(d.N, nmax, st);
 }
 
 size_t prop_smem(const Dims& d) { return prop_smem_floats(d.N, d.ncol, nullptr, nullptr) * sizeof(float); }

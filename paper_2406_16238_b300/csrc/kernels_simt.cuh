@@ -358,13 +358,12 @@ __global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double s
     s2 += wi * __ldcg(&eloc[3 * u + 1].x);
     s3 += wi * __ldcg(&eloc[3 * u + 2].x);
   }
-  s0 = block_sum(s0, red);
-  s1 = block_sum(s1, red);
-  s2 = block_sum(s2, red);
-  s3 = block_sum(s3, red);
+  const double s4[4] = {s0, s1, s2, s3};
+  __syncthreads();   // part[] and red[] are reused
+  block_sum_multi<4>(s4, part, red);
   if (tid == 0) {
     double* o = slot ? out + 4 * (size_t)(*slot) : out;
-    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
+    o[0] = red[0]; o[1] = red[1]; o[2] = red[2]; o[3] = red[3];
     if (slot) *slot += 1;
     *done = 0u;
   }
@@ -452,9 +451,14 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
           im[2 * a.kx] = hi;
         }
       }
-      const double l = a.lbar[g];
-      cm = cadd(cm, mk(-a.sdt * l * xs.y, a.sdt * l * xs.x));
-      xx = cadd(xx, mk(x * xb.x - 0.5 * (xb.x * xb.x - xb.y * xb.y), x * xb.y - xb.x * xb.y));
+      // c_mf += i sdt lbar_g xs;  x xbar - xbar^2 / 2 = (xbar_re (x - xbar_re / 2) + xbar_im^2 / 2,
+      // xbar_im (x - xbar_re)), written as fused multiply-adds
+      const double sl = a.sdt * a.lbar[g];
+      cm.x = fma(-sl, xs.y, cm.x);
+      cm.y = fma(sl, xs.x, cm.y);
+      xx.x = fma(xb.x, fma(-0.5, xb.x, x), xx.x);
+      xx.x = fma(0.5 * xb.y, xb.y, xx.x);
+      xx.y = fma(xb.y, xs.x, xx.y);
       a.xbar[(size_t)w * a.X + g] = xb;
     }
   }
@@ -1141,8 +1145,25 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
 // substitution on each row at the walkers' precision with R rounded once, and
 // log O -= smul sum log R_ii.  stage_psi: the block's columns are staged in
 // shared memory as binary64 rows P[j][p] with an odd row pitch.
+// The factorisation runs in one warp (warp-level syncs only): every lane forms
+// R_kk and 1 / R_kk itself, and the trailing update walks the packed upper
+// triangle in a table ordered by decreasing row, so the pairs of step k are its
+// first m (m + 1) / 2 entries (m = n - k - 1).
+// Shared memory: G [nmax^2] binary64 complex | 1 / R_kk [nmax] | pair table
+// [nmax (nmax + 1) / 2] (row, column bytes) | a region holding P during the
+// Gram product and R at the walkers' precision afterwards.
 // ============================================================================
 __host__ __device__ inline int qr_pitch(int N) { return N | 1; }
+__host__ __device__ inline size_t qr_off_rinv(int nmax) { return (size_t)nmax * nmax * 16; }
+__host__ __device__ inline size_t qr_off_tri(int nmax) { return qr_off_rinv(nmax) + ((size_t)nmax * 8 + 15) / 16 * 16; }
+__host__ __device__ inline size_t qr_off_region(int nmax) {
+  return qr_off_tri(nmax) + ((size_t)nmax * (nmax + 1) + 15) / 16 * 16;
+}
+template <typename R>
+__host__ __device__ inline size_t qr_smem_bytes(int N, int nmax, bool stage) {
+  const size_t pst = stage ? (size_t)nmax * qr_pitch(N) * 16 : 0, rl = (size_t)nmax * nmax * sizeof(cplx_t<R>);
+  return qr_off_region(nmax) + (pst > rl ? pst : rl);
+}
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int c00, int n0, int c01, int n1,
@@ -1150,85 +1171,91 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
                                                  int* status, int stage_psi) {
   using R2 = cplx_t<R>;
   extern __shared__ double2 sm_cq[];
-  __shared__ double logsum_s, rinv_s;
+  __shared__ double logsum_s;
   __shared__ int bad_s;
   const int w = blockIdx.x, tid = threadIdx.x;
   if (wgt[w] == 0.0) return;
   if (tid == 0) { logsum_s = 0.0; bad_s = 0; }
-  const int ldp = qr_pitch(N);
+  const int ldp = qr_pitch(N), nmax = max(n0, nblk > 1 ? n1 : 0);
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm_cq);
+  double2* G = sm_cq;                                                        // [n][n], becomes R (upper)
+  double* rinv = reinterpret_cast<double*>(base + qr_off_rinv(nmax));
+  uchar2* tri = reinterpret_cast<uchar2*>(base + qr_off_tri(nmax));
+  double2* P = reinterpret_cast<double2*>(base + qr_off_region(nmax));      // [n][ldp] during the Gram product
+  R2* Rl = reinterpret_cast<R2*>(base + qr_off_region(nmax));               // R at the walkers' precision, diagonal 1 / R_kk
   for (int s = 0; s < nblk; ++s) {
     const int c0 = s == 0 ? c00 : c01, n = s == 0 ? n0 : n1;
     if (n == 0) continue;
-    double2* G = sm_cq;                                 // [n][n], becomes R (upper)
-    R2* Rl = reinterpret_cast<R2*>(G + n * n);          // R at the walkers' precision, diagonal 1 / R_kk
-    double2* P = reinterpret_cast<double2*>(Rl + n * n + (n & 1) + n * (sizeof(double) / sizeof(R2) + 1));   // [n][ldp]
     R2* pw = psi + (size_t)w * N * ncol + c0;
     __syncthreads();
+    if (tid < n) {   // pair table: rows n - 1, n - 2, ..., each with its columns j >= i
+      const int m = n - 1 - tid;
+      for (int j = tid; j < n; ++j) tri[m * (m + 1) / 2 + (j - tid)] = make_uchar2((unsigned char)tid, (unsigned char)j);
+    }
     if (stage_psi) {
       for (int idx = tid; idx < n * N; idx += blockDim.x) {
         const int p = idx / n, j = idx % n;
         P[(size_t)j * ldp + p] = to_d2(pw[(size_t)p * ncol + j]);
       }
-      __syncthreads();
     }
+    __syncthreads();
     const int npk = n * (n + 1) / 2;
-    for (int e = tid; e < npk; e += blockDim.x) {   // packed upper triangle, row by row
-      int i = 0, rest = e;
-      while (rest >= n - i) { rest -= n - i; ++i; }
-      const int j = i + rest;
+    for (int e = tid; e < npk; e += blockDim.x) {   // packed upper triangle
+      const int i = tri[e].x, j = tri[e].y;
       double re = 0.0, im = 0.0;      // (psi^H psi)_ij = sum_p conj(psi_pi) psi_pj
       if (stage_psi) {
         const double2* u = P + (size_t)i * ldp;
         const double2* v = P + (size_t)j * ldp;
-        for (int p = 0; p < N; ++p) {
-          re += u[p].x * v[p].x + u[p].y * v[p].y;
-          im += u[p].x * v[p].y - u[p].y * v[p].x;
+        for (int p = 0; p < N; ++p) {   // four fused multiply-adds per term (no separate products)
+          re = fma(u[p].x, v[p].x, re);
+          re = fma(u[p].y, v[p].y, re);
+          im = fma(u[p].x, v[p].y, im);
+          im = fma(-u[p].y, v[p].x, im);
         }
       } else {
         for (int p = 0; p < N; ++p) {
           const double2 u = to_d2(pw[(size_t)p * ncol + i]);
           const double2 v = to_d2(pw[(size_t)p * ncol + j]);
-          re += u.x * v.x + u.y * v.y;
-          im += u.x * v.y - u.y * v.x;
+          re = fma(u.x, v.x, re);
+          re = fma(u.y, v.y, re);
+          im = fma(u.x, v.y, im);
+          im = fma(-u.y, v.x, im);
         }
       }
       G[i * n + j] = mk(re, im);
     }
     __syncthreads();
-    // right-looking Cholesky on the upper triangle: G_kk -> R_kk, row k -> R_kj (1 / R_kk kept in rinv)
-    double* rinv = reinterpret_cast<double*>(Rl + n * n);
-    for (int k = 0; k < n; ++k) {
-      if (tid == 0) {
+    // right-looking Cholesky on the upper triangle in warp 0: G_kk -> R_kk, row k -> R_kj
+    if (tid < 32) {
+      for (int k = 0; k < n; ++k) {
         const double d = G[k * n + k].x;
-        if (!(d > 0.0) || !isfinite(d)) bad_s = 1;
-        const double r = sqrt(fmax(d, 1e-300));
-        G[k * n + k] = mk(r, 0.0);
-        rinv_s = 1.0 / r;
-        rinv[k] = rinv_s;
+        const double r = sqrt(fmax(d, 1e-300)), ri = 1.0 / r;
+        __syncwarp();
+        if (tid == 0) {
+          if (!(d > 0.0) || !isfinite(d)) bad_s = 1;
+          G[k * n + k] = mk(r, 0.0);
+          rinv[k] = ri;
+        }
+        for (int j = k + 1 + tid; j < n; j += 32) G[k * n + j] = cscale(G[k * n + j], ri);
+        __syncwarp();
+        const int m = n - k - 1, tot = m * (m + 1) / 2;
+        for (int e = tid; e < tot; e += 32) {   // G_ij -= conj(R_ki) R_kj, k < i <= j
+          const int i = tri[e].x, j = tri[e].y;
+          const double2 rki = G[k * n + i], rkj = G[k * n + j];
+          double2 g = G[i * n + j];
+          g.x = fma(-rki.x, rkj.x, fma(-rki.y, rkj.y, g.x));
+          g.y = fma(-rki.x, rkj.y, fma(rki.y, rkj.x, g.y));
+          G[i * n + j] = g;
+        }
+        __syncwarp();
       }
-      __syncthreads();
-      const double ri = rinv_s;
-      for (int j = k + 1 + tid; j < n; j += blockDim.x) G[k * n + j] = cscale(G[k * n + j], ri);
-      __syncthreads();
-      const int rem = n - k - 1;
-      for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
-        const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-        if (j < i) continue;
-        const double2 rki = G[k * n + i], rkj = G[k * n + j];   // G_ij -= conj(R_ki) R_kj
-        double2 g = G[i * n + j];
-        g.x = fma(-rki.x, rkj.x, fma(-rki.y, rkj.y, g.x));
-        g.y = fma(-rki.x, rkj.y, fma(rki.y, rkj.x, g.y));
-        G[i * n + j] = g;
-      }
-      __syncthreads();
-    }
-    if (tid < 32) {   // sum_k log R_kk, one lane per diagonal entry
-      double ls = 0.0;
+      double ls = 0.0;   // sum_k log R_kk, one lane per diagonal entry
       for (int k = tid; k < n; k += 32) ls += log(G[k * n + k].x);
       ls = warp_sum(ls);
       if (tid == 0) logsum_s += ls;
     }
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each entry of R to R
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each entry of R to R (P is dead)
       const int i = idx / n, j = idx % n;
       Rl[idx] = from_d2<R>(i == j ? mk(rinv[i], 0.0) : (j > i ? G[idx] : mk(0.0, 0.0)));
     }
@@ -1250,8 +1277,8 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
         row[j] = o;
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (tid == 0) {
     if (bad_s) atomicOr(status, kStatusSingular);
     logO[w].x -= smul * logsum_s;
