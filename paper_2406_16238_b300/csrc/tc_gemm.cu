@@ -908,18 +908,23 @@ int exchange_groups(int n, int wpt0) {
 // Walker tiling of one block: epilogue groups, walkers per tile, MMA N and form.  The resident-A
 // form (k_exch_tm, BF16x3 only) needs the register-row epilogue (n <= 32), 2 bn + kst <= 512 tensor-memory
 // columns and two ring stages beside the epilogue buffers; it takes the largest group count (at
-// most `groups` when that is > 0) for which some multiple of it walkers fits, and the most walkers.
+// most `groups` when that is > 0) for which some multiple of it walkers fits, and the most walkers,
+// provided the tile holds at least 3/4 of the streamed form's walkers (for large N the tensor-memory
+// budget leaves too few columns and the narrow products run below the tensor pipe's rate).
 // Otherwise (or with form 1) the streamed form with the largest group count that fits.
 namespace {
 void exchange_config(TcState* st, BlockMaps& bm, int groups, int form) {
   const int n = bm.n, wpt0 = 256 / (2 * n);
+  int gs = exchange_groups(n, wpt0);
+  if (groups > 0) gs = std::max(1, std::min(gs, groups));
+  const int wpt_streamed = wpt0 / gs * gs;
   if (form != 1 && st->nseg == 3 && (n + 7) / 8 * 8 <= 32) {
     for (int g = std::min(4, wpt0); g >= 1; --g) {
       if (groups > 0 && g > groups) continue;
       int wpt = 0;
       for (int w = g; w <= wpt0; w += g)
         if (2 * ((w * 2 * n + 15) / 16 * 16) + st->kst <= 512) wpt = w;
-      if (wpt == 0) continue;
+      if (wpt == 0 || 4 * wpt < 3 * wpt_streamed) continue;
       const int bn = (wpt * 2 * n + 15) / 16 * 16;
       const int need = 1024 + g * ((epi_bytes_exchange(n, true) + 15) & ~15) + kTailBytes + 2 * tm_stage_bytes(bn);
       if (need > kMaxSmem) continue;
@@ -931,10 +936,8 @@ void exchange_config(TcState* st, BlockMaps& bm, int groups, int form) {
       return;
     }
   }
-  int g = exchange_groups(n, wpt0);
-  if (groups > 0) g = std::max(1, std::min(g, groups));
-  bm.groups = g;
-  bm.wpt = wpt0 / g * g;
+  bm.groups = gs;
+  bm.wpt = wpt_streamed;
   bm.bn = (bm.wpt * 2 * n + 15) / 16 * 16;
   bm.form = 0;
   bm.n_tiles = (st->W + bm.wpt - 1) / bm.wpt;
