@@ -240,6 +240,12 @@ struct afqmc_ctx {
   // CUDA graphs of the driver loop's step patterns (captured lazily on a private stream)
   bool graphs_on = true;
   cudaStream_t cap_stream = nullptr;
+  // the energy estimator kernel runs on `side` beside the following step's fields, VHS and
+  // propagation (it reads Theta, vbias, the exchange partials and the weights, which only the
+  // step's overlap rewrites); the overlap joins it first
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool join_pending = false;
   // the tensor-core exchange draws the current step's normals into L.x with a spare warp (its
   // binary64 work overlaps the contraction); the next fields kernel uses them instead of drawing
   bool normals_pending = false;
@@ -263,6 +269,9 @@ struct afqmc_ctx {
   ~afqmc_ctx() {
     drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : free_events) cudaEventDestroy(e);
   }
@@ -405,8 +414,18 @@ bool use_fused_propagation(const Dims& d) { return d.prec != AFQMC_PREC_FP64 && 
 
 bool use_tc_propagation(const afqmc_ctx* c) { return c->d.tensor() && c->tcs.pg.ok && c->prop_path == 0; }
 
+// The stream waits for an energy estimator launched beside it (no-op when none is pending).
+afqmc_status join_energy(afqmc_ctx* c) {
+  if (!c->join_pending) return AFQMC_OK;
+  c->join_pending = false;
+  CU(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  return AFQMC_OK;
+}
+
 template <typename R>
 afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
+  afqmc_status js = join_energy(c);   // the overlap rewrites Theta and the weights the estimator reads
+  if (js != AFQMC_OK) return js;
   StageTimer timer(c, AFQMC_STAGE_OVERLAP);
   const size_t sm = overlap_smem(c->d);
   if (overlap_stage(c->d)) k_overlap_lu<R, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
@@ -477,8 +496,10 @@ afqmc_status set_smem_limits(const Dims& d) {
 template <typename R>
 afqmc_status energy_cv_impl(afqmc_ctx* c, double* sums_dev, int* slot);
 
+// beside: a step follows at once, so the estimator kernel may run on the side stream until that
+// step's overlap (not while stage timing is on, which times it on the main stream).
 template <typename R>
-afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
+afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bool beside = false) {
   if (c->cv.enabled) return energy_cv_impl<R>(c, sums_dev, slot);
   afqmc_status st;
   if (!c->theta_fresh) {
@@ -497,13 +518,24 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr) {
     if ((st = launch_exchange<R>(c, 1)) != AFQMC_OK) return st;
   }
   delete tx;
+  const bool fork = beside && !c->prof && c->side != nullptr;
+  cudaStream_t es = c->stream;
+  if (fork) {
+    CU(cudaEventRecord(c->ev_fork, c->stream));
+    CU(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    es = c->side;
+  }
   StageTimer te(c, AFQMC_STAGE_ENERGY);
-  k_energy<R><<<c->d.W, 256, 0, c->stream>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
+  k_energy<R><<<c->d.W, 256, 0, es>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
                                               c->at<cplx_t<R>>(c->L.thetaT), c->at<R>(c->L.hrot_r),
                                               c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
                                               c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w), sums_dev, slot,
                                               reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64));
   CHECK_LAUNCH(c);
+  if (fork) {
+    CU(cudaEventRecord(c->ev_join, c->side));
+    c->join_pending = true;
+  }
   c->vbias_fresh = true;
   return AFQMC_OK;
 }
@@ -882,6 +914,7 @@ afqmc_status capture_graph(afqmc_ctx* c, F body, cudaGraph_t* out, unsigned long
   *nkernels = c->launches - l0;
   c->theta_fresh = tf; c->vbias_fresh = vf; c->host_step = hs; c->launches = l0; c->normals_pending = false;
   c->thb_valid = tb;
+  c->join_pending = false;   // every captured body ends after the overlap that joins the estimator
   if (st != AFQMC_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
   *out = graph;
@@ -907,7 +940,8 @@ afqmc_status graph_step(afqmc_ctx* c, bool energy) {
   if (!c->g_step[v]) {
     afqmc_status st = capture(c, [&]() -> afqmc_status {
       afqmc_status s2;
-      if (energy && (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot))) != AFQMC_OK)
+      if (energy &&
+          (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true)) != AFQMC_OK)
         return s2;
       return DISPATCH(c, step_impl);
     }, &c->g_step[v], &c->g_step_k[v]);
@@ -1006,6 +1040,11 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
   c->L = L;
   c->base = static_cast<char*>(workspace);
   c->stream = static_cast<cudaStream_t>(params->stream);
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    c->side = nullptr;   // the estimator then stays on the main stream
+  }
   c->dt = params->dt;
   c->sdt = std::sqrt(params->dt);
   c->cap = params->fb_cap;
@@ -1115,7 +1154,7 @@ afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int
     if (graphs) {
       if ((st = graph_step(ctx, energy)) != AFQMC_OK) return st;
     } else {
-      if (energy && (st = DISPATCH(ctx, energy_impl, hist + 4 * used)) != AFQMC_OK) return st;
+      if (energy && (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true)) != AFQMC_OK) return st;
       if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
     }
     if (energy) { ++used; ++total; }
@@ -1588,7 +1627,8 @@ afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb
     bool end_tf = false, end_vf = false, end_tb = false;
     afqmc_status st = capture_graph(c, [&]() -> afqmc_status {
       afqmc_status s2;
-      if (energy && (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot))) != AFQMC_OK)
+      if (energy &&
+          (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true)) != AFQMC_OK)
         return s2;
       if ((s2 = DISPATCH(c, step_impl)) != AFQMC_OK) return s2;
       if (qr && (s2 = DISPATCH(c, qr_impl)) != AFQMC_OK) return s2;
