@@ -173,11 +173,11 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
         }
         *dst = val;
       }
-      if (lane == 0) {
+      if (lane < 4) {   // the tile's four partial slots: the sum in the first, zeros in the others
         const float sr = (e.red[0].x + e.red[1].x) + (e.red[2].x + e.red[3].x);
         const float si = (e.red[0].y + e.red[1].y) + (e.red[2].y + e.red[3].y);
-        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] =
-            make_double2((double)(p.smul * sr), (double)(p.smul * si));
+        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + 4 * mt + lane] =
+            lane == 0 ? make_double2((double)(p.smul * sr), (double)(p.smul * si)) : make_double2(0.0, 0.0);
       }
     }
     if (v + p.g.epi_groups < p.wpt) named_bar(bar_id, 128);   // buffers reused by the next walker
@@ -210,9 +210,12 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
 // As exchange_tile, with the thread's own row T_ab (b < n <= NB) kept in registers: the real
 // parts come from columns [v 2n, v 2n + NB), the imaginary parts from [v 2n + n, v 2n + n + NB)
 // (the columns past the walker are read and ignored).  The row goes to shared memory as complex
-// entries, and each partner entry T_ba is read back with one 8-byte load.  After the second
-// barrier the four warps share the per-gamma traces (force bias): warp k sums the diagonals of
-// gammas 2k and 2k + 1 (then 2k + 8, 2k + 9, ...), one half-warp per gamma.
+// entries, and each partner entry T_ba is read back with one 8-byte load.  After that each warp
+// works alone: its exchange partial goes to slot 4 mt + (warp in group) of the walker's partials,
+// and the per-gamma traces (force bias) are summed by a segmented scan over the warp's rows (the
+// diagonal T_aa read back from the thread's staged row) and added to vbias, which the caller has
+// zeroed: a gamma block (n <= 32 rows) meets at most two warps, and two additions onto zero give
+// the same bits in either order, so the result does not depend on timing.
 template <int NB>
 __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc, const EpiSmem& e, int group,
                                   int wig, int r, int lane) {
@@ -228,6 +231,7 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
     tmem_ld_cols<NB>(tacc + (uint32_t)(v * n2), ur);
     tmem_ld_cols<NB>(tacc + (uint32_t)(v * n2 + n), ui);
     tmem_wait();
+    if (v > group) named_bar(bar_id, 128);   // every partner read of the previous walker is done
 #pragma unroll
     for (int b = 0; b < NB; ++b)
       if (b < n) rowp[b] = make_float2(__uint_as_float(ur[b]), __uint_as_float(ui[b]));
@@ -254,52 +258,30 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
           ei1 = fmaf(ti, q.x, ei1);
         }
       }
-      dg = rowp[a];
+      dg = rowp[a];   // T_aa
     }
-    e.diag[r] = dg;
     float er = er0 + er1, ei = ei0 + ei1;
     er = warp_sum_f(er);
     ei = warp_sum_f(ei);
-    if (lane == 0) e.red[wig] = make_float2(er, ei);
-    named_bar(bar_id, 128);
     const int w = nt * p.wpt + v;
-    if (w < p.W) {
-      for (int g0 = 2 * wig; p.vbias && g0 < p.gpt; g0 += 8) {   // half-warp h: gamma g0 + h, 16 lanes
-        const int gg = g0 + (lane >> 4), k = lane & 15;
-        float2 d = make_float2(0.f, 0.f);
-        if (gg < p.gpt) {
-          if (k < n) d = e.diag[gg * n + k];
-          if (k + 16 < n) {
-            const float2 d2 = e.diag[gg * n + k + 16];
-            d.x += d2.x;
-            d.y += d2.y;
-          }
-        }
+    if (lane == 0 && w < p.W)
+      p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + 4 * mt + wig] =
+          make_double2((double)(p.smul * er), (double)(p.smul * ei));
+    if (p.vbias) {   // inclusive segmented scan of the diagonal over this warp's rows of gamma block g
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
-          d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
-        }
-        const int gam = mt * p.gpt + gg;
-        if (k == 0 && gg < p.gpt && gam < p.X) {
-          float2* dst = p.vbias + (size_t)w * p.X + gam;
-          float2 val = make_float2(p.smul * d.x, p.smul * d.y);
-          if (p.vbias_add) {
-            val.x += dst->x;
-            val.y += dst->y;
-          }
-          *dst = val;
+      for (int o = 1; o < 32; o <<= 1) {
+        const float tx = __shfl_up_sync(0xffffffffu, dg.x, o), ty = __shfl_up_sync(0xffffffffu, dg.y, o);
+        if (lane >= o && r - o >= g * n) {
+          dg.x += tx;
+          dg.y += ty;
         }
       }
-      if (wig == 0 && lane == 0) {
-        const float sr = (e.red[0].x + e.red[1].x) + (e.red[2].x + e.red[3].x);
-        const float si = (e.red[0].y + e.red[1].y) + (e.red[2].y + e.red[3].y);
-        p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + mt] =
-            make_double2((double)(p.smul * sr), (double)(p.smul * si));
+      if (live && w < p.W && (lane == 31 || a == n - 1)) {   // last row of the block within this warp
+        float* dst = reinterpret_cast<float*>(p.vbias + (size_t)w * p.X + mt * p.gpt + g);
+        atomicAdd(dst, p.smul * dg.x);
+        atomicAdd(dst + 1, p.smul * dg.y);
       }
     }
-    // No barrier before the next walker: every partner read of buf happened before the barrier
-    // above, and e.diag / e.red are read before each warp reaches the next walker's first barrier.
   }
 }
 
@@ -965,7 +947,7 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     cur = align256(cur + (size_t)X * b.n * st->nseg * st->kst * 2);
     b.off_th = cur;
     cur = align256(cur + (size_t)W * 2 * b.n * st->nseg * st->kst * 2);
-    st->nchunk += b.m_tiles;
+    st->nchunk += 4 * b.m_tiles;   // four exchange partial slots per M tile (one per epilogue warp)
   }
   st->off_lt = cur;
   cur = align256(cur + (size_t)N * N * st->nseg * st->kx * 2);
@@ -1079,6 +1061,11 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
   int chunk = 0;
   bool first = true;
   if (nw <= 0) return AFQMC_OK;
+  // the register-row epilogue adds its per-gamma traces onto vbias
+  if (vbias && cudaMemsetAsync(vbias, 0, (size_t)nw * st->X * sizeof(float2), s) != cudaSuccess) {
+    snprintf(err, errlen, "tcgen05 exchange: clearing vbias failed");
+    return AFQMC_ECUDA;
+  }
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
     if (bm.n == 0) continue;
@@ -1135,7 +1122,7 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     else if (nb == 24) r = launch<0, 24>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
     else r = launch<0, 32>(g, bm.map_l, bm.map_th, p, s, launches, err, errlen);
     if (r != AFQMC_OK) return r;
-    chunk += bm.m_tiles;
+    chunk += 4 * bm.m_tiles;
     first = false;
   }
   return AFQMC_OK;

@@ -50,7 +50,7 @@ struct TcState {
   int prec = 0, W = 0, N = 0, X = 0, ncol = 0, nblk = 0;
   int kst = 0;        // padded length of one K segment of the exchange operands (multiple of 16)
   int nseg = 1;       // 1 (BF16) or 3 (BF16x3)
-  int nchunk = 0;     // exchange partials per walker (sum of m_tiles over blocks)
+  int nchunk = 0;     // exchange partial slots per walker (four per M tile, summed over blocks)
   BlockMaps blk[2];
   // VHS build
   int kx = 0;         // padded naux (multiple of 64)
@@ -88,8 +88,9 @@ struct NormalsJob {
   int W, X;
 };
 
-// vbias[w][g] = smul sum_s Tr T^{g s}, exch_part[w][chunk] = smul sum over the chunk's gammas of
-// sum_ab T_ab T_ba, with T^{g s} = Ltilde^{g s} Theta^s; Theta^T complex64 [W][ncol][N].
+// vbias[w][g] = smul sum_s Tr T^{g s} (vbias is cleared first), exch_part[w][slot]: the slots of each
+// M tile hold partial sums (one per epilogue warp, or the tile's sum and zeros) of smul sum over the
+// tile's gammas of sum_ab T_ab T_ba, with T^{g s} = Ltilde^{g s} Theta^s; Theta^T complex64 [W][ncol][N].
 // widx (optional, nw entries): the kernel works on walkers widx[0..nw) and writes their partials
 // to rows 0..nw of exch_part; vbias may be NULL (not written).
 // nj (optional): the first launch also draws those normals.  theta_ready: the bf16 operand copy of
