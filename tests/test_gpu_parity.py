@@ -350,3 +350,43 @@ def test_theta_kept_across_qr_matches_recomputation(prec, tol):
     scale = np.max(np.abs(e_fresh[:, 0]))
     assert np.max(np.abs(e_cached[:, 0] - e_fresh[:, 0])) < tol * scale
     ctx.close()
+
+
+EXCH_CASES = {
+    "rhf_N8": lambda: config_small(),                                                         # n = 2
+    "uhf_N37_20_17": lambda: make_problem(37, 20, 17, 60, 8.0, 43, unrestricted=True),       # two blocks
+    "rhf_N108_21": lambda: config_medium(),                                                   # the benchmark shape
+    "rhf_N64_32": lambda: make_problem(64, 32, 32, 96, 12.0, 49),                             # n = 32
+}
+
+
+@pytest.mark.parametrize("name", list(EXCH_CASES))
+def test_exchange_forms_and_group_counts_agree_with_oracle(name):
+    """The tensor-core exchange with the rotated Cholesky tile resident in tensor memory (form 0, where it
+    fits) and with both operands streamed (form 1), at every epilogue group count, on the same walkers:
+    per-walker E_L (whose J and K come from the exchange kernel's traces and partials) against the oracle
+    and between the settings."""
+    prob = EXCH_CASES[name]()
+    st = _setup(prob)
+    nw = 37
+    psi, w = _random_state(prob, nw, seed=12, spread=0.2)
+    ref = []
+    for i in range(nw):
+        _, th_a, th_b = orc.overlap_theta(st, psi[i])
+        ref.append(orc.local_energy(st, th_a, th_b)[0])
+    ref = np.array(ref)
+    ctx = _ctx(prob, nw, prec="bf16x3")
+    ctx.set_walkers(psi, w, 0)
+    seen = []
+    for form in (0, 1):
+        for groups in (1, 2, 3, 4):
+            ctx.set_tuning(exch_form=form, exch_groups=groups)
+            _, eloc = ctx.local_energy(per_walker=True)
+            scale = 1.0 + np.abs(ref)
+            assert np.all(np.abs(eloc[:, 0] - ref) < TC_REL_TOL["bf16x3"] * scale), (form, groups)
+            seen.append(eloc[:, 0].copy())
+    ctx.close()
+    # the settings sum the split products in different fp32 orders: agreement to 1e-5 relative, a tenth
+    # of the tolerance against the oracle
+    spread = np.max(np.abs(np.array(seen) - seen[0]), axis=0)
+    assert np.all(spread < 1e-5 * (1.0 + np.abs(ref))), np.max(spread / (1.0 + np.abs(ref)))
