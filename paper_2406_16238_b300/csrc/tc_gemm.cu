@@ -313,15 +313,11 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
   const int pq = mt * kBM + r;
   const bool live = pq < p.out_cols;
   const int pp = live ? pq / p.n : 0, qq = live ? pq - pp * p.n : 0;
-  const int ncols = p.g.bn / p.g.epi_groups;
+  const int ncols = p.g.bn / p.g.epi_groups;   // a multiple of 8
   const int cbeg = group * ncols;
   const size_t plane = (size_t)p.npad * p.kq;
-  float v[16];
-  for (int c = cbeg; c < cbeg + ncols; c += 16) {
-    tmem_ld16(tacc + (uint32_t)c, v);
-    if (!live) continue;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
+  auto put = [&](int c, int cnt, const float* v) {
+    for (int i = 0; i < cnt; ++i) {
       const int col = nt * p.g.n_step + c + i;
       if (col >= p.out_rows) break;
       __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * p.kq + qq;
@@ -329,6 +325,20 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
       dst[0] = hi;
       dst[2 * plane] = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
     }
+  };
+  float v[16];
+  int c = cbeg;
+  for (; c + 16 <= cbeg + ncols; c += 16) {
+    tmem_ld16(tacc + (uint32_t)c, v);
+    if (live) put(c, 16, v);
+  }
+  if (c < cbeg + ncols) {   // 8 columns left
+    uint32_t r8[8];
+    tmem_ld8_nowait(tacc + (uint32_t)c, r8);
+    tmem_wait();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r8[i]);
+    if (live) put(c, 8, v);
   }
 }
 
@@ -956,6 +966,20 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   st->vhs_m_tiles = (2 * W + kBM - 1) / kBM;
   st->vhs_n_tiles = (N * N + 255) / 256;
   st->pg = prop_geom(N, ncol);
+  // VHS planes GEMM width: M tiles x N tiles spread over the SMs, cost per tile ~ one k-step's
+  // shared-memory traffic (A: 4 KiB written and read, B: bn x 32 bytes written and read at 128 B
+  // per cycle, 64 + bn / 2 cycles); the width with the smallest busiest-SM cost (the last wave
+  // of a 256-wide tiling can be nearly empty)
+  {
+    const long long mt = ((long long)N * N + kBM - 1) / kBM;
+    const int sms = num_sms();
+    long long best = -1;
+    for (int bn : {256, 224, 192, 160, 128}) {
+      const long long tiles = mt * ((2LL * W + bn - 1) / bn);
+      const long long cost = ((tiles + sms - 1) / sms) * (64 + bn / 2);
+      if (best < 0 || cost < best) { best = cost; st->vhs_bn = bn; }
+    }
+  }
   if (st->pg.ok) {
     const PropGeom& pg = st->pg;
     st->off_vp = cur;
@@ -1027,7 +1051,7 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
   if (st->pg.ok &&
       (!make_map(&st->map_lt_a, lt, (unsigned long long)st->N * st->N, (unsigned long long)st->nseg * st->kx, kBM) ||
        !make_map(&st->map_coef_b, tcbuf + st->off_coef, (unsigned long long)st->W * 2,
-                 (unsigned long long)st->nseg * st->kx, 256))) {
+                 (unsigned long long)st->nseg * st->kx, (unsigned)st->vhs_bn))) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS plane operands");
     return AFQMC_ECUDA;
   }
@@ -1141,12 +1165,12 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   }
   Geom g{};
   g.m_tiles = (st->N * st->N + kBM - 1) / kBM;
-  g.n_tiles = (2 * st->W + 255) / 256;
+  g.n_tiles = (2 * st->W + st->vhs_bn - 1) / st->vhs_bn;
   g.k_blocks = st->nseg * st->kx / kBK;
   g.k_steps = st->nseg * st->kx / 16;
   g.m_step = kBM;
-  g.n_step = 256;
-  g.bn = 256;
+  g.n_step = st->vhs_bn;
+  g.bn = st->vhs_bn;
   if (!finish_geom(&g, 16, 4)) {
     snprintf(err, errlen, "tcgen05 VHS: shared memory plan failed");
     return AFQMC_EINVAL;

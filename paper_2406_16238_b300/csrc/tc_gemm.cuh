@@ -56,6 +56,7 @@ struct TcState {
   int kx = 0;         // padded naux (multiple of 64)
   size_t off_lt = 0, off_coef = 0;
   int vhs_m_tiles = 0, vhs_n_tiles = 0;
+  int vhs_bn = 256;   // N tile of the VHS planes GEMM (multiple of 32)
   CUtensorMap map_lt, map_coef;
   // tensor-core propagation
   PropGeom pg;
