@@ -828,12 +828,12 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
 // ============================================================================
 // STAGE: psi rows, Phi and the substitution vectors live in shared memory (Y); otherwise the
 // vectors live in Theta^T itself (row perm[k] holds y_k throughout, so no final permutation).
-// Shared memory: A [n][lda] binary64 | pivots, 1 / pivots [n] binary64 | perm, two row lists [3n] | F [n][n] R |
+// Shared memory: A [n][lda] binary64 | pivots, 1 / pivots [n] binary64 | perm [n] | F [n][n] R |
 // (STAGE) Y [N][ldy] R complex | Phi [N][n] R.
 template <typename R>
 __host__ __device__ inline size_t overlap_lu_smem(int N, int nmax, bool stage) {
   const int lda = nmax + 1, ldy = nmax | 1;
-  const size_t fixed = (size_t)nmax * lda * 16 + (size_t)nmax * 32 + ((size_t)nmax * 12 + 15) / 16 * 16 +
+  const size_t fixed = (size_t)nmax * lda * 16 + (size_t)nmax * 32 + ((size_t)nmax * 4 + 15) / 16 * 16 +
                        (size_t)nmax * nmax * 2 * sizeof(R);
   return fixed + (stage ? (size_t)N * ldy * 2 * sizeof(R) + (size_t)N * nmax * sizeof(R) : 0) + 16;
 }
@@ -856,8 +856,8 @@ template <typename R, bool STAGE>
 __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
   using R2 = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char sm_lu[];
-  __shared__ int sing_s, swaps_s, exp_s;
-  __shared__ double2 prod_s;
+  __shared__ int piv_s, sing_s, swaps_s, exp_s;
+  __shared__ double2 inv_s, prod_s;
   const int w = blockIdx.x, tid = threadIdx.x, N = a.N;
   if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
   if (a.mode == 1 && a.w[w] == 0.0) return;
@@ -866,9 +866,8 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
   double2* A = reinterpret_cast<double2*>(sm_lu);           // [n][lda] binary64, becomes L\U
   double2* pivv = A + (size_t)nmax * lda;                   // pivots U_kk
   double2* dinv = pivv + nmax;                              // 1 / U_kk
-  int* perm = reinterpret_cast<int*>(dinv + nmax);             // pivot row of each step (rows stay in place)
-  int* rlist = perm + nmax;                                   // two lists of the rows still to be pivoted
-  R2* F = reinterpret_cast<R2*>(reinterpret_cast<unsigned char*>(perm) + ((size_t)nmax * 12 + 15) / 16 * 16);
+  int* perm = reinterpret_cast<int*>(dinv + nmax);
+  R2* F = reinterpret_cast<R2*>(reinterpret_cast<unsigned char*>(perm) + ((size_t)nmax * 4 + 15) / 16 * 16);
   R2* Y = F + (size_t)nmax * nmax;                          // [N][ldy]: psi rows, then Theta rows
   R* PH = reinterpret_cast<R*>(Y + (size_t)N * ldy);        // [N][n] Phi block
   double ld_re = 0.0, ld_im = 0.0;
@@ -903,7 +902,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
         }
       }
     }
-    if (tid < n) rlist[tid] = tid;   // the rows in their initial order
+    if (tid < n) perm[tid] = tid;
     if (tid == 0) { sing_s = 0; swaps_s = 0; }
     __syncthreads();
     // A = Phi^T psi: 2 x 2 register tiles
@@ -952,85 +951,66 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
             A[(i0 + di) * lda + j0 + dj] = mk((double)acc[di][dj][0], (double)acc[di][dj][1]);
     }
     __syncthreads();
-    // LU with partial pivoting, rows kept in place.  The rows still to be pivoted are kept as a list
-    // in the order the row-swapping formulation would hold them (positions k .. n-1), so pivots,
-    // ties (lowest position), multipliers and the permutation's parity are those of that
-    // formulation; perm[k] is the row chosen at step k.  pivot_step (one warp): the largest
-    // |re| + |im| of column k over the list `cur` (m rows), its reciprocal, the list without it
-    // (`nxt`) and the multipliers of column k for those rows.  Look-ahead: while the other three warps
-    // apply step k to columns k+2 .., the pivot warp applies it to column k+1 and takes step k+1's pivot.
-    // the pivot warp varies with the walker, so the pivot chains of the CTAs sharing an SM tend to
-    // sit on different sub-partitions (each has its own binary64 pipe)
-    const int pw = (int)(((blockIdx.x >> 2) ^ blockIdx.x) & 3u), lane = tid & 31, wid = tid >> 5;
-    const int ut = wid < pw ? tid : tid - 32;   // index among the three update warps
-    auto pivot_step = [&](int k, const int* cur, int m, int* nxt) {
-      long long best = -1;
-      int bq = 0;
-      for (int q = lane; q < m; q += 32) {
-        const double2 v = A[cur[q] * lda + k];
-        const long long mg = __double_as_longlong(fabs(v.x) + fabs(v.y));   // non-negative: order as integers
-        if (mg > best) { best = mg; bq = q; }
-      }
+    for (int k = 0; k < n; ++k) {
+      if (tid < 32) {   // pivot: largest |re| + |im| in column k, lowest row on ties
+        // non-negative doubles order like their bit patterns: compare as integers
+        long long best = -1;
+        int bi = k;
+        for (int i = k + tid; i < n; i += 32) {
+          const double2 v = A[i * lda + k];
+          const long long m = __double_as_longlong(fabs(v.x) + fabs(v.y));
+          if (m > best) { best = m; bi = i; }
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-        if (ob > best || (ob == best && oq < bq)) { best = ob; bq = oq; }
-      }
-      // zero, NaN or infinity: the sum's bit pattern is 0 or has every exponent bit set
-      if (best <= 0 || best >= 0x7ff0000000000000LL) {
-        if (lane == 0) sing_s = 1;
-        return;
-      }
-      const int pv = cur[bq];
-      double2 inv = mk(0.0, 0.0);
-      if (lane == 0) {
-        const double2 pk = A[pv * lda + k];
-        const double r = 1.0 / fma(pk.x, pk.x, pk.y * pk.y);   // 1 / pk = conj(pk) / |pk|^2
-        inv = mk(pk.x * r, -pk.y * r);
-        dinv[k] = inv;
-        pivv[k] = pk;
-        perm[k] = pv;
-        if (bq != 0) swaps_s ^= 1;
-      }
-      inv.x = __shfl_sync(0xffffffffu, inv.x, 0);
-      inv.y = __shfl_sync(0xffffffffu, inv.y, 0);
-      for (int j = lane; j + 1 < m; j += 32) nxt[j] = (j == bq - 1) ? cur[0] : cur[j + 1];
-      __syncwarp();
-      for (int j = lane; j + 1 < m; j += 32) {
-        const int r = nxt[j];
-        const double2 v = A[r * lda + k];
-        A[r * lda + k] = mk(fma(v.x, inv.x, -v.y * inv.y), fma(v.x, inv.y, v.y * inv.x));
-      }
-      __syncwarp();
-    };
-    if (wid == pw) pivot_step(0, rlist, n, rlist + nmax);
-    __syncthreads();
-    for (int k = 0; k + 1 < n && !sing_s; ++k) {
-      int* cur = rlist + ((k & 1) ? 0 : nmax);   // rows still to be pivoted after step k
-      int* nxt = rlist + ((k & 1) ? nmax : 0);
-      const int m = n - k - 1, p = perm[k];
-      if (wid == pw) {
-        for (int j = lane; j < m; j += 32) {   // step k on column k+1
-          const int r = cur[j];
-          const double2 l = A[r * lda + k], u = A[p * lda + k + 1];
-          double2 v = A[r * lda + k + 1];
-          v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
-          v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
-          A[r * lda + k + 1] = v;
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        __syncwarp();
-        pivot_step(k + 1, cur, m, nxt);
-      } else {   // step k on columns k+2 .. n-1
-        const int cols = n - k - 2;
-        for (int idx = ut; idx < m * cols; idx += blockDim.x - 32) {
-          const int r = cur[idx / cols], j = k + 2 + idx % cols;
-          const double2 l = A[r * lda + k], u = A[p * lda + j];
-          double2 v = A[r * lda + j];
-          v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
-          v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
-          A[r * lda + j] = v;
+        if (tid == 0) {
+          piv_s = bi;
+          // zero, NaN or infinity: the sum's bit pattern is 0 or has every exponent bit set
+          if (best <= 0 || best >= 0x7ff0000000000000LL) sing_s = 1;
+          if (!sing_s) {
+            const double2 pk = A[bi * lda + k];
+            const double r = 1.0 / fma(pk.x, pk.x, pk.y * pk.y);   // 1 / pk = conj(pk) / |pk|^2
+            const double2 inv = mk(pk.x * r, -pk.y * r);
+            inv_s = inv;
+            dinv[k] = inv;
+            pivv[k] = pk;
+            if (bi != k) {
+              swaps_s ^= 1;
+              const int t = perm[k];
+              perm[k] = perm[bi];
+              perm[bi] = t;
+            }
+          }
         }
+      }
+      __syncthreads();
+      if (sing_s) break;
+      const int pv = piv_s;
+      if (pv != k)
+        for (int j = tid; j < n; j += blockDim.x) {
+          const double2 t = A[k * lda + j];
+          A[k * lda + j] = A[pv * lda + j];
+          A[pv * lda + j] = t;
+        }
+      __syncthreads();
+      const double2 inv = inv_s;
+      for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+        const double2 v = A[i * lda + k];
+        A[i * lda + k] = mk(fma(v.x, inv.x, -v.y * inv.y), fma(v.x, inv.y, v.y * inv.x));
+      }
+      __syncthreads();
+      const int rem = n - k - 1;
+      for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+        const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+        const double2 l = A[i * lda + k], u = A[k * lda + j];
+        double2 v = A[i * lda + j];
+        v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
+        v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
+        A[i * lda + j] = v;
       }
       __syncthreads();
     }
@@ -1059,7 +1039,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     }
     for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each factor entry to R
       const int i = idx / n, j = idx % n;
-      F[idx] = from_d2<R>(i == j ? dinv[i] : A[perm[i] * lda + j]);
+      F[idx] = from_d2<R>(i == j ? dinv[i] : A[i * lda + j]);
     }
     __syncthreads();
     R2* thw = a.thetaT + ((size_t)w * a.ncol + c0) * N;
