@@ -130,6 +130,13 @@ afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps);
  * Synchronises the stream when either output is non-NULL. */
 afqmc_status afqmc_local_energy(afqmc_ctx* ctx, double* sums, double* eloc);
 
+/* As afqmc_local_energy for the four sums only, without synchronising: the copy of sums[4] to
+ * `sums_host` is enqueued on the context's stream after the energy kernels (use page-locked host
+ * memory for an asynchronous copy).  The values are there once the stream has reached that point
+ * (afqmc_synchronize or any stream synchronisation); device-side conditions are reported by the
+ * next synchronising call. */
+afqmc_status afqmc_local_energy_async(afqmc_ctx* ctx, double* sums_host);
+
 /* QR stabilisation of every walker: psi^s = Q R with diag(R) > 0, psi^s <- Q,
  * log O -= sum log R_ii (all binary64). */
 afqmc_status afqmc_reortho(afqmc_ctx* ctx);

@@ -63,6 +63,7 @@ SIGNATURES = {
                             ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "afqmc_propagate": (_i32, [_vp, _i32]),
     "afqmc_local_energy": (_i32, [_vp, _dp, _dp]),
+    "afqmc_local_energy_async": (_i32, [_vp, _dp]),
     "afqmc_reortho": (_i32, [_vp]),
     "afqmc_popcontrol": (_i32, [_vp]),
     "afqmc_run": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
@@ -179,6 +180,13 @@ class Afqmc:
         if per_walker:
             return sums, eloc[..., 0] + 1j * eloc[..., 1]
         return sums
+
+    def local_energy_async(self, out):
+        """Enqueue the four estimator sums' copy into `out` (a contiguous float64 host array of at least
+        4 entries, page-locked for an asynchronous copy); valid after synchronize()."""
+        if out.dtype != np.float64 or out.size < 4 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous float64 array with at least 4 entries")
+        _check(self._lib.afqmc_local_energy_async(self._ctx, _ptr(out)))
 
     def reortho(self):
         _check(self._lib.afqmc_reortho(self._ctx))

@@ -499,8 +499,14 @@ afqmc_status energy_cv_impl(afqmc_ctx* c, double* sums_dev, int* slot);
 // beside: a step follows at once, so the estimator kernel may run on the side stream until that
 // step's overlap (not while stage timing is on, which times it on the main stream).
 template <typename R>
-afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bool beside = false) {
-  if (c->cv.enabled) return energy_cv_impl<R>(c, sums_dev, slot);
+afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bool beside = false,
+                         double* sums_host = nullptr) {
+  if (c->cv.enabled) {
+    afqmc_status sc = energy_cv_impl<R>(c, sums_dev, slot);
+    if (sc == AFQMC_OK && sums_host)
+      CU(cudaMemcpyAsync(sums_host, sums_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sc;
+  }
   afqmc_status st;
   if (!c->theta_fresh) {
     if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
@@ -532,6 +538,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
                                               c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w), sums_dev, slot,
                                               reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64));
   CHECK_LAUNCH(c);
+  if (sums_host) CU(cudaMemcpyAsync(sums_host, sums_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, es));
   if (fork) {
     CU(cudaEventRecord(c->ev_join, c->side));
     c->join_pending = true;
@@ -887,9 +894,11 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   return read_status(c);
 }
 
+// Every entry point but afqmc_propagate first orders the stream after an energy estimator still
+// running beside it (afqmc_local_energy_async); afqmc_propagate leaves that to the step's overlap.
 afqmc_status check_ctx(afqmc_ctx* c) {
   if (!c) return fail(AFQMC_EINVAL, "context is NULL");
-  return AFQMC_OK;
+  return join_energy(c);
 }
 
 #include "cv_host.inc"
@@ -1066,7 +1075,10 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
   return AFQMC_OK;
 }
 
-void afqmc_destroy(afqmc_ctx* ctx) { delete ctx; }
+void afqmc_destroy(afqmc_ctx* ctx) {
+  if (ctx && ctx->side) cudaStreamSynchronize(ctx->side);   // a copy into the caller's memory may be pending
+  delete ctx;
+}
 
 uint64_t afqmc_launch_count(afqmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
@@ -1095,9 +1107,10 @@ afqmc_status afqmc_stage_times(afqmc_ctx* ctx, double* ms, int64_t* count) {
 }
 
 afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps) {
-  afqmc_status st = check_ctx(ctx);
-  if (st != AFQMC_OK) return st;
+  if (!ctx) return fail(AFQMC_EINVAL, "context is NULL");   // an estimator beside it is joined by the overlap
+  afqmc_status st;
   if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
+  if (nsteps == 0 && (st = join_energy(ctx)) != AFQMC_OK) return st;
   for (int s = 0; s < nsteps; ++s)
     if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
   return AFQMC_OK;
@@ -1116,6 +1129,16 @@ afqmc_status afqmc_local_energy(afqmc_ctx* ctx, double* sums, double* eloc) {
                        ctx->stream));
   if (sums || eloc) return read_status(ctx);
   return AFQMC_OK;
+}
+
+afqmc_status afqmc_local_energy_async(afqmc_ctx* ctx, double* sums_host) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!sums_host) return fail(AFQMC_EINVAL, "afqmc_local_energy_async: sums_host is NULL");
+  // the estimator (and the copy) may run beside a following afqmc_propagate; any other entry
+  // point orders the stream after it first
+  double* dsums = ctx->at<double>(ctx->L.hist) + 4 * (kHistory - 1);
+  return DISPATCH(ctx, energy_impl, dsums, nullptr, true, sums_host);
 }
 
 afqmc_status afqmc_reortho(afqmc_ctx* ctx) {

@@ -390,3 +390,43 @@ def test_exchange_forms_and_group_counts_agree_with_oracle(name):
     # of the tolerance against the oracle
     spread = np.max(np.abs(np.array(seen) - seen[0]), axis=0)
     assert np.all(spread < 1e-5 * (1.0 + np.abs(ref))), np.max(spread / (1.0 + np.abs(ref)))
+
+
+def test_local_energy_async_matches_synchronous_sums():
+    """The asynchronous estimator readout copies the same four sums (bit for bit) into pinned memory."""
+    import torch
+    prob = config_small()
+    nw = 48
+    psi, w = _random_state(prob, nw, seed=21)
+    ctx = _ctx(prob, nw, prec="bf16x3")
+    ctx.set_walkers(psi, w, 0)
+    ref = ctx.local_energy()
+    out = torch.zeros(8, dtype=torch.float64).pin_memory().numpy()
+    ctx.local_energy_async(out[4:8])
+    ctx.synchronize(60.0)
+    assert np.array_equal(out[4:8], ref) and np.all(out[:4] == 0.0)
+    with pytest.raises(ValueError):
+        ctx.local_energy_async(np.zeros(3))
+    ctx.close()
+
+
+def test_async_energies_beside_steps_match_the_driver_loop():
+    """Per-step asynchronous readouts beside afqmc_propagate give the driver loop's energies bit for bit,
+    and a synchronising call between them (get_walkers) sees completed state."""
+    import torch
+    prob = config_small()
+    nw = 32
+    ref_ctx = _ctx(prob, nw, prec="bf16x3", seed=17)
+    ref_ctx.set_graphs(False)
+    ref = ref_ctx.run(6, energy_every=1, reortho_every=0, comb_every=0)
+    ref_ctx.close()
+    ctx = _ctx(prob, nw, prec="bf16x3", seed=17)
+    out = torch.zeros(4 * 6, dtype=torch.float64).pin_memory().numpy()
+    for s in range(6):
+        ctx.local_energy_async(out[4 * s:4 * s + 4])
+        ctx.propagate(1)
+        if s == 2:
+            ctx.get_walkers()
+    ctx.synchronize(60.0)
+    ctx.close()
+    assert np.array_equal(out.reshape(6, 4), np.asarray(ref).reshape(6, 4))
