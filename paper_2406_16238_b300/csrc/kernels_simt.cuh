@@ -505,8 +505,20 @@ __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long see
     __syncthreads();
     for (int i = threadIdx.x; i < len; i += blockDim.x) ws[i] = w[base + i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 0; i < len; ++i) {
+    if (threadIdx.x == 0) {   // eight weights loaded ahead of their additions (the chain of sums stays in order)
+      int i = 0;
+      for (; i + 8 <= len; i += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = ws[i + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          t = t + v[u];
+          ws[i + u] = t;
+          if (v[u] > 0.0) last = base + i + u;
+        }
+      }
+      for (; i < len; ++i) {
         const double wi = ws[i];
         t = t + wi;
         ws[i] = t;
