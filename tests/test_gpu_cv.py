@@ -101,3 +101,19 @@ def test_control_variate_run_tracks_the_plain_energy():
     assert np.all(np.isfinite(a))
     assert abs(d.mean()) < 5 * d.std(ddof=1) / np.sqrt(len(d)) + 1e-4, (d.mean(), d.std())
     assert np.max(np.abs(d)) < 0.05
+
+
+def test_async_readout_in_the_control_variate_form():
+    """afqmc_local_energy_async copies the control-variate estimator's sums as the synchronous call returns them."""
+    import torch
+    prob, ctx, _ = _trained_context("bf16x3", steps=4, epochs=5)
+    psi, logo, w, step = ctx.get_walkers()
+    ctx.cv_enable(True)
+    ref = ctx.local_energy()
+    ctx.set_walkers(psi, w, step)
+    out = torch.zeros(4, dtype=torch.float64).pin_memory().numpy()
+    ctx.local_energy_async(out)
+    ctx.synchronize(60.0)
+    ctx.cv_enable(False)
+    assert np.all(np.isfinite(out)) and out[1] > 0
+    assert np.array_equal(out, ref)

@@ -313,7 +313,8 @@ def test_full_size_sampled_walkers():
         assert abs(eloc1[i, 0] - e1) < 1e-10 * abs(e1)
 
 
-@pytest.mark.parametrize("prec,name,nw", [("fp64", "rhf_N8", 64), ("fp64", "uhf_N13_3_2", 16), ("bf16x3", "rhf_N8", 32)])
+@pytest.mark.parametrize("prec,name,nw", [("fp64", "rhf_N8", 64), ("fp64", "uhf_N13_3_2", 16), ("bf16x3", "rhf_N8", 32),
+                                          ("bf16x3", "uhf_N13_3_2", 24)])
 def test_graph_replay_is_bit_identical_to_direct_launches(prec, name, nw):
     """afqmc_run with captured CUDA graphs == direct launches, bit for bit (energy every 2nd step, QR, comb)."""
     prob = PROBLEMS[name]()
