@@ -260,28 +260,25 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
       }
       dg = rowp[a];   // T_aa
     }
+    // the warp's exchange sum (butterfly) and the inclusive segmented scan of the diagonal over the
+    // warp's rows of gamma block g, interleaved
     float er = er0 + er1, ei = ei0 + ei1;
-    er = warp_sum_f(er);
-    ei = warp_sum_f(ei);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      er += __shfl_xor_sync(0xffffffffu, er, 32 / (2 * o));
+      ei += __shfl_xor_sync(0xffffffffu, ei, 32 / (2 * o));
+      const float tx = __shfl_up_sync(0xffffffffu, dg.x, o), ty = __shfl_up_sync(0xffffffffu, dg.y, o);
+      if (lane >= o && r - o >= g * n) {
+        dg.x += tx;
+        dg.y += ty;
+      }
+    }
     const int w = nt * p.wpt + v;
     if (lane == 0 && w < p.W)
       p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + 4 * mt + wig] =
           make_double2((double)(p.smul * er), (double)(p.smul * ei));
-    if (p.vbias) {   // inclusive segmented scan of the diagonal over this warp's rows of gamma block g
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float tx = __shfl_up_sync(0xffffffffu, dg.x, o), ty = __shfl_up_sync(0xffffffffu, dg.y, o);
-        if (lane >= o && r - o >= g * n) {
-          dg.x += tx;
-          dg.y += ty;
-        }
-      }
-      if (live && w < p.W && (lane == 31 || a == n - 1)) {   // last row of the block within this warp
-        float* dst = reinterpret_cast<float*>(p.vbias + (size_t)w * p.X + mt * p.gpt + g);
-        atomicAdd(dst, p.smul * dg.x);
-        atomicAdd(dst + 1, p.smul * dg.y);
-      }
-    }
+    if (p.vbias && live && w < p.W && (lane == 31 || a == n - 1))   // last row of the block within this warp
+      atomicAdd(p.vbias + (size_t)w * p.X + mt * p.gpt + g, make_float2(p.smul * dg.x, p.smul * dg.y));
   }
 }
 
