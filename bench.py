@@ -316,6 +316,25 @@ def run_ours(args):
         fp64_form = {"value": nw / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": 5}
         c64.close()
         del c64
+    free_proj = None
+    if rank == 0:   # free projection (unshifted fields, complex weights, no comb) on the same workload
+        cfp = pkg.Afqmc(prob.h1e, prob.chol, prob.ecore, prob.nalpha, prob.nbeta, prob.psiT, nwalkers=nw,
+                        dt=WORKLOAD["dt"], seed=seed, prec=args.prec, device=dev, stream=stream)
+        cfp.set_free_projection(True)
+        cfp.run(3, 1, WORKLOAD["reortho_every"], 0)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        efp = cfp.run(10, 1, WORKLOAD["reortho_every"], 0)
+        ev1.record(stream)
+        ev1.synchronize()
+        msfp = ev0.elapsed_time(ev1) / 10
+        if not np.all(np.isfinite(efp)):
+            raise RuntimeError("free projection: non-finite estimator sums")
+        free_proj = {"value": nw / (msfp / 1e3), "unit": UNIT, "ms_per_step": msfp, "steps": 10,
+                     "form": args.prec, "note": "energy every step, QR every 5, no comb (Section "
+                     "\"Free projection AFQMC\")"}
+        cfp.close()
+        del cfp
     # end to end through the public API from pinned host buffers: create (H2D of h1e, L, psiT)
     # + the same steps with each step's energy sums copied to pinned host memory (stream-ordered,
     # asynchronous), the host waiting once at the end
@@ -373,6 +392,7 @@ def run_ours(args):
                        "value and ms_per_step come from the graph-replayed timed region",
         "step_flops_per_walker": fl,
         "fp64_form": fp64_form,
+        "free_projection": free_proj,
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "e2e": {"value": world * nw * args.steps / e2e_s, "unit": UNIT,

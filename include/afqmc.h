@@ -243,6 +243,20 @@ void afqmc_batch_destroy(afqmc_batch* b);
 afqmc_status afqmc_set_graphs(afqmc_ctx* ctx, int32_t enable);
 afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial);
 
+/* Free-projection AFQMC (Section "Free projection AFQMC"): enable = 1 switches the context to
+ * unconstrained propagation.  Each step draws the fields x ~ N(0,1) with no force-bias shift
+ * (xbar = 0; the mean-field subtraction and c_mf = i sqrt(dt) x.lbar stay) and carries complex
+ * weights w e^{i phi}, updated by the whole overlap ratio:
+ *   w e^{i phi} <- w e^{i phi} (O'/O) e^{c_mf} e^{dt (E_T - E_c)}   (no phaseless projection).
+ * While enabled the four estimator sums of afqmc_local_energy, afqmc_local_energy_async and
+ * afqmc_run are {Re, Im of sum w e^{i phi} E_L, Re, Im of sum w e^{i phi}} (the energy is the real
+ * part of their ratio), afqmc_popcontrol and comb_every > 0 return AFQMC_EINVAL, and the control
+ * variate cannot be enabled.  Switching (either way) sets every phase to 0; afqmc_set_walkers
+ * does too.  The weight magnitudes w stay where afqmc_get_walkers reports them. */
+afqmc_status afqmc_set_free_projection(afqmc_ctx* ctx, int32_t enable);
+/* Weight phases phi [nwalkers] (host, radians in (-pi, pi]); all 0 in phaseless propagation. */
+afqmc_status afqmc_get_weight_phases(afqmc_ctx* ctx, double* phase);
+
 /* Wait for the context's stream, polling, for at most timeout_s seconds. */
 afqmc_status afqmc_synchronize(afqmc_ctx* ctx, double timeout_s);
 

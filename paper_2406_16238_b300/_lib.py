@@ -74,6 +74,8 @@ SIGNATURES = {
     "afqmc_get_info": (_i32, [_vp, ctypes.POINTER(Info)]),
     "afqmc_set_etrial": (_i32, [_vp, ctypes.c_double]),
     "afqmc_set_graphs": (_i32, [_vp, _i32]),
+    "afqmc_set_free_projection": (_i32, [_vp, _i32]),
+    "afqmc_get_weight_phases": (_i32, [_vp, _dp]),
     "afqmc_autotune": (_i32, [_vp, _i32, ctypes.POINTER(Tuning)]),
     "afqmc_set_tuning": (_i32, [_vp, ctypes.POINTER(Tuning)]),
     "afqmc_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
@@ -289,6 +291,15 @@ class Afqmc:
 
     def set_graphs(self, enable=True):
         _check(self._lib.afqmc_set_graphs(self._ctx, 1 if enable else 0))
+
+    def set_free_projection(self, enable=True):
+        """Free projection (unshifted fields, complex weights w e^{i phi}, no comb) or back to phaseless."""
+        _check(self._lib.afqmc_set_free_projection(self._ctx, 1 if enable else 0))
+
+    def weight_phases(self):
+        ph = np.zeros(self.nwalkers)
+        _check(self._lib.afqmc_get_weight_phases(self._ctx, _ptr(ph)))
+        return ph
 
     def set_etrial(self, e):
         _check(self._lib.afqmc_set_etrial(self._ctx, float(e)))

@@ -64,7 +64,7 @@ struct Dims {
 
 // Offsets of every device buffer inside the workspace.
 struct Layout {
-  size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp;
+  size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp, wph;
   size_t phi, phi_r, hrot, hrot_r, lbar, lrot, chol, eh;
   size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
   size_t exch_part, eloc, hist, status, step, src, cum, neww, slot;
@@ -91,6 +91,7 @@ Layout plan(const Dims& d) {
   L.logO_tmp = take(W * 16);
   L.w = take(W * 8);
   L.w_tmp = take(W * 8);
+  L.wph = take(W * 8);
   L.phi = take(N * nc * 8);
   L.phi_r = take(N * nc * R);
   L.hrot = take(nc * N * 8);
@@ -231,6 +232,9 @@ struct afqmc_ctx {
   unsigned long long seed, host_step, launches;
   bool theta_fresh, vbias_fresh;
   int hist_used;
+  // free projection (Section "Free projection AFQMC"): no force-bias shift, complex weights
+  // w e^{i phi} (phases in L.wph), no phaseless projection and no comb
+  bool free_proj = false;
   tc::TcState tcs;
   CvState cv;
   int tile_cap = 4;          // largest CUDA-core GEMM register tile (4: 64-wide block tiles, 2: 32, 1: 16)
@@ -376,6 +380,7 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   a.dt = c->dt; a.e_trial = c->e_trial; a.e_c = c->e_c;
   a.eshift = std::exp(c->dt * (c->e_trial - c->e_c));
   a.step = mode == 1 ? c->at<unsigned long long>(c->L.step) : nullptr;
+  a.wph = (mode == 1 && c->free_proj) ? c->at<double>(c->L.wph) : nullptr;
   for (int s = 0; s < 2; ++s)
     a.thb[s] = (c->d.tensor() && s < c->d.nblk && c->tcs.blk[s].n > 0)
                    ? reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.blk[s].off_th)
@@ -535,7 +540,8 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
   k_energy<R><<<c->d.W, 256, 0, es>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
                                               c->at<cplx_t<R>>(c->L.thetaT), c->at<R>(c->L.hrot_r),
                                               c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
-                                              c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w), sums_dev, slot,
+                                              c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w),
+                                              c->free_proj ? c->at<double>(c->L.wph) : nullptr, sums_dev, slot,
                                               reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64));
   CHECK_LAUNCH(c);
   if (sums_host) CU(cudaMemcpyAsync(sums_host, sums_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, es));
@@ -566,7 +572,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     if ((st = launch_overlap<R>(c, 2)) != AFQMC_OK) return st;
     c->theta_fresh = true;
   }
-  if (!c->vbias_fresh) {
+  if (!c->vbias_fresh && !c->free_proj) {   // free projection draws unshifted fields
     StageTimer timer(c, AFQMC_STAGE_FORCE_BIAS);
     {
       // vbias[w][g] = smul * sum_k thetaT[w][k] * lrot[g][k],  k = (c, p)
@@ -587,6 +593,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar);
   fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
   fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
+  fa.free_proj = c->free_proj ? 1 : 0;
   if (d.tensor()) {
     fa.coefb = reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.off_coef);
     fa.kx = c->tcs.kx;
@@ -714,6 +721,7 @@ template <typename R>
 afqmc_status comb_impl(afqmc_ctx* c) {
   const Dims& d = c->d;
   using R2 = cplx_t<R>;
+  if (c->free_proj) return fail(AFQMC_EINVAL, "population control is not part of free projection");
   StageTimer timer(c, AFQMC_STAGE_COMB);
   k_comb_plan<<<1, 256, 0, c->stream>>>(d.W, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.w),
                                         c->at<double>(c->L.cum), c->at<int>(c->L.src), c->at<double>(c->L.neww),
@@ -879,6 +887,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.step, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.slot, 0, 256, c->stream));   // history slot, energy completion counter
+  CU(cudaMemsetAsync(c->base + c->L.wph, 0, (size_t)d.W * 8, c->stream));
   k_init_walkers<R><<<296, 256, 0, c->stream>>>(d.W, N, nc, c->at<double>(c->L.phi), c->at<cplx_t<R>>(c->L.psi),
                                                 c->at<double>(c->L.w));
   CHECK_LAUNCH(c);
@@ -1158,6 +1167,7 @@ afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;
   if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
+  if (ctx->free_proj && comb_every > 0) return fail(AFQMC_EINVAL, "free projection: comb_every must be <= 0");
   int used = 0, total = 0;
   double* hist = ctx->at<double>(ctx->L.hist);
   const bool graphs = ctx->graphs_on && !ctx->prof;
@@ -1258,6 +1268,7 @@ afqmc_status afqmc_set_walkers(afqmc_ctx* ctx, const double* psi, const double* 
     CU(cudaStreamSynchronize(ctx->stream));
   }
   CU(cudaMemcpyAsync(ctx->base + ctx->L.w, w, (size_t)d.W * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemsetAsync(ctx->base + ctx->L.wph, 0, (size_t)d.W * 8, ctx->stream));
   unsigned long long s64 = step;
   CU(cudaMemcpyAsync(ctx->base + ctx->L.step, &s64, 8, cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
@@ -1315,6 +1326,28 @@ afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial) {
     ctx->drop_graphs();
   }
   ctx->e_trial = e_trial;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_free_projection(afqmc_ctx* ctx, int32_t enable) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (enable && ctx->cv.enabled) return fail(AFQMC_EINVAL, "free projection: disable the control variate first");
+  if ((enable != 0) == ctx->free_proj) return AFQMC_OK;
+  CU(cudaStreamSynchronize(ctx->stream));   // captured graphs hold the other form's arguments
+  ctx->drop_graphs();
+  CU(cudaMemsetAsync(ctx->base + ctx->L.wph, 0, (size_t)ctx->d.W * 8, ctx->stream));
+  ctx->free_proj = enable != 0;
+  ctx->vbias_fresh = false;   // free projection may leave it stale: re-formed before a phaseless step
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_get_weight_phases(afqmc_ctx* ctx, double* phase) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!phase) return fail(AFQMC_EINVAL, "phase is NULL");
+  CU(cudaMemcpyAsync(phase, ctx->base + ctx->L.wph, (size_t)ctx->d.W * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
   return AFQMC_OK;
 }
 
@@ -1396,6 +1429,7 @@ afqmc_status afqmc_cv_enable(afqmc_ctx* ctx, int32_t enable) {
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;
   if (enable && !ctx->cv.attached) return fail(AFQMC_EINVAL, "cv: not attached");
+  if (enable && ctx->free_proj) return fail(AFQMC_EINVAL, "cv: not available in free projection");
   if ((enable != 0) != ctx->cv.enabled) {
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->drop_graphs();
@@ -1470,16 +1504,18 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
   const Dims& d = ctx->d;
   // snapshot of the walkers (host copies), restored after every trial
   const size_t pb = (size_t)d.W * d.N * d.ncol * 2 * d.rsz();
-  std::vector<char> psi(pb), logo((size_t)d.W * 16), w((size_t)d.W * 8);
+  std::vector<char> psi(pb), logo((size_t)d.W * 16), w((size_t)d.W * 8), wph((size_t)d.W * 8);
   CU(cudaMemcpyAsync(psi.data(), ctx->base + ctx->L.psi, pb, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaMemcpyAsync(logo.data(), ctx->base + ctx->L.logO, logo.size(), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaMemcpyAsync(w.data(), ctx->base + ctx->L.w, w.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(wph.data(), ctx->base + ctx->L.wph, wph.size(), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   const unsigned long long step0 = ctx->host_step;
   auto restore = [&]() -> afqmc_status {
     CU(cudaMemcpyAsync(ctx->base + ctx->L.psi, psi.data(), pb, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->base + ctx->L.logO, logo.data(), logo.size(), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->base + ctx->L.w, w.data(), w.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.wph, wph.data(), wph.size(), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->base + ctx->L.step, &step0, 8, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->host_step = step0;
@@ -1706,6 +1742,8 @@ afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_ever
   afqmc_ctx* c0 = b->sys[0];
   cudaStream_t s = c0->stream;
   const int nsys = (int)b->sys.size();
+  for (afqmc_ctx* c : b->sys)
+    if (c->free_proj && comb_every > 0) return fail(AFQMC_EINVAL, "batch: free projection with comb_every > 0");
   int total = 0;
   for (int k = 0; k < nsteps; ++k)
     if (energy_every > 0 && (c0->host_step + k) % (unsigned long long)energy_every == 0) ++total;

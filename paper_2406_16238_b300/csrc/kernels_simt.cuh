@@ -162,6 +162,7 @@ struct OverlapArgs {
   double dt, e_trial, e_c;
   double eshift;                  // exp(dt (E_T - E_c)), the same factor for every walker
   unsigned long long* step;       // incremented once (mode 1) if non-null
+  double* wph;                    // free projection (mode 1): weight phases [W]; null: phaseless
   // optional: Theta^T also as the tensor-core exchange operand of each spin block s, rows
   // (w, part, b) of nseg * kst bf16 = [hi | hi | lo] (hi only when nseg = 1)
   __nv_bfloat16* thb[2];
@@ -286,13 +287,14 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
 // Per-walker local energy from the pieces: E1 = smul sum htilde . Theta^T,
 // J = 1/2 sum_g vbias_g^2, K = 1/2 sum exchange partials.  eloc[w] = (E, E0+E1, J-K).
 // The last CTA to finish (completion counter `done`, reset by it) forms the weighted estimator
-// sums (ENumer, EDenom, E1Body, E2Body) over all walkers in a fixed order; with a slot counter
+// sums (ENumer, EDenom, E1Body, E2Body) over all walkers in a fixed order (free projection, wph
+// non-null: Re and Im of sum w e^{i phi} E_L, Re and Im of sum w e^{i phi}); with a slot counter
 // they go to out + 4 * (*slot) and the counter advances (graph-replayable history).
 template <typename R>
 __global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double smul, double ecore, int nchunk,
                                                 const cplx_t<R>* thetaT, const R* hrot_r, const cplx_t<R>* vbias,
                                                 const double2* exch_part, double2* eloc, int W, const double* wgt,
-                                                double* out, int* slot, unsigned int* done) {
+                                                const double* wph, double* out, int* slot, unsigned int* done) {
   __shared__ double red[32];
   __shared__ double part[6 * 256];
   __shared__ int last_s;
@@ -350,13 +352,28 @@ __global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double s
   if (!last_s) return;
   __threadfence();
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  for (int u = tid; u < W; u += blockDim.x) {
-    const double wi = wgt[u];
-    if (wi == 0.0) continue;
-    s0 += wi * __ldcg(&eloc[3 * u].x);
-    s1 += wi;
-    s2 += wi * __ldcg(&eloc[3 * u + 1].x);
-    s3 += wi * __ldcg(&eloc[3 * u + 2].x);
+  if (wph) {   // free projection: complex weights w e^{i phi}; (Re, Im) of sum w e^{i phi} E_L and of sum w e^{i phi}
+    for (int u = tid; u < W; u += blockDim.x) {
+      const double wi = wgt[u];
+      if (wi == 0.0) continue;
+      double sn, cs;
+      sincos(wph[u], &sn, &cs);
+      const double2 e = __ldcg(&eloc[3 * u]);
+      const double wr = wi * cs, wim = wi * sn;
+      s0 += wr * e.x - wim * e.y;
+      s1 += wr * e.y + wim * e.x;
+      s2 += wr;
+      s3 += wim;
+    }
+  } else {
+    for (int u = tid; u < W; u += blockDim.x) {
+      const double wi = wgt[u];
+      if (wi == 0.0) continue;
+      s0 += wi * __ldcg(&eloc[3 * u].x);
+      s1 += wi;
+      s2 += wi * __ldcg(&eloc[3 * u + 1].x);
+      s3 += wi * __ldcg(&eloc[3 * u + 2].x);
+    }
   }
   const double s4[4] = {s0, s1, s2, s3};
   __syncthreads();   // part[] and red[] are reused
@@ -389,6 +406,7 @@ struct FieldArgs {
   int kx, nseg;
   double2* cmf;             // [W]
   double2* xxbar;           // [W]
+  int free_proj;            // free projection: no force-bias shift (xbar = 0)
 };
 
 // The N(0,1) fields of every walker slot at the current step counter (stream 0) into x[w][g],
@@ -423,14 +441,17 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
       const int g = 2 * j + t;
       if (g >= a.X) break;
       const double x = a.x[(size_t)w * a.X + g];
-      const double2 vb = to_d2(a.vbias[(size_t)w * a.X + g]);
-      const double dre = vb.x - a.lbar[g], dim = vb.y;
-      double2 xb = mk(a.sdt * dim, -a.sdt * dre);
-      if (a.cap > 0.0) {   // |xb| > cap, tested on the squares (the square root only when capping)
-        const double m2 = xb.x * xb.x + xb.y * xb.y;
-        if (m2 > a.cap * a.cap) {
-          const double m = sqrt(m2);
-          if (m > a.cap) xb = cscale(xb, a.cap / m);
+      double2 xb = mk(0.0, 0.0);
+      if (!a.free_proj) {
+        const double2 vb = to_d2(a.vbias[(size_t)w * a.X + g]);
+        const double dre = vb.x - a.lbar[g], dim = vb.y;
+        xb = mk(a.sdt * dim, -a.sdt * dre);
+        if (a.cap > 0.0) {   // |xb| > cap, tested on the squares (the square root only when capping)
+          const double m2 = xb.x * xb.x + xb.y * xb.y;
+          if (m2 > a.cap * a.cap) {
+            const double m = sqrt(m2);
+            if (m > a.cap) xb = cscale(xb, a.cap / m);
+          }
         }
       }
       const double2 xs = mk(x - xb.x, -xb.y);
@@ -1138,8 +1159,14 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     const double2 xx = a.xxbar[w];
     const double ls_re = lo_new.x - lo_old.x + c.x;
     const double theta = lo_new.y - lo_old.y + c.y;
-    const double li_re = ls_re + xx.x;
-    double wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * a.eshift;
+    double wn;
+    if (a.wph) {   // free projection: the whole ratio (O'/O) e^{c_mf}, its phase kept with the weight
+      wn = a.w[w] * exp(ls_re) * a.eshift;
+      a.wph[w] = wrap_angle(a.wph[w] + theta);
+    } else {
+      const double li_re = ls_re + xx.x;
+      wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * a.eshift;
+    }
     if (!isfinite(wn)) {
       wn = 0.0;
       atomicOr(a.status, kStatusNonFinite);
