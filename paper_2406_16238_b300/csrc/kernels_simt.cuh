@@ -885,13 +885,114 @@ __device__ __forceinline__ double2 cmul_renorm(double2 a, double2 b, int* e) {
   return q;
 }
 
+// One element (4, 8 or 16 bytes, aligned to its size) from global to shared memory without a
+// register round trip (cp.async); cp_async_wait_all waits for the thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// acc -= a b (complex)
+template <typename R>
+__device__ __forceinline__ void csub(cplx_t<R>& acc, const cplx_t<R>& a, const cplx_t<R>& b) {
+  acc.x = fma(-a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(-a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+
+// Theta rows of one spin block from the staged psi rows: thread p solves row p in place in
+// Y[p] (z U = psi_p forward, then y L = z with unit lower L backward), four columns at a time
+// (the block's earlier entries are subtracted by a compact loop with four independent
+// accumulators, then the 4 x 4 triangle), and writes Theta^T[perm[i]][p] = y_i and its split-bf16
+// copy.  Loops stay rolled: the kernel runs between large tensor-core kernels, so straight-line
+// code would be fetched cold from L2 on every launch.
+template <typename R>
+__device__ __forceinline__ void subst_rows_blocked(cplx_t<R>* Y, int ldy, const cplx_t<R>* F, const int* perm, int n,
+                                                   int N, cplx_t<R>* thw, __nv_bfloat16* thb, int kst, int nseg, int w) {
+  using R2 = cplx_t<R>;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    R2* y = Y + (size_t)p * ldy;
+    for (int j0 = 0; j0 < n; j0 += 4) {   // z U = psi_p
+      const int nb = min(4, n - j0);
+      R2 acc[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[t].x = R(0);
+        acc[t].y = R(0);
+        if (t < nb) acc[t] = y[j0 + t];
+      }
+      for (int k = 0; k < j0; ++k) {
+        const R2 z = y[k];
+        const R2* f = F + k * n + j0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nb) csub<R>(acc[t], z, f[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t < nb) {
+          const R2 d = F[(j0 + t) * n + j0 + t];   // 1 / U_jj
+          const R2 z = acc[t];
+          acc[t].x = z.x * d.x - z.y * d.y;
+          acc[t].y = z.x * d.y + z.y * d.x;
+#pragma unroll
+          for (int t2 = t + 1; t2 < 4; ++t2)
+            if (t2 < nb) csub<R>(acc[t2], acc[t], F[(j0 + t) * n + j0 + t2]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nb) y[j0 + t] = acc[t];
+    }
+    for (int j0 = ((n - 1) / 4) * 4; j0 >= 0; j0 -= 4) {   // y L = z, blocks in descending order
+      const int nb = min(4, n - j0);
+      R2 acc[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        acc[t].x = R(0);
+        acc[t].y = R(0);
+        if (t < nb) acc[t] = y[j0 + t];
+      }
+      for (int k = j0 + nb; k < n; ++k) {
+        const R2 yk = y[k];
+        const R2* f = F + k * n + j0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nb) csub<R>(acc[t], yk, f[t]);
+      }
+#pragma unroll
+      for (int t = 3; t >= 1; --t)
+        if (t < nb) {
+#pragma unroll
+          for (int t2 = 0; t2 < t; ++t2) csub<R>(acc[t2], acc[t], F[(j0 + t) * n + j0 + t2]);
+        }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nb) y[j0 + t] = acc[t];
+    }
+    for (int i = 0; i < n; ++i) {   // Theta^T[perm[i]][p] = y_i (consecutive p: coalesced)
+      const R2 v = y[i];
+      const int b = perm[i];
+      thw[(size_t)b * N + p] = v;
+      if (thb) store_theta_bf16(thb, kst, nseg, n, w, b, p, v);
+    }
+  }
+}
+
+// 5 CTAs per SM: the W = 640 walkers of the benchmark shape run in one wave on 148 SMs.
 template <typename R, bool STAGE>
-__global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
+__global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
   using R2 = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char sm_lu[];
   __shared__ int piv_s, sing_s, swaps_s, exp_s;
   __shared__ double2 inv_s, prod_s;
+  __shared__ double ld_im_s;   // imaginary part of log det (its atan2 runs in a second warp)
   const int w = blockIdx.x, tid = threadIdx.x, N = a.N;
+  if (tid == 32) ld_im_s = 0.0;
   if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
   if (a.mode == 1 && a.w[w] == 0.0) return;
   const int nmax = max(a.nb[0], a.nblk > 1 ? a.nb[1] : 0);
@@ -903,37 +1004,20 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
   R2* F = reinterpret_cast<R2*>(reinterpret_cast<unsigned char*>(perm) + ((size_t)nmax * 4 + 15) / 16 * 16);
   R2* Y = F + (size_t)nmax * nmax;                          // [N][ldy]: psi rows, then Theta rows
   R* PH = reinterpret_cast<R*>(Y + (size_t)N * ldy);        // [N][n] Phi block
-  double ld_re = 0.0, ld_im = 0.0;
+  double ld_re = 0.0;
   bool singular = false;
   for (int s = 0; s < a.nblk; ++s) {
     const int c0 = a.c0[s], n = a.nb[s];
     if (n == 0) continue;
     __syncthreads();
     const R2* psw = a.psi + (size_t)w * N * a.ncol + c0;
-    if (STAGE) {   // batches of loads in flight before the stores
-      constexpr int U = 6;
-      for (int base = tid; base < N * n; base += U * 128) {
-        R2 pv[U];
-        R fv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int idx = base + u * 128;
-          if (idx < N * n) {
-            const int p = idx / n, j = idx - (idx / n) * n;
-            pv[u] = psw[(size_t)p * a.ncol + j];
-            fv[u] = a.phi_r[(size_t)p * a.ncol + c0 + j];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int idx = base + u * 128;
-          if (idx < N * n) {
-            const int p = idx / n, j = idx - (idx / n) * n;
-            Y[(size_t)p * ldy + j] = pv[u];
-            PH[idx] = fv[u];
-          }
-        }
+    if (STAGE) {   // asynchronous copies into shared memory, all of the block's in flight at once
+      for (int idx = tid; idx < N * n; idx += blockDim.x) {
+        const int p = idx / n, j = idx - p * n;
+        cp_async_elem<sizeof(R2)>(&Y[(size_t)p * ldy + j], &psw[(size_t)p * a.ncol + j]);
+        cp_async_elem<sizeof(R)>(&PH[idx], &a.phi_r[(size_t)p * a.ncol + c0 + j]);
       }
+      cp_async_wait_all();
     }
     if (tid < n) perm[tid] = tid;
     if (tid == 0) { sing_s = 0; swaps_s = 0; }
@@ -984,6 +1068,74 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
             A[(i0 + di) * lda + j0 + dj] = mk((double)acc[di][dj][0], (double)acc[di][dj][1]);
     }
     __syncthreads();
+    if (n <= 32) {
+      // One warp takes the pivot step: every lane holds its row's column-k entry and its
+      // reciprocal (formed while the pivot is being chosen), then swaps the rows and writes the
+      // multipliers; one barrier before and one after the trailing update.
+      const int lane = tid & 31;
+      for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+          const bool own = lane >= k && lane < n;
+          const double2 v = own ? A[lane * lda + k] : mk(0.0, 0.0);
+          // largest |re| + |im| (non-negative doubles order like their bit patterns), lowest row on ties
+          long long best = own ? __double_as_longlong(fabs(v.x) + fabs(v.y)) : -1ll;
+          int bi = own ? lane : 64;
+          // 1 / v = conj(v) / |v|^2 (lanes without a row divide 1 by 1, not by 0)
+          const double2 vr = own ? v : mk(1.0, 0.0);
+          const double r = 1.0 / fma(vr.x, vr.x, vr.y * vr.y);
+          double2 inv = mk(vr.x * r, -vr.y * r);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          // zero, NaN or infinity: the sum's bit pattern is 0 or has every exponent bit set
+          if (best <= 0 || best >= 0x7ff0000000000000LL) {
+            if (lane == 0) sing_s = 1;
+          } else {
+            inv = mk(__shfl_sync(0xffffffffu, inv.x, bi), __shfl_sync(0xffffffffu, inv.y, bi));
+            const double2 pk = mk(__shfl_sync(0xffffffffu, v.x, bi), __shfl_sync(0xffffffffu, v.y, bi));
+            const double2 vk = mk(__shfl_sync(0xffffffffu, v.x, k), __shfl_sync(0xffffffffu, v.y, k));
+            if (bi != k && lane < n && lane != k) {   // rows k and bi trade places (column k below)
+              const double2 t = A[k * lda + lane];
+              A[k * lda + lane] = A[bi * lda + lane];
+              A[bi * lda + lane] = t;
+            }
+            if (lane == k) A[k * lda + k] = pk;
+            if (lane > k && lane < n) {   // multiplier of the row now at `lane` (old row k if lane == bi)
+              const double2 src = lane == bi ? vk : v;
+              A[lane * lda + k] = mk(fma(src.x, inv.x, -src.y * inv.y), fma(src.x, inv.y, src.y * inv.x));
+            }
+            if (lane == 0) {
+              dinv[k] = inv;
+              pivv[k] = pk;
+              if (bi != k) {
+                swaps_s ^= 1;
+                const int t = perm[k];
+                perm[k] = perm[bi];
+                perm[bi] = t;
+              }
+            }
+          }
+        }
+        __syncthreads();
+        if (sing_s) break;
+        const int rem = n - k - 1;
+        // (i, j) of a flat index: the single-precision quotient is exact here (idx < 1024, rem <= 31)
+        const float frem = __frcp_rn((float)max(rem, 1));
+        for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+          const int io = (int)(((float)idx + 0.5f) * frem);
+          const int i = k + 1 + io, j = k + 1 + idx - io * rem;
+          const double2 l = A[i * lda + k], u = A[k * lda + j];
+          double2 v = A[i * lda + j];
+          v.x = fma(-l.x, u.x, fma(l.y, u.y, v.x));
+          v.y = fma(-l.x, u.y, fma(-l.y, u.x, v.y));
+          A[i * lda + j] = v;
+        }
+        __syncthreads();
+      }
+    } else
     for (int k = 0; k < n; ++k) {
       if (tid < 32) {   // pivot: largest |re| + |im| in column k, lowest row on ties
         // non-negative doubles order like their bit patterns: compare as integers
@@ -1076,71 +1228,70 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     }
     __syncthreads();
     R2* thw = a.thetaT + ((size_t)w * a.ncol + c0) * N;
-    for (int p = tid; p < N; p += blockDim.x) {
-      // y_k of row p: Y[p][k] (STAGE) or Theta^T[perm[k]][p]
-      auto at = [&](int k) -> R2& { return STAGE ? Y[(size_t)p * ldy + k] : thw[(size_t)perm[k] * N + p]; };
-      if (!STAGE)
+    if (STAGE) {
+      subst_rows_blocked<R>(Y, ldy, F, perm, n, N, thw, a.thb[s], a.kst, a.nseg, w);
+    } else {   // row perm[k] of Theta^T holds y_k of every psi row throughout (no final permutation)
+      for (int p = tid; p < N; p += blockDim.x) {
+        auto at = [&](int k) -> R2& { return thw[(size_t)perm[k] * N + p]; };
         for (int j = 0; j < n; ++j) at(j) = psw[(size_t)p * a.ncol + j];
-      for (int j = 0; j < n; ++j) {   // z U = psi_p (two independent partial sums)
-        R sr0 = at(j).x, si0 = at(j).y, sr1 = R(0), si1 = R(0);
-        int k = 0;
-        for (; k + 1 < j; k += 2) {
-          const R2 z0 = at(k), u0 = F[k * n + j], z1 = at(k + 1), u1 = F[(k + 1) * n + j];
-          sr0 -= z0.x * u0.x - z0.y * u0.y;
-          si0 -= z0.x * u0.y + z0.y * u0.x;
-          sr1 -= z1.x * u1.x - z1.y * u1.y;
-          si1 -= z1.x * u1.y + z1.y * u1.x;
+        for (int j = 0; j < n; ++j) {   // z U = psi_p (two independent partial sums)
+          R sr0 = at(j).x, si0 = at(j).y, sr1 = R(0), si1 = R(0);
+          int k = 0;
+          for (; k + 1 < j; k += 2) {
+            const R2 z0 = at(k), u0 = F[k * n + j], z1 = at(k + 1), u1 = F[(k + 1) * n + j];
+            sr0 -= z0.x * u0.x - z0.y * u0.y;
+            si0 -= z0.x * u0.y + z0.y * u0.x;
+            sr1 -= z1.x * u1.x - z1.y * u1.y;
+            si1 -= z1.x * u1.y + z1.y * u1.x;
+          }
+          if (k < j) {
+            const R2 z0 = at(k), u0 = F[k * n + j];
+            sr0 -= z0.x * u0.x - z0.y * u0.y;
+            si0 -= z0.x * u0.y + z0.y * u0.x;
+          }
+          const R sr = sr0 + sr1, si = si0 + si1;
+          const R2 d = F[j * n + j];
+          R2 o;
+          o.x = sr * d.x - si * d.y;
+          o.y = sr * d.y + si * d.x;
+          at(j) = o;
         }
-        if (k < j) {
-          const R2 z0 = at(k), u0 = F[k * n + j];
-          sr0 -= z0.x * u0.x - z0.y * u0.y;
-          si0 -= z0.x * u0.y + z0.y * u0.x;
+        for (int j = n - 2; j >= 0; --j) {   // y L = z (unit lower L)
+          R sr0 = at(j).x, si0 = at(j).y, sr1 = R(0), si1 = R(0);
+          int k = j + 1;
+          for (; k + 1 < n; k += 2) {
+            const R2 z0 = at(k), l0 = F[k * n + j], z1 = at(k + 1), l1 = F[(k + 1) * n + j];
+            sr0 -= z0.x * l0.x - z0.y * l0.y;
+            si0 -= z0.x * l0.y + z0.y * l0.x;
+            sr1 -= z1.x * l1.x - z1.y * l1.y;
+            si1 -= z1.x * l1.y + z1.y * l1.x;
+          }
+          if (k < n) {
+            const R2 z0 = at(k), l0 = F[k * n + j];
+            sr0 -= z0.x * l0.x - z0.y * l0.y;
+            si0 -= z0.x * l0.y + z0.y * l0.x;
+          }
+          R2 o;
+          o.x = sr0 + sr1;
+          o.y = si0 + si1;
+          at(j) = o;
         }
-        const R sr = sr0 + sr1, si = si0 + si1;
-        const R2 d = F[j * n + j];
-        R2 o;
-        o.x = sr * d.x - si * d.y;
-        o.y = sr * d.y + si * d.x;
-        at(j) = o;
       }
-      for (int j = n - 2; j >= 0; --j) {   // y L = z (unit lower L)
-        R sr0 = at(j).x, si0 = at(j).y, sr1 = R(0), si1 = R(0);
-        int k = j + 1;
-        for (; k + 1 < n; k += 2) {
-          const R2 z0 = at(k), l0 = F[k * n + j], z1 = at(k + 1), l1 = F[(k + 1) * n + j];
-          sr0 -= z0.x * l0.x - z0.y * l0.y;
-          si0 -= z0.x * l0.y + z0.y * l0.x;
-          sr1 -= z1.x * l1.x - z1.y * l1.y;
-          si1 -= z1.x * l1.y + z1.y * l1.x;
+      __syncthreads();
+      if (a.thb[s])
+        for (int idx = tid; idx < n * N; idx += blockDim.x) {
+          const int b = idx / N, p = idx % N;
+          store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, thw[(size_t)b * N + p]);
         }
-        if (k < n) {
-          const R2 z0 = at(k), l0 = F[k * n + j];
-          sr0 -= z0.x * l0.x - z0.y * l0.y;
-          si0 -= z0.x * l0.y + z0.y * l0.x;
-        }
-        R2 o;
-        o.x = sr0 + sr1;
-        o.y = si0 + si1;
-        at(j) = o;
-      }
     }
-    __syncthreads();
-    if (STAGE)
-      for (int idx = tid; idx < n * N; idx += blockDim.x) {   // Theta^T[perm[i]][p] = y_i
-        const int i = idx / N, p = idx % N;
-        const R2 v = Y[(size_t)p * ldy + i];
-        thw[(size_t)perm[i] * N + p] = v;
-        if (a.thb[s]) store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, perm[i], p, v);
-      }
-    else if (a.thb[s])
-      for (int idx = tid; idx < n * N; idx += blockDim.x) {
-        const int b = idx / N, p = idx % N;
-        store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, thw[(size_t)b * N + p]);
-      }
-    if (tid == 0) {   // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps)
+    // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps); the real and
+    // imaginary parts in two warps
+    if (tid == 0) {
       const double2 pr = prod_s;
       ld_re += 0.5 * log(fma(pr.x, pr.x, pr.y * pr.y)) + exp_s * 0.6931471805599453;   // |pr| in [1, 2 sqrt 2)
-      ld_im += atan2(pr.y, pr.x) + (swaps_s ? 3.141592653589793 : 0.0);
+    } else if (tid == 32) {
+      const double2 pr = prod_s;
+      ld_im_s += atan2(pr.y, pr.x) + (swaps_s ? 3.141592653589793 : 0.0);
     }
     __syncthreads();
   }
@@ -1150,7 +1301,7 @@ __global__ void __launch_bounds__(128) k_overlap_lu(OverlapArgs<R> a) {
     atomicOr(a.status, kStatusSingular);
     return;
   }
-  const double2 lo_new = mk(a.smul * ld_re, wrap_angle(a.smul * ld_im));
+  const double2 lo_new = mk(a.smul * ld_re, wrap_angle(a.smul * ld_im_s));
   if (a.mode == 0) {
     a.logO[w] = lo_new;
   } else if (a.mode == 1) {
