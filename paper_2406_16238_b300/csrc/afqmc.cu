@@ -65,7 +65,7 @@ struct Dims {
 // Offsets of every device buffer inside the workspace.
 struct Layout {
   size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp, wph;
-  size_t phi, phi_r, hrot, hrot_r, lbar, lrot, chol, eh;
+  size_t phi, phi_r, hrot, hrot_r, lbar, slbar, lrot, chol, eh;
   size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
   size_t exch_part, eloc, hist, status, step, src, cum, neww, slot;
   size_t tc;          // tensor-core operand buffers (BF16 forms)
@@ -97,6 +97,7 @@ Layout plan(const Dims& d) {
   L.hrot = take(nc * N * 8);
   L.hrot_r = take(nc * N * R);
   L.lbar = take(X * 8);
+  L.slbar = take(X * 8);
   L.lrot = take(X * nc * N * R);
   L.chol = take(X * N * N * R);
   L.eh = take(N * N * R);
@@ -590,7 +591,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   FieldArgs<R> fa{};
   fa.X = d.X; fa.sdt = c->sdt; fa.cap = c->cap; fa.seed = c->seed;
   fa.step = c->at<unsigned long long>(c->L.step);
-  fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar);
+  fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar); fa.slbar = c->at<double>(c->L.slbar);
   fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
   fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
   fa.free_proj = c->free_proj ? 1 : 0;
@@ -830,6 +831,9 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   CU(cudaMemcpyAsync(c->base + c->L.phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->base + c->L.hrot, hrot.data(), hrot.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->base + c->L.lbar, lbar.data(), lbar.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  std::vector<double> slbar(X);   // sqrt(dt) lbar for the fields kernel
+  for (int g = 0; g < X; ++g) slbar[g] = c->sdt * lbar[g];
+  CU(cudaMemcpyAsync(c->base + c->L.slbar, slbar.data(), slbar.size() * 8, cudaMemcpyHostToDevice, c->stream));
   {   // prod[g] = L^g L^g
     GemmDesc g = gdesc(N, N, N, X);
     g.A = chol64; g.sAb = (long long)N * N; g.sAm = N; g.sAk = 1;

@@ -399,6 +399,7 @@ struct FieldArgs {
   const unsigned long long* step;
   const cplx_t<R>* vbias;   // [W][X]
   const double* lbar;       // [X]
+  const double* slbar;      // [X] sqrt(dt) lbar
   double* x;                // [W][X]
   double2* xbar;            // [W][X]
   cplx_t<R>* coef;          // [W][X]
@@ -434,7 +435,10 @@ template <typename R>
 __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
   __shared__ double red[32];
   const int w = blockIdx.x, tid = threadIdx.x;
-  double2 cm = mk(0.0, 0.0), xx = mk(0.0, 0.0);
+  // c_mf = i sdt sum lbar_g xs_g; sum (x xbar - xbar^2 / 2) = sum (a x - (a^2 - b^2) / 2) +
+  // i sum b (x - a) for xbar = a + i b, kept as sum a x, sum (a^2 - b^2) and sum b (x - a)
+  double2 cm = mk(0.0, 0.0);
+  double s_ax = 0.0, s_q = 0.0, s_im = 0.0;
   const int npairs = (a.X + 1) / 2;
   for (int j = tid; j < npairs; j += blockDim.x) {
     for (int t = 0; t < 2; ++t) {
@@ -442,10 +446,10 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
       if (g >= a.X) break;
       const double x = a.x[(size_t)w * a.X + g];
       double2 xb = mk(0.0, 0.0);
-      if (!a.free_proj) {
+      const double sl = a.slbar[g];
+      if (!a.free_proj) {   // xbar = -i sdt (vbias - lbar)
         const double2 vb = to_d2(a.vbias[(size_t)w * a.X + g]);
-        const double dre = vb.x - a.lbar[g], dim = vb.y;
-        xb = mk(a.sdt * dim, -a.sdt * dre);
+        xb = mk(a.sdt * vb.y, fma(-a.sdt, vb.x, sl));
         if (a.cap > 0.0) {   // |xb| > cap, tested on the squares (the square root only when capping)
           const double m2 = xb.x * xb.x + xb.y * xb.y;
           if (m2 > a.cap * a.cap) {
@@ -455,7 +459,14 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
         }
       }
       const double2 xs = mk(x - xb.x, -xb.y);
-      const cplx_t<R> cf = from_d2<R>(mk(a.sdt * xs.y, -a.sdt * xs.x));
+      cplx_t<R> cf;   // -i sdt xs (binary32 forms: the product in binary32)
+      if constexpr (sizeof(R) == 4) {
+        const float sf = (float)a.sdt;
+        cf.x = sf * (float)xs.y;
+        cf.y = -sf * (float)xs.x;
+      } else {
+        cf = from_d2<R>(mk(a.sdt * xs.y, -a.sdt * xs.x));
+      }
       a.coef[(size_t)w * a.X + g] = cf;
       if (a.coefb) {
         const size_t rowlen = (size_t)a.nseg * a.kx;
@@ -472,19 +483,16 @@ __global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
           im[2 * a.kx] = hi;
         }
       }
-      // c_mf += i sdt lbar_g xs;  x xbar - xbar^2 / 2 = (xbar_re (x - xbar_re / 2) + xbar_im^2 / 2,
-      // xbar_im (x - xbar_re)), written as fused multiply-adds
-      const double sl = a.sdt * a.lbar[g];
       cm.x = fma(-sl, xs.y, cm.x);
       cm.y = fma(sl, xs.x, cm.y);
-      xx.x = fma(xb.x, fma(-0.5, xb.x, x), xx.x);
-      xx.x = fma(0.5 * xb.y, xb.y, xx.x);
-      xx.y = fma(xb.y, xs.x, xx.y);
+      s_ax = fma(xb.x, x, s_ax);
+      s_q = fma(xb.x, xb.x, fma(-xb.y, xb.y, s_q));
+      s_im = fma(xb.y, xs.x, s_im);
       a.xbar[(size_t)w * a.X + g] = xb;
     }
   }
   __shared__ double part[4 * 256];
-  const double v4[4] = {cm.x, cm.y, xx.x, xx.y};
+  const double v4[4] = {cm.x, cm.y, fma(-0.5, s_q, s_ax), s_im};
   block_sum_multi<4>(v4, part, red);
   if (tid == 0) {
     a.cmf[w] = mk(red[0], red[1]);
