@@ -1343,10 +1343,10 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
 // substitution on each row at the walkers' precision with R rounded once, and
 // log O -= smul sum log R_ii.  stage_psi: the block's columns are staged in
 // shared memory as binary64 rows P[j][p] with an odd row pitch.
-// The factorisation runs in one warp (warp-level syncs only): every lane forms
-// R_kk and 1 / R_kk itself, and the trailing update walks the packed upper
-// triangle in a table ordered by decreasing row, so the pairs of step k are its
-// first m (m + 1) / 2 entries (m = n - k - 1).
+// In the factorisation one warp forms R_kk, 1 / R_kk and row k, and the whole
+// CTA takes the trailing update, walking the packed upper triangle in a table
+// ordered by decreasing row, so the pairs of step k are its first m (m + 1) / 2
+// entries (m = n - k - 1).
 // Shared memory: G [nmax^2] binary64 complex | 1 / R_kk [nmax] | pair table
 // [nmax (nmax + 1) / 2] (row, column bytes) | a region holding P during the
 // Gram product and R at the walkers' precision afterwards.
@@ -1423,21 +1423,27 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
       G[i * n + j] = mk(re, im);
     }
     __syncthreads();
-    // right-looking Cholesky on the upper triangle in warp 0: G_kk -> R_kk, row k -> R_kj
-    if (tid < 32) {
+    // right-looking Cholesky on the upper triangle: G_kk -> R_kk and row k -> R_kj in one warp,
+    // the trailing update G_ij -= conj(R_ki) R_kj (k < i <= j) by the whole CTA.  The one-warp
+    // part runs in warp (blockIdx.x / 148) % 4: CTAs resident on one SM are usually 148 blocks
+    // apart, so their serial binary64 chains land on different sub-partitions.
+    {
+      const int sw = (blockIdx.x / 148) % 4, lane = tid & 31;
       for (int k = 0; k < n; ++k) {
-        const double d = G[k * n + k].x;
-        const double r = sqrt(fmax(d, 1e-300)), ri = 1.0 / r;
-        __syncwarp();
-        if (tid == 0) {
-          if (!(d > 0.0) || !isfinite(d)) bad_s = 1;
-          G[k * n + k] = mk(r, 0.0);
-          rinv[k] = ri;
+        if ((tid >> 5) == sw) {
+          const double d = G[k * n + k].x;
+          __syncwarp();   // every lane has read G_kk before lane 0 overwrites it
+          const double r = sqrt(fmax(d, 1e-300)), ri = 1.0 / r;
+          for (int j = k + 1 + lane; j < n; j += 32) G[k * n + j] = cscale(G[k * n + j], ri);
+          if (lane == 0) {
+            if (!(d > 0.0) || !isfinite(d)) bad_s = 1;
+            G[k * n + k] = mk(r, 0.0);
+            rinv[k] = ri;
+          }
         }
-        for (int j = k + 1 + tid; j < n; j += 32) G[k * n + j] = cscale(G[k * n + j], ri);
-        __syncwarp();
+        __syncthreads();
         const int m = n - k - 1, tot = m * (m + 1) / 2;
-        for (int e = tid; e < tot; e += 32) {   // G_ij -= conj(R_ki) R_kj, k < i <= j
+        for (int e = tid; e < tot; e += blockDim.x) {
           const int i = tri[e].x, j = tri[e].y;
           const double2 rki = G[k * n + i], rkj = G[k * n + j];
           double2 g = G[i * n + j];
@@ -1445,12 +1451,14 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
           g.y = fma(-rki.x, rkj.y, fma(rki.y, rkj.x, g.y));
           G[i * n + j] = g;
         }
-        __syncwarp();
+        __syncthreads();
       }
-      double ls = 0.0;   // sum_k log R_kk, one lane per diagonal entry
-      for (int k = tid; k < n; k += 32) ls += log(G[k * n + k].x);
-      ls = warp_sum(ls);
-      if (tid == 0) logsum_s += ls;
+      if (tid < 32) {
+        double ls = 0.0;   // sum_k log R_kk, one lane per diagonal entry
+        for (int k = tid; k < n; k += 32) ls += log(G[k * n + k].x);
+        ls = warp_sum(ls);
+        if (tid == 0) logsum_s += ls;
+      }
     }
     __syncthreads();
     for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each entry of R to R (P is dead)
