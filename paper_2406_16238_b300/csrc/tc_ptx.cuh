@@ -40,11 +40,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 // Bounded wait for the phase of `parity`; false on timeout or when another role aborted.
+// As mbar_try_wait, suspending the thread for up to 100 us (it resumes as soon as the phase
+// completes), so a waiting warp spends few issue slots on polling.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_suspend(bar, parity)) return true;
     if (*abort_flag) return false;
     if (global_ns() - t0 > kWaitNs) return false;
   }
