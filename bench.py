@@ -263,21 +263,23 @@ def run_ours(args):
         torch.distributed.barrier()
     l0 = ctx.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    step_ms = []
+    step_ms, sums_timed = [], []
     with ClockSampler(dev.index) as clk:
         torch.cuda.synchronize(dev)
         if per_step_flush:
             for _ in range(args.steps):
                 flush.zero_()
                 ev0.record(stream)
-                ctx.run(1, WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+                sums_timed.append(ctx.run(1, WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
+                                          WORKLOAD["comb_every"]))
                 ev1.record(stream)
                 ev1.synchronize()
                 step_ms.append(ev0.elapsed_time(ev1))
             total_ms = sum(step_ms)
         else:
             ev0.record(stream)
-            ctx.run(args.steps, WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+            sums_timed.append(ctx.run(args.steps, WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
+                                      WORKLOAD["comb_every"]))
             ev1.record(stream)
             ev1.synchronize()
             total_ms = ev0.elapsed_time(ev1)
@@ -369,6 +371,17 @@ def run_ours(args):
     if rank != 0:
         return None
     fl = step_flops_per_walker(prob.norb, ncol, prob.naux)
+    # error bar per second (reblocked mixed-energy series of the timed steps, first 20 % dropped):
+    # eta = 1 / (sigma_E^2 t_wall)
+    from paper_2406_16238_b300.analysis import energy_series, error_bar
+    e_timed = energy_series(np.concatenate(sums_timed))
+    e_kept = e_timed[len(e_timed) // 5:]
+    eb = error_bar(e_kept) if len(e_kept) >= 16 else float("nan")
+    eta = {"mean_energy_Ha": float(e_kept.mean()) if len(e_kept) else None,
+           "error_bar_Ha": eb if np.isfinite(eb) else None,
+           "eta_per_Ha2_s": (1.0 / (eb * eb * total_ms / 1e3)) if np.isfinite(eb) and eb > 0 else None,
+           "note": f"{len(e_kept)} of {len(e_timed)} timed steps' energies (first 20 % dropped), "
+                   "Flyvbjerg-Petersen reblocking; t_wall = the timed region"}
     rooflines = stage_rooflines(args.prec, prob.norb, ncol, prob.naux, nw, stages)
     dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_launch"] * rooflines[k]["launches_per_step"])
     roof = dict(rooflines[dominant])
@@ -391,6 +404,7 @@ def run_ours(args):
         "stages_note": f"per-stage CUDA events over {nprof} separately run steps (direct launches); "
                        "value and ms_per_step come from the graph-replayed timed region",
         "step_flops_per_walker": fl,
+        "error_bar_per_second": eta,
         "fp64_form": fp64_form,
         "free_projection": free_proj,
         "clocks": clk.summary(),

@@ -110,7 +110,7 @@ def test_free_projection_rules():
     assert np.all(np.isfinite(e))
 
 
-@pytest.mark.parametrize("prec,nw", [("fp64", 16), ("bf16x3", 24)])
+@pytest.mark.parametrize("prec,nw", [("fp64", 16), ("fp32", 16), ("bf16x3", 24)])
 def test_free_projection_graph_replay_is_bit_identical(prec, nw):
     """afqmc_run in free projection (energy every 2nd step, QR every 5) with and without graphs."""
     prob = PROBLEMS["uhf_N13_3_2"]()
