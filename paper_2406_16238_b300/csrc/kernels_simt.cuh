@@ -1433,7 +1433,8 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
         if ((tid >> 5) == sw) {
           const double d = G[k * n + k].x;
           __syncwarp();   // every lane has read G_kk before lane 0 overwrites it
-          const double r = sqrt(fmax(d, 1e-300)), ri = 1.0 / r;
+          // 1 / R_kk from one reciprocal square root and R_kk = G_kk / R_kk (no division)
+          const double dd = fmax(d, 1e-300), ri = rsqrt(dd), r = dd * ri;
           for (int j = k + 1 + lane; j < n; j += 32) G[k * n + j] = cscale(G[k * n + j], ri);
           if (lane == 0) {
             if (!(d > 0.0) || !isfinite(d)) bad_s = 1;
