@@ -430,9 +430,10 @@ __global__ void __launch_bounds__(128) k_normals(unsigned long long seed, const 
   }
 }
 
-// Fields of one walker per CTA from the normals x[w][g] drawn by k_normals.
+// Fields of one walker per CTA from the normals x[w][g] drawn by k_normals.  Registers held for
+// 5 CTAs per SM: W = 640 walkers in one wave on 148 SMs.
 template <typename R>
-__global__ void __launch_bounds__(256, 2) k_fields(FieldArgs<R> a) {
+__global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
   __shared__ double red[32];
   const int w = blockIdx.x, tid = threadIdx.x;
   // c_mf = i sdt sum lbar_g xs_g; sum (x xbar - xbar^2 / 2) = sum (a x - (a^2 - b^2) / 2) +
