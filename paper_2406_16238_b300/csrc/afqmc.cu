@@ -1050,13 +1050,16 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
   for (size_t i = 0; i < N * nt; ++i)
     if (!std::isfinite(psiT[i])) return fail(AFQMC_EINVAL, "psiT has a non-finite entry");
   for (size_t p = 0; p < N; ++p)
-    for (size_t q = p + 1; q < N; ++q) {
+    for (size_t q = p + 1; q < N; ++q)
       if (std::fabs(h1e[p * N + q] - h1e[q * N + p]) > 1e-12 * std::max(1.0, hmax))
         return fail(AFQMC_EINVAL, "h1e is not symmetric at (%zu, %zu)", p, q);
-      for (size_t g = 0; g < X; ++g)
-        if (std::fabs(chol[g * N * N + p * N + q] - chol[g * N * N + q * N + p]) > 1e-12 * std::max(1.0, lmax))
+  for (size_t g = 0; g < X; ++g) {   // one N x N slab at a time (cache-resident)
+    const double* Lg = chol + g * N * N;
+    for (size_t p = 0; p < N; ++p)
+      for (size_t q = p + 1; q < N; ++q)
+        if (std::fabs(Lg[p * N + q] - Lg[q * N + p]) > 1e-12 * std::max(1.0, lmax))
           return fail(AFQMC_EINVAL, "chol[%zu] is not symmetric at (%zu, %zu)", g, p, q);
-    }
+  }
   afqmc_ctx* c = new afqmc_ctx();
   c->d = d;
   c->L = L;
