@@ -536,6 +536,9 @@ __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long see
     for (int i = threadIdx.x; i < len; i += blockDim.x) ws[i] = w[base + i];
     __syncthreads();
     if (threadIdx.x == 0) {   // eight weights loaded ahead of their additions (the chain of sums stays in order)
+      // "w > 0" as a signed integer compare of the bit patterns (the same answer for every value but
+      // NaN, which makes the total non-finite anyway), which leaves the binary64 pipe to the chain of
+      // additions
       int i = 0;
       for (; i + 8 <= len; i += 8) {
         double v[8];
@@ -545,14 +548,14 @@ __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long see
         for (int u = 0; u < 8; ++u) {
           t = t + v[u];
           ws[i + u] = t;
-          if (v[u] > 0.0) last = base + i + u;
+          if (__double_as_longlong(v[u]) > 0) last = base + i + u;
         }
       }
       for (; i < len; ++i) {
         const double wi = ws[i];
         t = t + wi;
         ws[i] = t;
-        if (wi > 0.0) last = base + i;
+        if (__double_as_longlong(wi) > 0) last = base + i;
       }
     }
     __syncthreads();
@@ -1231,7 +1234,9 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
       }
       if (tid == 0) { prod_s = q; exp_s = e; }
     }
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {   // one rounding of each factor entry to R
+    // one rounding of each factor entry to R, by the warps other than the determinant's
+    for (int idx = tid - 32; idx < n * n; idx += (int)blockDim.x - 32) {
+      if (idx < 0) break;
       const int i = idx / n, j = idx % n;
       F[idx] = from_d2<R>(i == j ? dinv[i] : A[i * lda + j]);
     }
