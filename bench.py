@@ -370,13 +370,7 @@ def run_ours(args):
     ctx2 = pkg.Afqmc(h1e_p, chol_p, prob.ecore, prob.nalpha, prob.nbeta, psiT_p, nwalkers=nw, dt=WORKLOAD["dt"],
                      seed=seed + 1, prec=args.prec, device=dev, stream=stream)
     sums_host = torch.zeros(4 * args.steps, dtype=torch.float64).pin_memory().numpy()
-    for s in range(args.steps):
-        ctx2.local_energy_async(sums_host[4 * s:4 * s + 4])
-        ctx2.propagate(1)
-        if (s + 1) % WORKLOAD["reortho_every"] == 0:
-            ctx2.reortho()
-        if (s + 1) % WORKLOAD["comb_every"] == 0:
-            ctx2.popcontrol()
+    ctx2.run_async(args.steps, sums_host, WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
     ctx2.synchronize(600.0)
     e2e_s = time.perf_counter() - t0
     if not np.all(np.isfinite(sums_host)) or not np.all(sums_host[1::4] > 0):
@@ -431,8 +425,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "e2e": {"value": world * nw * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,
-                "note": "create from pinned host arrays + steps, each step's 4 energy sums copied to pinned host "
-                        "memory (asynchronous, stream-ordered), checked finite after the final synchronisation"},
+                "note": "create from pinned host arrays + afqmc_run_async (graph-replayed steps, each step's 4 "
+                        "energy sums copied to pinned host memory by an asynchronous stream-ordered copy), checked "
+                        "finite after the final synchronisation"},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, seed, args.cpu_budget)

@@ -67,6 +67,7 @@ SIGNATURES = {
     "afqmc_reortho": (_i32, [_vp]),
     "afqmc_popcontrol": (_i32, [_vp]),
     "afqmc_run": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
+    "afqmc_run_async": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
     "afqmc_get_walkers": (_i32, [_vp, _dp, _dp, _dp, ctypes.POINTER(_u64)]),
     "afqmc_set_walkers": (_i32, [_vp, _dp, _dp, _u64]),
     "afqmc_get_fields": (_i32, [_vp, _dp, _dp]),
@@ -203,6 +204,19 @@ class Afqmc:
         _check(self._lib.afqmc_run(self._ctx, int(nsteps), int(energy_every), int(reortho_every), int(comb_every),
                                    _ptr(out), ctypes.byref(nmeas)))
         return out[: nmeas.value]
+
+    def run_async(self, nsteps, out, energy_every=1, reortho_every=5, comb_every=10):
+        """The driver loop without synchronising: measurement k's four sums land in out[4k:4k+4] (a
+        contiguous float64 host array, page-locked for asynchronous copies) once the stream gets there
+        (synchronize()).  Returns the number of measurements."""
+        need = 4 * ((nsteps + energy_every - 1) // energy_every) if energy_every > 0 else 0   # at most
+        if energy_every > 0 and (out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size < need):
+            raise ValueError("out must be a contiguous float64 array with 4 entries per measurement")
+        nmeas = ctypes.c_int32()
+        _check(self._lib.afqmc_run_async(self._ctx, int(nsteps), int(energy_every), int(reortho_every),
+                                         int(comb_every), _ptr(out) if energy_every > 0 else None,
+                                         ctypes.byref(nmeas)))
+        return nmeas.value
 
     # --- state --------------------------------------------------------------------------
     def get_walkers(self):

@@ -1208,6 +1208,45 @@ afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int
   return read_status(ctx);
 }
 
+afqmc_status afqmc_run_async(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
+                             int32_t comb_every, double* energies_host, int32_t* nmeas) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
+  if (ctx->free_proj && comb_every > 0) return fail(AFQMC_EINVAL, "free projection: comb_every must be <= 0");
+  if (energy_every > 0 && !energies_host) return fail(AFQMC_EINVAL, "afqmc_run_async: energies_host is NULL");
+  int used = 0, total = 0;
+  double* hist = ctx->at<double>(ctx->L.hist);
+  const bool graphs = ctx->graphs_on && !ctx->prof;
+  if (graphs) CU(cudaMemsetAsync(ctx->base + ctx->L.slot, 0, sizeof(int), ctx->stream));
+  for (int s = 0; s < nsteps; ++s) {
+    const bool energy = energy_every > 0 && ctx->host_step % (unsigned long long)energy_every == 0;
+    if (energy && used == kHistory - 1) {   // the device history wraps; earlier copies are ordered before
+      used = 0;
+      if (graphs) CU(cudaMemsetAsync(ctx->base + ctx->L.slot, 0, sizeof(int), ctx->stream));
+    }
+    if (graphs) {
+      if ((st = graph_step(ctx, energy)) != AFQMC_OK) return st;
+      if (energy)   // after the step graph, which joins the estimator's branch
+        CU(cudaMemcpyAsync(energies_host + 4 * (size_t)total, hist + 4 * used, 4 * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+      if (energy &&
+          (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true, energies_host + 4 * (size_t)total)) !=
+              AFQMC_OK)
+        return st;
+      if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
+    }
+    if (energy) { ++used; ++total; }
+    if (reortho_every > 0 && ctx->host_step % (unsigned long long)reortho_every == 0)
+      if ((st = graphs ? graph_qr(ctx) : DISPATCH(ctx, qr_impl)) != AFQMC_OK) return st;
+    if (comb_every > 0 && ctx->host_step % (unsigned long long)comb_every == 0)
+      if ((st = graphs ? graph_comb(ctx) : DISPATCH(ctx, comb_impl)) != AFQMC_OK) return st;
+  }
+  if (nmeas) *nmeas = total;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_get_walkers(afqmc_ctx* ctx, double* psi, double* logO, double* w, uint64_t* step) {
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;

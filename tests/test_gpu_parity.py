@@ -431,3 +431,29 @@ def test_async_energies_beside_steps_match_the_driver_loop():
     ctx.synchronize(60.0)
     ctx.close()
     assert np.array_equal(out.reshape(6, 4), np.asarray(ref).reshape(6, 4))
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_run_async_matches_run(graphs):
+    """afqmc_run_async (no synchronisation, per-measurement asynchronous copies) gives the sums and walkers
+    of afqmc_run bit for bit, with and without graph replay."""
+    import torch
+    prob = PROBLEMS["uhf_N13_3_2"]()
+    out = {}
+    for mode in ("sync", "async"):
+        ctx = _ctx(prob, 24, prec="bf16x3", seed=5)
+        ctx.set_graphs(graphs)
+        if mode == "sync":
+            e = ctx.run(23, energy_every=2, reortho_every=5, comb_every=10)
+        else:
+            buf = torch.full((4 * 12,), float("nan"), dtype=torch.float64).pin_memory().numpy()
+            n = ctx.run_async(23, buf, energy_every=2, reortho_every=5, comb_every=10)
+            assert n == 12
+            ctx.synchronize()
+            e = buf[:4 * n].reshape(n, 4).copy()
+        psi, _, w, step = ctx.get_walkers()
+        out[mode] = (e, psi, w, step)
+        ctx.close()
+    assert out["sync"][0].shape == (12, 4)
+    for a, b in zip(out["sync"], out["async"]):
+        assert np.array_equal(a, b)
