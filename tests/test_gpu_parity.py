@@ -457,3 +457,21 @@ def test_run_async_matches_run(graphs):
     assert out["sync"][0].shape == (12, 4)
     for a, b in zip(out["sync"], out["async"]):
         assert np.array_equal(a, b)
+
+
+def test_run_async_across_the_history_wrap():
+    """More measurements than the device history holds (4096 slots): afqmc_run_async wraps it without
+    synchronising and still matches afqmc_run, which flushes."""
+    import torch
+    prob = PROBLEMS["rhf_N8"]()
+    nsteps = 4200
+    ctx = _ctx(prob, 16, seed=8)
+    e_sync = ctx.run(nsteps, energy_every=1, reortho_every=5, comb_every=10)
+    ctx.close()
+    ctx = _ctx(prob, 16, seed=8)
+    buf = torch.full((4 * nsteps,), float("nan"), dtype=torch.float64).pin_memory().numpy()
+    n = ctx.run_async(nsteps, buf, energy_every=1, reortho_every=5, comb_every=10)
+    ctx.synchronize()
+    ctx.close()
+    assert n == nsteps == e_sync.shape[0]
+    assert np.array_equal(buf.reshape(nsteps, 4), e_sync)
