@@ -475,3 +475,33 @@ def test_run_async_across_the_history_wrap():
     ctx.close()
     assert n == nsteps == e_sync.shape[0]
     assert np.array_equal(buf.reshape(nsteps, 4), e_sync)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_largest_occupation(prec):
+    """The largest spin blocks the library takes (64 + 64 electrons, N = 80; the LU beyond the one-warp
+    pivot step, the streamed exchange, propagation in column chunks, QR with n = 64): per-walker local
+    energies, then one step and a QR, against the oracle at the form's precision.  (The FP64 form's
+    CUDA-core exchange stages a whole walker block in shared memory and does not take blocks this big.)"""
+    prob = make_problem(80, 64, 64, 40, 8.0, 53, unrestricted=True)
+    st = _setup(prob)
+    nw, seed = 5, 21
+    ctx = _ctx(prob, nw, prec=prec, seed=seed)
+    psi, w = _random_state(prob, nw, seed=12, spread=0.1)
+    ctx.set_walkers(psi, w, 3)
+    _, eloc = ctx.local_energy(per_walker=True)
+    for i in range(nw):
+        _, th_a, th_b = orc.overlap_theta(st, psi[i])
+        e = orc.local_energy(st, th_a, th_b)
+        lim = (1e-5 if prec == "fp32" else TC_REL_TOL[prec]) * (1.0 + abs(e[2])) + 1e-6 * abs(e[1])
+        assert abs(eloc[i, 0] - e[0]) < lim, (i, eloc[i, 0], e[0])
+    ctx.propagate(1)
+    ctx.reortho()
+    psi_g, logo_g, w_g, step = ctx.get_walkers()
+    wk = orc.Walkers(psi.copy(), np.array([orc.overlap_theta(st, p)[0] for p in psi]), w.copy(), 3)
+    orc.phaseless_step(st, wk, seed, st.evar)
+    orc.reorthogonalise(st, wk)
+    assert step == 4
+    assert np.allclose(psi_g, wk.psi, rtol=0, atol=1e-4)
+    assert np.allclose(w_g, wk.w, rtol=1e-3, atol=0)
+    assert np.allclose(logo_g.real, wk.logo.real, rtol=0, atol=1e-3)
