@@ -505,3 +505,20 @@ def test_largest_occupation(prec):
     assert np.allclose(psi_g, wk.psi, rtol=0, atol=1e-4)
     assert np.allclose(w_g, wk.w, rtol=1e-3, atol=0)
     assert np.allclose(logo_g.real, wk.logo.real, rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("naux", [1, 2])
+def test_fewest_cholesky_vectors(prec, naux):
+    """Degenerate factorisations with one or two Cholesky vectors: three steps (QR after the second)
+    with the energy measured before each, against the oracle's loop on identical fields."""
+    prob = make_problem(6, 2, 2, naux, 2.0, 61 + naux, unrestricted=True)
+    nw, seed = 7, 44
+    st = _setup(prob)
+    ctx = _ctx(prob, nw, prec=prec, seed=seed)
+    e = ctx.run(3, energy_every=1, reortho_every=2, comb_every=0)
+    ref, _ = orc.run_phaseless(st, prob.psiT, nw, 3, seed, reortho_every=2, comb_every=0, energy_every=1)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert e.shape == ref.shape
+    assert np.allclose(e[:, 0] / e[:, 1], ref[:, 0] / ref[:, 1], rtol=0, atol=tol * max(1.0, abs(st.evar)))
+    assert np.allclose(e[:, 1], ref[:, 1], rtol=tol, atol=0)
