@@ -62,8 +62,9 @@ typedef enum {
  * FP64: walkers complex128, every product and sum in binary64.
  * FP32: walkers complex64, contractions in binary32 (CUDA cores).
  * BF16: walkers complex64, contractions on the tcgen05 tensor cores with bf16
- *       operands (L scaled per gamma by s_gamma = max|L^gamma|) and fp32
- *       accumulation.
+ *       operands and fp32 accumulation.  L is rounded to bf16 unscaled: bf16
+ *       has the exponent range of fp32, so a per-gamma scale would change no
+ *       rounding except in the subnormal range.
  * BF16X3: as BF16, but each fp32 operand is split into bf16 hi + lo parts and
  *       the products hi*hi + hi*lo + lo*hi are accumulated in fp32.
  * In every form the n x n overlap inverses and log-determinants, the phases
@@ -305,23 +306,30 @@ const char* afqmc_last_error(void);
  * callers in latency-critical loops that must not trigger the implicit
  * device-wide synchronisation of cudaMalloc/cudaFree.  It needs no context and
  * no workspace.
- *   w       device, [nwalkers] binary64 walker weights (input)
+ *   w       device, [nwalkers] binary64 walker weights, each finite and >= 0 (input)
  *   src     device, [nwalkers] int32: source walker of every new slot (output)
  *   neww    device, one binary64: the common new weight W_tot / nwalkers, or
- *           -1 if no weight is positive (src is then the identity) (output)
+ *           -1 if the weight total W_tot is not positive and finite (every
+ *           weight zero, or a NaN / Inf weight); src is then the identity
+ *           (output).  neww is the only signal: the call itself returns
+ *           without waiting for the kernel.
  * xi comes from Philox stream 1 at counter `step`, exactly as in
  * afqmc_popcontrol, so src and neww equal what afqmc_popcontrol applies.
  * Scratch: the prefix sums live in a file-scope device array of
  * AFQMC_NOALLOC_MAX_WALKERS + 64 eight-byte words (about 513 KiB) that every
  * GPU which loads the library holds until the process exits; nwalkers above
- * AFQMC_NOALLOC_MAX_WALKERS is rejected with AFQMC_EINVAL.  The first call on
- * a device looks the array's address up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every
- * call shares the one array and overwrites it: calls whose kernels can overlap
- * on the GPU (other streams, other host threads) race and may return wrong
- * plans, so order them on one stream.  Enqueued on `stream` (NULL: default
- * stream); returns without synchronising.  No cudaMalloc, cudaFree or
- * allocating library routine is called. */
+ * AFQMC_NOALLOC_MAX_WALKERS is rejected with AFQMC_EINVAL.  Set-up: the first
+ * call on a device (and the first after that device's context was destroyed
+ * and created again) looks the array's address up (cudaGetSymbolAddress) with
+ * that device current.  That first lookup may itself create the CUDA context
+ * and load the library's device code (lazy module loading), which reserves
+ * device memory and may synchronise; so make the first call outside any
+ * latency-critical loop and before any stream capture.  Later calls only
+ * enqueue.  Every call shares the one array and overwrites it: calls whose
+ * kernels can overlap on the GPU (other streams, other host threads) race and
+ * may return wrong plans, so order them on one stream.  Enqueued on `stream`
+ * (NULL: default stream); returns without synchronising.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
 #define AFQMC_NOALLOC_MAX_WALKERS 65536
 afqmc_status afqmc_comb_plan_noalloc(const double* w, int32_t nwalkers, uint64_t seed, uint64_t step,
                                      int32_t* src, double* neww, void* stream);

@@ -366,14 +366,34 @@ def comb_plan_noalloc(w, seed, step, src, neww, stream=None):
 
     For callers that cannot allocate device memory: the library uses a static
     device array for its scratch and allocates nothing; the caller owns every
-    buffer passed here.  Enqueued on `stream` (default: the current stream).
+    buffer passed here.  The three tensors must be contiguous and on one CUDA
+    device (ValueError otherwise); the call is made with that device current.
+    Enqueued on `stream` (default: that device's current stream).  neww = -1
+    reports a weight total that is not positive and finite (src is then the
+    identity).
     """
     import torch
     lib = load()
-    s = stream if stream is not None else torch.cuda.current_stream(w.device)
-    _check(lib.afqmc_comb_plan_noalloc(ctypes.c_void_p(w.data_ptr()), int(w.numel()), int(seed) & (2 ** 64 - 1),
-                                       int(step), ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(neww.data_ptr()),
-                                       ctypes.c_void_p(s.cuda_stream)))
+    for name, t, dt in (("w", w, torch.float64), ("src", src, torch.int32), ("neww", neww, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt} (got {t.dtype})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device != w.device:
+            raise ValueError(f"{name} is on {t.device}, w on {w.device}: all three must share one device")
+    if w.numel() < 1 or w.numel() > NOALLOC_MAX_WALKERS:
+        raise ValueError(f"w must hold 1 to {NOALLOC_MAX_WALKERS} weights (got {w.numel()})")
+    if src.numel() < w.numel():
+        raise ValueError(f"src holds {src.numel()} entries, fewer than the {w.numel()} weights")
+    if neww.numel() < 1:
+        raise ValueError("neww must hold one entry")
+    with torch.cuda.device(w.device):
+        s = stream if stream is not None else torch.cuda.current_stream(w.device)
+        _check(lib.afqmc_comb_plan_noalloc(ctypes.c_void_p(w.data_ptr()), int(w.numel()), int(seed) & (2 ** 64 - 1),
+                                           int(step), ctypes.c_void_p(src.data_ptr()),
+                                           ctypes.c_void_p(neww.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
 
 
 class Batch:

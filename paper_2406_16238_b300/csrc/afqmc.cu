@@ -15,6 +15,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+
 #include "afqmc.h"
 #include "kernels_simt.cuh"
 #include "cv_kernels.cuh"
@@ -1652,15 +1654,51 @@ afqmc_status afqmc_synchronize(afqmc_ctx* ctx, double timeout_s) {
 // Comb plan without allocation (afqmc_comb_plan_noalloc).  The prefix-sum scratch of
 // k_comb_plan lives in this file-scope device array instead of a workspace: words
 // [0, AFQMC_NOALLOC_MAX_WALKERS) hold the prefix sums, the tail holds the step counter
-// and the status word.  Host code never dereferences the symbol: it looks up the
-// array's device address once per device and passes that pointer to the kernels.
+// and the kernel's status word (internal: the caller's signal is neww).  Host code never
+// dereferences the symbol: it looks up the array's device address once per device and
+// context and passes that pointer to the kernels.
 namespace {
 
 static __device__ __align__(256) unsigned long long g_comb_scratch[AFQMC_NOALLOC_MAX_WALKERS + 64];
 
 constexpr int kMaxDevices = 256;
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;   // unique id of the CUDA context the address belongs to (0: none)
+  void* ptr = nullptr;
+};
 std::mutex g_comb_scratch_mu;
-void* g_comb_scratch_addr[kMaxDevices] = {};
+ScratchAddr g_comb_scratch_addr[kMaxDevices];
+
+typedef CUresult (*PFN_ctx_current)(CUcontext*);
+typedef CUresult (*PFN_ctx_id)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context (0 when there is none).  A context
+// that is destroyed and created again (cudaDeviceReset) gets a new id, so a cached symbol
+// address is looked up again instead of being reused.  The driver functions come through the
+// runtime's entry-point query, so the library does not link the driver library itself.
+cudaError_t current_context_id(unsigned long long* id) {
+  static PFN_ctx_current get_current = nullptr;
+  static PFN_ctx_id get_id = nullptr;
+  *id = 0;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess) return e;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorSymbolNotFound;
+    get_current = reinterpret_cast<PFN_ctx_current>(f1);
+    get_id = reinterpret_cast<PFN_ctx_id>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+  if (!ctx) return cudaSuccess;
+  if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+  return cudaSuccess;
+}
 
 __global__ void k_store_step(unsigned long long* dst, unsigned long long v) { *dst = v; }
 
@@ -1678,14 +1716,24 @@ extern "C" afqmc_status afqmc_comb_plan_noalloc(const double* w, int32_t nwalker
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_comb_scratch_mu);
-    if (!g_comb_scratch_addr[dev]) {
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess)
+      return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc: current context: %s", cudaGetErrorString(e));
+    ScratchAddr& slot = g_comb_scratch_addr[dev];
+    if (id == 0 || slot.ptr == nullptr || slot.ctx_id != id) {
+      // set-up for this device and context: the array's device address (the first lookup in a
+      // process may create the context and load the module)
       void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_comb_scratch);
+      e = cudaGetSymbolAddress(&p, g_comb_scratch);
       if (e != cudaSuccess || !p)
         return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      g_comb_scratch_addr[dev] = p;
+      if (id == 0 && (e = current_context_id(&id)) != cudaSuccess)
+        return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc: current context: %s", cudaGetErrorString(e));
+      slot.ctx_id = id;
+      slot.ptr = p;
     }
-    base = g_comb_scratch_addr[dev];
+    base = slot.ptr;
   }
   unsigned long long* words = static_cast<unsigned long long*>(base);
   double* cum = reinterpret_cast<double*>(words);

@@ -98,3 +98,13 @@ def test_null_context_is_rejected():
     assert lib.afqmc_propagate(None, 1) == 1
     assert lib.afqmc_reortho(None) == 1
     assert lib.afqmc_launch_count(None) == 0
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_any_call():
+    """The allocation-free comb plan's binding checks dtype, device, contiguity and sizes itself."""
+    import torch
+    w = torch.ones(4, dtype=torch.float64)
+    src = torch.zeros(4, dtype=torch.int32)
+    neww = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        pkg._lib.comb_plan_noalloc(w, 1, 0, src, neww)

@@ -72,3 +72,26 @@ def test_noalloc_comb_plan_rejects_oversized_batches():
     st = lib.afqmc_comb_plan_noalloc(ctypes.c_void_p(w.data_ptr()), _lib.NOALLOC_MAX_WALKERS + 1, 1, 0,
                                      ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(w.data_ptr()), None)
     assert st == 1 and "outside" in lib.afqmc_last_error().decode()
+
+
+@pytest.mark.parametrize("nw", [4097, _lib.NOALLOC_MAX_WALKERS])
+def test_noalloc_comb_plan_large_batches_match_the_oracle(nw):
+    """Batches beyond one shared-memory tile of the kernel (2048 weights), whose prefix sums are written to
+    and searched in the static array, up to its last prefix word: src and the new weight bit for bit
+    against the oracle's comb (binary64 prefix in index order, the same Philox xi), with zero weights."""
+    import torch
+    from oracle import afqmc as orc
+    from oracle import philox
+    rng = np.random.default_rng(nw)
+    seed, step = 99, 1234
+    w = rng.exponential(size=nw)
+    w[rng.choice(nw, size=nw // 7, replace=False)] = 0.0
+    w[-1] = 0.0
+    ref_src, ref_w = orc.comb_assignment(w, philox.comb_uniform(seed, step))
+    src = torch.full((nw,), -1, dtype=torch.int32, device="cuda")
+    neww = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):   # two calls in a row share the array
+        pkg._lib.comb_plan_noalloc(torch.tensor(w, dtype=torch.float64, device="cuda"), seed, step, src, neww)
+        torch.cuda.synchronize()
+        assert np.array_equal(src.cpu().numpy().astype(np.int64), ref_src)
+        assert float(neww.item()) == ref_w
