@@ -74,58 +74,185 @@ def step_flops_per_walker(norb, ncol, naux, taylor=6):
     return dict(exchange=exch, vhs=vhs, propagate=prop, overlap=ovl, total=exch + vhs + prop + ovl)
 
 
+class _CtypesNvml:
+    """The few NVML calls the clock sampler makes, through ctypes on the driver's libnvidia-ml (for
+    images without the pynvml module).  Names and return values follow pynvml's."""
+
+    NVML_CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} failed ({rc})")
+
+    def nvmlInit(self):
+        self._ok(self.lib.nvmlInit_v2(), "nvmlInit_v2")
+
+    def nvmlDeviceGetHandleByPciBusId(self, bus):
+        h = self.ct.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByPciBusId_v2(self.ct.c_char_p(bus), self.ct.byref(h)),
+                 "nvmlDeviceGetHandleByPciBusId_v2")
+        return h
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.ct.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(i), self.ct.byref(h)),
+                 "nvmlDeviceGetHandleByIndex_v2")
+        return h
+
+    def _uint(self, fn, *args):
+        v = self.ct.c_uint()
+        self._ok(getattr(self.lib, fn)(*args, self.ct.byref(v)), fn)
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, clk):
+        return self._uint("nvmlDeviceGetClockInfo", h, self.ct.c_int(clk))
+
+    def nvmlDeviceGetMaxClockInfo(self, h, clk):
+        return self._uint("nvmlDeviceGetMaxClockInfo", h, self.ct.c_int(clk))
+
+    def nvmlDeviceGetPowerUsage(self, h):
+        return self._uint("nvmlDeviceGetPowerUsage", h)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.ct.c_ulonglong()
+        self._ok(self.lib.nvmlDeviceGetCurrentClocksThrottleReasons(h, self.ct.byref(v)),
+                 "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return v.value
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """SM clock, its maximum, power and clock-event (throttle) reasons, polled through NVML every
+    ~2 ms in a background thread (nvidia-smi's 200 ms loop sees nothing of a 10 ms timed region).
+    mark_start()/mark_end() bracket the timed region; summary() reports the samples inside it (and,
+    separately, every sample of the run).  Falls back to nvidia-smi when NVML is unavailable."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.lines = []
+    def __init__(self, device):
+        self.device = device
+        self.samples = []          # (t, sm_mhz, max_mhz, power_w, reasons bitmask)
+        self.t0 = self.t1 = None
+        self._stop = threading.Event()
+        self.thread = None
+        self.nvml = None
+
+    def _handle(self):
+        try:
+            import pynvml
+        except ImportError:
+            pynvml = _CtypesNvml()
+        import torch
+        pynvml.nvmlInit()
+        self.nvml = pynvml
+        try:
+            props = torch.cuda.get_device_properties(self.device)
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+            return pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(self.device.index or 0)
+
+    def _poll(self, h):
+        nv = self.nvml
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while not self._stop.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                pw = nv.nvmlDeviceGetPowerUsage(h) / 1000.0
+                self.samples.append((time.perf_counter(), float(sm), float(mx), pw, int(rs)))
+            except Exception:
+                break
+            time.sleep(0.002)
+
+    SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_power_cap")
+
+    def _smi(self):
+        """Fallback: nvidia-smi's own loop at 10 ms, each line stamped on arrival."""
+        import torch
+        bits = [self.REASONS[k] for k in ("hw_slowdown", "sw_thermal_slowdown", "hw_thermal_slowdown",
+                                          "sw_power_cap")]
+        try:
+            props = torch.cuda.get_device_properties(self.device)
+            sel = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+        except Exception:   # noqa: BLE001
+            sel = str(self.device.index or 0)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", sel, f"--query-gpu={self.SMI_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError as e:
+            self.error = (self.error or "") + f"; nvidia-smi: {e}"
+            return
+        for ln in self.proc.stdout:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rs = sum(b for b, v in zip(bits, parts[3:7]) if v.lower() == "active")
+                self.samples.append((time.perf_counter(), float(parts[0]), float(parts[1]), float(parts[2]), rs))
+            except ValueError:
+                continue
+            if self._stop.is_set():
+                break
 
     def __enter__(self):
+        self.error = None
+        self.proc = None
+        self.mode = "NVML, polled every ~2 ms"
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except (OSError, FileNotFoundError):
-            self.proc = None
+            h = self._handle()
+            self.thread = threading.Thread(target=self._poll, args=(h,), daemon=True)
+        except Exception as e:   # noqa: BLE001  (reported in the summary)
+            self.error = f"NVML: {type(e).__name__}: {e}"
+            self.mode = "nvidia-smi -lms 10"
+            self.thread = threading.Thread(target=self._smi, daemon=True)
+        self.thread.start()
         return self
 
-    def _read(self):
-        for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def __exit__(self, *a):
+        self._stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    @staticmethod
+    def _summarise(rows):
+        sm = [r[1] for r in rows]
+        reasons = set()
+        for r in rows:
+            for nm, bit in ClockSampler.REASONS.items():
+                if r[4] & bit:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": rows[-1][2] if rows else None,
+                "power_w_max": max(r[3] for r in rows) if rows else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        rows = self.samples
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        out = self._summarise(inside)
+        out["source"] = self.mode + " during the timed region" + (f" ({self.error})" if self.error else "")
+        out["whole_run"] = self._summarise(rows)
+        return out
 
 
 def measured_peaks():
@@ -179,8 +306,10 @@ def stage_rooflines(prec, norb, ncol, naux, nw, stages, fp64_peak=None):
     """Algorithmic work per launch of the main stages against the peak of the unit that bounds them."""
     peaks, src = measured_peaks()
     tensor = prec in ("bf16", "bf16x3")
-    tpeak = peaks["bf16_tflops_sustained"] * (1.0 if prec == "bf16" else 1.0 / 3.0)
-    tnote = f"bf16 sustained ({src})" + ("" if prec == "bf16" else " / 3 products")
+    # the stage times come from a short pass (~20 steps, ~10 ms of GPU time) of direct launches: the
+    # burst bf16 rate is the matching peak (the sustained one applies to a seconds-long loop)
+    tpeak = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else 1.0 / 3.0)
+    tnote = f"bf16 burst ({src})" + ("" if prec == "bf16" else " / 3 products")
     alu = (fp64_peak or FP64_PEAK_TFLOPS) if prec == "fp64" else FP32_PEAK_TFLOPS
     anote = (("binary64 rate measured on this GPU (cuBLAS DGEMM 4096^3)" if fp64_peak else "nominal FP64 (recipe table)")
              if prec == "fp64" else "FP32 CUDA cores: 148 SM x 128 x 2 x 2.032 GHz")
@@ -275,6 +404,7 @@ def run_ours(args):
     info = ctx.info()
     ncol = prob.nalpha if info["restricted"] else prob.nalpha + prob.nbeta
     ws_bytes = info["workspace_bytes"]
+    clk = ClockSampler(dev).__enter__()
     ctx.run(args.warmup, WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
     torch.cuda.synchronize(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -284,26 +414,27 @@ def run_ours(args):
     l0 = ctx.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, sums_timed = [], []
-    with ClockSampler(dev.index) as clk:
-        torch.cuda.synchronize(dev)
-        if per_step_flush:
-            for _ in range(args.steps):
-                flush.zero_()
-                ev0.record(stream)
-                sums_timed.append(ctx.run(1, WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
-                                          WORKLOAD["comb_every"]))
-                ev1.record(stream)
-                ev1.synchronize()
-                step_ms.append(ev0.elapsed_time(ev1))
-            total_ms = sum(step_ms)
-        else:
+    torch.cuda.synchronize(dev)
+    clk.mark_start()
+    if per_step_flush:
+        for _ in range(args.steps):
+            flush.zero_()
             ev0.record(stream)
-            sums_timed.append(ctx.run(args.steps, WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
+            sums_timed.append(ctx.run(1, WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
                                       WORKLOAD["comb_every"]))
             ev1.record(stream)
             ev1.synchronize()
-            total_ms = ev0.elapsed_time(ev1)
-        torch.cuda.synchronize(dev)
+            step_ms.append(ev0.elapsed_time(ev1))
+        total_ms = sum(step_ms)
+    else:
+        ev0.record(stream)
+        sums_timed.append(ctx.run(args.steps, WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
+                                  WORKLOAD["comb_every"]))
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms = ev0.elapsed_time(ev1)
+    torch.cuda.synchronize(dev)
+    clk.mark_end()
     launches = ctx.launch_count() - l0
     # stage times from a separate pass with per-stage events (direct launches, no graph replay)
     nprof = min(args.steps, 20)
@@ -320,6 +451,7 @@ def run_ours(args):
     value = world * nw * args.steps / (total_ms / 1e3)
 
     if args.skip_extras:
+        clk.__exit__(None, None, None)
         ctx.close()
         return None if rank != 0 else {"value": value, "ms_per_step": total_ms / args.steps,
                                        "stages_ms_per_step": {k: v[0] / nprof for k, v in stages.items()
@@ -369,13 +501,25 @@ def run_ours(args):
     t0 = time.perf_counter()
     ctx2 = pkg.Afqmc(h1e_p, chol_p, prob.ecore, prob.nalpha, prob.nbeta, psiT_p, nwalkers=nw, dt=WORKLOAD["dt"],
                      seed=seed + 1, prec=args.prec, device=dev, stream=stream)
+    t1 = time.perf_counter()
     sums_host = torch.zeros(4 * args.steps, dtype=torch.float64).pin_memory().numpy()
-    ctx2.run_async(args.steps, sums_host, WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+    # first step alone (captures the step graphs on first use), then the remaining steps
+    ctx2.run_async(1, sums_host[:4], WORKLOAD["energy_every"], WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
     ctx2.synchronize(600.0)
-    e2e_s = time.perf_counter() - t0
+    t2 = time.perf_counter()
+    if args.steps > 1:
+        ctx2.run_async(args.steps - 1, sums_host[4:], WORKLOAD["energy_every"], WORKLOAD["reortho_every"],
+                       WORKLOAD["comb_every"])
+    ctx2.synchronize(600.0)
+    t3 = time.perf_counter()
+    e2e_s = t3 - t0
+    e2e_split = {"create_ms": 1e3 * (t1 - t0), "first_step_ms": 1e3 * (t2 - t1),
+                 "steady_value": (world * nw * (args.steps - 1) / (t3 - t2)) if args.steps > 1 else None}
     if not np.all(np.isfinite(sums_host)) or not np.all(sums_host[1::4] > 0):
         raise RuntimeError("end-to-end run: non-finite energy sums or a zero weight total")
     ctx2.close()
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
     h2d = prob.h1e.nbytes + prob.chol.nbytes + prob.psiT.nbytes
     if world > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
@@ -421,16 +565,22 @@ def run_ours(args):
         "error_bar_per_second": eta,
         "fp64_form": fp64_form,
         "free_projection": free_proj,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "gpu_launches": int(launches),
         "e2e": {"value": world * nw * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 32,
-                "note": "create from pinned host arrays + afqmc_run_async (graph-replayed steps, each step's 4 "
-                        "energy sums copied to pinned host memory by an asynchronous stream-ordered copy), checked "
-                        "finite after the final synchronisation"},
+                "create_ms": e2e_split["create_ms"], "first_step_ms": e2e_split["first_step_ms"],
+                "steady_value": e2e_split["steady_value"],
+                "note": "create from pinned host arrays (workspace allocation, H2D of h1e, L and psiT, device "
+                        "set-up) + afqmc_run_async (graph-replayed steps, the step graphs captured during the first "
+                        "step, each step's 4 energy sums copied to pinned host memory by an asynchronous "
+                        "stream-ordered copy), checked finite after the final synchronisation; steady_value = the "
+                        "steps after the first, from the host's clock"},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, seed, args.cpu_budget)
+    if not args.no_large and world == 1:
+        line["large_system"] = run_large(args, dev, stream)
     return line
 
 
@@ -457,11 +607,14 @@ def run_batched(args):
     torch.cuda.synchronize(dev)
     l0 = sum(c.launch_count() for c in ctxs)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    with ClockSampler(dev) as clk:
+        torch.cuda.synchronize(dev)
+        clk.mark_start()
         ev0.record(stream)
         e = b.run(args.steps, 1, 5, 10)
         ev1.record(stream)
         ev1.synchronize()
+        clk.mark_end()
     ms = ev0.elapsed_time(ev1)
     launches = sum(c.launch_count() for c in ctxs) - l0
     total_ws = len(ctxs) * 256 * args.steps
@@ -519,6 +672,86 @@ def run_cv(args):
                        "epochs": args.cv_epochs, "final_loss": float(losses[-1]) if len(losses) else None,
                        "collect_and_train_s": t_train},
             "forms": out}
+
+
+def large_rooflines(prec, norb, nblocks, nocc, naux, nw, stages):
+    """Rooflines of the large system's stages: the exchange and the propagation against the tensor
+    peak, the VHS build against HBM bandwidth (its bytes are L's bf16 copy, read once per step)."""
+    peaks, src = measured_peaks()
+    tpeak = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else 1.0 / 3.0)
+    tnote = f"bf16 burst ({src})" + ("" if prec == "bf16" else " / 3 products")
+    parts = 1 if prec == "bf16" else 2
+    kx = (naux + 63) // 64 * 64
+    ncol = nblocks * nocc
+    exch = nblocks * exchange_flops_per_walker(norb, nocc, naux) * nw
+    prop = (2 * (2 * 2 * norb * norb * ncol) + 6 * 8 * norb * norb * ncol) * nw
+    vhs_bytes = parts * norb * norb * kx * 2 + nw * 2 * parts * kx * 2 + nw * 4 * norb * norb * 2
+    work = {"exchange": (exch, "tensor", tpeak, "TFLOP/s", 1e12, tnote),
+            "propagate": (prop, "tensor", tpeak, "TFLOP/s", 1e12, tnote),
+            "vhs": (vhs_bytes, "hbm", peaks["hbm_gbs"], "GB/s", 1e9,
+                    f"HBM copy bandwidth ({src}); bytes = L^T bf16 {'hi + lo' if parts == 2 else 'hi'} read once, "
+                    "coefficients, V planes written")}
+    out = {}
+    for k, (amount, bound, peak, unit, scale, note) in work.items():
+        ms, cnt = stages.get(k, (0.0, 0))
+        if not cnt:
+            continue
+        per = ms / cnt
+        ach = amount / (per / 1e3) / scale
+        out[k] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                  "peak_source": note, ("algorithmic_flops_per_launch" if bound == "tensor" else
+                                        "algorithmic_bytes_per_launch"): amount,
+                  "ms_per_launch": per, "traffic": None}
+    return out
+
+
+def run_large(args, dev=None, stream=None, steps=10, warmup=2):
+    """The large system: N=1512, 42a+42b, naux=7560, UHF trial, 128 walkers; L drawn on the GPU in
+    binary32 chunks of 120 vectors and passed through the chunked set-up (never on the host)."""
+    import torch
+    import paper_2406_16238_b300 as pkg
+    from synthetic_inputs import config_large
+    dev = dev or torch.device("cuda", 0)
+    stream = stream or torch.cuda.current_stream(dev)
+    prob = config_large()
+    nw = 128
+    prec = "bf16" if args.prec == "bf16" else "bf16x3"
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ctx = pkg.Afqmc(prob.h1e, prob.chunks(120, device=dev), prob.ecore, prob.nalpha, prob.nbeta, prob.psiT,
+                    nwalkers=nw, dt=WORKLOAD["dt"], seed=240616241, prec=prec, naux=prob.naux, device=dev,
+                    stream=stream)
+    create_s = time.perf_counter() - t0
+    ws = ctx.info()["workspace_bytes"]
+    ctx.run(warmup, 1, WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count()
+    ev0.record(stream)
+    e = ctx.run(steps, 1, WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - l0
+    if not np.all(np.isfinite(e)):
+        raise RuntimeError("large system: non-finite estimator sums")
+    ctx.profile(True)
+    ctx.run(3, 1, WORKLOAD["reortho_every"], WORKLOAD["comb_every"])
+    torch.cuda.synchronize(dev)
+    stages = ctx.stage_times()
+    ctx.profile(False)
+    ctx.close()
+    del ctx
+    roof = large_rooflines(prec, prob.norb, 2, prob.nalpha, prob.naux, nw, stages)
+    return {"value": nw * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "form": prec, "dtype": DTYPE[prec], "gpu_launches": int(launches),
+            "workload": "large single system N=1512 42a+42b naux=7560 (tau=756) UHF W=128 dt=0.005 (E every "
+                        "step, QR/5, comb/10); L drawn on the GPU, binary32 chunks",
+            "create_s": create_s, "workspace_GiB": ws / 2 ** 30,
+            "l2": "inputs larger than L2 (L^T bf16 copy of tens of GB)",
+            "mean_energy_Ha": float(np.mean(e[:, 0] / e[:, 1])),
+            "stages_ms_per_step": {k: v[0] / 3 for k, v in stages.items()},
+            "rooflines": roof}
 
 
 REF_BUDGET_S = 150.0
@@ -579,7 +812,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-walkers", type=int, default=8)
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "cv"])
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "cv", "large"])
+    ap.add_argument("--no-large", action="store_true", help="leave the large-system measurement out of the line")
     ap.add_argument("--nsys", type=int, default=32)
     ap.add_argument("--cv-pairs", type=int, default=100000)
     ap.add_argument("--cv-epochs", type=int, default=30)
@@ -587,7 +821,8 @@ def main():
                     help="time the steps only (no accuracy check, e2e or CPU baseline), e.g. under ncu")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 2000 if args.workload == "medium" and args.impl == "ours" else 50
+        args.steps = (2000 if args.workload == "medium" and args.impl == "ours" else
+                      10 if args.workload == "large" else 50)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -596,6 +831,15 @@ def main():
         line = run_batched(args)
     elif args.workload == "cv":
         line = run_cv(args)
+    elif args.workload == "large":
+        r = run_large(args, steps=args.steps, warmup=args.warmup)
+        roof = max(r["rooflines"].values(), key=lambda v: v["ms_per_launch"]) if r["rooflines"] else None
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+                "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic",
+                "config": {"workload": r["workload"], "form": r["form"], "l2": r["l2"]},
+                "roofline": roof, "rooflines": r["rooflines"], "gpu_launches": r["gpu_launches"],
+                "stages_ms_per_step": r["stages_ms_per_step"], "create_s": r["create_s"]}
     else:
         line = run_ours(args)
     if line is not None:

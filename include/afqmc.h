@@ -116,6 +116,33 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore,
                           const double* psiT, const afqmc_params* params,
                           void* workspace, size_t workspace_bytes, afqmc_ctx** out);
 
+/* Chunked construction, for Hamiltonians whose Cholesky tensor is too large to pass (or to hold in
+ * binary64) at once.  afqmc_create_begin takes everything afqmc_create takes except chol, and
+ * returns a context in set-up.  afqmc_add_cholesky then passes the vectors L^gamma for gamma =
+ * gamma0 .. gamma0 + ngamma - 1 ([ngamma][norb][norb], each symmetric), in order and each exactly
+ * once, as binary64 (dtype AFQMC_DTYPE_F64) or binary32 (AFQMC_DTYPE_F32) from host memory
+ * (location AFQMC_HOST: copied through the workspace and checked on the host before the copy) or
+ * from device memory (AFQMC_DEVICE: read in place, checked on the device; the check is reported by
+ * afqmc_create_end).  The caller may reuse or free a chunk's memory when the call returns.
+ * afqmc_create_end finishes the set-up once every vector has been passed: the mean-field shift
+ * lbar_gamma = Tr L^gamma P_T, h_eff = h - 1/2 sum L L + sum lbar L, exp(-dt/2 h_eff) (all
+ * accumulated on the device one chunk at a time, binary64 sums), the half-rotated tensors, the
+ * walkers and E_var.  Until then every other call but afqmc_destroy rejects the context.  On an
+ * error the context stays allocated; afqmc_destroy frees it.  afqmc_create is begin + one
+ * afqmc_add_cholesky of every vector from host memory + end.  Set-up products that would cost more
+ * than ~4e11 binary64 operations (sum L L, Ltilde) run in binary32 in the reduced-precision forms;
+ * their sums over chunks stay binary64. */
+#define AFQMC_DTYPE_F64 0
+#define AFQMC_DTYPE_F32 1
+#define AFQMC_HOST 0
+#define AFQMC_DEVICE 1
+afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
+                                int32_t nbeta, const double* psiT, const afqmc_params* params, void* workspace,
+                                size_t workspace_bytes, afqmc_ctx** out);
+afqmc_status afqmc_add_cholesky(afqmc_ctx* ctx, int32_t gamma0, int32_t ngamma, const void* chol, int32_t dtype,
+                                int32_t location);
+afqmc_status afqmc_create_end(afqmc_ctx* ctx);
+
 /* nsteps phaseless steps (Eqs. 10-16), each: Green's function / Theta and the
  * force bias at the current walkers (reused from afqmc_local_energy when it
  * was measured at the same walkers), Philox fields x with counter = the step,

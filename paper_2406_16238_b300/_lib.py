@@ -61,6 +61,10 @@ SIGNATURES = {
     "afqmc_workspace_size": (_i32, [_i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
     "afqmc_create": (_i32, [_dp, _dp, ctypes.c_double, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params), _vp,
                             ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "afqmc_create_begin": (_i32, [_dp, ctypes.c_double, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params), _vp,
+                                  ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "afqmc_add_cholesky": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32]),
+    "afqmc_create_end": (_i32, [_vp]),
     "afqmc_propagate": (_i32, [_vp, _i32]),
     "afqmc_local_energy": (_i32, [_vp, _dp, _dp]),
     "afqmc_local_energy_async": (_i32, [_vp, _dp]),
@@ -140,18 +144,33 @@ def _ptr(a):
 
 
 class Afqmc:
-    """One walker batch of phaseless AFQMC on the current CUDA device (afqmc_create ... afqmc_destroy)."""
+    """One walker batch of phaseless AFQMC on the current CUDA device (afqmc_create ... afqmc_destroy).
+
+    chol is either the whole [naux, norb, norb] array (afqmc_create) or an iterable of Cholesky
+    chunks (then naux must be given): each chunk a [ngamma, norb, norb] float64 / float32 array
+    (host: numpy or a CPU torch tensor) or a CUDA torch tensor on the context's device, passed in
+    gamma order through afqmc_create_begin / afqmc_add_cholesky / afqmc_create_end.
+    """
 
     def __init__(self, h1e, chol, ecore, nalpha, nbeta, psiT, *, nwalkers, dt=0.005, taylor_order=6, fb_cap=1.0,
-                 seed=0, prec="fp64", e_trial=None, device=None, stream=None):
+                 seed=0, prec="fp64", e_trial=None, device=None, stream=None, naux=None):
         import torch
         lib = load()
         self.h1e = _f64(h1e)
         norb = self.h1e.shape[0]
-        self.chol = _f64(chol)
-        naux = self.chol.shape[0]
-        if self.chol.shape != (naux, norb, norb):
-            raise ValueError("chol must be [naux, norb, norb]")
+        if isinstance(chol, torch.Tensor):   # one chunk holding every vector
+            naux = int(chol.shape[0]) if naux is None else naux
+            chol = [chol]
+        chunked = not isinstance(chol, np.ndarray)
+        if chunked:
+            if naux is None:
+                raise ValueError("naux is required when chol is given in chunks")
+            self.chol = None
+        else:
+            self.chol = _f64(chol)
+            naux = self.chol.shape[0]
+            if self.chol.shape != (naux, norb, norb):
+                raise ValueError("chol must be [naux, norb, norb]")
         self.psiT = _f64(psiT, (norb, nalpha + nbeta))
         self.norb, self.naux, self.nalpha, self.nbeta, self.nwalkers = norb, naux, nalpha, nbeta, int(nwalkers)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -166,11 +185,46 @@ class Afqmc:
         with torch.cuda.device(self.device):
             self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
         ctx = ctypes.c_void_p()
-        _check(lib.afqmc_create(_ptr(self.h1e), _ptr(self.chol), float(ecore), norb, naux, nalpha, nbeta,
-                                _ptr(self.psiT), ctypes.byref(self.params), ctypes.c_void_p(self.workspace.data_ptr()),
-                                nbytes.value, ctypes.byref(ctx)))
-        self._ctx = ctx
         self._lib = lib
+        if not chunked:
+            _check(lib.afqmc_create(_ptr(self.h1e), _ptr(self.chol), float(ecore), norb, naux, nalpha, nbeta,
+                                    _ptr(self.psiT), ctypes.byref(self.params),
+                                    ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value, ctypes.byref(ctx)))
+            self._ctx = ctx
+            return
+        with torch.cuda.device(self.device):
+            _check(lib.afqmc_create_begin(_ptr(self.h1e), float(ecore), norb, naux, nalpha, nbeta, _ptr(self.psiT),
+                                          ctypes.byref(self.params), ctypes.c_void_p(self.workspace.data_ptr()),
+                                          nbytes.value, ctypes.byref(ctx)))
+            self._ctx = ctx
+            g0 = 0
+            for chunk in chol:
+                g0 += self._add_cholesky(g0, chunk, norb)
+            _check(lib.afqmc_create_end(self._ctx))
+
+    def _add_cholesky(self, g0, chunk, norb):
+        import torch
+        if isinstance(chunk, torch.Tensor):
+            if chunk.dtype not in (torch.float64, torch.float32):
+                raise ValueError("Cholesky chunks must be float64 or float32")
+            t = chunk.contiguous()
+            if t.is_cuda and t.device != self.device:
+                raise ValueError(f"chunk is on {t.device}, the context on {self.device}")
+            dtype = 0 if t.dtype == torch.float64 else 1
+            loc = 1 if t.is_cuda else 0
+            ptr, shape = t.data_ptr(), tuple(t.shape)
+            keep = t
+        else:
+            a = np.asarray(chunk)
+            if a.dtype not in (np.float64, np.float32):
+                a = a.astype(np.float64)
+            a = np.ascontiguousarray(a)
+            dtype, loc, ptr, shape, keep = (0 if a.dtype == np.float64 else 1), 0, a.ctypes.data, a.shape, a
+        if len(shape) != 3 or shape[1:] != (norb, norb):
+            raise ValueError(f"a Cholesky chunk must be [ngamma, {norb}, {norb}] (got {shape})")
+        _check(self._lib.afqmc_add_cholesky(self._ctx, int(g0), int(shape[0]), ctypes.c_void_p(ptr), dtype, loc))
+        del keep
+        return shape[0]
 
     # --- the hot path -------------------------------------------------------------------
     def propagate(self, nsteps=1):

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <random>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <cuda.h>
@@ -21,6 +22,7 @@
 #include "kernels_simt.cuh"
 #include "cv_kernels.cuh"
 #include "tc_gemm.cuh"
+#include "setup_kernels.cuh"
 
 using namespace afq;
 
@@ -68,11 +70,12 @@ struct Dims {
 struct Layout {
   size_t psi, thetaT, tA, tB, tC, psi_tmp, th_tmp, logO, logO_tmp, w, w_tmp, wph;
   size_t phi, phi_r, hrot, hrot_r, lbar, slbar, lrot, chol, eh;
+  size_t msum, lsum, pden, e1, e2;   // set-up: sum L L, sum lbar L, trial density, two N x N temporaries
   size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
-  size_t exch_part, eloc, hist, status, step, src, cum, neww, slot;
+  size_t exch_part, eloc, hist, status, step, src, cum, neww, slot, sflag;
   size_t tc;          // tensor-core operand buffers (BF16 forms)
-  size_t setup;       // set-up scratch (aliases vhs; binary64 L, L L products, Ltilde)
-  size_t setup_bytes, vhs_bytes, tc_bytes;
+  size_t stage;       // set-up staging of Cholesky chunks (aliases vhs, which the set-up does not use)
+  size_t stage_bytes, stage_bytes_avail, vhs_bytes, tc_bytes;
   size_t total;
 };
 
@@ -101,8 +104,15 @@ Layout plan(const Dims& d) {
   L.lbar = take(X * 8);
   L.slbar = take(X * 8);
   L.lrot = take(X * nc * N * R);
-  L.chol = take(X * N * N * R);
+  // L in the working precision feeds the CUDA-core VHS GEMM; the tensor-core forms read only their
+  // bf16 copy of L^T
+  L.chol = take(d.tensor() ? 0 : X * N * N * R);
   L.eh = take(N * N * R);
+  L.msum = take(N * N * 8);
+  L.lsum = take(N * N * 8);
+  L.pden = take(N * N * 8);
+  L.e1 = take(N * N * 8);
+  L.e2 = take(N * N * 8);
   L.vbias = take(W * X * C);
   L.x = take(W * X * 8);
   L.xbar = take(W * X * 16);
@@ -118,15 +128,19 @@ Layout plan(const Dims& d) {
   L.cum = take(W * 8);
   L.neww = take(256);
   L.slot = take(256);
+  L.sflag = take(256);   // set-up: input check flags, the 1-norm of the exponent
   {
     tc::TcState tmp;
     L.tc_bytes = tc::plan(&tmp, d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk);
   }
   L.tc = take(L.tc_bytes);
   L.vhs_bytes = W * N * N * C;
-  L.setup_bytes = align_up(X * N * N * 8, 256) * 2 + align_up(N * N * 8, 256) + align_up(X * nc * N * 8, 256);
-  L.vhs = take(std::max(L.vhs_bytes, L.setup_bytes));
-  L.setup = L.vhs;
+  // staging of at least one gamma: a host chunk's copy (binary64), its cast for the set-up GEMMs and
+  // the chunk's Ltilde (binary64)
+  L.stage_bytes = align_up(N * N * 8, 256) * 2 + align_up(nc * N * 8, 256);
+  L.stage_bytes_avail = std::max(L.vhs_bytes, L.stage_bytes);
+  L.vhs = take(L.stage_bytes_avail);
+  L.stage = L.vhs;
   L.total = align_up(cur, 256);
   return L;
 }
@@ -188,41 +202,6 @@ bool invert_small(std::vector<double>& a, int n) {   // Gauss-Jordan with partia
   return true;
 }
 
-void matmul(const std::vector<double>& a, const std::vector<double>& b, std::vector<double>& c, int n) {
-  c.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int k = 0; k < n; ++k) {
-      const double aik = a[(size_t)i * n + k];
-      if (aik == 0.0) continue;
-      for (int j = 0; j < n; ++j) c[(size_t)i * n + j] += aik * b[(size_t)k * n + j];
-    }
-}
-
-// exp(A) for a symmetric A by scaling and squaring of the Taylor series.
-void expm_host(const std::vector<double>& a, int n, std::vector<double>& out) {
-  double norm1 = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += std::fabs(a[(size_t)i * n + j]);
-    norm1 = std::max(norm1, s);
-  }
-  int sq = 0;
-  while (norm1 / std::ldexp(1.0, sq) > 0.25) ++sq;
-  const double scale = std::ldexp(1.0, -sq);
-  std::vector<double> b(a.size());
-  for (size_t i = 0; i < a.size(); ++i) b[i] = a[i] * scale;
-  out.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) out[(size_t)i * n + i] = 1.0;
-  std::vector<double> term = out, tmp;
-  for (int k = 1; k <= 30; ++k) {
-    matmul(term, b, tmp, n);
-    double tn = 0.0;
-    for (size_t i = 0; i < tmp.size(); ++i) { term[i] = tmp[i] / k; out[i] += term[i]; tn = std::max(tn, std::fabs(term[i])); }
-    if (tn < 1e-18) break;
-  }
-  for (int s = 0; s < sq; ++s) { matmul(out, out, tmp, n); out.swap(tmp); }
-}
-
 }  // namespace
 
 struct afqmc_ctx {
@@ -235,6 +214,12 @@ struct afqmc_ctx {
   unsigned long long seed, host_step, launches;
   bool theta_fresh, vbias_fresh;
   int hist_used;
+  // chunked set-up (afqmc_create_begin / afqmc_add_cholesky / afqmc_create_end)
+  bool building = false;     // true until afqmc_create_end succeeds
+  double e_trial_param = 0.0;   // params.e_trial (NaN: E_var once it is measured)
+  int chol_next = 0;         // first gamma not passed yet
+  bool setup_f32 = false;    // set-up GEMMs (sum L L, Ltilde) in binary32 (large problems, reduced forms)
+  std::vector<double> h1e_host;
   // free projection (Section "Free projection AFQMC"): no force-bias shift, complex weights
   // w e^{i phi} (phases in L.wph), no phaseless projection and no comb
   bool free_proj = false;
@@ -767,12 +752,15 @@ afqmc_status read_status(afqmc_ctx* c) {
 #define DISPATCH(ctx, fn, ...)                                                      \
   ((ctx)->d.prec == AFQMC_PREC_FP64 ? fn<double>(ctx, ##__VA_ARGS__) : fn<float>(ctx, ##__VA_ARGS__))
 
+// ---- chunked set-up ----------------------------------------------------------------------
+// begin: trial quantities (host, O(N^2 n)), zeroed accumulators on the device.
 template <typename R>
-afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, const double* psiT) {
+afqmc_status setup_begin(afqmc_ctx* c, const double* h1e, const double* psiT) {
   const Dims& d = c->d;
-  const int N = d.N, X = d.X, nc = d.ncol, nt = d.na + d.nb;
+  const int N = d.N, nc = d.ncol, nt = d.na + d.nb;
   afqmc_status st;
   if ((st = set_smem_limits<R>(d)) != AFQMC_OK) return st;
+  c->h1e_host.assign(h1e, h1e + (size_t)N * N);
   // trial columns that are stored (restricted: alpha only)
   std::vector<double> phi((size_t)N * nc);
   for (int p = 0; p < N; ++p)
@@ -804,90 +792,229 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
         P[(size_t)p * N + q] += acc;
       }
   }
-  // lbar_g = Tr(L^g P); E_c = E0 - 1/2 sum lbar^2; sum_g lbar_g L^g
-  std::vector<double> lbar(X), lsum((size_t)N * N, 0.0);
-  double l2 = 0.0;
-  for (int g = 0; g < X; ++g) {
-    const double* Lg = chol + (size_t)g * N * N;
-    double acc = 0.0;
-    for (size_t i = 0; i < (size_t)N * N; ++i) acc += Lg[i] * P[i];
-    lbar[g] = acc;
-    l2 += acc * acc;
-    for (size_t i = 0; i < (size_t)N * N; ++i) lsum[i] += acc * Lg[i];
-  }
-  c->e_c = c->ecore - 0.5 * l2;
   // htilde = Phi^T h  [nc][N]
   std::vector<double> hrot((size_t)nc * N, 0.0);
   for (int col = 0; col < nc; ++col)
-    for (int q = 0; q < N; ++q) {
-      double acc = 0.0;
-      for (int p = 0; p < N; ++p) acc += phi[(size_t)p * nc + col] * h1e[(size_t)p * N + q];
-      hrot[(size_t)col * N + q] = acc;
+    for (int p = 0; p < N; ++p) {
+      const double f = phi[(size_t)p * nc + col];
+      if (f == 0.0) continue;
+      for (int q = 0; q < N; ++q) hrot[(size_t)col * N + q] += f * h1e[(size_t)p * N + q];
     }
-  // device: binary64 L, products L^g L^g, Ltilde
-  double* chol64 = c->at<double>(c->L.setup);
-  double* prod = chol64 + align_up((size_t)X * N * N * 8, 256) / 8;
-  double* msum = prod + align_up((size_t)X * N * N * 8, 256) / 8;
-  double* lrot64 = msum + align_up((size_t)N * N * 8, 256) / 8;
-  CU(cudaMemcpyAsync(chol64, chol, (size_t)X * N * N * 8, cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->base + c->L.phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->base + c->L.hrot, hrot.data(), hrot.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(c->base + c->L.lbar, lbar.data(), lbar.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  std::vector<double> slbar(X);   // sqrt(dt) lbar for the fields kernel
-  for (int g = 0; g < X; ++g) slbar[g] = c->sdt * lbar[g];
-  CU(cudaMemcpyAsync(c->base + c->L.slbar, slbar.data(), slbar.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  {   // prod[g] = L^g L^g
-    GemmDesc g = gdesc(N, N, N, X);
-    g.A = chol64; g.sAb = (long long)N * N; g.sAm = N; g.sAk = 1;
-    g.B = chol64; g.sBb = (long long)N * N; g.sBk = N; g.sBn = 1;
-    g.C = prod; g.sCb = (long long)N * N; g.sCm = N; g.sCn = 1;
-    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
-    k_sum_batches<<<148, 256, 0, c->stream>>>(X, (size_t)N * N, prod, msum);
-    CHECK_LAUNCH(c);
-  }
-  {   // Ltilde[g] = Phi^T L^g  ([nc][N] per gamma)
-    GemmDesc g = gdesc(nc, N, N, X);
-    g.A = c->at<double>(c->L.phi); g.sAb = 0; g.sAm = 1; g.sAk = nc;
-    g.B = chol64; g.sBb = (long long)N * N; g.sBk = N; g.sBn = 1;
-    g.C = lrot64; g.sCb = (long long)nc * N; g.sCm = N; g.sCn = 1;
-    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
-  }
-  std::vector<double> m((size_t)N * N);
-  CU(cudaMemcpyAsync(m.data(), msum, m.size() * 8, cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  // h_eff = h - 1/2 sum L L + sum lbar L; E_h = exp(-dt/2 h_eff)
-  std::vector<double> heff((size_t)N * N), eh;
-  for (size_t i = 0; i < heff.size(); ++i) heff[i] = -0.5 * c->dt * (h1e[i] - 0.5 * m[i] + lsum[i]);
-  for (int p = 0; p < N; ++p)   // symmetrise the rounding
-    for (int q = p + 1; q < N; ++q) {
-      const double v = 0.5 * (heff[(size_t)p * N + q] + heff[(size_t)q * N + p]);
-      heff[(size_t)p * N + q] = heff[(size_t)q * N + p] = v;
-    }
-  expm_host(heff, N, eh);
-  std::vector<R> ehr(eh.begin(), eh.end());
-  CU(cudaMemcpyAsync(c->base + c->L.eh, ehr.data(), ehr.size() * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-  CU(cudaStreamSynchronize(c->stream));   // ehr goes out of scope
-  k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * N * N, chol64, c->at<R>(c->L.chol));
-  CHECK_LAUNCH(c);
-  k_convert<R><<<296, 256, 0, c->stream>>>((size_t)X * nc * N, lrot64, c->at<R>(c->L.lrot));
-  CHECK_LAUNCH(c);
+  CU(cudaMemcpyAsync(c->base + c->L.pden, P.data(), P.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.msum, 0, (size_t)N * N * 8, c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.lsum, 0, (size_t)N * N * 8, c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.sflag, 0, 256, c->stream));
   k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc, c->at<double>(c->L.phi), c->at<R>(c->L.phi_r));
   CHECK_LAUNCH(c);
   k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc, c->at<double>(c->L.hrot), c->at<R>(c->L.hrot_r));
   CHECK_LAUNCH(c);
-  if (d.prec == AFQMC_PREC_BF16 || d.prec == AFQMC_PREC_BF16X3) {
-    tc::plan(&c->tcs, d.prec, d.W, N, X, nc, d.c0, d.nbk, d.nblk);
-    if ((st = tc::prepare(&c->tcs, c->stream, c->at<char>(c->L.tc), chol64, lrot64, &c->launches, g_err,
-                          sizeof(g_err))) != AFQMC_OK)
+  // binary32 set-up GEMMs where binary64 would take seconds (reduced forms only): their rounding,
+  // ~1e-7 relative per sum, stays far below the forms' own
+  const double flops = 2.0 * d.X * (double)N * N * N + 2.0 * d.X * (double)nc * N * N;
+  c->setup_f32 = d.prec != AFQMC_PREC_FP64 && flops > 4e11;
+  if (d.tensor()) {
+    tc::plan(&c->tcs, d.prec, d.W, N, d.X, nc, d.c0, d.nbk, d.nblk);
+    if ((st = tc::begin(&c->tcs, c->stream, c->at<char>(c->L.tc), g_err, sizeof(g_err))) != AFQMC_OK) return st;
+  }
+  // the synchronisation keeps the host vectors alive until their copies are done
+  CU(cudaStreamSynchronize(c->stream));
+  return AFQMC_OK;
+}
+
+// One sub-chunk of gammas [g0, g0 + ng) already on the device (src, type T): checks, lbar, the
+// accumulators, Ltilde, and the working-precision / tensor-core copies of L.
+template <typename R, typename T, typename G>
+afqmc_status setup_chunk(afqmc_ctx* c, int g0, int ng, const T* src, char* scratch) {
+  const Dims& d = c->d;
+  const int N = d.N, nc = d.ncol;
+  const size_t NN = (size_t)N * N;
+  afqmc_status st;
+  k_chol_check<T><<<592, 256, 0, c->stream>>>(ng, N, src, c->at<int>(c->L.sflag));
+  CHECK_LAUNCH(c);
+  double* lbar = c->at<double>(c->L.lbar) + g0;
+  k_chunk_lbar<T><<<ng, 256, 0, c->stream>>>(N, src, c->at<double>(c->L.pden), lbar);
+  CHECK_LAUNCH(c);
+  k_chunk_lsum<T><<<(unsigned)std::min<size_t>(4 * 148, (NN + 255) / 256), 256, 0, c->stream>>>(
+      ng, NN, src, lbar, c->at<double>(c->L.lsum));
+  CHECK_LAUNCH(c);
+  // the chunk in the GEMM type
+  const G* sg;
+  char* cur = scratch;
+  if (std::is_same<T, G>::value) {
+    sg = reinterpret_cast<const G*>(src);
+  } else {
+    G* cast = reinterpret_cast<G*>(cur);
+    cur += align_up((size_t)ng * NN * sizeof(G), 256);
+    k_cast<T, G><<<592, 256, 0, c->stream>>>((size_t)ng * NN, src, cast);
+    CHECK_LAUNCH(c);
+    sg = cast;
+  }
+  {   // msum += sum_g L^g L^g = B^T B with B the chunk viewed as [ng N][N] (L^g symmetric)
+    GemmDesc g = gdesc(N, N, ng * N, 1);
+    g.A = sg; g.sAm = 1; g.sAk = N;
+    g.B = sg; g.sBk = N; g.sBn = 1;
+    if (std::is_same<G, double>::value) {
+      g.D = c->at<double>(c->L.msum); g.sDm = N; g.sDn = 1; g.d_add = 1;
+      if ((st = gemm<G, false, false>(c, g)) != AFQMC_OK) return st;
+    } else {   // binary32 partial sum of the chunk, added into the binary64 total
+      g.C = c->at<G>(c->L.e1); g.sCm = N; g.sCn = 1;
+      if ((st = gemm<G, false, false>(c, g)) != AFQMC_OK) return st;
+      k_add_f32_to_f64<<<592, 256, 0, c->stream>>>(NN, c->at<float>(c->L.e1), c->at<double>(c->L.msum));
+      CHECK_LAUNCH(c);
+    }
+  }
+  G* lrot = reinterpret_cast<G*>(cur);
+  {   // Ltilde[g] = Phi^T L^g  ([nc][N] per gamma)
+    GemmDesc g = gdesc(nc, N, N, ng);
+    g.A = std::is_same<G, double>::value ? c->at<void>(c->L.phi) : c->at<void>(c->L.phi_r);
+    g.sAb = 0; g.sAm = 1; g.sAk = nc;
+    g.B = sg; g.sBb = (long long)NN; g.sBk = N; g.sBn = 1;
+    g.C = lrot; g.sCb = (long long)nc * N; g.sCm = N; g.sCn = 1;
+    if ((st = gemm<G, false, false>(c, g)) != AFQMC_OK) return st;
+  }
+  k_cast<G, R><<<592, 256, 0, c->stream>>>((size_t)ng * nc * N, lrot, c->at<R>(c->L.lrot) + (size_t)g0 * nc * N);
+  CHECK_LAUNCH(c);
+  if (d.tensor()) {
+    if ((st = tc::load_chunk<T, G>(&c->tcs, c->stream, c->at<char>(c->L.tc), g0, ng, src, lrot, &c->launches, g_err,
+                                   sizeof(g_err))) != AFQMC_OK)
       return st;
+  } else {
+    k_cast<T, R><<<592, 256, 0, c->stream>>>((size_t)ng * NN, src, c->at<R>(c->L.chol) + (size_t)g0 * NN);
+    CHECK_LAUNCH(c);
+  }
+  return AFQMC_OK;
+}
+
+// Host-side check of a host chunk (before it is copied): finite entries, symmetric L^g.
+template <typename T>
+afqmc_status check_host_chunk(int g0, int ng, int N, const T* chol) {
+  const size_t NN = (size_t)N * N;
+  for (int g = 0; g < ng; ++g) {
+    const T* Lg = chol + (size_t)g * NN;
+    for (size_t i = 0; i < NN; ++i)
+      if (!std::isfinite((double)Lg[i])) return fail(AFQMC_EINVAL, "chol has a non-finite entry at %zu", (size_t)(g0 + g) * NN + i);
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        const double v = Lg[(size_t)p * N + q], u = Lg[(size_t)q * N + p];
+        if (std::fabs(v - u) > 1e-12 * std::max(1.0, std::max(std::fabs(v), std::fabs(u))))
+          return fail(AFQMC_EINVAL, "chol[%d] is not symmetric at (%d, %d)", g0 + g, p, q);
+      }
+  }
+  return AFQMC_OK;
+}
+
+// Gammas [g0, g0 + ng) from host or device memory, in sub-chunks that fit the staging region.
+template <typename R, typename T>
+afqmc_status setup_add(afqmc_ctx* c, int g0, int ng, const T* chol, bool on_device, bool host_checked) {
+  const Dims& d = c->d;
+  const size_t NN = (size_t)d.N * d.N;
+  const size_t per = (on_device ? 0 : align_up(NN * sizeof(T), 256)) + align_up(NN * 8, 256) +
+                     align_up((size_t)d.ncol * d.N * 8, 256);
+  const size_t cap = std::max<size_t>(1, c->L.stage_bytes_avail / per);
+  for (int a = 0; a < ng; a += (int)cap) {
+    const int n = (int)std::min<size_t>(cap, (size_t)(ng - a));
+    const T* part = chol + (size_t)a * NN;
+    char* scratch = c->base + c->L.stage;
+    const T* src = part;
+    if (!on_device) {
+      afqmc_status st;
+      if (!host_checked && (st = check_host_chunk<T>(g0 + a, n, d.N, part)) != AFQMC_OK) return st;
+      T* dst = reinterpret_cast<T*>(scratch);
+      CU(cudaMemcpyAsync(dst, part, (size_t)n * NN * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+      scratch += align_up((size_t)n * NN * sizeof(T), 256);
+      src = dst;
+    }
+    afqmc_status st = c->setup_f32 ? setup_chunk<R, T, float>(c, g0 + a, n, src, scratch)
+                                   : setup_chunk<R, T, double>(c, g0 + a, n, src, scratch);
+    if (st != AFQMC_OK) return st;
+    // the staging region is reused by the next sub-chunk (stream order), and a host chunk's
+    // pageable source must stay readable until its copy is done
+    if (!on_device) CU(cudaStreamSynchronize(c->stream));
+  }
+  // the caller may free or reuse a device chunk once the call returns
+  if (on_device) CU(cudaStreamSynchronize(c->stream));
+  return AFQMC_OK;
+}
+
+// end: h_eff, exp(-dt/2 h_eff), the mean-field constants, operand descriptors, walkers, E_var.
+template <typename R>
+afqmc_status setup_end(afqmc_ctx* c) {
+  const Dims& d = c->d;
+  const int N = d.N, X = d.X, nc = d.ncol;
+  const size_t NN = (size_t)N * N;
+  afqmc_status st;
+  int flags = 0;
+  CU(cudaMemcpyAsync(&flags, c->base + c->L.sflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> lbar(X);
+  CU(cudaMemcpyAsync(lbar.data(), c->base + c->L.lbar, (size_t)X * 8, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (flags & kSetupNonFinite) return fail(AFQMC_EINVAL, "chol has a non-finite entry");
+  if (flags & kSetupAsymmetric) return fail(AFQMC_EINVAL, "chol is not symmetric");
+  double l2 = 0.0;
+  for (int g = 0; g < X; ++g) l2 += lbar[g] * lbar[g];
+  c->e_c = c->ecore - 0.5 * l2;
+  std::vector<double> slbar(X);   // sqrt(dt) lbar for the fields kernel
+  for (int g = 0; g < X; ++g) slbar[g] = c->sdt * lbar[g];
+  CU(cudaMemcpyAsync(c->base + c->L.slbar, slbar.data(), slbar.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  // A = -dt/2 h_eff (e1), from h (e2)
+  double* A = c->at<double>(c->L.e1);
+  double* H = c->at<double>(c->L.e2);
+  CU(cudaMemcpyAsync(H, c->h1e_host.data(), NN * 8, cudaMemcpyHostToDevice, c->stream));
+  const unsigned eg = (unsigned)std::min<size_t>(4 * 148, (NN + 255) / 256);
+  k_heff<<<eg, 256, 0, c->stream>>>(N, -0.5 * c->dt, H, c->at<double>(c->L.msum), c->at<double>(c->L.lsum), A);
+  CHECK_LAUNCH(c);
+  double* dnorm = c->at<double>(c->L.sflag) + 8;
+  k_norm1<<<1, 1024, 0, c->stream>>>(N, A, dnorm);
+  CHECK_LAUNCH(c);
+  double norm = 0.0;
+  CU(cudaMemcpyAsync(&norm, dnorm, 8, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));   // also ends the uses of slbar and h1e_host
+  if (!std::isfinite(norm)) return fail(AFQMC_EINVAL, "h_eff is not finite");
+  // exp(A) = (exp(A / 2^s))^(2^s), ||A|| / 2^s <= 1/4, Taylor to degree m in Horner form
+  int sq = 0;
+  while (norm / std::ldexp(1.0, sq) > 0.25) ++sq;
+  const double sc = std::ldexp(1.0, -sq), theta = norm * sc;
+  int m = 2;
+  {
+    double term = theta * theta / 2.0;   // theta^(m+1) / (m+1)! for the first omitted term
+    term = term * theta / 3.0;
+    while (term > 5e-18 && m < 30) { ++m; term = term * theta / (m + 1); }
+  }
+  double* T = c->at<double>(c->L.msum);   // sum L L and lsum are no longer needed
+  double* Tn = c->at<double>(c->L.lsum);
+  k_identity_plus<<<eg, 256, 0, c->stream>>>(N, sc / m, 1.0, A, T);
+  CHECK_LAUNCH(c);
+  for (int k = m - 1; k >= 1; --k) {   // T <- I + (sc / k) A T
+    GemmDesc g = gdesc(N, N, N, 1);
+    g.A = A; g.sAm = N; g.sAk = 1;
+    g.B = T; g.sBk = N; g.sBn = 1;
+    g.C = Tn; g.sCm = N; g.sCn = 1;
+    g.alpha_re = sc / k;
+    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
+    k_identity_plus<<<eg, 256, 0, c->stream>>>(N, 1.0, 1.0, Tn, Tn);
+    CHECK_LAUNCH(c);
+    std::swap(T, Tn);
+  }
+  for (int s = 0; s < sq; ++s) {
+    GemmDesc g = gdesc(N, N, N, 1);
+    g.A = T; g.sAm = N; g.sAk = 1;
+    g.B = T; g.sBk = N; g.sBn = 1;
+    g.C = Tn; g.sCm = N; g.sCn = 1;
+    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
+    std::swap(T, Tn);
+  }
+  k_convert<R><<<64, 256, 0, c->stream>>>(NN, T, c->at<R>(c->L.eh));
+  CHECK_LAUNCH(c);
+  if (d.tensor()) {
+    if ((st = tc::finish(&c->tcs, c->at<char>(c->L.tc), g_err, sizeof(g_err))) != AFQMC_OK) return st;
     if (c->tcs.pg.ok) {   // F = E_h - I in binary64 for the tensor-core propagation
-      std::vector<double> f(eh);
-      for (int p = 0; p < N; ++p) f[(size_t)p * N + p] -= 1.0;
-      CU(cudaMemcpyAsync(prod, f.data(), f.size() * 8, cudaMemcpyHostToDevice, c->stream));
-      if ((st = tc::prepare_prop(&c->tcs, c->stream, c->at<char>(c->L.tc), prod, &c->launches, g_err,
+      k_identity_plus<<<eg, 256, 0, c->stream>>>(N, 1.0, -1.0, T, Tn);
+      CHECK_LAUNCH(c);
+      if ((st = tc::prepare_prop(&c->tcs, c->stream, c->at<char>(c->L.tc), Tn, &c->launches, g_err,
                                  sizeof(g_err))) != AFQMC_OK)
         return st;
-      CU(cudaStreamSynchronize(c->stream));   // f goes out of scope
     }
   }
   CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));
@@ -906,6 +1033,8 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
   CU(cudaMemcpyAsync(&e0, c->base + c->L.eloc, sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   c->e_var = e0.x;
+  c->h1e_host.clear();
+  c->h1e_host.shrink_to_fit();
   return read_status(c);
 }
 
@@ -913,6 +1042,7 @@ afqmc_status create_impl(afqmc_ctx* c, const double* h1e, const double* chol, co
 // running beside it (afqmc_local_energy_async); afqmc_propagate leaves that to the step's overlap.
 afqmc_status check_ctx(afqmc_ctx* c) {
   if (!c) return fail(AFQMC_EINVAL, "context is NULL");
+  if (c->building) return fail(AFQMC_EINVAL, "the context's set-up is not complete (afqmc_create_end)");
   return join_energy(c);
 }
 
@@ -1024,12 +1154,12 @@ afqmc_status afqmc_workspace_size(int32_t norb, int32_t naux, int32_t nalpha, in
   return AFQMC_OK;
 }
 
-afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, int32_t norb, int32_t naux,
-                          int32_t nalpha, int32_t nbeta, const double* psiT, const afqmc_params* params,
-                          void* workspace, size_t workspace_bytes, afqmc_ctx** out) {
+afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
+                                int32_t nbeta, const double* psiT, const afqmc_params* params, void* workspace,
+                                size_t workspace_bytes, afqmc_ctx** out) {
   if (!out) return fail(AFQMC_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!h1e || !chol) return fail(AFQMC_EINVAL, "h1e or chol is NULL");
+  if (!h1e) return fail(AFQMC_EINVAL, "h1e is NULL");
   Dims d{};
   afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d);
   if (st != AFQMC_OK) return st;
@@ -1039,15 +1169,11 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
   if (workspace_bytes < L.total)
     return fail(AFQMC_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
   if (!std::isfinite(ecore)) return fail(AFQMC_EINVAL, "ecore is not finite");
-  const size_t N = norb, X = naux, nt = nalpha + nbeta;
-  double lmax = 0.0, hmax = 0.0;
+  const size_t N = norb, nt = nalpha + nbeta;
+  double hmax = 0.0;
   for (size_t i = 0; i < N * N; ++i) {
     if (!std::isfinite(h1e[i])) return fail(AFQMC_EINVAL, "h1e has a non-finite entry");
     hmax = std::max(hmax, std::fabs(h1e[i]));
-  }
-  for (size_t i = 0; i < X * N * N; ++i) {
-    if (!std::isfinite(chol[i])) return fail(AFQMC_EINVAL, "chol has a non-finite entry at %zu", i);
-    lmax = std::max(lmax, std::fabs(chol[i]));
   }
   for (size_t i = 0; i < N * nt; ++i)
     if (!std::isfinite(psiT[i])) return fail(AFQMC_EINVAL, "psiT has a non-finite entry");
@@ -1055,13 +1181,6 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
     for (size_t q = p + 1; q < N; ++q)
       if (std::fabs(h1e[p * N + q] - h1e[q * N + p]) > 1e-12 * std::max(1.0, hmax))
         return fail(AFQMC_EINVAL, "h1e is not symmetric at (%zu, %zu)", p, q);
-  for (size_t g = 0; g < X; ++g) {   // one N x N slab at a time (cache-resident)
-    const double* Lg = chol + g * N * N;
-    for (size_t p = 0; p < N; ++p)
-      for (size_t q = p + 1; q < N; ++q)
-        if (std::fabs(Lg[p * N + q] - Lg[q * N + p]) > 1e-12 * std::max(1.0, lmax))
-          return fail(AFQMC_EINVAL, "chol[%zu] is not symmetric at (%zu, %zu)", g, p, q);
-  }
   afqmc_ctx* c = new afqmc_ctx();
   c->d = d;
   c->L = L;
@@ -1082,13 +1201,85 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, i
   c->host_step = 0;
   c->launches = 0;
   c->hist_used = 0;
-  c->e_trial = 0.0;
-  st = DISPATCH(c, create_impl, h1e, chol, psiT);
+  c->e_trial = std::isnan(params->e_trial) ? 0.0 : params->e_trial;
+  c->e_trial_param = params->e_trial;
+  c->building = true;
+  c->chol_next = 0;
+  st = DISPATCH(c, setup_begin, h1e, psiT);
   if (st != AFQMC_OK) {
     delete c;
     return st;
   }
-  c->e_trial = std::isnan(params->e_trial) ? c->e_var : params->e_trial;
+  *out = c;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_add_cholesky(afqmc_ctx* ctx, int32_t gamma0, int32_t ngamma, const void* chol, int32_t dtype,
+                                int32_t location) {
+  if (!ctx) return fail(AFQMC_EINVAL, "context is NULL");
+  if (!ctx->building) return fail(AFQMC_EINVAL, "afqmc_add_cholesky: the context's set-up is already complete");
+  if (!chol) return fail(AFQMC_EINVAL, "afqmc_add_cholesky: chol is NULL");
+  if (dtype != AFQMC_DTYPE_F64 && dtype != AFQMC_DTYPE_F32) return fail(AFQMC_EINVAL, "afqmc_add_cholesky: dtype %d", dtype);
+  if (location != AFQMC_HOST && location != AFQMC_DEVICE)
+    return fail(AFQMC_EINVAL, "afqmc_add_cholesky: location %d", location);
+  if (gamma0 != ctx->chol_next)
+    return fail(AFQMC_EINVAL, "afqmc_add_cholesky: expected gamma0 = %d (vectors are passed in order, once)",
+                ctx->chol_next);
+  if (ngamma < 1 || gamma0 + (long long)ngamma > ctx->d.X)
+    return fail(AFQMC_EINVAL, "afqmc_add_cholesky: gammas [%d, %lld) outside [0, %d)", gamma0,
+                gamma0 + (long long)ngamma, ctx->d.X);
+  const bool dev = location == AFQMC_DEVICE;
+  afqmc_status st;
+  if (dtype == AFQMC_DTYPE_F64)
+    st = DISPATCH(ctx, setup_add, gamma0, ngamma, static_cast<const double*>(chol), dev, false);
+  else
+    st = DISPATCH(ctx, setup_add, gamma0, ngamma, static_cast<const float*>(chol), dev, false);
+  if (st != AFQMC_OK) return st;
+  ctx->chol_next = gamma0 + ngamma;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_create_end(afqmc_ctx* ctx) {
+  if (!ctx) return fail(AFQMC_EINVAL, "context is NULL");
+  if (!ctx->building) return fail(AFQMC_EINVAL, "afqmc_create_end: the context's set-up is already complete");
+  if (ctx->chol_next != ctx->d.X)
+    return fail(AFQMC_EINVAL, "afqmc_create_end: %d of %d Cholesky vectors passed", ctx->chol_next, ctx->d.X);
+  afqmc_status st = DISPATCH(ctx, setup_end);
+  if (st != AFQMC_OK) return st;
+  ctx->building = false;
+  ctx->e_trial = std::isnan(ctx->e_trial_param) ? ctx->e_var : ctx->e_trial_param;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore, int32_t norb, int32_t naux,
+                          int32_t nalpha, int32_t nbeta, const double* psiT, const afqmc_params* params,
+                          void* workspace, size_t workspace_bytes, afqmc_ctx** out) {
+  if (!out) return fail(AFQMC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!h1e || !chol) return fail(AFQMC_EINVAL, "h1e or chol is NULL");
+  Dims d{};
+  afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d);
+  if (st != AFQMC_OK) return st;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(AFQMC_EINVAL, "workspace must be a non-NULL 256-byte aligned device pointer");
+  Layout L = plan(d);
+  if (workspace_bytes < L.total)
+    return fail(AFQMC_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
+  // every host input is checked before the device is touched
+  if ((st = check_host_chunk<double>(0, naux, norb, chol)) != AFQMC_OK) return st;
+  afqmc_ctx* c = nullptr;
+  if ((st = afqmc_create_begin(h1e, ecore, norb, naux, nalpha, nbeta, psiT, params, workspace, workspace_bytes,
+                               &c)) != AFQMC_OK)
+    return st;
+  st = DISPATCH(c, setup_add, 0, naux, chol, false, true);
+  if (st == AFQMC_OK) {
+    c->chol_next = naux;
+    st = afqmc_create_end(c);
+  }
+  if (st != AFQMC_OK) {
+    afqmc_destroy(c);
+    return st;
+  }
   *out = c;
   return AFQMC_OK;
 }
@@ -1126,6 +1317,7 @@ afqmc_status afqmc_stage_times(afqmc_ctx* ctx, double* ms, int64_t* count) {
 
 afqmc_status afqmc_propagate(afqmc_ctx* ctx, int32_t nsteps) {
   if (!ctx) return fail(AFQMC_EINVAL, "context is NULL");   // an estimator beside it is joined by the overlap
+  if (ctx->building) return fail(AFQMC_EINVAL, "the context's set-up is not complete (afqmc_create_end)");
   afqmc_status st;
   if (nsteps < 0) return fail(AFQMC_EINVAL, "nsteps < 0");
   if (nsteps == 0 && (st = join_energy(ctx)) != AFQMC_OK) return st;
@@ -1818,6 +2010,7 @@ afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batc
   *out = nullptr;
   for (int i = 0; i < nsys; ++i) {
     if (!ctxs[i]) return fail(AFQMC_EINVAL, "batch: context %d is NULL", i);
+    if (ctxs[i]->building) return fail(AFQMC_EINVAL, "batch: context %d has not finished its set-up", i);
     if (ctxs[i]->host_step != ctxs[0]->host_step) return fail(AFQMC_EINVAL, "batch: contexts must be at the same step");
     if (ctxs[i]->cv.enabled) return fail(AFQMC_EINVAL, "batch: the control-variate form is not batched");
   }

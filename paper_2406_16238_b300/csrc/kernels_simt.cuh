@@ -403,7 +403,7 @@ struct FieldArgs {
   double* x;                // [W][X]
   double2* xbar;            // [W][X]
   cplx_t<R>* coef;          // [W][X]
-  __nv_bfloat16* coefb;     // optional: rows (w, part) of nseg * kx bf16, [hi | lo | hi] (hi only if nseg = 1)
+  __nv_bfloat16* coefb;     // optional: rows (w, part) of bf16 [hi | lo] (kx each; hi only if nseg = 1)
   int kx, nseg;
   double2* cmf;             // [W]
   double2* xxbar;           // [W]
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
       }
       a.coef[(size_t)w * a.X + g] = cf;
       if (a.coefb) {
-        const size_t rowlen = (size_t)a.nseg * a.kx;
+        const size_t rowlen = (size_t)(a.nseg == 3 ? 2 : 1) * a.kx;
         __nv_bfloat16* re = a.coefb + (size_t)w * 2 * rowlen + g;
         __nv_bfloat16* im = re + rowlen;
         const float fx = (float)cf.x, fy = (float)cf.y;
@@ -480,8 +480,6 @@ __global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
         if (a.nseg == 3) {
           re[a.kx] = __float2bfloat16_rn(fx - __bfloat162float(hr));
           im[a.kx] = __float2bfloat16_rn(fy - __bfloat162float(hi));
-          re[2 * a.kx] = hr;
-          im[2 * a.kx] = hi;
         }
       }
       cm.x = fma(-sl, xs.y, cm.x);

@@ -36,6 +36,9 @@ struct Geom {
   int stages, epi_groups;
   int epi_bytes;            // per epilogue group
   int tmem_cols;
+  // split operands stored as [hi | lo] (seg elements each) and contracted as three products: virtual
+  // k-block v takes real k-block v / 3 of (A hi, B hi), (A lo, B hi), (A hi, B lo) for v % 3 = 0, 1, 2
+  int il3, seg;
 };
 
 struct Params {
@@ -410,8 +413,14 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
           if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
           uint8_t* sa = smem + (size_t)stage * stage_bytes;
           mbar_expect_tx(&full[stage], (uint32_t)stage_bytes);
-          tma_load_2d(sa, &mapA, &full[stage], kb * kBK, mt * g.m_step);
-          tma_load_2d(sa + kStageA, &mapB, &full[stage], kb * kBK, nt * g.n_step);
+          int ka = kb * kBK, kbb = kb * kBK;
+          if (g.il3) {
+            const int j = kb / 3, sv = kb - 3 * j;
+            ka = (sv == 1 ? g.seg : 0) + j * kBK;
+            kbb = (sv == 2 ? g.seg : 0) + j * kBK;
+          }
+          tma_load_2d(sa, &mapA, &full[stage], ka, mt * g.m_step);
+          tma_load_2d(sa + kStageA, &mapB, &full[stage], kbb, nt * g.n_step);
           if (++stage == g.stages) { stage = 0; ph ^= 1u; }
         }
       }
@@ -700,18 +709,20 @@ __global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int
   }
 }
 
-// Ltilde binary64 [X][ncol][N] -> block rows (g, a) of nseg * kst bf16: A = [hi | lo | hi].
-__global__ void k_lrot_bf16(int X, int N, int ncol, int c0, int n, int kst, int nseg, const double* lrot,
+// Ltilde [ng][ncol][N] (gammas g0 .. g0 + ng - 1, binary64 or binary32) -> block rows (g, a) of
+// nseg * kst bf16: A = [hi | lo | hi].
+template <typename T>
+__global__ void k_lrot_bf16(int g0, int ng, int N, int ncol, int c0, int n, int kst, int nseg, const T* lrot,
                             __nv_bfloat16* out) {
   const int rowlen = nseg * kst;
-  const size_t total = (size_t)X * n * kst;
+  const size_t total = (size_t)ng * n * kst;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const size_t row = idx / kst;
     const int pp = (int)(idx % kst);
     const int g = (int)(row / n), a = (int)(row % n);
-    const double v = pp < N ? lrot[((size_t)g * ncol + c0 + a) * N + pp] : 0.0;
+    const double v = pp < N ? (double)lrot[((size_t)g * ncol + c0 + a) * N + pp] : 0.0;
     const __nv_bfloat16 hi = __double2bfloat16(v);
-    __nv_bfloat16* dst = out + row * rowlen + pp;
+    __nv_bfloat16* dst = out + ((size_t)g0 * n + row) * rowlen + pp;
     dst[0] = hi;
     if (nseg == 3) {
       dst[kst] = __double2bfloat16(v - (double)__bfloat162float(hi));
@@ -720,28 +731,41 @@ __global__ void k_lrot_bf16(int X, int N, int ncol, int c0, int n, int kst, int 
   }
 }
 
-// L binary64 [X][N][N] -> Lt rows pq of nseg * kx bf16 (gamma contiguous): B = [hi | hi | lo].
-__global__ void k_lt_bf16(int X, int NN, int kx, int nseg, const double* chol, __nv_bfloat16* out) {
-  const int rowlen = nseg * kx;
-  const size_t total = (size_t)NN * kx;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t pq = idx / kx;
-    const int g = (int)(idx % kx);
-    const double v = g < X ? chol[(size_t)g * NN + pq] : 0.0;
-    const __nv_bfloat16 hi = __double2bfloat16(v);
-    __nv_bfloat16* dst = out + pq * rowlen + g;
+// L [ng][NN] (gammas g0 .. g0 + ng - 1) -> columns g0 .. g0 + ng - 1 of the Lt rows pq, each row
+// [hi | lo] (kx elements per part; hi only when nseg = 1).  A 32-gamma x 64-pq tile is transposed
+// through shared memory so that both the reads (pq contiguous) and the writes (gamma contiguous)
+// are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lt_bf16(int g0, int ng, size_t NN, int kx, int nseg, const T* chol,
+                                                 __nv_bfloat16* out) {
+  __shared__ float tile[32][65];
+  const int nparts = nseg == 3 ? 2 : 1;
+  const size_t rowlen = (size_t)nparts * kx;
+  const size_t pq0 = (size_t)blockIdx.x * 64;
+  const int gt = blockIdx.y * 32;
+  for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+    const int gl = i / 64, c = i % 64;
+    const size_t pq = pq0 + c;
+    tile[gl][c] = (gt + gl < ng && pq < NN) ? (float)chol[(size_t)(gt + gl) * NN + pq] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+    const int c = i / 32, gl = i % 32;
+    const size_t pq = pq0 + c;
+    if (gt + gl >= ng || pq >= NN) continue;
+    const float v = tile[gl][c];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16* dst = out + pq * rowlen + g0 + gt + gl;
     dst[0] = hi;
-    if (nseg == 3) {
-      dst[kx] = hi;
-      dst[2 * kx] = __double2bfloat16(v - (double)__bfloat162float(hi));
-    }
+    if (nseg == 3) dst[kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 
-// VHS coefficients complex64 [W][X] -> rows (w, part) of nseg * kx bf16: A = [hi | lo | hi].
+// VHS coefficients complex64 [W][X] -> rows (w, part) of [hi | lo] bf16 (kx elements per part; hi
+// only when nseg = 1).
 __global__ void k_coef_bf16(int W, int X, int kx, int nseg, const float2* coef, __nv_bfloat16* out) {
   const int w = blockIdx.x;
-  const int rowlen = nseg * kx;
+  const int rowlen = (nseg == 3 ? 2 : 1) * kx;
   for (int idx = threadIdx.x; idx < 2 * kx; idx += blockDim.x) {
     const int part = idx / kx, g = idx % kx;
     float v = 0.f;
@@ -752,10 +776,7 @@ __global__ void k_coef_bf16(int W, int X, int kx, int nseg, const float2* coef, 
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     __nv_bfloat16* dst = out + ((size_t)w * 2 + part) * rowlen + g;
     dst[0] = hi;
-    if (nseg == 3) {
-      dst[kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
-      dst[2 * kx] = hi;
-    }
+    if (nseg == 3) dst[kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 
@@ -956,10 +977,11 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     cur = align256(cur + (size_t)W * 2 * b.n * st->nseg * st->kst * 2);
     st->nchunk += 4 * b.m_tiles;   // four exchange partial slots per M tile (one per epilogue warp)
   }
+  st->vparts = st->nseg == 3 ? 2 : 1;   // VHS operands stored [hi | lo] (see Geom::il3)
   st->off_lt = cur;
-  cur = align256(cur + (size_t)N * N * st->nseg * st->kx * 2);
+  cur = align256(cur + (size_t)N * N * st->vparts * st->kx * 2);
   st->off_coef = cur;
-  cur = align256(cur + (size_t)W * 2 * st->nseg * st->kx * 2);
+  cur = align256(cur + (size_t)W * 2 * st->vparts * st->kx * 2);
   st->vhs_m_tiles = (2 * W + kBM - 1) / kBM;
   st->vhs_n_tiles = (N * N + 255) / 256;
   st->pg = prop_geom(N, ncol);
@@ -1010,26 +1032,57 @@ int set_exchange_groups(TcState* st, char* tcbuf, int groups, int form) {
   return used;
 }
 
-afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* chol64, const double* lrot64,
-                     unsigned long long* launches, char* err, size_t errlen) {
+afqmc_status begin(TcState* st, cudaStream_t s, char* tcbuf, char* err, size_t errlen) {
   if (!encode_fn()) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled is not available from the driver");
     return AFQMC_ECUDA;
   }
-  // the Theta and coefficient operands are also written by the overlap and fields kernels, which
-  // leave the K padding untouched: clear it once
-  if (cudaMemsetAsync(tcbuf, 0, st->off_lt, s) != cudaSuccess ||
-      cudaMemsetAsync(tcbuf + st->off_coef, 0, (size_t)st->W * 2 * st->nseg * st->kx * 2, s) != cudaSuccess) {
-    snprintf(err, errlen, "tc prepare: clearing the operand buffers failed");
+  // every operand's K padding stays zero (the overlap and fields kernels, and the chunked loads
+  // below, write only the data columns): clear the exchange operands, L^T and the coefficients once
+  if (cudaMemsetAsync(tcbuf, 0, st->off_coef + (size_t)st->W * 2 * st->vparts * st->kx * 2, s) != cudaSuccess) {
+    snprintf(err, errlen, "tc set-up: clearing the operand buffers failed");
     return AFQMC_ECUDA;
   }
+  return AFQMC_OK;
+}
+
+template <typename T, typename TL>
+afqmc_status load_chunk(TcState* st, cudaStream_t s, char* tcbuf, int g0, int ng, const T* chol, const TL* lrot,
+                        unsigned long long* launches, char* err, size_t errlen) {
+  for (int b = 0; b < st->nblk; ++b) {
+    const BlockMaps& bm = st->blk[b];
+    if (bm.n == 0) continue;
+    k_lrot_bf16<TL><<<592, 256, 0, s>>>(g0, ng, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, lrot,
+                                         reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_l));
+    ++*launches;
+  }
+  const size_t NN = (size_t)st->N * st->N;
+  const dim3 grid((unsigned)((NN + 63) / 64), (unsigned)((ng + 31) / 32));
+  k_lt_bf16<T><<<grid, 256, 0, s>>>(g0, ng, NN, st->kx, st->nseg, chol,
+                                     reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt));
+  ++*launches;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "tc set-up chunk: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+template afqmc_status load_chunk<double, double>(TcState*, cudaStream_t, char*, int, int, const double*,
+                                                 const double*, unsigned long long*, char*, size_t);
+template afqmc_status load_chunk<float, float>(TcState*, cudaStream_t, char*, int, int, const float*, const float*,
+                                               unsigned long long*, char*, size_t);
+template afqmc_status load_chunk<double, float>(TcState*, cudaStream_t, char*, int, int, const double*, const float*,
+                                                unsigned long long*, char*, size_t);
+template afqmc_status load_chunk<float, double>(TcState*, cudaStream_t, char*, int, int, const float*, const double*,
+                                                unsigned long long*, char*, size_t);
+
+afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen) {
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
     if (bm.n == 0) continue;
-    __nv_bfloat16* l = reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_l);
-    k_lrot_bf16<<<592, 256, 0, s>>>(st->X, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, lrot64, l);
-    ++*launches;
-    if (!make_map(&bm.map_l, l, (unsigned long long)st->X * bm.n, (unsigned long long)st->nseg * st->kst, kBM) ||
+    if (!make_map(&bm.map_l, tcbuf + bm.off_l, (unsigned long long)st->X * bm.n,
+                  (unsigned long long)st->nseg * st->kst, kBM) ||
         !make_map(&bm.map_th, tcbuf + bm.off_th, (unsigned long long)st->W * 2 * bm.n,
                   (unsigned long long)st->nseg * st->kst, (unsigned)bm.bn)) {
       snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the exchange operands");
@@ -1037,24 +1090,16 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
     }
   }
   __nv_bfloat16* lt = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt);
-  k_lt_bf16<<<1184, 256, 0, s>>>(st->X, st->N * st->N, st->kx, st->nseg, chol64, lt);
-  ++*launches;
-  if (!make_map(&st->map_lt, lt, (unsigned long long)st->N * st->N, (unsigned long long)st->nseg * st->kx, 256) ||
-      !make_map(&st->map_coef, tcbuf + st->off_coef, (unsigned long long)st->W * 2,
-                (unsigned long long)st->nseg * st->kx, kBM)) {
+  const unsigned long long vk = (unsigned long long)st->vparts * st->kx;
+  if (!make_map(&st->map_lt, lt, (unsigned long long)st->N * st->N, vk, 256) ||
+      !make_map(&st->map_coef, tcbuf + st->off_coef, (unsigned long long)st->W * 2, vk, kBM)) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS operands");
     return AFQMC_ECUDA;
   }
   if (st->pg.ok &&
-      (!make_map(&st->map_lt_a, lt, (unsigned long long)st->N * st->N, (unsigned long long)st->nseg * st->kx, kBM) ||
-       !make_map(&st->map_coef_b, tcbuf + st->off_coef, (unsigned long long)st->W * 2,
-                 (unsigned long long)st->nseg * st->kx, (unsigned)st->vhs_bn))) {
+      (!make_map(&st->map_lt_a, lt, (unsigned long long)st->N * st->N, vk, kBM) ||
+       !make_map(&st->map_coef_b, tcbuf + st->off_coef, (unsigned long long)st->W * 2, vk, (unsigned)st->vhs_bn))) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS plane operands");
-    return AFQMC_ECUDA;
-  }
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    snprintf(err, errlen, "tc prepare: %s", cudaGetErrorString(e));
     return AFQMC_ECUDA;
   }
   // reserve the kernels' shared memory now (not while a stream is being captured)
@@ -1070,6 +1115,11 @@ afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* cho
       cudaFuncSetAttribute(k_exch_tm<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_exch_tm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
     snprintf(err, errlen, "tcgen05 GEMM: cannot reserve shared memory");
+    return AFQMC_ECUDA;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "tc set-up: %s", cudaGetErrorString(e));
     return AFQMC_ECUDA;
   }
   st->ready = true;
@@ -1165,6 +1215,8 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   g.n_tiles = (2 * st->W + st->vhs_bn - 1) / st->vhs_bn;
   g.k_blocks = st->nseg * st->kx / kBK;
   g.k_steps = st->nseg * st->kx / 16;
+  g.il3 = st->nseg == 3 ? 1 : 0;
+  g.seg = st->kx;
   g.m_step = kBM;
   g.n_step = st->vhs_bn;
   g.bn = st->vhs_bn;
@@ -1194,6 +1246,8 @@ afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, f
   g.n_tiles = st->vhs_n_tiles;
   g.k_blocks = st->nseg * st->kx / kBK;
   g.k_steps = st->nseg * st->kx / 16;
+  g.il3 = st->nseg == 3 ? 1 : 0;
+  g.seg = st->kx;
   g.m_step = kBM;
   g.n_step = 256;
   g.bn = 256;

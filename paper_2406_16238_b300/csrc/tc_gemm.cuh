@@ -1,9 +1,11 @@
 // Tensor-core (tcgen05 + TMA) contractions for the BF16 and BF16x3 forms.
 //
 // Operands are bf16, K-major (the contracted index contiguous), rows padded to a
-// multiple of 64 elements with zeros.  BF16x3 stores the split operands
-// concatenated along K, A = [hi | lo | hi] and B = [hi | hi | lo], so one
-// bf16 GEMM with three times the K accumulates hi*hi + lo*hi + hi*lo in fp32.
+// multiple of 64 elements with zeros.  BF16x3 accumulates hi*hi + lo*hi + hi*lo
+// in fp32: the exchange operands are stored concatenated along K, A = [hi | lo |
+// hi] and B = [hi | hi | lo], so one bf16 GEMM with three times the K forms the
+// sum; the VHS operands (L^T, the coefficients) are stored once as [hi | lo] and
+// the kernel's producer picks the part of each operand per K block.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -54,6 +56,7 @@ struct TcState {
   BlockMaps blk[2];
   // VHS build
   int kx = 0;         // padded naux (multiple of 64)
+  int vparts = 1;     // stored parts of the VHS operands: [hi | lo] (BF16x3) or hi (BF16)
   size_t off_lt = 0, off_coef = 0;
   int vhs_m_tiles = 0, vhs_n_tiles = 0;
   int vhs_bn = 256;   // N tile of the VHS planes GEMM (multiple of 32)
@@ -75,10 +78,15 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
 // the walker tiling and the Theta tensor map; returns the groups in use for block 0.
 int set_exchange_groups(TcState* st, char* tcbuf, int groups, int form = 0);
 
-// One-time bf16 copies of Ltilde (from binary64 [X][ncol][N]) and of L^T (from binary64 [X][N][N]),
-// and the TMA descriptors over the tc buffer.
-afqmc_status prepare(TcState* st, cudaStream_t s, char* tcbuf, const double* chol64, const double* lrot64,
-                     unsigned long long* launches, char* err, size_t errlen);
+// Set-up of the tensor-core operands, which arrive in chunks of Cholesky vectors: begin clears the
+// operand buffers (their K padding must stay zero); load_chunk writes the bf16 copies of Ltilde
+// (from [ng][ncol][N]) and of L^T (from [ng][N][N]) for gammas g0 .. g0 + ng - 1; finish builds the
+// TMA descriptors over the tc buffer and reserves the kernels' shared memory.
+afqmc_status begin(TcState* st, cudaStream_t s, char* tcbuf, char* err, size_t errlen);
+template <typename T, typename TL>
+afqmc_status load_chunk(TcState* st, cudaStream_t s, char* tcbuf, int g0, int ng, const T* chol, const TL* lrot,
+                        unsigned long long* launches, char* err, size_t errlen);
+afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen);
 
 // N(0,1) fields of the step counter *step (stream 0) for W walker slots x X into x[w][g]; drawn by
 // a spare warp of the exchange kernel, whose binary64 pipe is otherwise idle.

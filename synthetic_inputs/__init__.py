@@ -21,6 +21,7 @@ method, and any determinant would do for parity.
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import numpy as np
 
@@ -182,3 +183,115 @@ def config_batched(nsys=32, seed_offset=4, nmin=50, nmax=300):
         probs.append(make_problem(n, nocc, nocc, 4 * n, 0.4 * n, BASE_SEED + 1000 + i, orthogonalise=False,
                                   scf_iterations=0, name=f"sys{i}_N{n}"))
     return probs
+
+
+# --- the large system (1512 orbitals, 42 + 42 electrons, naux = 7560) ---------------------------
+# Its Cholesky tensor (69 GB in binary32) is never materialised on the host.  Each entry comes from
+# a counter-based integer hash of (gamma, min(p, q), max(p, q)), so any chunk of gammas can be drawn
+# on its own, on the CPU (numpy) or on the GPU (torch), with identical bits:
+#   u = (hash + 1/2) 2^-31 - 1 in (-1, 1),   L^g_pq = s_g u,   s_g = exp(-g / tau) sqrt(3) / N,
+# s_g being exp(-g/tau) over the expected Frobenius norm (N / sqrt 3) of an N x N matrix of such u
+# (so ||L^g||_F ~ exp(-g / tau), with no reduction needed).  The hash is 32-bit integer mixing
+# (xor-shift and multiply by 0x45d9f3b, twice) in int64 arithmetic that never overflows.
+
+_M32 = 0xFFFFFFFF
+_MIX = 0x45D9F3B
+
+
+def _mix32(x, xp):
+    x = ((x >> 16) ^ x) * _MIX & _M32
+    x = ((x >> 16) ^ x) * _MIX & _M32
+    return (x >> 16) ^ x
+
+
+def _chol_hash(key, seed, xp):
+    """32-bit hash of the int64 entry keys (numpy or torch arrays)."""
+    hi = _mix32((key >> 32) + (seed & _M32), xp)
+    return _mix32((key & _M32) ^ hi, xp)
+
+
+def large_chol_scales(naux, norb, tau):
+    return [math.exp(-g / tau) * math.sqrt(3.0) / norb for g in range(naux)]
+
+
+def large_chol_chunk(g0, ng, norb, tau, seed, dtype=np.float32, device=None):
+    """Cholesky vectors g0 .. g0 + ng - 1 of the large synthetic system, [ng, norb, norb].
+
+    device None: a numpy array (CPU); else a torch tensor drawn on that device (same bits)."""
+    sc = large_chol_scales(g0 + ng, norb, tau)[g0:]
+    if device is None:
+        from concurrent.futures import ThreadPoolExecutor
+        idx = np.arange(norb, dtype=np.int64)
+        pair = np.minimum(idx[:, None], idx[None, :]) * norb + np.maximum(idx[:, None], idx[None, :])
+        out = np.empty((ng, norb, norb), dtype=dtype)
+
+        def one(k):   # numpy releases the GIL in these array operations
+            key = np.int64(g0 + k) * (norb * norb) + pair
+            h = _chol_hash(key, seed, np)
+            u = (h.astype(np.float64) + 0.5) * 2.0 ** -31 - 1.0
+            out[k] = (sc[k] * u).astype(dtype)
+
+        with ThreadPoolExecutor(max_workers=min(16, max(1, ng))) as ex:
+            list(ex.map(one, range(ng)))
+        return out
+    import torch
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    idx = torch.arange(norb, dtype=torch.int64, device=device)
+    pair = torch.minimum(idx[:, None], idx[None, :]) * norb + torch.maximum(idx[:, None], idx[None, :])
+    out = torch.empty((ng, norb, norb), dtype=tdt, device=device)
+    scales = torch.tensor(sc, dtype=torch.float64, device=device)
+    for k in range(ng):
+        key = (g0 + k) * (norb * norb) + pair
+        h = _chol_hash(key, seed, torch)
+        u = (h.to(torch.float64) + 0.5) * 2.0 ** -31 - 1.0
+        out[k] = (scales[k] * u).to(tdt)
+    return out
+
+
+@dataclasses.dataclass
+class LargeProblem:
+    """The large system without its Cholesky tensor: chunks come from large_chol_chunk."""
+
+    h1e: np.ndarray
+    ecore: float
+    nalpha: int
+    nbeta: int
+    psiT: np.ndarray
+    naux: int
+    tau: float
+    seed: int
+    name: str = ""
+
+    @property
+    def norb(self) -> int:
+        return self.h1e.shape[0]
+
+    def chunks(self, size, dtype=np.float32, device=None, naux=None):
+        """Iterator over [size, N, N] chunks of the first naux (default all) vectors."""
+        total = self.naux if naux is None else naux
+        for g0 in range(0, total, size):
+            yield large_chol_chunk(g0, min(size, total - g0), self.norb, self.tau, self.seed, dtype, device)
+
+    def dense(self, naux=None, dtype=np.float64):
+        """The first naux vectors as one host array (small naux only)."""
+        total = self.naux if naux is None else naux
+        return large_chol_chunk(0, total, self.norb, self.tau, self.seed, dtype)
+
+
+def config_large(naux=7560, seed_offset=3):
+    """N=1512, 42a+42b, naux=7560 (tau = naux/10), UHF trial: the benzene-dimer aug-cc-pVQZ shape.
+
+    The trial is the core guess (the 42 lowest eigenvectors of h1e; beta with its HOMO and LUMO
+    mixed by pi/4, which breaks the spin symmetry): 20 Roothaan iterations would need exchange
+    builds over the whole 69 GB tensor.  naux below 7560 gives the same system truncated to its
+    first naux vectors (tau stays 756), for checks against the oracle."""
+    norb, nocc, full = 1512, 42, 7560
+    seed = BASE_SEED + seed_offset
+    rng = np.random.default_rng(seed)
+    h1e = one_body(rng, norb)
+    _, c = np.linalg.eigh(h1e)
+    ca, cb = c[:, :nocc].copy(), c[:, :nocc + 1].copy()
+    h, l = cb[:, nocc - 1].copy(), cb[:, nocc].copy()
+    cb[:, nocc - 1] = (h + l) / np.sqrt(2.0)
+    psiT = np.ascontiguousarray(np.hstack([ca, cb[:, :nocc]]))
+    return LargeProblem(h1e, 1.5, nocc, nocc, psiT, naux, full / 10.0, seed, name=f"N1512_n42_X{naux}")
