@@ -137,7 +137,7 @@ Layout plan(const Dims& d) {
   L.vhs_bytes = W * N * N * C;
   // staging of at least one gamma: a host chunk's copy (binary64), its cast for the set-up GEMMs and
   // the chunk's Ltilde (binary64)
-  L.stage_bytes = align_up(N * N * 8, 256) * 2 + align_up(nc * N * 8, 256);
+  L.stage_bytes = align_up(N * N * 8, 256) * 2 + align_up(nc * N * 8, 256) + 1024;
   L.stage_bytes_avail = std::max(L.vhs_bytes, L.stage_bytes);
   L.vhs = take(L.stage_bytes_avail);
   L.stage = L.vhs;
@@ -912,7 +912,8 @@ afqmc_status setup_add(afqmc_ctx* c, int g0, int ng, const T* chol, bool on_devi
   const size_t NN = (size_t)d.N * d.N;
   const size_t per = (on_device ? 0 : align_up(NN * sizeof(T), 256)) + align_up(NN * 8, 256) +
                      align_up((size_t)d.ncol * d.N * 8, 256);
-  const size_t cap = std::max<size_t>(1, c->L.stage_bytes_avail / per);
+  // 1024 bytes of slack cover the 256-byte alignment of the three staged arrays
+  const size_t cap = std::max<size_t>(1, (c->L.stage_bytes_avail - 1024) / per);
   for (int a = 0; a < ng; a += (int)cap) {
     const int n = (int)std::min<size_t>(cap, (size_t)(ng - a));
     const T* part = chol + (size_t)a * NN;
