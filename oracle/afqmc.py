@@ -18,7 +18,7 @@ Conventions (the paper's notation; readings where it is silent are marked R#):
   exp(+sqrt(dt) x.vbar) is the scalar exp(c_mf), c_mf = i sqrt(dt) x.lbar.
 * R2 exp(VHS) is the Taylor series to order p (default 6); exp(-dt/2 h_eff)
   is exact (eigendecomposition).
-* Overlap <Psi_T|psi> = prod_s det(Phi_s^T psi_s) (Phi real); the log is
+* Overlap <Psi_T|psi> = prod_s det(Phi_s^+ psi_s) (Phi_s^+ = Phi_s^T for a real trial); the log is
   carried as log|det| + i arg(det), arg wrapped to (-pi, pi].
 * Green's function G_pq = <a+_p a_q> = [Theta Phi^T]_qp with
   Theta = psi (Phi^T psi)^-1 (the trial's calc_greens_function, Section
@@ -86,33 +86,61 @@ class Setup:
     evar: float
 
 
+def hc(a):
+    """Conjugate transpose (the plain transpose for real arrays)."""
+    return np.conj(a).T
+
+
 def trial_density(phi):
-    """P = Phi (Phi^T Phi)^-1 Phi^T, the trial's one-particle density (per spin)."""
+    """P = Phi (Phi^+ Phi)^-1 Phi^+, the trial's one-particle density (per spin)."""
     if phi.shape[1] == 0:
         return np.zeros((phi.shape[0], phi.shape[0]))
-    return phi @ np.linalg.inv(phi.T @ phi) @ phi.T
+    return phi @ np.linalg.inv(hc(phi) @ phi) @ hc(phi)
+
+
+def hermitian_fields(chol):
+    """Complex Cholesky vectors (Section "Support of complex Cholesky vectors"): from X complex L^g with
+    g_psqr = sum_g L^g_ps conj(L^g_rq), the 2X Hermitian one-body matrices of the auxiliary fields,
+    A^g = (L^g + L^g+) / 2 and B^g = i (L^g - L^g+) / 2, in the order A^0, B^0, A^1, B^1, ...
+
+    With the electron-exchange symmetry (ps|qr) = (qr|ps), sum_g L_g L_g+ = sum_g L_g+ L_g as Fock-space
+    operators, so the two-body part 1/2 sum_g L_g L_g+ (less its one-body normal-ordering term) equals
+    1/2 sum_g (A_g^2 + B_g^2): twice as many fields, each a Hermitian matrix that takes the place of a
+    real symmetric L^g in every formula below."""
+    chol = np.asarray(chol, dtype=np.complex128)
+    out = np.empty((2 * chol.shape[0],) + chol.shape[1:], dtype=np.complex128)
+    for g in range(chol.shape[0]):
+        lh = hc(chol[g])
+        out[2 * g] = 0.5 * (chol[g] + lh)
+        out[2 * g + 1] = 0.5j * (chol[g] - lh)
+    return out
 
 
 def build_setup(h1e, chol, ecore, nalpha, nbeta, psiT, dt) -> Setup:
-    """Set-up quantities of Eqs. 4-6 and the mean-field shift of Eq. 12 (reading R1)."""
-    h1e = np.asarray(h1e, dtype=np.float64)
-    chol = np.asarray(chol, dtype=np.float64)
+    """Set-up quantities of Eqs. 4-6 and the mean-field shift of Eq. 12 (reading R1).
+
+    chol holds the fields' one-body matrices: real symmetric L^g, or (complex Hamiltonians) the
+    Hermitian matrices of hermitian_fields; h1e and psiT may then be complex (h1e Hermitian)."""
+    cplx = np.iscomplexobj(h1e) or np.iscomplexobj(chol) or np.iscomplexobj(psiT)
+    dtype = np.complex128 if cplx else np.float64
+    h1e = np.asarray(h1e, dtype=dtype)
+    chol = np.asarray(chol, dtype=dtype)
     naux, norb, _ = chol.shape
-    phi_a = np.asarray(psiT[:, :nalpha], dtype=np.float64)
-    phi_b = np.asarray(psiT[:, nalpha:nalpha + nbeta], dtype=np.float64)
+    phi_a = np.asarray(psiT[:, :nalpha], dtype=dtype)
+    phi_b = np.asarray(psiT[:, nalpha:nalpha + nbeta], dtype=dtype)
     p_tot = trial_density(phi_a) + trial_density(phi_b)
-    # lbar_g = Tr(L^g (P_a + P_b)); <v_g>_T = i lbar_g
-    lbar = np.array([np.sum(chol[g] * p_tot.T) for g in range(naux)])
+    # lbar_g = Tr(L^g (P_a + P_b)) (real: both Hermitian); <v_g>_T = i lbar_g
+    lbar = np.array([np.sum(chol[g] * p_tot.T).real for g in range(naux)])
     # v0 = h - 1/2 sum_r (pr|rq) (Eq. 5); (pr|rq) = sum_g L^g_pr L^g_rq
     v0 = h1e - 0.5 * sum(chol[g] @ chol[g] for g in range(naux))
     heff = v0 + sum(lbar[g] * chol[g] for g in range(naux))
     evals, evecs = np.linalg.eigh(heff)
-    expm_half = (evecs * np.exp(-0.5 * dt * evals)[None, :]) @ evecs.T
+    expm_half = (evecs * np.exp(-0.5 * dt * evals)[None, :]) @ hc(evecs)
     ecore_mf = float(ecore - 0.5 * np.dot(lbar, lbar))
-    lrot_a = np.stack([phi_a.T @ chol[g] for g in range(naux)]) if nalpha else np.zeros((naux, 0, norb))
-    lrot_b = np.stack([phi_b.T @ chol[g] for g in range(naux)]) if nbeta else np.zeros((naux, 0, norb))
+    lrot_a = np.stack([hc(phi_a) @ chol[g] for g in range(naux)]) if nalpha else np.zeros((naux, 0, norb), dtype)
+    lrot_b = np.stack([hc(phi_b) @ chol[g] for g in range(naux)]) if nbeta else np.zeros((naux, 0, norb), dtype)
     st = Setup(norb, naux, nalpha, nbeta, float(dt), h1e, chol, float(ecore), phi_a, phi_b,
-               lbar, heff, expm_half, ecore_mf, lrot_a, lrot_b, phi_a.T @ h1e, phi_b.T @ h1e, 0.0)
+               lbar, heff, expm_half, ecore_mf, lrot_a, lrot_b, hc(phi_a) @ h1e, hc(phi_b) @ h1e, 0.0)
     psi0 = np.asarray(psiT, dtype=np.complex128)
     _, th_a, th_b = overlap_theta(st, psi0)
     st.evar = float(local_energy(st, th_a, th_b)[0].real)
@@ -137,7 +165,7 @@ def log_det(a):
 
 
 def overlap_theta(st: Setup, psi):
-    """log <Psi_T|psi> and Theta^s = psi^s (Phi^sT psi^s)^-1 for both spins."""
+    """log <Psi_T|psi> and Theta^s = psi^s (Phi^s+ psi^s)^-1 for both spins."""
     pa, pb = split_spins(st, psi)
     out = []
     logo = 0.0 + 0.0j
@@ -145,7 +173,7 @@ def overlap_theta(st: Setup, psi):
         if p.shape[1] == 0:
             out.append(np.zeros_like(p))
             continue
-        a = phi.T @ p
+        a = hc(phi) @ p
         ld = log_det(a)
         logo = logo + ld
         out.append(np.linalg.solve(a.T, p.T).T)
@@ -153,8 +181,8 @@ def overlap_theta(st: Setup, psi):
 
 
 def greens_function(phi, theta):
-    """G_pq = <a+_p a_q> = [Theta Phi^T]_qp for one spin."""
-    return (theta @ phi.T).T
+    """G_pq = <a+_p a_q> = [Theta Phi^+]_qp for one spin."""
+    return (theta @ hc(phi)).T
 
 
 def force_bias(st: Setup, th_a, th_b):

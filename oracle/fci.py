@@ -119,5 +119,11 @@ def eri_from_cholesky(chol):
     return np.einsum("gps,gqr->psqr", chol, chol)
 
 
+def eri_from_complex_cholesky(chol):
+    """g_psqr = (ps|qr) = sum_gamma L^g_ps conj(L^g_rq) for complex Cholesky vectors (the pair matrix
+    (ps),(rq) is Hermitian positive semidefinite); equals eri_from_cholesky for real symmetric L."""
+    return np.einsum("gps,grq->psqr", chol, np.conj(chol))
+
+
 def expm(mat):
     return scipy.linalg.expm(mat)

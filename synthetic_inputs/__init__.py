@@ -163,6 +163,33 @@ def tiny_problem(norb=4, nalpha=2, nbeta=2, naux=6, tau=3.0, seed=7, unrestricte
                         ecore=ecore, orthogonalise=True)
 
 
+def make_complex_problem(norb, nalpha, nbeta, npairs, tau, seed, unrestricted=False, ecore=0.9, name=""):
+    """A complex Hamiltonian (as with Bloch orbitals or a magnetic field): h1e complex Hermitian (the
+    real ramp plus Hermitian complex noise) and 2 npairs complex Cholesky vectors, K_k and K_k^+ for
+    random complex K_k scaled by exp(-k / tau) / ||K_k||_F.  A set closed under the conjugate transpose
+    gives an ERI g_psqr = sum_g L^g_ps conj(L^g_rq) with the electron-exchange symmetry (ps|qr) = (qr|ps)
+    of true integrals.  The trial is the core guess (lowest eigenvectors of h1e, complex), beta with its
+    HOMO and LUMO mixed by pi/4 when unrestricted."""
+    rng = np.random.default_rng(seed)
+    h = np.diag(np.linspace(0.0, 4.0, norb)).astype(np.complex128)
+    off = 0.1 * (rng.standard_normal((norb, norb)) + 1j * rng.standard_normal((norb, norb)))
+    off = np.triu(off, 1)
+    h1e = np.ascontiguousarray(h + off + off.conj().T)
+    chol = np.empty((2 * npairs, norb, norb), dtype=np.complex128)
+    for k in range(npairs):
+        a = rng.standard_normal((norb, norb)) + 1j * rng.standard_normal((norb, norb))
+        a *= math.exp(-k / tau) / np.linalg.norm(a)
+        chol[2 * k] = a
+        chol[2 * k + 1] = a.conj().T
+    _, c = np.linalg.eigh(h1e)
+    ca, cb = c[:, :nalpha].copy(), c.copy()
+    if unrestricted and 0 < nbeta < norb:
+        hh, ll = cb[:, nbeta - 1].copy(), cb[:, nbeta].copy()
+        cb[:, nbeta - 1] = (hh + ll) / np.sqrt(2.0)
+    psiT = np.ascontiguousarray(np.hstack([ca, cb[:, :nbeta]]))
+    return Problem(h1e, np.ascontiguousarray(chol), float(ecore), nalpha, nbeta, psiT, name)
+
+
 def random_walkers(rng, norb, ncols, nwalkers, spread=0.3, psiT=None):
     """Complex determinants near psiT (or random), for kernel-level parity cases."""
     base = psiT if psiT is not None else rng.standard_normal((norb, ncols))
