@@ -685,12 +685,14 @@ def large_rooflines(prec, norb, nblocks, nocc, naux, nw, stages):
     ncol = nblocks * nocc
     exch = nblocks * exchange_flops_per_walker(norb, nocc, naux) * nw
     prop = (2 * (2 * 2 * norb * norb * ncol) + 6 * 8 * norb * norb * ncol) * nw
-    vhs_bytes = parts * norb * norb * kx * 2 + nw * 2 * parts * kx * 2 + nw * 4 * norb * norb * 2
+    # L^T holds the packed upper triangle (N (N + 1) / 2 rows) where N > 128; the V planes are written whole
+    rows = norb * (norb + 1) // 2 if norb > 128 else norb * norb
+    vhs_bytes = parts * rows * kx * 2 + nw * 2 * parts * kx * 2 + nw * 4 * norb * norb * 2
     work = {"exchange": (exch, "tensor", tpeak, "TFLOP/s", 1e12, tnote),
             "propagate": (prop, "tensor", tpeak, "TFLOP/s", 1e12, tnote),
             "vhs": (vhs_bytes, "hbm", peaks["hbm_gbs"], "GB/s", 1e9,
-                    f"HBM copy bandwidth ({src}); bytes = L^T bf16 {'hi + lo' if parts == 2 else 'hi'} read once, "
-                    "coefficients, V planes written")}
+                    f"HBM copy bandwidth ({src}); bytes = packed L^T bf16 {'hi + lo' if parts == 2 else 'hi'} read "
+                    "once, coefficients, V planes written")}
     out = {}
     for k, (amount, bound, peak, unit, scale, note) in work.items():
         ms, cnt = stages.get(k, (0.0, 0))

@@ -1730,6 +1730,8 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t) {
   if (!t || (t->tile_cap != 1 && t->tile_cap != 2 && t->tile_cap != 4)) return fail(AFQMC_EINVAL, "tuning: tile_cap 1, 2 or 4");
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->drop_graphs();
+  if (ctx->d.tensor() && ctx->tcs.packed && t->prop_path != 0)
+    return fail(AFQMC_EINVAL, "tuning: with packed L^T (norb > 128) only the tensor-core propagation (prop_path 0) runs");
   ctx->tile_cap = t->tile_cap;
   ctx->prop_path = (t->prop_path >= 0 && t->prop_path <= 2) ? t->prop_path : 0;
   ctx->prop_tile = (t->prop_tile >= 0 && t->prop_tile <= 2) ? t->prop_tile : 0;
@@ -1773,6 +1775,7 @@ afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen)
       if (tc_ok)
         for (int form : {0, 1})
           if (form == 0 || (tc_cap == 4 && d.prec == AFQMC_PREC_BF16X3)) cands.push_back(afqmc_tuning{tc_cap, 0, g, 0, form, 0.f});
+      if (d.tensor() && ctx->tcs.packed) continue;   // packed L^T: the tensor-core propagation only
       if (fused_ok)
         for (int pt : {0, 1, 2}) cands.push_back(afqmc_tuning{tc_cap, 2, g, pt, 0, 0.f});
       cands.push_back(afqmc_tuning{tc_cap, 1, g, 0, 0, 0.f});

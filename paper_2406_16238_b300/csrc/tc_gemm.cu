@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "tc_gemm.cuh"
@@ -36,10 +37,32 @@ struct Geom {
   int stages, epi_groups;
   int epi_bytes;            // per epilogue group
   int tmem_cols;
-  // split operands stored as [hi | lo] (seg elements each) and contracted as three products: virtual
+  // il3: split operands stored as [hi | lo] (seg elements each), one operand tile per stage: virtual
   // k-block v takes real k-block v / 3 of (A hi, B hi), (A lo, B hi), (A hi, B lo) for v % 3 = 0, 1, 2
+  // (twice the stages of the dual form, for operands streamed from HBM)
   int il3, seg;
+  // dual: every stage holds the hi and lo parts of both operands of one real k-block (A hi at column
+  // 0, A lo at a_lo, B hi at b_hi, B lo at b_lo, plus kb * 64) and each 16-wide k-step issues the
+  // three split products, so each operand byte crosses shared memory once (k_blocks, k_steps: real)
+  int dual, a_lo, b_hi, b_lo;
+  int stage_bytes;
+  // tile order: 0: M tiles fastest; ntg > 0: groups of ntg N tiles, M tiles in turn within a group,
+  // N tiles fastest (concurrent CTAs share A tiles; a group's B tiles stay in L2)
+  int ntg;
 };
+
+__host__ __device__ __forceinline__ void tile_mn(const Geom& g, int t, int* mt, int* nt) {
+  if (g.ntg <= 0) {
+    *mt = t % g.m_tiles;
+    *nt = t / g.m_tiles;
+    return;
+  }
+  const int per = g.m_tiles * g.ntg;
+  const int grp = t / per, rem = t - grp * per;
+  const int nsz = g.n_tiles - grp * g.ntg < g.ntg ? g.n_tiles - grp * g.ntg : g.ntg;
+  *mt = rem / nsz;
+  *nt = grp * g.ntg + (rem - (rem / nsz) * nsz);
+}
 
 struct Params {
   Geom g;
@@ -56,6 +79,7 @@ struct Params {
   // bf16 plane epilogue
   __nv_bfloat16* planes;
   int npad, kq;   // plane rows, plane row pitch (elements)
+  const int* pairs;   // packed L^T: p N + q of each packed row (p <= q), or NULL (rows are pq)
   // exchange: an extra warp draws the step's normals (nrm.x != nullptr)
   NormalsJob nrm;
   // exchange with the Ltilde tile in tensor memory: segment length and the tensor-memory column of
@@ -308,11 +332,15 @@ __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int g
 // Tile rows are pq = p N + q (M over N^2), columns are (w, part) = 2 w + part.  Each value is
 // split into hi = bf16(v), lo = bf16(v - hi) and written to the plane
 // [w][hi re, hi im, lo re, lo im][npad][kq] at (p, q).  Consecutive lanes hold consecutive pq,
-// so every store instruction covers a contiguous run of q.
+// so every store instruction covers a contiguous run of q.  With packed L^T the rows are the pairs
+// p <= q (row-major over the upper triangle; out_cols = their count) and each value is also
+// written at (q, p): V is symmetric because every L^g is.
 __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
-  const int pq = mt * kBM + r;
-  const bool live = pq < p.out_cols;
-  const int pp = live ? pq / p.n : 0, qq = live ? pq - pp * p.n : 0;
+  const int row = mt * kBM + r;
+  const bool live = row < p.out_cols;
+  const int pq = live ? (p.pairs ? p.pairs[row] : row) : 0;
+  const int pp = pq / p.n, qq = pq - pp * p.n;
+  const bool mirror = p.pairs != nullptr && pp != qq;
   const int ncols = p.g.bn / p.g.epi_groups;   // a multiple of 8
   const int cbeg = group * ncols;
   const size_t plane = (size_t)p.npad * p.kq;
@@ -320,10 +348,17 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
     for (int i = 0; i < cnt; ++i) {
       const int col = nt * p.g.n_step + c + i;
       if (col >= p.out_rows) break;
-      __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * p.kq + qq;
+      __nv_bfloat16* base = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane;
+      __nv_bfloat16* dst = base + (size_t)pp * p.kq + qq;
       const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
       dst[0] = hi;
-      dst[2 * plane] = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
+      dst[2 * plane] = lo;
+      if (mirror) {
+        __nv_bfloat16* tr = base + (size_t)qq * p.kq + pp;
+        tr[0] = hi;
+        tr[2 * plane] = lo;
+      }
     }
   };
   float v[16];
@@ -367,7 +402,7 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const Geom& g = p.g;
-  const int stage_bytes = kStageA + g.bn * kBK * 2;
+  const int stage_bytes = g.stage_bytes;
   uint8_t* epi_base = smem + (size_t)g.stages * stage_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + (size_t)g.epi_groups * g.epi_bytes);
   uint64_t* full = bars;
@@ -408,11 +443,21 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       uint32_t ph = 0;
       bool go = true;
       for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
-        const int mt = t % g.m_tiles, nt = t / g.m_tiles;
+        int mt, nt;
+        tile_mn(g, t, &mt, &nt);
         for (int kb = 0; kb < g.k_blocks; ++kb) {
           if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
           uint8_t* sa = smem + (size_t)stage * stage_bytes;
           mbar_expect_tx(&full[stage], (uint32_t)stage_bytes);
+          if (g.dual) {
+            const int kc = kb * kBK, ay = mt * g.m_step, by = nt * g.n_step;
+            tma_load_2d(sa, &mapA, &full[stage], kc, ay);
+            tma_load_2d(sa + kStageA, &mapA, &full[stage], g.a_lo + kc, ay);
+            tma_load_2d(sa + 2 * kStageA, &mapB, &full[stage], g.b_hi + kc, by);
+            tma_load_2d(sa + 2 * kStageA + g.bn * 128, &mapB, &full[stage], g.b_lo + kc, by);
+            if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+            continue;
+          }
           int ka = kb * kBK, kbb = kb * kBK;
           if (g.il3) {
             const int j = kb / 3, sv = kb - 3 * j;
@@ -442,11 +487,24 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
         for (int kb = 0; kb < g.k_blocks; ++kb) {
           if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes), sb = sa + kStageA;
+          const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+          if (g.dual) {
+            const uint32_t sal = sa + kStageA, sb = sa + 2 * kStageA, sbl = sb + (uint32_t)(g.bn * 128);
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k)
-            if (kb * (kBK / 16) + k < g.k_steps)
-              umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < kBK / 16; ++k)
+              if (kb * (kBK / 16) + k < g.k_steps) {
+                const uint64_t ah = sw128_desc(sa + 32 * k), bh = sw128_desc(sb + 32 * k);
+                umma_bf16(dtm, ah, bh, idesc, (kb | k) != 0 ? 1u : 0u);                  // A hi B hi
+                umma_bf16(dtm, sw128_desc(sal + 32 * k), bh, idesc, 1u);                // A lo B hi
+                umma_bf16(dtm, ah, sw128_desc(sbl + 32 * k), idesc, 1u);                // A hi B lo
+              }
+          } else {
+            const uint32_t sb = sa + kStageA;
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+              if (kb * (kBK / 16) + k < g.k_steps)
+                umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
+          }
           umma_commit(&empty[stage]);
           if (++stage == g.stages) { stage = 0; ph ^= 1u; }
         }
@@ -475,7 +533,8 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       if (!ok) break;
       tc_fence_after();
       const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
-      const int mt = t % g.m_tiles, nt = t / g.m_tiles;
+      int mt, nt;
+      tile_mn(g, t, &mt, &nt);
       if constexpr (EPI == 0 && NB > 0) exchange_tile_reg<NB>(p, mt, nt, tacc, es, group, wig, r, lane);
       else if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
       else if (EPI == 1) store_tile(p, mt, nt, tacc, group, r);
@@ -731,13 +790,14 @@ __global__ void k_lrot_bf16(int g0, int ng, int N, int ncol, int c0, int n, int 
   }
 }
 
-// L [ng][NN] (gammas g0 .. g0 + ng - 1) -> columns g0 .. g0 + ng - 1 of the Lt rows pq, each row
-// [hi | lo] (kx elements per part; hi only when nseg = 1).  A 32-gamma x 64-pq tile is transposed
+// L [ng][NN] (gammas g0 .. g0 + ng - 1) -> columns g0 .. g0 + ng - 1 of the Lt rows, each row
+// [hi | lo] (kx elements per part; hi only when nseg = 1).  Rows are pq, or with packed L^T the
+// pairs p <= q listed in `pairs`.  A 32-gamma x 64-pq tile is transposed
 // through shared memory so that both the reads (pq contiguous) and the writes (gamma contiguous)
 // are coalesced.
 template <typename T>
-__global__ void __launch_bounds__(256) k_lt_bf16(int g0, int ng, size_t NN, int kx, int nseg, const T* chol,
-                                                 __nv_bfloat16* out) {
+__global__ void __launch_bounds__(256) k_lt_bf16(int g0, int ng, size_t NN, size_t nrows, const int* pairs, int kx,
+                                                 int nseg, const T* chol, __nv_bfloat16* out) {
   __shared__ float tile[32][65];
   const int nparts = nseg == 3 ? 2 : 1;
   const size_t rowlen = (size_t)nparts * kx;
@@ -745,14 +805,15 @@ __global__ void __launch_bounds__(256) k_lt_bf16(int g0, int ng, size_t NN, int 
   const int gt = blockIdx.y * 32;
   for (int i = threadIdx.x; i < 32 * 64; i += 256) {
     const int gl = i / 64, c = i % 64;
-    const size_t pq = pq0 + c;
-    tile[gl][c] = (gt + gl < ng && pq < NN) ? (float)chol[(size_t)(gt + gl) * NN + pq] : 0.f;
+    const size_t row = pq0 + c;
+    const size_t src = row < nrows ? (pairs ? (size_t)pairs[row] : row) : 0;
+    tile[gl][c] = (gt + gl < ng && row < nrows) ? (float)chol[(size_t)(gt + gl) * NN + src] : 0.f;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 32 * 64; i += 256) {
     const int c = i / 32, gl = i % 32;
     const size_t pq = pq0 + c;
-    if (gt + gl >= ng || pq >= NN) continue;
+    if (gt + gl >= ng || pq >= nrows) continue;
     const float v = tile[gl][c];
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     __nv_bfloat16* dst = out + pq * rowlen + g0 + gt + gl;
@@ -845,7 +906,8 @@ bool exchange_reg(int n, int wpt, int bn) {
 bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
   g->epi_groups = epi_groups;
   g->epi_bytes = (epi_bytes_per_group + 15) & ~15;
-  const int stage_bytes = kStageA + g->bn * kBK * 2;
+  const int stage_bytes = g->dual ? 2 * kStageA + 2 * g->bn * kBK * 2 : kStageA + g->bn * kBK * 2;
+  g->stage_bytes = stage_bytes;
   const int fixed = 1024 + epi_groups * g->epi_bytes + kTailBytes;
   int st = (kMaxSmem - fixed) / stage_bytes;
   if (st > 4) st = 4;
@@ -856,7 +918,7 @@ bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
 }
 
 size_t smem_bytes(const Geom& g) {
-  return 1024 + (size_t)g.stages * (kStageA + g.bn * kBK * 2) + (size_t)g.epi_groups * g.epi_bytes + kTailBytes;
+  return 1024 + (size_t)g.stages * g.stage_bytes + (size_t)g.epi_groups * g.epi_bytes + kTailBytes;
 }
 
 template <int EPI, int NB = 0>
@@ -946,6 +1008,30 @@ void exchange_config(TcState* st, BlockMaps& bm, int groups, int form) {
       return;
     }
   }
+  bm.dual = 0;
+  if (st->nseg == 3 && st->kst >= 512) {
+    // long K (large N): load each k-block's hi and lo parts once (dual stages); the most walkers per
+    // tile, then the most epilogue groups, whose buffers fit beside two stages
+    for (int wpt = wpt0; wpt >= 1 && !bm.dual; --wpt)
+      for (int g = std::min(4, wpt); g >= 1; --g) {
+        if (wpt % g || (groups > 0 && g > groups)) continue;
+        const int bn = (wpt * 2 * n + 15) / 16 * 16;
+        const int stage = 2 * kStageA + 2 * bn * 128;
+        const int need = 1024 + g * ((epi_bytes_exchange(n, exchange_reg(n, wpt, bn)) + 15) & ~15) + kTailBytes +
+                         2 * stage;
+        if (need > kMaxSmem) continue;
+        bm.dual = 1;
+        bm.groups = g;
+        bm.wpt = wpt;
+        bm.bn = bn;
+        break;
+      }
+    if (bm.dual) {
+      bm.form = 0;
+      bm.n_tiles = (st->W + bm.wpt - 1) / bm.wpt;
+      return;
+    }
+  }
   bm.groups = gs;
   bm.wpt = wpt_streamed;
   bm.bn = (bm.wpt * 2 * n + 15) / 16 * 16;
@@ -977,20 +1063,28 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     cur = align256(cur + (size_t)W * 2 * b.n * st->nseg * st->kst * 2);
     st->nchunk += 4 * b.m_tiles;   // four exchange partial slots per M tile (one per epilogue warp)
   }
-  st->vparts = st->nseg == 3 ? 2 : 1;   // VHS operands stored [hi | lo] (see Geom::il3)
+  st->vparts = st->nseg == 3 ? 2 : 1;   // VHS operands stored [hi | lo] (see Geom::dual)
+  st->pg = prop_geom(N, ncol);
+  // packed L^T (the upper triangle p <= q only) where the large-form propagation consumes the V
+  // planes: the VHS GEMM then reads half of L and its epilogue writes each V_pq at (p, q) and (q, p)
+  st->packed = (st->pg.ok && st->pg.large) ? 1 : 0;
+  st->lt_rows = st->packed ? (long long)N * (N + 1) / 2 : (long long)N * N;
+  if (st->packed) {
+    st->off_pairs = cur;
+    cur = align256(cur + (size_t)st->lt_rows * 4);
+  }
   st->off_lt = cur;
-  cur = align256(cur + (size_t)N * N * st->vparts * st->kx * 2);
+  cur = align256(cur + (size_t)st->lt_rows * st->vparts * st->kx * 2);
   st->off_coef = cur;
   cur = align256(cur + (size_t)W * 2 * st->vparts * st->kx * 2);
   st->vhs_m_tiles = (2 * W + kBM - 1) / kBM;
   st->vhs_n_tiles = (N * N + 255) / 256;
-  st->pg = prop_geom(N, ncol);
   // VHS planes GEMM width: M tiles x N tiles spread over the SMs, cost per tile ~ one k-step's
   // shared-memory traffic (A: 4 KiB written and read, B: bn x 32 bytes written and read at 128 B
   // per cycle, 64 + bn / 2 cycles); the width with the smallest busiest-SM cost (the last wave
   // of a 256-wide tiling can be nearly empty)
   {
-    const long long mt = ((long long)N * N + kBM - 1) / kBM;
+    const long long mt = (st->lt_rows + kBM - 1) / kBM;
     const int sms = num_sms();
     long long best = -1;
     for (int bn : {256, 224, 192, 160, 128}) {
@@ -1043,6 +1137,18 @@ afqmc_status begin(TcState* st, cudaStream_t s, char* tcbuf, char* err, size_t e
     snprintf(err, errlen, "tc set-up: clearing the operand buffers failed");
     return AFQMC_ECUDA;
   }
+  if (st->packed) {   // p N + q of each packed row, row-major over the upper triangle
+    std::vector<int> pairs((size_t)st->lt_rows);
+    size_t r = 0;
+    for (int pp = 0; pp < st->N; ++pp)
+      for (int qq = pp; qq < st->N; ++qq) pairs[r++] = pp * st->N + qq;
+    if (cudaMemcpyAsync(tcbuf + st->off_pairs, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      snprintf(err, errlen, "tc set-up: the packed pair table copy failed");
+      return AFQMC_ECUDA;
+    }
+  }
   return AFQMC_OK;
 }
 
@@ -1056,10 +1162,11 @@ afqmc_status load_chunk(TcState* st, cudaStream_t s, char* tcbuf, int g0, int ng
                                          reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_l));
     ++*launches;
   }
-  const size_t NN = (size_t)st->N * st->N;
-  const dim3 grid((unsigned)((NN + 63) / 64), (unsigned)((ng + 31) / 32));
-  k_lt_bf16<T><<<grid, 256, 0, s>>>(g0, ng, NN, st->kx, st->nseg, chol,
-                                     reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt));
+  const size_t NN = (size_t)st->N * st->N, nrows = (size_t)st->lt_rows;
+  const dim3 grid((unsigned)((nrows + 63) / 64), (unsigned)((ng + 31) / 32));
+  k_lt_bf16<T><<<grid, 256, 0, s>>>(g0, ng, NN, nrows, st->packed ? reinterpret_cast<const int*>(tcbuf + st->off_pairs)
+                                                                   : nullptr,
+                                     st->kx, st->nseg, chol, reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt));
   ++*launches;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1091,13 +1198,13 @@ afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen) {
   }
   __nv_bfloat16* lt = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt);
   const unsigned long long vk = (unsigned long long)st->vparts * st->kx;
-  if (!make_map(&st->map_lt, lt, (unsigned long long)st->N * st->N, vk, 256) ||
+  if (!make_map(&st->map_lt, lt, (unsigned long long)st->lt_rows, vk, 256) ||
       !make_map(&st->map_coef, tcbuf + st->off_coef, (unsigned long long)st->W * 2, vk, kBM)) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS operands");
     return AFQMC_ECUDA;
   }
   if (st->pg.ok &&
-      (!make_map(&st->map_lt_a, lt, (unsigned long long)st->N * st->N, vk, kBM) ||
+      (!make_map(&st->map_lt_a, lt, (unsigned long long)st->lt_rows, vk, kBM) ||
        !make_map(&st->map_coef_b, tcbuf + st->off_coef, (unsigned long long)st->W * 2, vk, (unsigned)st->vhs_bn))) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the VHS plane operands");
     return AFQMC_ECUDA;
@@ -1153,6 +1260,17 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     g.m_step = bm.gpt * bm.n;
     g.n_step = bm.wpt * 2 * bm.n;
     g.bn = bm.bn;
+    if (bm.form == 0 && bm.dual) {   // A = [hi | lo | hi], B = [hi | hi | lo]: parts at 0 / kst / 2 kst
+      g.dual = 1;
+      g.k_blocks = (st->kst + kBK - 1) / kBK;
+      g.k_steps = st->kst / 16;
+      g.a_lo = st->kst;
+      g.b_hi = 0;
+      g.b_lo = 2 * st->kst;
+      // groups of walker tiles whose Theta operand (hi and lo, ~bn x 2 kst bf16 each) stays in L2
+      const long long bt = (long long)g.bn * 2 * st->kst * 2;
+      g.ntg = (int)std::max(1LL, std::min<long long>(g.n_tiles, (32LL << 20) / bt));
+    }
     const bool reg = bm.form == 1 || exchange_reg(bm.n, bm.wpt, g.bn);
     const int epb = epi_bytes_exchange(bm.n, reg);
     if (bm.form == 0 && !finish_geom(&g, epb, bm.groups)) {
@@ -1199,6 +1317,11 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
   return AFQMC_OK;
 }
 
+// The VHS operands' form: dual stages (each operand byte once through shared memory) while L^T is
+// small enough to stay in L2; the interleaved single-tile stages (twice the ring depth) when L^T
+// streams from HBM, where hiding its latency matters more (measured at N = 1512: 19 vs 22 ms).
+bool vhs_dual(const TcState* st) { return (double)st->lt_rows * st->vparts * st->kx * 2 < 1e9; }
+
 afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, int* status,
                         unsigned long long* launches, char* err, size_t errlen, bool coef_ready) {
   if (!st->pg.ok) {
@@ -1211,12 +1334,21 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
     ++*launches;
   }
   Geom g{};
-  g.m_tiles = (st->N * st->N + kBM - 1) / kBM;
+  g.m_tiles = (int)((st->lt_rows + kBM - 1) / kBM);
   g.n_tiles = (2 * st->W + st->vhs_bn - 1) / st->vhs_bn;
   g.k_blocks = st->nseg * st->kx / kBK;
   g.k_steps = st->nseg * st->kx / 16;
-  g.il3 = st->nseg == 3 ? 1 : 0;
-  g.seg = st->kx;
+  if (st->nseg == 3 && vhs_dual(st)) {   // A = L^T [hi | lo], B = the coefficients [hi | lo]
+    g.dual = 1;
+    g.k_blocks = st->kx / kBK;
+    g.k_steps = st->kx / 16;
+    g.a_lo = st->kx;
+    g.b_hi = 0;
+    g.b_lo = st->kx;
+  } else if (st->nseg == 3) {
+    g.il3 = 1;
+    g.seg = st->kx;
+  }
   g.m_step = kBM;
   g.n_step = st->vhs_bn;
   g.bn = st->vhs_bn;
@@ -1229,7 +1361,8 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   p.status = status;
   p.n = st->N;
   p.out_rows = 2 * st->W;
-  p.out_cols = st->N * st->N;
+  p.out_cols = (int)st->lt_rows;
+  p.pairs = st->packed ? reinterpret_cast<const int*>(tcbuf + st->off_pairs) : nullptr;
   p.planes = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_vp);
   p.npad = st->pg.npad;
   p.kq = st->pg.kq;
@@ -1238,6 +1371,10 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
 
 afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, float* out, int* status,
                  unsigned long long* launches, char* err, size_t errlen) {
+  if (st->packed) {
+    snprintf(err, errlen, "tcgen05 VHS: packed L^T feeds only the tensor-core propagation");
+    return AFQMC_EINVAL;
+  }
   k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
                                     reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
   ++*launches;
@@ -1246,8 +1383,17 @@ afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, f
   g.n_tiles = st->vhs_n_tiles;
   g.k_blocks = st->nseg * st->kx / kBK;
   g.k_steps = st->nseg * st->kx / 16;
-  g.il3 = st->nseg == 3 ? 1 : 0;
-  g.seg = st->kx;
+  if (st->nseg == 3 && vhs_dual(st)) {   // A = the coefficients [hi | lo], B = L^T [hi | lo]
+    g.dual = 1;
+    g.k_blocks = st->kx / kBK;
+    g.k_steps = st->kx / 16;
+    g.a_lo = st->kx;
+    g.b_hi = 0;
+    g.b_lo = st->kx;
+  } else if (st->nseg == 3) {
+    g.il3 = 1;
+    g.seg = st->kx;
+  }
   g.m_step = kBM;
   g.n_step = 256;
   g.bn = 256;

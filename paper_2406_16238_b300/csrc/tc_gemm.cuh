@@ -22,6 +22,7 @@ struct BlockMaps {
   int bn;            // MMA N (multiple of 16, >= wpt * 2n)
   int groups;        // epilogue warpgroups of the exchange kernel (wpt is a multiple of it)
   int form;          // 1: the Ltilde tile stays in tensor memory (k_exch_tm), 0: both operands streamed
+  int dual;          // streamed form: each stage holds the hi and lo parts of both operands (long K)
   int m_tiles, n_tiles;
   size_t off_l, off_th;   // byte offsets of the bf16 Ltilde / Theta^T copies in the tc buffer
   CUtensorMap map_l, map_th;
@@ -57,6 +58,9 @@ struct TcState {
   // VHS build
   int kx = 0;         // padded naux (multiple of 64)
   int vparts = 1;     // stored parts of the VHS operands: [hi | lo] (BF16x3) or hi (BF16)
+  int packed = 0;     // L^T holds only the pairs p <= q (large-form propagation; see plan)
+  long long lt_rows = 0;   // rows of L^T: N^2, or N (N + 1) / 2 when packed
+  size_t off_pairs = 0;    // packed: int32 p N + q per row
   size_t off_lt = 0, off_coef = 0;
   int vhs_m_tiles = 0, vhs_n_tiles = 0;
   int vhs_bn = 256;   // N tile of the VHS planes GEMM (multiple of 32)
