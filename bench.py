@@ -715,7 +715,7 @@ def run_large(args, dev=None, stream=None, steps=10, warmup=2):
     from synthetic_inputs import config_large
     dev = dev or torch.device("cuda", 0)
     stream = stream or torch.cuda.current_stream(dev)
-    prob = config_large()
+    prob = config_large(naux=getattr(args, "large_naux", None) or 7560)
     nw = 128
     prec = "bf16" if args.prec == "bf16" else "bf16x3"
     torch.cuda.synchronize(dev)
@@ -747,7 +747,7 @@ def run_large(args, dev=None, stream=None, steps=10, warmup=2):
     roof = large_rooflines(prec, prob.norb, 2, prob.nalpha, prob.naux, nw, stages)
     return {"value": nw * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
             "warmup": warmup, "form": prec, "dtype": DTYPE[prec], "gpu_launches": int(launches),
-            "workload": "large single system N=1512 42a+42b naux=7560 (tau=756) UHF W=128 dt=0.005 (E every "
+            "workload": f"large single system N=1512 42a+42b naux={prob.naux} (tau=756) UHF W=128 dt=0.005 (E every "
                         "step, QR/5, comb/10); L drawn on the GPU, binary32 chunks",
             "create_s": create_s, "workspace_GiB": ws / 2 ** 30,
             "l2": "inputs larger than L2 (L^T bf16 copy of tens of GB)",
@@ -816,6 +816,8 @@ def main():
     ap.add_argument("--ref-walkers", type=int, default=8)
     ap.add_argument("--workload", default="medium", choices=["medium", "batched", "cv", "large"])
     ap.add_argument("--no-large", action="store_true", help="leave the large-system measurement out of the line")
+    ap.add_argument("--large-naux", type=int, default=None,
+                    help="the large system truncated to its first naux Cholesky vectors (a small case for ncu)")
     ap.add_argument("--nsys", type=int, default=32)
     ap.add_argument("--cv-pairs", type=int, default=100000)
     ap.add_argument("--cv-epochs", type=int, default=30)

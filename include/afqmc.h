@@ -134,6 +134,8 @@ afqmc_status afqmc_create(const double* h1e, const double* chol, double ecore,
  * their sums over chunks stay binary64. */
 #define AFQMC_DTYPE_F64 0
 #define AFQMC_DTYPE_F32 1
+#define AFQMC_DTYPE_C128 2   /* complex, interleaved (re, im) binary64: complex contexts only */
+#define AFQMC_DTYPE_C64 3    /* complex, interleaved (re, im) binary32: complex contexts only */
 #define AFQMC_HOST 0
 #define AFQMC_DEVICE 1
 afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
@@ -142,6 +144,25 @@ afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, i
 afqmc_status afqmc_add_cholesky(afqmc_ctx* ctx, int32_t gamma0, int32_t ngamma, const void* chol, int32_t dtype,
                                 int32_t location);
 afqmc_status afqmc_create_end(afqmc_ctx* ctx);
+
+/* Complex Hamiltonians (Section "Support of complex Cholesky vectors": complex orbitals, as with
+ * Bloch orbitals, a magnetic field or spin-orbit coupling).  As afqmc_create_begin, with
+ *   h1e   [norb][norb][2]          complex Hermitian one-body integrals (interleaved re, im)
+ *   psiT  [norb][nalpha+nbeta][2]  complex trial orbitals
+ *   naux                           the number of complex Cholesky vectors L^gamma, passed to
+ *                                  afqmc_add_cholesky as AFQMC_DTYPE_C128 / C64 chunks
+ *                                  [ngamma][norb][norb][2] with g_psqr = sum L_ps conj(L_rq)
+ *                                  (the integrals' exchange symmetry (ps|qr) = (qr|ps) assumed).
+ * Each vector gives two auxiliary fields with the Hermitian matrices A = (L + L^+) / 2 and
+ * B = i (L - L^+) / 2, so the context draws 2 naux fields per walker (afqmc_get_fields, info.naux
+ * report 2 naux); every formula of the real case holds with the trial's conjugate transpose.
+ * Complex contexts run in the FP64 and FP32 forms (CUDA cores; the BF16 forms are rejected), without
+ * the control variate. */
+afqmc_status afqmc_workspace_size_complex(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta,
+                                          const double* psiT, const afqmc_params* params, size_t* bytes);
+afqmc_status afqmc_create_begin_complex(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
+                                        int32_t nbeta, const double* psiT, const afqmc_params* params,
+                                        void* workspace, size_t workspace_bytes, afqmc_ctx** out);
 
 /* nsteps phaseless steps (Eqs. 10-16), each: Green's function / Theta and the
  * force bias at the current walkers (reused from afqmc_local_energy when it

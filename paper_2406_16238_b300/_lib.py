@@ -65,6 +65,10 @@ SIGNATURES = {
                                   ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "afqmc_add_cholesky": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32]),
     "afqmc_create_end": (_i32, [_vp]),
+    "afqmc_workspace_size_complex": (_i32, [_i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params),
+                                            ctypes.POINTER(ctypes.c_size_t)]),
+    "afqmc_create_begin_complex": (_i32, [_dp, ctypes.c_double, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(Params),
+                                          _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
     "afqmc_propagate": (_i32, [_vp, _i32]),
     "afqmc_local_energy": (_i32, [_vp, _dp, _dp]),
     "afqmc_local_energy_async": (_i32, [_vp, _dp]),
@@ -156,6 +160,14 @@ class Afqmc:
                  seed=0, prec="fp64", e_trial=None, device=None, stream=None, naux=None):
         import torch
         lib = load()
+        # complex Hamiltonian (complex h1e, psiT or Cholesky vectors): the complex entry points
+        self.cplx = (np.iscomplexobj(h1e) or np.iscomplexobj(psiT) or
+                     (isinstance(chol, np.ndarray) and np.iscomplexobj(chol)) or
+                     (isinstance(chol, torch.Tensor) and chol.is_complex()))
+        if self.cplx:
+            self._init_complex(lib, h1e, chol, ecore, nalpha, nbeta, psiT, nwalkers, dt, taylor_order, fb_cap,
+                               seed, prec, e_trial, device, stream, naux)
+            return
         self.h1e = _f64(h1e)
         norb = self.h1e.shape[0]
         if isinstance(chol, torch.Tensor):   # one chunk holding every vector
@@ -202,24 +214,74 @@ class Afqmc:
                 g0 += self._add_cholesky(g0, chunk, norb)
             _check(lib.afqmc_create_end(self._ctx))
 
+    def _init_complex(self, lib, h1e, chol, ecore, nalpha, nbeta, psiT, nwalkers, dt, taylor_order, fb_cap, seed,
+                      prec, e_trial, device, stream, naux):
+        """afqmc_create_begin_complex + afqmc_add_cholesky (complex chunks) + afqmc_create_end."""
+        import torch
+        h = np.asarray(h1e, dtype=np.complex128)
+        norb = h.shape[0]
+        pt = np.asarray(psiT, dtype=np.complex128)
+        if pt.shape != (norb, nalpha + nbeta):
+            raise ValueError(f"psiT must be [{norb}, {nalpha + nbeta}]")
+        self.h1e = np.ascontiguousarray(np.stack([h.real, h.imag], axis=-1))
+        self.psiT = np.ascontiguousarray(np.stack([pt.real, pt.imag], axis=-1))
+        if isinstance(chol, (np.ndarray, torch.Tensor)):
+            naux = int(chol.shape[0]) if naux is None else naux
+            chol = [chol]
+        if naux is None:
+            raise ValueError("naux is required when chol is given in chunks")
+        self.chol = None
+        self.norb, self.nalpha, self.nbeta, self.nwalkers = norb, nalpha, nbeta, int(nwalkers)
+        self.naux = 2 * naux   # auxiliary fields
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.prec = prec
+        self.params = Params(float(dt), int(nwalkers), int(taylor_order), float(fb_cap), int(seed) & (2 ** 64 - 1),
+                             PREC[prec], 0, math.nan if e_trial is None else float(e_trial),
+                             ctypes.c_void_p(self.stream.cuda_stream))
+        nbytes = ctypes.c_size_t()
+        _check(lib.afqmc_workspace_size_complex(norb, naux, nalpha, nbeta, _ptr(self.psiT), ctypes.byref(self.params),
+                                                ctypes.byref(nbytes)))
+        self._lib = lib
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+            _check(lib.afqmc_create_begin_complex(_ptr(self.h1e), float(ecore), norb, naux, nalpha, nbeta,
+                                                  _ptr(self.psiT), ctypes.byref(self.params),
+                                                  ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                                  ctypes.byref(ctx)))
+            self._ctx = ctx
+            g0 = 0
+            for chunk in chol:
+                g0 += self._add_cholesky(g0, chunk, norb)
+            _check(lib.afqmc_create_end(self._ctx))
+
     def _add_cholesky(self, g0, chunk, norb):
         import torch
+        codes = {torch.float64: 0, torch.float32: 1, torch.complex128: 2, torch.complex64: 3}
         if isinstance(chunk, torch.Tensor):
-            if chunk.dtype not in (torch.float64, torch.float32):
-                raise ValueError("Cholesky chunks must be float64 or float32")
             t = chunk.contiguous()
+            if self.cplx and not t.is_complex():
+                t = t.to(torch.complex128)
+            if t.dtype not in codes:
+                raise ValueError("Cholesky chunks must be float64 / float32 (complex128 / complex64 if complex)")
             if t.is_cuda and t.device != self.device:
                 raise ValueError(f"chunk is on {t.device}, the context on {self.device}")
-            dtype = 0 if t.dtype == torch.float64 else 1
+            dtype = codes[t.dtype]
             loc = 1 if t.is_cuda else 0
             ptr, shape = t.data_ptr(), tuple(t.shape)
             keep = t
         else:
             a = np.asarray(chunk)
-            if a.dtype not in (np.float64, np.float32):
+            if self.cplx:
+                if a.dtype not in (np.complex128, np.complex64):
+                    a = a.astype(np.complex128)
+            elif a.dtype not in (np.float64, np.float32):
                 a = a.astype(np.float64)
             a = np.ascontiguousarray(a)
-            dtype, loc, ptr, shape, keep = (0 if a.dtype == np.float64 else 1), 0, a.ctypes.data, a.shape, a
+            dtype = {np.dtype(np.float64): 0, np.dtype(np.float32): 1, np.dtype(np.complex128): 2,
+                     np.dtype(np.complex64): 3}[a.dtype]
+            loc, ptr, shape, keep = 0, a.ctypes.data, a.shape, a
         if len(shape) != 3 or shape[1:] != (norb, norb):
             raise ValueError(f"a Cholesky chunk must be [ngamma, {norb}, {norb}] (got {shape})")
         _check(self._lib.afqmc_add_cholesky(self._ctx, int(g0), int(shape[0]), ctypes.c_void_p(ptr), dtype, loc))

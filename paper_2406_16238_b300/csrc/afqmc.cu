@@ -9,6 +9,7 @@
 #include <cstring>
 #include <algorithm>
 #include <chrono>
+#include <complex>
 #include <map>
 #include <mutex>
 #include <random>
@@ -62,7 +63,9 @@ struct Dims {
   bool restricted;
   int prec;
   int gchunk, nchunk;
+  bool cplx = false;   // complex Hamiltonian: X = 2 x the complex Cholesky vectors (Hermitian fields)
   size_t rsz() const { return prec == AFQMC_PREC_FP64 ? 8 : 4; }
+  size_t cm() const { return cplx ? 2 : 1; }   // trial, htilde, Ltilde, L, E_h and set-up arrays: complex
   bool tensor() const { return prec == AFQMC_PREC_BF16 || prec == AFQMC_PREC_BF16X3; }
 };
 
@@ -97,22 +100,23 @@ Layout plan(const Dims& d) {
   L.w = take(W * 8);
   L.w_tmp = take(W * 8);
   L.wph = take(W * 8);
-  L.phi = take(N * nc * 8);
-  L.phi_r = take(N * nc * R);
-  L.hrot = take(nc * N * 8);
-  L.hrot_r = take(nc * N * R);
+  const size_t cm = d.cm();
+  L.phi = take(N * nc * 8 * cm);
+  L.phi_r = take(N * nc * R * cm);
+  L.hrot = take(nc * N * 8 * cm);
+  L.hrot_r = take(nc * N * R * cm);
   L.lbar = take(X * 8);
   L.slbar = take(X * 8);
-  L.lrot = take(X * nc * N * R);
+  L.lrot = take(X * nc * N * R * cm);
   // L in the working precision feeds the CUDA-core VHS GEMM; the tensor-core forms read only their
   // bf16 copy of L^T
-  L.chol = take(d.tensor() ? 0 : X * N * N * R);
-  L.eh = take(N * N * R);
-  L.msum = take(N * N * 8);
-  L.lsum = take(N * N * 8);
-  L.pden = take(N * N * 8);
-  L.e1 = take(N * N * 8);
-  L.e2 = take(N * N * 8);
+  L.chol = take(d.tensor() ? 0 : X * N * N * R * cm);
+  L.eh = take(N * N * R * cm);
+  L.msum = take(N * N * 8 * cm);
+  L.lsum = take(N * N * 8 * cm);
+  L.pden = take(N * N * 8 * cm);
+  L.e1 = take(N * N * 8 * cm);
+  L.e2 = take(N * N * 8 * cm);
   L.vbias = take(W * X * C);
   L.x = take(W * X * 8);
   L.xbar = take(W * X * 16);
@@ -137,7 +141,9 @@ Layout plan(const Dims& d) {
   L.vhs_bytes = W * N * N * C;
   // staging of at least one gamma: a host chunk's copy (binary64), its cast for the set-up GEMMs and
   // the chunk's Ltilde (binary64)
-  L.stage_bytes = align_up(N * N * 8, 256) * 2 + align_up(nc * N * 8, 256) + 1024;
+  // (complex: the chunk's copy, its two Hermitian fields and their Ltilde, all complex binary64)
+  L.stage_bytes = d.cplx ? align_up(N * N * 16, 256) + align_up(2 * N * N * 16, 256) + align_up(2 * nc * N * 16, 256) + 1024
+                         : align_up(N * N * 8, 256) * 2 + align_up(nc * N * 8, 256) + 1024;
   L.stage_bytes_avail = std::max(L.vhs_bytes, L.stage_bytes);
   L.vhs = take(L.stage_bytes_avail);
   L.stage = L.vhs;
@@ -146,7 +152,7 @@ Layout plan(const Dims& d) {
 }
 
 afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta, const double* psiT,
-                       const afqmc_params* p, Dims* d) {
+                       const afqmc_params* p, Dims* d, bool cplx = false) {
   if (!p) return fail(AFQMC_EINVAL, "params is NULL");
   if (norb < 1 || naux < 1) return fail(AFQMC_EINVAL, "norb and naux must be >= 1 (got %d, %d)", norb, naux);
   if (nalpha < 1 || nbeta < 0 || nalpha > norb || nbeta > norb || nalpha > kMaxOcc || nbeta > kMaxOcc)
@@ -159,19 +165,24 @@ afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta
   if (p->reserved != 0) return fail(AFQMC_EINVAL, "params.reserved must be 0");
   if (!psiT) return fail(AFQMC_EINVAL, "psiT is NULL");
   if ((long long)norb * norb > (1ll << 31) / 2) return fail(AFQMC_EINVAL, "norb too large");
-  d->N = norb; d->X = naux; d->na = nalpha; d->nb = nbeta; d->W = p->nwalkers; d->prec = p->prec;
+  if (cplx && (p->prec == AFQMC_PREC_BF16 || p->prec == AFQMC_PREC_BF16X3))
+    return fail(AFQMC_EINVAL, "complex Hamiltonians run in the FP64 and FP32 forms");
+  if (cplx && (long long)naux * 2 > (1ll << 30)) return fail(AFQMC_EINVAL, "naux too large");
+  d->N = norb; d->X = cplx ? 2 * naux : naux; d->na = nalpha; d->nb = nbeta; d->W = p->nwalkers; d->prec = p->prec;
+  d->cplx = cplx;
   bool same = nalpha == nbeta;
   const int nt = nalpha + nbeta;
+  const int e = cplx ? 2 : 1;   // doubles per trial entry
   for (int r = 0; same && r < norb; ++r)
-    for (int c = 0; c < nalpha; ++c)
-      if (psiT[(size_t)r * nt + c] != psiT[(size_t)r * nt + nalpha + c]) { same = false; break; }
+    for (int c = 0; c < nalpha * e; ++c)
+      if (psiT[((size_t)r * nt) * e + c] != psiT[((size_t)r * nt + nalpha) * e + c]) { same = false; break; }
   d->restricted = same;
   d->ncol = same ? nalpha : nt;
   d->nblk = (same || nbeta == 0) ? 1 : 2;
   d->c0[0] = 0; d->nbk[0] = nalpha;
   d->c0[1] = nalpha; d->nbk[1] = same ? 0 : nbeta;
   d->gchunk = 8;
-  d->nchunk = (naux + d->gchunk - 1) / d->gchunk;
+  d->nchunk = (d->X + d->gchunk - 1) / d->gchunk;
   if (d->tensor()) {   // exchange partials come per (spin block, M tile) of the tensor-core kernel
     tc::TcState tmp;
     tc::plan(&tmp, d->prec, d->W, d->N, d->X, d->ncol, d->c0, d->nbk, d->nblk);
@@ -181,26 +192,30 @@ afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta
 }
 
 // Host binary64 helpers for the set-up ------------------------------------------------
-bool invert_small(std::vector<double>& a, int n) {   // Gauss-Jordan with partial pivoting, in place
-  std::vector<double> inv(n * n, 0.0);
-  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+template <typename S>
+bool invert_small(std::vector<S>& a, int n) {   // Gauss-Jordan with partial pivoting, in place
+  std::vector<S> inv((size_t)n * n, S(0.0));
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = S(1.0);
   for (int k = 0; k < n; ++k) {
     int pv = k;
-    for (int i = k + 1; i < n; ++i) if (std::fabs(a[i * n + k]) > std::fabs(a[pv * n + k])) pv = i;
-    if (a[pv * n + k] == 0.0) return false;
-    for (int j = 0; j < n; ++j) { std::swap(a[k * n + j], a[pv * n + j]); std::swap(inv[k * n + j], inv[pv * n + j]); }
-    const double d = a[k * n + k];
-    for (int j = 0; j < n; ++j) { a[k * n + j] /= d; inv[k * n + j] /= d; }
+    for (int i = k + 1; i < n; ++i) if (std::abs(a[(size_t)i * n + k]) > std::abs(a[(size_t)pv * n + k])) pv = i;
+    if (std::abs(a[(size_t)pv * n + k]) == 0.0) return false;
+    for (int j = 0; j < n; ++j) { std::swap(a[(size_t)k * n + j], a[(size_t)pv * n + j]); std::swap(inv[(size_t)k * n + j], inv[(size_t)pv * n + j]); }
+    const S d = a[(size_t)k * n + k];
+    for (int j = 0; j < n; ++j) { a[(size_t)k * n + j] /= d; inv[(size_t)k * n + j] /= d; }
     for (int i = 0; i < n; ++i) {
       if (i == k) continue;
-      const double f = a[i * n + k];
-      if (f == 0.0) continue;
-      for (int j = 0; j < n; ++j) { a[i * n + j] -= f * a[k * n + j]; inv[i * n + j] -= f * inv[k * n + j]; }
+      const S f = a[(size_t)i * n + k];
+      if (f == S(0.0)) continue;
+      for (int j = 0; j < n; ++j) { a[(size_t)i * n + j] -= f * a[(size_t)k * n + j]; inv[(size_t)i * n + j] -= f * inv[(size_t)k * n + j]; }
     }
   }
   a = inv;
   return true;
 }
+
+inline double conj_s(double x) { return x; }
+inline std::complex<double> conj_s(std::complex<double> x) { return std::conj(x); }
 
 }  // namespace
 
@@ -358,6 +373,7 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   a.psi = c->at<cplx_t<R>>(c->L.psi);
   a.phi = c->at<double>(c->L.phi);
   a.phi_r = c->at<R>(c->L.phi_r);
+  a.phi_c = c->d.cplx ? c->at<cplx_t<R>>(c->L.phi_r) : nullptr;
   a.thetaT = c->at<cplx_t<R>>(c->L.thetaT);
   a.logO = c->at<double2>(c->L.logO);
   a.w = c->at<double>(c->L.w);
@@ -380,14 +396,15 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
 
 bool overlap_stage(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
-  const size_t sm = d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, true)
-                                              : overlap_lu_smem<float>(d.N, nmax, true);
+  const size_t sm = d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, true, d.cplx)
+                                              : overlap_lu_smem<float>(d.N, nmax, true, d.cplx);
   return sm <= 100 * 1024;   // leaves room for two CTAs per SM
 }
 size_t overlap_smem(const Dims& d) {
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
   const bool st = overlap_stage(d);
-  return d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, st) : overlap_lu_smem<float>(d.N, nmax, st);
+  return d.prec == AFQMC_PREC_FP64 ? overlap_lu_smem<double>(d.N, nmax, st, d.cplx)
+                                   : overlap_lu_smem<float>(d.N, nmax, st, d.cplx);
 }
 
 bool qr_stage_psi(const Dims& d) {
@@ -403,7 +420,9 @@ size_t qr_smem(const Dims& d) {
 
 size_t prop_smem(const Dims& d) { return prop_smem_floats(d.N, d.ncol, nullptr, nullptr) * sizeof(float); }
 
-bool use_fused_propagation(const Dims& d) { return d.prec != AFQMC_PREC_FP64 && prop_smem(d) <= 227 * 1024; }
+bool use_fused_propagation(const Dims& d) {
+  return d.prec != AFQMC_PREC_FP64 && !d.cplx && prop_smem(d) <= 227 * 1024;   // real E_h only
+}
 
 bool use_tc_propagation(const afqmc_ctx* c) { return c->d.tensor() && c->tcs.pg.ok && c->prop_path == 0; }
 
@@ -421,8 +440,15 @@ afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
   if (js != AFQMC_OK) return js;
   StageTimer timer(c, AFQMC_STAGE_OVERLAP);
   const size_t sm = overlap_smem(c->d);
-  if (overlap_stage(c->d)) k_overlap_lu<R, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
-  else k_overlap_lu<R, false><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+  const bool stg = overlap_stage(c->d);
+  if (c->d.cplx) {
+    if (stg) k_overlap_lu<R, true, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+    else k_overlap_lu<R, false, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+  } else if (stg) {
+    k_overlap_lu<R, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+  } else {
+    k_overlap_lu<R, false><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+  }
   c->thb_valid = c->d.tensor();
   CHECK_LAUNCH(c);
   return AFQMC_OK;
@@ -432,7 +458,7 @@ size_t exchange_smem(const Dims& d) {
   const size_t R = d.rsz();
   const int nmax = std::max(d.nbk[0], d.nblk > 1 ? d.nbk[1] : 0);
   const size_t cn = (size_t)d.ncol * d.N;
-  return cn * 2 * R + (cn + (cn & 1)) * R + (size_t)nmax * nmax * 2 * R;
+  return cn * 2 * R + (d.cplx ? 2 * cn : cn + (cn & 1)) * R + (size_t)nmax * nmax * 2 * R;
 }
 
 template <typename R>
@@ -443,13 +469,15 @@ afqmc_status launch_exchange(afqmc_ctx* c, int with_exchange, const int* widx = 
   a.smul = c->smul; a.gchunk = c->d.gchunk; a.nchunk = c->d.nchunk;
   a.thetaT = c->at<cplx_t<R>>(c->L.thetaT);
   a.lrot = c->at<R>(c->L.lrot);
+  a.lrot_c = c->d.cplx ? c->at<cplx_t<R>>(c->L.lrot) : nullptr;
   a.vbias = c->at<cplx_t<R>>(c->L.vbias);
   a.exch_part = c->at<double2>(c->L.exch_part);
   a.with_exchange = with_exchange;
   a.widx = widx;
   a.with_vbias = widx ? 0 : 1;
   dim3 grid(c->d.nchunk, rows < 0 ? c->d.W : rows);
-  k_exchange<R><<<grid, 256, exchange_smem(c->d), c->stream>>>(a);
+  if (c->d.cplx) k_exchange<R, true><<<grid, 256, exchange_smem(c->d), c->stream>>>(a);
+  else k_exchange<R><<<grid, 256, exchange_smem(c->d), c->stream>>>(a);
   CHECK_LAUNCH(c);
   return AFQMC_OK;
 }
@@ -478,6 +506,9 @@ afqmc_status set_smem_limits(const Dims& d) {
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, true>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, false>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_exchange<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_exchange<R, true>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, true, true>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, false, true>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_chol<R>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<4, 2>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<8, 2>))) != AFQMC_OK) return st_;
@@ -525,8 +556,9 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
     es = c->side;
   }
   StageTimer te(c, AFQMC_STAGE_ENERGY);
-  k_energy<R><<<c->d.W, 256, 0, es>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
-                                              c->at<cplx_t<R>>(c->L.thetaT), c->at<R>(c->L.hrot_r),
+  auto kern = c->d.cplx ? k_energy<R, true> : k_energy<R, false>;
+  kern<<<c->d.W, 256, 0, es>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
+                                              c->at<cplx_t<R>>(c->L.thetaT), c->at<void>(c->L.hrot_r),
                                               c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
                                               c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w),
                                               c->free_proj ? c->at<double>(c->L.wph) : nullptr, sums_dev, slot,
@@ -569,7 +601,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
       g.B = c->at<R>(c->L.lrot); g.sBk = 1; g.sBn = (long long)d.ncol * d.N;
       g.C = c->at<R2>(c->L.vbias); g.sCm = d.X; g.sCn = 1;
       g.alpha_re = c->smul;
-      if ((st = gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
+      if ((st = d.cplx ? gemm<R, true, true>(c, g) : gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
     }
   }
   StageTimer* tf = new StageTimer(c, AFQMC_STAGE_FIELDS);
@@ -607,7 +639,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     g.A = c->at<R2>(c->L.coef); g.sAm = d.X; g.sAk = 1;
     g.B = c->at<R>(c->L.chol); g.sBk = NN; g.sBn = 1;
     g.C = c->at<R2>(c->L.vhs); g.sCm = NN; g.sCn = 1;
-    if ((st = gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
+    if ((st = d.cplx ? gemm<R, true, true>(c, g) : gemm<R, true, false>(c, g)) != AFQMC_OK) return st;
   }
   delete tv;
   // psi <- E_h Taylor(VHS) E_h psi   (tA = accumulator, tB/tC = Taylor terms)
@@ -660,7 +692,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     g.C = c->at<R2>(c->L.tB); g.sCb = Nc; g.sCm = d.ncol; g.sCn = 1;
     g.D = c->at<R2>(c->L.tA); g.sDb = Nc; g.sDm = d.ncol; g.sDn = 1; g.d_add = 0;
     g.skip = skip;
-    if ((st = gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
+    if ((st = d.cplx ? gemm<R, true, true>(c, g) : gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
   }
   size_t tin = c->L.tB, tout = c->L.tC;
   for (int k = 1; k <= c->taylor; ++k) {
@@ -681,7 +713,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     g.B = c->at<R2>(c->L.tA); g.sBb = Nc; g.sBk = d.ncol; g.sBn = 1;
     g.C = c->at<R2>(c->L.psi); g.sCb = Nc; g.sCm = d.ncol; g.sCn = 1;
     g.skip = skip;
-    if ((st = gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
+    if ((st = d.cplx ? gemm<R, true, true>(c, g) : gemm<R, false, true>(c, g)) != AFQMC_OK) return st;
   }
   delete tp;
   if ((st = launch_overlap<R>(c, 1)) != AFQMC_OK) return st;
@@ -753,66 +785,71 @@ afqmc_status read_status(afqmc_ctx* c) {
   ((ctx)->d.prec == AFQMC_PREC_FP64 ? fn<double>(ctx, ##__VA_ARGS__) : fn<float>(ctx, ##__VA_ARGS__))
 
 // ---- chunked set-up ----------------------------------------------------------------------
-// begin: trial quantities (host, O(N^2 n)), zeroed accumulators on the device.
-template <typename R>
-afqmc_status setup_begin(afqmc_ctx* c, const double* h1e, const double* psiT) {
+// begin: trial quantities (host, O(N^2 n)), zeroed accumulators on the device.  S is the host scalar
+// of the Hamiltonian (double, or std::complex<double> for a complex one, whose arrays are
+// interleaved (re, im) pairs).
+template <typename R, typename S>
+afqmc_status setup_begin_s(afqmc_ctx* c, const double* h1e_d, const double* psiT_d) {
   const Dims& d = c->d;
   const int N = d.N, nc = d.ncol, nt = d.na + d.nb;
+  const S* h1e = reinterpret_cast<const S*>(h1e_d);
+  const S* psiT = reinterpret_cast<const S*>(psiT_d);
   afqmc_status st;
   if ((st = set_smem_limits<R>(d)) != AFQMC_OK) return st;
-  c->h1e_host.assign(h1e, h1e + (size_t)N * N);
+  c->h1e_host.assign(h1e_d, h1e_d + (size_t)N * N * d.cm());
   // trial columns that are stored (restricted: alpha only)
-  std::vector<double> phi((size_t)N * nc);
+  std::vector<S> phi((size_t)N * nc);
   for (int p = 0; p < N; ++p)
     for (int col = 0; col < nc; ++col) phi[(size_t)p * nc + col] = psiT[(size_t)p * nt + col];
-  // P = sum_s Phi_s (Phi_s^T Phi_s)^-1 Phi_s^T over both spins
-  std::vector<double> P((size_t)N * N, 0.0);
+  // P = sum_s Phi_s (Phi_s^+ Phi_s)^-1 Phi_s^+ over both spins
+  std::vector<S> P((size_t)N * N, S(0.0));
   for (int s = 0; s < 2; ++s) {
     const int off = s == 0 ? 0 : d.na, n = s == 0 ? d.na : d.nb;
     if (n == 0) continue;
-    std::vector<double> S((size_t)n * n, 0.0);
+    std::vector<S> Sm((size_t)n * n, S(0.0));
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        double acc = 0.0;
-        for (int p = 0; p < N; ++p) acc += psiT[(size_t)p * nt + off + i] * psiT[(size_t)p * nt + off + j];
-        S[(size_t)i * n + j] = acc;
+        S acc(0.0);
+        for (int p = 0; p < N; ++p) acc += conj_s(psiT[(size_t)p * nt + off + i]) * psiT[(size_t)p * nt + off + j];
+        Sm[(size_t)i * n + j] = acc;
       }
-    if (!invert_small(S, n)) return fail(AFQMC_EINVAL, "trial orbitals of spin %d are linearly dependent", s);
-    std::vector<double> tmp((size_t)N * n, 0.0);   // Phi S^-1
+    if (!invert_small(Sm, n)) return fail(AFQMC_EINVAL, "trial orbitals of spin %d are linearly dependent", s);
+    std::vector<S> tmp((size_t)N * n, S(0.0));   // Phi S^-1
     for (int p = 0; p < N; ++p)
       for (int j = 0; j < n; ++j) {
-        double acc = 0.0;
-        for (int i = 0; i < n; ++i) acc += psiT[(size_t)p * nt + off + i] * S[(size_t)i * n + j];
+        S acc(0.0);
+        for (int i = 0; i < n; ++i) acc += psiT[(size_t)p * nt + off + i] * Sm[(size_t)i * n + j];
         tmp[(size_t)p * n + j] = acc;
       }
     for (int p = 0; p < N; ++p)
       for (int q = 0; q < N; ++q) {
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc += tmp[(size_t)p * n + j] * psiT[(size_t)q * nt + off + j];
+        S acc(0.0);
+        for (int j = 0; j < n; ++j) acc += tmp[(size_t)p * n + j] * conj_s(psiT[(size_t)q * nt + off + j]);
         P[(size_t)p * N + q] += acc;
       }
   }
-  // htilde = Phi^T h  [nc][N]
-  std::vector<double> hrot((size_t)nc * N, 0.0);
+  // htilde = Phi^+ h  [nc][N]
+  std::vector<S> hrot((size_t)nc * N, S(0.0));
   for (int col = 0; col < nc; ++col)
     for (int p = 0; p < N; ++p) {
-      const double f = phi[(size_t)p * nc + col];
-      if (f == 0.0) continue;
+      const S f = conj_s(phi[(size_t)p * nc + col]);
+      if (f == S(0.0)) continue;
       for (int q = 0; q < N; ++q) hrot[(size_t)col * N + q] += f * h1e[(size_t)p * N + q];
     }
-  CU(cudaMemcpyAsync(c->base + c->L.phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(c->base + c->L.hrot, hrot.data(), hrot.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(c->base + c->L.pden, P.data(), P.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemsetAsync(c->base + c->L.msum, 0, (size_t)N * N * 8, c->stream));
-  CU(cudaMemsetAsync(c->base + c->L.lsum, 0, (size_t)N * N * 8, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.phi, phi.data(), phi.size() * sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.hrot, hrot.data(), hrot.size() * sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->base + c->L.pden, P.data(), P.size() * sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.msum, 0, (size_t)N * N * sizeof(S), c->stream));
+  CU(cudaMemsetAsync(c->base + c->L.lsum, 0, (size_t)N * N * sizeof(S), c->stream));
   CU(cudaMemsetAsync(c->base + c->L.sflag, 0, 256, c->stream));
-  k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc, c->at<double>(c->L.phi), c->at<R>(c->L.phi_r));
+  const size_t cm = d.cm();
+  k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc * cm, c->at<double>(c->L.phi), c->at<R>(c->L.phi_r));
   CHECK_LAUNCH(c);
-  k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc, c->at<double>(c->L.hrot), c->at<R>(c->L.hrot_r));
+  k_convert<R><<<64, 256, 0, c->stream>>>((size_t)N * nc * cm, c->at<double>(c->L.hrot), c->at<R>(c->L.hrot_r));
   CHECK_LAUNCH(c);
   // binary32 set-up GEMMs where binary64 would take seconds (reduced forms only): their rounding,
   // ~1e-7 relative per sum, stays far below the forms' own
-  const double flops = 2.0 * d.X * (double)N * N * N + 2.0 * d.X * (double)nc * N * N;
+  const double flops = 2.0 * d.X * (double)N * N * N * cm * cm + 2.0 * d.X * (double)nc * N * N * cm * cm;
   c->setup_f32 = d.prec != AFQMC_PREC_FP64 && flops > 4e11;
   if (d.tensor()) {
     tc::plan(&c->tcs, d.prec, d.W, N, d.X, nc, d.c0, d.nbk, d.nblk);
@@ -821,6 +858,11 @@ afqmc_status setup_begin(afqmc_ctx* c, const double* h1e, const double* psiT) {
   // the synchronisation keeps the host vectors alive until their copies are done
   CU(cudaStreamSynchronize(c->stream));
   return AFQMC_OK;
+}
+
+template <typename R>
+afqmc_status setup_begin(afqmc_ctx* c, const double* h1e, const double* psiT) {
+  return c->d.cplx ? setup_begin_s<R, std::complex<double>>(c, h1e, psiT) : setup_begin_s<R, double>(c, h1e, psiT);
 }
 
 // One sub-chunk of gammas [g0, g0 + ng) already on the device (src, type T): checks, lbar, the
@@ -887,20 +929,101 @@ afqmc_status setup_chunk(afqmc_ctx* c, int g0, int ng, const T* src, char* scrat
   return AFQMC_OK;
 }
 
-// Host-side check of a host chunk (before it is copied): finite entries, symmetric L^g.
+// Complex Hamiltonian: one sub-chunk of complex Cholesky vectors [g0, g0 + ng) (src, interleaved
+// (re, im) of type T) becomes the Hermitian fields 2 g0 .. 2 (g0 + ng) - 1; their lbar, sums, Ltilde
+// and working-precision copies as in setup_chunk, with complex GEMMs (M^g Hermitian, so
+// sum M M = sum M^+ M, and Ltilde = Phi^+ M).
+template <typename R, typename T, typename G>
+afqmc_status setup_chunk_c(afqmc_ctx* c, int g0, int ng, const T* src, char* scratch) {
+  using G2 = cplx_t<G>;
+  const Dims& d = c->d;
+  const int N = d.N, nc = d.ncol, nf = 2 * ng, f0 = 2 * g0;
+  const size_t NN = (size_t)N * N;
+  afqmc_status st;
+  k_chol_check_c<T><<<592, 256, 0, c->stream>>>(ng, N, src, c->at<int>(c->L.sflag));
+  CHECK_LAUNCH(c);
+  G* fields = reinterpret_cast<G*>(scratch);
+  char* cur = scratch + align_up((size_t)nf * NN * 2 * sizeof(G), 256);
+  k_hermitian_fields<T, G><<<592, 256, 0, c->stream>>>(ng, N, src, fields);
+  CHECK_LAUNCH(c);
+  double* lbar = c->at<double>(c->L.lbar) + f0;
+  k_chunk_lbar_c<G><<<nf, 256, 0, c->stream>>>(N, fields, c->at<double>(c->L.pden), lbar);
+  CHECK_LAUNCH(c);
+  // lsum += sum_f lbar_f M^f: lbar is real, so the interleaved arrays are summed as real ones
+  k_chunk_lsum<G><<<(unsigned)std::min<size_t>(4 * 148, (2 * NN + 255) / 256), 256, 0, c->stream>>>(
+      nf, 2 * NN, fields, lbar, c->at<double>(c->L.lsum));
+  CHECK_LAUNCH(c);
+  {   // msum += sum_f M^f+ M^f = B^+ B with B the fields viewed as [nf N][N]
+    GemmDesc g = gdesc(N, N, nf * N, 1);
+    g.A = fields; g.sAm = 1; g.sAk = N; g.conj_a = 1;
+    g.B = fields; g.sBk = N; g.sBn = 1;
+    if (std::is_same<G, double>::value) {
+      g.D = c->at<double2>(c->L.msum); g.sDm = N; g.sDn = 1; g.d_add = 1;
+      if ((st = gemm<G, true, true>(c, g)) != AFQMC_OK) return st;
+    } else {
+      g.C = c->at<G2>(c->L.e1); g.sCm = N; g.sCn = 1;
+      if ((st = gemm<G, true, true>(c, g)) != AFQMC_OK) return st;
+      k_add_f32_to_f64<<<592, 256, 0, c->stream>>>(2 * NN, c->at<float>(c->L.e1), c->at<double>(c->L.msum));
+      CHECK_LAUNCH(c);
+    }
+  }
+  G2* lrot = reinterpret_cast<G2*>(cur);
+  {   // Ltilde[f] = Phi^+ M^f  ([nc][N] per field)
+    GemmDesc g = gdesc(nc, N, N, nf);
+    g.A = std::is_same<G, double>::value ? c->at<void>(c->L.phi) : c->at<void>(c->L.phi_r);
+    g.sAb = 0; g.sAm = 1; g.sAk = nc; g.conj_a = 1;
+    g.B = fields; g.sBb = (long long)NN; g.sBk = N; g.sBn = 1;
+    g.C = lrot; g.sCb = (long long)nc * N; g.sCm = N; g.sCn = 1;
+    if ((st = gemm<G, true, true>(c, g)) != AFQMC_OK) return st;
+  }
+  k_cast<G, R><<<592, 256, 0, c->stream>>>((size_t)nf * nc * N * 2, reinterpret_cast<const G*>(lrot),
+                                            c->at<R>(c->L.lrot) + (size_t)f0 * nc * N * 2);
+  CHECK_LAUNCH(c);
+  k_cast<G, R><<<592, 256, 0, c->stream>>>((size_t)nf * NN * 2, fields, c->at<R>(c->L.chol) + (size_t)f0 * NN * 2);
+  CHECK_LAUNCH(c);
+  return AFQMC_OK;
+}
+
+// Host-side check of a host chunk (before it is copied): finite entries, symmetric L^g.  One pass
+// over the upper triangle of each L^g, the vectors split over host threads; the first bad vector
+// (in gamma order) is reported.
 template <typename T>
 afqmc_status check_host_chunk(int g0, int ng, int N, const T* chol) {
   const size_t NN = (size_t)N * N;
-  for (int g = 0; g < ng; ++g) {
+  auto bad_in = [&](int g, int* kind, int* bp, int* bq) {
     const T* Lg = chol + (size_t)g * NN;
-    for (size_t i = 0; i < NN; ++i)
-      if (!std::isfinite((double)Lg[i])) return fail(AFQMC_EINVAL, "chol has a non-finite entry at %zu", (size_t)(g0 + g) * NN + i);
-    for (int p = 0; p < N; ++p)
+    for (int p = 0; p < N; ++p) {
+      if (!std::isfinite((double)Lg[(size_t)p * N + p])) { *kind = 1; *bp = p; *bq = p; return true; }
       for (int q = p + 1; q < N; ++q) {
         const double v = Lg[(size_t)p * N + q], u = Lg[(size_t)q * N + p];
-        if (std::fabs(v - u) > 1e-12 * std::max(1.0, std::max(std::fabs(v), std::fabs(u))))
-          return fail(AFQMC_EINVAL, "chol[%d] is not symmetric at (%d, %d)", g0 + g, p, q);
+        if (!std::isfinite(v) || !std::isfinite(u)) { *kind = 1; *bp = p; *bq = q; return true; }
+        if (std::fabs(v - u) > 1e-12 * std::max(1.0, std::max(std::fabs(v), std::fabs(u)))) {
+          *kind = 2; *bp = p; *bq = q; return true;
+        }
       }
+    }
+    return false;
+  };
+  const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const int per = (ng + nth - 1) / nth;
+  std::vector<int> first(nth, -1), kinds(nth, 0), ps(nth, 0), qs(nth, 0);
+  auto work = [&](int t) {
+    for (int g = t * per; g < std::min(ng, (t + 1) * per); ++g)
+      if (bad_in(g, &kinds[t], &ps[t], &qs[t])) { first[t] = g; return; }
+  };
+  if ((size_t)ng * NN < ((size_t)1 << 20) || nth == 1) {
+    work(0);
+    for (int t = 1; t < nth; ++t) work(t);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  for (int t = 0; t < nth; ++t) {
+    if (first[t] < 0) continue;
+    const int g = g0 + first[t];
+    if (kinds[t] == 1) return fail(AFQMC_EINVAL, "chol has a non-finite entry (vector %d, %d, %d)", g, ps[t], qs[t]);
+    return fail(AFQMC_EINVAL, "chol[%d] is not symmetric at (%d, %d)", g, ps[t], qs[t]);
   }
   return AFQMC_OK;
 }
@@ -909,9 +1032,11 @@ afqmc_status check_host_chunk(int g0, int ng, int N, const T* chol) {
 template <typename R, typename T>
 afqmc_status setup_add(afqmc_ctx* c, int g0, int ng, const T* chol, bool on_device, bool host_checked) {
   const Dims& d = c->d;
-  const size_t NN = (size_t)d.N * d.N;
-  const size_t per = (on_device ? 0 : align_up(NN * sizeof(T), 256)) + align_up(NN * 8, 256) +
-                     align_up((size_t)d.ncol * d.N * 8, 256);
+  const size_t NN = (size_t)d.N * d.N * d.cm();   // T elements per vector (complex: interleaved)
+  const size_t per = d.cplx ? (on_device ? 0 : align_up(NN * sizeof(T), 256)) + align_up(2 * NN * 8, 256) +
+                                  align_up((size_t)2 * d.ncol * d.N * 16, 256)
+                            : (on_device ? 0 : align_up(NN * sizeof(T), 256)) + align_up(NN * 8, 256) +
+                                  align_up((size_t)d.ncol * d.N * 8, 256);
   // 1024 bytes of slack cover the 256-byte alignment of the three staged arrays
   const size_t cap = std::max<size_t>(1, (c->L.stage_bytes_avail - 1024) / per);
   for (int a = 0; a < ng; a += (int)cap) {
@@ -921,14 +1046,16 @@ afqmc_status setup_add(afqmc_ctx* c, int g0, int ng, const T* chol, bool on_devi
     const T* src = part;
     if (!on_device) {
       afqmc_status st;
-      if (!host_checked && (st = check_host_chunk<T>(g0 + a, n, d.N, part)) != AFQMC_OK) return st;
+      if (!d.cplx && !host_checked && (st = check_host_chunk<T>(g0 + a, n, d.N, part)) != AFQMC_OK) return st;
       T* dst = reinterpret_cast<T*>(scratch);
       CU(cudaMemcpyAsync(dst, part, (size_t)n * NN * sizeof(T), cudaMemcpyHostToDevice, c->stream));
       scratch += align_up((size_t)n * NN * sizeof(T), 256);
       src = dst;
     }
-    afqmc_status st = c->setup_f32 ? setup_chunk<R, T, float>(c, g0 + a, n, src, scratch)
-                                   : setup_chunk<R, T, double>(c, g0 + a, n, src, scratch);
+    afqmc_status st = d.cplx ? (c->setup_f32 ? setup_chunk_c<R, T, float>(c, g0 + a, n, src, scratch)
+                                             : setup_chunk_c<R, T, double>(c, g0 + a, n, src, scratch))
+                             : (c->setup_f32 ? setup_chunk<R, T, float>(c, g0 + a, n, src, scratch)
+                                             : setup_chunk<R, T, double>(c, g0 + a, n, src, scratch));
     if (st != AFQMC_OK) return st;
     // the staging region is reused by the next sub-chunk (stream order), and a host chunk's
     // pageable source must stay readable until its copy is done
@@ -962,12 +1089,15 @@ afqmc_status setup_end(afqmc_ctx* c) {
   // A = -dt/2 h_eff (e1), from h (e2)
   double* A = c->at<double>(c->L.e1);
   double* H = c->at<double>(c->L.e2);
-  CU(cudaMemcpyAsync(H, c->h1e_host.data(), NN * 8, cudaMemcpyHostToDevice, c->stream));
+  const bool cx = d.cplx;
+  CU(cudaMemcpyAsync(H, c->h1e_host.data(), NN * 8 * d.cm(), cudaMemcpyHostToDevice, c->stream));
   const unsigned eg = (unsigned)std::min<size_t>(4 * 148, (NN + 255) / 256);
-  k_heff<<<eg, 256, 0, c->stream>>>(N, -0.5 * c->dt, H, c->at<double>(c->L.msum), c->at<double>(c->L.lsum), A);
+  if (cx) k_heff_c<<<eg, 256, 0, c->stream>>>(N, -0.5 * c->dt, H, c->at<double>(c->L.msum), c->at<double>(c->L.lsum), A);
+  else k_heff<<<eg, 256, 0, c->stream>>>(N, -0.5 * c->dt, H, c->at<double>(c->L.msum), c->at<double>(c->L.lsum), A);
   CHECK_LAUNCH(c);
   double* dnorm = c->at<double>(c->L.sflag) + 8;
-  k_norm1<<<1, 1024, 0, c->stream>>>(N, A, dnorm);
+  if (cx) k_norm1_c<<<1, 1024, 0, c->stream>>>(N, A, dnorm);
+  else k_norm1<<<1, 1024, 0, c->stream>>>(N, A, dnorm);
   CHECK_LAUNCH(c);
   double norm = 0.0;
   CU(cudaMemcpyAsync(&norm, dnorm, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -985,34 +1115,36 @@ afqmc_status setup_end(afqmc_ctx* c) {
   }
   double* T = c->at<double>(c->L.msum);   // sum L L and lsum are no longer needed
   double* Tn = c->at<double>(c->L.lsum);
-  k_identity_plus<<<eg, 256, 0, c->stream>>>(N, sc / m, 1.0, A, T);
-  CHECK_LAUNCH(c);
-  for (int k = m - 1; k >= 1; --k) {   // T <- I + (sc / k) A T
-    GemmDesc g = gdesc(N, N, N, 1);
-    g.A = A; g.sAm = N; g.sAk = 1;
-    g.B = T; g.sBk = N; g.sBn = 1;
-    g.C = Tn; g.sCm = N; g.sCn = 1;
-    g.alpha_re = sc / k;
-    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
-    k_identity_plus<<<eg, 256, 0, c->stream>>>(N, 1.0, 1.0, Tn, Tn);
+  auto idplus = [&](double alpha, double diag, const double* B, double* out) -> afqmc_status {
+    if (cx) k_identity_plus_c<<<eg, 256, 0, c->stream>>>(N, alpha, diag, B, out);
+    else k_identity_plus<<<eg, 256, 0, c->stream>>>(N, alpha, diag, B, out);
     CHECK_LAUNCH(c);
+    return AFQMC_OK;
+  };
+  auto mm = [&](const double* X1, const double* X2, double* out, double alpha) -> afqmc_status {
+    GemmDesc g = gdesc(N, N, N, 1);
+    g.A = X1; g.sAm = N; g.sAk = 1;
+    g.B = X2; g.sBk = N; g.sBn = 1;
+    g.C = out; g.sCm = N; g.sCn = 1;
+    g.alpha_re = alpha;
+    return cx ? gemm<double, true, true>(c, g) : gemm<double, false, false>(c, g);
+  };
+  if ((st = idplus(sc / m, 1.0, A, T)) != AFQMC_OK) return st;
+  for (int k = m - 1; k >= 1; --k) {   // T <- I + (sc / k) A T
+    if ((st = mm(A, T, Tn, sc / k)) != AFQMC_OK) return st;
+    if ((st = idplus(1.0, 1.0, Tn, Tn)) != AFQMC_OK) return st;
     std::swap(T, Tn);
   }
   for (int s = 0; s < sq; ++s) {
-    GemmDesc g = gdesc(N, N, N, 1);
-    g.A = T; g.sAm = N; g.sAk = 1;
-    g.B = T; g.sBk = N; g.sBn = 1;
-    g.C = Tn; g.sCm = N; g.sCn = 1;
-    if ((st = gemm<double, false, false>(c, g)) != AFQMC_OK) return st;
+    if ((st = mm(T, T, Tn, 1.0)) != AFQMC_OK) return st;
     std::swap(T, Tn);
   }
-  k_convert<R><<<64, 256, 0, c->stream>>>(NN, T, c->at<R>(c->L.eh));
+  k_convert<R><<<64, 256, 0, c->stream>>>(NN * d.cm(), T, c->at<R>(c->L.eh));
   CHECK_LAUNCH(c);
   if (d.tensor()) {
     if ((st = tc::finish(&c->tcs, c->at<char>(c->L.tc), g_err, sizeof(g_err))) != AFQMC_OK) return st;
     if (c->tcs.pg.ok) {   // F = E_h - I in binary64 for the tensor-core propagation
-      k_identity_plus<<<eg, 256, 0, c->stream>>>(N, 1.0, -1.0, T, Tn);
-      CHECK_LAUNCH(c);
+      if ((st = idplus(1.0, -1.0, T, Tn)) != AFQMC_OK) return st;
       if ((st = tc::prepare_prop(&c->tcs, c->stream, c->at<char>(c->L.tc), Tn, &c->launches, g_err,
                                  sizeof(g_err))) != AFQMC_OK)
         return st;
@@ -1023,7 +1155,7 @@ afqmc_status setup_end(afqmc_ctx* c) {
   CU(cudaMemsetAsync(c->base + c->L.slot, 0, 256, c->stream));   // history slot, energy completion counter
   CU(cudaMemsetAsync(c->base + c->L.wph, 0, (size_t)d.W * 8, c->stream));
   k_init_walkers<R><<<296, 256, 0, c->stream>>>(d.W, N, nc, c->at<double>(c->L.phi), c->at<cplx_t<R>>(c->L.psi),
-                                                c->at<double>(c->L.w));
+                                                c->at<double>(c->L.w), cx ? 1 : 0);
   CHECK_LAUNCH(c);
   if ((st = launch_overlap<R>(c, 0)) != AFQMC_OK) return st;
   c->theta_fresh = true;
@@ -1155,14 +1287,17 @@ afqmc_status afqmc_workspace_size(int32_t norb, int32_t naux, int32_t nalpha, in
   return AFQMC_OK;
 }
 
-afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
-                                int32_t nbeta, const double* psiT, const afqmc_params* params, void* workspace,
-                                size_t workspace_bytes, afqmc_ctx** out) {
+}  // extern "C"
+
+namespace {
+afqmc_status create_begin_impl(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
+                               int32_t nbeta, const double* psiT, const afqmc_params* params, void* workspace,
+                               size_t workspace_bytes, afqmc_ctx** out, bool cplx) {
   if (!out) return fail(AFQMC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!h1e) return fail(AFQMC_EINVAL, "h1e is NULL");
   Dims d{};
-  afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d);
+  afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d, cplx);
   if (st != AFQMC_OK) return st;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return fail(AFQMC_EINVAL, "workspace must be a non-NULL 256-byte aligned device pointer");
@@ -1170,18 +1305,21 @@ afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, i
   if (workspace_bytes < L.total)
     return fail(AFQMC_ENOMEM, "workspace has %zu bytes, %zu needed", workspace_bytes, L.total);
   if (!std::isfinite(ecore)) return fail(AFQMC_EINVAL, "ecore is not finite");
-  const size_t N = norb, nt = nalpha + nbeta;
+  const size_t N = norb, nt = nalpha + nbeta, e = cplx ? 2 : 1;
   double hmax = 0.0;
-  for (size_t i = 0; i < N * N; ++i) {
+  for (size_t i = 0; i < N * N * e; ++i) {
     if (!std::isfinite(h1e[i])) return fail(AFQMC_EINVAL, "h1e has a non-finite entry");
     hmax = std::max(hmax, std::fabs(h1e[i]));
   }
-  for (size_t i = 0; i < N * nt; ++i)
+  for (size_t i = 0; i < N * nt * e; ++i)
     if (!std::isfinite(psiT[i])) return fail(AFQMC_EINVAL, "psiT has a non-finite entry");
   for (size_t p = 0; p < N; ++p)
-    for (size_t q = p + 1; q < N; ++q)
-      if (std::fabs(h1e[p * N + q] - h1e[q * N + p]) > 1e-12 * std::max(1.0, hmax))
-        return fail(AFQMC_EINVAL, "h1e is not symmetric at (%zu, %zu)", p, q);
+    for (size_t q = (cplx ? p : p + 1); q < N; ++q) {   // symmetric, or Hermitian (h_qp = conj h_pq)
+      const double dr = h1e[(p * N + q) * e] - h1e[(q * N + p) * e];
+      const double di = cplx ? h1e[(p * N + q) * e + 1] + h1e[(q * N + p) * e + 1] : 0.0;
+      if (std::fabs(dr) + std::fabs(di) > 1e-12 * std::max(1.0, hmax))
+        return fail(AFQMC_EINVAL, "h1e is not %s at (%zu, %zu)", cplx ? "Hermitian" : "symmetric", p, q);
+    }
   afqmc_ctx* c = new afqmc_ctx();
   c->d = d;
   c->L = L;
@@ -1215,23 +1353,57 @@ afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, i
   return AFQMC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+afqmc_status afqmc_create_begin(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
+                                int32_t nbeta, const double* psiT, const afqmc_params* params, void* workspace,
+                                size_t workspace_bytes, afqmc_ctx** out) {
+  return create_begin_impl(h1e, ecore, norb, naux, nalpha, nbeta, psiT, params, workspace, workspace_bytes, out,
+                           false);
+}
+
+afqmc_status afqmc_create_begin_complex(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,
+                                        int32_t nbeta, const double* psiT, const afqmc_params* params,
+                                        void* workspace, size_t workspace_bytes, afqmc_ctx** out) {
+  return create_begin_impl(h1e, ecore, norb, naux, nalpha, nbeta, psiT, params, workspace, workspace_bytes, out,
+                           true);
+}
+
+afqmc_status afqmc_workspace_size_complex(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta,
+                                          const double* psiT, const afqmc_params* params, size_t* bytes) {
+  if (!bytes) return fail(AFQMC_EINVAL, "bytes is NULL");
+  Dims d{};
+  afqmc_status st = make_dims(norb, naux, nalpha, nbeta, psiT, params, &d, true);
+  if (st != AFQMC_OK) return st;
+  *bytes = plan(d).total;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_add_cholesky(afqmc_ctx* ctx, int32_t gamma0, int32_t ngamma, const void* chol, int32_t dtype,
                                 int32_t location) {
   if (!ctx) return fail(AFQMC_EINVAL, "context is NULL");
   if (!ctx->building) return fail(AFQMC_EINVAL, "afqmc_add_cholesky: the context's set-up is already complete");
   if (!chol) return fail(AFQMC_EINVAL, "afqmc_add_cholesky: chol is NULL");
-  if (dtype != AFQMC_DTYPE_F64 && dtype != AFQMC_DTYPE_F32) return fail(AFQMC_EINVAL, "afqmc_add_cholesky: dtype %d", dtype);
+  const bool cdt = dtype == AFQMC_DTYPE_C128 || dtype == AFQMC_DTYPE_C64;
+  if (dtype != AFQMC_DTYPE_F64 && dtype != AFQMC_DTYPE_F32 && !cdt)
+    return fail(AFQMC_EINVAL, "afqmc_add_cholesky: dtype %d", dtype);
+  if (cdt != ctx->d.cplx)
+    return fail(AFQMC_EINVAL, "afqmc_add_cholesky: %s vectors for a %s context", cdt ? "complex" : "real",
+                ctx->d.cplx ? "complex" : "real");
   if (location != AFQMC_HOST && location != AFQMC_DEVICE)
     return fail(AFQMC_EINVAL, "afqmc_add_cholesky: location %d", location);
   if (gamma0 != ctx->chol_next)
     return fail(AFQMC_EINVAL, "afqmc_add_cholesky: expected gamma0 = %d (vectors are passed in order, once)",
                 ctx->chol_next);
-  if (ngamma < 1 || gamma0 + (long long)ngamma > ctx->d.X)
+  const int nvec = ctx->d.cplx ? ctx->d.X / 2 : ctx->d.X;
+  if (ngamma < 1 || gamma0 + (long long)ngamma > nvec)
     return fail(AFQMC_EINVAL, "afqmc_add_cholesky: gammas [%d, %lld) outside [0, %d)", gamma0,
-                gamma0 + (long long)ngamma, ctx->d.X);
+                gamma0 + (long long)ngamma, nvec);
   const bool dev = location == AFQMC_DEVICE;
   afqmc_status st;
-  if (dtype == AFQMC_DTYPE_F64)
+  if (dtype == AFQMC_DTYPE_F64 || dtype == AFQMC_DTYPE_C128)
     st = DISPATCH(ctx, setup_add, gamma0, ngamma, static_cast<const double*>(chol), dev, false);
   else
     st = DISPATCH(ctx, setup_add, gamma0, ngamma, static_cast<const float*>(chol), dev, false);
@@ -1243,8 +1415,9 @@ afqmc_status afqmc_add_cholesky(afqmc_ctx* ctx, int32_t gamma0, int32_t ngamma, 
 afqmc_status afqmc_create_end(afqmc_ctx* ctx) {
   if (!ctx) return fail(AFQMC_EINVAL, "context is NULL");
   if (!ctx->building) return fail(AFQMC_EINVAL, "afqmc_create_end: the context's set-up is already complete");
-  if (ctx->chol_next != ctx->d.X)
-    return fail(AFQMC_EINVAL, "afqmc_create_end: %d of %d Cholesky vectors passed", ctx->chol_next, ctx->d.X);
+  const int nvec = ctx->d.cplx ? ctx->d.X / 2 : ctx->d.X;
+  if (ctx->chol_next != nvec)
+    return fail(AFQMC_EINVAL, "afqmc_create_end: %d of %d Cholesky vectors passed", ctx->chol_next, nvec);
   afqmc_status st = DISPATCH(ctx, setup_end);
   if (st != AFQMC_OK) return st;
   ctx->building = false;
@@ -1607,6 +1780,7 @@ afqmc_status afqmc_cv_attach(afqmc_ctx* ctx, int32_t capacity, int32_t batch, do
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;
   if (capacity < 1 || batch < 1) return fail(AFQMC_EINVAL, "cv: capacity and batch must be >= 1");
+  if (ctx->d.cplx) return fail(AFQMC_EINVAL, "cv: the control variate takes real Hamiltonians");
   if (!(sample_frac > 0.0 && sample_frac <= 1.0)) return fail(AFQMC_EINVAL, "cv: sample_frac must be in (0, 1]");
   if (ctx->d.W > 8192) return fail(AFQMC_EINVAL, "cv: at most 8192 walkers (subsample drawn in one block)");
   if (!dev || (reinterpret_cast<uintptr_t>(dev) & 255)) return fail(AFQMC_EINVAL, "cv: device block must be 256-byte aligned");

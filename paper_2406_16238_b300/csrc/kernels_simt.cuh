@@ -2,6 +2,7 @@
 // the FP64 form, float for the reduced forms).  Overlap inverses and
 // log-determinants, weights, QR and all energy reductions are binary64 in both.
 #pragma once
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -26,6 +27,7 @@ struct GemmDesc {
   const double* skip;
   int a_planar;          // complex A stored as separate real and imaginary planes
   long long a_im_off;    // element offset of the imaginary plane (a_planar)
+  int conj_a;            // complex A enters conjugated (A^+ with the transposing strides)
 };
 
 // Block tile BM x BN = 16 TM x 16 TN, each of the 256 threads owns a TM x TN register tile.
@@ -62,6 +64,7 @@ __global__ void __launch_bounds__(256) k_gemm(GemmDesc g) {
         if (CA) {
           if (g.a_planar) { vr = ((const R*)Ab)[idx]; vi = ((const R*)Ab)[idx + g.a_im_off]; }
           else { R2 v = ((const R2*)Ab)[idx]; vr = v.x; vi = v.y; }
+          if (g.conj_a) vi = -vi;
         } else vr = ((const R*)Ab)[idx];
       }
       As_re[kk][mm] = vr;
@@ -152,6 +155,7 @@ struct OverlapArgs {
   const cplx_t<R>* psi;           // [W][N][ncol]
   const double* phi;              // [N][ncol]
   const R* phi_r;                 // [N][ncol] at the walkers' precision
+  const cplx_t<R>* phi_c;         // complex trial [N][ncol] (complex Hamiltonians; A = Phi^+ psi)
   cplx_t<R>* thetaT;              // [W][ncol][N]
   double2* logO;                  // [W]
   double* w;                      // [W]
@@ -210,6 +214,7 @@ struct ExchangeArgs {
   int gchunk, nchunk;
   const cplx_t<R>* thetaT;   // [W][ncol][N]
   const R* lrot;             // [X][ncol][N]
+  const cplx_t<R>* lrot_c;   // complex Ltilde [X][ncol][N] (complex Hamiltonians), used by k_exchange<R, true>
   cplx_t<R>* vbias;          // [W][X]
   double2* exch_part;        // [rows][nchunk]
   int with_exchange;
@@ -217,24 +222,26 @@ struct ExchangeArgs {
   int with_vbias;
 };
 
-template <typename R>
+template <typename R, bool CL = false>
 __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
   using R2 = cplx_t<R>;
+  using LT = typename std::conditional<CL, R2, R>::type;
   extern __shared__ __align__(16) unsigned char sm_ex[];
   __shared__ double red[32];
   const int chunk = blockIdx.x, row = blockIdx.y, tid = threadIdx.x;
   const int w = a.widx ? a.widx[row] : row;
   const int cn = a.ncol * a.N;
   R2* th = (R2*)sm_ex;                                // [ncol][N]
-  R* lr = (R*)(th + cn);                              // [ncol][N]
+  LT* lr = (LT*)(th + cn);                            // [ncol][N]
   const int nmax = max(a.nb[0], a.nblk > 1 ? a.nb[1] : 0);
-  R2* T = (R2*)(lr + cn + (cn & 1));                  // [nmax][nmax]
+  R2* T = (R2*)((R*)lr + (CL ? 2 * cn : cn + (cn & 1)));   // [nmax][nmax]
+  const LT* lsrc = CL ? reinterpret_cast<const LT*>(a.lrot_c) : reinterpret_cast<const LT*>(a.lrot);
   for (int i = tid; i < cn; i += blockDim.x) th[i] = a.thetaT[(size_t)w * cn + i];
   double2 exx = mk(0.0, 0.0);
   const int g0 = chunk * a.gchunk, g1 = min(a.X, g0 + a.gchunk);
   for (int g = g0; g < g1; ++g) {
     __syncthreads();
-    for (int i = tid; i < cn; i += blockDim.x) lr[i] = a.lrot[(size_t)g * cn + i];
+    for (int i = tid; i < cn; i += blockDim.x) lr[i] = lsrc[(size_t)g * cn + i];
     __syncthreads();
     double2 vb = mk(0.0, 0.0);
     for (int s = 0; s < a.nblk; ++s) {
@@ -242,14 +249,20 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
       if (n == 0) continue;
       for (int idx = tid; idx < n * n; idx += blockDim.x) {
         const int ia = idx / n, ib = idx % n;
-        const R* lrow = lr + (size_t)(c0 + ia) * a.N;
+        const LT* lrow = lr + (size_t)(c0 + ia) * a.N;
         const R2* trow = th + (size_t)(c0 + ib) * a.N;
         R sr = R(0), si = R(0);
         for (int p = 0; p < a.N; ++p) {
-          const R l = lrow[p];
           const R2 t = trow[p];
-          sr += l * t.x;
-          si += l * t.y;
+          if constexpr (CL) {
+            const R2 l = lrow[p];
+            sr += l.x * t.x - l.y * t.y;
+            si += l.x * t.y + l.y * t.x;
+          } else {
+            const R l = lrow[p];
+            sr += l * t.x;
+            si += l * t.y;
+          }
         }
         R2 v;
         v.x = sr;
@@ -290,9 +303,9 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
 // sums (ENumer, EDenom, E1Body, E2Body) over all walkers in a fixed order (free projection, wph
 // non-null: Re and Im of sum w e^{i phi} E_L, Re and Im of sum w e^{i phi}); with a slot counter
 // they go to out + 4 * (*slot) and the counter advances (graph-replayable history).
-template <typename R>
+template <typename R, bool CH = false>
 __global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double smul, double ecore, int nchunk,
-                                                const cplx_t<R>* thetaT, const R* hrot_r, const cplx_t<R>* vbias,
+                                                const cplx_t<R>* thetaT, const void* hrot_v, const cplx_t<R>* vbias,
                                                 const double2* exch_part, double2* eloc, int W, const double* wgt,
                                                 const double* wph, double* out, int* slot, unsigned int* done) {
   __shared__ double red[32];
@@ -304,6 +317,15 @@ __global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double s
   // per-thread partials at the walkers' precision (four independent chains), summed in binary64
   R ar[4] = {R(0), R(0), R(0), R(0)}, ai[4] = {R(0), R(0), R(0), R(0)};
   int i = tid;
+  const R* hrot_r = static_cast<const R*>(hrot_v);
+  if constexpr (CH) {   // complex htilde: sum htilde Theta^T, complex products
+    const cplx_t<R>* hc = static_cast<const cplx_t<R>*>(hrot_v);
+    for (; i < cn; i += 256) {
+      const cplx_t<R> t = th[i], h = hc[i];
+      ar[0] += t.x * h.x - t.y * h.y;
+      ai[0] += t.x * h.y + t.y * h.x;
+    }
+  }
   for (; i + 3 * 256 < cn; i += 4 * 256) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -602,10 +624,11 @@ __global__ void __launch_bounds__(256) k_comb_gather(int W, int psi_elems, int t
 
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_init_walkers(int W, int N, int ncol, const double* phi, cplx_t<R>* psi, double* w) {
+__global__ void k_init_walkers(int W, int N, int ncol, const double* phi, cplx_t<R>* psi, double* w, int cplx) {
   const size_t total = (size_t)W * N * ncol;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    psi[i] = from_d2<R>(mk(phi[i % ((size_t)N * ncol)], 0.0));
+    const size_t k = i % ((size_t)N * ncol);
+    psi[i] = from_d2<R>(cplx ? mk(phi[2 * k], phi[2 * k + 1]) : mk(phi[k], 0.0));
     if (i < (size_t)W) w[i] = 1.0;
   }
 }
@@ -874,11 +897,11 @@ __global__ void __launch_bounds__(512) k_propagate_smem(PropArgs a) {
 // Shared memory: A [n][lda] binary64 | pivots, 1 / pivots [n] binary64 | perm [n] | F [n][n] R |
 // (STAGE) Y [N][ldy] R complex | Phi [N][n] R.
 template <typename R>
-__host__ __device__ inline size_t overlap_lu_smem(int N, int nmax, bool stage) {
+__host__ __device__ inline size_t overlap_lu_smem(int N, int nmax, bool stage, bool cphi = false) {
   const int lda = nmax + 1, ldy = nmax | 1;
   const size_t fixed = (size_t)nmax * lda * 16 + (size_t)nmax * 32 + ((size_t)nmax * 4 + 15) / 16 * 16 +
                        (size_t)nmax * nmax * 2 * sizeof(R);
-  return fixed + (stage ? (size_t)N * ldy * 2 * sizeof(R) + (size_t)N * nmax * sizeof(R) : 0) + 16;
+  return fixed + (stage ? (size_t)N * ldy * 2 * sizeof(R) + (size_t)N * nmax * sizeof(R) * (cphi ? 2 : 1) : 0) + 16;
 }
 
 // Complex product with the larger component renormalised to [1, 2) (exact power of two); e
@@ -994,7 +1017,7 @@ __device__ __forceinline__ void subst_rows_blocked(cplx_t<R>* Y, int ldy, const 
 }
 
 // 5 CTAs per SM: the W = 640 walkers of the benchmark shape run in one wave on 148 SMs.
-template <typename R, bool STAGE>
+template <typename R, bool STAGE, bool CPHI = false>
 __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
   using R2 = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char sm_lu[];
@@ -1025,52 +1048,71 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
       for (int idx = tid; idx < N * n; idx += blockDim.x) {
         const int p = idx / n, j = idx - p * n;
         cp_async_elem<sizeof(R2)>(&Y[(size_t)p * ldy + j], &psw[(size_t)p * a.ncol + j]);
-        cp_async_elem<sizeof(R)>(&PH[idx], &a.phi_r[(size_t)p * a.ncol + c0 + j]);
+        if (CPHI) cp_async_elem<sizeof(R2)>(&reinterpret_cast<R2*>(PH)[idx], &a.phi_c[(size_t)p * a.ncol + c0 + j]);
+        else cp_async_elem<sizeof(R)>(&PH[idx], &a.phi_r[(size_t)p * a.ncol + c0 + j]);
       }
       cp_async_wait_all();
     }
     if (tid < n) perm[tid] = tid;
     if (tid == 0) { sing_s = 0; swaps_s = 0; }
     __syncthreads();
-    // A = Phi^T psi: 2 x 2 register tiles
+    // A = Phi^T psi (Phi^+ psi for a complex trial): 2 x 2 register tiles
     const int nt = (n + 1) / 2;
     for (int t = tid; t < nt * nt; t += blockDim.x) {
       const int i0 = 2 * (t / nt), j0 = 2 * (t % nt);
       const bool i1ok = i0 + 1 < n, j1ok = j0 + 1 < n;
       R acc[2][2][2] = {};
-      auto fetch = [&](int p, R& ph0, R& ph1, R2& ps0, R2& ps1) {
-        if (STAGE) {
-          ph0 = PH[p * n + i0];
-          ph1 = i1ok ? PH[p * n + i0 + 1] : R(0);
-          ps0 = Y[(size_t)p * ldy + j0];
-          ps1 = j1ok ? Y[(size_t)p * ldy + j0 + 1] : ps0;
-        } else {
-          ph0 = a.phi_r[(size_t)p * a.ncol + c0 + i0];
-          ph1 = i1ok ? a.phi_r[(size_t)p * a.ncol + c0 + i0 + 1] : R(0);
-          ps0 = psw[(size_t)p * a.ncol + j0];
-          ps1 = j1ok ? psw[(size_t)p * a.ncol + j0 + 1] : ps0;
+      if (CPHI) {
+        const R2* PHc = reinterpret_cast<const R2*>(PH);
+        for (int p = 0; p < N; ++p) {
+          R2 f[2], g[2];
+          f[0] = STAGE ? PHc[p * n + i0] : a.phi_c[(size_t)p * a.ncol + c0 + i0];
+          f[1] = i1ok ? (STAGE ? PHc[p * n + i0 + 1] : a.phi_c[(size_t)p * a.ncol + c0 + i0 + 1]) : R2{R(0), R(0)};
+          g[0] = STAGE ? Y[(size_t)p * ldy + j0] : psw[(size_t)p * a.ncol + j0];
+          g[1] = j1ok ? (STAGE ? Y[(size_t)p * ldy + j0 + 1] : psw[(size_t)p * a.ncol + j0 + 1]) : g[0];
+#pragma unroll
+          for (int di = 0; di < 2; ++di)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj) {   // conj(f) g
+              acc[di][dj][0] += f[di].x * g[dj].x + f[di].y * g[dj].y;
+              acc[di][dj][1] += f[di].x * g[dj].y - f[di].y * g[dj].x;
+            }
         }
-      };
-      auto mac = [&](R ph0, R ph1, R2 ps0, R2 ps1) {
-        acc[0][0][0] += ph0 * ps0.x; acc[0][0][1] += ph0 * ps0.y;
-        acc[0][1][0] += ph0 * ps1.x; acc[0][1][1] += ph0 * ps1.y;
-        acc[1][0][0] += ph1 * ps0.x; acc[1][0][1] += ph1 * ps0.y;
-        acc[1][1][0] += ph1 * ps1.x; acc[1][1][1] += ph1 * ps1.y;
-      };
-      int p = 0;
-      for (; p + 4 <= N; p += 4) {   // four rows of loads in flight, then their products in order
-        R f0[4], f1[4];
-        R2 g0[4], g1[4];
+      } else {
+        auto fetch = [&](int p, R& ph0, R& ph1, R2& ps0, R2& ps1) {
+          if (STAGE) {
+            ph0 = PH[p * n + i0];
+            ph1 = i1ok ? PH[p * n + i0 + 1] : R(0);
+            ps0 = Y[(size_t)p * ldy + j0];
+            ps1 = j1ok ? Y[(size_t)p * ldy + j0 + 1] : ps0;
+          } else {
+            ph0 = a.phi_r[(size_t)p * a.ncol + c0 + i0];
+            ph1 = i1ok ? a.phi_r[(size_t)p * a.ncol + c0 + i0 + 1] : R(0);
+            ps0 = psw[(size_t)p * a.ncol + j0];
+            ps1 = j1ok ? psw[(size_t)p * a.ncol + j0 + 1] : ps0;
+          }
+        };
+        auto mac = [&](R ph0, R ph1, R2 ps0, R2 ps1) {
+          acc[0][0][0] += ph0 * ps0.x; acc[0][0][1] += ph0 * ps0.y;
+          acc[0][1][0] += ph0 * ps1.x; acc[0][1][1] += ph0 * ps1.y;
+          acc[1][0][0] += ph1 * ps0.x; acc[1][0][1] += ph1 * ps0.y;
+          acc[1][1][0] += ph1 * ps1.x; acc[1][1][1] += ph1 * ps1.y;
+        };
+        int p = 0;
+        for (; p + 4 <= N; p += 4) {   // four rows of loads in flight, then their products in order
+          R f0[4], f1[4];
+          R2 g0[4], g1[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) fetch(p + u, f0[u], f1[u], g0[u], g1[u]);
+          for (int u = 0; u < 4; ++u) fetch(p + u, f0[u], f1[u], g0[u], g1[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) mac(f0[u], f1[u], g0[u], g1[u]);
-      }
-      for (; p < N; ++p) {
-        R f0, f1;
-        R2 g0, g1;
-        fetch(p, f0, f1, g0, g1);
-        mac(f0, f1, g0, g1);
+          for (int u = 0; u < 4; ++u) mac(f0[u], f1[u], g0[u], g1[u]);
+        }
+        for (; p < N; ++p) {
+          R f0, f1;
+          R2 g0, g1;
+          fetch(p, f0, f1, g0, g1);
+          mac(f0, f1, g0, g1);
+        }
       }
       for (int di = 0; di < 2; ++di)
         for (int dj = 0; dj < 2; ++dj)

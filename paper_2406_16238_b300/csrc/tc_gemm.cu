@@ -79,7 +79,8 @@ struct Params {
   // bf16 plane epilogue
   __nv_bfloat16* planes;
   int npad, kq;   // plane rows, plane row pitch (elements)
-  const int* pairs;   // packed L^T: p N + q of each packed row (p <= q), or NULL (rows are pq)
+  const int* pairs;   // packed L^T: p N + q of each packed row (p <= q; -1: a row left out), or NULL
+  const int2* blocks; // packed L^T: the (8-row p block, 16-column q block) of each M tile
   // exchange: an extra warp draws the step's normals (nrm.x != nullptr)
   NormalsJob nrm;
   // exchange with the Ltilde tile in tensor memory: segment length and the tensor-memory column of
@@ -332,15 +333,11 @@ __device__ void store_tile(const Params& p, int mt, int nt, uint32_t tacc, int g
 // Tile rows are pq = p N + q (M over N^2), columns are (w, part) = 2 w + part.  Each value is
 // split into hi = bf16(v), lo = bf16(v - hi) and written to the plane
 // [w][hi re, hi im, lo re, lo im][npad][kq] at (p, q).  Consecutive lanes hold consecutive pq,
-// so every store instruction covers a contiguous run of q.  With packed L^T the rows are the pairs
-// p <= q (row-major over the upper triangle; out_cols = their count) and each value is also
-// written at (q, p): V is symmetric because every L^g is.
+// so every store instruction covers a contiguous run of q.
 __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int group, int r) {
-  const int row = mt * kBM + r;
-  const bool live = row < p.out_cols;
-  const int pq = live ? (p.pairs ? p.pairs[row] : row) : 0;
-  const int pp = pq / p.n, qq = pq - pp * p.n;
-  const bool mirror = p.pairs != nullptr && pp != qq;
+  const int pq = mt * kBM + r;
+  const bool live = pq < p.out_cols;
+  const int pp = live ? pq / p.n : 0, qq = live ? pq - pp * p.n : 0;
   const int ncols = p.g.bn / p.g.epi_groups;   // a multiple of 8
   const int cbeg = group * ncols;
   const size_t plane = (size_t)p.npad * p.kq;
@@ -348,17 +345,10 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
     for (int i = 0; i < cnt; ++i) {
       const int col = nt * p.g.n_step + c + i;
       if (col >= p.out_rows) break;
-      __nv_bfloat16* base = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane;
-      __nv_bfloat16* dst = base + (size_t)pp * p.kq + qq;
+      __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * p.kq + qq;
       const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
       dst[0] = hi;
-      dst[2 * plane] = lo;
-      if (mirror) {
-        __nv_bfloat16* tr = base + (size_t)qq * p.kq + pp;
-        tr[0] = hi;
-        tr[2 * plane] = lo;
-      }
+      dst[2 * plane] = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
     }
   };
   float v[16];
@@ -374,6 +364,64 @@ __device__ void store_planes(const Params& p, int mt, int nt, uint32_t tacc, int
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r8[i]);
     if (live) put(c, 8, v);
+  }
+}
+
+// Packed L^T: each M tile is one block of the symmetric V, p in [8 bi, 8 bi + 8) x q in
+// [16 bj, 16 bj + 16) (row r = 16 (p - 8 bi) + q - 16 bj), with 8 bi <= 16 bj + 15.  Entries with
+// p <= q are written at (p, q): a warp covers two p rows of 16 q (two full 32-byte sectors).  Entries
+// with p < q are also written at (q, p): staged per group in shared memory, eight columns at a time,
+// then written as rows of 8 consecutive p (16-byte stores; blocks (bi, bj) and (bi + 1, bj) are
+// consecutive tiles, so the other half of each sector follows at once).  stage: 8 columns x 128 rows x
+// (hi, lo) bf16 = 4 KiB per group.
+__device__ void store_planes_packed(const Params& p, int mt, int nt, uint32_t tacc, int group, int r,
+                                    __nv_bfloat16* stage) {
+  const int2 blk = p.blocks[mt];
+  const int p0 = 8 * blk.x, q0 = 16 * blk.y;
+  const int pp = p0 + (r >> 4), qq = q0 + (r & 15);
+  const bool direct = pp < p.n && qq < p.n && pp <= qq;
+  const bool full = p0 + 7 < q0;   // every entry of the block has p < q
+  const int ncols = p.g.bn / p.g.epi_groups;   // a multiple of 8
+  const int cbeg = group * ncols;
+  const size_t plane = (size_t)p.npad * p.kq;
+  const int tid = r;   // 0 .. 127 within the group
+  for (int c = cbeg; c < cbeg + ncols; c += 8) {
+    uint32_t r8[8];
+    tmem_ld8_nowait(tacc + (uint32_t)c, r8);
+    tmem_wait();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float v = __uint_as_float(r8[i]);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      const int col = nt * p.g.n_step + c + i;
+      if (direct && col < p.out_rows) {
+        __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1)) * plane + (size_t)pp * p.kq + qq;
+        dst[0] = hi;
+        dst[2 * plane] = lo;
+      }
+      stage[(i * 2 + 0) * 128 + r] = hi;
+      stage[(i * 2 + 1) * 128 + r] = lo;
+    }
+    named_bar(5 + group, 128);
+    // mirrored rows: 8 columns x 2 parts x 16 q rows, 8 consecutive p each
+    for (int task = tid; task < 8 * 2 * 16; task += 128) {
+      const int i = task >> 5, hl = (task >> 4) & 1, ql = task & 15;
+      const int col = nt * p.g.n_step + c + i, q = q0 + ql;
+      if (col >= p.out_rows || q >= p.n) continue;
+      const __nv_bfloat16* src = stage + (i * 2 + hl) * 128 + ql;   // rows 16 pl + ql
+      __nv_bfloat16* dst = p.planes + ((size_t)(col >> 1) * 4 + (col & 1) + 2 * hl) * plane + (size_t)q * p.kq + p0;
+      if (full) {
+        __align__(16) __nv_bfloat16 row[8];
+#pragma unroll
+        for (int pl = 0; pl < 8; ++pl) row[pl] = src[16 * pl];
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(row);
+      } else {
+        for (int pl = 0; pl < 8; ++pl)
+          if (p0 + pl < q && p0 + pl < p.n) dst[pl] = src[16 * pl];
+      }
+    }
+    named_bar(5 + group, 128);   // the stage is rewritten by the next columns
   }
 }
 
@@ -538,6 +586,9 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       if constexpr (EPI == 0 && NB > 0) exchange_tile_reg<NB>(p, mt, nt, tacc, es, group, wig, r, lane);
       else if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
       else if (EPI == 1) store_tile(p, mt, nt, tacc, group, r);
+      else if (p.blocks)
+        store_planes_packed(p, mt, nt, tacc, group, r,
+                            reinterpret_cast<__nv_bfloat16*>(epi_base + (size_t)group * g.epi_bytes + 16));
       else store_planes(p, mt, nt, tacc, group, r);
       tc_fence_before();
       __syncwarp();
@@ -806,8 +857,8 @@ __global__ void __launch_bounds__(256) k_lt_bf16(int g0, int ng, size_t NN, size
   for (int i = threadIdx.x; i < 32 * 64; i += 256) {
     const int gl = i / 64, c = i % 64;
     const size_t row = pq0 + c;
-    const size_t src = row < nrows ? (pairs ? (size_t)pairs[row] : row) : 0;
-    tile[gl][c] = (gt + gl < ng && row < nrows) ? (float)chol[(size_t)(gt + gl) * NN + src] : 0.f;
+    const long long src = row < nrows ? (pairs ? (long long)pairs[row] : (long long)row) : -1;
+    tile[gl][c] = (gt + gl < ng && src >= 0) ? (float)chol[(size_t)(gt + gl) * NN + (size_t)src] : 0.f;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 32 * 64; i += 256) {
@@ -1068,10 +1119,18 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   // packed L^T (the upper triangle p <= q only) where the large-form propagation consumes the V
   // planes: the VHS GEMM then reads half of L and its epilogue writes each V_pq at (p, q) and (q, p)
   st->packed = (st->pg.ok && st->pg.large) ? 1 : 0;
-  st->lt_rows = st->packed ? (long long)N * (N + 1) / 2 : (long long)N * N;
-  if (st->packed) {
+  st->lt_rows = (long long)N * N;
+  st->nblocks = 0;
+  if (st->packed) {   // blocks of 8 p x 16 q touching the upper triangle, 128 rows each
+    const int bi = (N + 7) / 8, bj = (N + 15) / 16;
+    long long nb = 0;
+    for (int j = 0; j < bj; ++j) nb += std::min(bi, (16 * j + 15) / 8 + 1);
+    st->nblocks = nb;
+    st->lt_rows = nb * 128;
     st->off_pairs = cur;
     cur = align256(cur + (size_t)st->lt_rows * 4);
+    st->off_blocks = cur;
+    cur = align256(cur + (size_t)nb * 8);
   }
   st->off_lt = cur;
   cur = align256(cur + (size_t)st->lt_rows * st->vparts * st->kx * 2);
@@ -1137,12 +1196,22 @@ afqmc_status begin(TcState* st, cudaStream_t s, char* tcbuf, char* err, size_t e
     snprintf(err, errlen, "tc set-up: clearing the operand buffers failed");
     return AFQMC_ECUDA;
   }
-  if (st->packed) {   // p N + q of each packed row, row-major over the upper triangle
+  if (st->packed) {   // blocks in q-block order, p blocks ascending; p N + q per row, -1 where left out
+    const int N = st->N, bi = (N + 7) / 8, bj = (N + 15) / 16;
     std::vector<int> pairs((size_t)st->lt_rows);
-    size_t r = 0;
-    for (int pp = 0; pp < st->N; ++pp)
-      for (int qq = pp; qq < st->N; ++qq) pairs[r++] = pp * st->N + qq;
+    std::vector<int2> blocks((size_t)st->nblocks);
+    size_t b = 0;
+    for (int j = 0; j < bj; ++j)
+      for (int i = 0; i < std::min(bi, (16 * j + 15) / 8 + 1); ++i, ++b) {
+        blocks[b] = make_int2(i, j);
+        for (int r = 0; r < 128; ++r) {
+          const int pp = 8 * i + r / 16, qq = 16 * j + r % 16;
+          pairs[b * 128 + r] = (pp < N && qq < N && pp <= qq) ? pp * N + qq : -1;
+        }
+      }
     if (cudaMemcpyAsync(tcbuf + st->off_pairs, pairs.data(), pairs.size() * 4, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(tcbuf + st->off_blocks, blocks.data(), blocks.size() * 8, cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       snprintf(err, errlen, "tc set-up: the packed pair table copy failed");
@@ -1352,7 +1421,7 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   g.m_step = kBM;
   g.n_step = st->vhs_bn;
   g.bn = st->vhs_bn;
-  if (!finish_geom(&g, 16, 4)) {
+  if (!finish_geom(&g, 16 + (st->packed ? 4096 : 0), 4)) {
     snprintf(err, errlen, "tcgen05 VHS: shared memory plan failed");
     return AFQMC_EINVAL;
   }
@@ -1363,6 +1432,7 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   p.out_rows = 2 * st->W;
   p.out_cols = (int)st->lt_rows;
   p.pairs = st->packed ? reinterpret_cast<const int*>(tcbuf + st->off_pairs) : nullptr;
+  p.blocks = st->packed ? reinterpret_cast<const int2*>(tcbuf + st->off_blocks) : nullptr;
   p.planes = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_vp);
   p.npad = st->pg.npad;
   p.kq = st->pg.kq;

@@ -58,9 +58,11 @@ struct TcState {
   // VHS build
   int kx = 0;         // padded naux (multiple of 64)
   int vparts = 1;     // stored parts of the VHS operands: [hi | lo] (BF16x3) or hi (BF16)
-  int packed = 0;     // L^T holds only the pairs p <= q (large-form propagation; see plan)
-  long long lt_rows = 0;   // rows of L^T: N^2, or N (N + 1) / 2 when packed
-  size_t off_pairs = 0;    // packed: int32 p N + q per row
+  int packed = 0;     // L^T holds only blocks touching the upper triangle (large-form propagation; see plan)
+  long long lt_rows = 0;   // rows of L^T: N^2, or 128 per packed block
+  long long nblocks = 0;   // packed: 8 x 16 (p, q) blocks, one M tile each
+  size_t off_pairs = 0;    // packed: int32 p N + q per row (-1: a row left out)
+  size_t off_blocks = 0;   // packed: int2 (p block, q block) per M tile
   size_t off_lt = 0, off_coef = 0;
   int vhs_m_tiles = 0, vhs_n_tiles = 0;
   int vhs_bn = 256;   // N tile of the VHS planes GEMM (multiple of 32)
