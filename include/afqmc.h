@@ -156,8 +156,10 @@ afqmc_status afqmc_create_end(afqmc_ctx* ctx);
  * Each vector gives two auxiliary fields with the Hermitian matrices A = (L + L^+) / 2 and
  * B = i (L - L^+) / 2, so the context draws 2 naux fields per walker (afqmc_get_fields, info.naux
  * report 2 naux); every formula of the real case holds with the trial's conjugate transpose.
- * Complex contexts run in the FP64 and FP32 forms (CUDA cores; the BF16 forms are rejected), without
- * the control variate. */
+ * Every precision form runs complex contexts.  The BF16 / BF16X3 forms realify each contraction along
+ * K (a complex product as one real GEMM over [Re | Im] halves: the exchange, the VHS build over the
+ * 2 naux fields and the propagation with complex E_h all take twice the K of a real context of the
+ * same size).  The control variate takes real Hamiltonians only. */
 afqmc_status afqmc_workspace_size_complex(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta,
                                           const double* psiT, const afqmc_params* params, size_t* bytes);
 afqmc_status afqmc_create_begin_complex(const double* h1e, double ecore, int32_t norb, int32_t naux, int32_t nalpha,

@@ -135,7 +135,7 @@ Layout plan(const Dims& d) {
   L.sflag = take(256);   // set-up: input check flags, the 1-norm of the exponent
   {
     tc::TcState tmp;
-    L.tc_bytes = tc::plan(&tmp, d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk);
+    L.tc_bytes = tc::plan(&tmp, d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk, d.cplx);
   }
   L.tc = take(L.tc_bytes);
   L.vhs_bytes = W * N * N * C;
@@ -165,8 +165,6 @@ afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta
   if (p->reserved != 0) return fail(AFQMC_EINVAL, "params.reserved must be 0");
   if (!psiT) return fail(AFQMC_EINVAL, "psiT is NULL");
   if ((long long)norb * norb > (1ll << 31) / 2) return fail(AFQMC_EINVAL, "norb too large");
-  if (cplx && (p->prec == AFQMC_PREC_BF16 || p->prec == AFQMC_PREC_BF16X3))
-    return fail(AFQMC_EINVAL, "complex Hamiltonians run in the FP64 and FP32 forms");
   if (cplx && (long long)naux * 2 > (1ll << 30)) return fail(AFQMC_EINVAL, "naux too large");
   d->N = norb; d->X = cplx ? 2 * naux : naux; d->na = nalpha; d->nb = nbeta; d->W = p->nwalkers; d->prec = p->prec;
   d->cplx = cplx;
@@ -185,7 +183,7 @@ afqmc_status make_dims(int32_t norb, int32_t naux, int32_t nalpha, int32_t nbeta
   d->nchunk = (d->X + d->gchunk - 1) / d->gchunk;
   if (d->tensor()) {   // exchange partials come per (spin block, M tile) of the tensor-core kernel
     tc::TcState tmp;
-    tc::plan(&tmp, d->prec, d->W, d->N, d->X, d->ncol, d->c0, d->nbk, d->nblk);
+    tc::plan(&tmp, d->prec, d->W, d->N, d->X, d->ncol, d->c0, d->nbk, d->nblk, cplx);
     d->nchunk = tmp.nchunk;
   }
   return AFQMC_OK;
@@ -391,6 +389,7 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
                    : nullptr;
   a.kst = c->tcs.kst;
   a.nseg = c->tcs.nseg;
+  a.kst0 = (c->d.cplx && c->d.tensor()) ? c->tcs.kst0 : 0;
   return a;
 }
 
@@ -618,6 +617,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
     fa.coefb = reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.off_coef);
     fa.kx = c->tcs.kx;
     fa.nseg = c->tcs.nseg;
+    fa.kx0 = d.cplx ? c->tcs.kx0 : 0;
   }
   k_fields<R><<<d.W, 256, 0, c->stream>>>(fa);
   delete tf;
@@ -852,7 +852,7 @@ afqmc_status setup_begin_s(afqmc_ctx* c, const double* h1e_d, const double* psiT
   const double flops = 2.0 * d.X * (double)N * N * N * cm * cm + 2.0 * d.X * (double)nc * N * N * cm * cm;
   c->setup_f32 = d.prec != AFQMC_PREC_FP64 && flops > 4e11;
   if (d.tensor()) {
-    tc::plan(&c->tcs, d.prec, d.W, N, d.X, nc, d.c0, d.nbk, d.nblk);
+    tc::plan(&c->tcs, d.prec, d.W, N, d.X, nc, d.c0, d.nbk, d.nblk, d.cplx);
     if ((st = tc::begin(&c->tcs, c->stream, c->at<char>(c->L.tc), g_err, sizeof(g_err))) != AFQMC_OK) return st;
   }
   // the synchronisation keeps the host vectors alive until their copies are done
@@ -979,6 +979,9 @@ afqmc_status setup_chunk_c(afqmc_ctx* c, int g0, int ng, const T* src, char* scr
   k_cast<G, R><<<592, 256, 0, c->stream>>>((size_t)nf * nc * N * 2, reinterpret_cast<const G*>(lrot),
                                             c->at<R>(c->L.lrot) + (size_t)f0 * nc * N * 2);
   CHECK_LAUNCH(c);
+  if (d.tensor())   // the realified bf16 operands of the exchange and the VHS build
+    return tc::load_chunk_c<G>(&c->tcs, c->stream, c->at<char>(c->L.tc), f0, nf, fields,
+                               reinterpret_cast<const G*>(lrot), &c->launches, g_err, sizeof(g_err));
   k_cast<G, R><<<592, 256, 0, c->stream>>>((size_t)nf * NN * 2, fields, c->at<R>(c->L.chol) + (size_t)f0 * NN * 2);
   CHECK_LAUNCH(c);
   return AFQMC_OK;

@@ -171,24 +171,37 @@ struct OverlapArgs {
   // (w, part, b) of nseg * kst bf16 = [hi | hi | lo] (hi only when nseg = 1)
   __nv_bfloat16* thb[2];
   int kst, nseg;
+  int kst0;                       // complex Hamiltonian: the realified operand layout (0: real)
 };
 
 // Theta^T entry (b, p) of walker w as the split-bf16 exchange operand of its block.
 template <typename R2>
 __device__ __forceinline__ void store_theta_bf16(__nv_bfloat16* out, int kst, int nseg, int n, int w, int b, int p,
-                                                 R2 v) {
+                                                 R2 v, int kst0 = 0) {
   const size_t rowlen = (size_t)nseg * kst;
   __nv_bfloat16* re = out + ((size_t)w * 2 * n + b) * rowlen + p;
   __nv_bfloat16* im = re + (size_t)n * rowlen;
   const float fx = (float)v.x, fy = (float)v.y;
   const __nv_bfloat16 hr = __float2bfloat16_rn(fx), hi = __float2bfloat16_rn(fy);
+  const __nv_bfloat16 lr = __float2bfloat16_rn(fx - __bfloat162float(hr));
+  const __nv_bfloat16 li = __float2bfloat16_rn(fy - __bfloat162float(hi));
   re[0] = hr;
   im[0] = hi;
   if (nseg == 3) {
     re[kst] = hr;
     im[kst] = hi;
-    re[2 * kst] = __float2bfloat16_rn(fx - __bfloat162float(hr));
-    im[2 * kst] = __float2bfloat16_rn(fy - __bfloat162float(hi));
+    re[2 * kst] = lr;
+    im[2 * kst] = li;
+  }
+  if (kst0) {   // complex Hamiltonian: rows [Re | Im] and [Im | -Re] (each real part kst0 long)
+    re[kst0] = hi;
+    im[kst0] = __hneg(hr);
+    if (nseg == 3) {
+      re[kst + kst0] = hi;
+      im[kst + kst0] = __hneg(hr);
+      re[2 * kst + kst0] = li;
+      im[2 * kst + kst0] = __hneg(lr);
+    }
   }
 }
 
@@ -427,6 +440,7 @@ struct FieldArgs {
   cplx_t<R>* coef;          // [W][X]
   __nv_bfloat16* coefb;     // optional: rows (w, part) of bf16 [hi | lo] (kx each; hi only if nseg = 1)
   int kx, nseg;
+  int kx0;                  // complex Hamiltonian: rows (w, 0) = [Re c | -Im c], (w, 1) = [Im c | Re c] (kx0 each)
   double2* cmf;             // [W]
   double2* xxbar;           // [W]
   int free_proj;            // free projection: no force-bias shift (xbar = 0)
@@ -497,11 +511,21 @@ __global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
         __nv_bfloat16* im = re + rowlen;
         const float fx = (float)cf.x, fy = (float)cf.y;
         const __nv_bfloat16 hr = __float2bfloat16_rn(fx), hi = __float2bfloat16_rn(fy);
+        const __nv_bfloat16 lr = __float2bfloat16_rn(fx - __bfloat162float(hr));
+        const __nv_bfloat16 li = __float2bfloat16_rn(fy - __bfloat162float(hi));
         re[0] = hr;
         im[0] = hi;
         if (a.nseg == 3) {
-          re[a.kx] = __float2bfloat16_rn(fx - __bfloat162float(hr));
-          im[a.kx] = __float2bfloat16_rn(fy - __bfloat162float(hi));
+          re[a.kx] = lr;
+          im[a.kx] = li;
+        }
+        if (a.kx0) {   // the second real part of each complex row
+          re[a.kx0] = __hneg(hi);
+          im[a.kx0] = hr;
+          if (a.nseg == 3) {
+            re[a.kx + a.kx0] = __hneg(li);
+            im[a.kx + a.kx0] = lr;
+          }
         }
       }
       cm.x = fma(-sl, xs.y, cm.x);
@@ -945,7 +969,8 @@ __device__ __forceinline__ void csub(cplx_t<R>& acc, const cplx_t<R>& a, const c
 // code would be fetched cold from L2 on every launch.
 template <typename R>
 __device__ __forceinline__ void subst_rows_blocked(cplx_t<R>* Y, int ldy, const cplx_t<R>* F, const int* perm, int n,
-                                                   int N, cplx_t<R>* thw, __nv_bfloat16* thb, int kst, int nseg, int w) {
+                                                   int N, cplx_t<R>* thw, __nv_bfloat16* thb, int kst, int nseg, int w,
+                                                   int kst0 = 0) {
   using R2 = cplx_t<R>;
   for (int p = threadIdx.x; p < N; p += blockDim.x) {
     R2* y = Y + (size_t)p * ldy;
@@ -1011,7 +1036,7 @@ __device__ __forceinline__ void subst_rows_blocked(cplx_t<R>* Y, int ldy, const 
       const R2 v = y[i];
       const int b = perm[i];
       thw[(size_t)b * N + p] = v;
-      if (thb) store_theta_bf16(thb, kst, nseg, n, w, b, p, v);
+      if (thb) store_theta_bf16(thb, kst, nseg, n, w, b, p, v, kst0);
     }
   }
 }
@@ -1257,7 +1282,7 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
         const int b = idx / N, p = idx % N;
         const R2 z = from_d2<R>(mk(0.0, 0.0));
         a.thetaT[((size_t)w * a.ncol + c0 + b) * N + p] = z;
-        if (a.thb[s]) store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, z);
+        if (a.thb[s]) store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, z, a.kst0);
       }
       continue;
     }
@@ -1283,7 +1308,7 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
     __syncthreads();
     R2* thw = a.thetaT + ((size_t)w * a.ncol + c0) * N;
     if (STAGE) {
-      subst_rows_blocked<R>(Y, ldy, F, perm, n, N, thw, a.thb[s], a.kst, a.nseg, w);
+      subst_rows_blocked<R>(Y, ldy, F, perm, n, N, thw, a.thb[s], a.kst, a.nseg, w, a.kst0);
     } else {   // row perm[k] of Theta^T holds y_k of every psi row throughout (no final permutation)
       for (int p = tid; p < N; p += blockDim.x) {
         auto at = [&](int k) -> R2& { return thw[(size_t)perm[k] * N + p]; };
@@ -1335,7 +1360,7 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
       if (a.thb[s])
         for (int idx = tid; idx < n * N; idx += blockDim.x) {
           const int b = idx / N, p = idx % N;
-          store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, thw[(size_t)b * N + p]);
+          store_theta_bf16(a.thb[s], a.kst, a.nseg, n, w, b, p, thw[(size_t)b * N + p], a.kst0);
         }
     }
     // log det = log(prod) + exp ln 2 (+ i pi for an odd number of row swaps); the real and

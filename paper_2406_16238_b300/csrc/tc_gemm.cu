@@ -796,20 +796,24 @@ __global__ void __launch_bounds__(608, 1) k_exch_tm(const __grid_constant__ CUte
 // ----------------------------------------------------------------------------- operand conversion
 // Theta^T complex64 [W][ncol][N] -> per block rows (w, part, b) of nseg * kst bf16: B = [hi | hi | lo].
 __global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int nseg, const float2* thetaT,
-                             __nv_bfloat16* out, const int* widx) {
+                             __nv_bfloat16* out, const int* widx, int kst0 = 0) {
   const int w = blockIdx.x;              // output row block
   const int src = widx ? widx[w] : w;    // walker it holds
   const int rowlen = nseg * kst;
   for (int idx = threadIdx.x; idx < 2 * n * kst; idx += blockDim.x) {
-    const int row = idx / kst, pp = idx % kst;
+    const int row = idx / kst, k = idx % kst;
     const int part = row / n, b = row % n;
+    // complex Hamiltonian (kst0 > 0): row (w, 0, b) = [Re | Im], row (w, 1, b) = [Im | -Re]
+    const int half = kst0 ? k / kst0 : 0, pp = kst0 ? k - half * kst0 : k;
     float v = 0.f;
     if (pp < N) {
       const float2 t = thetaT[((size_t)src * ncol + c0 + b) * N + pp];
-      v = part ? t.y : t.x;
+      if (!kst0) v = part ? t.y : t.x;
+      else if (part == 0) v = half ? t.y : t.x;
+      else v = half ? -t.x : t.y;
     }
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    __nv_bfloat16* dst = out + ((size_t)w * 2 * n + row) * rowlen + pp;
+    __nv_bfloat16* dst = out + ((size_t)w * 2 * n + row) * rowlen + k;
     dst[0] = hi;
     if (nseg == 3) {
       const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
@@ -873,20 +877,80 @@ __global__ void __launch_bounds__(256) k_lt_bf16(int g0, int ng, size_t NN, size
   }
 }
 
+// Complex Hamiltonian, exchange A: Ltilde complex [nf][ncol][N] (fields f0 ..) -> block rows (f, a) of
+// nseg * kst bf16, each segment [Re (kst0) | -Im (kst0)], segments [hi | lo | hi].
+template <typename G>
+__global__ void k_lrot_bf16_c(int f0, int nf, int N, int ncol, int c0, int n, int kst, int kst0, int nseg,
+                              const G* lrot, __nv_bfloat16* out) {
+  const int rowlen = nseg * kst;
+  const size_t total = (size_t)nf * n * kst;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = idx / kst;
+    const int k = (int)(idx % kst), part = k / kst0, pp = k - part * kst0;
+    const int g = (int)(row / n), a = (int)(row % n);
+    double v = 0.0;
+    if (pp < N) {
+      const size_t e = 2 * (((size_t)g * ncol + c0 + a) * N + pp);
+      v = part ? -(double)lrot[e + 1] : (double)lrot[e];
+    }
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    __nv_bfloat16* dst = out + ((size_t)f0 * n + row) * rowlen + k;
+    dst[0] = hi;
+    if (nseg == 3) {
+      dst[kst] = __double2bfloat16(v - (double)__bfloat162float(hi));
+      dst[2 * kst] = hi;
+    }
+  }
+}
+
+// Complex Hamiltonian, VHS A: fields complex [nf][NN] (f0 ..) -> columns f0 + f (real part) and
+// kx0 + f0 + f (imaginary part) of the Lt rows pq, each row [hi | lo] of kx.
+template <typename G>
+__global__ void __launch_bounds__(256) k_lt_bf16_c(int f0, int nf, size_t NN, int kx, int kx0, int nseg,
+                                                   const G* fields, __nv_bfloat16* out) {
+  __shared__ float tile[2][32][65];
+  const size_t rowlen = (size_t)(nseg == 3 ? 2 : 1) * kx;
+  const size_t pq0 = (size_t)blockIdx.x * 64;
+  const int gt = blockIdx.y * 32;
+  for (int i = threadIdx.x; i < 32 * 64; i += 256) {
+    const int gl = i / 64, c = i % 64;
+    const size_t pq = pq0 + c;
+    const bool ok = gt + gl < nf && pq < NN;
+    const size_t e = 2 * ((size_t)(gt + gl) * NN + pq);
+    tile[0][gl][c] = ok ? (float)fields[e] : 0.f;
+    tile[1][gl][c] = ok ? (float)fields[e + 1] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * 32 * 64; i += 256) {
+    const int part = i / 2048, rem = i % 2048, c = rem / 32, gl = rem % 32;
+    const size_t pq = pq0 + c;
+    if (gt + gl >= nf || pq >= NN) continue;
+    const float v = tile[part][gl][c];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16* dst = out + pq * rowlen + (size_t)part * kx0 + f0 + gt + gl;
+    dst[0] = hi;
+    if (nseg == 3) dst[kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
 // VHS coefficients complex64 [W][X] -> rows (w, part) of [hi | lo] bf16 (kx elements per part; hi
-// only when nseg = 1).
-__global__ void k_coef_bf16(int W, int X, int kx, int nseg, const float2* coef, __nv_bfloat16* out) {
+// only when nseg = 1).  Complex Hamiltonian (kx0 > 0): row (w, 0) = [Re c | -Im c], row (w, 1) =
+// [Im c | Re c], each real part kx0 long.
+__global__ void k_coef_bf16(int W, int X, int kx, int nseg, const float2* coef, __nv_bfloat16* out, int kx0 = 0) {
   const int w = blockIdx.x;
   const int rowlen = (nseg == 3 ? 2 : 1) * kx;
   for (int idx = threadIdx.x; idx < 2 * kx; idx += blockDim.x) {
-    const int part = idx / kx, g = idx % kx;
+    const int part = idx / kx, k = idx % kx;
+    const int half = kx0 ? k / kx0 : 0, g = kx0 ? k - half * kx0 : k;
     float v = 0.f;
     if (g < X) {
       const float2 c = coef[(size_t)w * X + g];
-      v = part ? c.y : c.x;
+      if (!kx0) v = part ? c.y : c.x;
+      else if (part == 0) v = half ? -c.y : c.x;
+      else v = half ? c.x : c.y;
     }
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    __nv_bfloat16* dst = out + ((size_t)w * 2 + part) * rowlen + g;
+    __nv_bfloat16* dst = out + ((size_t)w * 2 + part) * rowlen + k;
     dst[0] = hi;
     if (nseg == 3) dst[kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
@@ -1091,13 +1155,21 @@ void exchange_config(TcState* st, BlockMaps& bm, int groups, int form) {
 }
 }  // namespace
 
-size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk) {
+size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk,
+            bool cplx) {
   if (prec != AFQMC_PREC_BF16 && prec != AFQMC_PREC_BF16X3) return 0;
   st->prec = prec;
   st->W = W; st->N = N; st->X = X; st->ncol = ncol; st->nblk = nblk;
+  st->cplx = cplx ? 1 : 0;
   st->nseg = prec == AFQMC_PREC_BF16X3 ? 3 : 1;
-  st->kst = (N + 15) / 16 * 16;   // segments padded to the MMA k-step only; the last TMA box reads past K
-  st->kx = (X + kBK - 1) / kBK * kBK;
+  // segments padded to the MMA k-step only; the last TMA box reads past K.  A complex Hamiltonian
+  // realifies every contraction along K: exchange A rows [Re Ltilde | -Im Ltilde], B rows
+  // [Re Theta | Im Theta] and [Im Theta | -Re Theta]; VHS A rows [Re M | Im M] over the fields, B rows
+  // [Re c | -Im c] and [Im c | Re c]; each real part padded to kst0 / kx0
+  st->kst0 = (N + 15) / 16 * 16;
+  st->kst = cplx ? 2 * st->kst0 : st->kst0;
+  st->kx0 = (X + kBK - 1) / kBK * kBK;
+  st->kx = cplx ? 2 * st->kx0 : st->kx0;
   size_t cur = 0;
   st->nchunk = 0;
   for (int s = 0; s < nblk; ++s) {
@@ -1115,10 +1187,11 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     st->nchunk += 4 * b.m_tiles;   // four exchange partial slots per M tile (one per epilogue warp)
   }
   st->vparts = st->nseg == 3 ? 2 : 1;   // VHS operands stored [hi | lo] (see Geom::dual)
-  st->pg = prop_geom(N, ncol);
+  st->pg = prop_geom(N, ncol, cplx);
   // packed L^T (the upper triangle p <= q only) where the large-form propagation consumes the V
   // planes: the VHS GEMM then reads half of L and its epilogue writes each V_pq at (p, q) and (q, p)
-  st->packed = (st->pg.ok && st->pg.large) ? 1 : 0;
+  // (V symmetric: real symmetric L; a complex Hamiltonian's V is not, so it keeps every row)
+  st->packed = (st->pg.ok && st->pg.large && !cplx) ? 1 : 0;
   st->lt_rows = (long long)N * N;
   st->nblocks = 0;
   if (st->packed) {   // blocks of 8 p x 16 q touching the upper triangle, 128 rows each
@@ -1157,7 +1230,7 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
     st->off_vp = cur;
     cur = align256(cur + (size_t)W * 4 * pg.npad * pg.kq * 2);
     st->off_fp = cur;
-    cur = align256(cur + (size_t)2 * pg.npad * pg.kq * 2);
+    cur = align256(cur + (size_t)(pg.cplx_f ? 4 : 2) * pg.npad * pg.kq * 2);
     if (pg.large) {   // term operands (two, ping-pong) and the Taylor sum
       for (int i = 0; i < 2; ++i) {
         st->off_b[i] = cur;
@@ -1253,6 +1326,33 @@ template afqmc_status load_chunk<double, float>(TcState*, cudaStream_t, char*, i
 template afqmc_status load_chunk<float, double>(TcState*, cudaStream_t, char*, int, int, const float*, const double*,
                                                 unsigned long long*, char*, size_t);
 
+template <typename G>
+afqmc_status load_chunk_c(TcState* st, cudaStream_t s, char* tcbuf, int f0, int nf, const G* fields, const G* lrot,
+                          unsigned long long* launches, char* err, size_t errlen) {
+  for (int b = 0; b < st->nblk; ++b) {
+    const BlockMaps& bm = st->blk[b];
+    if (bm.n == 0) continue;
+    k_lrot_bf16_c<G><<<592, 256, 0, s>>>(f0, nf, st->N, st->ncol, bm.c0, bm.n, st->kst, st->kst0, st->nseg, lrot,
+                                          reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_l));
+    ++*launches;
+  }
+  const size_t NN = (size_t)st->N * st->N;
+  const dim3 grid((unsigned)((NN + 63) / 64), (unsigned)((nf + 31) / 32));
+  k_lt_bf16_c<G><<<grid, 256, 0, s>>>(f0, nf, NN, st->kx, st->kx0, st->nseg, fields,
+                                       reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_lt));
+  ++*launches;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "tc set-up chunk (complex): %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+template afqmc_status load_chunk_c<double>(TcState*, cudaStream_t, char*, int, int, const double*, const double*,
+                                           unsigned long long*, char*, size_t);
+template afqmc_status load_chunk_c<float>(TcState*, cudaStream_t, char*, int, int, const float*, const float*,
+                                          unsigned long long*, char*, size_t);
+
 afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen) {
   for (int b = 0; b < st->nblk; ++b) {
     BlockMaps& bm = st->blk[b];
@@ -1318,7 +1418,8 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
     if (bm.n == 0) continue;
     if (!theta_ready || widx) {
       k_theta_bf16<<<nw, 256, 0, s>>>(nw, st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, thetaT,
-                                      reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th), widx);
+                                      reinterpret_cast<__nv_bfloat16*>(tcbuf + bm.off_th), widx,
+                                      st->cplx ? st->kst0 : 0);
       ++*launches;
     }
     Geom g{};
@@ -1399,7 +1500,7 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
   }
   if (!coef_ready) {
     k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
-                                      reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
+                                      reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef), st->cplx ? st->kx0 : 0);
     ++*launches;
   }
   Geom g{};
@@ -1446,7 +1547,7 @@ afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, f
     return AFQMC_EINVAL;
   }
   k_coef_bf16<<<st->W, 256, 0, s>>>(st->W, st->X, st->kx, st->nseg, coef,
-                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef));
+                                    reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_coef), st->cplx ? st->kx0 : 0);
   ++*launches;
   Geom g{};
   g.m_tiles = st->vhs_m_tiles;

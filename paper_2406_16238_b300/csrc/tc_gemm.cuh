@@ -36,7 +36,10 @@ struct BlockMaps {
 // 4 cwp rows: the term's hi parts, then its lo parts) | mbarriers.
 struct PropGeom {
   int ok = 0;
-  int large = 0;       // 1: N > 128, the batched form (V streamed per product, one launch per product)
+  int large = 0;       // 1: N > 128 (or a complex Hamiltonian), the batched form (V streamed per product,
+                       // one launch per product)
+  int cplx_f = 0;      // complex E_h: F = E_h - I as four planes [Re hi, Im hi, Re lo, Im lo], F products
+                       // over two K halves like the V products
   int npad = 0;        // N rounded up to 8: rows of the V and F planes
   int kq = 0;          // row pitch of the planes: 128 (N <= 128) or N rounded up to 64
   int ncolp = 0;       // large form: walker columns rounded up to 8 (B operand rows 2 ncolp)
@@ -47,10 +50,12 @@ struct PropGeom {
   int off_vlo = 0, off_fhi = 0, off_flo = 0, off_b = 0, off_bar = 0;
   int smem = 0;        // dynamic shared memory bytes including the alignment slack
 };
-PropGeom prop_geom(int N, int ncol);
+PropGeom prop_geom(int N, int ncol, bool cplx = false);
 
 struct TcState {
   int prec = 0, W = 0, N = 0, X = 0, ncol = 0, nblk = 0;
+  int cplx = 0;       // complex Hamiltonian: operands realified along K (see plan)
+  int kst0 = 0, kx0 = 0;   // complex: the padded length of one real part (exchange: N, VHS: fields)
   int kst = 0;        // padded length of one K segment of the exchange operands (multiple of 16)
   int nseg = 1;       // 1 (BF16) or 3 (BF16x3)
   int nchunk = 0;     // exchange partial slots per walker (four per M tile, summed over blocks)
@@ -77,7 +82,8 @@ struct TcState {
 };
 
 // Fills the geometry of st (no device work) and returns the bytes of the tc buffer.
-size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk);
+size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0, const int* nb, int nblk,
+            bool cplx = false);
 
 // Caps the exchange epilogue warpgroups at `groups` (0: largest that fits), selects the form (0: the
 // Ltilde tile resident in tensor memory where it fits, else streamed; 1: streamed) and re-derives
@@ -92,6 +98,11 @@ afqmc_status begin(TcState* st, cudaStream_t s, char* tcbuf, char* err, size_t e
 template <typename T, typename TL>
 afqmc_status load_chunk(TcState* st, cudaStream_t s, char* tcbuf, int g0, int ng, const T* chol, const TL* lrot,
                         unsigned long long* launches, char* err, size_t errlen);
+// Complex Hamiltonian: fields f0 .. f0 + nf - 1 (complex [nf][N][N], interleaved) and their Ltilde
+// (complex [nf][ncol][N]) into the realified operands.
+template <typename G>
+afqmc_status load_chunk_c(TcState* st, cudaStream_t s, char* tcbuf, int f0, int nf, const G* fields, const G* lrot,
+                          unsigned long long* launches, char* err, size_t errlen);
 afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen);
 
 // N(0,1) fields of the step counter *step (stream 0) for W walker slots x X into x[w][g]; drawn by

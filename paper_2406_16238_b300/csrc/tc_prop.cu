@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
 // mode order + 1: D = F acc, psi = acc + D.
 struct PropGemmParams {
   int N, npad, kq, nq, ncol, ncolp, bn, mtiles, W, order, mode, stages;
+  int cplx_f;   // complex F: four planes like V, F products over both K halves
   float2* psi;
   const double* w;
   float2* acc;
@@ -371,8 +372,8 @@ struct PropGemmParams {
 };
 
 __device__ __forceinline__ int prop_kblocks(const PropGemmParams& a) {
-  const bool fmode = a.mode == 0 || a.mode == a.order + 1;
-  return 3 * (fmode ? 1 : 2) * a.nq;
+  const bool freal = (a.mode == 0 || a.mode == a.order + 1) && !a.cplx_f;
+  return 3 * (freal ? 1 : 2) * a.nq;
 }
 
 // TMA coordinates and k-steps of k-block j of tile (wk, mt): segments (A hi, B hi), (A lo, B hi),
@@ -381,11 +382,12 @@ __device__ __forceinline__ int prop_kblocks(const PropGemmParams& a) {
 __device__ __forceinline__ void prop_kblock(const PropGemmParams& a, int wk, int mt, int j, int* ax, int* ay, int* bx,
                                             int* by, int* ksteps) {
   const bool fmode = a.mode == 0 || a.mode == a.order + 1;
-  const int halves = fmode ? 1 : 2;
+  const bool freal = fmode && !a.cplx_f;
+  const int halves = freal ? 1 : 2;
   const int seg = j / (halves * a.nq), h = (j / a.nq) % halves, qb = j % a.nq;
   const int alo = seg == 1 ? 1 : 0, blo = seg == 2 ? 1 : 0;
   *ax = qb * 64;
-  *ay = fmode ? alo * a.npad + mt * 128 : (wk * 4 + 2 * alo + h) * a.npad + mt * 128;
+  *ay = freal ? alo * a.npad + mt * 128 : ((fmode ? 0 : wk) * 4 + 2 * alo + h) * a.npad + mt * 128;
   *bx = h * a.kq + qb * 64;
   *by = (wk * 2 + blo) * a.bn;
   *ksteps = min(4, (a.N - qb * 64 + 15) / 16);
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(192, 1) k_prop_gemm(const __grid_constant__ CU
                 u = make_float2(d.x * s, d.y * s);
               } else {
                 u = sum;
-                both = false;
+                both = a.cplx_f != 0;   // a real F product reads the first K half only
               }
             } else {
               const float2 sum = accrow[c];
@@ -578,7 +580,8 @@ __global__ void __launch_bounds__(192, 1) k_prop_gemm(const __grid_constant__ CU
 
 // First operand of the large form: psi of every walker as split bf16 rows (real parts, then
 // imaginary parts) over the first K half; K positions N .. kq - 1 and padding columns are zero.
-__global__ void k_psi_to_b(int W, int N, int ncol, int ncolp, int kq, const float2* psi, __nv_bfloat16* b) {
+__global__ void k_psi_to_b(int W, int N, int ncol, int ncolp, int kq, const float2* psi, __nv_bfloat16* b,
+                           int both) {
   const int bn = 2 * ncolp;
   const size_t kk2 = (size_t)2 * kq;
   const size_t total = (size_t)W * ncolp * kq;
@@ -592,21 +595,32 @@ __global__ void k_psi_to_b(int W, int N, int ncol, int ncolp, int kq, const floa
     const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
     __nv_bfloat16* bw = b + (size_t)wk * 2 * bn * kk2;
     const size_t lo = (size_t)bn * kk2;
+    const __nv_bfloat16 rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+    const __nv_bfloat16 il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
     bw[(size_t)c * kk2 + p] = rh;
-    bw[lo + (size_t)c * kk2 + p] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+    bw[lo + (size_t)c * kk2 + p] = rl;
     bw[(size_t)(ncolp + c) * kk2 + p] = ih;
-    bw[lo + (size_t)(ncolp + c) * kk2 + p] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+    bw[lo + (size_t)(ncolp + c) * kk2 + p] = il;
+    if (both) {   // the second K half for a complex first product: rows [Re | -Im] and [Im | Re]
+      bw[(size_t)c * kk2 + kq + p] = __hneg(ih);
+      bw[lo + (size_t)c * kk2 + kq + p] = __hneg(il);
+      bw[(size_t)(ncolp + c) * kk2 + kq + p] = rh;
+      bw[lo + (size_t)(ncolp + c) * kk2 + kq + p] = rl;
+    }
   }
 }
 
-// F = E_h - I (binary64 [N][N]) -> planes [hi, lo][npad][kq], zero outside N x N.
-__global__ void k_f_planes(int N, int npad, int kq, const double* f64, __nv_bfloat16* out) {
-  const int per = npad * kq;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * per; idx += gridDim.x * blockDim.x) {
+// F = E_h - I (binary64 [N][N]) -> planes [hi, lo][npad][kq], zero outside N x N.  Complex F
+// (interleaved binary64): planes [Re hi, Im hi, Re lo, Im lo], the order of the V planes.
+__global__ void k_f_planes(int N, int npad, int kq, const double* f64, __nv_bfloat16* out, int cplx) {
+  const int per = npad * kq, np = cplx ? 4 : 2;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < np * per; idx += gridDim.x * blockDim.x) {
     const int pl = idx / per, rem = idx % per, p = rem / kq, q = rem % kq;
-    const double v = (p < N && q < N) ? f64[(size_t)p * N + q] : 0.0;
+    const int part = cplx ? (pl & 1) : 0, lo = cplx ? pl >> 1 : pl;
+    const size_t e = (size_t)p * N + q;
+    const double v = (p < N && q < N) ? (cplx ? f64[2 * e + part] : f64[e]) : 0.0;
     const __nv_bfloat16 hi = __double2bfloat16(v);
-    out[idx] = pl ? __double2bfloat16(v - (double)__bfloat162float(hi)) : hi;
+    out[idx] = lo ? __double2bfloat16(v - (double)__bfloat162float(hi)) : hi;
   }
 }
 
@@ -629,12 +643,13 @@ afqmc_status launch_prop(const TcState* st, cudaStream_t s, const PropTcParams& 
 int prop_gemm_stages(int bn) { return std::min(6, (kMaxSmem - 1024 - 256) / (16384 + bn * 128)); }
 size_t prop_gemm_smem(int bn) { return 1024 + (size_t)prop_gemm_stages(bn) * (16384 + bn * 128) + 256; }
 
-PropGeom prop_geom(int N, int ncol) {
+PropGeom prop_geom(int N, int ncol, bool cplx) {
   PropGeom g{};
   if (N < 1 || ncol < 1) return g;
-  if (N > 128) {   // large form
+  if (N > 128 || cplx) {   // large form (a complex E_h has no room beside V in the fused kernel)
     if (ncol > 128) return g;
     g.large = 1;
+    g.cplx_f = cplx ? 1 : 0;
     g.npad = (N + 7) / 8 * 8;
     g.kq = (N + 63) / 64 * 64;
     g.ncolp = (ncol + 7) / 8 * 8;
@@ -681,11 +696,11 @@ afqmc_status prepare_prop(TcState* st, cudaStream_t s, char* tcbuf, const double
     snprintf(err, errlen, "tensor-core propagation: clearing the V planes failed");
     return AFQMC_ECUDA;
   }
-  k_f_planes<<<64, 256, 0, s>>>(st->N, g.npad, g.kq, f64, fp);
+  k_f_planes<<<64, 256, 0, s>>>(st->N, g.npad, g.kq, f64, fp, g.cplx_f);
   ++*launches;
   const unsigned box = g.large ? 128u : (unsigned)g.npad;   // one 128-row tile, or every row
   if (!make_map(&st->map_vp, vp, (unsigned long long)st->W * 4 * g.npad, g.kq, box) ||
-      !make_map(&st->map_fp, fp, (unsigned long long)2 * g.npad, g.kq, box)) {
+      !make_map(&st->map_fp, fp, (unsigned long long)(g.cplx_f ? 4 : 2) * g.npad, g.kq, box)) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed for the propagation planes");
     return AFQMC_ECUDA;
   }
@@ -731,9 +746,10 @@ afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, floa
   if (g.large) {
     __nv_bfloat16* b[2] = {reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_b[0]),
                            reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_b[1])};
-    k_psi_to_b<<<1184, 256, 0, s>>>(st->W, st->N, st->ncol, g.ncolp, g.kq, psi, b[0]);
+    k_psi_to_b<<<1184, 256, 0, s>>>(st->W, st->N, st->ncol, g.ncolp, g.kq, psi, b[0], g.cplx_f);
     ++*launches;
     PropGemmParams q{};
+    q.cplx_f = g.cplx_f;
     q.N = st->N; q.npad = g.npad; q.kq = g.kq; q.nq = g.kq / 64; q.ncol = st->ncol; q.ncolp = g.ncolp;
     q.bn = 2 * g.ncolp; q.mtiles = g.mtiles; q.W = st->W; q.order = order;
     q.stages = prop_gemm_stages(q.bn);
