@@ -584,9 +584,35 @@ def run_ours(args):
     return line
 
 
+def batched_rooflines(prec, systems, stages, steps):
+    """Work per grouped launch (sums over the systems) of the grouped stages against the tensor peak."""
+    peaks, src = measured_peaks()
+    tpeak = peaks["bf16_tflops"] * (1.0 if prec == "bf16" else 1.0 / 3.0)
+    tnote = f"bf16 burst ({src})" + ("" if prec == "bf16" else " / 3 products")
+    work = {"exchange": 0.0, "vhs": 0.0, "propagate": 0.0}
+    for norb, ncol, naux, nw in systems:
+        fl = step_flops_per_walker(norb, ncol, naux)
+        for k in work:
+            work[k] += fl[k] * nw
+    out = {}
+    for k, flops in work.items():
+        ms, cnt = stages.get(k, (0.0, 0))
+        if not cnt:
+            continue
+        # the propagation stage is one small-form launch plus, for N > 128, one launch per product
+        per = ms / steps
+        ach = flops / (per / 1e3) / 1e12
+        out[k] = {"bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
+                  "peak_source": tnote, "algorithmic_flops_per_step": flops, "ms_per_step": per,
+                  "launches_per_step": cnt / steps, "traffic": None}
+    return out
+
+
 def run_batched(args):
     """32 uneven systems (N ~ U[50, 300], n = N/6, naux = 4N), 256 walkers each, split-bf16 GEMMs
-    with fp32 accumulation, autotuned per system, one CUDA graph launch per step."""
+    with fp32 accumulation, autotuned per system, one CUDA graph launch per step: in the grouped form
+    every stage is one launch over the work of all systems (the per-system graphs form is timed beside
+    it on the same systems)."""
     import torch
     import paper_2406_16238_b300 as pkg
     from paper_2406_16238_b300._lib import Batch
@@ -594,37 +620,65 @@ def run_batched(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     probs = config_batched(nsys=args.nsys)
-    ctxs, tunings, sizes = [], [], []
+    ctxs, tunings, sizes, shapes = [], [], [], []
     for i, p in enumerate(probs):
         c = pkg.Afqmc(p.h1e, p.chol, p.ecore, p.nalpha, p.nbeta, p.psiT, nwalkers=256, dt=WORKLOAD["dt"],
                       seed=240616238 + i, prec=args.prec, device=dev, stream=stream)
         tunings.append(c.autotune(steps=2))
         ctxs.append(c)
         sizes.append(p.norb)
+        info = c.info()
+        shapes.append((p.norb, info["nalpha"] if info["restricted"] else info["nalpha"] + info["nbeta"], info["naux"],
+                       256))
         p.chol = None
-    b = Batch(ctxs)
-    b.run(args.warmup, 1, 5, 10)
-    torch.cuda.synchronize(dev)
-    l0 = sum(c.launch_count() for c in ctxs)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev) as clk:
+    b = Batch(ctxs, mode=args.batch_mode)
+    form = b.mode()
+
+    def timed(nsteps):
         torch.cuda.synchronize(dev)
-        clk.mark_start()
-        ev0.record(stream)
-        e = b.run(args.steps, 1, 5, 10)
-        ev1.record(stream)
-        ev1.synchronize()
-        clk.mark_end()
-    ms = ev0.elapsed_time(ev1)
-    launches = sum(c.launch_count() for c in ctxs) - l0
+        l0 = sum(c.launch_count() for c in ctxs)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            torch.cuda.synchronize(dev)
+            clk.mark_start()
+            ev0.record(stream)
+            e = b.run(nsteps, 1, 5, 10)
+            ev1.record(stream)
+            ev1.synchronize()
+            clk.mark_end()
+        return ev0.elapsed_time(ev1), e, sum(c.launch_count() for c in ctxs) - l0, clk.summary()
+
+    b.run(args.warmup, 1, 5, 10)
+    ms, e, launches, clocks = timed(args.steps)
     total_ws = len(ctxs) * 256 * args.steps
+    extra = {}
+    if form == "grouped":
+        # stage trace of the grouped launches (direct launches between CUDA events)
+        b.profile(True)
+        nprof = 10
+        b.run(nprof, 1, 5, 10)
+        st = b.stage_times()
+        b.profile(False)
+        rl = batched_rooflines(args.prec, shapes, st, nprof)
+        extra["rooflines"] = rl
+        if "exchange" in rl:
+            r = dict(rl["exchange"])
+            r["kernel"] = "k_tc_gemm<0, 0, true> (grouped exchange over every system's tiles)"
+            extra["roofline"] = r
+        extra["stage_ms_per_step"] = {k: v[0] / nprof for k, v in st.items() if v[1]}
+        # the per-system graphs form on the same systems, for comparison
+        b.set_mode("graphs")
+        b.run(2, 1, 5, 10)
+        gms, _, gl, _ = timed(args.steps)
+        extra["graphs_form"] = {"value": total_ws / (gms / 1e3), "ms_per_step": gms / args.steps,
+                                "gpu_launches": int(gl)}
     return {"metric": METRIC, "value": total_ws / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": {"workload": f"batched uneven systems: {len(ctxs)} x (N in [50,300], n=N/6, naux=4N, W=256), "
-                                   "one CUDA graph launch per step", "form": args.prec, "norb": sizes,
-                       "tuning": tunings, "l2": "inputs larger than L2"},
-            "energies_finite": bool(np.isfinite(e).all()), "clocks": clk.summary(), "gpu_launches": int(launches)}
+                                   "one CUDA graph launch per step", "form": args.prec, "batch_form": form,
+                       "norb": sizes, "tuning": tunings, "l2": "inputs larger than L2"},
+            "energies_finite": bool(np.isfinite(e).all()), "clocks": clocks, "gpu_launches": int(launches), **extra}
 
 
 def run_cv(args):
@@ -819,6 +873,8 @@ def main():
     ap.add_argument("--large-naux", type=int, default=None,
                     help="the large system truncated to its first naux Cholesky vectors (a small case for ncu)")
     ap.add_argument("--nsys", type=int, default=32)
+    ap.add_argument("--batch-mode", default="auto", choices=["auto", "grouped", "graphs"],
+                    help="batched workload: one launch per stage over all systems, or per-system graphs")
     ap.add_argument("--cv-pairs", type=int, default=100000)
     ap.add_argument("--cv-epochs", type=int, default=30)
     ap.add_argument("--skip-extras", action="store_true",

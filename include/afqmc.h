@@ -288,14 +288,46 @@ typedef struct {
 afqmc_status afqmc_autotune(afqmc_ctx* ctx, int32_t steps, afqmc_tuning* chosen);
 afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t);
 
-/* Batched independent systems: the contexts (same device, same nwalkers cadence) advance in
- * lockstep, each step being ONE CUDA graph launch whose branches are the systems' step graphs,
- * so uneven systems run concurrently.  energies (host, may be NULL): [nsys][nmeas][4].
- * The batch launches on the first context's stream; do not use the contexts concurrently. */
+/* Batched independent systems: the contexts (same device) advance in lockstep, each step being ONE
+ * CUDA graph launch.  energies (host, may be NULL): [nsys][nmeas][4].  The batch launches on the
+ * first context's stream; do not use the contexts concurrently.  Two forms:
+ *   AFQMC_BATCH_GROUPED: every stage of the step is ONE kernel launch over the work of all systems:
+ *     the exchange (with the force bias and the step's normals) and the VHS build as persistent
+ *     tcgen05 kernels over a (system, spin block, tile) work list ordered by tile cost, with each
+ *     system's tensor maps and parameters in device memory; the propagation as one launch over every
+ *     walker of the N <= 128 systems (contiguous walker ranges per CTA balanced by cost) and one
+ *     launch per Taylor product over every (walker, row tile) of the N > 128 systems; the overlap,
+ *     fields, energy, QR and comb kernels as one launch over every walker.  Needs every context in
+ *     the same tensor-core form (BF16 / BF16X3), real, phaseless, with the tensor-core propagation
+ *     and the same Taylor order.  exch_groups caps the exchange's epilogue warpgroups (0: the most
+ *     that fit every system).  The descriptors (a few KB of device memory) are allocated on the
+ *     first grouped run, not inside the caller's workspaces.
+ *   AFQMC_BATCH_GRAPHS: one graph launch whose branches are the systems' own step graphs (any form).
+ *   AFQMC_BATCH_AUTO (default): grouped where the contexts allow it, else graphs.
+ * The graphs form gives bit for bit the results of running each context alone.  The grouped form
+ * runs the same arithmetic but for the exchange, which it takes in the streamed form (both operands
+ * through the shared-memory ring) at every step, also to form the force bias of steps without an
+ * energy measurement: its results agree with the solo runs to the form's rounding. */
 typedef struct afqmc_batch afqmc_batch;
+#define AFQMC_BATCH_AUTO 0
+#define AFQMC_BATCH_GROUPED 1
+#define AFQMC_BATCH_GRAPHS 2
 afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batch** out);
 afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
                              int32_t comb_every, double* energies, int32_t* nmeas);
+afqmc_status afqmc_batch_set_mode(afqmc_batch* b, int32_t mode, int32_t exch_groups);
+/* The form the next afqmc_batch_run takes (AFQMC_BATCH_GROUPED or AFQMC_BATCH_GRAPHS). */
+afqmc_status afqmc_batch_get_mode(afqmc_batch* b, int32_t* mode);
+/* Stage tracing of the grouped form: with enable = 1 (counters cleared) afqmc_batch_run launches each
+ * grouped stage directly between CUDA events instead of replaying its graph; afqmc_batch_stage_times
+ * synchronises and returns per stage (AFQMC_STAGE_*) the milliseconds and launches so far, the
+ * exchange stage being the grouped exchange kernel alone (the cleared vbias and the Theta operands
+ * count as AFQMC_STAGE_FORCE_BIAS).  Either array may be NULL. */
+afqmc_status afqmc_batch_profile(afqmc_batch* b, int32_t enable);
+/* A text description of the grouped launches (one line per launch: problems, tiles, grid, ring
+ * stages, epilogue groups, shared and tensor memory), NUL-terminated and cut to len bytes. */
+afqmc_status afqmc_batch_describe(afqmc_batch* b, char* buf, size_t len);
+afqmc_status afqmc_batch_stage_times(afqmc_batch* b, double* ms, int64_t* count);
 void afqmc_batch_destroy(afqmc_batch* b);
 
 /* afqmc_run replays each step pattern (energy + propagation, propagation alone, QR, comb) as a

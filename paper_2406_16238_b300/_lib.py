@@ -90,6 +90,11 @@ SIGNATURES = {
     "afqmc_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "afqmc_batch_run": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
     "afqmc_batch_destroy": (None, [_vp]),
+    "afqmc_batch_set_mode": (_i32, [_vp, _i32, _i32]),
+    "afqmc_batch_get_mode": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "afqmc_batch_profile": (_i32, [_vp, _i32]),
+    "afqmc_batch_describe": (_i32, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
+    "afqmc_batch_stage_times": (_i32, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "afqmc_cv_workspace_size": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_size_t)]),
     "afqmc_cv_attach": (_i32, [_vp, _i32, _i32, ctypes.c_double, _u64, _vp, ctypes.c_size_t]),
     "afqmc_cv_collect": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(_i32)]),
@@ -512,16 +517,49 @@ def comb_plan_noalloc(w, seed, step, src, neww, stream=None):
                                            ctypes.c_void_p(neww.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
 
 
-class Batch:
-    """Independent contexts advanced in lockstep, one CUDA graph launch per step (afqmc_batch_*)."""
+BATCH_MODES = {"auto": 0, "grouped": 1, "graphs": 2}
 
-    def __init__(self, contexts):
+
+class Batch:
+    """Independent contexts advanced in lockstep, one CUDA graph launch per step (afqmc_batch_*):
+    mode "grouped" (one launch per stage over every system), "graphs" (one child graph per system)
+    or "auto" (grouped where the contexts allow it)."""
+
+    def __init__(self, contexts, mode="auto", exch_groups=0):
         self._lib = load()
         self.contexts = list(contexts)
         arr = (ctypes.c_void_p * len(self.contexts))(*[c._ctx.value for c in self.contexts])
         b = ctypes.c_void_p()
         _check(self._lib.afqmc_batch_create(len(self.contexts), arr, ctypes.byref(b)))
         self._b = b
+        self.set_mode(mode, exch_groups)
+
+    def set_mode(self, mode="auto", exch_groups=0):
+        if mode not in BATCH_MODES:
+            raise ValueError(f"mode must be one of {sorted(BATCH_MODES)}")
+        _check(self._lib.afqmc_batch_set_mode(self._b, BATCH_MODES[mode], int(exch_groups)))
+
+    def profile(self, enable=True):
+        _check(self._lib.afqmc_batch_profile(self._b, 1 if enable else 0))
+
+    def stage_times(self):
+        """{stage: (ms, launches)} of the grouped stages traced since profile(True)."""
+        ms = np.zeros(len(STAGES))
+        n = (ctypes.c_int64 * len(STAGES))()
+        _check(self._lib.afqmc_batch_stage_times(self._b, _ptr(ms), n))
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(STAGES)}
+
+    def describe(self):
+        """The grouped launches' plan as text (after the first grouped run)."""
+        buf = ctypes.create_string_buffer(8192)
+        _check(self._lib.afqmc_batch_describe(self._b, buf, len(buf)))
+        return buf.value.decode()
+
+    def mode(self):
+        """The form the next run takes: "grouped" or "graphs"."""
+        m = ctypes.c_int32()
+        _check(self._lib.afqmc_batch_get_mode(self._b, ctypes.byref(m)))
+        return {1: "grouped", 2: "graphs"}[m.value]
 
     def run(self, nsteps, energy_every=1, reortho_every=5, comb_every=10):
         start = self.contexts[0].info()["step"]

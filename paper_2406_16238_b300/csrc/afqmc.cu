@@ -15,6 +15,7 @@
 #include <random>
 #include <thread>
 #include <type_traits>
+#include <string>
 #include <vector>
 
 #include <cuda.h>
@@ -259,7 +260,9 @@ struct afqmc_ctx {
   unsigned long long g_step_k[8] = {};  // bit 2: the energy reuses the bf16 Theta operand
   cudaGraphExec_t g_qr = nullptr, g_comb[2] = {};
   unsigned long long g_qr_k = 0, g_comb_k[2] = {};
+  unsigned long long graph_gen = 0;   // bumped whenever captured launch parameters go stale
   void drop_graphs() {
+    ++graph_gen;
     for (auto& g : g_step) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     for (auto& g : g_comb) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     if (g_qr) { cudaGraphExecDestroy(g_qr); g_qr = nullptr; }
@@ -519,6 +522,25 @@ afqmc_status set_smem_limits(const Dims& d) {
 template <typename R>
 afqmc_status energy_cv_impl(afqmc_ctx* c, double* sums_dev, int* slot);
 
+template <typename R>
+EnergyArgs<R> energy_args(afqmc_ctx* c, double* sums_dev, int* slot) {
+  EnergyArgs<R> a{};
+  a.N = c->d.N; a.X = c->d.X; a.ncol = c->d.ncol;
+  a.smul = c->smul; a.ecore = c->ecore; a.nchunk = c->d.nchunk;
+  a.thetaT = c->at<cplx_t<R>>(c->L.thetaT);
+  a.hrot = c->at<void>(c->L.hrot_r);
+  a.vbias = c->at<cplx_t<R>>(c->L.vbias);
+  a.exch_part = c->at<double2>(c->L.exch_part);
+  a.eloc = c->at<double2>(c->L.eloc);
+  a.W = c->d.W;
+  a.wgt = c->at<double>(c->L.w);
+  a.wph = c->free_proj ? c->at<double>(c->L.wph) : nullptr;
+  a.out = sums_dev;
+  a.slot = slot;
+  a.done = reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64);
+  return a;
+}
+
 // beside: a step follows at once, so the estimator kernel may run on the side stream until that
 // step's overlap (not while stage timing is on, which times it on the main stream).
 template <typename R>
@@ -556,12 +578,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
   }
   StageTimer te(c, AFQMC_STAGE_ENERGY);
   auto kern = c->d.cplx ? k_energy<R, true> : k_energy<R, false>;
-  kern<<<c->d.W, 256, 0, es>>>(c->d.N, c->d.X, c->d.ncol, c->smul, c->ecore, c->d.nchunk,
-                                              c->at<cplx_t<R>>(c->L.thetaT), c->at<void>(c->L.hrot_r),
-                                              c->at<cplx_t<R>>(c->L.vbias), c->at<double2>(c->L.exch_part),
-                                              c->at<double2>(c->L.eloc), c->d.W, c->at<double>(c->L.w),
-                                              c->free_proj ? c->at<double>(c->L.wph) : nullptr, sums_dev, slot,
-                                              reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64));
+  kern<<<c->d.W, 256, 0, es>>>(energy_args<R>(c, sums_dev, slot));
   CHECK_LAUNCH(c);
   if (sums_host) CU(cudaMemcpyAsync(sums_host, sums_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, es));
   if (fork) {
@@ -570,6 +587,26 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
   }
   c->vbias_fresh = true;
   return AFQMC_OK;
+}
+
+template <typename R>
+FieldArgs<R> field_args(afqmc_ctx* c) {
+  using R2 = cplx_t<R>;
+  const Dims& d = c->d;
+  FieldArgs<R> fa{};
+  fa.X = d.X; fa.sdt = c->sdt; fa.cap = c->cap; fa.seed = c->seed;
+  fa.step = c->at<unsigned long long>(c->L.step);
+  fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar); fa.slbar = c->at<double>(c->L.slbar);
+  fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
+  fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
+  fa.free_proj = c->free_proj ? 1 : 0;
+  if (d.tensor()) {
+    fa.coefb = reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.off_coef);
+    fa.kx = c->tcs.kx;
+    fa.nseg = c->tcs.nseg;
+    fa.kx0 = d.cplx ? c->tcs.kx0 : 0;
+  }
+  return fa;
 }
 
 // Draws the current step's normals into L.x (unless the energy's tensor-core exchange already has).
@@ -606,20 +643,7 @@ afqmc_status step_impl(afqmc_ctx* c) {
   StageTimer* tf = new StageTimer(c, AFQMC_STAGE_FIELDS);
   if (!c->normals_pending && (st = draw_normals(c)) != AFQMC_OK) return st;
   c->normals_pending = false;
-  FieldArgs<R> fa{};
-  fa.X = d.X; fa.sdt = c->sdt; fa.cap = c->cap; fa.seed = c->seed;
-  fa.step = c->at<unsigned long long>(c->L.step);
-  fa.vbias = c->at<R2>(c->L.vbias); fa.lbar = c->at<double>(c->L.lbar); fa.slbar = c->at<double>(c->L.slbar);
-  fa.x = c->at<double>(c->L.x); fa.xbar = c->at<double2>(c->L.xbar); fa.coef = c->at<R2>(c->L.coef);
-  fa.cmf = c->at<double2>(c->L.cmf); fa.xxbar = c->at<double2>(c->L.xxbar);
-  fa.free_proj = c->free_proj ? 1 : 0;
-  if (d.tensor()) {
-    fa.coefb = reinterpret_cast<__nv_bfloat16*>(c->at<char>(c->L.tc) + c->tcs.off_coef);
-    fa.kx = c->tcs.kx;
-    fa.nseg = c->tcs.nseg;
-    fa.kx0 = d.cplx ? c->tcs.kx0 : 0;
-  }
-  k_fields<R><<<d.W, 256, 0, c->stream>>>(fa);
+  k_fields<R><<<d.W, 256, 0, c->stream>>>(field_args<R>(c));
   delete tf;
   CHECK_LAUNCH(c);
   const long long NN = (long long)d.N * d.N, Nc = (long long)d.N * d.ncol;
@@ -724,13 +748,18 @@ afqmc_status step_impl(afqmc_ctx* c) {
 }
 
 template <typename R>
+QrArgs<R> qr_args(afqmc_ctx* c) {
+  const Dims& d = c->d;
+  return QrArgs<R>{d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1], c->smul,
+                   c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO), c->at<double>(c->L.w),
+                   c->at<int>(c->L.status), qr_stage_psi(d) ? 1 : 0};
+}
+
+template <typename R>
 afqmc_status qr_impl(afqmc_ctx* c) {
   const Dims& d = c->d;
   StageTimer timer(c, AFQMC_STAGE_QR);
-  k_qr_chol<R><<<d.W, 256, qr_smem(d), c->stream>>>(d.N, d.ncol, d.nblk, d.c0[0], d.nbk[0], d.c0[1], d.nbk[1],
-                                                   c->smul, c->at<cplx_t<R>>(c->L.psi), c->at<double2>(c->L.logO),
-                                                   c->at<double>(c->L.w), c->at<int>(c->L.status),
-                                                   qr_stage_psi(d) ? 1 : 0);
+  k_qr_chol<R><<<d.W, 256, qr_smem(d), c->stream>>>(qr_args<R>(c));
   CHECK_LAUNCH(c);
   // Theta = psi (Phi^T psi)^-1 is unchanged by psi -> psi R^-1 (Phi^T psi picks up the same R^-1),
   // so Theta, its bf16 copy and the force bias stay valid; log O was updated by -sum log R_ii.
@@ -2132,14 +2161,297 @@ struct afqmc_batch {
     std::vector<unsigned long long> nk;
     std::vector<char> end_theta, end_vbias, end_thb;
   };
-  std::map<int, Exec> cache;
-  ~afqmc_batch() {
+  std::map<int, Exec> cache;   // child-graph form: one child graph per system and step kind
+  // Grouped form (every system in a tensor-core form, real, phaseless): one launch per stage over
+  // the work of every system, the step captured as one graph per step kind.
+  int mode = AFQMC_BATCH_AUTO;
+  int exch_groups = 0;          // epilogue warpgroups of the grouped exchange (0: the most that fit)
+  bool g_ready = false;
+  afq::tc::GroupGemm g_exch, g_vhs;
+  afq::tc::GroupProp g_prop;
+  std::vector<void*> g_dev;     // device argument arrays of the grouped per-walker kernels
+  void *a_first = nullptr, *a_energy = nullptr, *a_fields = nullptr, *a_overlap = nullptr, *a_stage = nullptr,
+       *a_qr = nullptr, *a_comb = nullptr, *a_zero = nullptr;
+  int total_w = 0, max_w = 0;
+  size_t ovl_smem = 0, qr_smem = 0, max_vbias = 0;
+  cudaStream_t s2 = nullptr;            // second stream of the grouped step's forks
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  struct GExec {
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long nk = 0;
+  };
+  std::map<int, GExec> gcache;
+  std::vector<unsigned long long> gens;   // the contexts' graph generations the caches were built at
+  // stage tracing of the grouped form (direct launches with CUDA events around each stage)
+  bool prof = false;
+  struct Pending { int stage; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  double stage_ms[AFQMC_NSTAGES] = {};
+  long long stage_n[AFQMC_NSTAGES] = {};
+  cudaEvent_t event() {
+    if (!free_events.empty()) {
+      cudaEvent_t e = free_events.back();
+      free_events.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drop_grouped() {
+    for (auto& kv : gcache)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    gcache.clear();
+    afq::tc::group_free(&g_exch);
+    afq::tc::group_free(&g_vhs);
+    afq::tc::group_prop_free(&g_prop);
+    for (void* d : g_dev) cudaFree(d);
+    g_dev.clear();
+    g_ready = false;
+  }
+  void drop_all() {
     for (auto& kv : cache)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    cache.clear();
+    drop_grouped();
+  }
+  ~afqmc_batch() {
+    drop_all();
+    if (s2) cudaStreamDestroy(s2);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+    for (auto e : free_events) cudaEventDestroy(e);
   }
 };
 
 namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Grouped batch: every stage of the step is one launch over the work of all systems.
+
+// Whether every context admits the grouped form (else *why says what does not).
+bool grouped_ok(const afqmc_batch* b, const char** why) {
+  const afqmc_ctx* c0 = b->sys[0];
+  for (const afqmc_ctx* c : b->sys) {
+    if (!c->d.tensor()) { *why = "a context is not in a tensor-core form"; return false; }
+    if (c->d.prec != c0->d.prec) { *why = "the contexts use different precision forms"; return false; }
+    if (c->d.cplx) { *why = "a context has a complex Hamiltonian"; return false; }
+    if (c->free_proj) { *why = "a context runs free projection"; return false; }
+    if (!use_tc_propagation(c)) { *why = "a context does not use the tensor-core propagation"; return false; }
+    if (c->taylor != c0->taylor) { *why = "the contexts use different Taylor orders"; return false; }
+    if (c->prof) { *why = "a context is being traced"; return false; }
+  }
+  return true;
+}
+
+template <typename T>
+afqmc_status upload(afqmc_batch* b, const std::vector<T>& v, void** dev) {
+  *dev = nullptr;
+  if (v.empty()) return AFQMC_OK;
+  void* p = nullptr;
+  CU(cudaMalloc(&p, v.size() * sizeof(T)));
+  b->g_dev.push_back(p);
+  CU(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *dev = p;
+  return AFQMC_OK;
+}
+
+// The grouped launches' descriptors: the tcgen05 problems (exchange, VHS, propagation) and the
+// argument arrays of the per-walker kernels, in device memory.
+afqmc_status batch_grouped_plan(afqmc_batch* b) {
+  using R = float;
+  b->drop_grouped();
+  const int nsys = (int)b->sys.size();
+  std::vector<tc::GroupSystem> gs(nsys);
+  std::vector<tc::GroupPropSystem> ps(nsys);
+  std::vector<EnergyArgs<R>> ea(nsys);
+  std::vector<FieldArgs<R>> fa(nsys);
+  std::vector<OverlapArgs<R>> oa(nsys);
+  std::vector<QrArgs<R>> qa(nsys);
+  std::vector<CombArgs<R>> ca(nsys);
+  std::vector<ZeroArgs> za(nsys);
+  std::vector<int> stage(nsys), first(nsys + 1, 0);
+  b->ovl_smem = b->qr_smem = b->max_vbias = 0;
+  b->max_w = 0;
+  for (int i = 0; i < nsys; ++i) {
+    afqmc_ctx* c = b->sys[i];
+    const Dims& d = c->d;
+    char* tcbuf = c->at<char>(c->L.tc);
+    int* status = c->at<int>(c->L.status);
+    gs[i] = tc::GroupSystem{&c->tcs, tcbuf, c->smul, c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias),
+                            c->at<double2>(c->L.exch_part), status,
+                            tc::NormalsJob{c->at<double>(c->L.x), c->seed, c->at<unsigned long long>(c->L.step), d.W,
+                                           d.X}};
+    ps[i] = tc::GroupPropSystem{&c->tcs, tcbuf, c->at<float2>(c->L.psi), c->at<double>(c->L.w), status};
+    ea[i] = energy_args<R>(c, c->at<double>(c->L.hist), c->at<int>(c->L.slot));
+    fa[i] = field_args<R>(c);
+    oa[i] = overlap_args<R>(c, 1);
+    stage[i] = overlap_stage(d) ? 1 : 0;
+    b->ovl_smem = std::max(b->ovl_smem, overlap_smem(d));
+    qa[i] = qr_args<R>(c);
+    b->qr_smem = std::max(b->qr_smem, qr_smem(d));
+    ca[i] = CombArgs<R>{d.W, d.N * d.ncol, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.cum),
+                        c->at<int>(c->L.src), c->at<double>(c->L.neww), status, c->at<float2>(c->L.psi),
+                        c->at<float2>(c->L.psi_tmp), c->at<float2>(c->L.thetaT), c->at<float2>(c->L.th_tmp),
+                        c->at<double2>(c->L.logO), c->at<double2>(c->L.logO_tmp), c->at<double>(c->L.w),
+                        c->at<double>(c->L.w_tmp)};
+    za[i] = ZeroArgs{c->at<float2>(c->L.vbias), (size_t)d.W * d.X};
+    b->max_vbias = std::max(b->max_vbias, (size_t)d.W * d.X);
+    b->max_w = std::max(b->max_w, d.W);
+    first[i + 1] = first[i] + d.W;
+  }
+  b->total_w = first[nsys];
+  afqmc_status st;
+  if ((st = tc::group_exchange_plan(gs.data(), nsys, b->exch_groups, &b->g_exch, g_err, sizeof(g_err))) != AFQMC_OK ||
+      (st = tc::group_vhs_plan(gs.data(), nsys, &b->g_vhs, g_err, sizeof(g_err))) != AFQMC_OK ||
+      (st = tc::group_prop_plan(ps.data(), nsys, b->sys[0]->taylor, &b->g_prop, g_err, sizeof(g_err))) != AFQMC_OK) {
+    b->drop_grouped();
+    return st;
+  }
+  if ((st = upload(b, first, &b->a_first)) != AFQMC_OK || (st = upload(b, ea, &b->a_energy)) != AFQMC_OK ||
+      (st = upload(b, fa, &b->a_fields)) != AFQMC_OK || (st = upload(b, oa, &b->a_overlap)) != AFQMC_OK ||
+      (st = upload(b, stage, &b->a_stage)) != AFQMC_OK || (st = upload(b, qa, &b->a_qr)) != AFQMC_OK ||
+      (st = upload(b, ca, &b->a_comb)) != AFQMC_OK || (st = upload(b, za, &b->a_zero)) != AFQMC_OK) {
+    b->drop_grouped();
+    return st;
+  }
+  if ((st = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_group<R>))) != AFQMC_OK ||
+      (st = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_group<R>))) != AFQMC_OK) {
+    b->drop_grouped();
+    return st;
+  }
+  if (!b->s2) CU(cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking));
+  if (!b->ev_fork) CU(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  if (!b->ev_join) CU(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  b->g_ready = true;
+  return AFQMC_OK;
+}
+
+// s2 waits for s (fork) / s waits for s2 (join): the grouped stages whose launches are independent
+// (exchange classes; small- and large-form propagation) run on both streams.
+afqmc_status batch_fork(afqmc_batch* b, cudaStream_t s) {
+  CU(cudaEventRecord(b->ev_fork, s));
+  CU(cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
+  return AFQMC_OK;
+}
+afqmc_status batch_join(afqmc_batch* b, cudaStream_t s) {
+  CU(cudaEventRecord(b->ev_join, b->s2));
+  CU(cudaStreamWaitEvent(s, b->ev_join, 0));
+  return AFQMC_OK;
+}
+
+// Events around one stage of a directly launched grouped step (tracing on).
+struct BatchStage {
+  afqmc_batch* b;
+  cudaStream_t s;
+  int stage;
+  cudaEvent_t e0 = nullptr;
+  BatchStage(afqmc_batch* b_, cudaStream_t s_, int st) : b(b_), s(s_), stage(st) {
+    if (b->prof) {
+      e0 = b->event();
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~BatchStage() {
+    if (!e0) return;
+    cudaEvent_t e1 = b->event();
+    cudaEventRecord(e1, s);
+    b->pending.push_back({stage, e0, e1});
+  }
+};
+
+// One grouped step on stream s: the exchange (force bias, exchange partials, the step's normals;
+// the Theta operands rebuilt first unless thb), the energy estimator (energy), fields, the VHS
+// planes, the propagation and the new overlaps of every system, then QR and the comb.
+afqmc_status batch_grouped_step(afqmc_batch* b, cudaStream_t s, bool energy, bool qr, bool comb, bool thb,
+                                unsigned long long* nk) {
+  using R = float;
+  const int nsys = (int)b->sys.size();
+  const int* first = static_cast<const int*>(b->a_first);
+  afqmc_status st;
+  {
+    BatchStage t(b, s, AFQMC_STAGE_FORCE_BIAS);   // the cleared vbias and the bf16 Theta operands
+    const unsigned zb = (unsigned)std::min<size_t>(1184, (b->max_vbias + 255) / 256);
+    k_zero_group<<<dim3(zb, nsys), 256, 0, s>>>(static_cast<const ZeroArgs*>(b->a_zero));
+    ++*nk;
+    if (!thb && (st = tc::group_theta(b->g_exch, s, nk, g_err, sizeof(g_err))) != AFQMC_OK) return st;
+  }
+  {
+    BatchStage t(b, s, AFQMC_STAGE_EXCHANGE);
+    const bool two = b->g_exch.nparts > 1;
+    if (two && (st = batch_fork(b, s)) != AFQMC_OK) return st;
+    if ((st = tc::group_gemm(b->g_exch, s, true, nk, g_err, sizeof(g_err), two ? b->s2 : nullptr)) != AFQMC_OK)
+      return st;
+    if (two && (st = batch_join(b, s)) != AFQMC_OK) return st;
+  }
+  if (energy) {
+    BatchStage t(b, s, AFQMC_STAGE_ENERGY);
+    k_energy_group<R><<<b->total_w, 256, 0, s>>>(static_cast<const EnergyArgs<R>*>(b->a_energy), first, nsys);
+    ++*nk;
+  }
+  {
+    BatchStage t(b, s, AFQMC_STAGE_FIELDS);
+    k_fields_group<R><<<b->total_w, 256, 0, s>>>(static_cast<const FieldArgs<R>*>(b->a_fields), first, nsys);
+    ++*nk;
+  }
+  {
+    BatchStage t(b, s, AFQMC_STAGE_VHS);
+    if ((st = tc::group_gemm(b->g_vhs, s, false, nk, g_err, sizeof(g_err))) != AFQMC_OK) return st;
+  }
+  {
+    BatchStage t(b, s, AFQMC_STAGE_PROPAGATE);
+    const bool two = b->g_prop.nsmall > 0 && b->g_prop.nlarge > 0;
+    if (two && (st = batch_fork(b, s)) != AFQMC_OK) return st;
+    if ((st = tc::group_propagate(b->g_prop, s, nk, g_err, sizeof(g_err), two ? b->s2 : nullptr)) != AFQMC_OK)
+      return st;
+    if (two && (st = batch_join(b, s)) != AFQMC_OK) return st;
+  }
+  {
+    BatchStage t(b, s, AFQMC_STAGE_OVERLAP);
+    k_overlap_group<R><<<b->total_w, 128, b->ovl_smem, s>>>(static_cast<const OverlapArgs<R>*>(b->a_overlap), first,
+                                                            static_cast<const int*>(b->a_stage), nsys);
+    ++*nk;
+  }
+  if (qr) {
+    BatchStage t(b, s, AFQMC_STAGE_QR);
+    k_qr_group<R><<<b->total_w, 256, b->qr_smem, s>>>(static_cast<const QrArgs<R>*>(b->a_qr), first, nsys);
+    ++*nk;
+  }
+  if (comb) {
+    BatchStage t(b, s, AFQMC_STAGE_COMB);
+    const CombArgs<R>* ca = static_cast<const CombArgs<R>*>(b->a_comb);
+    k_comb_plan_group<R><<<nsys, 256, 0, s>>>(ca);
+    k_comb_gather_group<R><<<b->total_w, 256, 0, s>>>(ca, first, nsys);
+    k_comb_back_group<R><<<b->total_w, 256, 0, s>>>(ca, first, nsys);
+    *nk += 3;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "grouped batch step: %s", cudaGetErrorString(e));
+  return AFQMC_OK;
+}
+
+// The executable graph of one grouped step kind (key: energy | qr << 1 | comb << 2 | thb << 3).
+afqmc_status batch_grouped_exec(afqmc_batch* b, int key, afqmc_batch::GExec** out) {
+  auto it = b->gcache.find(key);
+  if (it != b->gcache.end()) { *out = &it->second; return AFQMC_OK; }
+  afqmc_ctx* c0 = b->sys[0];
+  if (!c0->cap_stream) CU(cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));
+  afqmc_batch::GExec ex;
+  CU(cudaStreamBeginCapture(c0->cap_stream, cudaStreamCaptureModeThreadLocal));
+  afqmc_status st = batch_grouped_step(b, c0->cap_stream, key & 1, key & 2, key & 4, key & 8, &ex.nk);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c0->cap_stream, &g);
+  if (st != AFQMC_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return fail(AFQMC_ECUDA, "grouped batch capture: %s", cudaGetErrorString(e));
+  const cudaError_t ie = cudaGraphInstantiate(&ex.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return fail(AFQMC_ECUDA, "grouped batch graph instantiation: %s", cudaGetErrorString(ie));
+  auto res = b->gcache.emplace(key, ex);
+  *out = &res.first->second;
+  return AFQMC_OK;
+}
 
 afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb, afqmc_batch::Exec** out) {
   auto it = b->cache.find(key);
@@ -2203,6 +2515,81 @@ afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batc
 
 void afqmc_batch_destroy(afqmc_batch* b) { delete b; }
 
+afqmc_status afqmc_batch_set_mode(afqmc_batch* b, int32_t mode, int32_t exch_groups) {
+  if (!b) return fail(AFQMC_EINVAL, "batch is NULL");
+  if (mode < AFQMC_BATCH_AUTO || mode > AFQMC_BATCH_GRAPHS) return fail(AFQMC_EINVAL, "batch: unknown mode %d", mode);
+  if (exch_groups < 0 || exch_groups > 4) return fail(AFQMC_EINVAL, "batch: exch_groups must be in [0, 4]");
+  for (afqmc_ctx* c : b->sys) CU(cudaStreamSynchronize(c->stream));
+  if (mode != b->mode || exch_groups != b->exch_groups) b->drop_grouped();
+  b->mode = mode;
+  b->exch_groups = exch_groups;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_profile(afqmc_batch* b, int32_t enable) {
+  if (!b) return fail(AFQMC_EINVAL, "batch is NULL");
+  b->prof = enable != 0;
+  if (b->prof) {
+    std::fill(b->stage_ms, b->stage_ms + AFQMC_NSTAGES, 0.0);
+    std::fill(b->stage_n, b->stage_n + AFQMC_NSTAGES, 0LL);
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_stage_times(afqmc_batch* b, double* ms, int64_t* count) {
+  if (!b) return fail(AFQMC_EINVAL, "batch is NULL");
+  CU(cudaStreamSynchronize(b->sys[0]->stream));
+  for (auto& q : b->pending) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, q.a, q.b));
+    b->stage_ms[q.stage] += t;
+    b->stage_n[q.stage] += 1;
+    b->free_events.push_back(q.a);
+    b->free_events.push_back(q.b);
+  }
+  b->pending.clear();
+  for (int i = 0; i < AFQMC_NSTAGES; ++i) {
+    if (ms) ms[i] = b->stage_ms[i];
+    if (count) count[i] = b->stage_n[i];
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_describe(afqmc_batch* b, char* buf, size_t len) {
+  if (!b || !buf || len == 0) return fail(AFQMC_EINVAL, "batch or buffer is NULL");
+  std::string out;
+  char line[256];
+  if (!b->g_ready) {
+    out = "grouped launches not planned (runs in the graphs form, or before the first grouped run)\n";
+  } else {
+    auto part = [&](const char* what, const tc::GroupLaunch& gl) {
+      snprintf(line, sizeof(line),
+               "%s: %d problems, %d tiles, grid %d, %d stages of %d B, %d epilogue groups x %d B (width %d), "
+               "%d TMEM cols, %zu B smem\n",
+               what, gl.nprob, gl.tiles, gl.grid, gl.stages, gl.stage_stride, gl.epi_groups, gl.epi_bytes, gl.nb,
+               gl.tmem_cols, gl.smem);
+      out += line;
+    };
+    for (int k = 0; k < b->g_exch.nparts; ++k) part("exchange", b->g_exch.part[k]);
+    for (int k = 0; k < b->g_vhs.nparts; ++k) part("vhs", b->g_vhs.part[k]);
+    snprintf(line, sizeof(line), "propagate: %d small-form systems (grid %d, %zu B smem), %d large-form systems "
+             "(%d tiles, grid %d, %d stages)\n", b->g_prop.nsmall, b->g_prop.small_grid, b->g_prop.small_smem,
+             b->g_prop.nlarge, b->g_prop.large_tiles, b->g_prop.large_grid, b->g_prop.large_stages);
+    out += line;
+    snprintf(line, sizeof(line), "per-walker kernels: %d walkers in %zu systems\n", b->total_w, b->sys.size());
+    out += line;
+  }
+  snprintf(buf, len, "%s", out.c_str());
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_get_mode(afqmc_batch* b, int32_t* mode) {
+  if (!b || !mode) return fail(AFQMC_EINVAL, "batch or mode is NULL");
+  const char* why = "";
+  *mode = (b->mode != AFQMC_BATCH_GRAPHS && grouped_ok(b, &why)) ? AFQMC_BATCH_GROUPED : AFQMC_BATCH_GRAPHS;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
                              int32_t comb_every, double* energies, int32_t* nmeas) {
   if (!b) return fail(AFQMC_EINVAL, "batch is NULL");
@@ -2231,6 +2618,60 @@ afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_ever
     CU(cudaMemsetAsync(c->base + c->L.slot, 0, sizeof(int), s));
   }
   afqmc_status st;
+  // cached launches hold parameters (E_T, tuning) that a context may have changed since
+  std::vector<unsigned long long> gens;
+  for (afqmc_ctx* c : b->sys) gens.push_back(c->graph_gen);
+  if (gens != b->gens) {
+    b->drop_all();
+    b->gens = gens;
+  }
+  const char* why = "";
+  const bool grouped = b->mode != AFQMC_BATCH_GRAPHS && grouped_ok(b, &why);
+  if (b->mode == AFQMC_BATCH_GROUPED && !grouped) return fail(AFQMC_EINVAL, "batch: grouped form: %s", why);
+  if (grouped) {
+    if (!b->g_ready && (st = batch_grouped_plan(b)) != AFQMC_OK) return st;
+    bool thb = true;
+    for (afqmc_ctx* c : b->sys) {   // every system starts from its own Theta (and the same step kind)
+      if (!c->theta_fresh) {
+        if ((st = DISPATCH(c, launch_overlap, 2)) != AFQMC_OK) return st;
+        c->theta_fresh = true;
+      }
+      thb = thb && c->thb_valid;
+      CU(cudaStreamSynchronize(c->stream));
+    }
+    for (int k = 0; k < nsteps; ++k) {
+      const unsigned long long hs = c0->host_step;
+      const bool energy = energy_every > 0 && hs % (unsigned long long)energy_every == 0;
+      const bool qr = reortho_every > 0 && (hs + 1) % (unsigned long long)reortho_every == 0;
+      const bool comb = comb_every > 0 && (hs + 1) % (unsigned long long)comb_every == 0;
+      const int key = (energy ? 1 : 0) | (qr ? 2 : 0) | (comb ? 4 : 0) | (thb ? 8 : 0);
+      if (energy && used == kHistory - 1 && (st = flush()) != AFQMC_OK) return st;
+      if (b->prof) {   // direct launches, timed per stage
+        unsigned long long nk = 0;
+        if ((st = batch_grouped_step(b, s, energy, qr, comb, thb, &nk)) != AFQMC_OK) return st;
+        c0->launches += nk;
+      } else {
+        afqmc_batch::GExec* ex = nullptr;
+        if ((st = batch_grouped_exec(b, key, &ex)) != AFQMC_OK) return st;
+        CU(cudaGraphLaunch(ex->exec, s));
+        c0->launches += ex->nk;
+      }
+      for (afqmc_ctx* c : b->sys) {
+        c->theta_fresh = true;
+        c->thb_valid = !comb;   // the overlap writes the bf16 Theta operand; the comb reorders Theta only
+        c->vbias_fresh = false;
+        c->normals_pending = false;
+        c->host_step++;
+      }
+      thb = !comb;
+      if (energy) ++used;
+    }
+    if ((st = flush()) != AFQMC_OK) return st;
+    if (nmeas) *nmeas = total;
+    for (afqmc_ctx* c : b->sys)
+      if ((st = read_status(c)) != AFQMC_OK) return st;
+    return AFQMC_OK;
+  }
   for (int k = 0; k < nsteps; ++k) {
     const unsigned long long hs = c0->host_step;
     const bool energy = energy_every > 0 && hs % (unsigned long long)energy_every == 0;

@@ -37,6 +37,18 @@ __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   return mk((a.x * r + a.y) / den, (a.y * r - a.x) / den);
 }
 
+// Grouped launches over several systems: block b of the flattened grid belongs to the system s with
+// first[s] <= b < first[s + 1] (first[0] = 0, first[nsys] = the grid size).
+__device__ __forceinline__ int group_of(const int* __restrict__ first, int nsys, int b) {
+  int lo = 0, hi = nsys;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(first + mid) <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

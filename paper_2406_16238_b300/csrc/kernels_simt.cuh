@@ -316,15 +316,42 @@ __global__ void __launch_bounds__(256) k_exchange(ExchangeArgs<R> a) {
 // sums (ENumer, EDenom, E1Body, E2Body) over all walkers in a fixed order (free projection, wph
 // non-null: Re and Im of sum w e^{i phi} E_L, Re and Im of sum w e^{i phi}); with a slot counter
 // they go to out + 4 * (*slot) and the counter advances (graph-replayable history).
-template <typename R, bool CH = false>
-__global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double smul, double ecore, int nchunk,
-                                                const cplx_t<R>* thetaT, const void* hrot_v, const cplx_t<R>* vbias,
-                                                const double2* exch_part, double2* eloc, int W, const double* wgt,
-                                                const double* wph, double* out, int* slot, unsigned int* done) {
+template <typename R>
+struct EnergyArgs {
+  int N, X, ncol;
+  double smul, ecore;
+  int nchunk;
+  const cplx_t<R>* thetaT;
+  const void* hrot;           // htilde: real [ncol][N] at the walkers' precision, or complex (CH)
+  const cplx_t<R>* vbias;
+  const double2* exch_part;
+  double2* eloc;
+  int W;
+  const double* wgt;
+  const double* wph;
+  double* out;
+  int* slot;
+  unsigned int* done;
+};
+
+template <typename R, bool CH>
+__device__ __forceinline__ void energy_walker(const EnergyArgs<R> A, const int w) {
+  const int N = A.N, X = A.X, ncol = A.ncol, nchunk = A.nchunk, W = A.W;
+  const double smul = A.smul, ecore = A.ecore;
+  const cplx_t<R>* thetaT = A.thetaT;
+  const void* hrot_v = A.hrot;
+  const cplx_t<R>* vbias = A.vbias;
+  const double2* exch_part = A.exch_part;
+  double2* eloc = A.eloc;
+  const double* wgt = A.wgt;
+  const double* wph = A.wph;
+  double* out = A.out;
+  int* slot = A.slot;
+  unsigned int* done = A.done;
   __shared__ double red[32];
   __shared__ double part[6 * 256];
   __shared__ int last_s;
-  const int w = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int cn = ncol * N;
   const cplx_t<R>* th = thetaT + (size_t)w * cn;
   // per-thread partials at the walkers' precision (four independent chains), summed in binary64
@@ -421,6 +448,18 @@ __global__ void __launch_bounds__(256) k_energy(int N, int X, int ncol, double s
   }
 }
 
+template <typename R, bool CH = false>
+__global__ void __launch_bounds__(256) k_energy(EnergyArgs<R> a) {
+  energy_walker<R, CH>(a, blockIdx.x);
+}
+// Several systems in one launch, one block per walker (each system's last block forms its sums).
+template <typename R, bool CH = false>
+__global__ void __launch_bounds__(256) k_energy_group(const EnergyArgs<R>* __restrict__ args,
+                                                      const int* __restrict__ first, int nsys) {
+  const int s = group_of(first, nsys, blockIdx.x);
+  energy_walker<R, CH>(args[s], blockIdx.x - first[s]);
+}
+
 // ============================================================================
 // Fields (Eq. 8, 10, 12): x ~ N(0,1) (Philox), xbar = -i sqrt(dt)(vbias - lbar)
 // capped, xs = x - xbar, VHS coefficient -i sqrt(dt) xs, c_mf = i sqrt(dt) xs.lbar,
@@ -448,11 +487,8 @@ struct FieldArgs {
 
 // The N(0,1) fields of every walker slot at the current step counter (stream 0) into x[w][g],
 // one thread per pair (2j, 2j+1), grid-stride.
-__global__ void __launch_bounds__(128) k_normals(unsigned long long seed, const unsigned long long* step, int W,
-                                                 int X, double* x) {
-  __shared__ SeriesTables tab;
-  if (threadIdx.x == 0) fill_series_tables(&tab);
-  __syncthreads();
+__device__ __forceinline__ void normals_grid(unsigned long long seed, const unsigned long long* step, int W, int X,
+                                             double* x, const SeriesTables& tab) {
   const unsigned long long st = *step;
   const int npairs = (X + 1) / 2;
   const long long total = (long long)W * npairs;
@@ -465,13 +501,45 @@ __global__ void __launch_bounds__(128) k_normals(unsigned long long seed, const 
     if (2 * j + 1 < X) x[(size_t)w * X + 2 * j + 1] = z1;
   }
 }
+__global__ void __launch_bounds__(128) k_normals(unsigned long long seed, const unsigned long long* step, int W,
+                                                 int X, double* x) {
+  __shared__ SeriesTables tab;
+  if (threadIdx.x == 0) fill_series_tables(&tab);
+  __syncthreads();
+  normals_grid(seed, step, W, X, x, tab);
+}
+// Several systems: blockIdx.y is the system.
+struct NormalsArgs {
+  unsigned long long seed;
+  const unsigned long long* step;
+  int W, X;
+  double* x;
+};
+__global__ void __launch_bounds__(128) k_normals_group(const NormalsArgs* __restrict__ args) {
+  __shared__ SeriesTables tab;
+  if (threadIdx.x == 0) fill_series_tables(&tab);
+  __syncthreads();
+  const NormalsArgs a = args[blockIdx.y];
+  normals_grid(a.seed, a.step, a.W, a.X, a.x, tab);
+}
+
+// Zeroes n[s] float2 at p[s] for system s = blockIdx.y.
+struct ZeroArgs {
+  float2* p;
+  size_t n;
+};
+__global__ void k_zero_group(const ZeroArgs* __restrict__ args) {
+  const ZeroArgs a = args[blockIdx.y];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.n; i += (size_t)gridDim.x * blockDim.x)
+    a.p[i] = make_float2(0.f, 0.f);
+}
 
 // Fields of one walker per CTA from the normals x[w][g] drawn by k_normals.  Registers held for
 // 5 CTAs per SM: W = 640 walkers in one wave on 148 SMs.
 template <typename R>
-__global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
+__device__ __forceinline__ void fields_walker(const FieldArgs<R> a, const int w) {
   __shared__ double red[32];
-  const int w = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   // c_mf = i sdt sum lbar_g xs_g; sum (x xbar - xbar^2 / 2) = sum (a x - (a^2 - b^2) / 2) +
   // i sum b (x - a) for xbar = a + i b, kept as sum a x, sum (a^2 - b^2) and sum b (x - a)
   double2 cm = mk(0.0, 0.0);
@@ -544,6 +612,16 @@ __global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
     a.xxbar[w] = mk(red[2], red[3]);
   }
 }
+template <typename R>
+__global__ void __launch_bounds__(256, 5) k_fields(FieldArgs<R> a) {
+  fields_walker<R>(a, blockIdx.x);
+}
+template <typename R>
+__global__ void __launch_bounds__(256, 5) k_fields_group(const FieldArgs<R>* __restrict__ args,
+                                                         const int* __restrict__ first, int nsys) {
+  const int s = group_of(first, nsys, blockIdx.x);
+  fields_walker<R>(args[s], blockIdx.x - first[s]);
+}
 
 // Standalone draw (C-ABI afqmc_draw_normals): grid over walker slots.
 __global__ void __launch_bounds__(256) k_draw_normals(unsigned long long seed, unsigned long long step,
@@ -565,9 +643,8 @@ __global__ void __launch_bounds__(256) k_draw_normals(unsigned long long seed, u
 // Comb population control.  One CTA: sequential (index-order) binary64 prefix
 // of the weights, xi from Philox stream 1, tooth search.  Then a gather.
 // ============================================================================
-__global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long seed, const unsigned long long* step,
-                                                   const double* w, double* cum, int* src, double* neww,
-                                                   int* status) {
+__device__ __forceinline__ void comb_plan(int W, unsigned long long seed, const unsigned long long* step,
+                                          const double* w, double* cum, int* src, double* neww, int* status) {
   constexpr int kTile = 2048;
   __shared__ double ws[kTile];
   __shared__ double total_s, xi_s;
@@ -630,12 +707,43 @@ __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long see
   }
 }
 
+__global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long seed, const unsigned long long* step,
+                                                   const double* w, double* cum, int* src, double* neww,
+                                                   int* status) {
+  comb_plan(W, seed, step, w, cum, src, neww, status);
+}
+
+// The comb of several systems (one launch per phase): the plans (one block per system), the gather of
+// every system's walkers into its spare buffers (one block per walker), and the copy back.
 template <typename R>
-__global__ void __launch_bounds__(256) k_comb_gather(int W, int psi_elems, int th_elems, const int* src,
-                                                     const double* neww, const cplx_t<R>* psi, cplx_t<R>* psi_out,
-                                                     const cplx_t<R>* th, cplx_t<R>* th_out, const double2* logO,
-                                                     double2* logO_out, const double* w, double* w_out) {
-  const int k = blockIdx.x;
+struct CombArgs {
+  int W, psi_elems;
+  unsigned long long seed;
+  const unsigned long long* step;
+  double* cum;
+  int* src;
+  double* neww;
+  int* status;
+  cplx_t<R>* psi;
+  cplx_t<R>* psi_tmp;
+  cplx_t<R>* th;
+  cplx_t<R>* th_tmp;
+  double2* logO;
+  double2* logO_tmp;
+  double* w;
+  double* w_tmp;
+};
+template <typename R>
+__global__ void __launch_bounds__(256) k_comb_plan_group(const CombArgs<R>* __restrict__ args) {
+  const CombArgs<R> a = args[blockIdx.x];
+  comb_plan(a.W, a.seed, a.step, a.w, a.cum, a.src, a.neww, a.status);
+}
+
+template <typename R>
+__device__ __forceinline__ void comb_gather(int k, int psi_elems, int th_elems, const int* src, const double* neww,
+                                            const cplx_t<R>* psi, cplx_t<R>* psi_out, const cplx_t<R>* th,
+                                            cplx_t<R>* th_out, const double2* logO, double2* logO_out,
+                                            const double* w, double* w_out) {
   const int s = src[k];
   const double nw = *neww;
   for (int i = threadIdx.x; i < psi_elems; i += blockDim.x) psi_out[(size_t)k * psi_elems + i] = psi[(size_t)s * psi_elems + i];
@@ -643,6 +751,39 @@ __global__ void __launch_bounds__(256) k_comb_gather(int W, int psi_elems, int t
   if (threadIdx.x == 0) {
     logO_out[k] = logO[s];
     w_out[k] = nw >= 0.0 ? nw : w[s];
+  }
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_comb_gather(int W, int psi_elems, int th_elems, const int* src,
+                                                     const double* neww, const cplx_t<R>* psi, cplx_t<R>* psi_out,
+                                                     const cplx_t<R>* th, cplx_t<R>* th_out, const double2* logO,
+                                                     double2* logO_out, const double* w, double* w_out) {
+  (void)W;
+  comb_gather<R>(blockIdx.x, psi_elems, th_elems, src, neww, psi, psi_out, th, th_out, logO, logO_out, w, w_out);
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_comb_gather_group(const CombArgs<R>* __restrict__ args,
+                                                           const int* __restrict__ first, int nsys) {
+  const int s = group_of(first, nsys, blockIdx.x);
+  const CombArgs<R> a = args[s];
+  comb_gather<R>(blockIdx.x - first[s], a.psi_elems, a.psi_elems, a.src, a.neww, a.psi, a.psi_tmp, a.th, a.th_tmp,
+                 a.logO, a.logO_tmp, a.w, a.w_tmp);
+}
+// The gathered walkers back into place (walker k of system s per block).
+template <typename R>
+__global__ void __launch_bounds__(256) k_comb_back_group(const CombArgs<R>* __restrict__ args,
+                                                         const int* __restrict__ first, int nsys) {
+  const int s = group_of(first, nsys, blockIdx.x);
+  const CombArgs<R> a = args[s];
+  const int k = blockIdx.x - first[s];
+  const size_t off = (size_t)k * a.psi_elems;
+  for (int i = threadIdx.x; i < a.psi_elems; i += blockDim.x) {
+    a.psi[off + i] = a.psi_tmp[off + i];
+    a.th[off + i] = a.th_tmp[off + i];
+  }
+  if (threadIdx.x == 0) {
+    a.logO[k] = a.logO_tmp[k];
+    a.w[k] = a.w_tmp[k];
   }
 }
 
@@ -1042,14 +1183,14 @@ __device__ __forceinline__ void subst_rows_blocked(cplx_t<R>* Y, int ldy, const 
 }
 
 // 5 CTAs per SM: the W = 640 walkers of the benchmark shape run in one wave on 148 SMs.
-template <typename R, bool STAGE, bool CPHI = false>
-__global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
+template <typename R, bool STAGE, bool CPHI>
+__device__ __forceinline__ void overlap_walker(const OverlapArgs<R> a, const int w) {
   using R2 = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char sm_lu[];
   __shared__ int piv_s, sing_s, swaps_s, exp_s;
   __shared__ double2 inv_s, prod_s;
   __shared__ double ld_im_s;   // imaginary part of log det (its atan2 runs in a second warp)
-  const int w = blockIdx.x, tid = threadIdx.x, N = a.N;
+  const int tid = threadIdx.x, N = a.N;
   if (tid == 32) ld_im_s = 0.0;
   if (a.mode == 1 && a.step != nullptr && w == 0 && tid == 0) *a.step += 1ull;
   if (a.mode == 1 && a.w[w] == 0.0) return;
@@ -1405,6 +1546,20 @@ __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
     a.logO[w] = lo_new;
   }
 }
+template <typename R, bool STAGE, bool CPHI = false>
+__global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
+  overlap_walker<R, STAGE, CPHI>(a, blockIdx.x);
+}
+// Several systems in one launch, one block per walker; stage[s]: system s stages psi and Theta
+// in shared memory (the launch's shared memory covers the largest system's need).
+template <typename R, bool CPHI = false>
+__global__ void __launch_bounds__(128, 5) k_overlap_group(const OverlapArgs<R>* __restrict__ args,
+                                                          const int* __restrict__ first,
+                                                          const int* __restrict__ stage, int nsys) {
+  const int s = group_of(first, nsys, blockIdx.x);
+  if (stage[s]) overlap_walker<R, true, CPHI>(args[s], blockIdx.x - first[s]);
+  else overlap_walker<R, false, CPHI>(args[s], blockIdx.x - first[s]);
+}
 
 // ============================================================================
 // Cholesky QR, one CTA per walker: G = psi^H psi accumulated in binary64
@@ -1435,14 +1590,30 @@ __host__ __device__ inline size_t qr_smem_bytes(int N, int nmax, bool stage) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int c00, int n0, int c01, int n1,
-                                                 double smul, cplx_t<R>* psi, double2* logO, const double* wgt,
-                                                 int* status, int stage_psi) {
+struct QrArgs {
+  int N, ncol, nblk, c00, n0, c01, n1;
+  double smul;
+  cplx_t<R>* psi;
+  double2* logO;
+  const double* wgt;
+  int* status;
+  int stage_psi;
+};
+
+template <typename R>
+__device__ __forceinline__ void qr_walker(const QrArgs<R> A, const int w) {
+  const int N = A.N, ncol = A.ncol, nblk = A.nblk, c00 = A.c00, n0 = A.n0, c01 = A.c01, n1 = A.n1;
+  const double smul = A.smul;
+  cplx_t<R>* psi = A.psi;
+  double2* logO = A.logO;
+  const double* wgt = A.wgt;
+  int* status = A.status;
+  const int stage_psi = A.stage_psi;
   using R2 = cplx_t<R>;
   extern __shared__ double2 sm_cq[];
   __shared__ double logsum_s;
   __shared__ int bad_s;
-  const int w = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   if (wgt[w] == 0.0) return;
   if (tid == 0) { logsum_s = 0.0; bad_s = 0; }
   const int ldp = qr_pitch(N), nmax = max(n0, nblk > 1 ? n1 : 0);
@@ -1561,6 +1732,16 @@ __global__ void __launch_bounds__(256) k_qr_chol(int N, int ncol, int nblk, int 
     if (bad_s) atomicOr(status, kStatusSingular);
     logO[w].x -= smul * logsum_s;
   }
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_qr_chol(QrArgs<R> a) {
+  qr_walker<R>(a, blockIdx.x);
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_qr_group(const QrArgs<R>* __restrict__ args, const int* __restrict__ first,
+                                                  int nsys) {
+  const int s = group_of(first, nsys, blockIdx.x);
+  qr_walker<R>(args[s], blockIdx.x - first[s]);
 }
 
 }  // namespace afq

@@ -28,6 +28,7 @@ namespace tc {
 
 constexpr int kStageA = kBM * kBK * 2;           // 16 KiB
 constexpr int kTailBytes = 512;                  // mbarriers, TMEM slot, abort flag (< 256 B), then the series tables
+constexpr int kParamSlot = 384;                  // grouped launch: one epilogue group's copy of its problem's Params
 
 struct Geom {
   int m_tiles, n_tiles, k_blocks;
@@ -68,7 +69,8 @@ struct Params {
   Geom g;
   int* status;
   // exchange epilogue
-  int W, X, n, gpt, wpt, chunk_offset, nchunk, vbias_add;
+  int W, X, n, gpt, wpt, chunk_offset, nchunk;
+  int vbias_add;   // staged epilogue: 0 store, 1 add (second spin block), 2 atomic add (grouped launch)
   float smul;
   float2* vbias;
   double2* exch_part;
@@ -195,6 +197,10 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
         }
         float2* dst = p.vbias + (size_t)w * p.X + gam;
         float2 val = make_float2(p.smul * sr, p.smul * si);
+        if (p.vbias_add == 2) {   // grouped launch: both spin blocks run at once, onto a cleared vbias
+          atomicAdd(dst, val);
+          continue;
+        }
         if (p.vbias_add) {
           val.x += dst->x;
           val.y += dst->y;
@@ -444,39 +450,93 @@ __device__ void draw_normals_warp(const NormalsJob& nj, uint8_t* tab_mem, int la
 }
 
 // ----------------------------------------------------------------------------- the kernel
-template <int EPI, int NB = 0>
+// GROUP: one persistent launch over the tiles of several independent problems (systems, spin
+// blocks).  Problem i owns tiles [tile0, tile0 + tiles) of the launch's list (in problem order, each
+// CTA's tiles ascending, so a cursor finds the problem); its tensor maps and parameters are read
+// from device memory.  The ring of stages, the epilogue buffers and the two accumulators are laid
+// out for the largest problem (GroupArgs); each problem's own Geom gives its tiles, K blocks, MMA N
+// and the bytes a stage receives.
+static_assert(sizeof(Params) <= kParamSlot && sizeof(Params) % 4 == 0, "parameter slot");
+
+struct GroupProblem {   // aligned as its tensor maps
+  CUtensorMap mapA, mapB;
+  Params p;        // p.g: the problem's own tiles, MMA N, stage bytes, epilogue groups and buffers
+  int tile0, tiles;
+  int nb;          // exchange: register-row epilogue width (8, 16, 24, 32), 0: the staged epilogue (one per launch)
+};
+struct GroupArgs {
+  const GroupProblem* probs;
+  int nprob, tiles;
+  int stages, stage_stride, epi_groups, epi_bytes, tmem_cols, acc_stride;
+  const NormalsJob* nrm;   // exchange: normals drawn by the spare warp, one job per system
+  int nnrm;
+};
+
+template <int EPI, int NB = 0, bool GROUP = false>
 __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
-                                                    const __grid_constant__ CUtensorMap mapB, const Params p) {
+                                                    const __grid_constant__ CUtensorMap mapB,
+                                                    const __grid_constant__ Params p,
+                                                    const __grid_constant__ GroupArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const Geom& g = p.g;
-  const int stage_bytes = g.stage_bytes;
-  uint8_t* epi_base = smem + (size_t)g.stages * stage_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + (size_t)g.epi_groups * g.epi_bytes);
+  const int stages = GROUP ? ga.stages : p.g.stages;
+  const int stride = GROUP ? ga.stage_stride : p.g.stage_bytes;
+  const int egroups = GROUP ? ga.epi_groups : p.g.epi_groups;
+  const int ebytes = GROUP ? ga.epi_bytes : p.g.epi_bytes;
+  const int tmem_cols = GROUP ? ga.tmem_cols : p.g.tmem_cols;
+  const uint32_t acc_stride = (uint32_t)(GROUP ? ga.acc_stride : p.g.bn);
+  const int tiles = GROUP ? ga.tiles : p.g.m_tiles * p.g.n_tiles;
+  uint8_t* epi_base = smem + (size_t)stages * stride;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + (size_t)egroups * ebytes);
   uint64_t* full = bars;
-  uint64_t* empty = bars + g.stages;
-  uint64_t* tfull = bars + 2 * g.stages;
+  uint64_t* empty = bars + stages;
+  uint64_t* tfull = bars + 2 * stages;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles = g.m_tiles * g.n_tiles;
+
+  // the problem of tile t: parameters, maps, the tile's index within the problem, epilogue width
+  struct Item {
+    const Params* p;
+    const CUtensorMap* a;
+    const CUtensorMap* b;
+    int t, nb;
+  };
+  auto resolve = [&](int t, int& cur) -> Item {
+    if constexpr (GROUP) {
+      while (cur + 1 < ga.nprob && t >= ga.probs[cur + 1].tile0) ++cur;
+      const GroupProblem& pr = ga.probs[cur];
+      return Item{&pr.p, &pr.mapA, &pr.mapB, t - pr.tile0, pr.nb};
+    } else {
+      (void)cur;
+      return Item{&p, &mapA, &mapB, t, NB};
+    }
+  };
+  auto give_up = [&]() {
+    if constexpr (GROUP) {
+      for (int i = 0; i < ga.nprob; ++i) atomicOr(ga.probs[i].p.status, kStatusTimeout);
+    } else {
+      atomicOr(p.status, kStatusTimeout);
+    }
+    *abort_flag = 1;
+  };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < g.stages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 4 * g.epi_groups);
+      mbar_init(&tempty[a], 4 * egroups);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(g.tmem_cols)
+                 "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -487,23 +547,25 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
 
   if (warp == 0) {
     if (lane == 0) {   // TMA producer
-      int stage = 0;
+      int stage = 0, cur = 0;
       uint32_t ph = 0;
       bool go = true;
       for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
+        const Item it = resolve(t, cur);
+        const Geom g = it.p->g;   // a register copy: the copies' asm would force reloads of a reference
         int mt, nt;
-        tile_mn(g, t, &mt, &nt);
+        tile_mn(g, it.t, &mt, &nt);
         for (int kb = 0; kb < g.k_blocks; ++kb) {
           if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
-          uint8_t* sa = smem + (size_t)stage * stage_bytes;
-          mbar_expect_tx(&full[stage], (uint32_t)stage_bytes);
+          uint8_t* sa = smem + (size_t)stage * stride;
+          mbar_expect_tx(&full[stage], (uint32_t)g.stage_bytes);
           if (g.dual) {
             const int kc = kb * kBK, ay = mt * g.m_step, by = nt * g.n_step;
-            tma_load_2d(sa, &mapA, &full[stage], kc, ay);
-            tma_load_2d(sa + kStageA, &mapA, &full[stage], g.a_lo + kc, ay);
-            tma_load_2d(sa + 2 * kStageA, &mapB, &full[stage], g.b_hi + kc, by);
-            tma_load_2d(sa + 2 * kStageA + g.bn * 128, &mapB, &full[stage], g.b_lo + kc, by);
-            if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+            tma_load_2d(sa, it.a, &full[stage], kc, ay);
+            tma_load_2d(sa + kStageA, it.a, &full[stage], g.a_lo + kc, ay);
+            tma_load_2d(sa + 2 * kStageA, it.b, &full[stage], g.b_hi + kc, by);
+            tma_load_2d(sa + 2 * kStageA + g.bn * 128, it.b, &full[stage], g.b_lo + kc, by);
+            if (++stage == stages) { stage = 0; ph ^= 1u; }
             continue;
           }
           int ka = kb * kBK, kbb = kb * kBK;
@@ -512,30 +574,31 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
             ka = (sv == 1 ? g.seg : 0) + j * kBK;
             kbb = (sv == 2 ? g.seg : 0) + j * kBK;
           }
-          tma_load_2d(sa, &mapA, &full[stage], ka, mt * g.m_step);
-          tma_load_2d(sa + kStageA, &mapB, &full[stage], kbb, nt * g.n_step);
-          if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+          tma_load_2d(sa, it.a, &full[stage], ka, mt * g.m_step);
+          tma_load_2d(sa + kStageA, it.b, &full[stage], kbb, nt * g.n_step);
+          if (++stage == stages) { stage = 0; ph ^= 1u; }
         }
       }
-      if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+      if (!go) give_up();
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
-      int stage = 0;
+      int stage = 0, n_it = 0, cur = 0;
       uint32_t ph = 0;
-      int it = 0;
       bool go = true;
-      const uint32_t idesc = idesc_bf16(g.bn);
-      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x, ++it) {
-        const int acc = it & 1;
-        const uint32_t aph = (uint32_t)(it >> 1) & 1u;
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x, ++n_it) {
+        const Item it = resolve(t, cur);
+        const Geom g = it.p->g;   // a register copy (see the producer)
+        const uint32_t idesc = idesc_bf16(g.bn);
+        const int acc = n_it & 1;
+        const uint32_t aph = (uint32_t)(n_it >> 1) & 1u;
         if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { go = false; break; }
         tc_fence_after();
-        const uint32_t dtm = tmem_base + (uint32_t)(acc * g.bn);
+        const uint32_t dtm = tmem_base + (uint32_t)acc * acc_stride;
         for (int kb = 0; kb < g.k_blocks; ++kb) {
           if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes);
+          const uint32_t sa = smem_u32(smem + (size_t)stage * stride);
           if (g.dual) {
             const uint32_t sal = sa + kStageA, sb = sa + 2 * kStageA, sbl = sb + (uint32_t)(g.bn * 128);
 #pragma unroll
@@ -554,42 +617,74 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
                 umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, (kb | k) != 0 ? 1u : 0u);
           }
           umma_commit(&empty[stage]);
-          if (++stage == g.stages) { stage = 0; ph ^= 1u; }
+          if (++stage == stages) { stage = 0; ph ^= 1u; }
         }
         if (!go) break;
         umma_commit(&tfull[acc]);
       }
-      if (!go) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
+      if (!go) give_up();
     }
-  } else if (warp >= 2 + 4 * g.epi_groups) {   // spare warp: the step's normals (binary64 pipe)
-    if (EPI == 0 && p.nrm.x) draw_normals_warp(p.nrm, reinterpret_cast<uint8_t*>(bars) + 256, lane);
+  } else if (warp >= 2 + 4 * egroups) {   // spare warp: the step's normals (binary64 pipe)
+    if constexpr (GROUP) {
+      for (int j = 0; j < ga.nnrm; ++j) draw_normals_warp(ga.nrm[j], reinterpret_cast<uint8_t*>(bars) + 256, lane);
+    } else {
+      if (EPI == 0 && p.nrm.x) draw_normals_warp(p.nrm, reinterpret_cast<uint8_t*>(bars) + 256, lane);
+    }
   } else {   // epilogue warps
     const int ew = warp - 2, group = ew >> 2, wig = ew & 3, q = warp & 3;
     const int r = 32 * q + lane;
-    const EpiSmem es = epi_smem(epi_base, p, group, NB > 0);
-    int it = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
-      const int acc = it & 1;
-      const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-      if (wig == 0 && lane == 0) {   // slot it & 1 is rewritten two tiles later, after this group's next barrier
+    // the group's tile-ready flags: EpiSmem::ok (single problem), or a launch-wide slot in the tail
+    // (grouped: each problem lays out its own epilogue buffers)
+    int* ok_flags = GROUP ? reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(bars) + 128) + 2 * group
+                          : reinterpret_cast<int*>(epi_base + (size_t)group * ebytes);
+    const EpiSmem es0 = epi_smem(epi_base, p, group, NB > 0);                      // single problem
+    int n_it = 0, cur = 0, loaded = -1;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++n_it) {
+      const int acc = n_it & 1;
+      const uint32_t aph = (uint32_t)(n_it >> 1) & 1u;
+      if (wig == 0 && lane == 0) {   // slot n_it & 1 is rewritten two tiles later, after this group's next barrier
         const bool ok = mbar_wait(&tfull[acc], aph, abort_flag);
-        if (!ok) { atomicOr(p.status, kStatusTimeout); *abort_flag = 1; }
-        es.ok[it & 1] = ok ? 1 : 0;
+        if (!ok) give_up();
+        ok_flags[n_it & 1] = ok ? 1 : 0;
       }
       named_bar(1 + group, 128);   // also: every thread of the group is done with the previous tile's buffers
-      const int ok = es.ok[it & 1];
+      const int ok = ok_flags[n_it & 1];
       if (!ok) break;
       tc_fence_after();
-      const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * g.bn);
+      const Item it = resolve(t, cur);
+      const Params* ppp = it.p;
+      if constexpr (GROUP) {   // the problem's parameters into the group's shared-memory slot
+        Params* slot = reinterpret_cast<Params*>(reinterpret_cast<uint8_t*>(bars) + kTailBytes + group * kParamSlot);
+        if (cur != loaded) {   // every thread of the group is past the previous tile (barrier above)
+          const int* src = reinterpret_cast<const int*>(it.p);
+          int* dst = reinterpret_cast<int*>(slot);
+          for (int i = r; i < (int)(sizeof(Params) / 4); i += 128) dst[i] = src[i];
+          named_bar(1 + group, 128);
+          loaded = cur;
+        }
+        ppp = slot;
+      }
+      const Params& pp = *ppp;
+      const uint32_t tacc = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride;
       int mt, nt;
-      tile_mn(g, t, &mt, &nt);
-      if constexpr (EPI == 0 && NB > 0) exchange_tile_reg<NB>(p, mt, nt, tacc, es, group, wig, r, lane);
-      else if (EPI == 0) exchange_tile(p, mt, nt, tacc, es, group, wig, r, lane);
-      else if (EPI == 1) store_tile(p, mt, nt, tacc, group, r);
-      else if (p.blocks)
-        store_planes_packed(p, mt, nt, tacc, group, r,
-                            reinterpret_cast<__nv_bfloat16*>(epi_base + (size_t)group * g.epi_bytes + 16));
-      else store_planes(p, mt, nt, tacc, group, r);
+      tile_mn(pp.g, it.t, &mt, &nt);
+      if (GROUP && group >= pp.g.epi_groups) {
+        // a problem with fewer epilogue groups than the launch: this group idles for the tile
+      } else if constexpr (EPI == 0 && !GROUP) {
+        if constexpr (NB > 0) exchange_tile_reg<NB>(pp, mt, nt, tacc, es0, group, wig, r, lane);
+        else exchange_tile(pp, mt, nt, tacc, es0, group, wig, r, lane);
+      } else if constexpr (EPI == 0) {   // grouped: every problem of the launch has the epilogue width NB
+        const EpiSmem es = epi_smem(epi_base, pp, group, NB > 0);
+        if constexpr (NB > 0) exchange_tile_reg<NB>(pp, mt, nt, tacc, es, group, wig, r, lane);
+        else exchange_tile(pp, mt, nt, tacc, es, group, wig, r, lane);
+      } else if constexpr (EPI == 1) {
+        store_tile(pp, mt, nt, tacc, group, r);
+      } else if (pp.blocks) {
+        store_planes_packed(pp, mt, nt, tacc, group, r,
+                            reinterpret_cast<__nv_bfloat16*>(epi_base + (size_t)group * pp.g.epi_bytes + 16));
+      } else {
+        store_planes(pp, mt, nt, tacc, group, r);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -604,7 +699,7 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
   __syncthreads();
   tc_fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(g.tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols) : "memory");
 }
 
 
@@ -795,10 +890,9 @@ __global__ void __launch_bounds__(608, 1) k_exch_tm(const __grid_constant__ CUte
 
 // ----------------------------------------------------------------------------- operand conversion
 // Theta^T complex64 [W][ncol][N] -> per block rows (w, part, b) of nseg * kst bf16: B = [hi | hi | lo].
-__global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int nseg, const float2* thetaT,
-                             __nv_bfloat16* out, const int* widx, int kst0 = 0) {
-  const int w = blockIdx.x;              // output row block
-  const int src = widx ? widx[w] : w;    // walker it holds
+// Row block w holds walker src.
+__device__ __forceinline__ void theta_bf16_rows(int w, int src, int N, int ncol, int c0, int n, int kst, int nseg,
+                                                const float2* thetaT, __nv_bfloat16* out, int kst0) {
   const int rowlen = nseg * kst;
   for (int idx = threadIdx.x; idx < 2 * n * kst; idx += blockDim.x) {
     const int row = idx / kst, k = idx % kst;
@@ -821,6 +915,26 @@ __global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int
       dst[2 * kst] = lo;
     }
   }
+}
+
+__global__ void k_theta_bf16(int W, int N, int ncol, int c0, int n, int kst, int nseg, const float2* thetaT,
+                             __nv_bfloat16* out, const int* widx, int kst0 = 0) {
+  (void)W;
+  const int w = blockIdx.x;   // output row block
+  theta_bf16_rows(w, widx ? widx[w] : w, N, ncol, c0, n, kst, nseg, thetaT, out, kst0);
+}
+
+// The bf16 Theta^T operands of several (system, spin block) jobs, one block per walker.
+struct ThetaJob {
+  int N, ncol, c0, n, kst, nseg, kst0;
+  const float2* thetaT;
+  __nv_bfloat16* out;
+};
+__global__ void k_theta_bf16_group(const ThetaJob* __restrict__ jobs, const int* __restrict__ first, int njobs) {
+  const int j = group_of(first, njobs, blockIdx.x);
+  const ThetaJob& a = jobs[j];
+  const int w = blockIdx.x - first[j];
+  theta_bf16_rows(w, w, a.N, a.ncol, a.c0, a.n, a.kst, a.nseg, a.thetaT, a.out, a.kst0);
 }
 
 // Ltilde [ng][ncol][N] (gammas g0 .. g0 + ng - 1, binary64 or binary32) -> block rows (g, a) of
@@ -1017,6 +1131,16 @@ bool exchange_reg(int n, int wpt, int bn) {
   return nb <= 32 && bn + (wpt - 1) * 2 * n + n + nb <= tmem_cols_for(bn);
 }
 
+// Tile order of the streamed exchange.  The dual form (long K), or any Ltilde block too large to stay
+// in L2, takes groups of walker tiles whose Theta operand (~32 MB) stays in L2, the M tiles in turn
+// within a group: each Ltilde tile then streams from HBM once per group, not once per walker tile.
+int exchange_ntg(const TcState* st, const BlockMaps& bm, const Geom& g) {
+  const long long a_bytes = (long long)st->X * bm.n * st->nseg * st->kst * 2;
+  if (!g.dual && a_bytes <= (24LL << 20)) return 0;
+  const long long bt = (long long)g.bn * (g.dual ? 2 : st->nseg) * st->kst * 2;   // Theta bytes per tile
+  return (int)std::max(1LL, std::min<long long>(g.n_tiles, (32LL << 20) / bt));
+}
+
 // Pick the stage count for a given B box height and epilogue footprint.
 bool finish_geom(Geom* g, int epi_bytes_per_group, int epi_groups) {
   g->epi_groups = epi_groups;
@@ -1046,7 +1170,7 @@ afqmc_status launch(const Geom& g, const CUtensorMap& a, const CUtensorMap& b, c
   }
   const int tiles = g.m_tiles * g.n_tiles;
   const int grid = std::min(tiles, num_sms());
-  k_tc_gemm<EPI, NB><<<grid, 64 + 128 * g.epi_groups + (p.nrm.x ? 32 : 0), sm, s>>>(a, b, p);
+  k_tc_gemm<EPI, NB><<<grid, 64 + 128 * g.epi_groups + (p.nrm.x ? 32 : 0), sm, s>>>(a, b, p, GroupArgs{});
   ++*launches;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1380,6 +1504,18 @@ afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen) {
   }
   // reserve the kernels' shared memory now (not while a stream is being captured)
   if (cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 24, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<0, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_tc_gemm<2, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+          cudaSuccess ||
       cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_tc_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_tc_gemm<0, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess ||
@@ -1437,10 +1573,8 @@ afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, con
       g.a_lo = st->kst;
       g.b_hi = 0;
       g.b_lo = 2 * st->kst;
-      // groups of walker tiles whose Theta operand (hi and lo, ~bn x 2 kst bf16 each) stays in L2
-      const long long bt = (long long)g.bn * 2 * st->kst * 2;
-      g.ntg = (int)std::max(1LL, std::min<long long>(g.n_tiles, (32LL << 20) / bt));
     }
+    if (bm.form == 0) g.ntg = exchange_ntg(st, bm, g);
     const bool reg = bm.form == 1 || exchange_reg(bm.n, bm.wpt, g.bn);
     const int epb = epi_bytes_exchange(bm.n, reg);
     if (bm.form == 0 && !finish_geom(&g, epb, bm.groups)) {
@@ -1580,6 +1714,378 @@ afqmc_status vhs(TcState* st, cudaStream_t s, char* tcbuf, const float2* coef, f
   p.out_rows = 2 * st->W;
   p.out_cols = st->N * st->N;
   return launch<1>(g, st->map_coef, st->map_lt, p, s, launches, err, errlen);
+}
+
+// ----------------------------------------------------------------------------- grouped launches
+namespace {
+
+template <typename T>
+afqmc_status to_device(const std::vector<T>& v, void** dev, char* err, size_t errlen) {
+  *dev = nullptr;
+  if (v.empty()) return AFQMC_OK;
+  if (cudaMalloc(dev, v.size() * sizeof(T)) != cudaSuccess ||
+      cudaMemcpy(*dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    snprintf(err, errlen, "grouped launch: device descriptors (%zu bytes)", v.size() * sizeof(T));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
+// Problems in order of the cost of one tile (K blocks x MMA N x products per k-step), the most
+// expensive first (the CTAs take tiles in turn), and their tile ranges; returns the tile count.
+int order_problems(std::vector<GroupProblem>& pr) {
+  auto cost = [](const GroupProblem& q) { return (long long)q.p.g.k_blocks * q.p.g.bn * (q.p.g.dual ? 3 : 1); };
+  std::stable_sort(pr.begin(), pr.end(), [&](const GroupProblem& a, const GroupProblem& b) { return cost(a) > cost(b); });
+  int t = 0;
+  for (auto& q : pr) {
+    q.tile0 = t;
+    q.tiles = q.p.g.m_tiles * q.p.g.n_tiles;
+    t += q.tiles;
+  }
+  return t;
+}
+
+int stage_bytes_of(const Geom& g) { return g.dual ? 2 * kStageA + 2 * g.bn * kBK * 2 : kStageA + g.bn * kBK * 2; }
+
+// The launch layout for the problems, each with its own epilogue groups and buffers (p.g.epi_groups,
+// p.g.epi_bytes): the stage stride, the epilogue region (the largest problem's), ring depth and
+// accumulators.  The launch runs the most groups any problem uses; a problem's surplus groups idle.
+bool group_layout(std::vector<GroupProblem>& pr, GroupLaunch* gg) {
+  int stride = 0, acc = 0, groups = 1, region = 0;
+  for (auto& q : pr) {
+    q.p.g.epi_bytes = (q.p.g.epi_bytes + 15) & ~15;
+    stride = std::max(stride, q.p.g.stage_bytes);
+    acc = std::max(acc, q.p.g.bn);
+    groups = std::max(groups, q.p.g.epi_groups);
+    region = std::max(region, q.p.g.epi_groups * q.p.g.epi_bytes);
+  }
+  const int per = ((region + groups - 1) / groups + 15) & ~15;   // the kernel sizes the region as groups x per
+  const int st = std::min(4, (kMaxSmem - 1024 - groups * per - kTailBytes - 4 * kParamSlot) / std::max(1, stride));
+  if (st < 2) return false;
+  gg->stages = st;
+  gg->stage_stride = stride;
+  gg->epi_groups = groups;
+  gg->epi_bytes = per;
+  gg->acc_stride = acc;
+  gg->tmem_cols = tmem_cols_for(acc);
+  if (gg->tmem_cols > 512) return false;
+  for (auto& q : pr) {
+    q.p.g.stages = st;
+    q.p.g.tmem_cols = gg->tmem_cols;
+  }
+  gg->smem = 1024 + (size_t)st * stride + (size_t)groups * per + kTailBytes + 4 * kParamSlot;
+  return gg->smem <= (size_t)kMaxSmem;
+}
+
+}  // namespace
+
+namespace {
+// Ring depth of a launch whose largest stage is `stride` bytes and largest epilogue region `region`.
+int group_stages(int stride, int region) {
+  return std::min(4, (kMaxSmem - 1024 - region - kTailBytes - 4 * kParamSlot) / std::max(1, stride));
+}
+int epi_region(const GroupProblem& q) { return q.p.g.epi_groups * ((q.p.g.epi_bytes + 15) & ~15); }
+
+// Problem (system i, block b) of the grouped exchange in the streamed form with at most cap
+// epilogue groups; the register-row epilogue where its loads stay within `acc` accumulator
+// columns of a launch whose tensor memory is laid out for MMA N <= acc.
+bool exchange_problem(const GroupSystem& sy, int b, int cap, int acc_min, GroupProblem* out, char* err,
+                      size_t errlen) {
+  TcState* st = sy.st;
+  BlockMaps bm = st->blk[b];   // a copy: the system's own exchange keeps its form
+  exchange_config(st, bm, cap, 1);
+  int chunk = 0;   // exchange partial slots of the earlier blocks
+  for (int b0 = 0; b0 < b; ++b0) chunk += 4 * st->blk[b0].m_tiles;
+  GroupProblem q{};
+  Geom& g = q.p.g;
+  g.m_tiles = bm.m_tiles;
+  g.n_tiles = (st->W + bm.wpt - 1) / bm.wpt;
+  g.k_blocks = (st->nseg * st->kst + kBK - 1) / kBK;
+  g.k_steps = st->nseg * st->kst / 16;
+  g.m_step = bm.gpt * bm.n;
+  g.n_step = bm.wpt * 2 * bm.n;
+  g.bn = bm.bn;
+  g.epi_groups = bm.groups;
+  if (bm.dual) {
+    g.dual = 1;
+    g.k_blocks = (st->kst + kBK - 1) / kBK;
+    g.k_steps = st->kst / 16;
+    g.a_lo = st->kst;
+    g.b_hi = 0;
+    g.b_lo = 2 * st->kst;
+  }
+  g.ntg = exchange_ntg(st, bm, g);
+  g.stage_bytes = stage_bytes_of(g);
+  q.mapA = bm.map_l;
+  if (!make_map(&q.mapB, sy.tcbuf + bm.off_th, (unsigned long long)st->W * 2 * bm.n,
+                (unsigned long long)st->nseg * st->kst, (unsigned)bm.bn)) {
+    snprintf(err, errlen, "grouped exchange: tensor map of the Theta operand");
+    return false;
+  }
+  Params& p = q.p;
+  p.status = sy.status;
+  p.W = st->W; p.X = st->X; p.n = bm.n; p.gpt = bm.gpt; p.wpt = bm.wpt;
+  p.chunk_offset = chunk; p.nchunk = st->nchunk;
+  p.vbias_add = 2;
+  p.smul = (float)sy.smul;
+  p.vbias = sy.vbias;
+  p.exch_part = sy.exch_part;
+  const int acc = std::max(acc_min, g.bn), nb = (bm.n + 7) / 8 * 8;
+  const bool reg = nb <= 32 && exchange_reg(p.n, p.wpt, g.bn) && acc + (p.wpt - 1) * 2 * p.n + p.n + nb <= tmem_cols_for(acc);
+  q.nb = reg ? nb : 0;
+  g.epi_bytes = epi_bytes_exchange(p.n, reg);
+  *out = q;
+  return true;
+}
+}  // namespace
+
+afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, GroupGemm* gg, char* err,
+                                 size_t errlen) {
+  *gg = GroupGemm{};
+  gg->epi = 0;
+  std::vector<ThetaJob> th;
+  std::vector<int> th_first(1, 0);
+  std::vector<NormalsJob> nrm;
+  // 1. every (system, block) in its own configuration: at most `groups` epilogue groups (0: the
+  //    system's tuned count where its exchange is streamed), fewer until two ring stages fit
+  struct Cand { int sys, blk, cap, stages; GroupProblem q; };
+  std::vector<Cand> cands;
+  for (int i = 0; i < nsys; ++i)
+    for (int b = 0; b < sys[i].st->nblk; ++b) {
+      const BlockMaps& bm = sys[i].st->blk[b];
+      if (bm.n == 0) continue;
+      Cand c{i, b, groups > 0 ? std::min(groups, 4) : (bm.form == 0 ? std::max(1, bm.groups) : 4), 0, GroupProblem{}};
+      for (;;) {
+        if (!exchange_problem(sys[i], b, c.cap, 0, &c.q, err, errlen)) return AFQMC_ECUDA;
+        c.stages = group_stages(c.q.p.g.stage_bytes, epi_region(c.q));
+        if (c.stages >= 2 || c.q.p.g.epi_groups <= 1) break;
+        c.cap = c.q.p.g.epi_groups - 1;
+      }
+      if (c.stages < 2) {
+        snprintf(err, errlen, "grouped exchange: system %d does not fit shared memory", i);
+        return AFQMC_EINVAL;
+      }
+      cands.push_back(c);
+    }
+  // 2. classes: a problem joins the first class whose merged layout keeps its ring depth (and the
+  //    class's); at most 8 classes, the rest going where the merged depth is largest
+  struct Cls { std::vector<int> mem; int stride = 0, region = 0, bn = 0, stages = 0, nb = 0; };
+  // a register-row problem keeps its epilogue under a launch whose accumulators are `acc` wide
+  auto reg_fits = [&](const Cand& c, int acc) {
+    const Params& p = c.q.p;
+    return c.q.nb == 0 || acc + (p.wpt - 1) * 2 * p.n + p.n + c.q.nb <= tmem_cols_for(acc);
+  };
+  std::vector<Cls> cls;
+  std::vector<int> order(cands.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cands[x].stages > cands[y].stages; });
+  for (int k : order) {
+    const Cand& c = cands[k];
+    int pick = -1, best = -1;
+    for (int j = 0; j < (int)cls.size(); ++j) {
+      if (cls[j].nb != c.q.nb) continue;   // one epilogue width per launch
+      const int acc = std::max(cls[j].bn, c.q.p.g.bn);
+      bool fits = reg_fits(c, acc);
+      for (int m : cls[j].mem) fits = fits && reg_fits(cands[m], acc);
+      if (!fits) continue;
+      const int d = group_stages(std::max(cls[j].stride, c.q.p.g.stage_bytes), std::max(cls[j].region, epi_region(c.q)));
+      if (d == c.stages && d == cls[j].stages) { pick = j; break; }
+      if (d >= 2 && d > best) { best = d; if ((int)cls.size() >= 8) pick = j; }
+    }
+    if (pick < 0 && (int)cls.size() < 8) {
+      cls.push_back(Cls{});
+      pick = (int)cls.size() - 1;
+      cls[pick].nb = c.q.nb;
+    }
+    if (pick < 0) {
+      snprintf(err, errlen, "grouped exchange: no shared-memory layout fits every system");
+      return AFQMC_EINVAL;
+    }
+    Cls& L = cls[pick];
+    L.mem.push_back(k);
+    L.stride = std::max(L.stride, c.q.p.g.stage_bytes);
+    L.region = std::max(L.region, epi_region(c.q));
+    L.bn = std::max(L.bn, c.q.p.g.bn);
+    L.stages = group_stages(L.stride, L.region);
+  }
+  // 3. one launch per class, the register-row epilogues decided against the class's accumulators
+  for (const Cls& L : cls) {
+    std::vector<GroupProblem> pr;
+    for (int k : L.mem) {
+      GroupProblem q;
+      if (!exchange_problem(sys[cands[k].sys], cands[k].blk, cands[k].cap, L.bn, &q, err, errlen)) {
+        group_free(gg);
+        return AFQMC_ECUDA;
+      }
+      pr.push_back(q);
+    }
+    GroupLaunch& gl = gg->part[gg->nparts];
+    gl.nb = L.nb;
+    for (const auto& q : pr)
+      if (q.nb != L.nb) {
+        snprintf(err, errlen, "grouped exchange: mixed epilogue widths in one launch");
+        group_free(gg);
+        return AFQMC_EINVAL;
+      }
+    if (!group_layout(pr, &gl)) {
+      snprintf(err, errlen, "grouped exchange: no shared-memory layout fits every system");
+      group_free(gg);
+      return AFQMC_EINVAL;
+    }
+    gl.tiles = order_problems(pr);
+    gl.nprob = (int)pr.size();
+    gl.grid = std::min(gl.tiles, num_sms());
+    afqmc_status r;
+    if ((r = to_device(pr, &gl.dev_probs, err, errlen)) != AFQMC_OK) {
+      group_free(gg);
+      return r;
+    }
+    ++gg->nparts;
+  }
+  for (int i = 0; i < nsys; ++i) {
+    TcState* st = sys[i].st;
+    if (sys[i].nj.x) nrm.push_back(sys[i].nj);
+    for (int b = 0; b < st->nblk; ++b) {
+      const BlockMaps& bm = st->blk[b];
+      if (bm.n == 0) continue;
+      ThetaJob j{st->N, st->ncol, bm.c0, bm.n, st->kst, st->nseg, st->cplx ? st->kst0 : 0, sys[i].thetaT,
+                 reinterpret_cast<__nv_bfloat16*>(sys[i].tcbuf + bm.off_th)};
+      th.push_back(j);
+      th_first.push_back(th_first.back() + st->W);
+    }
+  }
+  gg->nnrm = (int)nrm.size();
+  gg->ntheta = (int)th.size();
+  gg->theta_blocks = th_first.back();
+  afqmc_status r;
+  if ((r = to_device(nrm, &gg->dev_nrm, err, errlen)) != AFQMC_OK ||
+      (r = to_device(th, &gg->dev_theta, err, errlen)) != AFQMC_OK ||
+      (r = to_device(th_first, &gg->dev_theta_first, err, errlen)) != AFQMC_OK) {
+    group_free(gg);
+    return r;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status group_vhs_plan(const GroupSystem* sys, int nsys, GroupGemm* gg, char* err, size_t errlen) {
+  *gg = GroupGemm{};
+  gg->epi = 2;
+  std::vector<GroupProblem> pr;
+  for (int i = 0; i < nsys; ++i) {
+    TcState* st = sys[i].st;
+    char* tcbuf = sys[i].tcbuf;
+    if (!st->pg.ok) {
+      snprintf(err, errlen, "grouped VHS: system %d has no tensor-core propagation", i);
+      return AFQMC_EINVAL;
+    }
+    GroupProblem q{};
+    Geom& g = q.p.g;
+    g.m_tiles = (int)((st->lt_rows + kBM - 1) / kBM);
+    g.n_tiles = (2 * st->W + st->vhs_bn - 1) / st->vhs_bn;
+    g.k_blocks = st->nseg * st->kx / kBK;
+    g.k_steps = st->nseg * st->kx / 16;
+    if (st->nseg == 3 && vhs_dual(st)) {
+      g.dual = 1;
+      g.k_blocks = st->kx / kBK;
+      g.k_steps = st->kx / 16;
+      g.a_lo = st->kx;
+      g.b_hi = 0;
+      g.b_lo = st->kx;
+    } else if (st->nseg == 3) {
+      g.il3 = 1;
+      g.seg = st->kx;
+    }
+    g.m_step = kBM;
+    g.n_step = st->vhs_bn;
+    g.bn = st->vhs_bn;
+    g.stage_bytes = stage_bytes_of(g);
+    q.mapA = st->map_lt_a;
+    q.mapB = st->map_coef_b;
+    Params& p = q.p;
+    p.status = sys[i].status;
+    p.n = st->N;
+    p.out_rows = 2 * st->W;
+    p.out_cols = (int)st->lt_rows;
+    p.pairs = st->packed ? reinterpret_cast<const int*>(tcbuf + st->off_pairs) : nullptr;
+    p.blocks = st->packed ? reinterpret_cast<const int2*>(tcbuf + st->off_blocks) : nullptr;
+    p.planes = reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_vp);
+    p.npad = st->pg.npad;
+    p.kq = st->pg.kq;
+    g.epi_groups = 4;
+    g.epi_bytes = 16 + (st->packed ? 4096 : 0);   // packed: the mirrored rows' staging
+    pr.push_back(q);
+  }
+  GroupLaunch& gl = gg->part[0];
+  if (pr.empty() || !group_layout(pr, &gl)) {
+    snprintf(err, errlen, "grouped VHS: no shared-memory layout fits every system");
+    return AFQMC_EINVAL;
+  }
+  gl.tiles = order_problems(pr);
+  gl.nprob = (int)pr.size();
+  gl.grid = std::min(gl.tiles, num_sms());
+  gg->nparts = 1;
+  return to_device(pr, &gl.dev_probs, err, errlen);
+}
+
+afqmc_status group_gemm(const GroupGemm& gg, cudaStream_t s, bool normals, unsigned long long* launches, char* err,
+                        size_t errlen, cudaStream_t s2) {
+  for (int k = 0; k < gg.nparts; ++k) {
+    const GroupLaunch& gl = gg.part[k];
+    const cudaStream_t sk = (s2 && (k & 1)) ? s2 : s;
+    GroupArgs ga{};
+    ga.probs = static_cast<const GroupProblem*>(gl.dev_probs);
+    ga.nprob = gl.nprob;
+    ga.tiles = gl.tiles;
+    ga.stages = gl.stages;
+    ga.stage_stride = gl.stage_stride;
+    ga.epi_groups = gl.epi_groups;
+    ga.epi_bytes = gl.epi_bytes;
+    ga.tmem_cols = gl.tmem_cols;
+    ga.acc_stride = gl.acc_stride;
+    const bool draw = normals && k == 0;   // the first launch draws every system's normals
+    ga.nrm = draw ? static_cast<const NormalsJob*>(gg.dev_nrm) : nullptr;
+    ga.nnrm = draw ? gg.nnrm : 0;
+    const int threads = 64 + 128 * gl.epi_groups + (ga.nnrm ? 32 : 0);
+    const CUtensorMap none{};
+    const Params p0{};
+    if (gg.epi == 2) k_tc_gemm<2, 0, true><<<gl.grid, threads, gl.smem, sk>>>(none, none, p0, ga);
+    else if (gl.nb == 8) k_tc_gemm<0, 8, true><<<gl.grid, threads, gl.smem, sk>>>(none, none, p0, ga);
+    else if (gl.nb == 16) k_tc_gemm<0, 16, true><<<gl.grid, threads, gl.smem, sk>>>(none, none, p0, ga);
+    else if (gl.nb == 24) k_tc_gemm<0, 24, true><<<gl.grid, threads, gl.smem, sk>>>(none, none, p0, ga);
+    else if (gl.nb == 32) k_tc_gemm<0, 32, true><<<gl.grid, threads, gl.smem, sk>>>(none, none, p0, ga);
+    else k_tc_gemm<0, 0, true><<<gl.grid, threads, gl.smem, sk>>>(none, none, p0, ga);
+    ++*launches;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      snprintf(err, errlen, "grouped tcgen05 GEMM launch: %s", cudaGetErrorString(e));
+      return AFQMC_ECUDA;
+    }
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status group_theta(const GroupGemm& gg, cudaStream_t s, unsigned long long* launches, char* err, size_t errlen) {
+  if (gg.ntheta == 0) return AFQMC_OK;
+  k_theta_bf16_group<<<gg.theta_blocks, 256, 0, s>>>(static_cast<const ThetaJob*>(gg.dev_theta),
+                                                     static_cast<const int*>(gg.dev_theta_first), gg.ntheta);
+  ++*launches;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "grouped Theta conversion: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
+void group_free(GroupGemm* gg) {
+  for (auto& gl : gg->part) {
+    if (gl.dev_probs) cudaFree(gl.dev_probs);
+    gl.dev_probs = nullptr;
+  }
+  for (void* p : {gg->dev_nrm, gg->dev_theta, gg->dev_theta_first})
+    if (p) cudaFree(p);
+  gg->dev_nrm = gg->dev_theta = gg->dev_theta_first = nullptr;
+  gg->nparts = 0;
 }
 
 }  // namespace tc

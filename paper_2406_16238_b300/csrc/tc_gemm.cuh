@@ -143,5 +143,85 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
 afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, float2* psi, const double* w,
                        int* status, unsigned long long* launches, char* err, size_t errlen);
 
+// ------------------------------------------------------------------ grouped launches (uneven batches)
+// One persistent launch of the exchange (or the VHS planes) contraction over the tiles of several
+// systems and spin blocks (a work list ordered by tile cost), with the problems' tensor maps and
+// parameters in device memory.
+struct GroupSystem {
+  TcState* st;
+  char* tcbuf;
+  double smul;
+  const float2* thetaT;   // exchange: Theta^T complex64 [W][ncol][N]
+  float2* vbias;          // exchange: cleared before the launch, every block adds its traces
+  double2* exch_part;
+  int* status;
+  NormalsJob nj;          // exchange: the step's normals (nj.x == nullptr: none)
+};
+struct GroupLaunch {   // one persistent launch over several problems
+  int nprob = 0, tiles = 0, grid = 0;
+  int stages = 0, stage_stride = 0, epi_groups = 0, epi_bytes = 0, tmem_cols = 0, acc_stride = 0;
+  int nb = 0;                          // exchange: the launch's register-row epilogue width (0: staged)
+  size_t smem = 0;
+  void* dev_probs = nullptr;           // the problems (device)
+};
+struct GroupGemm {
+  int epi = 0;              // 0: exchange and force bias, 2: VHS planes
+  int nparts = 0;           // exchange: one launch per class of problems with one ring depth
+  GroupLaunch part[8];
+  void* dev_nrm = nullptr;             // NormalsJob per system (device)
+  int nnrm = 0;
+  void* dev_theta = nullptr;           // exchange: Theta^T conversion jobs, one per (system, block)
+  void* dev_theta_first = nullptr;     // their first block in the grid
+  int ntheta = 0, theta_blocks = 0;
+};
+// Exchange over every (system, block) in the streamed form, each with its own walker tiling and
+// epilogue warpgroups (at most `groups`; 0: the system's own tuned count), in as few launches as keep
+// every problem's own ring depth: problems whose largest stage and epilogue buffers leave the same
+// number of stages share a launch (at most 8 launches).  The systems' own exchange forms are left as
+// they are.
+afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, GroupGemm* gg, char* err,
+                                 size_t errlen);
+afqmc_status group_vhs_plan(const GroupSystem* sys, int nsys, GroupGemm* gg, char* err, size_t errlen);
+// normals: the exchange launch also draws every system's normals of the current step counter.
+// s2 (optional): every second launch goes there (the caller orders s2 after s before the call and s
+// after s2 afterwards), so that one launch's last wave overlaps the next one's first.
+afqmc_status group_gemm(const GroupGemm& gg, cudaStream_t s, bool normals, unsigned long long* launches, char* err,
+                        size_t errlen, cudaStream_t s2 = nullptr);
+// The bf16 Theta^T operands of every (system, block) from Theta^T (when the copies are stale).
+afqmc_status group_theta(const GroupGemm& gg, cudaStream_t s, unsigned long long* launches, char* err,
+                         size_t errlen);
+void group_free(GroupGemm* gg);
+
+// The tensor-core propagation of several systems: the small-form systems (N <= 128) in one launch
+// over all their walkers (contiguous walker ranges per CTA, balanced by cost), the large-form ones
+// in one launch per product over all their (walker, row tile) pairs.  Every system takes the same
+// Taylor order.
+struct GroupPropSystem {
+  TcState* st;
+  char* tcbuf;
+  float2* psi;
+  const double* w;
+  int* status;
+};
+struct GroupProp {
+  int order = 0;
+  int nsmall = 0, small_grid = 0, small_off_bar = 0, small_tmem = 0;
+  size_t small_smem = 0;
+  void* dev_small = nullptr;   // small-form systems (device)
+  void* dev_cta = nullptr;     // first walker of each CTA (device, small_grid + 1)
+  int nlarge = 0, large_tiles = 0, large_grid = 0, large_stages = 0, large_stride = 0, large_tmem = 0,
+      large_acc = 0;
+  size_t large_smem = 0;
+  void* dev_large = nullptr;   // large-form systems (device)
+  void* dev_psib = nullptr;    // their first-operand jobs (device)
+};
+afqmc_status group_prop_plan(const GroupPropSystem* sys, int nsys, int order, GroupProp* gp, char* err,
+                             size_t errlen);
+// s2 (optional, ordered by the caller as for group_gemm): the large-form launches go there, beside
+// the small-form one.
+afqmc_status group_propagate(const GroupProp& gp, cudaStream_t s, unsigned long long* launches, char* err,
+                             size_t errlen, cudaStream_t s2 = nullptr);
+void group_prop_free(GroupProp* gp);
+
 }  // namespace tc
 }  // namespace afq

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "common.cuh"
 #include "tc_gemm.cuh"
@@ -353,6 +354,247 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------------------------
+// Grouped small form: one launch over the walkers of several systems (N <= 128).  CTA b takes the
+// walkers [cta_first[b], cta_first[b + 1]) of the launch's list (the systems in turn; contiguous
+// ranges balanced by cost on the host, so a CTA rarely changes system).  Each system keeps its own
+// shared-memory layout and operand width (CWP, dispatched per walker); the mbarriers sit past the
+// largest layout.  On a change of system the MMA thread first waits for the B operand of the new
+// walker, which the epilogue writes only after it has read the previous walker's last product, so
+// no copy into the new layout can meet a product still reading the old one; then it loads the new
+// system's F and the walker's V.  The next walker's V is prefetched only within a system.
+struct PropTcProblem {   // aligned as its tensor maps
+  CUtensorMap mapV, mapF;
+  PropTcParams p;
+  int cwp;
+  int item0;   // the system's walker 0 in the launch's list
+};
+
+template <int CWP>
+__device__ __forceinline__ bool prop_mma_item(uint8_t* sm, uint32_t tmem, const PropTcProblem& pr, int wk, int nxt,
+                                              bool fresh, uint64_t* bar_v, uint64_t* bar_f, uint64_t* bar_mma,
+                                              uint64_t* bar_b, volatile int* abort_flag, uint32_t& ph_b,
+                                              uint32_t& ph_v, uint32_t& ph_f) {
+  const PropTcParams a = pr.p;   // a register copy: the MMAs' asm would force reloads of a reference
+  const uint32_t s0 = smem_u32(sm);
+  const uint32_t vatom = (uint32_t)a.npad * 128u, batom = 4u * CWP * 128u;
+  const uint32_t idesc_w = idesc_bf16(4 * CWP), idesc_n = idesc_bf16(2 * CWP);
+  const uint64_t dvhi = sw128_desc(s0), dvlo = sw128_desc(s0 + (uint32_t)a.off_vlo);
+  const uint64_t dfhi = sw128_desc(s0 + (uint32_t)a.off_fhi), dflo = sw128_desc(s0 + (uint32_t)a.off_flo);
+  const uint64_t db = sw128_desc(s0 + (uint32_t)a.off_b);
+  auto issue_v = [&](int w) {
+    mbar_expect_tx(bar_v, 8u * vatom);
+    for (int pl = 0; pl < 4; ++pl)
+      for (int at = 0; at < 2; ++at) {
+        const uint32_t dst = (pl < 2 ? 0u : (uint32_t)a.off_vlo) + (uint32_t)((pl & 1) * 2 + at) * vatom;
+        tma_load_2d(sm + dst, &pr.mapV, bar_v, 64 * at, (w * 4 + pl) * a.npad);
+      }
+  };
+  auto product = [&](bool isv) {
+    const uint64_t ah = isv ? dvhi : dfhi, al = isv ? dvlo : dflo;
+    for (int h = 0; h < (isv ? 2 : 1); ++h) {
+      const uint32_t d = tmem + (uint32_t)(h * 4 * CWP);
+      for (int ks = 0; ks < a.nk; ++ks) {
+        const uint32_t ko = (uint32_t)(ks & 3) * 32u;
+        const uint64_t ao = ((uint32_t)(2 * h + (ks >> 2)) * vatom + ko) >> 4;
+        const uint64_t bo = ((uint32_t)(ks >> 2) * batom + ko) >> 4;
+        umma_bf16(d, ah + ao, db + bo, idesc_w, ks > 0 ? 1u : 0u);   // A hi [B hi; B lo]
+        umma_bf16(d, al + ao, db + bo, idesc_n, 1u);                 // A lo B hi
+      }
+    }
+    umma_commit(bar_mma);
+  };
+  for (int ch = 0; ch < a.nch; ++ch) {
+    if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
+    ph_b ^= 1u;
+    if (ch == 0 && fresh) {   // a new system: its F, then this walker's V
+      mbar_expect_tx(bar_f, 4u * vatom);
+      for (int pl = 0; pl < 2; ++pl)
+        for (int at = 0; at < 2; ++at)
+          tma_load_2d(sm + (pl ? a.off_flo : a.off_fhi) + at * vatom, &pr.mapF, bar_f, 64 * at, pl * a.npad);
+      issue_v(wk);
+      if (!mbar_wait(bar_f, ph_f, abort_flag)) return false;
+      ph_f ^= 1u;
+    }
+    tc_fence_after();
+    product(false);   // F psi
+    for (int k = 1; k <= a.order; ++k) {
+      if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
+      ph_b ^= 1u;
+      if (ch == 0 && k == 1) {
+        if (!mbar_wait(bar_v, ph_v, abort_flag)) return false;
+        ph_v ^= 1u;
+        if (nxt >= 0)
+          for (int pl = 0; pl < 4; ++pl)
+            for (int at = 0; at < 2; ++at) tma_prefetch_l2_2d(&pr.mapV, 64 * at, (nxt * 4 + pl) * a.npad);
+      }
+      tc_fence_after();
+      product(true);   // V t_{k-1} / k
+    }
+    if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
+    ph_b ^= 1u;
+    if (ch == a.nch - 1 && nxt >= 0) issue_v(nxt);   // every V product of this walker has completed
+    tc_fence_after();
+    product(false);   // F acc
+  }
+  return true;
+}
+
+template <int CWP>
+__device__ __forceinline__ bool prop_epi_item(uint8_t* sm, uint32_t tmem, const PropTcParams a, int wk, int warp,
+                                              int lane, uint64_t* bar_mma, uint64_t* bar_b, volatile int* abort_flag,
+                                              uint32_t& ph_m) {
+  constexpr int SW = CWP / 4;
+  const int quad = warp & 3, j0 = (warp >> 2) * SW;
+  const int p = 32 * quad + lane;
+  const bool row = p < a.N;
+  const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
+  uint8_t* bsm = sm + a.off_b;
+  float accr[SW], acci[SW], dr[SW], di[SW];
+  for (int ch = 0; ch < a.nch; ++ch) {
+    const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
+    float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol + c0;
+#pragma unroll
+    for (int jj = 0; jj < SW; ++jj) {
+      const float2 v = (row && j0 + jj < cwn) ? prow[j0 + jj] : make_float2(0.f, 0.f);
+      accr[jj] = dr[jj] = v.x;
+      acci[jj] = di[jj] = v.y;
+    }
+    write_b<CWP, SW>(bsm, p, j0, dr, di);
+    signal_b(bar_b, lane);
+    if (!warp_wait(bar_mma, ph_m, abort_flag, lane)) return false;
+    ph_m ^= 1u;
+    load_d<CWP, SW, false>(trow, j0, dr, di);   // F psi
+#pragma unroll
+    for (int jj = 0; jj < SW; ++jj) {   // t_0 = psi + F psi
+      accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
+      acci[jj] = row ? acci[jj] + di[jj] : 0.f;
+    }
+    write_b<CWP, SW>(bsm, p, j0, accr, acci);
+    signal_b(bar_b, lane);
+    for (int k = 1; k <= a.order; ++k) {
+      if (!warp_wait(bar_mma, ph_m, abort_flag, lane)) return false;
+      ph_m ^= 1u;
+      load_d<CWP, SW, true>(trow, j0, dr, di);   // t_k
+      const float s = 1.f / (float)(k + 1);
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) {
+        const float tr = row ? dr[jj] : 0.f, ti = row ? di[jj] : 0.f;
+        accr[jj] += tr;
+        acci[jj] += ti;
+        dr[jj] = tr * s;   // next operand t_k / (k + 1)
+        di[jj] = ti * s;
+      }
+      if (k < a.order) write_b<CWP, SW>(bsm, p, j0, dr, di);
+      else write_b<CWP, SW>(bsm, p, j0, accr, acci);
+      signal_b(bar_b, lane);
+    }
+    if (!warp_wait(bar_mma, ph_m, abort_flag, lane)) return false;
+    ph_m ^= 1u;
+    load_d<CWP, SW, false>(trow, j0, dr, di);   // F acc
+#pragma unroll
+    for (int jj = 0; jj < SW; ++jj)
+      if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc_group(const PropTcProblem* __restrict__ probs, int nprob,
+                                                                   const int* __restrict__ cta_first, int off_bar,
+                                                                   int tmem_cols) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + off_bar);
+  uint64_t* bar_v = bars;
+  uint64_t* bar_f = bars + 1;
+  uint64_t* bar_mma = bars + 2;
+  uint64_t* bar_b = bars + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(bar_v, 1);
+    mbar_init(bar_f, 1);
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_b, kEpiWarps);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kEpiWarps) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int i0 = cta_first[blockIdx.x], i1 = cta_first[blockIdx.x + 1];
+  auto system_of = [&](int i, int& cur) {
+    while (cur + 1 < nprob && i >= probs[cur + 1].item0) ++cur;
+    return cur;
+  };
+  auto live = [&](int i, int c) { return probs[c].p.w[i - probs[c].item0] != 0.0; };
+  auto give_up = [&]() {
+    for (int c = 0; c < nprob; ++c) atomicOr(probs[c].p.status, kStatusTimeout);
+    *abort_flag = 1;
+  };
+  if (warp == kEpiWarps) {
+    if (lane == 0) {   // TMA + MMA issue
+      uint32_t ph_b = 0, ph_v = 0, ph_f = 0;
+      int cur = 0, loaded = -1;
+      bool go = true;
+      for (int i = i0; i < i1 && go; ++i) {
+        const int c = system_of(i, cur);
+        if (!live(i, c)) continue;
+        const PropTcProblem& pr = probs[c];
+        const int end = min(i1, pr.item0 + pr.p.W);
+        int nxt = -1;   // the next live walker of this system in the CTA's range
+        for (int j = i + 1; j < end; ++j)
+          if (live(j, c)) { nxt = j - pr.item0; break; }
+        const bool fresh = c != loaded;
+        loaded = c;
+        const int wk = i - pr.item0;
+        switch (pr.cwp) {
+          case 8: go = prop_mma_item<8>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
+          case 16: go = prop_mma_item<16>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
+          case 24: go = prop_mma_item<24>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
+          default: go = prop_mma_item<32>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
+        }
+      }
+      if (!go) give_up();
+    }
+  } else {   // epilogue warps
+    uint32_t ph_m = 0;
+    int cur = 0;
+    bool go = true;
+    for (int i = i0; i < i1 && go; ++i) {
+      const int c = system_of(i, cur);
+      if (!live(i, c)) continue;
+      const PropTcProblem& pr = probs[c];
+      const int wk = i - pr.item0;
+      switch (pr.cwp) {
+        case 8: go = prop_epi_item<8>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
+        case 16: go = prop_epi_item<16>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
+        case 24: go = prop_epi_item<24>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
+        default: go = prop_epi_item<32>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
+      }
+    }
+    if (!go && lane == 0) give_up();
+  }
+  if (threadIdx.x == 0 && *abort_flag) {   // let in-flight copies and MMAs drain before freeing tensor memory
+    const unsigned long long t0 = global_ns();
+    while (global_ns() - t0 < 2000000ull) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kEpiWarps)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
 // Large form (N > 128): one launch per product over all (walker, 128-row tile) pairs.  A is the
 // walker's V (K = Re V | Im V) or F, streamed through a ring of TMA stages; B is the current term
 // as split bf16 [hi, lo][2 ncolp rows][2 kq] (rows: real parts, then imaginary parts; K halves as
@@ -393,24 +635,83 @@ __device__ __forceinline__ void prop_kblock(const PropGemmParams& a, int wk, int
   *ksteps = min(4, (a.N - qb * 64 + 15) / 16);
 }
 
-__global__ void __launch_bounds__(192, 1) k_prop_gemm(const __grid_constant__ CUtensorMap mapA,
-                                                      const __grid_constant__ CUtensorMap mapB,
-                                                      const PropGemmParams a) {
+// GROUP: one launch per product over the (walker, 128-row tile) pairs of several systems.  System i
+// owns tiles [tile0, tile0 + tiles) of the launch; its maps (V, F and both term operands) and
+// parameters are read from device memory, the product index comes from the launch, and the ring
+// of stages and the accumulators are laid out for the widest system.
+struct PropGemmProblem {   // aligned as its tensor maps
+  CUtensorMap mapV, mapF, mapB[2];
+  PropGemmParams p;            // p.mode is the launch's
+  __nv_bfloat16* b[2];         // term operands: product m reads b[m % 2], writes b[(m + 1) % 2]
+  int tile0, tiles;
+};
+struct PropGroupArgs {
+  const PropGemmProblem* probs;
+  int nprob, tiles, mode, stages, stride, tmem_cols, acc_stride;
+};
+
+template <bool GROUP>
+__global__ void __launch_bounds__(192, 1) k_prop_gemm_t(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapB,
+                                                        const __grid_constant__ PropGemmParams a0,
+                                                        const __grid_constant__ PropGroupArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const int stage_bytes = 16384 + a.bn * 128;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)a.stages * stage_bytes);
+  const int stages = GROUP ? ga.stages : a0.stages;
+  const int stride = GROUP ? ga.stride : 16384 + a0.bn * 128;
+  const uint32_t acc_stride = (uint32_t)(GROUP ? ga.acc_stride : a0.bn);
+  const int tiles = GROUP ? ga.tiles : a0.W * a0.mtiles;
+  const int tmem_cols = GROUP ? ga.tmem_cols
+                              : (2 * a0.bn <= 32 ? 32 : (2 * a0.bn <= 64 ? 64 : (2 * a0.bn <= 128 ? 128 : (2 * a0.bn <= 256 ? 256 : 512))));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * stride);
   uint64_t* full = bars;
-  uint64_t* empty = bars + a.stages;
-  uint64_t* tfull = bars + 2 * a.stages;
+  uint64_t* empty = bars + stages;
+  uint64_t* tfull = bars + 2 * stages;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles = a.W * a.mtiles, nkb = prop_kblocks(a);
-  const int tmem_cols = 2 * a.bn <= 32 ? 32 : (2 * a.bn <= 64 ? 64 : (2 * a.bn <= 128 ? 128 : (2 * a.bn <= 256 ? 256 : 512)));
+
+  // tile t: its system's parameters (with the launch's product) and maps, walker and row tile
+  struct Item {
+    PropGemmParams a;
+    const CUtensorMap* ma;
+    const CUtensorMap* mb;
+    int wk, mt;
+  };
+  auto resolve = [&](int t, int& cur) -> Item {
+    Item it;
+    if constexpr (GROUP) {
+      while (cur + 1 < ga.nprob && t >= ga.probs[cur + 1].tile0) ++cur;
+      const PropGemmProblem& pr = ga.probs[cur];
+      it.a = pr.p;
+      it.a.mode = ga.mode;
+      it.a.bnext = pr.b[(ga.mode + 1) % 2];
+      const bool fmode = ga.mode == 0 || ga.mode == it.a.order + 1;
+      it.ma = fmode ? &pr.mapF : &pr.mapV;
+      it.mb = &pr.mapB[ga.mode % 2];
+      t -= pr.tile0;
+    } else {
+      (void)cur;
+      it.a = a0;
+      it.ma = &mapA;
+      it.mb = &mapB;
+    }
+    it.wk = t / it.a.mtiles;
+    it.mt = t - it.wk * it.a.mtiles;
+    return it;
+  };
+  auto give_up = [&](int* status) {
+    if constexpr (GROUP) {
+      (void)status;
+      for (int i = 0; i < ga.nprob; ++i) atomicOr(ga.probs[i].p.status, kStatusTimeout);
+    } else {
+      atomicOr(status, kStatusTimeout);
+    }
+    *abort_flag = 1;
+  };
   if (threadIdx.x == 0) {
-    for (int s = 0; s < a.stages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -434,80 +735,89 @@ __global__ void __launch_bounds__(192, 1) k_prop_gemm(const __grid_constant__ CU
 
   if (warp == 0) {
     if (lane == 0) {   // TMA producer
-      int stage = 0;
+      int stage = 0, cur = 0;
       uint32_t ph = 0;
       bool go = true;
+      int* status = a0.status;
       for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
-        const int wk = t / a.mtiles, mt = t % a.mtiles;
-        if (a.w[wk] == 0.0) continue;
+        const Item it = resolve(t, cur);
+        const PropGemmParams& a = it.a;
+        status = a.status;
+        if (a.w[it.wk] == 0.0) continue;
+        const int nkb = prop_kblocks(a), bytes = 16384 + a.bn * 128;
         for (int j = 0; j < nkb; ++j) {
           int ax, ay, bx, by, ks;
-          prop_kblock(a, wk, mt, j, &ax, &ay, &bx, &by, &ks);
+          prop_kblock(a, it.wk, it.mt, j, &ax, &ay, &bx, &by, &ks);
           if (!mbar_wait(&empty[stage], ph ^ 1u, abort_flag)) { go = false; break; }
-          uint8_t* sa = smem + (size_t)stage * stage_bytes;
-          mbar_expect_tx(&full[stage], (uint32_t)stage_bytes);
-          tma_load_2d(sa, &mapA, &full[stage], ax, ay);
-          tma_load_2d(sa + 16384, &mapB, &full[stage], bx, by);
-          if (++stage == a.stages) { stage = 0; ph ^= 1u; }
+          uint8_t* sa = smem + (size_t)stage * stride;
+          mbar_expect_tx(&full[stage], (uint32_t)bytes);
+          tma_load_2d(sa, it.ma, &full[stage], ax, ay);
+          tma_load_2d(sa + 16384, it.mb, &full[stage], bx, by);
+          if (++stage == stages) { stage = 0; ph ^= 1u; }
         }
       }
-      if (!go) { atomicOr(a.status, kStatusTimeout); *abort_flag = 1; }
+      if (!go) give_up(status);
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
-      int stage = 0;
+      int stage = 0, n_it = 0, cur = 0;
       uint32_t ph = 0;
-      int it = 0;
       bool go = true;
-      const uint32_t idesc = idesc_bf16(a.bn);
+      int* status = a0.status;
       for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
-        const int wk = t / a.mtiles;
-        if (a.w[wk] == 0.0) continue;
-        const int acc = it & 1;
-        const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-        ++it;
+        const Item it = resolve(t, cur);
+        const PropGemmParams& a = it.a;
+        status = a.status;
+        if (a.w[it.wk] == 0.0) continue;
+        const uint32_t idesc = idesc_bf16(a.bn);
+        const int nkb = prop_kblocks(a);
+        const int acc = n_it & 1;
+        const uint32_t aph = (uint32_t)(n_it >> 1) & 1u;
+        ++n_it;
         if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { go = false; break; }
         tc_fence_after();
-        const uint32_t dtm = tmem + (uint32_t)(acc * a.bn);
+        const uint32_t dtm = tmem + (uint32_t)acc * acc_stride;
         bool first = true;
         for (int j = 0; j < nkb; ++j) {
           int ax, ay, bx, by, ks;
-          prop_kblock(a, wk, t % a.mtiles, j, &ax, &ay, &bx, &by, &ks);
+          prop_kblock(a, it.wk, it.mt, j, &ax, &ay, &bx, &by, &ks);
           if (!mbar_wait(&full[stage], ph, abort_flag)) { go = false; break; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + (size_t)stage * stage_bytes), sb = sa + 16384;
+          const uint32_t sa = smem_u32(smem + (size_t)stage * stride), sb = sa + 16384;
           for (int k = 0; k < ks; ++k) {
             umma_bf16(dtm, sw128_desc(sa + 32 * k), sw128_desc(sb + 32 * k), idesc, first ? 0u : 1u);
             first = false;
           }
           umma_commit(&empty[stage]);
-          if (++stage == a.stages) { stage = 0; ph ^= 1u; }
+          if (++stage == stages) { stage = 0; ph ^= 1u; }
         }
         if (!go) break;
         umma_commit(&tfull[acc]);
       }
-      if (!go) { atomicOr(a.status, kStatusTimeout); *abort_flag = 1; }
+      if (!go) give_up(status);
     }
   } else {   // epilogue: warps 2-5, lane quadrant warp % 4
     const int q = warp & 3;
-    int it = 0;
-    const float s = (a.mode >= 1 && a.mode < a.order) ? 1.f / (float)(a.mode + 1) : 1.f;
-    const size_t kk2 = (size_t)2 * a.kq;
+    int n_it = 0, cur = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-      const int wk = t / a.mtiles, mt = t % a.mtiles;
+      const Item it = resolve(t, cur);
+      const PropGemmParams& a = it.a;
+      const int wk = it.wk, mt = it.mt;
       if (a.w[wk] == 0.0) continue;
-      const int acc = it & 1;
-      const uint32_t aph = (uint32_t)(it >> 1) & 1u;
-      ++it;
+      const float s = (a.mode >= 1 && a.mode < a.order) ? 1.f / (float)(a.mode + 1) : 1.f;
+      const size_t kk2 = (size_t)2 * a.kq;
+      const int acc = n_it & 1;
+      const uint32_t aph = (uint32_t)(n_it >> 1) & 1u;
+      ++n_it;
       int ok = 0;
       if (lane == 0) ok = mbar_wait(&tfull[acc], aph, abort_flag) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) {
-        if (lane == 0) { atomicOr(a.status, kStatusTimeout); *abort_flag = 1; }
+        if (lane == 0) give_up(a.status);
         break;
       }
       tc_fence_after();
-      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * a.bn);
+      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)acc * acc_stride;
       const int p = mt * 128 + 32 * q + lane;
       const bool row = p < a.N, kpad = p < a.kq;
       float2* accrow = a.acc + ((size_t)wk * a.npad + (row ? p : 0)) * a.ncolp;
@@ -578,36 +888,48 @@ __global__ void __launch_bounds__(192, 1) k_prop_gemm(const __grid_constant__ CU
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+
 // First operand of the large form: psi of every walker as split bf16 rows (real parts, then
 // imaginary parts) over the first K half; K positions N .. kq - 1 and padding columns are zero.
-__global__ void k_psi_to_b(int W, int N, int ncol, int ncolp, int kq, const float2* psi, __nv_bfloat16* b,
-                           int both) {
-  const int bn = 2 * ncolp;
-  const size_t kk2 = (size_t)2 * kq;
-  const size_t total = (size_t)W * ncolp * kq;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(idx % kq);
-    const size_t r = idx / kq;
-    const int c = (int)(r % ncolp);
-    const int wk = (int)(r / ncolp);
+struct PsiToB {
+  int W, N, ncol, ncolp, kq, both;
+  const float2* psi;
+  __nv_bfloat16* b;
+};
+__device__ __forceinline__ void psi_to_b(const PsiToB& a, size_t first, size_t step) {
+  const size_t kk2 = (size_t)2 * a.kq;
+  const int bn = 2 * a.ncolp;
+  const size_t total = (size_t)a.W * a.ncolp * a.kq;
+  for (size_t idx = first; idx < total; idx += step) {
+    const int p = (int)(idx % a.kq);
+    const size_t r = idx / a.kq;
+    const int c = (int)(r % a.ncolp);
+    const int wk = (int)(r / a.ncolp);
     float2 v = make_float2(0.f, 0.f);
-    if (p < N && c < ncol) v = psi[((size_t)wk * N + p) * ncol + c];
+    if (p < a.N && c < a.ncol) v = a.psi[((size_t)wk * a.N + p) * a.ncol + c];
     const __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-    __nv_bfloat16* bw = b + (size_t)wk * 2 * bn * kk2;
-    const size_t lo = (size_t)bn * kk2;
     const __nv_bfloat16 rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
     const __nv_bfloat16 il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+    __nv_bfloat16* bw = a.b + (size_t)wk * 2 * bn * kk2;
+    const size_t lo = (size_t)bn * kk2;
     bw[(size_t)c * kk2 + p] = rh;
     bw[lo + (size_t)c * kk2 + p] = rl;
-    bw[(size_t)(ncolp + c) * kk2 + p] = ih;
-    bw[lo + (size_t)(ncolp + c) * kk2 + p] = il;
-    if (both) {   // the second K half for a complex first product: rows [Re | -Im] and [Im | Re]
-      bw[(size_t)c * kk2 + kq + p] = __hneg(ih);
-      bw[lo + (size_t)c * kk2 + kq + p] = __hneg(il);
-      bw[(size_t)(ncolp + c) * kk2 + kq + p] = rh;
-      bw[lo + (size_t)(ncolp + c) * kk2 + kq + p] = rl;
+    bw[(size_t)(a.ncolp + c) * kk2 + p] = ih;
+    bw[lo + (size_t)(a.ncolp + c) * kk2 + p] = il;
+    if (a.both) {   // the second K half for a complex first product: rows [Re | -Im] and [Im | Re]
+      bw[(size_t)c * kk2 + a.kq + p] = __hneg(ih);
+      bw[lo + (size_t)c * kk2 + a.kq + p] = __hneg(il);
+      bw[(size_t)(a.ncolp + c) * kk2 + a.kq + p] = rh;
+      bw[lo + (size_t)(a.ncolp + c) * kk2 + a.kq + p] = rl;
     }
   }
+}
+__global__ void k_psi_to_b(PsiToB a) {
+  psi_to_b(a, blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+// Several systems at once: blockIdx.y is the system.
+__global__ void k_psi_to_b_group(const PsiToB* __restrict__ jobs) {
+  psi_to_b(jobs[blockIdx.y], blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 // F = E_h - I (binary64 [N][N]) -> planes [hi, lo][npad][kq], zero outside N x N.  Complex F
@@ -715,7 +1037,10 @@ afqmc_status prepare_prop(TcState* st, cudaStream_t s, char* tcbuf, const double
         return AFQMC_ECUDA;
       }
     }
-    if (cudaFuncSetAttribute(k_prop_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_prop_gemm_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_prop_gemm_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+            cudaSuccess) {
       snprintf(err, errlen, "tensor-core propagation: cannot reserve shared memory");
       return AFQMC_ECUDA;
     }
@@ -746,7 +1071,7 @@ afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, floa
   if (g.large) {
     __nv_bfloat16* b[2] = {reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_b[0]),
                            reinterpret_cast<__nv_bfloat16*>(tcbuf + st->off_b[1])};
-    k_psi_to_b<<<1184, 256, 0, s>>>(st->W, st->N, st->ncol, g.ncolp, g.kq, psi, b[0], g.cplx_f);
+    k_psi_to_b<<<1184, 256, 0, s>>>(PsiToB{st->W, st->N, st->ncol, g.ncolp, g.kq, g.cplx_f, psi, b[0]});
     ++*launches;
     PropGemmParams q{};
     q.cplx_f = g.cplx_f;
@@ -760,7 +1085,8 @@ afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, floa
       q.mode = m;
       q.bnext = b[(m + 1) % 2];
       const bool fmode = m == 0 || m == order + 1;
-      k_prop_gemm<<<grid, 192, smem, s>>>(fmode ? st->map_fp : st->map_vp, st->map_b[m % 2], q);
+      k_prop_gemm_t<false><<<grid, 192, smem, s>>>(fmode ? st->map_fp : st->map_vp, st->map_b[m % 2], q,
+                                                   PropGroupArgs{});
       ++*launches;
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
@@ -785,6 +1111,188 @@ afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, floa
     case 24: return launch_prop<24>(st, s, p, launches, err, errlen);
     default: return launch_prop<32>(st, s, p, launches, err, errlen);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Grouped propagation of several systems: the small-form systems in one k_prop_tc_group launch, the
+// large-form systems in one k_prop_gemm_t<true> launch per product.
+namespace {
+template <typename T>
+afqmc_status to_device_p(const std::vector<T>& v, void** dev, char* err, size_t errlen) {
+  *dev = nullptr;
+  if (v.empty()) return AFQMC_OK;
+  if (cudaMalloc(dev, v.size() * sizeof(T)) != cudaSuccess ||
+      cudaMemcpy(*dev, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    snprintf(err, errlen, "grouped propagation: device descriptors (%zu bytes)", v.size() * sizeof(T));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+int tmem_pow2(int cols) {
+  int c = 32;
+  while (c < cols) c <<= 1;
+  return c;
+}
+}  // namespace
+
+afqmc_status group_prop_plan(const GroupPropSystem* sys, int nsys, int order, GroupProp* gp, char* err,
+                             size_t errlen) {
+  *gp = GroupProp{};
+  gp->order = order;
+  std::vector<PropTcProblem> small;
+  std::vector<double> cost;   // per small-form walker
+  std::vector<PropGemmProblem> large;
+  std::vector<PsiToB> psib;
+  int items = 0, off_bar = 0, tcols = 32;
+  for (int i = 0; i < nsys; ++i) {
+    TcState* st = sys[i].st;
+    const PropGeom& g = st->pg;
+    if (!g.ok) {
+      snprintf(err, errlen, "grouped propagation: system %d has no tensor-core propagation", i);
+      return AFQMC_EINVAL;
+    }
+    if (!g.large) {
+      PropTcProblem q{};
+      q.mapV = st->map_vp;
+      q.mapF = st->map_fp;
+      PropTcParams& p = q.p;
+      p.N = st->N; p.npad = g.npad; p.nk = g.nk; p.ncol = st->ncol; p.cw = g.cw; p.nch = g.nch;
+      p.order = order; p.W = st->W;
+      p.off_vlo = g.off_vlo; p.off_fhi = g.off_fhi; p.off_flo = g.off_flo; p.off_b = g.off_b; p.off_bar = g.off_bar;
+      p.tmem_cols = 8 * g.cwp <= 64 ? 64 : (8 * g.cwp <= 128 ? 128 : 256);
+      p.psi = sys[i].psi;
+      p.w = sys[i].w;
+      p.status = sys[i].status;
+      q.cwp = g.cwp;
+      q.item0 = items;
+      items += st->W;
+      off_bar = std::max(off_bar, g.off_bar);
+      tcols = std::max(tcols, p.tmem_cols);
+      // cost of a walker: per chunk, order + 2 chained products (hand-off ~3k cycles each) and their MMAs
+      const double c = (double)g.nch * ((order + 2) * 3000.0 + 55.0 * g.nk * (4.0 + 4.0 * order));
+      for (int w = 0; w < st->W; ++w) cost.push_back(c);
+      small.push_back(q);
+    } else {
+      PropGemmProblem q{};
+      q.mapV = st->map_vp;
+      q.mapF = st->map_fp;
+      q.mapB[0] = st->map_b[0];
+      q.mapB[1] = st->map_b[1];
+      PropGemmParams& p = q.p;
+      p.cplx_f = g.cplx_f;
+      p.N = st->N; p.npad = g.npad; p.kq = g.kq; p.nq = g.kq / 64; p.ncol = st->ncol; p.ncolp = g.ncolp;
+      p.bn = 2 * g.ncolp; p.mtiles = g.mtiles; p.W = st->W; p.order = order;
+      p.stages = prop_gemm_stages(p.bn);
+      p.psi = sys[i].psi; p.w = sys[i].w; p.status = sys[i].status;
+      p.acc = reinterpret_cast<float2*>(sys[i].tcbuf + st->off_acc);
+      for (int k = 0; k < 2; ++k) q.b[k] = reinterpret_cast<__nv_bfloat16*>(sys[i].tcbuf + st->off_b[k]);
+      large.push_back(q);
+      psib.push_back(PsiToB{st->W, st->N, st->ncol, g.ncolp, g.kq, g.cplx_f, sys[i].psi, q.b[0]});
+    }
+  }
+  afqmc_status r;
+  if (!small.empty()) {
+    // contiguous walker ranges of about equal cost, one per CTA
+    const int grid = std::min(items, num_sms());
+    double total = 0.0;
+    for (double c : cost) total += c;
+    std::vector<int> first(grid + 1, items);
+    first[0] = 0;
+    double acc = 0.0;
+    int b = 1;
+    for (int it = 0; it < items && b < grid; ++it) {
+      acc += cost[it];
+      if (acc >= total * b / grid) first[b++] = it + 1;
+    }
+    for (; b < grid; ++b) first[b] = items;
+    gp->nsmall = (int)small.size();
+    gp->small_grid = grid;
+    gp->small_off_bar = off_bar;
+    gp->small_tmem = tcols;
+    gp->small_smem = 1024 + (size_t)off_bar + 64;
+    if (cudaFuncSetAttribute(k_prop_tc_group, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+      snprintf(err, errlen, "grouped propagation: cannot reserve shared memory");
+      return AFQMC_ECUDA;
+    }
+    if ((r = to_device_p(small, &gp->dev_small, err, errlen)) != AFQMC_OK ||
+        (r = to_device_p(first, &gp->dev_cta, err, errlen)) != AFQMC_OK) {
+      group_prop_free(gp);
+      return r;
+    }
+  }
+  if (!large.empty()) {
+    std::stable_sort(large.begin(), large.end(), [](const PropGemmProblem& a, const PropGemmProblem& b) {
+      return (long long)a.p.nq * a.p.bn > (long long)b.p.nq * b.p.bn;
+    });
+    int t = 0, bn = 0;
+    for (auto& q : large) {
+      q.tile0 = t;
+      q.tiles = q.p.W * q.p.mtiles;
+      t += q.tiles;
+      bn = std::max(bn, q.p.bn);
+    }
+    gp->nlarge = (int)large.size();
+    gp->large_tiles = t;
+    gp->large_grid = std::min(t, num_sms());
+    gp->large_stages = prop_gemm_stages(bn);
+    gp->large_stride = 16384 + bn * 128;
+    gp->large_acc = bn;
+    gp->large_tmem = tmem_pow2(2 * bn);
+    gp->large_smem = prop_gemm_smem(bn);
+    if (gp->large_stages < 2 || gp->large_tmem > 512) {
+      snprintf(err, errlen, "grouped propagation: no layout fits the widest system");
+      group_prop_free(gp);
+      return AFQMC_EINVAL;
+    }
+    if ((r = to_device_p(large, &gp->dev_large, err, errlen)) != AFQMC_OK ||
+        (r = to_device_p(psib, &gp->dev_psib, err, errlen)) != AFQMC_OK) {
+      group_prop_free(gp);
+      return r;
+    }
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status group_propagate(const GroupProp& gp, cudaStream_t s, unsigned long long* launches, char* err,
+                             size_t errlen, cudaStream_t s2) {
+  const cudaStream_t sl = s2 ? s2 : s;   // the large-form launches
+  if (gp.nsmall) {
+    k_prop_tc_group<<<gp.small_grid, kPropThreads, gp.small_smem, s>>>(
+        static_cast<const PropTcProblem*>(gp.dev_small), gp.nsmall, static_cast<const int*>(gp.dev_cta),
+        gp.small_off_bar, gp.small_tmem);
+    ++*launches;
+  }
+  if (gp.nlarge) {
+    k_psi_to_b_group<<<dim3(296, gp.nlarge), 256, 0, sl>>>(static_cast<const PsiToB*>(gp.dev_psib));
+    ++*launches;
+    PropGroupArgs ga{};
+    ga.probs = static_cast<const PropGemmProblem*>(gp.dev_large);
+    ga.nprob = gp.nlarge;
+    ga.tiles = gp.large_tiles;
+    ga.stages = gp.large_stages;
+    ga.stride = gp.large_stride;
+    ga.tmem_cols = gp.large_tmem;
+    ga.acc_stride = gp.large_acc;
+    const CUtensorMap none{};
+    const PropGemmParams p0{};
+    for (int m = 0; m <= gp.order + 1; ++m) {   // operand m % 2 in, (m + 1) % 2 out
+      ga.mode = m;
+      k_prop_gemm_t<true><<<gp.large_grid, 192, gp.large_smem, sl>>>(none, none, p0, ga);
+      ++*launches;
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(err, errlen, "grouped propagation launch: %s", cudaGetErrorString(e));
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
+void group_prop_free(GroupProp* gp) {
+  for (void* p : {gp->dev_small, gp->dev_cta, gp->dev_large, gp->dev_psib})
+    if (p) cudaFree(p);
+  gp->dev_small = gp->dev_cta = gp->dev_large = gp->dev_psib = nullptr;
 }
 
 }  // namespace tc

@@ -44,7 +44,7 @@ def test_batch_reproduces_individual_runs(prec):
         solo.append((c.run(13, 2, 5, 10), c.get_walkers()))
         c.close()
     ctxs = [_ctx(p, nw, prec, sd) for p, sd in zip(probs, seeds)]
-    b = Batch(ctxs)
+    b = Batch(ctxs, mode="graphs")   # the systems' own step graphs: bit for bit the solo runs
     e = b.run(13, energy_every=2, reortho_every=5, comb_every=10)
     assert e.shape == (4, 7, 4)
     for i, c in enumerate(ctxs):

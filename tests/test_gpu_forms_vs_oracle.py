@@ -73,15 +73,17 @@ def _batch_problems():
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_uneven_batch_tracks_the_oracle(prec):
-    """One graph launch per step over three uneven systems (N = 30, 90, 210): each system's mixed energy
-    over 6 steps (QR every 5, no comb) against the oracle's trajectory on the same fields."""
+    """One graph launch per step over three uneven systems (N = 30, 90, 210; BF16x3: one launch per
+    stage over all three, N = 210 in the large propagation form): each system's mixed energy over 6
+    steps (QR every 5, no comb) against the oracle's trajectory on the same fields."""
     from paper_2406_16238_b300._lib import Batch
     probs = _batch_problems()
     nw, nsteps = 8, 6
     seeds = [71, 72, 73]
     ctxs = [pkg.Afqmc(p.h1e, p.chol, p.ecore, p.nalpha, p.nbeta, p.psiT, nwalkers=nw, dt=0.005, seed=s, prec=prec)
             for p, s in zip(probs, seeds)]
-    b = Batch(ctxs)
+    b = Batch(ctxs, mode="graphs" if prec == "fp32" else "grouped")   # tensor-core forms: grouped launches
+    assert b.mode() == ("graphs" if prec == "fp32" else "grouped")
     e = b.run(nsteps, energy_every=1, reortho_every=5, comb_every=0)
     b.close()
     for c in ctxs:
