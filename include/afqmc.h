@@ -299,8 +299,10 @@ afqmc_status afqmc_set_tuning(afqmc_ctx* ctx, const afqmc_tuning* t);
  *     launch per Taylor product over every (walker, row tile) of the N > 128 systems; the overlap,
  *     fields, energy, QR and comb kernels as one launch over every walker.  Needs every context in
  *     the same tensor-core form (BF16 / BF16X3), real, phaseless, with the tensor-core propagation
- *     and the same Taylor order.  exch_groups caps the exchange's epilogue warpgroups (0: the most
- *     that fit every system).  The descriptors (a few KB of device memory) are allocated on the
+ *     and the same Taylor order.  exch_groups caps the exchange's epilogue warpgroups (0: each
+ *     system's own tuned count).  branches (0: 2, at most 4): the systems split into that many
+ *     branches of about equal work, whose grouped launches run side by side on as many streams (one
+ *     launch per stage and branch), so one branch's last wave overlaps another's work.  The descriptors (a few KB of device memory) are allocated on the
  *     first grouped run, not inside the caller's workspaces.
  *   AFQMC_BATCH_GRAPHS: one graph launch whose branches are the systems' own step graphs (any form).
  *   AFQMC_BATCH_AUTO (default): grouped where the contexts allow it, else graphs.
@@ -315,7 +317,7 @@ typedef struct afqmc_batch afqmc_batch;
 afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batch** out);
 afqmc_status afqmc_batch_run(afqmc_batch* b, int32_t nsteps, int32_t energy_every, int32_t reortho_every,
                              int32_t comb_every, double* energies, int32_t* nmeas);
-afqmc_status afqmc_batch_set_mode(afqmc_batch* b, int32_t mode, int32_t exch_groups);
+afqmc_status afqmc_batch_set_mode(afqmc_batch* b, int32_t mode, int32_t exch_groups, int32_t branches);
 /* The form the next afqmc_batch_run takes (AFQMC_BATCH_GROUPED or AFQMC_BATCH_GRAPHS). */
 afqmc_status afqmc_batch_get_mode(afqmc_batch* b, int32_t* mode);
 /* Stage tracing of the grouped form: with enable = 1 (counters cleared) afqmc_batch_run launches each

@@ -90,7 +90,7 @@ SIGNATURES = {
     "afqmc_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "afqmc_batch_run": (_i32, [_vp, _i32, _i32, _i32, _i32, _dp, ctypes.POINTER(_i32)]),
     "afqmc_batch_destroy": (None, [_vp]),
-    "afqmc_batch_set_mode": (_i32, [_vp, _i32, _i32]),
+    "afqmc_batch_set_mode": (_i32, [_vp, _i32, _i32, _i32]),
     "afqmc_batch_get_mode": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "afqmc_batch_profile": (_i32, [_vp, _i32]),
     "afqmc_batch_describe": (_i32, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -525,19 +525,19 @@ class Batch:
     mode "grouped" (one launch per stage over every system), "graphs" (one child graph per system)
     or "auto" (grouped where the contexts allow it)."""
 
-    def __init__(self, contexts, mode="auto", exch_groups=0):
+    def __init__(self, contexts, mode="auto", exch_groups=0, branches=0):
         self._lib = load()
         self.contexts = list(contexts)
         arr = (ctypes.c_void_p * len(self.contexts))(*[c._ctx.value for c in self.contexts])
         b = ctypes.c_void_p()
         _check(self._lib.afqmc_batch_create(len(self.contexts), arr, ctypes.byref(b)))
         self._b = b
-        self.set_mode(mode, exch_groups)
+        self.set_mode(mode, exch_groups, branches)
 
-    def set_mode(self, mode="auto", exch_groups=0):
+    def set_mode(self, mode="auto", exch_groups=0, branches=0):
         if mode not in BATCH_MODES:
             raise ValueError(f"mode must be one of {sorted(BATCH_MODES)}")
-        _check(self._lib.afqmc_batch_set_mode(self._b, BATCH_MODES[mode], int(exch_groups)))
+        _check(self._lib.afqmc_batch_set_mode(self._b, BATCH_MODES[mode], int(exch_groups), int(branches)))
 
     def profile(self, enable=True):
         _check(self._lib.afqmc_batch_profile(self._b, 1 if enable else 0))

@@ -2166,16 +2166,22 @@ struct afqmc_batch {
   // the work of every system, the step captured as one graph per step kind.
   int mode = AFQMC_BATCH_AUTO;
   int exch_groups = 0;          // epilogue warpgroups of the grouped exchange (0: the most that fit)
+  int nbranch_req = 0;          // branches of the grouped step (0: two where there are two systems)
   bool g_ready = false;
-  afq::tc::GroupGemm g_exch, g_vhs;
-  afq::tc::GroupProp g_prop;
+  struct Branch {               // the systems of one branch and their grouped launches
+    std::vector<int> sys;       // indices into the batch's contexts
+    afq::tc::GroupGemm exch, vhs;
+    afq::tc::GroupProp prop;
+    void *a_first = nullptr, *a_energy = nullptr, *a_fields = nullptr, *a_overlap = nullptr, *a_stage = nullptr,
+         *a_qr = nullptr, *a_comb = nullptr, *a_zero = nullptr;
+    int total_w = 0;
+    size_t ovl_smem = 0, qr_smem = 0, max_vbias = 0;
+  };
+  std::vector<Branch> br;
   std::vector<void*> g_dev;     // device argument arrays of the grouped per-walker kernels
-  void *a_first = nullptr, *a_energy = nullptr, *a_fields = nullptr, *a_overlap = nullptr, *a_stage = nullptr,
-       *a_qr = nullptr, *a_comb = nullptr, *a_zero = nullptr;
-  int total_w = 0, max_w = 0;
-  size_t ovl_smem = 0, qr_smem = 0, max_vbias = 0;
-  cudaStream_t s2 = nullptr;            // second stream of the grouped step's forks
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  static constexpr int kMaxBranches = 4;
+  cudaStream_t bs[kMaxBranches - 1] = {};   // further streams of the grouped step's forks
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxBranches - 1] = {};
   struct GExec {
     cudaGraphExec_t exec = nullptr;
     unsigned long long nk = 0;
@@ -2203,9 +2209,12 @@ struct afqmc_batch {
     for (auto& kv : gcache)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     gcache.clear();
-    afq::tc::group_free(&g_exch);
-    afq::tc::group_free(&g_vhs);
-    afq::tc::group_prop_free(&g_prop);
+    for (auto& x : br) {
+      afq::tc::group_free(&x.exch);
+      afq::tc::group_free(&x.vhs);
+      afq::tc::group_prop_free(&x.prop);
+    }
+    br.clear();
     for (void* d : g_dev) cudaFree(d);
     g_dev.clear();
     g_ready = false;
@@ -2218,9 +2227,11 @@ struct afqmc_batch {
   }
   ~afqmc_batch() {
     drop_all();
-    if (s2) cudaStreamDestroy(s2);
+    for (auto x : bs)
+      if (x) cudaStreamDestroy(x);
     if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
+    for (auto e : ev_join)
+      if (e) cudaEventDestroy(e);
     for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
     for (auto e : free_events) cudaEventDestroy(e);
   }
@@ -2258,12 +2269,11 @@ afqmc_status upload(afqmc_batch* b, const std::vector<T>& v, void** dev) {
   return AFQMC_OK;
 }
 
-// The grouped launches' descriptors: the tcgen05 problems (exchange, VHS, propagation) and the
+// The grouped launches of one branch: the tcgen05 problems (exchange, VHS, propagation) and the
 // argument arrays of the per-walker kernels, in device memory.
-afqmc_status batch_grouped_plan(afqmc_batch* b) {
+afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
   using R = float;
-  b->drop_grouped();
-  const int nsys = (int)b->sys.size();
+  const int nsys = (int)x.sys.size();
   std::vector<tc::GroupSystem> gs(nsys);
   std::vector<tc::GroupPropSystem> ps(nsys);
   std::vector<EnergyArgs<R>> ea(nsys);
@@ -2273,10 +2283,8 @@ afqmc_status batch_grouped_plan(afqmc_batch* b) {
   std::vector<CombArgs<R>> ca(nsys);
   std::vector<ZeroArgs> za(nsys);
   std::vector<int> stage(nsys), first(nsys + 1, 0);
-  b->ovl_smem = b->qr_smem = b->max_vbias = 0;
-  b->max_w = 0;
   for (int i = 0; i < nsys; ++i) {
-    afqmc_ctx* c = b->sys[i];
+    afqmc_ctx* c = b->sys[x.sys[i]];
     const Dims& d = c->d;
     char* tcbuf = c->at<char>(c->L.tc);
     int* status = c->at<int>(c->L.status);
@@ -2289,56 +2297,92 @@ afqmc_status batch_grouped_plan(afqmc_batch* b) {
     fa[i] = field_args<R>(c);
     oa[i] = overlap_args<R>(c, 1);
     stage[i] = overlap_stage(d) ? 1 : 0;
-    b->ovl_smem = std::max(b->ovl_smem, overlap_smem(d));
+    x.ovl_smem = std::max(x.ovl_smem, overlap_smem(d));
     qa[i] = qr_args<R>(c);
-    b->qr_smem = std::max(b->qr_smem, qr_smem(d));
+    x.qr_smem = std::max(x.qr_smem, qr_smem(d));
     ca[i] = CombArgs<R>{d.W, d.N * d.ncol, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.cum),
                         c->at<int>(c->L.src), c->at<double>(c->L.neww), status, c->at<float2>(c->L.psi),
                         c->at<float2>(c->L.psi_tmp), c->at<float2>(c->L.thetaT), c->at<float2>(c->L.th_tmp),
                         c->at<double2>(c->L.logO), c->at<double2>(c->L.logO_tmp), c->at<double>(c->L.w),
                         c->at<double>(c->L.w_tmp)};
     za[i] = ZeroArgs{c->at<float2>(c->L.vbias), (size_t)d.W * d.X};
-    b->max_vbias = std::max(b->max_vbias, (size_t)d.W * d.X);
-    b->max_w = std::max(b->max_w, d.W);
+    x.max_vbias = std::max(x.max_vbias, (size_t)d.W * d.X);
     first[i + 1] = first[i] + d.W;
   }
-  b->total_w = first[nsys];
+  x.total_w = first[nsys];
   afqmc_status st;
-  if ((st = tc::group_exchange_plan(gs.data(), nsys, b->exch_groups, &b->g_exch, g_err, sizeof(g_err))) != AFQMC_OK ||
-      (st = tc::group_vhs_plan(gs.data(), nsys, &b->g_vhs, g_err, sizeof(g_err))) != AFQMC_OK ||
-      (st = tc::group_prop_plan(ps.data(), nsys, b->sys[0]->taylor, &b->g_prop, g_err, sizeof(g_err))) != AFQMC_OK) {
-    b->drop_grouped();
+  if ((st = tc::group_exchange_plan(gs.data(), nsys, b->exch_groups, &x.exch, g_err, sizeof(g_err))) != AFQMC_OK ||
+      (st = tc::group_vhs_plan(gs.data(), nsys, &x.vhs, g_err, sizeof(g_err))) != AFQMC_OK ||
+      (st = tc::group_prop_plan(ps.data(), nsys, b->sys[0]->taylor, &x.prop, g_err, sizeof(g_err))) != AFQMC_OK)
     return st;
-  }
-  if ((st = upload(b, first, &b->a_first)) != AFQMC_OK || (st = upload(b, ea, &b->a_energy)) != AFQMC_OK ||
-      (st = upload(b, fa, &b->a_fields)) != AFQMC_OK || (st = upload(b, oa, &b->a_overlap)) != AFQMC_OK ||
-      (st = upload(b, stage, &b->a_stage)) != AFQMC_OK || (st = upload(b, qa, &b->a_qr)) != AFQMC_OK ||
-      (st = upload(b, ca, &b->a_comb)) != AFQMC_OK || (st = upload(b, za, &b->a_zero)) != AFQMC_OK) {
-    b->drop_grouped();
+  if ((st = upload(b, first, &x.a_first)) != AFQMC_OK || (st = upload(b, ea, &x.a_energy)) != AFQMC_OK ||
+      (st = upload(b, fa, &x.a_fields)) != AFQMC_OK || (st = upload(b, oa, &x.a_overlap)) != AFQMC_OK ||
+      (st = upload(b, stage, &x.a_stage)) != AFQMC_OK || (st = upload(b, qa, &x.a_qr)) != AFQMC_OK ||
+      (st = upload(b, ca, &x.a_comb)) != AFQMC_OK || (st = upload(b, za, &x.a_zero)) != AFQMC_OK)
     return st;
+  return AFQMC_OK;
+}
+
+// The systems split into branches of about equal work (the exchange, VHS and propagation flops; the
+// largest first, each to the lightest branch), each branch planned on its own.
+afqmc_status batch_grouped_plan(afqmc_batch* b) {
+  using R = float;
+  b->drop_grouped();
+  const int nsys = (int)b->sys.size();
+  const int nb = std::max(1, std::min(nsys, b->nbranch_req > 0 ? b->nbranch_req : 2));
+  std::vector<double> cost(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    const afqmc_ctx* c = b->sys[i];
+    const Dims& d = c->d;
+    double n2 = 0.0;
+    for (int k = 0; k < d.nblk; ++k) n2 += (double)d.nbk[k] * d.nbk[k];
+    cost[i] = 4.0 * n2 * d.N * d.X * d.W + 4.0 * d.X * (double)d.N * d.N * d.W +
+              8.0 * (c->taylor + 2) * (double)d.N * d.N * d.ncol * d.W;
   }
+  std::vector<int> order(nsys);
+  for (int i = 0; i < nsys; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  b->br.assign(nb, afqmc_batch::Branch{});
+  std::vector<double> load(nb, 0.0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->br[k].sys.push_back(i);
+    load[k] += cost[i];
+  }
+  for (auto& x : b->br) std::sort(x.sys.begin(), x.sys.end());
+  afqmc_status st;
+  for (auto& x : b->br)
+    if ((st = branch_plan(b, x)) != AFQMC_OK) {
+      b->drop_grouped();
+      return st;
+    }
   if ((st = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_group<R>))) != AFQMC_OK ||
       (st = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_group<R>))) != AFQMC_OK) {
     b->drop_grouped();
     return st;
   }
-  if (!b->s2) CU(cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking));
+  for (int k = 0; k < afqmc_batch::kMaxBranches - 1; ++k) {
+    if (!b->bs[k]) CU(cudaStreamCreateWithFlags(&b->bs[k], cudaStreamNonBlocking));
+    if (!b->ev_join[k]) CU(cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming));
+  }
   if (!b->ev_fork) CU(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-  if (!b->ev_join) CU(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
   b->g_ready = true;
   return AFQMC_OK;
 }
 
-// s2 waits for s (fork) / s waits for s2 (join): the grouped stages whose launches are independent
-// (exchange classes; small- and large-form propagation) run on both streams.
-afqmc_status batch_fork(afqmc_batch* b, cudaStream_t s) {
+// Streams bs[0 .. n) wait for s (fork) / s waits for them (join): independent grouped launches (the
+// branches; within a lone branch the exchange classes and the small- and large-form propagation)
+// run side by side.
+afqmc_status batch_fork(afqmc_batch* b, cudaStream_t s, int n = 1) {
   CU(cudaEventRecord(b->ev_fork, s));
-  CU(cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
+  for (int k = 0; k < n; ++k) CU(cudaStreamWaitEvent(b->bs[k], b->ev_fork, 0));
   return AFQMC_OK;
 }
-afqmc_status batch_join(afqmc_batch* b, cudaStream_t s) {
-  CU(cudaEventRecord(b->ev_join, b->s2));
-  CU(cudaStreamWaitEvent(s, b->ev_join, 0));
+afqmc_status batch_join(afqmc_batch* b, cudaStream_t s, int n = 1) {
+  for (int k = 0; k < n; ++k) {
+    CU(cudaEventRecord(b->ev_join[k], b->bs[k]));
+    CU(cudaStreamWaitEvent(s, b->ev_join[k], 0));
+  }
   return AFQMC_OK;
 }
 
@@ -2365,71 +2409,90 @@ struct BatchStage {
 // One grouped step on stream s: the exchange (force bias, exchange partials, the step's normals;
 // the Theta operands rebuilt first unless thb), the energy estimator (energy), fields, the VHS
 // planes, the propagation and the new overlaps of every system, then QR and the comb.
-afqmc_status batch_grouped_step(afqmc_batch* b, cudaStream_t s, bool energy, bool qr, bool comb, bool thb,
-                                unsigned long long* nk) {
+afqmc_status branch_step(afqmc_batch* b, afqmc_batch::Branch& x, cudaStream_t s, bool energy, bool qr, bool comb,
+                         bool thb, bool forks, unsigned long long* nk) {
   using R = float;
-  const int nsys = (int)b->sys.size();
-  const int* first = static_cast<const int*>(b->a_first);
+  const int nsys = (int)x.sys.size();
+  const int* first = static_cast<const int*>(x.a_first);
   afqmc_status st;
   {
     BatchStage t(b, s, AFQMC_STAGE_FORCE_BIAS);   // the cleared vbias and the bf16 Theta operands
-    const unsigned zb = (unsigned)std::min<size_t>(1184, (b->max_vbias + 255) / 256);
-    k_zero_group<<<dim3(zb, nsys), 256, 0, s>>>(static_cast<const ZeroArgs*>(b->a_zero));
+    const unsigned zb = (unsigned)std::min<size_t>(1184, (x.max_vbias + 255) / 256);
+    k_zero_group<<<dim3(zb, nsys), 256, 0, s>>>(static_cast<const ZeroArgs*>(x.a_zero));
     ++*nk;
-    if (!thb && (st = tc::group_theta(b->g_exch, s, nk, g_err, sizeof(g_err))) != AFQMC_OK) return st;
+    if (!thb && (st = tc::group_theta(x.exch, s, nk, g_err, sizeof(g_err))) != AFQMC_OK) return st;
   }
   {
     BatchStage t(b, s, AFQMC_STAGE_EXCHANGE);
-    const bool two = b->g_exch.nparts > 1;
+    const bool two = forks && x.exch.nparts > 1;
     if (two && (st = batch_fork(b, s)) != AFQMC_OK) return st;
-    if ((st = tc::group_gemm(b->g_exch, s, true, nk, g_err, sizeof(g_err), two ? b->s2 : nullptr)) != AFQMC_OK)
+    if ((st = tc::group_gemm(x.exch, s, true, nk, g_err, sizeof(g_err), two ? b->bs[0] : nullptr)) != AFQMC_OK)
       return st;
     if (two && (st = batch_join(b, s)) != AFQMC_OK) return st;
   }
   if (energy) {
     BatchStage t(b, s, AFQMC_STAGE_ENERGY);
-    k_energy_group<R><<<b->total_w, 256, 0, s>>>(static_cast<const EnergyArgs<R>*>(b->a_energy), first, nsys);
+    k_energy_group<R><<<x.total_w, 256, 0, s>>>(static_cast<const EnergyArgs<R>*>(x.a_energy), first, nsys);
     ++*nk;
   }
   {
     BatchStage t(b, s, AFQMC_STAGE_FIELDS);
-    k_fields_group<R><<<b->total_w, 256, 0, s>>>(static_cast<const FieldArgs<R>*>(b->a_fields), first, nsys);
+    k_fields_group<R><<<x.total_w, 256, 0, s>>>(static_cast<const FieldArgs<R>*>(x.a_fields), first, nsys);
     ++*nk;
   }
   {
     BatchStage t(b, s, AFQMC_STAGE_VHS);
-    if ((st = tc::group_gemm(b->g_vhs, s, false, nk, g_err, sizeof(g_err))) != AFQMC_OK) return st;
+    if ((st = tc::group_gemm(x.vhs, s, false, nk, g_err, sizeof(g_err))) != AFQMC_OK) return st;
   }
   {
     BatchStage t(b, s, AFQMC_STAGE_PROPAGATE);
-    const bool two = b->g_prop.nsmall > 0 && b->g_prop.nlarge > 0;
+    const bool two = forks && x.prop.nsmall > 0 && x.prop.nlarge > 0;
     if (two && (st = batch_fork(b, s)) != AFQMC_OK) return st;
-    if ((st = tc::group_propagate(b->g_prop, s, nk, g_err, sizeof(g_err), two ? b->s2 : nullptr)) != AFQMC_OK)
+    if ((st = tc::group_propagate(x.prop, s, nk, g_err, sizeof(g_err), two ? b->bs[0] : nullptr)) != AFQMC_OK)
       return st;
     if (two && (st = batch_join(b, s)) != AFQMC_OK) return st;
   }
   {
     BatchStage t(b, s, AFQMC_STAGE_OVERLAP);
-    k_overlap_group<R><<<b->total_w, 128, b->ovl_smem, s>>>(static_cast<const OverlapArgs<R>*>(b->a_overlap), first,
-                                                            static_cast<const int*>(b->a_stage), nsys);
+    k_overlap_group<R><<<x.total_w, 128, x.ovl_smem, s>>>(static_cast<const OverlapArgs<R>*>(x.a_overlap), first,
+                                                            static_cast<const int*>(x.a_stage), nsys);
     ++*nk;
   }
   if (qr) {
     BatchStage t(b, s, AFQMC_STAGE_QR);
-    k_qr_group<R><<<b->total_w, 256, b->qr_smem, s>>>(static_cast<const QrArgs<R>*>(b->a_qr), first, nsys);
+    k_qr_group<R><<<x.total_w, 256, x.qr_smem, s>>>(static_cast<const QrArgs<R>*>(x.a_qr), first, nsys);
     ++*nk;
   }
   if (comb) {
     BatchStage t(b, s, AFQMC_STAGE_COMB);
-    const CombArgs<R>* ca = static_cast<const CombArgs<R>*>(b->a_comb);
+    const CombArgs<R>* ca = static_cast<const CombArgs<R>*>(x.a_comb);
     k_comb_plan_group<R><<<nsys, 256, 0, s>>>(ca);
-    k_comb_gather_group<R><<<b->total_w, 256, 0, s>>>(ca, first, nsys);
-    k_comb_back_group<R><<<b->total_w, 256, 0, s>>>(ca, first, nsys);
+    k_comb_gather_group<R><<<x.total_w, 256, 0, s>>>(ca, first, nsys);
+    k_comb_back_group<R><<<x.total_w, 256, 0, s>>>(ca, first, nsys);
     *nk += 3;
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "grouped batch step: %s", cudaGetErrorString(e));
   return AFQMC_OK;
+}
+
+// One grouped step of every branch: side by side on s and the further streams, or in turn on s (one
+// branch, or tracing, where the stages' events must not overlap); a lone branch forks its
+// independent launches instead.
+afqmc_status batch_grouped_step(afqmc_batch* b, cudaStream_t s, bool energy, bool qr, bool comb, bool thb,
+                                unsigned long long* nk) {
+  afqmc_status st;
+  if (b->br.size() == 1 || b->prof) {
+    for (auto& x : b->br)
+      if ((st = branch_step(b, x, s, energy, qr, comb, thb, true, nk)) != AFQMC_OK) return st;
+    return AFQMC_OK;
+  }
+  const int n = (int)b->br.size() - 1;
+  if ((st = batch_fork(b, s, n)) != AFQMC_OK) return st;
+  for (int k = 0; k <= n; ++k)
+    if ((st = branch_step(b, b->br[k], k ? b->bs[k - 1] : s, energy, qr, comb, thb, false, nk)) != AFQMC_OK)
+      return st;
+  return batch_join(b, s, n);
 }
 
 // The executable graph of one grouped step kind (key: energy | qr << 1 | comb << 2 | thb << 3).
@@ -2515,14 +2578,17 @@ afqmc_status afqmc_batch_create(int32_t nsys, afqmc_ctx* const* ctxs, afqmc_batc
 
 void afqmc_batch_destroy(afqmc_batch* b) { delete b; }
 
-afqmc_status afqmc_batch_set_mode(afqmc_batch* b, int32_t mode, int32_t exch_groups) {
+afqmc_status afqmc_batch_set_mode(afqmc_batch* b, int32_t mode, int32_t exch_groups, int32_t branches) {
   if (!b) return fail(AFQMC_EINVAL, "batch is NULL");
   if (mode < AFQMC_BATCH_AUTO || mode > AFQMC_BATCH_GRAPHS) return fail(AFQMC_EINVAL, "batch: unknown mode %d", mode);
   if (exch_groups < 0 || exch_groups > 4) return fail(AFQMC_EINVAL, "batch: exch_groups must be in [0, 4]");
+  if (branches < 0 || branches > afqmc_batch::kMaxBranches)
+    return fail(AFQMC_EINVAL, "batch: branches must be in [0, %d]", afqmc_batch::kMaxBranches);
   for (afqmc_ctx* c : b->sys) CU(cudaStreamSynchronize(c->stream));
-  if (mode != b->mode || exch_groups != b->exch_groups) b->drop_grouped();
+  if (mode != b->mode || exch_groups != b->exch_groups || branches != b->nbranch_req) b->drop_grouped();
   b->mode = mode;
   b->exch_groups = exch_groups;
+  b->nbranch_req = branches;
   return AFQMC_OK;
 }
 
@@ -2570,14 +2636,18 @@ afqmc_status afqmc_batch_describe(afqmc_batch* b, char* buf, size_t len) {
                gl.tmem_cols, gl.smem);
       out += line;
     };
-    for (int k = 0; k < b->g_exch.nparts; ++k) part("exchange", b->g_exch.part[k]);
-    for (int k = 0; k < b->g_vhs.nparts; ++k) part("vhs", b->g_vhs.part[k]);
-    snprintf(line, sizeof(line), "propagate: %d small-form systems (grid %d, %zu B smem), %d large-form systems "
-             "(%d tiles, grid %d, %d stages)\n", b->g_prop.nsmall, b->g_prop.small_grid, b->g_prop.small_smem,
-             b->g_prop.nlarge, b->g_prop.large_tiles, b->g_prop.large_grid, b->g_prop.large_stages);
-    out += line;
-    snprintf(line, sizeof(line), "per-walker kernels: %d walkers in %zu systems\n", b->total_w, b->sys.size());
-    out += line;
+    for (size_t k = 0; k < b->br.size(); ++k) {
+      const afqmc_batch::Branch& x = b->br[k];
+      snprintf(line, sizeof(line), "branch %zu of %zu: %zu systems, %d walkers\n", k + 1, b->br.size(), x.sys.size(),
+               x.total_w);
+      out += line;
+      for (int j = 0; j < x.exch.nparts; ++j) part("  exchange", x.exch.part[j]);
+      for (int j = 0; j < x.vhs.nparts; ++j) part("  vhs", x.vhs.part[j]);
+      snprintf(line, sizeof(line), "  propagate: %d small-form systems (grid %d, %zu B smem), %d large-form systems "
+               "(%d tiles, grid %d, %d stages)\n", x.prop.nsmall, x.prop.small_grid, x.prop.small_smem,
+               x.prop.nlarge, x.prop.large_tiles, x.prop.large_grid, x.prop.large_stages);
+      out += line;
+    }
   }
   snprintf(buf, len, "%s", out.c_str());
   return AFQMC_OK;

@@ -497,20 +497,23 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // the problem of tile t: parameters, maps, the tile's index within the problem, epilogue width
+  // (grouped: each problem's tiles start at a multiple of the grid, so all CTAs enter a problem at
+  // the same turn; the slots between problems are skipped)
   struct Item {
     const Params* p;
     const CUtensorMap* a;
     const CUtensorMap* b;
     int t, nb;
+    bool valid;
   };
   auto resolve = [&](int t, int& cur) -> Item {
     if constexpr (GROUP) {
       while (cur + 1 < ga.nprob && t >= ga.probs[cur + 1].tile0) ++cur;
       const GroupProblem& pr = ga.probs[cur];
-      return Item{&pr.p, &pr.mapA, &pr.mapB, t - pr.tile0, pr.nb};
+      return Item{&pr.p, &pr.mapA, &pr.mapB, t - pr.tile0, pr.nb, t - pr.tile0 < pr.tiles};
     } else {
       (void)cur;
-      return Item{&p, &mapA, &mapB, t, NB};
+      return Item{&p, &mapA, &mapB, t, NB, true};
     }
   };
   auto give_up = [&]() {
@@ -552,6 +555,7 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       bool go = true;
       for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
         const Item it = resolve(t, cur);
+        if (!it.valid) continue;
         const Geom g = it.p->g;   // a register copy: the copies' asm would force reloads of a reference
         int mt, nt;
         tile_mn(g, it.t, &mt, &nt);
@@ -586,12 +590,14 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
       int stage = 0, n_it = 0, cur = 0;
       uint32_t ph = 0;
       bool go = true;
-      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x, ++n_it) {
+      for (int t = blockIdx.x; t < tiles && go; t += gridDim.x) {
         const Item it = resolve(t, cur);
+        if (!it.valid) continue;
         const Geom g = it.p->g;   // a register copy (see the producer)
         const uint32_t idesc = idesc_bf16(g.bn);
         const int acc = n_it & 1;
         const uint32_t aph = (uint32_t)(n_it >> 1) & 1u;
+        ++n_it;
         if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) { go = false; break; }
         tc_fence_after();
         const uint32_t dtm = tmem_base + (uint32_t)acc * acc_stride;
@@ -639,19 +645,21 @@ __global__ void __launch_bounds__(608, 1) k_tc_gemm(const __grid_constant__ CUte
                           : reinterpret_cast<int*>(epi_base + (size_t)group * ebytes);
     const EpiSmem es0 = epi_smem(epi_base, p, group, NB > 0);                      // single problem
     int n_it = 0, cur = 0, loaded = -1;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++n_it) {
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const Item it = resolve(t, cur);
+      if (!it.valid) continue;
       const int acc = n_it & 1;
       const uint32_t aph = (uint32_t)(n_it >> 1) & 1u;
-      if (wig == 0 && lane == 0) {   // slot n_it & 1 is rewritten two tiles later, after this group's next barrier
+      ++n_it;
+      if (wig == 0 && lane == 0) {   // slot acc is rewritten two tiles later, after this group's next barrier
         const bool ok = mbar_wait(&tfull[acc], aph, abort_flag);
         if (!ok) give_up();
-        ok_flags[n_it & 1] = ok ? 1 : 0;
+        ok_flags[acc] = ok ? 1 : 0;
       }
       named_bar(1 + group, 128);   // also: every thread of the group is done with the previous tile's buffers
-      const int ok = ok_flags[n_it & 1];
+      const int ok = ok_flags[acc];
       if (!ok) break;
       tc_fence_after();
-      const Item it = resolve(t, cur);
       const Params* ppp = it.p;
       if constexpr (GROUP) {   // the problem's parameters into the group's shared-memory slot
         Params* slot = reinterpret_cast<Params*>(reinterpret_cast<uint8_t*>(bars) + kTailBytes + group * kParamSlot);
@@ -1733,11 +1741,16 @@ afqmc_status to_device(const std::vector<T>& v, void** dev, char* err, size_t er
 
 // Problems in order of the cost of one tile (K blocks x MMA N x products per k-step), the most
 // expensive first (the CTAs take tiles in turn), and their tile ranges; returns the tile count.
+// Each problem's first tile is rounded up to a multiple of the SM count, so that the CTAs (one per
+// SM, taking every SM-count-th tile) enter each problem at the same turn: at most one problem's
+// operands compete for L2 at a time.
 int order_problems(std::vector<GroupProblem>& pr) {
   auto cost = [](const GroupProblem& q) { return (long long)q.p.g.k_blocks * q.p.g.bn * (q.p.g.dual ? 3 : 1); };
   std::stable_sort(pr.begin(), pr.end(), [&](const GroupProblem& a, const GroupProblem& b) { return cost(a) > cost(b); });
+  const int sms = num_sms();
   int t = 0;
   for (auto& q : pr) {
+    t = (t + sms - 1) / sms * sms;
     q.tile0 = t;
     q.tiles = q.p.g.m_tiles * q.p.g.n_tiles;
     t += q.tiles;
@@ -1780,6 +1793,11 @@ bool group_layout(std::vector<GroupProblem>& pr, GroupLaunch* gg) {
 }  // namespace
 
 namespace {
+int first_block(const TcState* st) {
+  for (int b = 0; b < st->nblk; ++b)
+    if (st->blk[b].n > 0) return b;
+  return 0;
+}
 // Ring depth of a launch whose largest stage is `stride` bytes and largest epilogue region `region`.
 int group_stages(int stride, int region) {
   return std::min(4, (kMaxSmem - 1024 - region - kTailBytes - 4 * kParamSlot) / std::max(1, stride));
@@ -1845,7 +1863,6 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
   gg->epi = 0;
   std::vector<ThetaJob> th;
   std::vector<int> th_first(1, 0);
-  std::vector<NormalsJob> nrm;
   // 1. every (system, block) in its own configuration: at most `groups` epilogue groups (0: the
   //    system's tuned count where its exchange is streamed), fewer until two ring stages fit
   struct Cand { int sys, blk, cap, stages; GroupProblem q; };
@@ -1911,6 +1928,9 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
   // 3. one launch per class, the register-row epilogues decided against the class's accumulators
   for (const Cls& L : cls) {
     std::vector<GroupProblem> pr;
+    std::vector<NormalsJob> nrm;   // drawn by this launch's spare warp: its systems' first blocks
+    for (int k : L.mem)
+      if (sys[cands[k].sys].nj.x && cands[k].blk == first_block(sys[cands[k].sys].st)) nrm.push_back(sys[cands[k].sys].nj);
     for (int k : L.mem) {
       GroupProblem q;
       if (!exchange_problem(sys[cands[k].sys], cands[k].blk, cands[k].cap, L.bn, &q, err, errlen)) {
@@ -1935,8 +1955,10 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
     gl.tiles = order_problems(pr);
     gl.nprob = (int)pr.size();
     gl.grid = std::min(gl.tiles, num_sms());
+    gl.nnrm = (int)nrm.size();
     afqmc_status r;
-    if ((r = to_device(pr, &gl.dev_probs, err, errlen)) != AFQMC_OK) {
+    if ((r = to_device(pr, &gl.dev_probs, err, errlen)) != AFQMC_OK ||
+        (r = to_device(nrm, &gl.dev_nrm, err, errlen)) != AFQMC_OK) {
       group_free(gg);
       return r;
     }
@@ -1944,7 +1966,6 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
   }
   for (int i = 0; i < nsys; ++i) {
     TcState* st = sys[i].st;
-    if (sys[i].nj.x) nrm.push_back(sys[i].nj);
     for (int b = 0; b < st->nblk; ++b) {
       const BlockMaps& bm = st->blk[b];
       if (bm.n == 0) continue;
@@ -1954,12 +1975,10 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
       th_first.push_back(th_first.back() + st->W);
     }
   }
-  gg->nnrm = (int)nrm.size();
   gg->ntheta = (int)th.size();
   gg->theta_blocks = th_first.back();
   afqmc_status r;
-  if ((r = to_device(nrm, &gg->dev_nrm, err, errlen)) != AFQMC_OK ||
-      (r = to_device(th, &gg->dev_theta, err, errlen)) != AFQMC_OK ||
+  if ((r = to_device(th, &gg->dev_theta, err, errlen)) != AFQMC_OK ||
       (r = to_device(th_first, &gg->dev_theta_first, err, errlen)) != AFQMC_OK) {
     group_free(gg);
     return r;
@@ -2042,9 +2061,9 @@ afqmc_status group_gemm(const GroupGemm& gg, cudaStream_t s, bool normals, unsig
     ga.epi_bytes = gl.epi_bytes;
     ga.tmem_cols = gl.tmem_cols;
     ga.acc_stride = gl.acc_stride;
-    const bool draw = normals && k == 0;   // the first launch draws every system's normals
-    ga.nrm = draw ? static_cast<const NormalsJob*>(gg.dev_nrm) : nullptr;
-    ga.nnrm = draw ? gg.nnrm : 0;
+    const bool draw = normals && gl.nnrm > 0;   // each launch draws the normals of its systems
+    ga.nrm = draw ? static_cast<const NormalsJob*>(gl.dev_nrm) : nullptr;
+    ga.nnrm = draw ? gl.nnrm : 0;
     const int threads = 64 + 128 * gl.epi_groups + (ga.nnrm ? 32 : 0);
     const CUtensorMap none{};
     const Params p0{};
@@ -2080,11 +2099,12 @@ afqmc_status group_theta(const GroupGemm& gg, cudaStream_t s, unsigned long long
 void group_free(GroupGemm* gg) {
   for (auto& gl : gg->part) {
     if (gl.dev_probs) cudaFree(gl.dev_probs);
-    gl.dev_probs = nullptr;
+    if (gl.dev_nrm) cudaFree(gl.dev_nrm);
+    gl.dev_probs = gl.dev_nrm = nullptr;
   }
-  for (void* p : {gg->dev_nrm, gg->dev_theta, gg->dev_theta_first})
+  for (void* p : {gg->dev_theta, gg->dev_theta_first})
     if (p) cudaFree(p);
-  gg->dev_nrm = gg->dev_theta = gg->dev_theta_first = nullptr;
+  gg->dev_theta = gg->dev_theta_first = nullptr;
   gg->nparts = 0;
 }
 

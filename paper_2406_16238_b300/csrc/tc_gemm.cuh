@@ -163,13 +163,13 @@ struct GroupLaunch {   // one persistent launch over several problems
   int nb = 0;                          // exchange: the launch's register-row epilogue width (0: staged)
   size_t smem = 0;
   void* dev_probs = nullptr;           // the problems (device)
+  void* dev_nrm = nullptr;             // exchange: NormalsJob of the systems whose first block is here
+  int nnrm = 0;
 };
 struct GroupGemm {
   int epi = 0;              // 0: exchange and force bias, 2: VHS planes
   int nparts = 0;           // exchange: one launch per class of problems with one ring depth
   GroupLaunch part[8];
-  void* dev_nrm = nullptr;             // NormalsJob per system (device)
-  int nnrm = 0;
   void* dev_theta = nullptr;           // exchange: Theta^T conversion jobs, one per (system, block)
   void* dev_theta_first = nullptr;     // their first block in the grid
   int ntheta = 0, theta_blocks = 0;

@@ -30,7 +30,7 @@ def _contexts(probs, prec, nw=16):
                       prec=prec) for i, p in enumerate(probs)]
 
 
-def _run(probs, prec, mode, nsteps=11, groups=0, zero=None):
+def _run(probs, prec, mode, nsteps=11, groups=0, zero=None, branches=0):
     ctxs = _contexts(probs, prec)
     if zero is not None:   # walkers of weight zero are frozen (skipped by every grouped kernel)
         for c in ctxs:
@@ -38,7 +38,7 @@ def _run(probs, prec, mode, nsteps=11, groups=0, zero=None):
             w = w.copy()
             w[zero] = 0.0
             c.set_walkers(psi, w, step)
-    b = Batch(ctxs, mode=mode, exch_groups=groups)
+    b = Batch(ctxs, mode=mode, exch_groups=groups, branches=branches)
     assert b.mode() == mode
     e = b.run(nsteps, energy_every=1, reortho_every=3, comb_every=5)
     walkers = [c.get_walkers() for c in ctxs]
@@ -53,11 +53,12 @@ def systems():
     return _systems()
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-5), ("bf16", 2e-4)])
-def test_grouped_launches_agree_with_per_system_graphs(systems, prec, tol):
+@pytest.mark.parametrize("prec,tol,branches", [("bf16x3", 2e-5, 2), ("bf16x3", 2e-5, 1), ("bf16", 2e-4, 0)])
+def test_grouped_launches_agree_with_per_system_graphs(systems, prec, tol, branches):
     """11 steps with energy every step, QR every 3 and comb every 5 (so the steps after a comb
-    rebuild the bf16 Theta operands): mixed energies, weights and step counters."""
-    eg, wg = _run(systems, prec, "grouped")
+    rebuild the bf16 Theta operands): mixed energies, weights and step counters; one branch of
+    grouped launches, or two side by side."""
+    eg, wg = _run(systems, prec, "grouped", branches=branches)
     er, wr = _run(systems, prec, "graphs")
     assert eg.shape == er.shape == (4, 11, 4)
     assert np.all(np.isfinite(eg))
