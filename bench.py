@@ -581,6 +581,13 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(prob, seed, args.cpu_budget)
     if not args.no_large and world == 1:
         line["large_system"] = run_large(args, dev, stream)
+    if not args.no_batched and world == 1:
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup = 20, 3
+        b = run_batched(bargs)
+        line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "config", "clocks",
+                                             "gpu_launches", "roofline", "rooflines", "stage_ms_per_step",
+                                             "graphs_form", "energies_finite") if k in b}
     return line
 
 
@@ -873,6 +880,7 @@ def main():
     ap.add_argument("--large-naux", type=int, default=None,
                     help="the large system truncated to its first naux Cholesky vectors (a small case for ncu)")
     ap.add_argument("--nsys", type=int, default=32)
+    ap.add_argument("--no-batched", action="store_true", help="leave the uneven-batch measurement out of the line")
     ap.add_argument("--batch-mode", default="auto", choices=["auto", "grouped", "graphs"],
                     help="batched workload: one launch per stage over all systems, or per-system graphs")
     ap.add_argument("--cv-pairs", type=int, default=100000)

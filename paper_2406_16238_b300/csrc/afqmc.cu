@@ -2482,9 +2482,9 @@ afqmc_status branch_step(afqmc_batch* b, afqmc_batch::Branch& x, cudaStream_t s,
 afqmc_status batch_grouped_step(afqmc_batch* b, cudaStream_t s, bool energy, bool qr, bool comb, bool thb,
                                 unsigned long long* nk) {
   afqmc_status st;
-  if (b->br.size() == 1 || b->prof) {
+  if (b->br.size() == 1 || b->prof) {   // tracing: every launch alone, so each stage times its kernels
     for (auto& x : b->br)
-      if ((st = branch_step(b, x, s, energy, qr, comb, thb, true, nk)) != AFQMC_OK) return st;
+      if ((st = branch_step(b, x, s, energy, qr, comb, thb, !b->prof, nk)) != AFQMC_OK) return st;
     return AFQMC_OK;
   }
   const int n = (int)b->br.size() - 1;
