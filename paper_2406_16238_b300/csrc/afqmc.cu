@@ -1844,10 +1844,8 @@ afqmc_status afqmc_cv_attach(afqmc_ctx* ctx, int32_t capacity, int32_t batch, do
   const float ident[2] = {0.f, 1.f};
   CU(cudaMemcpyAsync(v.ystat, ident, 8, cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
-  int P2 = 1;
-  while (P2 < ctx->d.W) P2 <<= 1;
-  (void)P2;
   if ((st = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_cv_select))) != AFQMC_OK) return st;
+  if ((st = tc::gemm_f32_prepare(g_err, sizeof(g_err))) != AFQMC_OK) return fail(st, "cv: %s", g_err);
   ctx->drop_graphs();
   ctx->cv = v;
   return AFQMC_OK;

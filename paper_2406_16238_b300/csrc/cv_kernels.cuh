@@ -278,6 +278,8 @@ struct CvState {
   float *Zw = nullptr, *WA1 = nullptr, *WA2 = nullptr, *WA3 = nullptr, *wout = nullptr, *fw = nullptr;
   int *perm = nullptr, *sel = nullptr;
   double *a = nullptr, *e1 = nullptr;
+  char* tc_scratch = nullptr;   // split-bf16 operands of the tensor-core GEMMs
+  size_t tc_bytes = 0;
   // parameter blocks inside P (and the same offsets inside G, Mo, Vo)
   size_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, oW4 = 0, ob4 = 0;
 };

@@ -2108,5 +2108,85 @@ void group_free(GroupGemm* gg) {
   gg->nparts = 0;
 }
 
+// ----------------------------------------------------------------------------- general fp32 GEMM
+// One operand (rows x K, element (i, k) at src[i si + k sk]) as split bf16 K-major rows [hi | lo] of
+// kx (K padded to the k-block) each, zeros in the padding.
+__global__ void k_split_rows(int rows, int K, int kx, const float* src, long long si, long long sk,
+                             __nv_bfloat16* out) {
+  const size_t total = (size_t)rows * kx;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / kx), k = (int)(idx % kx);
+    const float v = k < K ? src[(size_t)i * si + (size_t)k * sk] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16* row = out + (size_t)i * 2 * kx;
+    row[k] = hi;
+    row[kx + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+}
+
+afqmc_status gemm_f32_prepare(char* err, size_t errlen) {
+  if (cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess) {
+    snprintf(err, errlen, "tcgen05 fp32 GEMM: cannot reserve shared memory");
+    return AFQMC_ECUDA;
+  }
+  return AFQMC_OK;
+}
+
+size_t gemm_f32_scratch(int M, int N, int K) {
+  const size_t kx = ((size_t)K + kBK - 1) / kBK * kBK;
+  return align256((size_t)M * 2 * kx * 2) + align256((size_t)N * 2 * kx * 2);
+}
+
+afqmc_status gemm_f32(cudaStream_t s, int M, int N, int K, const float* A, long long sAm, long long sAk,
+                      const float* B, long long sBk, long long sBn, float* C, long long ldc, char* scratch,
+                      size_t scratch_bytes, int* status, unsigned long long* launches, char* err, size_t errlen) {
+  if (M < 1 || N < 1 || K < 1 || N % 16 != 0) {
+    snprintf(err, errlen, "tcgen05 fp32 GEMM: shape %d x %d x %d (N a multiple of 16)", M, N, K);
+    return AFQMC_EINVAL;
+  }
+  if (gemm_f32_scratch(M, N, K) > scratch_bytes) {
+    snprintf(err, errlen, "tcgen05 fp32 GEMM: scratch too small for %d x %d x %d", M, N, K);
+    return AFQMC_EINVAL;
+  }
+  const int kx = (K + kBK - 1) / kBK * kBK;
+  __nv_bfloat16* a = reinterpret_cast<__nv_bfloat16*>(scratch);
+  __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(scratch + align256((size_t)M * 2 * kx * 2));
+  const int ga = (int)std::min<size_t>(1184, ((size_t)M * kx + 255) / 256);
+  const int gb = (int)std::min<size_t>(1184, ((size_t)N * kx + 255) / 256);
+  k_split_rows<<<ga, 256, 0, s>>>(M, K, kx, A, sAm, sAk, a);
+  k_split_rows<<<gb, 256, 0, s>>>(N, K, kx, B, sBn, sBk, b);
+  *launches += 2;
+  Geom g{};
+  g.bn = std::min(256, N);
+  g.m_tiles = (M + kBM - 1) / kBM;
+  g.n_tiles = (N + g.bn - 1) / g.bn;
+  g.il3 = 1;   // A [hi | lo] x B [hi | lo]: hi hi, lo hi, hi lo per k-block
+  g.seg = kx;
+  g.k_blocks = 3 * kx / kBK;
+  g.k_steps = 3 * kx / 16;
+  g.m_step = kBM;
+  g.n_step = g.bn;
+  int groups = 4;   // each epilogue group stores a multiple of 16 columns
+  while (g.bn % (16 * groups)) --groups;
+  if (!finish_geom(&g, 16, groups)) {
+    snprintf(err, errlen, "tcgen05 fp32 GEMM: shared memory plan failed");
+    return AFQMC_EINVAL;
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a, (unsigned long long)M, 2ull * kx, kBM) ||
+      !make_map(&mb, b, (unsigned long long)N, 2ull * kx, (unsigned)g.bn)) {
+    snprintf(err, errlen, "tcgen05 fp32 GEMM: tensor maps");
+    return AFQMC_ECUDA;
+  }
+  Params p{};
+  p.g = g;
+  p.status = status;
+  p.out = C;
+  p.ldo = ldc;
+  p.out_rows = M;
+  p.out_cols = N;
+  return launch<1>(g, ma, mb, p, s, launches, err, errlen);
+}
+
 }  // namespace tc
 }  // namespace afq

@@ -143,6 +143,16 @@ afqmc_status vhs_planes(TcState* st, cudaStream_t s, char* tcbuf, const float2* 
 afqmc_status propagate(TcState* st, cudaStream_t s, char* tcbuf, int order, float2* psi, const double* w,
                        int* status, unsigned long long* launches, char* err, size_t errlen);
 
+// C[M][N] (row pitch ldc) = A B in fp32 with split-bf16 tensor-core products (hi hi + lo hi + hi lo,
+// fp32 accumulation): A element (i, k) at A[i sAm + k sAk], B element (k, j) at B[k sBk + j sBn]; N a
+// multiple of 16.  The operands are first split into bf16 K-major rows in `scratch`
+// (gemm_f32_scratch(M, N, K) bytes, 256-byte aligned).
+size_t gemm_f32_scratch(int M, int N, int K);
+afqmc_status gemm_f32_prepare(char* err, size_t errlen);   // once, outside stream capture
+afqmc_status gemm_f32(cudaStream_t s, int M, int N, int K, const float* A, long long sAm, long long sAk,
+                      const float* B, long long sBk, long long sBn, float* C, long long ldc, char* scratch,
+                      size_t scratch_bytes, int* status, unsigned long long* launches, char* err, size_t errlen);
+
 // ------------------------------------------------------------------ grouped launches (uneven batches)
 // One persistent launch of the exchange (or the VHS planes) contraction over the tiles of several
 // systems and spin blocks (a work list ordered by tile cost), with the problems' tensor maps and

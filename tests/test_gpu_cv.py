@@ -43,6 +43,32 @@ def test_network_forward_and_gradients_match_the_oracle():
         assert np.linalg.norm(blk_g - blk_ref.reshape(-1)) <= 1e-4 * max(np.linalg.norm(blk_ref), 1e-12)
 
 
+def test_network_on_the_tensor_cores_matches_the_oracle():
+    """512-row batches run every layer's product of at least 128 x 64 x 64 on the tensor cores (split
+    bf16, three products, fp32 accumulation: ~2^-16 relative per product): output, loss and gradients
+    against the oracle at 1e-4 relative (the CUDA-core test above holds the binary32 path to 2e-5)."""
+    prob = config_medium()
+    ctx = _ctx(prob, 16)
+    ctx.cv_attach(capacity=1024, batch=512)
+    dim = ctx.cv_dim
+    assert dim == 2 * prob.norb + 8 and dim >= 64
+    params = mlp.init_params(dim, seed=5)
+    ctx.cv_set_params(_flat(params))
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((512, dim)).astype(np.float32)
+    y = rng.standard_normal(512).astype(np.float32)
+    out, loss, grads = ctx.cv_eval(x, y)
+    p32 = [p.astype(np.float32).astype(np.float64) for p in params]
+    ref_out, _ = mlp.forward(p32, x.astype(np.float64))
+    ref_loss, ref_grads = mlp.loss_and_grads(p32, x.astype(np.float64), y.astype(np.float64))
+    assert np.allclose(out, ref_out, rtol=0, atol=1e-4 * np.max(np.abs(ref_out)))
+    assert abs(loss - ref_loss) < 1e-4 * ref_loss
+    for blk_g, blk_ref in zip(np.split(grads, np.cumsum([p.size for p in params])[:-1]), ref_grads):
+        assert np.linalg.norm(blk_g - blk_ref.reshape(-1)) <= 1e-4 * max(np.linalg.norm(blk_ref), 1e-12)
+    assert ctx.launch_count() > 0
+    ctx.close()
+
+
 def _trained_context(prec, nw=640, steps=12, epochs=40):
     prob = config_medium()
     ctx = _ctx(prob, nw, prec=prec, seed=7)
