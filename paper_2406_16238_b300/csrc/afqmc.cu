@@ -2173,7 +2173,10 @@ struct afqmc_batch {
     void *a_first = nullptr, *a_energy = nullptr, *a_fields = nullptr, *a_overlap = nullptr, *a_stage = nullptr,
          *a_qr = nullptr, *a_comb = nullptr, *a_zero = nullptr;
     int total_w = 0;
-    size_t ovl_smem = 0, qr_smem = 0, max_vbias = 0;
+    size_t max_vbias = 0;
+    // the overlap and QR launches: walker ranges [w0, w1) of systems with similar shared memory
+    struct SmemClass { int w0, w1; size_t smem; };
+    std::vector<SmemClass> ovl, qr;
   };
   std::vector<Branch> br;
   std::vector<void*> g_dev;     // device argument arrays of the grouped per-walker kernels
@@ -2281,6 +2284,11 @@ afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
   std::vector<CombArgs<R>> ca(nsys);
   std::vector<ZeroArgs> za(nsys);
   std::vector<int> stage(nsys), first(nsys + 1, 0);
+  // systems in order of their overlap kernel's shared memory, so that the overlap and QR launches can
+  // take runs of systems with similar needs (a launch reserves its largest system's shared memory)
+  std::stable_sort(x.sys.begin(), x.sys.end(),
+                   [&](int p, int q) { return overlap_smem(b->sys[p]->d) < overlap_smem(b->sys[q]->d); });
+  std::vector<size_t> osm(nsys), qsm(nsys);
   for (int i = 0; i < nsys; ++i) {
     afqmc_ctx* c = b->sys[x.sys[i]];
     const Dims& d = c->d;
@@ -2295,9 +2303,9 @@ afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
     fa[i] = field_args<R>(c);
     oa[i] = overlap_args<R>(c, 1);
     stage[i] = overlap_stage(d) ? 1 : 0;
-    x.ovl_smem = std::max(x.ovl_smem, overlap_smem(d));
+    osm[i] = overlap_smem(d);
     qa[i] = qr_args<R>(c);
-    x.qr_smem = std::max(x.qr_smem, qr_smem(d));
+    qsm[i] = qr_smem(d);
     ca[i] = CombArgs<R>{d.W, d.N * d.ncol, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.cum),
                         c->at<int>(c->L.src), c->at<double>(c->L.neww), status, c->at<float2>(c->L.psi),
                         c->at<float2>(c->L.psi_tmp), c->at<float2>(c->L.thetaT), c->at<float2>(c->L.th_tmp),
@@ -2308,6 +2316,20 @@ afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
     first[i + 1] = first[i] + d.W;
   }
   x.total_w = first[nsys];
+  // runs of systems whose shared memory is within a factor of two of the run's first (at most 4 runs)
+  auto classes = [&](const std::vector<size_t>& sm, std::vector<afqmc_batch::Branch::SmemClass>& out) {
+    out.clear();
+    int i0 = 0;
+    for (int i = 1; i <= nsys; ++i)
+      if (i == nsys || (sm[i] > 2 * std::max<size_t>(sm[i0], 16384) && out.size() < 3)) {
+        size_t m = 0;
+        for (int k = i0; k < i; ++k) m = std::max(m, sm[k]);
+        out.push_back({first[i0], first[i], m});
+        i0 = i;
+      }
+  };
+  classes(osm, x.ovl);
+  classes(qsm, x.qr);
   afqmc_status st;
   if ((st = tc::group_exchange_plan(gs.data(), nsys, b->exch_groups, &x.exch, g_err, sizeof(g_err))) != AFQMC_OK ||
       (st = tc::group_vhs_plan(gs.data(), nsys, &x.vhs, g_err, sizeof(g_err))) != AFQMC_OK ||
@@ -2452,14 +2474,18 @@ afqmc_status branch_step(afqmc_batch* b, afqmc_batch::Branch& x, cudaStream_t s,
   }
   {
     BatchStage t(b, s, AFQMC_STAGE_OVERLAP);
-    k_overlap_group<R><<<x.total_w, 128, x.ovl_smem, s>>>(static_cast<const OverlapArgs<R>*>(x.a_overlap), first,
-                                                            static_cast<const int*>(x.a_stage), nsys);
-    ++*nk;
+    for (const auto& k : x.ovl) {
+      k_overlap_group<R><<<k.w1 - k.w0, 128, k.smem, s>>>(static_cast<const OverlapArgs<R>*>(x.a_overlap), first,
+                                                          static_cast<const int*>(x.a_stage), nsys, k.w0);
+      ++*nk;
+    }
   }
   if (qr) {
     BatchStage t(b, s, AFQMC_STAGE_QR);
-    k_qr_group<R><<<x.total_w, 256, x.qr_smem, s>>>(static_cast<const QrArgs<R>*>(x.a_qr), first, nsys);
-    ++*nk;
+    for (const auto& k : x.qr) {
+      k_qr_group<R><<<k.w1 - k.w0, 256, k.smem, s>>>(static_cast<const QrArgs<R>*>(x.a_qr), first, nsys, k.w0);
+      ++*nk;
+    }
   }
   if (comb) {
     BatchStage t(b, s, AFQMC_STAGE_COMB);

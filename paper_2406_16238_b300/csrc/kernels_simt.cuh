@@ -1550,15 +1550,16 @@ template <typename R, bool STAGE, bool CPHI = false>
 __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
   overlap_walker<R, STAGE, CPHI>(a, blockIdx.x);
 }
-// Several systems in one launch, one block per walker; stage[s]: system s stages psi and Theta
-// in shared memory (the launch's shared memory covers the largest system's need).
+// Several systems in one launch, one block per walker (block b is walker b + base of the list);
+// stage[s]: system s stages psi and Theta in shared memory (the launch's shared memory covers the
+// largest need among its systems).
 template <typename R, bool CPHI = false>
 __global__ void __launch_bounds__(128, 5) k_overlap_group(const OverlapArgs<R>* __restrict__ args,
                                                           const int* __restrict__ first,
-                                                          const int* __restrict__ stage, int nsys) {
-  const int s = group_of(first, nsys, blockIdx.x);
-  if (stage[s]) overlap_walker<R, true, CPHI>(args[s], blockIdx.x - first[s]);
-  else overlap_walker<R, false, CPHI>(args[s], blockIdx.x - first[s]);
+                                                          const int* __restrict__ stage, int nsys, int base) {
+  const int b = blockIdx.x + base, s = group_of(first, nsys, b);
+  if (stage[s]) overlap_walker<R, true, CPHI>(args[s], b - first[s]);
+  else overlap_walker<R, false, CPHI>(args[s], b - first[s]);
 }
 
 // ============================================================================
@@ -1739,9 +1740,9 @@ __global__ void __launch_bounds__(256) k_qr_chol(QrArgs<R> a) {
 }
 template <typename R>
 __global__ void __launch_bounds__(256) k_qr_group(const QrArgs<R>* __restrict__ args, const int* __restrict__ first,
-                                                  int nsys) {
-  const int s = group_of(first, nsys, blockIdx.x);
-  qr_walker<R>(args[s], blockIdx.x - first[s]);
+                                                  int nsys, int base) {
+  const int b = blockIdx.x + base, s = group_of(first, nsys, b);
+  qr_walker<R>(args[s], b - first[s]);
 }
 
 }  // namespace afq

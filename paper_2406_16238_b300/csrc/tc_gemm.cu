@@ -1885,7 +1885,7 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
       cands.push_back(c);
     }
   // 2. classes: a problem joins the first class whose merged layout keeps its ring depth (and the
-  //    class's); at most 8 classes, the rest going where the merged depth is largest
+  //    class's), else opens a class of its own
   struct Cls { std::vector<int> mem; int stride = 0, region = 0, bn = 0, stages = 0, nb = 0; };
   // a register-row problem keeps its epilogue under a launch whose accumulators are `acc` wide
   auto reg_fits = [&](const Cand& c, int acc) {
@@ -1898,7 +1898,7 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cands[x].stages > cands[y].stages; });
   for (int k : order) {
     const Cand& c = cands[k];
-    int pick = -1, best = -1;
+    int pick = -1;
     for (int j = 0; j < (int)cls.size(); ++j) {
       if (cls[j].nb != c.q.nb) continue;   // one epilogue width per launch
       const int acc = std::max(cls[j].bn, c.q.p.g.bn);
@@ -1907,16 +1907,11 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
       if (!fits) continue;
       const int d = group_stages(std::max(cls[j].stride, c.q.p.g.stage_bytes), std::max(cls[j].region, epi_region(c.q)));
       if (d == c.stages && d == cls[j].stages) { pick = j; break; }
-      if (d >= 2 && d > best) { best = d; if ((int)cls.size() >= 8) pick = j; }
     }
-    if (pick < 0 && (int)cls.size() < 8) {
+    if (pick < 0) {
       cls.push_back(Cls{});
       pick = (int)cls.size() - 1;
       cls[pick].nb = c.q.nb;
-    }
-    if (pick < 0) {
-      snprintf(err, errlen, "grouped exchange: no shared-memory layout fits every system");
-      return AFQMC_EINVAL;
     }
     Cls& L = cls[pick];
     L.mem.push_back(k);
@@ -1939,7 +1934,8 @@ afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, G
       }
       pr.push_back(q);
     }
-    GroupLaunch& gl = gg->part[gg->nparts];
+    gg->part.emplace_back();
+    GroupLaunch& gl = gg->part.back();
     gl.nb = L.nb;
     for (const auto& q : pr)
       if (q.nb != L.nb) {
@@ -2034,6 +2030,7 @@ afqmc_status group_vhs_plan(const GroupSystem* sys, int nsys, GroupGemm* gg, cha
     g.epi_bytes = 16 + (st->packed ? 4096 : 0);   // packed: the mirrored rows' staging
     pr.push_back(q);
   }
+  gg->part.assign(1, GroupLaunch{});
   GroupLaunch& gl = gg->part[0];
   if (pr.empty() || !group_layout(pr, &gl)) {
     snprintf(err, errlen, "grouped VHS: no shared-memory layout fits every system");
@@ -2105,6 +2102,7 @@ void group_free(GroupGemm* gg) {
   for (void* p : {gg->dev_theta, gg->dev_theta_first})
     if (p) cudaFree(p);
   gg->dev_theta = gg->dev_theta_first = nullptr;
+  gg->part.clear();
   gg->nparts = 0;
 }
 

@@ -10,6 +10,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "afqmc.h"
 
 namespace afq {
@@ -179,7 +181,7 @@ struct GroupLaunch {   // one persistent launch over several problems
 struct GroupGemm {
   int epi = 0;              // 0: exchange and force bias, 2: VHS planes
   int nparts = 0;           // exchange: one launch per class of problems with one ring depth
-  GroupLaunch part[8];
+  std::vector<GroupLaunch> part;
   void* dev_theta = nullptr;           // exchange: Theta^T conversion jobs, one per (system, block)
   void* dev_theta_first = nullptr;     // their first block in the grid
   int ntheta = 0, theta_blocks = 0;
@@ -187,7 +189,7 @@ struct GroupGemm {
 // Exchange over every (system, block) in the streamed form, each with its own walker tiling and
 // epilogue warpgroups (at most `groups`; 0: the system's own tuned count), in as few launches as keep
 // every problem's own ring depth: problems whose largest stage and epilogue buffers leave the same
-// number of stages share a launch (at most 8 launches).  The systems' own exchange forms are left as
+// number of stages share a launch.  The systems' own exchange forms are left as
 // they are.
 afqmc_status group_exchange_plan(const GroupSystem* sys, int nsys, int groups, GroupGemm* gg, char* err,
                                  size_t errlen);
