@@ -101,3 +101,47 @@ def test_grouped_form_needs_one_tensor_core_form():
     b.close()
     for c in ctxs:
         c.close()
+
+
+def test_grouped_steps_without_energy_and_uneven_cadence(systems):
+    """Energy every third step, QR every 4, comb every 6: the grouped steps without an energy
+    measurement form the force bias with the grouped exchange (the per-system graphs with a CUDA-core
+    product), so the two agree to rounding; the step counters and measurement counts match."""
+    def run(mode):
+        ctxs = _contexts(systems[:3], "bf16x3")
+        b = Batch(ctxs, mode=mode)
+        e = b.run(13, energy_every=3, reortho_every=4, comb_every=6)
+        steps = [c.get_walkers()[3] for c in ctxs]
+        b.close()
+        for c in ctxs:
+            c.close()
+        return e, steps
+    eg, sg = run("grouped")
+    er, sr = run("graphs")
+    assert eg.shape == er.shape == (3, 5, 4) and sg == sr == [13, 13, 13]
+    assert np.max(np.abs(eg[:, :, 0] / eg[:, :, 1] - er[:, :, 0] / er[:, :, 1])) < 2e-5
+
+
+def test_complex_and_free_projection_contexts_batch_as_graphs():
+    from synthetic_inputs import make_complex_problem
+    pc = make_complex_problem(10, 3, 2, 6, 3.0, 72, unrestricted=True)
+    pr = _systems()[0]
+    ctxs = [pkg.Afqmc(pc.h1e, pc.chol, pc.ecore, pc.nalpha, pc.nbeta, pc.psiT, nwalkers=8, prec="bf16x3"),
+            pkg.Afqmc(pr.h1e, pr.chol, pr.ecore, pr.nalpha, pr.nbeta, pr.psiT, nwalkers=8, prec="bf16x3")]
+    b = Batch(ctxs)
+    assert b.mode() == "graphs"   # a complex Hamiltonian: the per-system graphs
+    e = b.run(3, energy_every=1, reortho_every=5, comb_every=0)
+    assert np.all(np.isfinite(e))
+    b.close()
+    for c in ctxs:
+        c.close()
+    c1, c2 = [pkg.Afqmc(pr.h1e, pr.chol, pr.ecore, pr.nalpha, pr.nbeta, pr.psiT, nwalkers=8, prec="bf16x3")
+              for _ in range(2)]
+    c2.set_free_projection(True)
+    b = Batch([c1, c2])
+    assert b.mode() == "graphs"   # free projection: the per-system graphs
+    e = b.run(2, energy_every=1, reortho_every=5, comb_every=0)
+    assert np.all(np.isfinite(e))
+    b.close()
+    for c in (c1, c2):
+        c.close()
