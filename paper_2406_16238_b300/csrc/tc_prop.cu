@@ -85,7 +85,7 @@ __device__ __forceinline__ void signal_b(uint64_t* bar_b, int lane) {
   if (lane == 0) mbar_arrive(bar_b);
 }
 
-// Lane 0 waits, the warp follows its verdict (tcgen05.ld needs the whole warp).
+// Lane 0 waits, the warp follows its outcome (tcgen05.ld needs the whole warp).
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int lane) {
   int ok = 0;
   if (lane == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
