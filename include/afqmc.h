@@ -337,6 +337,16 @@ void afqmc_batch_destroy(afqmc_batch* b);
  * directly.  Results are identical either way.  Tracing (afqmc_profile) uses direct launches. */
 afqmc_status afqmc_set_graphs(afqmc_ctx* ctx, int32_t enable);
 afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial);
+/* E_T of the weight factor exp(dt (E_T - E_c)) (Eqs. 13-16; the paper leaves the constant out)
+ * follows the estimate (enable = 1): E_T starts from its current value and two running sums from
+ * zero; every energy that afqmc_run, afqmc_run_async or afqmc_batch_run measures adds its ENumer
+ * and EDenom to the sums, and every comb sets E_T = sum ENumer / sum EDenom (E_T stays while the
+ * sum of EDenom is 0).  The factor is common to all weights, so energies and comb decisions are
+ * those of a fixed E_T; it keeps the total weight from drifting as exp(dt (E_T - E) t).  E_T then
+ * lives in device memory: afqmc_get_info synchronises the stream and reports it, afqmc_set_etrial
+ * overwrites it (the sums stay).  enable = 0 keeps the value reached; enabling again restarts the
+ * sums.  afqmc_local_energy and free projection leave the sums alone.  Synchronises the stream. */
+afqmc_status afqmc_set_etrial_update(afqmc_ctx* ctx, int32_t enable);
 
 /* Free-projection AFQMC (Section "Free projection AFQMC"): enable = 1 switches the context to
  * unconstrained propagation.  Each step draws the fields x ~ N(0,1) with no force-bias shift

@@ -31,8 +31,10 @@ Conventions (the paper's notation; readings where it is silent are marked R#):
   I = S exp(x.xbar - xbar.xbar / 2), theta = arg S,
   w <- w |I| max(0, cos theta) exp(dt (E_T - E_c)).
   R4 E_T (energy shift) defaults to the trial's variational energy and is a
-  common factor of all weights; R5 walkers of weight 0 are frozen until the
-  next comb.
+  common factor of all weights; optionally (TrialEnergy) it is replaced at
+  each comb by the running mixed estimate sum ENumer / sum EDenom of the
+  measurements made since the state was created; R5 walkers of weight 0 are
+  frozen until the next comb.
 * Local energy (Eq. 9), half-rotated: T^{g s} = Ltilde^{g s} Theta^s,
   E1 = sum_s Tr(htilde^s Theta^s), J = 1/2 sum_g (sum_s Tr T^{g s})^2,
   K = 1/2 sum_{g s} Tr(T^{g s} T^{g s}), E_L = E0 + E1 + J - K.
@@ -364,9 +366,35 @@ def population_control(wk: Walkers, seed):
     return src, xi
 
 
+@dataclasses.dataclass
+class TrialEnergy:
+    """E_T that follows the estimate (R4): the shift in use and the running sums it is taken from.
+
+    The paper leaves the constant factor of Eq. 14 out; in this reading E_T starts at a given value
+    (E_var by default) and, at each comb, becomes the mixed estimate accumulated so far,
+    num / den = sum ENumer / sum EDenom over every measurement made while this state was in use.
+    Before the first measurement (den = 0) E_T keeps its value.
+    """
+    et: float
+    num: float = 0.0
+    den: float = 0.0
+
+    def measured(self, sums):
+        self.num += float(sums[0])
+        self.den += float(sums[1])
+
+    def at_comb(self):
+        if self.den > 0.0:
+            self.et = self.num / self.den
+
+
 def run_phaseless(st: Setup, psiT, nwalkers, nsteps, seed, e_trial=None, fb_cap=1.0, order=6,
-                  reortho_every=5, comb_every=10, energy_every=1, walkers=None):
-    """The block loop (R8).  Returns per-measurement estimator sums and the final walkers."""
+                  reortho_every=5, comb_every=10, energy_every=1, walkers=None, trial_energy=None):
+    """The block loop (R8).  Returns per-measurement estimator sums and the final walkers.
+
+    trial_energy (a TrialEnergy, updated in place): E_T is taken from it and updated at each comb
+    (e_trial is then unused); without it E_T stays at e_trial (E_var by default).
+    """
     wk = walkers if walkers is not None else init_walkers(st, psiT, nwalkers)
     et = st.evar if e_trial is None else e_trial
     history = []
@@ -374,11 +402,17 @@ def run_phaseless(st: Setup, psiT, nwalkers, nsteps, seed, e_trial=None, fb_cap=
         if energy_every and wk.step % energy_every == 0:
             sums, _ = energy_sums(st, wk)
             history.append(sums)
+            if trial_energy is not None:
+                trial_energy.measured(sums)
+        if trial_energy is not None:
+            et = trial_energy.et
         phaseless_step(st, wk, seed, et, fb_cap, order)
         if reortho_every and wk.step % reortho_every == 0:
             reorthogonalise(st, wk)
         if comb_every and wk.step % comb_every == 0:
             population_control(wk, seed)
+            if trial_energy is not None:
+                trial_energy.at_comb()
     return np.array(history), wk
 
 

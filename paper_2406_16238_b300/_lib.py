@@ -82,6 +82,7 @@ SIGNATURES = {
     "afqmc_draw_normals": (_i32, [_u64, _u64, ctypes.c_uint32, _i32, _i32, _vp, _vp]),
     "afqmc_get_info": (_i32, [_vp, ctypes.POINTER(Info)]),
     "afqmc_set_etrial": (_i32, [_vp, ctypes.c_double]),
+    "afqmc_set_etrial_update": (_i32, [_vp, _i32]),
     "afqmc_set_graphs": (_i32, [_vp, _i32]),
     "afqmc_set_free_projection": (_i32, [_vp, _i32]),
     "afqmc_get_weight_phases": (_i32, [_vp, _dp]),
@@ -438,6 +439,15 @@ class Afqmc:
 
     def set_etrial(self, e):
         _check(self._lib.afqmc_set_etrial(self._ctx, float(e)))
+
+    def set_etrial_update(self, enable=True):
+        """E_T replaced at each comb by the running mixed estimate of the run's measurements (or fixed again)."""
+        _check(self._lib.afqmc_set_etrial_update(self._ctx, 1 if enable else 0))
+
+    @property
+    def e_trial(self):
+        """The energy shift E_T in use (read from the device while it follows the estimate)."""
+        return self.info()["e_trial"]
 
     def synchronize(self, timeout_s=60.0):
         _check(self._lib.afqmc_synchronize(self._ctx, float(timeout_s)))

@@ -77,6 +77,7 @@ struct Layout {
   size_t msum, lsum, pden, e1, e2;   // set-up: sum L L, sum lbar L, trial density, two N x N temporaries
   size_t vbias, x, xbar, coef, cmf, xxbar, vhs;
   size_t exch_part, eloc, hist, status, step, src, cum, neww, slot, sflag;
+  size_t etr;         // {E_T, sum ENumer, sum EDenom} when E_T follows the running estimate
   size_t tc;          // tensor-core operand buffers (BF16 forms)
   size_t stage;       // set-up staging of Cholesky chunks (aliases vhs, which the set-up does not use)
   size_t stage_bytes, stage_bytes_avail, vhs_bytes, tc_bytes;
@@ -134,6 +135,7 @@ Layout plan(const Dims& d) {
   L.neww = take(256);
   L.slot = take(256);
   L.sflag = take(256);   // set-up: input check flags, the 1-norm of the exponent
+  L.etr = take(256);
   {
     tc::TcState tmp;
     L.tc_bytes = tc::plan(&tmp, d.prec, d.W, d.N, d.X, d.ncol, d.c0, d.nbk, d.nblk, d.cplx);
@@ -237,6 +239,8 @@ struct afqmc_ctx {
   // free projection (Section "Free projection AFQMC"): no force-bias shift, complex weights
   // w e^{i phi} (phases in L.wph), no phaseless projection and no comb
   bool free_proj = false;
+  // E_T replaced at each comb by the running mixed estimate (device words L.etr)
+  bool et_update = false;
   tc::TcState tcs;
   CvState cv;
   int tile_cap = 4;          // largest CUDA-core GEMM register tile (4: 64-wide block tiles, 2: 32, 1: 16)
@@ -384,6 +388,7 @@ OverlapArgs<R> overlap_args(afqmc_ctx* c, int mode) {
   a.xxbar = c->at<double2>(c->L.xxbar);
   a.dt = c->dt; a.e_trial = c->e_trial; a.e_c = c->e_c;
   a.eshift = std::exp(c->dt * (c->e_trial - c->e_c));
+  a.etr = (mode == 1 && c->et_update && !c->free_proj) ? c->at<double>(c->L.etr) : nullptr;
   a.step = mode == 1 ? c->at<unsigned long long>(c->L.step) : nullptr;
   a.wph = (mode == 1 && c->free_proj) ? c->at<double>(c->L.wph) : nullptr;
   for (int s = 0; s < 2; ++s)
@@ -520,10 +525,11 @@ afqmc_status set_smem_limits(const Dims& d) {
 
 // Local energy at the current walkers into eloc and the weighted sums into sums_dev.
 template <typename R>
-afqmc_status energy_cv_impl(afqmc_ctx* c, double* sums_dev, int* slot);
+afqmc_status energy_cv_impl(afqmc_ctx* c, double* sums_dev, int* slot, bool run);
 
+// run: a measurement of the run loop, which also feeds the running sums of E_T when it follows them.
 template <typename R>
-EnergyArgs<R> energy_args(afqmc_ctx* c, double* sums_dev, int* slot) {
+EnergyArgs<R> energy_args(afqmc_ctx* c, double* sums_dev, int* slot, bool run = false) {
   EnergyArgs<R> a{};
   a.N = c->d.N; a.X = c->d.X; a.ncol = c->d.ncol;
   a.smul = c->smul; a.ecore = c->ecore; a.nchunk = c->d.nchunk;
@@ -538,6 +544,7 @@ EnergyArgs<R> energy_args(afqmc_ctx* c, double* sums_dev, int* slot) {
   a.out = sums_dev;
   a.slot = slot;
   a.done = reinterpret_cast<unsigned int*>(c->base + c->L.slot + 64);
+  a.etacc = (run && c->et_update && !c->free_proj) ? c->at<double>(c->L.etr) : nullptr;
   return a;
 }
 
@@ -545,9 +552,9 @@ EnergyArgs<R> energy_args(afqmc_ctx* c, double* sums_dev, int* slot) {
 // step's overlap (not while stage timing is on, which times it on the main stream).
 template <typename R>
 afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bool beside = false,
-                         double* sums_host = nullptr) {
+                         double* sums_host = nullptr, bool run = false) {
   if (c->cv.enabled) {
-    afqmc_status sc = energy_cv_impl<R>(c, sums_dev, slot);
+    afqmc_status sc = energy_cv_impl<R>(c, sums_dev, slot, run);
     if (sc == AFQMC_OK && sums_host)
       CU(cudaMemcpyAsync(sums_host, sums_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return sc;
@@ -578,7 +585,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
   }
   StageTimer te(c, AFQMC_STAGE_ENERGY);
   auto kern = c->d.cplx ? k_energy<R, true> : k_energy<R, false>;
-  kern<<<c->d.W, 256, 0, es>>>(energy_args<R>(c, sums_dev, slot));
+  kern<<<c->d.W, 256, 0, es>>>(energy_args<R>(c, sums_dev, slot, run));
   CHECK_LAUNCH(c);
   if (sums_host) CU(cudaMemcpyAsync(sums_host, sums_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, es));
   if (fork) {
@@ -774,7 +781,7 @@ afqmc_status comb_impl(afqmc_ctx* c) {
   StageTimer timer(c, AFQMC_STAGE_COMB);
   k_comb_plan<<<1, 256, 0, c->stream>>>(d.W, c->seed, c->at<unsigned long long>(c->L.step), c->at<double>(c->L.w),
                                         c->at<double>(c->L.cum), c->at<int>(c->L.src), c->at<double>(c->L.neww),
-                                        c->at<int>(c->L.status));
+                                        c->at<int>(c->L.status), c->et_update ? c->at<double>(c->L.etr) : nullptr);
   CHECK_LAUNCH(c);
   const int pe = d.N * d.ncol;
   if (!c->theta_fresh) {
@@ -1185,6 +1192,7 @@ afqmc_status setup_end(afqmc_ctx* c) {
   CU(cudaMemsetAsync(c->base + c->L.status, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.step, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.slot, 0, 256, c->stream));   // history slot, energy completion counter
+  CU(cudaMemsetAsync(c->base + c->L.etr, 0, 256, c->stream));
   CU(cudaMemsetAsync(c->base + c->L.wph, 0, (size_t)d.W * 8, c->stream));
   k_init_walkers<R><<<296, 256, 0, c->stream>>>(d.W, N, nc, c->at<double>(c->L.phi), c->at<cplx_t<R>>(c->L.psi),
                                                 c->at<double>(c->L.w), cx ? 1 : 0);
@@ -1260,7 +1268,8 @@ afqmc_status graph_step(afqmc_ctx* c, bool energy) {
     afqmc_status st = capture(c, [&]() -> afqmc_status {
       afqmc_status s2;
       if (energy &&
-          (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true)) != AFQMC_OK)
+          (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true, nullptr, true)) !=
+              AFQMC_OK)
         return s2;
       return DISPATCH(c, step_impl);
     }, &c->g_step[v], &c->g_step_k[v]);
@@ -1594,7 +1603,8 @@ afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int
     if (graphs) {
       if ((st = graph_step(ctx, energy)) != AFQMC_OK) return st;
     } else {
-      if (energy && (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true)) != AFQMC_OK) return st;
+      if (energy && (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true, nullptr, true)) != AFQMC_OK)
+        return st;
       if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
     }
     if (energy) { ++used; ++total; }
@@ -1632,7 +1642,7 @@ afqmc_status afqmc_run_async(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_ever
                            cudaMemcpyDeviceToHost, ctx->stream));
     } else {
       if (energy &&
-          (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true, energies_host + 4 * (size_t)total)) !=
+          (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true, energies_host + 4 * (size_t)total, true)) !=
               AFQMC_OK)
         return st;
       if ((st = DISPATCH(ctx, step_impl)) != AFQMC_OK) return st;
@@ -1758,6 +1768,12 @@ afqmc_status afqmc_get_info(afqmc_ctx* ctx, afqmc_info* info) {
   info->nwalkers = ctx->d.W; info->restricted = ctx->d.restricted ? 1 : 0; info->prec = ctx->d.prec;
   info->reserved = 0;
   info->step = ctx->host_step;
+  if (ctx->et_update) {   // E_T lives on the device, where each comb updates it
+    double et;
+    CU(cudaMemcpyAsync(&et, ctx->base + ctx->L.etr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->e_trial = et;
+  }
   info->e_var = ctx->e_var; info->e_trial = ctx->e_trial; info->e_core_mf = ctx->e_c;
   info->workspace_bytes = ctx->L.total;
   return AFQMC_OK;
@@ -1767,11 +1783,35 @@ afqmc_status afqmc_set_etrial(afqmc_ctx* ctx, double e_trial) {
   afqmc_status st = check_ctx(ctx);
   if (st != AFQMC_OK) return st;
   if (!std::isfinite(e_trial)) return fail(AFQMC_EINVAL, "e_trial must be finite");
-  if (e_trial != ctx->e_trial) {
+  if (ctx->et_update) {   // the device copy is the one in use (the running sums stay)
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.etr, &e_trial, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  } else if (e_trial != ctx->e_trial) {
     CU(cudaStreamSynchronize(ctx->stream));   // captured graphs hold the old value: rebuild them
     ctx->drop_graphs();
   }
   ctx->e_trial = e_trial;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_etrial_update(afqmc_ctx* ctx, int32_t enable) {
+  afqmc_status st = check_ctx(ctx);
+  if (st != AFQMC_OK) return st;
+  if (!enable && !ctx->et_update) return AFQMC_OK;
+  CU(cudaStreamSynchronize(ctx->stream));   // captured graphs hold the other form's arguments
+  if (ctx->et_update) {                     // keep the value reached so far
+    double et;
+    CU(cudaMemcpyAsync(&et, ctx->base + ctx->L.etr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->e_trial = et;
+  }
+  ctx->drop_graphs();
+  if (enable) {   // E_T from its current value, the running sums from zero
+    const double words[3] = {ctx->e_trial, 0.0, 0.0};
+    CU(cudaMemcpyAsync(ctx->base + ctx->L.etr, words, sizeof(words), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  ctx->et_update = enable != 0;
   return AFQMC_OK;
 }
 
@@ -2144,7 +2184,7 @@ extern "C" afqmc_status afqmc_comb_plan_noalloc(const double* w, int32_t nwalker
   k_store_step<<<1, 1, 0, s>>>(step_word, (unsigned long long)step);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc launch: %s", cudaGetErrorString(e));
-  k_comb_plan<<<1, 256, 0, s>>>(nwalkers, seed, step_word, w, cum, src, neww, status);
+  k_comb_plan<<<1, 256, 0, s>>>(nwalkers, seed, step_word, w, cum, src, neww, status, nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(AFQMC_ECUDA, "afqmc_comb_plan_noalloc launch: %s", cudaGetErrorString(e));
   return AFQMC_OK;
@@ -2299,7 +2339,7 @@ afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
                             tc::NormalsJob{c->at<double>(c->L.x), c->seed, c->at<unsigned long long>(c->L.step), d.W,
                                            d.X}};
     ps[i] = tc::GroupPropSystem{&c->tcs, tcbuf, c->at<float2>(c->L.psi), c->at<double>(c->L.w), status};
-    ea[i] = energy_args<R>(c, c->at<double>(c->L.hist), c->at<int>(c->L.slot));
+    ea[i] = energy_args<R>(c, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true);
     fa[i] = field_args<R>(c);
     oa[i] = overlap_args<R>(c, 1);
     stage[i] = overlap_stage(d) ? 1 : 0;
@@ -2310,7 +2350,7 @@ afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
                         c->at<int>(c->L.src), c->at<double>(c->L.neww), status, c->at<float2>(c->L.psi),
                         c->at<float2>(c->L.psi_tmp), c->at<float2>(c->L.thetaT), c->at<float2>(c->L.th_tmp),
                         c->at<double2>(c->L.logO), c->at<double2>(c->L.logO_tmp), c->at<double>(c->L.w),
-                        c->at<double>(c->L.w_tmp)};
+                        c->at<double>(c->L.w_tmp), c->et_update ? c->at<double>(c->L.etr) : nullptr};
     za[i] = ZeroArgs{c->at<float2>(c->L.vbias), (size_t)d.W * d.X};
     x.max_vbias = std::max(x.max_vbias, (size_t)d.W * d.X);
     first[i + 1] = first[i] + d.W;
@@ -2553,7 +2593,8 @@ afqmc_status batch_exec(afqmc_batch* b, int key, bool energy, bool qr, bool comb
     afqmc_status st = capture_graph(c, [&]() -> afqmc_status {
       afqmc_status s2;
       if (energy &&
-          (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true)) != AFQMC_OK)
+          (s2 = DISPATCH(c, energy_impl, c->at<double>(c->L.hist), c->at<int>(c->L.slot), true, nullptr, true)) !=
+              AFQMC_OK)
         return s2;
       if ((s2 = DISPATCH(c, step_impl)) != AFQMC_OK) return s2;
       if (qr && (s2 = DISPATCH(c, qr_impl)) != AFQMC_OK) return s2;

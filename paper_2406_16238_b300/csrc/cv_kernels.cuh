@@ -212,10 +212,12 @@ __global__ void __launch_bounds__(256) k_cv_walker(int N, int X, int ncol, doubl
 }
 
 // Estimator sums of the control-variate form:
-// out = {ENumer_CV, EDenom, E1Body, ENumer_CV - E1Body}, fixed reduction order, optional history slot.
+// out = {ENumer_CV, EDenom, E1Body, ENumer_CV - E1Body}, fixed reduction order, optional history slot
+// and running sums of E_T (etacc[1], etacc[2]).
 __global__ void __launch_bounds__(256) k_cv_sums(int W, int m, int nchunk, const double* w, const double* a,
                                                  const double* e1, const float* f, const int* sel,
-                                                 const double2* exch_part, double* out, int* slot) {
+                                                 const double2* exch_part, double* out, int* slot,
+                                                 double* etacc) {
   __shared__ double red[32];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, sc = 0.0;
   for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -242,6 +244,10 @@ __global__ void __launch_bounds__(256) k_cv_sums(int W, int m, int nchunk, const
     const double num = s0 - ((double)W / (double)m) * sc;
     o[0] = num; o[1] = s1; o[2] = s2; o[3] = num - s2;
     if (slot) *slot += 1;
+    if (etacc) {   // running sums of E_T
+      etacc[1] += num;
+      etacc[2] += s1;
+    }
   }
 }
 

@@ -165,6 +165,7 @@ struct OverlapArgs {
   const double2* xxbar;           // [W]
   double dt, e_trial, e_c;
   double eshift;                  // exp(dt (E_T - E_c)), the same factor for every walker
+  const double* etr;              // non-null: E_T = etr[0] on the device (updated at each comb), eshift unused
   unsigned long long* step;       // incremented once (mode 1) if non-null
   double* wph;                    // free projection (mode 1): weight phases [W]; null: phaseless
   // optional: Theta^T also as the tensor-core exchange operand of each spin block s, rows
@@ -332,6 +333,7 @@ struct EnergyArgs {
   double* out;
   int* slot;
   unsigned int* done;
+  double* etacc;              // non-null: ENumer and EDenom also added to etacc[1], etacc[2] (running sums of E_T)
 };
 
 template <typename R, bool CH>
@@ -444,6 +446,10 @@ __device__ __forceinline__ void energy_walker(const EnergyArgs<R> A, const int w
     double* o = slot ? out + 4 * (size_t)(*slot) : out;
     o[0] = red[0]; o[1] = red[1]; o[2] = red[2]; o[3] = red[3];
     if (slot) *slot += 1;
+    if (A.etacc) {
+      A.etacc[1] += red[0];
+      A.etacc[2] += red[1];
+    }
     *done = 0u;
   }
 }
@@ -643,8 +649,11 @@ __global__ void __launch_bounds__(256) k_draw_normals(unsigned long long seed, u
 // Comb population control.  One CTA: sequential (index-order) binary64 prefix
 // of the weights, xi from Philox stream 1, tooth search.  Then a gather.
 // ============================================================================
+// et (optional): E_T and its running sums {E_T, sum ENumer, sum EDenom}; E_T becomes the running mixed
+// estimate sum ENumer / sum EDenom once a measurement has been made.
 __device__ __forceinline__ void comb_plan(int W, unsigned long long seed, const unsigned long long* step,
-                                          const double* w, double* cum, int* src, double* neww, int* status) {
+                                          const double* w, double* cum, int* src, double* neww, int* status,
+                                          double* et = nullptr) {
   constexpr int kTile = 2048;
   __shared__ double ws[kTile];
   __shared__ double total_s, xi_s;
@@ -691,6 +700,7 @@ __device__ __forceinline__ void comb_plan(int W, unsigned long long seed, const 
     xi_s = uniform52(r.x, r.y);
     if (!ok_s) atomicOr(status, kStatusNoWalkers);
     *neww = ok_s ? t / (double)W : -1.0;
+    if (et && et[2] > 0.0) et[0] = et[1] / et[2];
   }
   __syncthreads();
   const double total = total_s, xi = xi_s;
@@ -709,8 +719,8 @@ __device__ __forceinline__ void comb_plan(int W, unsigned long long seed, const 
 
 __global__ void __launch_bounds__(256) k_comb_plan(int W, unsigned long long seed, const unsigned long long* step,
                                                    const double* w, double* cum, int* src, double* neww,
-                                                   int* status) {
-  comb_plan(W, seed, step, w, cum, src, neww, status);
+                                                   int* status, double* et) {
+  comb_plan(W, seed, step, w, cum, src, neww, status, et);
 }
 
 // The comb of several systems (one launch per phase): the plans (one block per system), the gather of
@@ -732,11 +742,12 @@ struct CombArgs {
   double2* logO_tmp;
   double* w;
   double* w_tmp;
+  double* et;
 };
 template <typename R>
 __global__ void __launch_bounds__(256) k_comb_plan_group(const CombArgs<R>* __restrict__ args) {
   const CombArgs<R> a = args[blockIdx.x];
-  comb_plan(a.W, a.seed, a.step, a.w, a.cum, a.src, a.neww, a.status);
+  comb_plan(a.W, a.seed, a.step, a.w, a.cum, a.src, a.neww, a.status, a.et);
 }
 
 template <typename R>
@@ -1530,13 +1541,14 @@ __device__ __forceinline__ void overlap_walker(const OverlapArgs<R> a, const int
     const double2 xx = a.xxbar[w];
     const double ls_re = lo_new.x - lo_old.x + c.x;
     const double theta = lo_new.y - lo_old.y + c.y;
+    const double eshift = a.etr ? exp(a.dt * (a.etr[0] - a.e_c)) : a.eshift;
     double wn;
     if (a.wph) {   // free projection: the whole ratio (O'/O) e^{c_mf}, its phase kept with the weight
-      wn = a.w[w] * exp(ls_re) * a.eshift;
+      wn = a.w[w] * exp(ls_re) * eshift;
       a.wph[w] = wrap_angle(a.wph[w] + theta);
     } else {
       const double li_re = ls_re + xx.x;
-      wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * a.eshift;
+      wn = a.w[w] * exp(li_re) * fmax(0.0, cos(theta)) * eshift;
     }
     if (!isfinite(wn)) {
       wn = 0.0;

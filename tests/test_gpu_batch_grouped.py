@@ -30,8 +30,11 @@ def _contexts(probs, prec, nw=16):
                       prec=prec) for i, p in enumerate(probs)]
 
 
-def _run(probs, prec, mode, nsteps=11, groups=0, zero=None, branches=0):
+def _run(probs, prec, mode, nsteps=11, groups=0, zero=None, branches=0, et_out=None):
     ctxs = _contexts(probs, prec)
+    if et_out is not None:   # E_T follows the running estimate
+        for c in ctxs:
+            c.set_etrial_update(True)
     if zero is not None:   # walkers of weight zero are frozen (skipped by every grouped kernel)
         for c in ctxs:
             psi, _, w, step = c.get_walkers()
@@ -42,6 +45,8 @@ def _run(probs, prec, mode, nsteps=11, groups=0, zero=None, branches=0):
     assert b.mode() == mode
     e = b.run(nsteps, energy_every=1, reortho_every=3, comb_every=5)
     walkers = [c.get_walkers() for c in ctxs]
+    if et_out is not None:
+        et_out.extend(c.e_trial for c in ctxs)
     b.close()
     for c in ctxs:
         c.close()
@@ -145,3 +150,18 @@ def test_complex_and_free_projection_contexts_batch_as_graphs():
     b.close()
     for c in (c1, c2):
         c.close()
+
+
+def test_grouped_trial_energy_update(systems):
+    """E_T following the running estimate in grouped launches agrees with the per-system graphs
+    (each system's own sums and comb), and moves off E_var."""
+    etg, etr = [], []
+    eg, wg = _run(systems, "bf16x3", "grouped", et_out=etg)
+    er, wr = _run(systems, "bf16x3", "graphs", et_out=etr)
+    assert np.max(np.abs(eg[:, :, 0] / eg[:, :, 1] - er[:, :, 0] / er[:, :, 1])) < 2e-5
+    for (_, _, w_g, _), (_, _, w_r, _) in zip(wg, wr):
+        assert np.allclose(w_g, w_r, rtol=1e-3, atol=0)
+    for a, b, e in zip(etg, etr, er):
+        assert abs(a - b) < 2e-5
+        mix = np.sum(e[:10, 0]) / np.sum(e[:10, 1])   # the last comb, after step 10 (comb every 5)
+        assert abs(b - mix) < 1e-9 * abs(mix)

@@ -131,6 +131,42 @@ def test_trajectory_parity_small_config():
     assert np.allclose(psi_g, wk.psi, atol=1e-9)
 
 
+def test_trial_energy_update_parity():
+    """E_T replaced at each comb by the running mixed estimate (FP64 form) against the oracle, run
+    in two calls; the estimator sums' EDenom column and the weights carry every shift applied, E_T
+    the last estimate.  Direct launches give the same numbers as the captured graphs, and the
+    mixed energies are those of a fixed E_T."""
+    prob = config_small()
+    nw, seed, n1, n2 = 64, 240616239, 23, 22
+    st = _setup(prob)
+    te = orc.TrialEnergy(st.evar)
+    ha, wka = orc.run_phaseless(st, prob.psiT, nw, n1, seed, reortho_every=5, comb_every=10, trial_energy=te)
+    hb, wkb = orc.run_phaseless(st, prob.psiT, nw, n2, seed, reortho_every=5, comb_every=10, trial_energy=te,
+                                walkers=wka)
+    hist = np.vstack([ha, hb])
+    out = []
+    for graphs in (True, False):
+        ctx = _ctx(prob, nw, seed=seed)
+        ctx.set_graphs(graphs)
+        assert ctx.e_trial == ctx.info()["e_var"]
+        ctx.set_etrial_update(True)
+        e = np.vstack([ctx.run(n1, energy_every=1, reortho_every=5, comb_every=10),
+                       ctx.run(n2, energy_every=1, reortho_every=5, comb_every=10)])
+        out.append((e, ctx.get_walkers()[2], ctx.e_trial))
+        ctx.close()
+    (e_gpu, w_gpu, et_gpu), (e_dir, w_dir, et_dir) = out
+    assert np.array_equal(e_gpu, e_dir) and np.array_equal(w_gpu, w_dir) and et_gpu == et_dir
+    assert np.max(np.abs(e_gpu[:, 0] / e_gpu[:, 1] - hist[:, 0] / hist[:, 1]) / np.abs(hist[:, 0] / hist[:, 1])) < 1e-10
+    assert np.allclose(e_gpu[:, 1], hist[:, 1], rtol=1e-10, atol=0)
+    assert np.allclose(w_gpu, wkb.w, rtol=1e-10, atol=0)
+    assert abs(et_gpu - te.et) < 1e-10 * abs(te.et)
+    assert te.et != st.evar
+    fixed = _ctx(prob, nw, seed=seed)
+    e_fix = fixed.run(n1 + n2, energy_every=1, reortho_every=5, comb_every=10)
+    assert np.allclose(e_fix[:, 0] / e_fix[:, 1], e_gpu[:, 0] / e_gpu[:, 1], rtol=1e-12, atol=0)
+    fixed.close()
+
+
 def test_qr_parity():
     prob = PROBLEMS["uhf_N13_3_2"]()
     st = _setup(prob)

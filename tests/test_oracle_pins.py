@@ -334,6 +334,44 @@ def test_energy_shift_invariance_and_trajectory_sanity():
     assert np.all(np.isfinite(e1))
 
 
+def test_trial_energy_follows_the_running_estimate():
+    """E_T replaced at each comb by the running mixed estimate (R4 option): since the factor
+    exp(dt (E_T - E_c)) multiplies every weight alike and the comb is scale-equivariant, the
+    energies and walkers equal those of a fixed E_T, and the weights differ by exactly
+    prod_t exp(dt (E_T(t) - E_var)) with E_T(t) rebuilt here from the measured sums."""
+    prob = tiny_problem(4, 2, 2, naux=6, seed=7)
+    dt = 0.01
+    st = orc.build_setup(prob.h1e, prob.chol, prob.ecore, 2, 2, prob.psiT, dt)
+    nsteps, comb = 35, 10
+    h0, wk0 = orc.run_phaseless(st, prob.psiT, 16, nsteps, seed=99, reortho_every=5, comb_every=comb)
+    te = orc.TrialEnergy(st.evar)
+    h1, wk1 = orc.run_phaseless(st, prob.psiT, 16, nsteps, seed=99, reortho_every=5, comb_every=comb,
+                                trial_energy=te)
+    assert np.allclose(h1[:, 0] / h1[:, 1], h0[:, 0] / h0[:, 1], rtol=1e-13, atol=0)
+    assert np.allclose(wk1.psi, wk0.psi, atol=1e-13)
+    # E_T in force during step t: E_var until the first comb (after step comb-1), then the
+    # mixed estimate over the measurements at the starts of steps 0 .. c-1 of the last comb at c
+    # (the sums of this run: their weight totals carry the shifts applied so far)
+    et = np.full(nsteps, st.evar)
+    for t in range(nsteps):
+        c = (t // comb) * comb
+        if c > 0:
+            et[t] = np.sum(h1[:c, 0]) / np.sum(h1[:c, 1])
+    log_ratio = dt * np.sum(et - st.evar)
+    assert abs(te.et - np.sum(h1[:30, 0]) / np.sum(h1[:30, 1])) < 1e-12 * abs(te.et)
+    assert np.allclose(h1[:, 1], h0[:, 1] * np.exp(dt * np.cumsum(np.r_[0.0, et[:-1] - st.evar])),
+                       rtol=1e-11, atol=0)
+    assert np.allclose(wk1.w, wk0.w * math.exp(log_ratio), rtol=1e-11, atol=0)
+    # the same run in two calls continues the state (sums and E_T carried over)
+    te2 = orc.TrialEnergy(st.evar)
+    ha, wka = orc.run_phaseless(st, prob.psiT, 16, 17, seed=99, reortho_every=5, comb_every=comb,
+                                trial_energy=te2)
+    hb, wkb = orc.run_phaseless(st, prob.psiT, 16, nsteps - 17, seed=99, reortho_every=5,
+                                comb_every=comb, trial_energy=te2, walkers=wka)
+    assert np.array_equal(np.vstack([ha, hb]), h1)
+    assert np.array_equal(wkb.w, wk1.w) and te2.et == te.et
+
+
 @pytest.mark.slow
 def test_free_projection_converges_to_fci():
     """Free projection (Section "Free projection AFQMC") reaches E_FCI within error + Trotter bias."""
