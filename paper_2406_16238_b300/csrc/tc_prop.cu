@@ -15,8 +15,10 @@
 // Roles: warp 16 (one thread) loads F once and each walker's V planes by TMA and issues the MMAs;
 // warps 0-15 read the accumulator, warp w covering lanes 32 (w % 4) .. + 31 (rows p) and a
 // quarter of the chunk's columns: it keeps its part of row p of acc in registers and writes the
-// matching entries of column k = p of the next B operand (hi and lo) into shared memory.  V of the
-// next walker is fetched as soon as the last Taylor product of the current one has completed.
+// matching entries of column k = p of the next B operand (hi and lo) into shared memory; the
+// propagated chunk leaves through the B buffer, staged so that consecutive threads write
+// consecutive addresses of psi.  V of the next walker is fetched as soon as the last Taylor
+// product of the current one has completed.
 // Rows p >= N of D (padding, and rows npad .. 127 which the MMA reads from the following buffer)
 // are never used: those threads write zeros into B.  Every wait is bounded.
 #include <cuda_bf16.h>
@@ -59,21 +61,45 @@ __device__ __forceinline__ void st_bf16(uint8_t* base, uint32_t off, __nv_bfloat
 // term (ur, ui).  B is K-major with 128-byte swizzling, two 64-wide K atoms of 4 CWP rows; the
 // slice owns hi rows 2 j0 + jj (real parts) and 2 j0 + SW + jj (imaginary parts), and the lo rows
 // 2 CWP further on, so its accumulator columns are consecutive.
+// The byte offsets depend only on the thread.  Where 2 j0 is a multiple of 8 (SW = 4, 8) the rows
+// of the slice have compile-time swizzle phases (n & 7) and each offset is two operations from a
+// per-thread base; otherwise (SW = 2, 6) the 2 SW offsets are formed once and kept.
 template <int CWP, int SW>
-__device__ __forceinline__ void write_b(uint8_t* b, int p, int j0, const float* ur, const float* ui) {
-  constexpr int ab = 4 * CWP * 128;
+struct BOffsets {
+  static constexpr bool kPhase = (2 * SW) % 8 == 0;
+  static constexpr int ab = 4 * CWP * 128;
+  uint32_t o[kPhase ? 2 : 2 * SW];
+  __device__ __forceinline__ BOffsets(int p, int j0) {
+    if constexpr (kPhase) {
+      o[0] = (uint32_t)((p >> 6) * ab + ((2 * j0) >> 3) * 1024 + ((p & 7) << 1));
+      o[1] = (uint32_t)((p & 63) >> 3);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) {
+        o[jj] = sw_off(2 * j0 + jj, p, ab);
+        o[SW + jj] = sw_off(2 * j0 + SW + jj, p, ab);
+      }
+    }
+  }
+  // row 2 j0 + c of the slice (c = jj for real parts, SW + jj for imaginary parts)
+  __device__ __forceinline__ uint32_t at(int c) const {
+    if constexpr (kPhase) return o[0] + (uint32_t)((c >> 3) * 1024 + (c & 7) * 128) + ((o[1] ^ (uint32_t)(c & 7)) << 4);
+    else return o[c];
+  }
+};
+
+template <int CWP, int SW>
+__device__ __forceinline__ void write_b(uint8_t* b, const BOffsets<CWP, SW>& bo, const float* ur, const float* ui) {
   constexpr uint32_t lo = 256u * CWP;   // 2 CWP rows further (2 CWP is a multiple of 8)
 #pragma unroll
-  for (int jj = 0; jj < SW; ++jj) {
-    const __nv_bfloat16 rh = __float2bfloat16_rn(ur[jj]);
-    const __nv_bfloat16 rl = __float2bfloat16_rn(ur[jj] - __bfloat162float(rh));
-    const __nv_bfloat16 ih = __float2bfloat16_rn(ui[jj]);
-    const __nv_bfloat16 il = __float2bfloat16_rn(ui[jj] - __bfloat162float(ih));
-    const uint32_t o_r = sw_off(2 * j0 + jj, p, ab), o_i = sw_off(2 * j0 + SW + jj, p, ab);
-    st_bf16(b, o_r, rh);
-    st_bf16(b, o_r + lo, rl);
-    st_bf16(b, o_i, ih);
-    st_bf16(b, o_i + lo, il);
+  for (int jj = 0; jj < SW; ++jj) {   // (real, imaginary) rounded as one pair
+    const __nv_bfloat162 h = __floats2bfloat162_rn(ur[jj], ui[jj]);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(ur[jj] - __low2float(h), ui[jj] - __high2float(h));
+    const uint32_t o_r = bo.at(jj), o_i = bo.at(SW + jj);
+    st_bf16(b, o_r, __low2bfloat16(h));
+    st_bf16(b, o_r + lo, __low2bfloat16(l));
+    st_bf16(b, o_i, __high2bfloat16(h));
+    st_bf16(b, o_i + lo, __high2bfloat16(l));
   }
 }
 
@@ -143,241 +169,45 @@ __device__ __forceinline__ void load_d(uint32_t trow, int j0, float* dr, float* 
 constexpr int kEpiWarps = 16;                 // 4 lane quadrants x 4 column slices
 constexpr int kPropThreads = 32 * kEpiWarps + 32;
 
-template <int CWP>
-__global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_constant__ CUtensorMap mapV,
-                                                             const __grid_constant__ CUtensorMap mapF,
-                                                             const PropTcParams a) {
-  constexpr int SW = CWP / 4;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + a.off_bar);
-  uint64_t* bar_v = bars;
-  uint64_t* bar_f = bars + 1;
-  uint64_t* bar_mma = bars + 2;
-  uint64_t* bar_b = bars + 3;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    mbar_init(bar_v, 1);
-    mbar_init(bar_f, 1);
-    mbar_init(bar_mma, 1);
-    mbar_init(bar_b, kEpiWarps);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == kEpiWarps) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(a.tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  auto next_live = [&](int from) {
-    for (int k = from; k < a.W; k += gridDim.x)
-      if (a.w[k] != 0.0) return k;
-    return a.W;
-  };
-
-  if (warp == kEpiWarps) {
-    if (lane == 0) {   // TMA + MMA issue
-      const uint32_t s0 = smem_u32(sm);
-      const uint32_t vatom = (uint32_t)a.npad * 128u, batom = 4u * CWP * 128u;
-      const uint32_t idesc_w = idesc_bf16(4 * CWP), idesc_n = idesc_bf16(2 * CWP);
-      // descriptors are linear in the address: desc(base + off) = desc(base) + off / 16
-      const uint64_t dvhi = sw128_desc(s0), dvlo = sw128_desc(s0 + (uint32_t)a.off_vlo);
-      const uint64_t dfhi = sw128_desc(s0 + (uint32_t)a.off_fhi), dflo = sw128_desc(s0 + (uint32_t)a.off_flo);
-      const uint64_t db = sw128_desc(s0 + (uint32_t)a.off_b);
-      auto issue_v = [&](int wk) {
-        mbar_expect_tx(bar_v, 8u * vatom);
-        for (int pl = 0; pl < 4; ++pl)
-          for (int at = 0; at < 2; ++at) {
-            const uint32_t dst = (pl < 2 ? 0u : (uint32_t)a.off_vlo) + (uint32_t)((pl & 1) * 2 + at) * vatom;
-            tma_load_2d(sm + dst, &mapV, bar_v, 64 * at, (wk * 4 + pl) * a.npad);
-          }
-      };
-      // F: D1 = F t.  V: D1 = Re V t (A atoms 0, 1), D2 = Im V t (A atoms 2, 3).
-      auto product = [&](bool isv) {
-        const uint64_t ah = isv ? dvhi : dfhi, al = isv ? dvlo : dflo;
-        for (int h = 0; h < (isv ? 2 : 1); ++h) {
-          const uint32_t d = tmem + (uint32_t)(h * 4 * CWP);
-          for (int ks = 0; ks < a.nk; ++ks) {
-            const uint32_t ko = (uint32_t)(ks & 3) * 32u;
-            const uint64_t ao = ((uint32_t)(2 * h + (ks >> 2)) * vatom + ko) >> 4;
-            const uint64_t bo = ((uint32_t)(ks >> 2) * batom + ko) >> 4;
-            umma_bf16(d, ah + ao, db + bo, idesc_w, ks > 0 ? 1u : 0u);   // A hi [B hi; B lo]
-            umma_bf16(d, al + ao, db + bo, idesc_n, 1u);                 // A lo B hi
-          }
-        }
-        umma_commit(bar_mma);
-      };
-      bool go = true;
-      uint32_t ph_b = 0, ph_v = 0;
-      int wk = next_live(blockIdx.x);
-      if (wk < a.W) {
-        mbar_expect_tx(bar_f, 4u * vatom);
-        for (int pl = 0; pl < 2; ++pl)
-          for (int at = 0; at < 2; ++at)
-            tma_load_2d(sm + (pl ? a.off_flo : a.off_fhi) + at * vatom, &mapF, bar_f, 64 * at, pl * a.npad);
-        issue_v(wk);
-      }
-      bool f_ready = false;
-      while (wk < a.W && go) {
-        const int nxt = next_live(wk + gridDim.x);
-        for (int ch = 0; ch < a.nch && go; ++ch) {
-          if (!mbar_wait(bar_b, ph_b, abort_flag)) { go = false; break; }
-          ph_b ^= 1u;
-          if (!f_ready) {
-            if (!mbar_wait(bar_f, 0, abort_flag)) { go = false; break; }
-            f_ready = true;
-          }
-          tc_fence_after();
-          product(false);   // F psi
-          for (int k = 1; k <= a.order && go; ++k) {
-            if (!mbar_wait(bar_b, ph_b, abort_flag)) { go = false; break; }
-            ph_b ^= 1u;
-            if (ch == 0 && k == 1) {
-              if (!mbar_wait(bar_v, ph_v, abort_flag)) { go = false; break; }
-              ph_v ^= 1u;
-              if (nxt < a.W)   // the next walker's V into L2 now, into shared memory later
-                for (int pl = 0; pl < 4; ++pl)
-                  for (int at = 0; at < 2; ++at) tma_prefetch_l2_2d(&mapV, 64 * at, (nxt * 4 + pl) * a.npad);
-            }
-            tc_fence_after();
-            product(true);   // V t_{k-1} / k
-          }
-          if (!go) break;
-          if (!mbar_wait(bar_b, ph_b, abort_flag)) { go = false; break; }
-          ph_b ^= 1u;
-          if (ch == a.nch - 1 && nxt < a.W) issue_v(nxt);   // every V product of this walker has completed
-          tc_fence_after();
-          product(false);   // F acc
-        }
-        wk = nxt;
-      }
-      if (!go) {
-        atomicOr(a.status, kStatusTimeout);
-        *abort_flag = 1;
-      }
-    }
-  } else {   // epilogue warp: lanes 32 (warp % 4) .. + 31, columns j0 .. j0 + SW - 1 of the chunk
-    const int quad = warp & 3, j0 = (warp >> 2) * SW;
-    const int p = 32 * quad + lane;
-    const bool row = p < a.N;
-    const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
-    uint8_t* bsm = sm + a.off_b;
-    uint32_t ph_m = 0;
-    bool go = true;
-    float accr[SW], acci[SW], dr[SW], di[SW];
-    float2 nxv[SW];   // this thread's psi slice of the next (walker, chunk), loaded one item ahead
-    auto load_slice = [&](int w_, int c_) {
-      const int c0 = c_ * a.cw, cwn = min(a.cw, a.ncol - c0);
-      const float2* src = a.psi + ((size_t)w_ * a.N + (row ? p : 0)) * a.ncol + c0;
-#pragma unroll
-      for (int jj = 0; jj < SW; ++jj) nxv[jj] = (row && j0 + jj < cwn) ? src[j0 + jj] : make_float2(0.f, 0.f);
-    };
-    int wk = next_live(blockIdx.x), ch = 0;
-    if (wk < a.W) load_slice(wk, 0);
-    while (wk < a.W && go) {
-      const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
-      float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol + c0;
-#pragma unroll
-      for (int jj = 0; jj < SW; ++jj) {
-        accr[jj] = dr[jj] = nxv[jj].x;
-        acci[jj] = di[jj] = nxv[jj].y;
-      }
-      int nwk = wk, nch = ch + 1;
-      if (nch == a.nch) {
-        nch = 0;
-        nwk = next_live(wk + gridDim.x);
-      }
-      if (nwk < a.W) load_slice(nwk, nch);   // lands while this item's products run
-      write_b<CWP, SW>(bsm, p, j0, dr, di);
-      signal_b(bar_b, lane);
-      if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
-      ph_m ^= 1u;
-      load_d<CWP, SW, false>(trow, j0, dr, di);   // F psi
-#pragma unroll
-      for (int jj = 0; jj < SW; ++jj) {   // t_0 = psi + F psi
-        accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
-        acci[jj] = row ? acci[jj] + di[jj] : 0.f;
-      }
-      write_b<CWP, SW>(bsm, p, j0, accr, acci);
-      signal_b(bar_b, lane);
-      for (int k = 1; k <= a.order; ++k) {
-        if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
-        ph_m ^= 1u;
-        load_d<CWP, SW, true>(trow, j0, dr, di);   // t_k
-        const float s = 1.f / (float)(k + 1);
-#pragma unroll
-        for (int jj = 0; jj < SW; ++jj) {
-          const float tr = row ? dr[jj] : 0.f, ti = row ? di[jj] : 0.f;
-          accr[jj] += tr;
-          acci[jj] += ti;
-          dr[jj] = tr * s;   // next operand t_k / (k + 1)
-          di[jj] = ti * s;
-        }
-        if (k < a.order) write_b<CWP, SW>(bsm, p, j0, dr, di);
-        else write_b<CWP, SW>(bsm, p, j0, accr, acci);
-        signal_b(bar_b, lane);
-      }
-      if (!go) break;
-      if (!(go = warp_wait(bar_mma, ph_m, abort_flag, lane))) break;
-      ph_m ^= 1u;
-      load_d<CWP, SW, false>(trow, j0, dr, di);   // F acc
-#pragma unroll
-      for (int jj = 0; jj < SW; ++jj)
-        if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
-      wk = nwk;
-      ch = nch;
-    }
-    if (!go && lane == 0) {
-      atomicOr(a.status, kStatusTimeout);
-      *abort_flag = 1;
-    }
-  }
-  if (threadIdx.x == 0 && *abort_flag) {   // let in-flight copies and MMAs drain before freeing tensor memory
-    const unsigned long long t0 = global_ns();
-    while (global_ns() - t0 < 2000000ull) {
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == kEpiWarps)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
-}
-
-// ---------------------------------------------------------------------------------------------
-// Grouped small form: one launch over the walkers of several systems (N <= 128).  CTA b takes the
-// walkers [cta_first[b], cta_first[b + 1]) of the launch's list (the systems in turn; contiguous
-// ranges balanced by cost on the host, so a CTA rarely changes system).  Each system keeps its own
-// shared-memory layout and operand width (CWP, dispatched per walker); the mbarriers sit past the
-// largest layout.  On a change of system the MMA thread first waits for the B operand of the new
-// walker, which the epilogue writes only after it has read the previous walker's last product, so
-// no copy into the new layout can meet a product still reading the old one; then it loads the new
-// system's F and the walker's V.  The next walker's V is prefetched only within a system.
-struct PropTcProblem {   // aligned as its tensor maps
-  CUtensorMap mapV, mapF;
-  PropTcParams p;
-  int cwp;
-  int item0;   // the system's walker 0 in the launch's list
+// The walkers one CTA propagates for one system: wk = first, first + stride, ... below end, the
+// walkers of weight zero skipped.
+struct WalkerRun {
+  int first, stride, end;
 };
 
+__device__ __forceinline__ int run_next_live(const double* w, const WalkerRun& r, int from) {
+  for (int k = from; k < r.end; k += r.stride)
+    if (w[k] != 0.0) return k;
+  return r.end;
+}
+
+// The 16 epilogue warps meet (bounded wait); shared-memory writes made before are visible after.
+__device__ __forceinline__ bool epi_sync(uint64_t* bar_e, uint32_t& ph, volatile int* abort_flag, int lane) {
+  __threadfence_block();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar_e);
+  const bool ok = warp_wait(bar_e, ph, abort_flag, lane);
+  ph ^= 1u;
+  return ok;
+}
+
+// TMA and MMA issue (lane 0 of warp 16) for a run of walkers of one system: per walker and column
+// chunk F psi, the Taylor terms V t / k, F acc.  F is loaded at the start of the run and each
+// walker's V one walker ahead (into L2 as soon as the current walker's first V product may start,
+// into shared memory once its last V product has completed).  idle: no product has been issued in
+// this CTA yet, so F and the first V are requested at once; otherwise only after the first
+// walker's B operand is ready (the epilogue writes it after reading the previous walker's last
+// product, so no copy into this system's layout can meet a product still reading another's).
 template <int CWP>
-__device__ __forceinline__ bool prop_mma_item(uint8_t* sm, uint32_t tmem, const PropTcProblem& pr, int wk, int nxt,
-                                              bool fresh, uint64_t* bar_v, uint64_t* bar_f, uint64_t* bar_mma,
-                                              uint64_t* bar_b, volatile int* abort_flag, uint32_t& ph_b,
-                                              uint32_t& ph_v, uint32_t& ph_f) {
-  const PropTcParams a = pr.p;   // a register copy: the MMAs' asm would force reloads of a reference
+__device__ __forceinline__ bool prop_mma_run(uint8_t* sm, uint32_t tmem, const CUtensorMap* mapV,
+                                             const CUtensorMap* mapF, const PropTcParams a, const WalkerRun r,
+                                             bool& idle, uint64_t* bar_v, uint64_t* bar_f, uint64_t* bar_mma,
+                                             uint64_t* bar_b, volatile int* abort_flag, uint32_t& ph_b,
+                                             uint32_t& ph_v, uint32_t& ph_f, int lane) {
+  if (lane != 0) return true;
   const uint32_t s0 = smem_u32(sm);
   const uint32_t vatom = (uint32_t)a.npad * 128u, batom = 4u * CWP * 128u;
-  const uint32_t idesc_w = idesc_bf16(4 * CWP), idesc_n = idesc_bf16(2 * CWP);
+  // descriptors are linear in the address: desc(base + off) = desc(base) + off / 16
   const uint64_t dvhi = sw128_desc(s0), dvlo = sw128_desc(s0 + (uint32_t)a.off_vlo);
   const uint64_t dfhi = sw128_desc(s0 + (uint32_t)a.off_fhi), dflo = sw128_desc(s0 + (uint32_t)a.off_flo);
   const uint64_t db = sw128_desc(s0 + (uint32_t)a.off_b);
@@ -386,9 +216,19 @@ __device__ __forceinline__ bool prop_mma_item(uint8_t* sm, uint32_t tmem, const 
     for (int pl = 0; pl < 4; ++pl)
       for (int at = 0; at < 2; ++at) {
         const uint32_t dst = (pl < 2 ? 0u : (uint32_t)a.off_vlo) + (uint32_t)((pl & 1) * 2 + at) * vatom;
-        tma_load_2d(sm + dst, &pr.mapV, bar_v, 64 * at, (w * 4 + pl) * a.npad);
+        tma_load_2d(sm + dst, mapV, bar_v, 64 * at, (w * 4 + pl) * a.npad);
       }
   };
+  auto issue_f = [&]() {
+    mbar_expect_tx(bar_f, 4u * vatom);
+    for (int pl = 0; pl < 2; ++pl)
+      for (int at = 0; at < 2; ++at)
+        tma_load_2d(sm + (pl ? a.off_flo : a.off_fhi) + at * vatom, mapF, bar_f, 64 * at, pl * a.npad);
+  };
+  const uint32_t idesc_w = idesc_bf16(4 * CWP), idesc_n = idesc_bf16(2 * CWP);
+  // F: D1 = F t.  V: D1 = Re V t (A atoms 0, 1), D2 = Im V t (A atoms 2, 3).  Per 16-wide k-step
+  // A hi [B hi; B lo] (N = 4 CWP) and A lo B hi (N = 2 CWP).  Returns false once another role has
+  // given up (recorded in the status word), so no further product is issued.
   auto product = [&](bool isv) {
     const uint64_t ah = isv ? dvhi : dfhi, al = isv ? dvlo : dflo;
     for (int h = 0; h < (isv ? 2 : 1); ++h) {
@@ -402,65 +242,136 @@ __device__ __forceinline__ bool prop_mma_item(uint8_t* sm, uint32_t tmem, const 
       }
     }
     umma_commit(bar_mma);
-  };
-  for (int ch = 0; ch < a.nch; ++ch) {
-    if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
-    ph_b ^= 1u;
-    if (ch == 0 && fresh) {   // a new system: its F, then this walker's V
-      mbar_expect_tx(bar_f, 4u * vatom);
-      for (int pl = 0; pl < 2; ++pl)
-        for (int at = 0; at < 2; ++at)
-          tma_load_2d(sm + (pl ? a.off_flo : a.off_fhi) + at * vatom, &pr.mapF, bar_f, 64 * at, pl * a.npad);
-      issue_v(wk);
-      if (!mbar_wait(bar_f, ph_f, abort_flag)) return false;
-      ph_f ^= 1u;
+    // An empty asm consuming blockIdx.x: with this nvcc the issue loop compiled with it runs the
+    // propagation in 0.084 ms instead of 0.096 ms at N = 108, W = 640 (measured; the code generation
+    // differs, why is not known).  It has no effect on the results.
+    asm volatile("" ::"r"(blockIdx.x));
+    if (*abort_flag) {   // another role gave up: record it and issue nothing more
+      atomicOr(a.status, kStatusTimeout);
+      return false;
     }
-    tc_fence_after();
-    product(false);   // F psi
-    for (int k = 1; k <= a.order; ++k) {
+    return true;
+  };
+  int wk = run_next_live(a.w, r, r.first);
+  if (wk >= r.end) return true;
+  const bool early = idle;
+  if (early) {
+    issue_f();
+    issue_v(wk);
+  }
+  idle = false;
+  bool first = true;
+  while (wk < r.end) {
+    const int nxt = run_next_live(a.w, r, wk + r.stride);
+    for (int ch = 0; ch < a.nch; ++ch) {
       if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
       ph_b ^= 1u;
-      if (ch == 0 && k == 1) {
-        if (!mbar_wait(bar_v, ph_v, abort_flag)) return false;
-        ph_v ^= 1u;
-        if (nxt >= 0)
-          for (int pl = 0; pl < 4; ++pl)
-            for (int at = 0; at < 2; ++at) tma_prefetch_l2_2d(&pr.mapV, 64 * at, (nxt * 4 + pl) * a.npad);
+      if (first) {
+        if (!early) {
+          issue_f();
+          issue_v(wk);
+        }
+        if (!mbar_wait(bar_f, ph_f, abort_flag)) return false;
+        ph_f ^= 1u;
+        first = false;
       }
       tc_fence_after();
-      product(true);   // V t_{k-1} / k
+      if (!product(false)) return false;   // F psi
+      for (int k = 1; k <= a.order; ++k) {
+        if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
+        ph_b ^= 1u;
+        if (ch == 0 && k == 1) {
+          if (!mbar_wait(bar_v, ph_v, abort_flag)) return false;
+          ph_v ^= 1u;
+          if (nxt < r.end)   // the next walker's V into L2 now, into shared memory later
+            for (int pl = 0; pl < 4; ++pl)
+              for (int at = 0; at < 2; ++at) tma_prefetch_l2_2d(mapV, 64 * at, (nxt * 4 + pl) * a.npad);
+        }
+        tc_fence_after();
+        if (!product(true)) return false;   // V t_{k-1} / k
+      }
+      if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
+      ph_b ^= 1u;
+      if (ch == a.nch - 1 && nxt < r.end) issue_v(nxt);   // every V product of this walker has completed
+      tc_fence_after();
+      if (!product(false)) return false;   // F acc
     }
-    if (!mbar_wait(bar_b, ph_b, abort_flag)) return false;
-    ph_b ^= 1u;
-    if (ch == a.nch - 1 && nxt >= 0) issue_v(nxt);   // every V product of this walker has completed
-    tc_fence_after();
-    product(false);   // F acc
+    wk = nxt;
   }
   return true;
 }
 
-template <int CWP>
-__device__ __forceinline__ bool prop_epi_item(uint8_t* sm, uint32_t tmem, const PropTcParams a, int wk, int warp,
-                                              int lane, uint64_t* bar_mma, uint64_t* bar_b, volatile int* abort_flag,
-                                              uint32_t& ph_m) {
+// Epilogue (warps 0-15) for a run of walkers of one system: warp w covers lanes 32 (w % 4) .. + 31
+// (rows p) and columns j0 .. j0 + SW - 1 of the chunk.  The next item's psi slice is loaded while
+// the current item's products run: into registers (PF), or into L2 and read at the item's start
+// (fewer live registers, for the grouped kernel).  The propagated chunk is staged in the B buffer
+// (free once the last product has completed: N cwn complex entries fit in its 1024 CWP bytes for
+// N <= 128) and written to psi by consecutive threads on consecutive addresses.
+template <int CWP, bool PF>
+__device__ __forceinline__ bool prop_epi_run(uint8_t* sm, uint32_t tmem, const PropTcParams& a, const WalkerRun r,
+                                             int warp, int lane, uint64_t* bar_mma, uint64_t* bar_b, uint64_t* bar_e,
+                                             volatile int* abort_flag, uint32_t& ph_m, uint32_t& ph_e) {
   constexpr int SW = CWP / 4;
   const int quad = warp & 3, j0 = (warp >> 2) * SW;
   const int p = 32 * quad + lane;
   const bool row = p < a.N;
   const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
   uint8_t* bsm = sm + a.off_b;
+  float2* stage = reinterpret_cast<float2*>(bsm);
+  const int tid = threadIdx.x;   // 0 .. 511 over the epilogue warps
+  const BOffsets<CWP, SW> bo(p, j0);
   float accr[SW], acci[SW], dr[SW], di[SW];
-  for (int ch = 0; ch < a.nch; ++ch) {
-    const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
-    float2* prow = a.psi + ((size_t)wk * a.N + (row ? p : 0)) * a.ncol + c0;
+  float2 nxv[PF ? SW : 1];
+  auto slice_src = [&](int w_, int c_) { return a.psi + ((size_t)w_ * a.N + (row ? p : 0)) * a.ncol + c_ * a.cw; };
+  auto load_slice = [&](int w_, int c_) {
+    const int cwn = min(a.cw, a.ncol - c_ * a.cw);
+    const float2* src = slice_src(w_, c_);
 #pragma unroll
-    for (int jj = 0; jj < SW; ++jj) {
-      const float2 v = (row && j0 + jj < cwn) ? prow[j0 + jj] : make_float2(0.f, 0.f);
-      accr[jj] = dr[jj] = v.x;
-      acci[jj] = di[jj] = v.y;
+    for (int jj = 0; jj < SW; ++jj) nxv[PF ? jj : 0] = (row && j0 + jj < cwn) ? src[j0 + jj] : make_float2(0.f, 0.f);
+  };
+  // (wk, ch) the current item, (nwk, nch) the next one: found during the previous item, so the
+  // weight read that finds it is hidden behind a product
+  auto next_item = [&](int w_, int c_, int& w2, int& c2) {
+    w2 = w_;
+    c2 = c_ + 1;
+    if (c2 == a.nch) {
+      c2 = 0;
+      w2 = run_next_live(a.w, r, w_ + r.stride);
     }
-    write_b<CWP, SW>(bsm, p, j0, dr, di);
+  };
+  int wk = run_next_live(a.w, r, r.first), ch = 0, nwk, nch;
+  if (wk < r.end) next_item(wk, ch, nwk, nch);
+  if (PF && wk < r.end) load_slice(wk, 0);
+  while (wk < r.end) {
+    const int c0 = ch * a.cw, cwn = min(a.cw, a.ncol - c0);
+    int nnwk = r.end, nnch = 0;
+    if constexpr (PF) {
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) {
+        accr[jj] = dr[jj] = nxv[jj].x;
+        acci[jj] = di[jj] = nxv[jj].y;
+      }
+    } else {
+      const float2* src = slice_src(wk, ch);
+#pragma unroll
+      for (int jj = 0; jj < SW; ++jj) {
+        const float2 v = (row && j0 + jj < cwn) ? src[j0 + jj] : make_float2(0.f, 0.f);
+        accr[jj] = dr[jj] = v.x;
+        acci[jj] = di[jj] = v.y;
+      }
+    }
+    write_b<CWP, SW>(bsm, bo, dr, di);
     signal_b(bar_b, lane);
+    if (nwk < r.end) {   // lands while this item's products run
+      if constexpr (PF) {
+        load_slice(nwk, nch);
+      } else if (row && j0 == 0) {   // one thread per row: the first and last lines of its segment
+        const float2* src = slice_src(nwk, nch);
+        const int cwn2 = min(a.cw, a.ncol - nch * a.cw);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(src) : "memory");
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(src + cwn2 - 1) : "memory");
+      }
+    }
     if (!warp_wait(bar_mma, ph_m, abort_flag, lane)) return false;
     ph_m ^= 1u;
     load_d<CWP, SW, false>(trow, j0, dr, di);   // F psi
@@ -469,8 +380,9 @@ __device__ __forceinline__ bool prop_epi_item(uint8_t* sm, uint32_t tmem, const 
       accr[jj] = row ? accr[jj] + dr[jj] : 0.f;
       acci[jj] = row ? acci[jj] + di[jj] : 0.f;
     }
-    write_b<CWP, SW>(bsm, p, j0, accr, acci);
+    write_b<CWP, SW>(bsm, bo, accr, acci);
     signal_b(bar_b, lane);
+    next_item(nwk, nch, nnwk, nnch);   // while the first V product runs
     for (int k = 1; k <= a.order; ++k) {
       if (!warp_wait(bar_mma, ph_m, abort_flag, lane)) return false;
       ph_m ^= 1u;
@@ -484,8 +396,8 @@ __device__ __forceinline__ bool prop_epi_item(uint8_t* sm, uint32_t tmem, const 
         dr[jj] = tr * s;   // next operand t_k / (k + 1)
         di[jj] = ti * s;
       }
-      if (k < a.order) write_b<CWP, SW>(bsm, p, j0, dr, di);
-      else write_b<CWP, SW>(bsm, p, j0, accr, acci);
+      if (k < a.order) write_b<CWP, SW>(bsm, bo, dr, di);
+      else write_b<CWP, SW>(bsm, bo, accr, acci);
       signal_b(bar_b, lane);
     }
     if (!warp_wait(bar_mma, ph_m, abort_flag, lane)) return false;
@@ -493,30 +405,51 @@ __device__ __forceinline__ bool prop_epi_item(uint8_t* sm, uint32_t tmem, const 
     load_d<CWP, SW, false>(trow, j0, dr, di);   // F acc
 #pragma unroll
     for (int jj = 0; jj < SW; ++jj)
-      if (row && j0 + jj < cwn) prow[j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
+      if (row && j0 + jj < cwn) stage[p * cwn + j0 + jj] = make_float2(accr[jj] + dr[jj], acci[jj] + di[jj]);
+    if (!epi_sync(bar_e, ph_e, abort_flag, lane)) return false;
+    float2* dst = a.psi + (size_t)wk * a.N * a.ncol + c0;
+    const int n = a.N * cwn;
+    if (cwn == a.ncol) {   // the walker's rows are one contiguous block
+      for (int e = tid; e < n; e += 32 * kEpiWarps) dst[e] = stage[e];
+    } else {
+      for (int e = tid; e < n; e += 32 * kEpiWarps) {
+        const int pp = e / cwn;
+        dst[(size_t)pp * a.ncol + (e - pp * cwn)] = stage[e];
+      }
+    }
+    if (!epi_sync(bar_e, ph_e, abort_flag, lane)) return false;   // the B buffer is free again
+    wk = nwk;
+    ch = nch;
+    nwk = nnwk;
+    nch = nnch;
   }
   return true;
 }
 
-__global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc_group(const PropTcProblem* __restrict__ probs, int nprob,
-                                                                   const int* __restrict__ cta_first, int off_bar,
-                                                                   int tmem_cols) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+// Shared set-up of both small-form kernels: mbarriers, tensor memory.
+struct PropBars {
+  uint64_t *v, *f, *mma, *b, *e;
+  volatile int* abort_flag;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ PropBars prop_begin(uint8_t* sm, int off_bar, int tmem_cols, int warp) {
+  PropBars pb;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + off_bar);
-  uint64_t* bar_v = bars;
-  uint64_t* bar_f = bars + 1;
-  uint64_t* bar_mma = bars + 2;
-  uint64_t* bar_b = bars + 3;
+  pb.v = bars;
+  pb.f = bars + 1;
+  pb.mma = bars + 2;
+  pb.b = bars + 3;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pb.abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  pb.e = bars + 5;
   if (threadIdx.x == 0) {
-    mbar_init(bar_v, 1);
-    mbar_init(bar_f, 1);
-    mbar_init(bar_mma, 1);
-    mbar_init(bar_b, kEpiWarps);
-    *abort_flag = 0;
+    mbar_init(pb.v, 1);
+    mbar_init(pb.f, 1);
+    mbar_init(pb.mma, 1);
+    mbar_init(pb.b, kEpiWarps);
+    mbar_init(pb.e, kEpiWarps);
+    *pb.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kEpiWarps) {
@@ -528,61 +461,13 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc_group(const PropTcP
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const int i0 = cta_first[blockIdx.x], i1 = cta_first[blockIdx.x + 1];
-  auto system_of = [&](int i, int& cur) {
-    while (cur + 1 < nprob && i >= probs[cur + 1].item0) ++cur;
-    return cur;
-  };
-  auto live = [&](int i, int c) { return probs[c].p.w[i - probs[c].item0] != 0.0; };
-  auto give_up = [&]() {
-    for (int c = 0; c < nprob; ++c) atomicOr(probs[c].p.status, kStatusTimeout);
-    *abort_flag = 1;
-  };
-  if (warp == kEpiWarps) {
-    if (lane == 0) {   // TMA + MMA issue
-      uint32_t ph_b = 0, ph_v = 0, ph_f = 0;
-      int cur = 0, loaded = -1;
-      bool go = true;
-      for (int i = i0; i < i1 && go; ++i) {
-        const int c = system_of(i, cur);
-        if (!live(i, c)) continue;
-        const PropTcProblem& pr = probs[c];
-        const int end = min(i1, pr.item0 + pr.p.W);
-        int nxt = -1;   // the next live walker of this system in the CTA's range
-        for (int j = i + 1; j < end; ++j)
-          if (live(j, c)) { nxt = j - pr.item0; break; }
-        const bool fresh = c != loaded;
-        loaded = c;
-        const int wk = i - pr.item0;
-        switch (pr.cwp) {
-          case 8: go = prop_mma_item<8>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
-          case 16: go = prop_mma_item<16>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
-          case 24: go = prop_mma_item<24>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
-          default: go = prop_mma_item<32>(sm, tmem, pr, wk, nxt, fresh, bar_v, bar_f, bar_mma, bar_b, abort_flag, ph_b, ph_v, ph_f); break;
-        }
-      }
-      if (!go) give_up();
-    }
-  } else {   // epilogue warps
-    uint32_t ph_m = 0;
-    int cur = 0;
-    bool go = true;
-    for (int i = i0; i < i1 && go; ++i) {
-      const int c = system_of(i, cur);
-      if (!live(i, c)) continue;
-      const PropTcProblem& pr = probs[c];
-      const int wk = i - pr.item0;
-      switch (pr.cwp) {
-        case 8: go = prop_epi_item<8>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
-        case 16: go = prop_epi_item<16>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
-        case 24: go = prop_epi_item<24>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
-        default: go = prop_epi_item<32>(sm, tmem, pr.p, wk, warp, lane, bar_mma, bar_b, abort_flag, ph_m); break;
-      }
-    }
-    if (!go && lane == 0) give_up();
-  }
-  if (threadIdx.x == 0 && *abort_flag) {   // let in-flight copies and MMAs drain before freeing tensor memory
+  pb.tmem = *tmem_slot;
+  return pb;
+}
+
+// After an abort, in-flight copies and MMAs drain before tensor memory is freed.
+__device__ __forceinline__ void prop_end(const PropBars& pb, int tmem_cols, int warp) {
+  if (threadIdx.x == 0 && *pb.abort_flag) {
     const unsigned long long t0 = global_ns();
     while (global_ns() - t0 < 2000000ull) {
     }
@@ -591,7 +476,92 @@ __global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc_group(const PropTcP
   __syncthreads();
   tc_fence_after();
   if (warp == kEpiWarps)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(pb.tmem), "r"(tmem_cols) : "memory");
+}
+
+template <int CWP>
+__global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc(const __grid_constant__ CUtensorMap mapV,
+                                                             const __grid_constant__ CUtensorMap mapF,
+                                                             const __grid_constant__ PropTcParams a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const PropBars pb = prop_begin(sm, a.off_bar, a.tmem_cols, warp);
+  const WalkerRun r{(int)blockIdx.x, (int)gridDim.x, a.W};
+  bool go = true;
+  if (warp == kEpiWarps) {
+    uint32_t ph_b = 0, ph_v = 0, ph_f = 0;
+    bool idle = true;
+    go = prop_mma_run<CWP>(sm, pb.tmem, &mapV, &mapF, a, r, idle, pb.v, pb.f, pb.mma, pb.b, pb.abort_flag, ph_b,
+                           ph_v, ph_f, lane);
+  } else {
+    uint32_t ph_m = 0, ph_e = 0;
+    go = prop_epi_run<CWP, true>(sm, pb.tmem, a, r, warp, lane, pb.mma, pb.b, pb.e, pb.abort_flag, ph_m, ph_e);
+  }
+  if (!go && lane == 0) {
+    atomicOr(a.status, kStatusTimeout);
+    *pb.abort_flag = 1;
+  }
+  prop_end(pb, a.tmem_cols, warp);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Grouped small form: one launch over the walkers of several systems (N <= 128).  CTA b takes the
+// walkers [cta_first[b], cta_first[b + 1]) of the launch's list (the systems in turn; contiguous
+// ranges balanced by cost on the host, so a CTA rarely changes system), as one run of walkers per
+// system.  Each system keeps its own shared-memory layout and operand width (CWP, dispatched per
+// run); the mbarriers sit past the largest layout.  The next walker's V is prefetched only within
+// a system.
+struct PropTcProblem {   // aligned as its tensor maps
+  CUtensorMap mapV, mapF;
+  PropTcParams p;
+  int cwp;
+  int item0;   // the system's walker 0 in the launch's list
+};
+
+__global__ void __launch_bounds__(kPropThreads, 1) k_prop_tc_group(const PropTcProblem* __restrict__ probs, int nprob,
+                                                                   const int* __restrict__ cta_first, int off_bar,
+                                                                   int tmem_cols) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const PropBars pb = prop_begin(sm, off_bar, tmem_cols, warp);
+  const int i0 = cta_first[blockIdx.x], i1 = cta_first[blockIdx.x + 1];
+  const bool mma = warp == kEpiWarps;
+  bool go = true;
+  {
+    uint32_t ph_b = 0, ph_v = 0, ph_f = 0, ph_m = 0, ph_e = 0;
+    bool idle = true;
+    int cur = 0;
+    for (int i = i0; i < i1 && go;) {
+      while (cur + 1 < nprob && i >= probs[cur + 1].item0) ++cur;
+      const PropTcProblem& pr = probs[cur];
+      const int end = min(i1, pr.item0 + pr.p.W);
+      const WalkerRun r{i - pr.item0, 1, end - pr.item0};
+      if (mma) {
+        const PropTcParams a = pr.p;   // a register copy: the MMAs' asm would force reloads of a reference
+        switch (pr.cwp) {
+          case 8: go = prop_mma_run<8>(sm, pb.tmem, &pr.mapV, &pr.mapF, a, r, idle, pb.v, pb.f, pb.mma, pb.b, pb.abort_flag, ph_b, ph_v, ph_f, lane); break;
+          case 16: go = prop_mma_run<16>(sm, pb.tmem, &pr.mapV, &pr.mapF, a, r, idle, pb.v, pb.f, pb.mma, pb.b, pb.abort_flag, ph_b, ph_v, ph_f, lane); break;
+          case 24: go = prop_mma_run<24>(sm, pb.tmem, &pr.mapV, &pr.mapF, a, r, idle, pb.v, pb.f, pb.mma, pb.b, pb.abort_flag, ph_b, ph_v, ph_f, lane); break;
+          default: go = prop_mma_run<32>(sm, pb.tmem, &pr.mapV, &pr.mapF, a, r, idle, pb.v, pb.f, pb.mma, pb.b, pb.abort_flag, ph_b, ph_v, ph_f, lane); break;
+        }
+      } else {
+        switch (pr.cwp) {
+          case 8: go = prop_epi_run<8, false>(sm, pb.tmem, pr.p, r, warp, lane, pb.mma, pb.b, pb.e, pb.abort_flag, ph_m, ph_e); break;
+          case 16: go = prop_epi_run<16, false>(sm, pb.tmem, pr.p, r, warp, lane, pb.mma, pb.b, pb.e, pb.abort_flag, ph_m, ph_e); break;
+          case 24: go = prop_epi_run<24, false>(sm, pb.tmem, pr.p, r, warp, lane, pb.mma, pb.b, pb.e, pb.abort_flag, ph_m, ph_e); break;
+          default: go = prop_epi_run<32, false>(sm, pb.tmem, pr.p, r, warp, lane, pb.mma, pb.b, pb.e, pb.abort_flag, ph_m, ph_e); break;
+        }
+      }
+      i = end;
+    }
+  }
+  if (!go && lane == 0) {
+    for (int c = 0; c < nprob; ++c) atomicOr(probs[c].p.status, kStatusTimeout);
+    *pb.abort_flag = 1;
+  }
+  prop_end(pb, tmem_cols, warp);
 }
 
 // ---------------------------------------------------------------------------------------------
