@@ -335,7 +335,8 @@ def stage_rooflines(prec, norb, ncol, naux, nw, stages, fp64_peak=None):
         ach = flops / (per / 1e3) / 1e12
         out[k] = {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                   "peak_source": note, "algorithmic_flops_per_launch": flops, "ms_per_launch": per,
-                  "launches_per_step": cnt / max(1, stages.get("_steps", (1, 1))[0]), "traffic": None}
+                  "launches_per_step": cnt / max(1, stages.get("_steps", (1, 1))[0]),
+                  "traffic": traffic_from_profiles(prec, k)}   # DRAM bytes per launch (ncu), while unchanged
     return out
 
 
