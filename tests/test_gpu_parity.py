@@ -167,6 +167,35 @@ def test_trial_energy_update_parity():
     fixed.close()
 
 
+def test_trial_energy_update_switching():
+    """E_T following the estimate: afqmc_set_etrial overwrites the device value and the next comb
+    replaces it; switching off keeps the value reached; switching on again restarts the running sums
+    (the estimate after the next comb uses only the measurements made since)."""
+    prob = config_small()
+    ctx = _ctx(prob, 32, seed=77)
+    ctx.set_etrial_update(True)
+    h1 = ctx.run(20, energy_every=1, reortho_every=5, comb_every=10)
+    est = np.sum(h1[:, 0]) / np.sum(h1[:, 1])
+    assert abs(ctx.e_trial - est) < 1e-12 * abs(est)
+    ctx.set_etrial(est + 0.25)
+    assert ctx.e_trial == est + 0.25
+    h2 = ctx.run(10, energy_every=1, reortho_every=5, comb_every=10)   # one comb: the running sums win
+    est2 = (np.sum(h1[:, 0]) + np.sum(h2[:, 0])) / (np.sum(h1[:, 1]) + np.sum(h2[:, 1]))
+    assert abs(ctx.e_trial - est2) < 1e-12 * abs(est2)
+    ctx.set_etrial_update(False)
+    ctx.run(10, energy_every=1, reortho_every=5, comb_every=10)
+    assert ctx.e_trial == est2
+    ctx.set_etrial_update(True)   # the sums start again from zero
+    h3 = ctx.run(10, energy_every=1, reortho_every=5, comb_every=10)
+    est3 = np.sum(h3[:, 0]) / np.sum(h3[:, 1])
+    assert abs(ctx.e_trial - est3) < 1e-12 * abs(est3)
+    e_before = ctx.e_trial
+    ctx.local_energy()   # a standalone measurement leaves the sums alone
+    ctx.run(10, energy_every=0, reortho_every=5, comb_every=10)   # a comb with no new measurement
+    assert abs(ctx.e_trial - e_before) < 1e-12 * abs(e_before)
+    ctx.close()
+
+
 def test_qr_parity():
     prob = PROBLEMS["uhf_N13_3_2"]()
     st = _setup(prob)
