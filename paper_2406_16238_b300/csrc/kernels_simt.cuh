@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace afq {
 
@@ -1576,7 +1577,10 @@ __global__ void __launch_bounds__(128, 5) k_overlap_group(const OverlapArgs<R>* 
 
 // ============================================================================
 // Cholesky QR, one CTA per walker: G = psi^H psi accumulated in binary64
-// (Hermitian; products of walker-precision entries are exact in binary64),
+// (Hermitian; products of walker-precision entries are exact in binary64; for
+// binary32 walkers staged in shared memory the sums are compensated binary32
+// dot products (Dot2), as accurate as binary64 accumulation here and several
+// times cheaper on this GPU, then rounded once to binary64),
 // G = R^H R in binary64 with R upper triangular and diag R > 0, then
 // psi <- psi R^-1 (= Q with diag R > 0, the unique thin QR) by forward
 // substitution on each row at the walkers' precision with R rounded once, and
@@ -1645,10 +1649,13 @@ __device__ __forceinline__ void qr_walker(const QrArgs<R> A, const int w) {
       const int m = n - 1 - tid;
       for (int j = tid; j < n; ++j) tri[m * (m + 1) / 2 + (j - tid)] = make_uchar2((unsigned char)tid, (unsigned char)j);
     }
+    constexpr bool kDot2 = std::is_same<R, float>::value;
+    float2* Pf = reinterpret_cast<float2*>(P);   // binary32 staging (Dot2 Gram)
     if (stage_psi) {
       for (int idx = tid; idx < n * N; idx += blockDim.x) {
         const int p = idx / n, j = idx % n;
-        P[(size_t)j * ldp + p] = to_d2(pw[(size_t)p * ncol + j]);
+        if (kDot2) Pf[(size_t)j * ldp + p] = make_float2((float)pw[(size_t)p * ncol + j].x, (float)pw[(size_t)p * ncol + j].y);
+        else P[(size_t)j * ldp + p] = to_d2(pw[(size_t)p * ncol + j]);
       }
     }
     __syncthreads();
@@ -1656,7 +1663,20 @@ __device__ __forceinline__ void qr_walker(const QrArgs<R> A, const int w) {
     for (int e = tid; e < npk; e += blockDim.x) {   // packed upper triangle
       const int i = tri[e].x, j = tri[e].y;
       double re = 0.0, im = 0.0;      // (psi^H psi)_ij = sum_p conj(psi_pi) psi_pj
-      if (stage_psi) {
+      if (kDot2 && stage_psi) {
+        const float2* u = Pf + (size_t)i * ldp;
+        const float2* v = Pf + (size_t)j * ldp;
+        dot2 sr{0.f, 0.f}, si{0.f, 0.f};
+        for (int p = 0; p < N; ++p) {
+          const float2 a = u[p], b = v[p];
+          dot2_add(sr, a.x, b.x);
+          dot2_add(sr, a.y, b.y);
+          dot2_add(si, a.x, b.y);
+          dot2_add(si, -a.y, b.x);
+        }
+        re = dot2_value(sr);
+        im = dot2_value(si);
+      } else if (stage_psi) {
         const double2* u = P + (size_t)i * ldp;
         const double2* v = P + (size_t)j * ldp;
         for (int p = 0; p < N; ++p) {   // four fused multiply-adds per term (no separate products)
