@@ -1578,9 +1578,9 @@ __global__ void __launch_bounds__(128, 5) k_overlap_group(const OverlapArgs<R>* 
 // ============================================================================
 // Cholesky QR, one CTA per walker: G = psi^H psi accumulated in binary64
 // (Hermitian; products of walker-precision entries are exact in binary64; for
-// binary32 walkers staged in shared memory the sums are compensated binary32
-// dot products (Dot2), as accurate as binary64 accumulation here and several
-// times cheaper on this GPU, then rounded once to binary64),
+// binary32 walkers the sums are compensated binary32 dot products (Dot2), as
+// accurate as binary64 accumulation here and several times cheaper on this
+// GPU, then rounded once to binary64),
 // G = R^H R in binary64 with R upper triangular and diag R > 0, then
 // psi <- psi R^-1 (= Q with diag R > 0, the unique thin QR) by forward
 // substitution on each row at the walkers' precision with R rounded once, and
@@ -1685,6 +1685,17 @@ __device__ __forceinline__ void qr_walker(const QrArgs<R> A, const int w) {
           im = fma(u[p].x, v[p].y, im);
           im = fma(-u[p].y, v[p].x, im);
         }
+      } else if (kDot2) {   // binary32 walkers read in place (large N)
+        dot2 sr{0.f, 0.f}, si{0.f, 0.f};
+        for (int p = 0; p < N; ++p) {
+          const R2 a = pw[(size_t)p * ncol + i], b = pw[(size_t)p * ncol + j];
+          dot2_add(sr, (float)a.x, (float)b.x);
+          dot2_add(sr, (float)a.y, (float)b.y);
+          dot2_add(si, (float)a.x, (float)b.y);
+          dot2_add(si, -(float)a.y, (float)b.x);
+        }
+        re = dot2_value(sr);
+        im = dot2_value(si);
       } else {
         for (int p = 0; p < N; ++p) {
           const double2 u = to_d2(pw[(size_t)p * ncol + i]);
