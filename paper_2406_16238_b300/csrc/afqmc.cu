@@ -448,13 +448,14 @@ afqmc_status launch_overlap(afqmc_ctx* c, int mode) {
   StageTimer timer(c, AFQMC_STAGE_OVERLAP);
   const size_t sm = overlap_smem(c->d);
   const bool stg = overlap_stage(c->d);
+  // psi and Phi that do not fit shared memory (large N) are read in place by a wide CTA per walker
   if (c->d.cplx) {
     if (stg) k_overlap_lu<R, true, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
-    else k_overlap_lu<R, false, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+    else k_overlap_lu_wide<R, true><<<c->d.W, 512, sm, c->stream>>>(overlap_args<R>(c, mode));
   } else if (stg) {
     k_overlap_lu<R, true><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
   } else {
-    k_overlap_lu<R, false><<<c->d.W, 128, sm, c->stream>>>(overlap_args<R>(c, mode));
+    k_overlap_lu_wide<R><<<c->d.W, 512, sm, c->stream>>>(overlap_args<R>(c, mode));
   }
   c->thb_valid = c->d.tensor();
   CHECK_LAUNCH(c);
@@ -517,6 +518,9 @@ afqmc_status set_smem_limits(const Dims& d) {
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, true, true>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu<R, false, true>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_chol<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_qr_chol_wide<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu_wide<R>))) != AFQMC_OK) return st_;
+  if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_overlap_lu_wide<R, true>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<4, 2>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<8, 2>))) != AFQMC_OK) return st_;
   if ((st_ = allow_max_dynamic_smem(reinterpret_cast<const void*>(k_propagate_smem<4, 4>))) != AFQMC_OK) return st_;
@@ -766,7 +770,8 @@ template <typename R>
 afqmc_status qr_impl(afqmc_ctx* c) {
   const Dims& d = c->d;
   StageTimer timer(c, AFQMC_STAGE_QR);
-  k_qr_chol<R><<<d.W, 256, qr_smem(d), c->stream>>>(qr_args<R>(c));
+  if (qr_stage_psi(d)) k_qr_chol<R><<<d.W, 256, qr_smem(d), c->stream>>>(qr_args<R>(c));
+  else k_qr_chol_wide<R><<<d.W, 1024, qr_smem(d), c->stream>>>(qr_args<R>(c));   // psi read in place (large N)
   CHECK_LAUNCH(c);
   // Theta = psi (Phi^T psi)^-1 is unchanged by psi -> psi R^-1 (Phi^T psi picks up the same R^-1),
   // so Theta, its bf16 copy and the force bias stay valid; log O was updated by -sum log R_ii.

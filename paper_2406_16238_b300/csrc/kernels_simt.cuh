@@ -1563,6 +1563,11 @@ template <typename R, bool STAGE, bool CPHI = false>
 __global__ void __launch_bounds__(128, 5) k_overlap_lu(OverlapArgs<R> a) {
   overlap_walker<R, STAGE, CPHI>(a, blockIdx.x);
 }
+// Large N (psi and Phi read in place, few walkers per SM): one wide CTA per walker.
+template <typename R, bool CPHI = false>
+__global__ void __launch_bounds__(512, 1) k_overlap_lu_wide(OverlapArgs<R> a) {
+  overlap_walker<R, false, CPHI>(a, blockIdx.x);
+}
 // Several systems in one launch, one block per walker (block b is walker b + base of the list);
 // stage[s]: system s stages psi and Theta in shared memory (the launch's shared memory covers the
 // largest need among its systems).
@@ -1779,6 +1784,11 @@ __device__ __forceinline__ void qr_walker(const QrArgs<R> A, const int w) {
 }
 template <typename R>
 __global__ void __launch_bounds__(256) k_qr_chol(QrArgs<R> a) {
+  qr_walker<R>(a, blockIdx.x);
+}
+// Large N (psi read in place, few walkers per SM): one wide CTA per walker.
+template <typename R>
+__global__ void __launch_bounds__(1024, 1) k_qr_chol_wide(QrArgs<R> a) {
   qr_walker<R>(a, blockIdx.x);
 }
 template <typename R>
