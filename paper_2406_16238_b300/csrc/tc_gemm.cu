@@ -1343,17 +1343,17 @@ size_t plan(TcState* st, int prec, int W, int N, int X, int ncol, const int* c0,
   cur = align256(cur + (size_t)W * 2 * st->vparts * st->kx * 2);
   st->vhs_m_tiles = (2 * W + kBM - 1) / kBM;
   st->vhs_n_tiles = (N * N + 255) / 256;
-  // VHS planes GEMM width: M tiles x N tiles spread over the SMs, cost per tile ~ one k-step's
-  // shared-memory traffic (A: 4 KiB written and read, B: bn x 32 bytes written and read at 128 B
-  // per cycle, 64 + bn / 2 cycles); the width with the smallest busiest-SM cost (the last wave
-  // of a 256-wide tiling can be nearly empty)
+  // VHS planes GEMM width: M tiles x N tiles spread over the SMs; a tile costs about 48 + bn units
+  // (measured at N = 108, X = 432, W = 640 over bn = 128 .. 256: 7.3, 8.8, 10.0, 11.7 and 12.8 us
+  // per wave of tiles); the width with the smallest busiest-SM cost (the last wave of a wide
+  // tiling can be nearly empty, a ragged last column tile costs a full one)
   {
     const long long mt = (st->lt_rows + kBM - 1) / kBM;
     const int sms = num_sms();
     long long best = -1;
     for (int bn : {256, 224, 192, 160, 128}) {
       const long long tiles = mt * ((2LL * W + bn - 1) / bn);
-      const long long cost = ((tiles + sms - 1) / sms) * (64 + bn / 2);
+      const long long cost = ((tiles + sms - 1) / sms) * (48 + bn);
       if (best < 0 || cost < best) { best = cost; st->vhs_bn = bn; }
     }
   }
