@@ -541,6 +541,7 @@ EnergyArgs<R> energy_args(afqmc_ctx* c, double* sums_dev, int* slot, bool run = 
   a.hrot = c->at<void>(c->L.hrot_r);
   a.vbias = c->at<cplx_t<R>>(c->L.vbias);
   a.exch_part = c->at<double2>(c->L.exch_part);
+  a.exch_part_f = c->d.tensor() ? c->at<float2>(c->L.exch_part) : nullptr;   // the tensor-core exchange's format
   a.eloc = c->at<double2>(c->L.eloc);
   a.W = c->d.W;
   a.wgt = c->at<double>(c->L.w);
@@ -572,7 +573,7 @@ afqmc_status energy_impl(afqmc_ctx* c, double* sums_dev, int* slot = nullptr, bo
   if (c->d.prec == AFQMC_PREC_BF16 || c->d.prec == AFQMC_PREC_BF16X3) {
     tc::NormalsJob nj{c->at<double>(c->L.x), c->seed, c->at<unsigned long long>(c->L.step), c->d.W, c->d.X};
     if ((st = tc::exchange(&c->tcs, c->stream, c->at<char>(c->L.tc), c->smul, c->at<float2>(c->L.thetaT),
-                           c->at<float2>(c->L.vbias), c->at<double2>(c->L.exch_part), c->at<int>(c->L.status),
+                           c->at<float2>(c->L.vbias), c->at<float2>(c->L.exch_part), c->at<int>(c->L.status),
                            nullptr, c->d.W, &c->launches, g_err, sizeof(g_err), &nj, c->thb_valid)) != AFQMC_OK)
       return st;
     c->normals_pending = true;   // valid for the next step_impl while the step counter is unchanged
@@ -2340,7 +2341,7 @@ afqmc_status branch_plan(afqmc_batch* b, afqmc_batch::Branch& x) {
     char* tcbuf = c->at<char>(c->L.tc);
     int* status = c->at<int>(c->L.status);
     gs[i] = tc::GroupSystem{&c->tcs, tcbuf, c->smul, c->at<float2>(c->L.thetaT), c->at<float2>(c->L.vbias),
-                            c->at<double2>(c->L.exch_part), status,
+                            c->at<float2>(c->L.exch_part), status,
                             tc::NormalsJob{c->at<double>(c->L.x), c->seed, c->at<unsigned long long>(c->L.step), d.W,
                                            d.X}};
     ps[i] = tc::GroupPropSystem{&c->tcs, tcbuf, c->at<float2>(c->L.psi), c->at<double>(c->L.w), status};

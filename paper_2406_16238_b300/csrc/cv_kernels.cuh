@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(256) k_cv_walker(int N, int X, int ncol, doubl
 // and running sums of E_T (etacc[1], etacc[2]).
 __global__ void __launch_bounds__(256) k_cv_sums(int W, int m, int nchunk, const double* w, const double* a,
                                                  const double* e1, const float* f, const int* sel,
-                                                 const double2* exch_part, double* out, int* slot,
+                                                 const double2* exch_part, const float2* exch_part_f, double* out,
+                                                 int* slot,
                                                  double* etacc) {
   __shared__ double red[32];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, sc = 0.0;
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(256) k_cv_sums(int W, int m, int nchunk, const
     const double wi = w[i];
     if (wi == 0.0) continue;
     double k = 0.0;
-    for (int c = 0; c < nchunk; ++c) k += exch_part[(size_t)j * nchunk + c].x;
+    for (int c = 0; c < nchunk; ++c)
+      k += exch_part_f ? (double)exch_part_f[(size_t)j * nchunk + c].x : exch_part[(size_t)j * nchunk + c].x;
     sc += wi * (0.5 * k - (double)f[i]);
   }
   s0 = block_sum(s0, red);
@@ -252,11 +254,12 @@ __global__ void __launch_bounds__(256) k_cv_sums(int W, int m, int nchunk, const
 }
 
 // Exact K = Re(1/2 sum of exchange partials) of every walker (training targets).
-__global__ void k_exact_k(int W, int nchunk, const double2* exch_part, float* k_out) {
+__global__ void k_exact_k(int W, int nchunk, const double2* exch_part, const float2* exch_part_f, float* k_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= W) return;
   double k = 0.0;
-  for (int c = 0; c < nchunk; ++c) k += exch_part[(size_t)i * nchunk + c].x;
+  for (int c = 0; c < nchunk; ++c)
+    k += exch_part_f ? (double)exch_part_f[(size_t)i * nchunk + c].x : exch_part[(size_t)i * nchunk + c].x;
   k_out[i] = (float)(0.5 * k);
 }
 

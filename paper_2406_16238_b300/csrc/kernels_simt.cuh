@@ -326,7 +326,8 @@ struct EnergyArgs {
   const cplx_t<R>* thetaT;
   const void* hrot;           // htilde: real [ncol][N] at the walkers' precision, or complex (CH)
   const cplx_t<R>* vbias;
-  const double2* exch_part;
+  const double2* exch_part;   // binary64 partials (CUDA-core exchange), or
+  const float2* exch_part_f;  // binary32 partials (tensor-core exchange), when non-null
   double2* eloc;
   int W;
   const double* wgt;
@@ -345,6 +346,7 @@ __device__ __forceinline__ void energy_walker(const EnergyArgs<R> A, const int w
   const void* hrot_v = A.hrot;
   const cplx_t<R>* vbias = A.vbias;
   const double2* exch_part = A.exch_part;
+  const float2* exch_part_f = A.exch_part_f;
   double2* eloc = A.eloc;
   const double* wgt = A.wgt;
   const double* wph = A.wph;
@@ -397,7 +399,7 @@ __device__ __forceinline__ void energy_walker(const EnergyArgs<R> A, const int w
   v[3] = ji;
   double kr = 0.0, ki = 0.0;
   for (int c = tid; c < nchunk; c += 256) {
-    const double2 e = exch_part[(size_t)w * nchunk + c];
+    const double2 e = exch_part_f ? to_d2(exch_part_f[(size_t)w * nchunk + c]) : exch_part[(size_t)w * nchunk + c];
     kr += e.x;
     ki += e.y;
   }

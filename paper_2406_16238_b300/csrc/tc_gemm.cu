@@ -73,7 +73,7 @@ struct Params {
   int vbias_add;   // staged epilogue: 0 store, 1 add (second spin block), 2 atomic add (grouped launch)
   float smul;
   float2* vbias;
-  double2* exch_part;
+  float2* exch_part;   // binary32 partials (the epilogue's sums are binary32)
   // store epilogue
   float* out;
   long long ldo;
@@ -211,7 +211,7 @@ __device__ void exchange_tile(const Params& p, int mt, int nt, uint32_t tacc, co
         const float sr = (e.red[0].x + e.red[1].x) + (e.red[2].x + e.red[3].x);
         const float si = (e.red[0].y + e.red[1].y) + (e.red[2].y + e.red[3].y);
         p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + 4 * mt + lane] =
-            lane == 0 ? make_double2((double)(p.smul * sr), (double)(p.smul * si)) : make_double2(0.0, 0.0);
+            lane == 0 ? make_float2(p.smul * sr, p.smul * si) : make_float2(0.f, 0.f);
       }
     }
     if (v + p.g.epi_groups < p.wpt) named_bar(bar_id, 128);   // buffers reused by the next walker
@@ -309,8 +309,7 @@ __device__ void exchange_tile_reg(const Params& p, int mt, int nt, uint32_t tacc
     }
     const int w = nt * p.wpt + v;
     if (lane == 0 && w < p.W)
-      p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + 4 * mt + wig] =
-          make_double2((double)(p.smul * er), (double)(p.smul * ei));
+      p.exch_part[(size_t)w * p.nchunk + p.chunk_offset + 4 * mt + wig] = make_float2(p.smul * er, p.smul * ei);
     if (p.vbias && live && w < p.W && (lane == 31 || a == n - 1))   // last row of the block within this warp
       atomicAdd(p.vbias + (size_t)w * p.X + mt * p.gpt + g, make_float2(p.smul * dg.x, p.smul * dg.y));
   }
@@ -1547,7 +1546,7 @@ afqmc_status finish(TcState* st, char* tcbuf, char* err, size_t errlen) {
 }
 
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
-                      double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
+                      float2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
                       char* err, size_t errlen, const NormalsJob* nj, bool theta_ready) {
   int chunk = 0;
   bool first = true;

@@ -124,7 +124,7 @@ struct NormalsJob {
 // nj (optional): the first launch also draws those normals.  theta_ready: the bf16 operand copy of
 // Theta^T (every walker, in walker order) is already current, so it is not rebuilt (ignored with widx).
 afqmc_status exchange(TcState* st, cudaStream_t s, char* tcbuf, double smul, const float2* thetaT, float2* vbias,
-                      double2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
+                      float2* exch_part, int* status, const int* widx, int nw, unsigned long long* launches,
                       char* err, size_t errlen, const NormalsJob* nj = nullptr, bool theta_ready = false);
 
 // VHS planar fp32: out[w][0][pq] + i out[w][1][pq] = sum_g coef[w][g] L^g_pq, coef complex64 [W][X].
@@ -165,7 +165,7 @@ struct GroupSystem {
   double smul;
   const float2* thetaT;   // exchange: Theta^T complex64 [W][ncol][N]
   float2* vbias;          // exchange: cleared before the launch, every block adds its traces
-  double2* exch_part;
+  float2* exch_part;      // exchange: binary32 partials
   int* status;
   NormalsJob nj;          // exchange: the step's normals (nj.x == nullptr: none)
 };
