@@ -208,9 +208,11 @@ afqmc_status afqmc_run(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int
 
 /* As afqmc_run, without synchronising: every measurement's four sums are copied to
  * energies_host + 4 k (k = 0, 1, ... in order) by an asynchronous copy enqueued right after its
- * step (use page-locked memory for the copies to overlap; energies_host must hold 4 sums per
- * measurement, and may be NULL only when energy_every <= 0).  The values are there once the stream
- * has reached that point (afqmc_synchronize or any stream synchronisation).  nmeas (may be NULL)
+ * step (with CUDA graphs on a private copy stream, so the next step does not wait for the copy;
+ * the context's stream waits for the copies before the call returns: work enqueued on it later is
+ * ordered after them).  Use page-locked memory for the copies to overlap; energies_host must hold 4
+ * sums per measurement, and may be NULL only when energy_every <= 0.  The values are there once
+ * the stream has reached the end of the call (afqmc_synchronize or any stream synchronisation).  nmeas (may be NULL)
  * receives the number of measurements at once.  Device-side conditions are reported by the next
  * synchronising call. */
 afqmc_status afqmc_run_async(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_every, int32_t reortho_every,

@@ -256,6 +256,11 @@ struct afqmc_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool join_pending = false;
+  // afqmc_run_async's per-measurement copies to the caller's host array run on `copy_stream`
+  // (after each step graph, off the main stream; the main stream waits for them only before the
+  // device history is reused and at the end of the call)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copy = nullptr, ev_copied = nullptr;
   // the tensor-core exchange draws the current step's normals into L.x with a spare warp (its
   // binary64 work overlaps the contraction); the next fields kernel uses them instead of drawing
   bool normals_pending = false;
@@ -284,6 +289,9 @@ struct afqmc_ctx {
     if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (ev_copy) cudaEventDestroy(ev_copy);
+    if (ev_copied) cudaEventDestroy(ev_copied);
     for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : free_events) cudaEventDestroy(e);
   }
@@ -1634,18 +1642,36 @@ afqmc_status afqmc_run_async(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_ever
   int used = 0, total = 0;
   double* hist = ctx->at<double>(ctx->L.hist);
   const bool graphs = ctx->graphs_on && !ctx->prof;
+  if (graphs && energy_every > 0 && !ctx->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+  }
+  bool copies = false;   // copies enqueued on copy_stream that the main stream has not waited for
+  auto wait_copies = [&]() -> afqmc_status {
+    if (!copies) return AFQMC_OK;
+    CU(cudaEventRecord(ctx->ev_copied, ctx->copy_stream));
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied, 0));
+    copies = false;
+    return AFQMC_OK;
+  };
   if (graphs) CU(cudaMemsetAsync(ctx->base + ctx->L.slot, 0, sizeof(int), ctx->stream));
   for (int s = 0; s < nsteps; ++s) {
     const bool energy = energy_every > 0 && ctx->host_step % (unsigned long long)energy_every == 0;
-    if (energy && used == kHistory - 1) {   // the device history wraps; earlier copies are ordered before
+    if (energy && used == kHistory - 1) {   // the device history wraps: its copies come first
       used = 0;
+      if ((st = wait_copies()) != AFQMC_OK) return st;
       if (graphs) CU(cudaMemsetAsync(ctx->base + ctx->L.slot, 0, sizeof(int), ctx->stream));
     }
     if (graphs) {
       if ((st = graph_step(ctx, energy)) != AFQMC_OK) return st;
-      if (energy)   // after the step graph, which joins the estimator's branch
+      if (energy) {   // after the step graph, which joins the estimator's branch; off the main stream
+        CU(cudaEventRecord(ctx->ev_copy, ctx->stream));
+        CU(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_copy, 0));
         CU(cudaMemcpyAsync(energies_host + 4 * (size_t)total, hist + 4 * used, 4 * sizeof(double),
-                           cudaMemcpyDeviceToHost, ctx->stream));
+                           cudaMemcpyDeviceToHost, ctx->copy_stream));
+        copies = true;
+      }
     } else {
       if (energy &&
           (st = DISPATCH(ctx, energy_impl, hist + 4 * used, nullptr, true, energies_host + 4 * (size_t)total, true)) !=
@@ -1659,6 +1685,7 @@ afqmc_status afqmc_run_async(afqmc_ctx* ctx, int32_t nsteps, int32_t energy_ever
     if (comb_every > 0 && ctx->host_step % (unsigned long long)comb_every == 0)
       if ((st = graphs ? graph_comb(ctx) : DISPATCH(ctx, comb_impl)) != AFQMC_OK) return st;
   }
+  if ((st = wait_copies()) != AFQMC_OK) return st;   // the main stream's work after this call sees them
   if (nmeas) *nmeas = total;
   return AFQMC_OK;
 }
