@@ -1,11 +1,11 @@
-// Error-free transformations on binary32 (Knuth's TwoSum, Dekker's FastTwoSum, TwoProduct by the
-// FMA) and the compensated dot product built on them (Ogita, Rump and Oishi, "Accurate sum and dot
-// product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): a sum of products of binary32 numbers
-// computed as if in twice the working precision and then rounded.  On this GPU binary32 runs on
-// every lane at full rate while a binary64 instruction occupies its sub-partition's pipe for about
-// 64 cycles, so long binary64 accumulations of binary32 products (the Gram matrix of the QR) are
-// formed this way.  Every step uses round-to-nearest intrinsics, so the compiler cannot contract
-// or reassociate the transformations.
+// Error-free transformations on binary32 (Knuth's TwoSum, TwoProduct by the FMA) and the
+// compensated dot product built on them (Ogita, Rump and Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26 (2005), algorithm Dot2): a sum of products of binary32 numbers computed
+// as if in twice the working precision and then rounded.  On this GPU binary32 runs on every lane
+// at full rate while a binary64 instruction occupies its sub-partition's pipe for about 64 cycles,
+// so long binary64 accumulations of binary32 products (the Gram matrix of the QR) are formed this
+// way.  Every step uses round-to-nearest intrinsics, so the compiler cannot contract or
+// reassociate the transformations.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,11 +22,6 @@ __device__ __forceinline__ ff ff_two_sum(float a, float b) {
   const float bb = __fsub_rn(s, a);
   const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
   return ff{s, e};
-}
-// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker's FastTwoSum)
-__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 // p + e = a b exactly (barring underflow): the FMA returns the rounding error of the product
 __device__ __forceinline__ ff ff_two_prod(float a, float b) {
